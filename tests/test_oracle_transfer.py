@@ -1,0 +1,207 @@
+"""Pins for the oracle's Lagrangian-Eulerian transfers and springs.
+
+* Eq. (discrForceCouple): total spread force equals the node force times the
+  discrete unity sum; springs obey Newton's third law, so a spring network
+  spreads (nearly) zero total force; the three-node example of Fig. 3.
+* Spreading and interpolation with the same width are adjoint in the h^D
+  inner product, for any positions (including the wall truncation rule).
+* Eq. (discrVelCouple) with phi1 and width h reproduces linear fields.
+* Eq. (ViscExp): mu = mu_max at a node lying on a grid point (Fig. 4 setup).
+* Eq. (springF), Eq. (defineK): two-node tension and the breaking rule.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1302_3663_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def grid2(n=(32, 16), periodic=(1, 0), h=1.0 / 32, **kw):
+    return W.base_params(2, n, periodic, 0, h, **kw)
+
+
+def grid3(n=(8, 8, 16), periodic=(0, 0, 1), h=1.0 / 8, **kw):
+    return W.base_params(3, n, periodic, 2, h, **kw)
+
+
+def coords(o, stag, level=0):
+    n, s = o.dims(level)
+    h = o.prm["h"] * 2 ** level
+    ax = []
+    for a in range(o.dim):
+        ax.append((np.arange(s[a]) + 0.5 * stag[a]) * h)
+    return ax
+
+
+def inner(o, a, b):
+    return float((a * b).sum()) * o.prm["h"] ** o.dim
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("width", ["omega", "h"])
+def test_spread_interp_adjoint(dim, width):
+    prm = grid2(omega=0.021, omega_mu=0.021) if dim == 2 else grid3(omega=0.2, omega_mu=0.2)
+    o = O.Oracle(prm)
+    rng = np.random.default_rng(7 + dim)
+    L = [prm["n"][a] * prm["h"] for a in range(dim)]
+    X = rng.uniform(0, 1, size=(40, dim)) * np.array(L)
+    X[:5, 1] = rng.uniform(0, 0.6 * prm["h"], 5)      # hugging the y = 0 wall
+    X[5:8, 0] = L[0] - rng.uniform(0, prm["h"], 3)    # near the upper x boundary
+    o.set_nodes(X)
+    w = prm["omega"] if width == "omega" else prm["h"]
+    F = rng.normal(size=40)
+    kinds = [0, 1, O.KIND_CELL] + ([2, O.KIND_EDGE[(0, 2)], O.KIND_EDGE[(1, 2)]] if dim == 3 else [])
+    kinds.append(O.KIND_EDGE[(0, 1)])
+    for kind in kinds:
+        u = rng.normal(size=o.shape())
+        lhs = inner(o, o.spread_sum(kind, F, w), u)
+        rhs = float((F * o.interp(kind, u, w)).sum())
+        assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + abs(rhs) + 1e-300) + 1e-15
+
+
+def test_interp_linear_exact_phi1():
+    prm = grid2(n=(32, 32), periodic=(1, 1), phi_kind=1)
+    o = O.Oracle(prm)
+    rng = np.random.default_rng(1)
+    X = rng.uniform(0.2, 0.8, size=(20, 2))
+    o.set_nodes(X)
+    h = prm["h"]
+    for kind, stag in ((0, (0, 1)), (1, (1, 0)), (O.KIND_CELL, (1, 1))):
+        xs, ys = coords(o, stag)
+        u = 0.3 + 1.7 * xs[None, :] - 0.9 * ys[:, None]
+        U = o.interp(kind, u, h)
+        assert np.max(np.abs(U - (0.3 + 1.7 * X[:, 0] - 0.9 * X[:, 1]))) < 1e-13
+
+
+def test_interp_constant_exact_phi2():
+    prm = grid2(n=(32, 32), periodic=(1, 1), phi_kind=2)
+    o = O.Oracle(prm)
+    X = np.random.default_rng(2).uniform(0, 1, size=(20, 2))
+    o.set_nodes(X)
+    U = o.interp(0, np.full(o.shape(), 2.25), prm["h"])
+    assert np.max(np.abs(U - 2.25)) < 1e-14
+
+
+def test_fig3_three_node_force_example():
+    g = json.load(open(os.path.join(GOLD, "fig3_force_example.json")))
+    Xs = [eval(e, {"pi": math.pi}) for e in g["X_expr"]]
+    F = np.array(g["F"])
+    assert abs(F.sum()) == 0.0
+    totals = []
+    for h in g["h"]:
+        n = int(round(1.0 / h))
+        prm = grid2(n=(n, n), periodic=(1, 1), h=h, omega=g["omega"])
+        o = O.Oracle(prm)
+        X = np.array([[x, 0.5] for x in Xs])
+        o.set_nodes(X)
+        f = o.spread_sum(0, F, g["omega"])
+        totals.append(abs(f.sum()) * h * h)
+        # the spread force is a sum of three bumps of widths 4 omega
+        xs, ys = coords(o, (0, 1))
+        assert np.all(f[:, (xs < Xs[0] - 2 * g["omega"]) | (xs > Xs[2] + 2 * g["omega"])] == 0.0)
+    # Fig. 3: finer grids represent the node forces more accurately; the total
+    # tends to sum F = 0
+    assert totals[-1] < 1e-3 * np.abs(F).sum()
+    assert totals[-1] < totals[0]
+
+
+def test_spring_network_spreads_zero_force_phi1_exact():
+    # Newton's third law per spring + phi1 unity with omega = 2h: zero net force
+    prm = grid2(n=(64, 64), periodic=(1, 1), h=1.0 / 64, phi_kind=1, omega=2.0 / 64,
+                omega_mu=2.0 / 64)
+    o = O.Oracle(prm)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(0.3, 0.7, size=(60, 2))
+    ab, rest = W.springs_within(X, 0.08)
+    o.set_nodes(X + rng.normal(scale=0.003, size=X.shape))
+    o.set_springs(ab, rest, np.full(len(rest), 2.0), np.full(len(rest), 5.0))
+    o.refresh()
+    Fn = o.node_forces()
+    assert np.abs(Fn).max() > 1e-4
+    assert np.abs(Fn.sum(axis=0)).max() < 1e-14 * np.abs(Fn).sum()
+    for d in range(2):
+        f = o.get("force", d)
+        assert abs(f.sum() * prm["h"] ** 2) < 1e-13 * np.abs(Fn).sum()
+
+
+def test_fig4_mu_max_at_node_on_grid_point():
+    g = json.load(open(os.path.join(GOLD, "fig4_viscosity_example.json")))
+    Xs = [eval(e, {"pi": math.pi}) for e in g["X_expr"]]
+    for h in g["h"]:
+        n = int(round(1.0 / h))
+        prm = grid2(n=(n, n // 2), periodic=(1, 0), h=h, omega=g["omega"], omega_mu=g["omega"],
+                    mu_ratio=100.0)
+        o = O.Oracle(prm)
+        y0 = 0.25  # a grid line for every h in the list
+        o.set_nodes(np.array([[x, y0] for x in Xs]))
+        mu_out, mu_max = prm["mu_f"], prm["mu_f"] * prm["mu_ratio"]
+        me = o.spread_max(O.KIND_EDGE[(0, 1)], g["omega"], mu_out, mu_max)
+        i, j = int(round(Xs[0] / h)), int(round(y0 / h))
+        assert abs(me[j, i] - mu_max) <= 1e-14 * mu_max
+        assert me.min() == mu_out and me.max() <= mu_max * (1 + 1e-14)
+        mc = o.spread_max(O.KIND_CELL, g["omega"], mu_out, mu_max)
+        assert mc.max() < mu_max and mc.min() == mu_out
+
+
+def two_node(dist, rest, K=3.0, brk=0.5, periodic=(1, 1), n=(32, 32)):
+    prm = grid2(n=n, periodic=periodic)
+    o = O.Oracle(prm)
+    X = np.array([[0.375, 0.5], [0.375 + dist[0], 0.5 + dist[1]]])
+    o.set_nodes(X)
+    o.set_springs(np.array([[0, 1]]), np.array([rest]), np.array([K]), np.array([brk]))
+    o.refresh()
+    return o
+
+
+def test_spring_tension_closed_form():
+    d = np.array([0.03, 0.04])  # length 0.05
+    o = two_node(d, rest=0.04, K=3.0)
+    F = o.node_forces()
+    T = 3.0 * (0.05 - 0.04)
+    assert np.allclose(F[0], T * d / 0.05, rtol=0, atol=1e-15)
+    assert np.allclose(F[1], -T * d / 0.05, rtol=0, atol=1e-15)
+    # compressed spring pushes the nodes apart
+    o = two_node(d, rest=0.06, K=3.0)
+    assert np.dot(o.node_forces()[0], d) < 0
+
+
+def test_spring_breaks_beyond_threshold_and_stays_broken():
+    # Sec. 3.2: springs break when stretched beyond (1 + eps_b) of the rest length
+    o = two_node(np.array([0.061, 0.0]), rest=0.04, brk=0.5)  # 1.525 r > 1.5 r
+    ids, steps = o.broken()
+    assert list(ids) == [0] and list(steps) == [0]
+    assert np.all(o.node_forces() == 0.0)
+    o.set_nodes(np.array([[0.4, 0.5], [0.44, 0.5]]))   # back to rest: still broken
+    o.refresh()
+    assert np.all(o.node_forces() == 0.0)
+    assert len(o.broken()[0]) == 1
+    o2 = two_node(np.array([0.0595, 0.0]), rest=0.04, brk=0.5)
+    assert len(o2.broken()[0]) == 0
+
+
+def test_spring_minimum_image_across_periodic_axis():
+    prm = grid2(n=(32, 16), periodic=(1, 0))
+    o = O.Oracle(prm)
+    X = np.array([[0.99, 0.2], [0.02, 0.2]])       # 0.03 apart through x = 1
+    o.set_nodes(X)
+    o.set_springs(np.array([[0, 1]]), np.array([0.02]), np.array([1.0]), np.array([1.0]))
+    o.refresh()
+    F = o.node_forces()
+    assert abs(F[0, 0] - 0.01) < 1e-15 and abs(F[1, 0] + 0.01) < 1e-15
+    assert len(o.broken()[0]) == 0
+
+
+def test_paper_break_rule_twice_rest_length():
+    # Eq. (defineK): K = F_max / r and eps_b = 1 give tension F_max at 2 r
+    Fmax, r = 0.75, 1.0 / 32   # binary-exact, so that |d| is exactly 2 r
+    o = two_node(np.array([2 * r, 0.0]), rest=r, K=Fmax / r, brk=1.0)
+    assert len(o.broken()[0]) == 0
+    assert abs(np.linalg.norm(o.node_forces()[0]) - Fmax) < 1e-14
+    o = two_node(np.array([2 * r * (1 + 1e-9), 0.0]), rest=r, K=Fmax / r, brk=1.0)
+    assert len(o.broken()[0]) == 1
