@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: cell-steps per second of the biofilm IBM time step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3]
+                    [--impl ours|reference]
+
+One step is one full time step of the method (momentum right-hand side,
+viscous multigrid solve, divergence, pressure multigrid solve, projection,
+interpolation and node move, springs, spreads, coefficient hierarchy) on the
+chosen synthetic workload, replayed from a CUDA graph. ``value`` is
+(cells x steps x ranks) / device time with every input resident on the GPU;
+``e2e`` repeats the run through the public C ABI from host buffers (context
+creation and node/spring upload included, node positions read back after
+every step, fields read back at the end). Multi-GPU runs are independent
+replicas (a single simulation does not shard): one process per GPU under
+torchrun, max-over-ranks time.
+
+``--impl reference`` times the FP64 CPU oracle (OpenMP, all host cores) on the
+same workload and prints the same JSON line with "impl": "reference".
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s & V-cycle HBM roofline frac; served p50/p99 step latency vs FP64"
+UNIT = "cell-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="c3")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0: FP64; 1: FP32 V-cycles in FP64 defect correction")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_workload(name, precision):
+    from paper_1302_3663_gb300 import workloads as W
+    inst = W.CONFIGS[name]()
+    if precision is not None:
+        inst["params"]["precision"] = precision
+    return inst
+
+
+def describe(inst):
+    from paper_1302_3663_gb300 import workloads as W
+    p = inst["params"]
+    n = p["n"][:p["dim"]]
+    prec = "fp64" if p.get("precision", 0) == 0 else "fp32 V-cycles in fp64 defect correction"
+    vc = ("%d viscous + %d pressure V(%d,%d) cycles per step" %
+          (p["vc_visc"], p["vc_p"], p["nu1"], p["nu2"]) if p["vc_visc"] > 0
+          else "V-cycles to relative residual %.0e" % p["rtol"])
+    return {
+        "workload": "%s: %s grid, %d nodes, %d springs, density ratio %g, viscosity ratio %g"
+                    % (inst["name"], "x".join(map(str, n)), inst["X"].shape[0],
+                       inst["ab"].shape[0], p["rho_ratio"], p["mu_ratio"]),
+        "cells": W.cells(p),
+        "precision": prec,
+        "solver": vc,
+        "dt": p["dt"],
+        "parallelism": "replicas (one independent simulation per GPU)",
+    }
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(world, v):
+    import torch
+    if world == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def alg_bytes_visc_launch(dim, cells):
+    # one colour of one component: u_d (read + write), rhs_d, m_d, mu_c, and
+    # per other axis one edge-mu array and one cross component: (5 + 2(D-1)) x
+    # 8 B per cell for a full sweep, half of it per colour
+    return (5 + 2 * (dim - 1)) * 8 * cells / 2.0
+
+
+def cpu_baseline(inst, max_seconds=30.0):
+    """The oracle as it stands, on the host cores: one time step of the same
+    workload (a bounded sample), cell-steps per second."""
+    from oracle import oracle as O
+    from paper_1302_3663_gb300 import workloads as W
+    prm = dict(inst["params"], precision=0)
+    o = O.Oracle(prm, omp=True)
+    o.set_nodes(inst["X"])
+    o.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+    o.refresh()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > max_seconds / 2 or steps >= 3:
+            break
+    cells = W.cells(prm)
+    return {"value": cells * steps / el, "unit": UNIT, "cores": O.num_threads(True),
+            "kind": "oracle",
+            "sample": "%d full time step(s) of %s in FP64 (OpenMP oracle, %.1f s)"
+                      % (steps, inst["name"], el)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+
+    world, rank, local = dist_setup(args)
+    inst = load_workload(args.config, args.precision)
+    prm = inst["params"]
+    cells = W.cells(prm)
+    stream = torch.cuda.Stream()
+    ctx = bfibm.load_instance(inst, stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    launches = ctx.launches_per_step()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        ctx.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    barrier(world)
+    ms = max_over_ranks(world, e0.elapsed_time(e1))
+    value = cells * args.steps * world / (ms / 1e3)
+    st = ctx.get_stats()
+
+    # dominant kernel: viscous red-black sweep on the finest grid, timed alone
+    sweeps = 10
+    ctx.smooth_viscous(0, 2, sync=True)
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    ctx.smooth_viscous(0, sweeps, sync=False)
+    k1.record(stream)
+    k1.synchronize()
+    nlaunch = sweeps * 2 * prm["dim"]
+    launch_s = k0.elapsed_time(k1) / 1e3 / nlaunch
+    peak, peak_src = measured_peak()
+    alg = alg_bytes_visc_launch(prm["dim"], cells)
+    achieved = alg / launch_s / 1e9
+    roof = {"kernel": "k_v_rbgs (viscous red-black sweep, one colour of one component, "
+                      "finest grid)",
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "alg_bytes_per_launch": alg, "launch_us": round(launch_s * 1e6, 2),
+            "peak_source": peak_src}
+    ctx.close()
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prm.get("precision", 0) == 0 else "f64+f32",
+           "data": "synthetic (seeded mounds standing in for the measured S. epidermidis "
+                   "coordinates)",
+           "config": dict(describe(inst), l2="working set larger than L2 (%.2f GB of grids); "
+                          "no flush" % (bfibm.footprint(prm, inst['X'].shape[0],
+                                                        inst['ab'].shape[0]) / 1e9)),
+           "roofline": roof, "clocks": clk.summary(),
+           "gpu_launches": launches * args.steps if launches > 0 else None,
+           "final_stats": {"div_max": st["div_max"], "kinetic": st["kinetic"],
+                           "broken": st["broken_total"]}}
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(inst, args, world, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(inst)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_e2e(inst, args, world, stream):
+    """The same run through the public API from host buffers."""
+    import numpy as np
+    import torch
+
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+    prm = inst["params"]
+    cells = W.cells(prm)
+    eta, dim = inst["X"].shape
+    pinned = torch.empty((eta, dim), dtype=torch.float64, pin_memory=True).numpy()
+    Xh = torch.empty((eta, dim), dtype=torch.float64, pin_memory=True).numpy()
+    Xh[:] = inst["X"]
+    barrier(world)
+    t0 = time.perf_counter()
+    ctx = bfibm.Context(prm, stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.set_nodes(Xh)
+    ctx.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+    for k in range(args.steps):
+        ctx.step(1)
+        ctx.get_nodes(pinned)
+    fields = [ctx.get_velocity(d) for d in range(dim)] + [ctx.get_pressure()]
+    ctx.close()
+    el = time.perf_counter() - t0
+    el = max_over_ranks(world, el)
+    h2d = (Xh.nbytes + inst["ab"].nbytes + 3 * inst["rest"].nbytes) / args.steps
+    d2h = pinned.nbytes + sum(f.nbytes for f in fields) / args.steps
+    return {"value": cells * args.steps * world / el, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "note": "context creation, node/spring upload, every step's node positions "
+                    "read back, final u and p read back; wall clock"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1302_3663_gb300 import workloads as W
+    inst = load_workload(args.config, 0)
+    prm = inst["params"]
+    cells = W.cells(prm)
+    o = O.Oracle(prm, omp=True)
+    o.set_nodes(inst["X"])
+    o.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+    o.refresh()
+    # each step is one full oracle time step of the workload; the count is
+    # bounded so that the whole run stays within a few minutes
+    t_one = time.perf_counter()
+    o.step(1)
+    t_one = time.perf_counter() - t_one
+    budget = 150.0
+    k_timed = max(1, min(args.steps, int(budget / max(t_one, 1e-3)) - args.warmup))
+    k_warm = max(0, min(args.warmup - 1, int(budget / max(t_one, 1e-3)) - k_timed - 1))
+    o.step(k_warm)
+    t0 = time.perf_counter()
+    o.step(k_timed)
+    el = time.perf_counter() - t0
+    value = cells * k_timed / el
+    cores = O.num_threads(True)
+    sample = ("%d timed oracle time steps of %s (after %d warm-up), FP64, OpenMP"
+              % (k_timed, inst["name"], k_warm + 1))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": world, "steps": k_timed, "warmup": k_warm + 1,
+           "ms_per_step": el / k_timed * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": describe(inst),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

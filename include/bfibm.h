@@ -1,0 +1,211 @@
+/*
+ * bfibm.h -- C ABI of the GB300 biofilm immersed-boundary time step.
+ *
+ * One context holds one simulation of the method of Hammond et al.,
+ * arXiv:1302.3663: incompressible Navier-Stokes with variable density and
+ * viscosity on a staggered grid (Eq. NSdis1-1, Eq. NSdis2-NSdis4), solved by
+ * red-black multigrid (Sec. 3.5), coupled to Lagrangian nodes through the
+ * width-omega delta of Eq. (Dirac Delta Approx) and joined by breakable
+ * Hookean springs (Eq. springF, Sec. 3.2). All arithmetic runs in CUDA
+ * kernels on the device that was current when the context was created.
+ *
+ * Conventions
+ *   - Every function returns a bfibm_status and never aborts. After a CUDA
+ *     error the context is poisoned: later calls return BFIBM_ESTATE.
+ *     bfibm_last_error() gives the message of the last failure.
+ *   - Host pointers are caller-owned. Inputs are copied before the call
+ *     returns; outputs are written before the call returns (the call
+ *     synchronises the context's stream when it reads data back).
+ *   - Work is queued on the context's stream: the stream given to
+ *     bfibm_create, or a stream the library creates when that is NULL.
+ *   - One context is used by one host thread at a time.
+ *
+ * Grid layout shared by every field exchanged through this interface
+ *   - n[a] cells of width h along axis a (n[2] = 1 when dim == 2). Axis a is
+ *     periodic or bounded by no-slip walls at 0 and n[a] h.
+ *   - A field is exchanged as a dense array of extents s[a] = n[a] + 1 along
+ *     each wall axis and s[a] = n[a] along each periodic axis, x fastest
+ *     (C order [s2][s1][s0]). Index i along axis a is the point at i h for a
+ *     face/edge axis of that field and (i + 1/2) h for a centre axis.
+ *   - Pressure p sits at cell centres (entries with some index i_a == n_a are
+ *     unused, returned as 0). Velocity component d sits on the d-faces; the
+ *     faces on walls (i_d = 0 and n_d) hold 0. mu_de sits on the (d,e)-edges.
+ */
+#ifndef BFIBM_H
+#define BFIBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bfibm_ctx bfibm_ctx;
+
+typedef enum {
+  BFIBM_OK = 0,
+  BFIBM_EINVAL = 1,   /* bad argument; nothing changed */
+  BFIBM_ENOMEM = 2,   /* device or host allocation failed; nothing changed */
+  BFIBM_ECUDA = 3,    /* a CUDA call failed; the context is poisoned */
+  BFIBM_ENOCONV = 4,  /* relative-residual mode hit max_cycles; state is valid */
+  BFIBM_ETIMEOUT = 5, /* a bounded device wait gave up; the context is poisoned */
+  BFIBM_ESTATE = 6    /* the context is poisoned or not ready for the call */
+} bfibm_status;
+
+/* Parameters (model units). Eq. (N-SnondimFull): sigma = Strouhal number,
+   euler = Euler number, inv_re = 1/Re, c_force = L f0 / (rho0 u0^2). */
+typedef struct {
+  int32_t dim;            /* 2 or 3 */
+  int32_t n[3];           /* cells per axis; n[2] = 1 when dim == 2; each >= 2 */
+  int32_t periodic[3];    /* 1: periodic axis, 0: no-slip walls */
+  int32_t flow_axis;      /* axis of the body force */
+  int32_t phi_kind;       /* 1: Eq. (PhiPeskin), 2: Eq. (PhiCosAlternative) */
+  int32_t mg_levels_max;  /* multigrid levels (Sec. 4.3.1: at most 6 help) */
+  int32_t nu1, nu2;       /* pre/post red-black sweeps per level */
+  int32_t vc_visc, vc_p;  /* > 0: fixed V-cycles per solve; 0: until rtol */
+  int32_t max_cycles;     /* cap in rtol mode */
+  int32_t coarse_sweeps;  /* red-black sweeps on the coarsest grid */
+  int32_t precision;      /* 0: FP64 throughout; 1: FP32 V-cycles inside FP64
+                             defect correction (fine residual, divergence and
+                             coarsest solve stay FP64) */
+  double h;               /* mesh width, equal on every axis */
+  double rho_f, mu_f;     /* fluid density and viscosity */
+  double rho_ratio;       /* biofilm density ratio: rho_b = (rho_ratio - 1) rho_f */
+  double mu_ratio;        /* mu_max = mu_ratio * mu_f, Eq. (ViscExp) */
+  double omega;           /* delta width for f and rho, Eq. (discrForceCouple/DensCouple) */
+  double omega_mu;        /* delta width in Eq. (ViscExp) */
+  double d0_vol;          /* d0^D, mean volume per node, Eq. (discrDensCouple) */
+  double dt, sigma, euler, inv_re, c_force;
+  double body_force;      /* G along flow_axis, used when u_center <= 0 */
+  double u_center;        /* > 0: G chosen so the laminar centreline speed is u_center */
+  double ic_scale;        /* initial velocity = ic_scale * laminar profile */
+  double rtol;            /* relative residual target (Sec. 4.1 uses 1e-9) */
+  double gamma_coarse;    /* gamma of Eq. (ViscCoarseGrid) on every coarse level */
+} bfibm_params;
+
+typedef struct {
+  int32_t cycles_visc, cycles_p;     /* V-cycles used by the last solves */
+  int32_t broken_total;              /* springs broken so far */
+  int32_t clamped_total;             /* node moves clamped back onto a wall */
+  double res_visc, res_p;            /* last relative residuals (0 if not collected) */
+  double div_max;                    /* max |D.u| of the current velocity */
+  double kinetic;                    /* sum over faces of u_d^2 h^D (Sec. 4.3.4) */
+  int64_t step;                      /* completed time steps */
+} bfibm_stats;
+
+/* Field selectors for bfibm_get_field / bfibm_set_field (see layout above). */
+enum {
+  BFIBM_F_U = 0,       /* velocity u^n, component comp (level 0 only) */
+  BFIBM_F_UT = 1,      /* viscous multigrid iterate (level 0: u~), component comp */
+  BFIBM_F_URHS = 2,    /* viscous right-hand side, component comp */
+  BFIBM_F_P = 3,       /* pressure multigrid iterate (level 0: p) */
+  BFIBM_F_PRHS = 4,    /* pressure right-hand side */
+  BFIBM_F_RHO = 5,     /* density on the comp-faces (level 0 only) */
+  BFIBM_F_FORCE = 6,   /* Eulerian force density, component comp (level 0 only) */
+  BFIBM_F_MUC = 7,     /* viscosity at centres */
+  BFIBM_F_MUE = 8,     /* viscosity on edges: comp 0 = xy, 1 = xz, 2 = yz */
+  BFIBM_F_BETA = 9,    /* 1/rho on the comp-faces (restricted on coarse levels) */
+  BFIBM_F_M = 10,      /* rho sigma / dt on the comp-faces */
+  BFIBM_F_URES = 11,   /* viscous residual, component comp */
+  BFIBM_F_PRES = 12    /* pressure residual */
+};
+
+/* Stage selectors for bfibm_stage. */
+enum {
+  BFIBM_STAGE_RHS = 0,        /* Eq. (NSdis1-1) right-hand side; u~ <- u^n */
+  BFIBM_STAGE_DIVERGENCE = 1, /* b = (sigma/euler) D.u~ / dt, mean removed (Eq. NSdis4) */
+  BFIBM_STAGE_PROJECT = 2,    /* u = u~ - (euler dt/sigma) beta D p (Eq. NSdis2) */
+  BFIBM_STAGE_INTERP_ADVANCE = 3, /* U by Eq. (discrVelCouple), X += dt/sigma U */
+  BFIBM_STAGE_SPRINGS = 4     /* break test and node forces, Eq. (springF) */
+};
+
+/* Create a context. p is validated and copied; stream may be NULL (the
+   library then creates its own non-blocking stream). Allocates every grid
+   array of every multigrid level on the current device, evaluates the
+   laminar initial velocity (Eq. 2DlaminarSoln / 3DlaminarFlow) and a uniform
+   fluid. Errors: BFIBM_EINVAL (bad parameters), BFIBM_ENOMEM, BFIBM_ECUDA. */
+bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out);
+
+/* Load eta node positions X (eta x dim doubles, row-major, host). Every
+   coordinate must lie in [0, L) on a periodic axis and in [0, L] on a wall
+   axis (L = n h), else BFIBM_EINVAL and nothing changes. Replaces the
+   springs' endpoints' meaning: load springs after nodes. */
+bfibm_status bfibm_set_nodes(bfibm_ctx* c, int64_t eta, const double* X);
+
+/* Load m springs: node pairs ab (m x 2 int32), rest lengths, Hookean
+   coefficients K and break strains (a spring breaks once its length exceeds
+   (1 + break_strain) * rest; Sec. 3.2 uses 1). All host arrays. */
+bfibm_status bfibm_set_springs(bfibm_ctx* c, int64_t m, const int32_t* ab, const double* rest,
+                               const double* K, const double* break_strain);
+
+/* Overwrite velocity component comp (host array in the field layout). */
+bfibm_status bfibm_set_velocity(bfibm_ctx* c, int comp, const double* u);
+
+/* Advance nsteps time steps in the order of Sec. 3.4: u~ (Eq. NSdis1-1), p
+   (Eq. NSdis4), u (Eq. NSdis2), U (Eq. discrVelCouple), X, then springs,
+   f, rho, mu (Eq. discrForceCouple, discrDensCouple, ViscExp) at the new
+   positions. Returns once the work is queued (fixed V-cycle mode) or done
+   (rtol mode, which reads residual norms back). BFIBM_ENOCONV if a solve
+   stopped at max_cycles. */
+bfibm_status bfibm_step(bfibm_ctx* c, int nsteps);
+
+/* Read results into host buffers (field layout; X as eta x dim). */
+bfibm_status bfibm_get_velocity(bfibm_ctx* c, int comp, double* out);
+bfibm_status bfibm_get_pressure(bfibm_ctx* c, double* out);
+bfibm_status bfibm_get_nodes(bfibm_ctx* c, double* X);
+/* Broken springs as (spring id, step) pairs sorted by step then id; at most
+   cap pairs are written, *n receives the total count. */
+bfibm_status bfibm_get_broken(bfibm_ctx* c, int64_t cap, int64_t* n, int32_t* spring_id,
+                              int32_t* step);
+bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out);
+const char* bfibm_last_error(const bfibm_ctx* c);
+void bfibm_destroy(bfibm_ctx* c);
+
+/* Operator-level access, for inspection and verification of single stages.
+   Fields use the layout above at multigrid level `level` (0 = finest). */
+bfibm_status bfibm_get_field(bfibm_ctx* c, int which, int comp, int level, double* out);
+bfibm_status bfibm_set_field(bfibm_ctx* c, int which, int comp, int level, const double* in);
+/* Device-to-device variants: `dev` is a device pointer to a dense field array. */
+bfibm_status bfibm_get_field_dev(bfibm_ctx* c, int which, int comp, int level, double* dev);
+bfibm_status bfibm_set_field_dev(bfibm_ctx* c, int which, int comp, int level, const double* dev);
+/* Node forces F (eta x dim, host) from the last spring stage. */
+bfibm_status bfibm_get_node_forces(bfibm_ctx* c, double* F);
+/* Break test, forces, spreads and coefficient hierarchy at the current nodes. */
+bfibm_status bfibm_refresh(bfibm_ctx* c);
+/* beta = 1/rho and m = rho sigma/dt on the fine faces, then every coarse level. */
+bfibm_status bfibm_build_coefficients(bfibm_ctx* c);
+bfibm_status bfibm_stage(bfibm_ctx* c, int stage);
+/* Multigrid solves on level 0 (ncycles > 0 fixed, 0 = until rtol); the cycles
+   used are written to *cycles when cycles is not NULL. */
+bfibm_status bfibm_solve_pressure(bfibm_ctx* c, int ncycles, int32_t* cycles);
+bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles);
+/* nsweeps red-black sweeps on one level (Sec. 3.5). Asynchronous: returns
+   once the kernels are queued on the context's stream. */
+bfibm_status bfibm_smooth_pressure(bfibm_ctx* c, int level, int nsweeps);
+bfibm_status bfibm_smooth_viscous(bfibm_ctx* c, int level, int nsweeps);
+/* Residual on one level (synchronous). */
+bfibm_status bfibm_residual_pressure(bfibm_ctx* c, int level);
+bfibm_status bfibm_residual_viscous(bfibm_ctx* c, int level);
+/* Wait for all work queued on the context's stream. */
+bfibm_status bfibm_synchronize(bfibm_ctx* c);
+/* Number of multigrid levels and their cell counts / storage extents. */
+bfibm_status bfibm_levels(bfibm_ctx* c, int32_t* nlevels);
+bfibm_status bfibm_level_dims(bfibm_ctx* c, int level, int32_t n[3], int32_t s[3]);
+/* Body force G in use (Eq. 2DlaminarSoln / 3DlaminarFlow when u_center > 0). */
+bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
+/* Options: BFIBM_OPT_STATS (1: residual norms after every fixed-count solve,
+   default 1), BFIBM_OPT_GRAPH (1: replay fixed-count steps as a CUDA graph,
+   default 1). */
+enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1 };
+bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
+/* Kernel launches in one replayed time step (the kernel nodes of the captured
+   step graph), or -1 when no graph has been captured yet. */
+bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n);
+/* Device bytes a context with these parameters allocates for its grids. */
+bfibm_status bfibm_footprint(const bfibm_params* p, int64_t eta, int64_t nsprings,
+                             int64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFIBM_H */

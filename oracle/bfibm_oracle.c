@@ -1215,7 +1215,9 @@ void* or_create(const or_params* P) {
   S->P = *P;
   S->D = P->dim;
   if (S->D == 2) { S->P.n[2] = 1; S->P.periodic[2] = 1; }
-  /* levels: halve while every axis is even and the halved minimum is >= 2 */
+  /* levels: halve while every axis is even, the halved minimum is >= 2 and
+     every halved periodic axis stays even (so that red-black colouring is
+     consistent across the periodic wrap) */
   int n[3] = {S->P.n[0], S->P.n[1], S->P.n[2]};
   S->L = 0;
   for (;;) {
@@ -1230,7 +1232,11 @@ void* or_create(const or_params* P) {
     S->L++;
     if (S->L >= P->mg_levels_max || S->L >= OR_MAXLEV) break;
     int ok = 1, mn = 1 << 30;
-    for (int a = 0; a < S->D; ++a) { if (n[a] % 2) ok = 0; if (n[a] / 2 < mn) mn = n[a] / 2; }
+    for (int a = 0; a < S->D; ++a) {
+      if (n[a] % 2) ok = 0;
+      if (n[a] / 2 < mn) mn = n[a] / 2;
+      if (S->P.periodic[a] && (n[a] / 2) % 2) ok = 0;
+    }
     if (!ok || mn < 2) break;
     for (int a = 0; a < S->D; ++a) n[a] /= 2;
   }

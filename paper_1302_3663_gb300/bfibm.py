@@ -1,0 +1,343 @@
+"""Python binding of libbfibm (include/bfibm.h): argument marshalling only.
+
+Every call goes through the C ABI; every arithmetic step runs in the CUDA
+kernels of the library. There is no CPU path: if the shared library cannot be
+built or loaded, importing ``lib()`` raises.
+
+Fields are exchanged as float64 numpy arrays in the ABI's dense layout:
+shape ``(s2, s1, s0)`` in 3D and ``(s1, s0)`` in 2D, with ``s[a] = n[a] + 1``
+on wall axes and ``n[a]`` on periodic axes.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTATE"]
+
+FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
+         "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12}
+STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
+OPT_STATS, OPT_GRAPH = 0, 1
+
+
+class BfibmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+class bfibm_params(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32 * 3), ("periodic", C.c_int32 * 3),
+                ("flow_axis", C.c_int32), ("phi_kind", C.c_int32), ("mg_levels_max", C.c_int32),
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("vc_visc", C.c_int32),
+                ("vc_p", C.c_int32), ("max_cycles", C.c_int32), ("coarse_sweeps", C.c_int32),
+                ("precision", C.c_int32),
+                ("h", C.c_double), ("rho_f", C.c_double), ("mu_f", C.c_double),
+                ("rho_ratio", C.c_double), ("mu_ratio", C.c_double), ("omega", C.c_double),
+                ("omega_mu", C.c_double), ("d0_vol", C.c_double), ("dt", C.c_double),
+                ("sigma", C.c_double), ("euler", C.c_double), ("inv_re", C.c_double),
+                ("c_force", C.c_double), ("body_force", C.c_double), ("u_center", C.c_double),
+                ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double)]
+
+
+class bfibm_stats(C.Structure):
+    _fields_ = [("cycles_visc", C.c_int32), ("cycles_p", C.c_int32),
+                ("broken_total", C.c_int32), ("clamped_total", C.c_int32),
+                ("res_visc", C.c_double), ("res_p", C.c_double), ("div_max", C.c_double),
+                ("kinetic", C.c_double), ("step", C.c_int64)]
+
+
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int32)
+_V = C.c_void_p
+_i = C.c_int
+_L = C.c_int64
+
+# name -> argument types (all return bfibm_status unless listed in _RES)
+SIGNATURES = {
+    "bfibm_create": [C.POINTER(bfibm_params), _V, C.POINTER(_V)],
+    "bfibm_set_nodes": [_V, _L, _DP],
+    "bfibm_set_springs": [_V, _L, _IP, _DP, _DP, _DP],
+    "bfibm_set_velocity": [_V, _i, _DP],
+    "bfibm_step": [_V, _i],
+    "bfibm_get_velocity": [_V, _i, _DP],
+    "bfibm_get_pressure": [_V, _DP],
+    "bfibm_get_nodes": [_V, _DP],
+    "bfibm_get_broken": [_V, _L, C.POINTER(_L), _IP, _IP],
+    "bfibm_get_stats": [_V, C.POINTER(bfibm_stats)],
+    "bfibm_last_error": [_V],
+    "bfibm_destroy": [_V],
+    "bfibm_get_field": [_V, _i, _i, _i, _DP],
+    "bfibm_set_field": [_V, _i, _i, _i, _DP],
+    "bfibm_get_field_dev": [_V, _i, _i, _i, _V],
+    "bfibm_set_field_dev": [_V, _i, _i, _i, _V],
+    "bfibm_get_node_forces": [_V, _DP],
+    "bfibm_refresh": [_V],
+    "bfibm_build_coefficients": [_V],
+    "bfibm_stage": [_V, _i],
+    "bfibm_solve_pressure": [_V, _i, _IP],
+    "bfibm_solve_viscous": [_V, _i, _IP],
+    "bfibm_smooth_pressure": [_V, _i, _i],
+    "bfibm_smooth_viscous": [_V, _i, _i],
+    "bfibm_synchronize": [_V],
+    "bfibm_residual_pressure": [_V, _i],
+    "bfibm_residual_viscous": [_V, _i],
+    "bfibm_levels": [_V, _IP],
+    "bfibm_level_dims": [_V, _i, _IP, _IP],
+    "bfibm_body_force": [_V, _DP],
+    "bfibm_set_option": [_V, _i, _L],
+    "bfibm_launches_per_step": [_V, C.POINTER(_L)],
+    "bfibm_footprint": [C.POINTER(bfibm_params), _L, _L, C.POINTER(_L)],
+}
+_RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None}
+
+_LIB = None
+
+
+def lib():
+    """Load (building first if needed) libbfibm.so and set the prototypes."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build()
+    L = C.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _RES.get(name, C.c_int)
+    _LIB = L
+    return L
+
+
+def library_path():
+    return _build.LIB
+
+
+def make_params(prm):
+    """bfibm_params from a workload parameter dict."""
+    P = bfibm_params()
+    P.dim = prm["dim"]
+    for a in range(3):
+        P.n[a] = int(prm["n"][a])
+        P.periodic[a] = int(prm["periodic"][a])
+    for k in ("flow_axis", "phi_kind", "mg_levels_max", "nu1", "nu2", "vc_visc", "vc_p",
+              "max_cycles", "coarse_sweeps", "precision"):
+        setattr(P, k, int(prm.get(k, 0)))
+    for k in ("h", "rho_f", "mu_f", "rho_ratio", "mu_ratio", "omega", "omega_mu", "d0_vol", "dt",
+              "sigma", "euler", "inv_re", "c_force", "body_force", "u_center", "ic_scale", "rtol",
+              "gamma_coarse"):
+        setattr(P, k, float(prm[k]))
+    return P
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def footprint(prm, eta=0, nsprings=0):
+    out = _L(0)
+    P = make_params(prm)
+    st = lib().bfibm_footprint(C.byref(P), int(eta), int(nsprings), C.byref(out))
+    if st != OK:
+        raise BfibmError(st, "bfibm_footprint")
+    return out.value
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Context:
+    """One simulation on the current CUDA device (see bfibm_create)."""
+
+    def __init__(self, prm, stream=None):
+        self.lib = lib()
+        self.prm = dict(prm)
+        self.dim = prm["dim"]
+        self._P = make_params(prm)
+        h = _V()
+        st = self.lib.bfibm_create(C.byref(self._P), _stream_handle(stream), C.byref(h))
+        if st != OK:
+            raise BfibmError(st, "bfibm_create rejected the parameters or failed")
+        self.h = h
+        self.eta = 0
+        nl = C.c_int32(0)
+        self.lib.bfibm_levels(self.h, C.byref(nl))
+        self.levels = nl.value
+
+    def _chk(self, st, what, allow=(OK,)):
+        if st not in allow:
+            msg = self.lib.bfibm_last_error(self.h)
+            raise BfibmError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bfibm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # geometry ----------------------------------------------------------------
+    def dims(self, level=0):
+        n = (C.c_int32 * 3)()
+        s = (C.c_int32 * 3)()
+        self._chk(self.lib.bfibm_level_dims(self.h, level, n, s), "bfibm_level_dims")
+        return tuple(n), tuple(s)
+
+    def shape(self, level=0):
+        _, s = self.dims(level)
+        return (s[2], s[1], s[0]) if self.dim == 3 else (s[1], s[0])
+
+    @property
+    def body_force(self):
+        g = C.c_double(0)
+        self._chk(self.lib.bfibm_body_force(self.h, C.byref(g)), "bfibm_body_force")
+        return g.value
+
+    # state -------------------------------------------------------------------
+    def set_nodes(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, self.dim)
+        self._chk(self.lib.bfibm_set_nodes(self.h, X.shape[0], _dp(X)), "bfibm_set_nodes")
+        self.eta = X.shape[0]
+
+    def set_springs(self, ab, rest, K, brk):
+        ab = np.ascontiguousarray(ab, dtype=np.int32).reshape(-1, 2)
+        rest, K, brk = (np.ascontiguousarray(a, dtype=np.float64) for a in (rest, K, brk))
+        self._chk(self.lib.bfibm_set_springs(self.h, ab.shape[0], ab.ctypes.data_as(_IP),
+                                             _dp(rest), _dp(K), _dp(brk)), "bfibm_set_springs")
+
+    def set_velocity(self, comp, u):
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.shape())
+        self._chk(self.lib.bfibm_set_velocity(self.h, comp, _dp(u)), "bfibm_set_velocity")
+
+    def step(self, n=1):
+        return self._chk(self.lib.bfibm_step(self.h, int(n)), "bfibm_step", (OK, ENOCONV))
+
+    def get_velocity(self, comp, out=None):
+        out = np.empty(self.shape()) if out is None else out
+        self._chk(self.lib.bfibm_get_velocity(self.h, comp, _dp(out)), "bfibm_get_velocity")
+        return out
+
+    def get_pressure(self, out=None):
+        out = np.empty(self.shape()) if out is None else out
+        self._chk(self.lib.bfibm_get_pressure(self.h, _dp(out)), "bfibm_get_pressure")
+        return out
+
+    def get_nodes(self, out=None):
+        out = np.empty((self.eta, self.dim)) if out is None else out
+        self._chk(self.lib.bfibm_get_nodes(self.h, _dp(out)), "bfibm_get_nodes")
+        return out
+
+    def get_node_forces(self):
+        out = np.empty((self.eta, self.dim))
+        self._chk(self.lib.bfibm_get_node_forces(self.h, _dp(out)), "bfibm_get_node_forces")
+        return out
+
+    def get_broken(self):
+        n = _L(0)
+        self._chk(self.lib.bfibm_get_broken(self.h, 0, C.byref(n), None, None), "bfibm_get_broken")
+        cnt = n.value
+        ids = np.zeros(max(cnt, 1), dtype=np.int32)
+        steps = np.zeros(max(cnt, 1), dtype=np.int32)
+        self._chk(self.lib.bfibm_get_broken(self.h, cnt, C.byref(n), ids.ctypes.data_as(_IP),
+                                            steps.ctypes.data_as(_IP)), "bfibm_get_broken")
+        return ids[:cnt].copy(), steps[:cnt].copy()
+
+    def get_stats(self):
+        st = bfibm_stats()
+        self._chk(self.lib.bfibm_get_stats(self.h, C.byref(st)), "bfibm_get_stats")
+        return {k: getattr(st, k) for k, _ in bfibm_stats._fields_}
+
+    # operator-level ----------------------------------------------------------
+    def get_field(self, which, comp=0, level=0):
+        out = np.empty(self.shape(level))
+        self._chk(self.lib.bfibm_get_field(self.h, FIELD[which], comp, level, _dp(out)),
+                  "bfibm_get_field")
+        return out
+
+    def set_field(self, which, arr, comp=0, level=0):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape(level))
+        self._chk(self.lib.bfibm_set_field(self.h, FIELD[which], comp, level, _dp(a)),
+                  "bfibm_set_field")
+
+    def get_field_dev(self, which, dev_ptr, comp=0, level=0):
+        self._chk(self.lib.bfibm_get_field_dev(self.h, FIELD[which], comp, level, int(dev_ptr)),
+                  "bfibm_get_field_dev")
+
+    def set_field_dev(self, which, dev_ptr, comp=0, level=0):
+        self._chk(self.lib.bfibm_set_field_dev(self.h, FIELD[which], comp, level, int(dev_ptr)),
+                  "bfibm_set_field_dev")
+
+    def refresh(self):
+        self._chk(self.lib.bfibm_refresh(self.h), "bfibm_refresh")
+
+    def build_coefficients(self):
+        self._chk(self.lib.bfibm_build_coefficients(self.h), "bfibm_build_coefficients")
+
+    def stage(self, name):
+        self._chk(self.lib.bfibm_stage(self.h, STAGE[name]), "bfibm_stage")
+
+    def solve_pressure(self, ncycles):
+        cyc = C.c_int32(0)
+        self._chk(self.lib.bfibm_solve_pressure(self.h, int(ncycles), C.byref(cyc)),
+                  "bfibm_solve_pressure", (OK, ENOCONV))
+        return cyc.value
+
+    def solve_viscous(self, ncycles):
+        cyc = C.c_int32(0)
+        self._chk(self.lib.bfibm_solve_viscous(self.h, int(ncycles), C.byref(cyc)),
+                  "bfibm_solve_viscous", (OK, ENOCONV))
+        return cyc.value
+
+    def smooth_pressure(self, level=0, nsweeps=1, sync=True):
+        self._chk(self.lib.bfibm_smooth_pressure(self.h, level, nsweeps), "bfibm_smooth_pressure")
+        if sync:
+            self.synchronize()
+
+    def smooth_viscous(self, level=0, nsweeps=1, sync=True):
+        self._chk(self.lib.bfibm_smooth_viscous(self.h, level, nsweeps), "bfibm_smooth_viscous")
+        if sync:
+            self.synchronize()
+
+    def synchronize(self):
+        self._chk(self.lib.bfibm_synchronize(self.h), "bfibm_synchronize")
+
+    def residual_pressure(self, level=0):
+        self._chk(self.lib.bfibm_residual_pressure(self.h, level), "bfibm_residual_pressure")
+        return self.get_field("pres", 0, level)
+
+    def residual_viscous(self, level=0):
+        self._chk(self.lib.bfibm_residual_viscous(self.h, level), "bfibm_residual_viscous")
+        return [self.get_field("ures", d, level) for d in range(self.dim)]
+
+    def launches_per_step(self):
+        n = _L(0)
+        self._chk(self.lib.bfibm_launches_per_step(self.h, C.byref(n)), "bfibm_launches_per_step")
+        return n.value
+
+    def set_option(self, opt, value):
+        self._chk(self.lib.bfibm_set_option(self.h, opt, int(value)), "bfibm_set_option")
+
+
+def load_instance(inst, stream=None, prm_override=None):
+    """Context with a workload instance's parameters, nodes and springs loaded."""
+    prm = dict(inst["params"])
+    if prm_override:
+        prm.update(prm_override)
+    ctx = Context(prm, stream=stream)
+    ctx.set_nodes(inst["X"])
+    ctx.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+    return ctx

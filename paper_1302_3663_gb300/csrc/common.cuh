@@ -1,0 +1,160 @@
+// Internal declarations shared by the CUDA translation units of libbfibm.
+// Kernels live in stencil.cu (Eulerian grid work) and lagrangian.cu (nodes,
+// springs, transfers); solver.cu holds the context, the multigrid driver and
+// the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bf {
+
+constexpr int kMaxLevels = 8;
+constexpr int kRedBlocks = 1024;   // blocks of every partial-reduction kernel
+
+// Geometry of one multigrid level. Every array of the level shares it.
+// Storage extent s[a] = n[a] + 1 on a wall axis (room for the upper wall
+// face/edge), n[a] on a periodic axis; x is contiguous, rows are padded to
+// st[1] elements.
+struct Geo {
+  int n[3];
+  int s[3];
+  int per[3];
+  long long st[3];   // strides in elements: 1, pitch, pitch * s[1]
+  double h;
+};
+
+__host__ __device__ inline long long gidx(const Geo& g, int i, int j, int k) {
+  return (long long)i + g.st[1] * j + g.st[2] * k;
+}
+
+template <typename T>
+struct LevelPtrs {
+  T* p;          // pressure iterate
+  T* pf;         // pressure rhs
+  T* pr;         // pressure residual
+  T* beta[3];    // 1/rho on faces (restricted)
+  T* u[3];       // viscous iterate
+  T* uf[3];      // viscous rhs
+  T* ur[3];      // viscous residual
+  T* m[3];       // rho sigma / dt on faces
+  T* muc;        // mu at centres
+  T* mue[3];     // mu on edges: xy, xz, yz
+};
+
+struct Scalars {
+  double* partial;   // kRedBlocks partial results
+  double* out;       // 16 finalized scalars
+};
+
+// ---------------------------------------------------------------- stencil.cu
+// Pressure: one colour of red-black Gauss-Seidel for D.(beta D p) = f.
+template <typename T>
+void launch_p_rbgs(int D, const Geo& g, const LevelPtrs<T>& L, int colour, cudaStream_t s);
+template <typename T>
+void launch_p_residual(int D, const Geo& g, const LevelPtrs<T>& L, cudaStream_t s);
+// Viscous: one colour of component d.
+template <typename T>
+void launch_v_rbgs(int D, const Geo& g, const LevelPtrs<T>& L, int d, int colour, double inv_re,
+                   cudaStream_t s);
+template <typename T>
+void launch_v_residual(int D, const Geo& g, const LevelPtrs<T>& L, double inv_re, cudaStream_t s);
+// Transfers between level l (fine) and l+1 (coarse).
+template <typename T>
+void launch_restrict_cell(int D, const Geo& gf, const Geo& gc, const T* rf, T* fc, T* xc,
+                          cudaStream_t s);
+template <typename T>
+void launch_restrict_face(int D, int d, const Geo& gf, const Geo& gc, const T* rf, T* fc, T* xc,
+                          cudaStream_t s);
+template <typename T>
+void launch_prolong_cell(int D, const Geo& gf, const Geo& gc, const T* ec, T* xf, cudaStream_t s);
+template <typename T>
+void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec, T* xf,
+                         cudaStream_t s);
+// Coarsest level: the whole solve in one block.
+template <typename T>
+void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cudaStream_t s);
+template <typename T>
+void launch_coarse_v(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, double inv_re,
+                     cudaStream_t s);
+
+// FP64-only grid stages.
+void launch_coef_fine(int D, const Geo& g, double* const rho[3], double* beta[3], double* m[3],
+                      double msc, cudaStream_t s);
+void launch_coef_restrict(int D, const Geo& gf, const Geo& gc, const LevelPtrs<double>& F,
+                          const LevelPtrs<double>& C, double gamma, cudaStream_t s);
+void launch_adv_rhs(int D, const Geo& g, double* const uvel[3], double* const rho[3],
+                    double* const frc[3], const LevelPtrs<double>& L0, double c_force,
+                    int flow_axis, const double* G_dev, cudaStream_t s);
+void launch_divergence(int D, const Geo& g, double* const u[3], double* b, double scale,
+                       Scalars sc, cudaStream_t s);
+void launch_project(int D, const Geo& g, double* const ut[3], const double* p,
+                    double* const beta[3], double* uvel[3], double coef, cudaStream_t s);
+// mean over cells of a (deterministic two-pass) subtracted from a
+void launch_sub_mean(int D, const Geo& g, double* a, Scalars sc, cudaStream_t s);
+// sum of squares over the unknowns (cells if ncomp == 0, else the faces of
+// ncomp components) -> sc.out[slot]
+void launch_norm2(int D, const Geo& g, double* const a[3], int ncomp, Scalars sc, int slot,
+                  cudaStream_t s);
+// max |D.u| -> sc.out[slot], sum u^2 h^D -> sc.out[slot + 1]
+void launch_div_ke(int D, const Geo& g, double* const u[3], Scalars sc, int slot, cudaStream_t s);
+// laminar initial velocity and body force
+void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_center,
+                    double body_force, double ic_scale, double* ucomp, double* G_dev,
+                    cudaStream_t s);
+void launch_fill(double* a, long long n, double v, cudaStream_t s);
+
+// ------------------------------------------------------------ lagrangian.cu
+struct NodeSet {
+  long long eta;
+  double* X;    // eta x 3
+  double* U;    // eta x 3
+  double* F;    // eta x 3
+  int* tile;    // eta: tile of each node
+  int* perm;    // eta: nodes sorted by tile
+  int* count;   // ntiles + 1
+  int* start;   // ntiles + 1
+  int* cursor;  // ntiles
+  int* clamped; // 1 counter
+};
+struct SpringSet {
+  long long m;
+  int* ab;          // m x 2
+  double* rest;
+  double* K;
+  double* brk;
+  int* broken;      // m flags
+  int* ev_id;       // m slots
+  int* ev_step;
+  int* ev_count;    // 1 counter
+  long long* step;  // device step counter
+};
+struct TileGeo {
+  int T[3];         // cells per tile and axis
+  int nt[3];        // tiles per axis
+  int H;            // halo (grid points) around a tile in shared memory
+  int ntiles;
+};
+struct SpreadArgs {
+  int D;
+  int phi_kind;
+  double omega, omega_mu;
+  double amp_rho;     // rho_b d0^D
+  double mu_out, mu_coef;   // (2 w)^D (mu_max - mu_out)
+};
+
+void launch_springs(int D, const Geo& g, const NodeSet& N, const SpringSet& S, cudaStream_t s);
+void launch_bin(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, cudaStream_t s);
+void launch_reset_fields(int D, const Geo& g, double* frc[3], double* rho[3], double* muc,
+                         double* mue[3], double rho_f, double mu_f, cudaStream_t s);
+void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, const SpreadArgs& a,
+                   double* frc[3], double* rho[3], double* muc, double* mue[3], cudaStream_t s);
+void launch_interp_advance(int D, const Geo& g, const NodeSet& N, double* const uvel[3],
+                           int phi_kind, double dt_over_sigma, cudaStream_t s);
+void launch_step_increment(long long* step, cudaStream_t s);
+size_t spread_smem_bytes(int D, const TileGeo& tg);
+// opt the spread kernel into more than 48 KB of dynamic shared memory (call
+// once, outside stream capture)
+cudaError_t spread_set_smem(int D, size_t bytes);
+
+}  // namespace bf

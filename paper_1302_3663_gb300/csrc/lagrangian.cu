@@ -1,0 +1,488 @@
+// Lagrangian kernels: breakable Hookean springs (Eq. springF, Sec. 3.2),
+// binning of nodes into cell tiles, the spreads of force and density
+// (Eq. discrForceCouple, Eq. discrDensCouple) and of the viscosity maximum
+// (Eq. ViscExp), and the velocity interpolation with the width-h delta
+// (Eq. discrVelCouple) fused with the explicit Euler move of the nodes.
+//
+// Spreading: nodes are counting-sorted by the cell tile that holds them; one
+// block per tile accumulates the contributions of its nodes in shared memory
+// (the tile plus a halo as wide as the kernel support) and then flushes the
+// non-zero entries to the grid with one global atomic each. When the support
+// is too wide for the shared region, the block adds to the grid directly.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "common.cuh"
+
+namespace bf {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// Eq. (PhiPeskin)
+__device__ __forceinline__ double phi1(double r) {
+  double a = fabs(r);
+  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+  if (a < 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+  return 0.0;
+}
+// Eq. (PhiCosAlternative)
+__device__ __forceinline__ double phi2(double r) {
+  double a = fabs(r);
+  if (a < 2.0) return 0.25 * (1.0 + cos(CUDART_PI * r / 2.0));
+  return 0.0;
+}
+__device__ __forceinline__ double phi(int kind, double r) { return kind == 1 ? phi1(r) : phi2(r); }
+
+// index of grid point i of a kind (stag: 0 face axis, 1 centre axis) along
+// axis a, wrapped on periodic axes; -1 where the point would lie beyond a wall
+__device__ __forceinline__ int kind_index(const Geo& g, int stag, int a, int i) {
+  int n = g.n[a];
+  if (g.per[a]) return ((i % n) + n) % n;
+  int hi = stag ? n - 1 : n;
+  return (i < 0 || i > hi) ? -1 : i;
+}
+
+__device__ __forceinline__ void support(const Geo& g, int stag, double X, double w, int& lo,
+                                        int& hi) {
+  double q = X / g.h - 0.5 * stag;
+  double R = w / g.h;
+  lo = (int)floor(q - 2.0 * R) + 1;
+  hi = (int)ceil(q + 2.0 * R) - 1;
+}
+
+// Visit every point of the grid kind inside the support of width w around X:
+// fn(i, j, k unwrapped, global index, prod of phi).
+template <int D, typename Fn>
+__device__ __forceinline__ void for_support(const Geo& g, const int stag[3], const double* X,
+                                            double w, int kind, Fn fn) {
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) support(g, stag[a], X[a], w, lo[a], hi[a]);
+  for (int k = lo[2]; k <= hi[2]; ++k) {
+    int kk = 0;
+    double pz = 1.0;
+    if constexpr (D == 3) {
+      kk = kind_index(g, stag[2], 2, k);
+      if (kk < 0) continue;
+      pz = phi(kind, ((k + 0.5 * stag[2]) * g.h - X[2]) / w);
+    }
+    for (int j = lo[1]; j <= hi[1]; ++j) {
+      int jj = kind_index(g, stag[1], 1, j);
+      if (jj < 0) continue;
+      double py = phi(kind, ((j + 0.5 * stag[1]) * g.h - X[1]) / w);
+      for (int i = lo[0]; i <= hi[0]; ++i) {
+        int ii = kind_index(g, stag[0], 0, i);
+        if (ii < 0) continue;
+        double px = phi(kind, ((i + 0.5 * stag[0]) * g.h - X[0]) / w);
+        fn(i, j, k, gidx(g, ii, jj, kk), px * py * pz);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Springs: break test on the squared length without fused multiply-adds (so
+// the decision matches a plain IEEE evaluation), then the tension
+// T = K (|d| - r) pulls both nodes along d (Eq. springF).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_springs(int D, Geo g, NodeSet N, SpringSet S) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= S.m) return;
+  if (S.broken[q]) return;
+  int a = S.ab[2 * q], b = S.ab[2 * q + 1];
+  double dv[3] = {0.0, 0.0, 0.0};
+  for (int ax = 0; ax < D; ++ax) {
+    double v = N.X[3 * (long long)b + ax] - N.X[3 * (long long)a + ax];
+    if (g.per[ax]) {
+      double Lx = g.n[ax] * g.h;
+      if (v > 0.5 * Lx) v -= Lx;
+      else if (v < -0.5 * Lx) v += Lx;
+    }
+    dv[ax] = v;
+  }
+  double len2 = __dadd_rn(__dmul_rn(dv[0], dv[0]), __dmul_rn(dv[1], dv[1]));
+  len2 = __dadd_rn(len2, __dmul_rn(dv[2], dv[2]));
+  double thr = __dmul_rn(__dadd_rn(1.0, S.brk[q]), S.rest[q]);
+  if (len2 > __dmul_rn(thr, thr)) {
+    S.broken[q] = 1;
+    int slot = atomicAdd(S.ev_count, 1);
+    if (slot < S.m) {
+      S.ev_id[slot] = (int)q;
+      S.ev_step[slot] = (int)(*S.step);
+    }
+    return;
+  }
+  double len = sqrt(len2);
+  if (len == 0.0) return;
+  double T = S.K[q] * (len - S.rest[q]);
+  for (int ax = 0; ax < D; ++ax) {
+    double f = T * dv[ax] / len;
+    atomicAdd(&N.F[3 * (long long)a + ax], f);
+    atomicAdd(&N.F[3 * (long long)b + ax], -f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Binning by cell tile (counting sort).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tile_of(int D, const Geo& g, const TileGeo& tg, const double* X) {
+  int t[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) {
+    int c = (int)floor(X[a] / (tg.T[a] * g.h));
+    t[a] = c < 0 ? 0 : (c >= tg.nt[a] ? tg.nt[a] - 1 : c);
+  }
+  return t[0] + tg.nt[0] * (t[1] + tg.nt[1] * t[2]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_bin_count(int D, Geo g, TileGeo tg, NodeSet N) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= N.eta) return;
+  int t = tile_of(D, g, tg, &N.X[3 * s]);
+  N.tile[s] = t;
+  atomicAdd(&N.count[t], 1);
+}
+
+// exclusive scan of the tile counts in one block
+__global__ void __launch_bounds__(1024) k_bin_scan(TileGeo tg, NodeSet N) {
+  __shared__ int part[1024];
+  int nt = tg.ntiles;
+  int per = (nt + blockDim.x - 1) / blockDim.x;
+  int b0 = threadIdx.x * per, b1 = min(nt, b0 + per);
+  int s = 0;
+  for (int t = b0; t < b1; ++t) s += N.count[t];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int t = b0; t < b1; ++t) {
+    N.start[t] = run;
+    N.cursor[t] = run;
+    run += N.count[t];
+  }
+  if (threadIdx.x == blockDim.x - 1) N.start[nt] = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kBlock) k_bin_scatter(NodeSet N) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= N.eta) return;
+  int pos = atomicAdd(&N.cursor[N.tile[s]], 1);
+  N.perm[pos] = (int)s;
+}
+
+// ---------------------------------------------------------------------------
+// Field reset before spreading: f = 0, rho = rho_f, mu = mu_f everywhere.
+// ---------------------------------------------------------------------------
+struct FieldPtrs {
+  double* frc[3];
+  double* rho[3];
+  double* muc;
+  double* mue[3];
+};
+
+__global__ void __launch_bounds__(kBlock) k_reset(int D, Geo g, FieldPtrs P, double rho_f,
+                                                  double mu_f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.s[0] || j >= g.s[1] || k >= g.s[2]) return;
+  long long c = gidx(g, i, j, k);
+  for (int d = 0; d < D; ++d) {
+    P.frc[d][c] = 0.0;
+    P.rho[d][c] = rho_f;
+  }
+  P.muc[c] = mu_f;
+  int ne = D == 3 ? 3 : 1;
+  for (int e = 0; e < ne; ++e) P.mue[e][c] = mu_f;
+}
+
+// ---------------------------------------------------------------------------
+// Tile spread. Shared region per axis: [t T - H, t T + T + H).
+// ---------------------------------------------------------------------------
+struct SpreadK {
+  Geo g;
+  TileGeo tg;
+  NodeSet N;
+  SpreadArgs a;
+  FieldPtrs P;
+  int use_smem;
+  int R[3];
+  int vol;
+};
+
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_spread(SpreadK A) {
+  extern __shared__ double smem[];
+  const Geo& g = A.g;
+  int t = blockIdx.x;
+  int s0 = A.N.start[t], s1 = A.N.start[t + 1];
+  if (s0 == s1) return;
+  int tc[3] = {t % A.tg.nt[0], (t / A.tg.nt[0]) % A.tg.nt[1], t / (A.tg.nt[0] * A.tg.nt[1])};
+  int base[3];
+  for (int a = 0; a < 3; ++a) base[a] = (a < D) ? tc[a] * A.tg.T[a] - A.tg.H : 0;
+  double* accF = smem;
+  double* accR = smem + A.vol;
+  unsigned long long* accM = reinterpret_cast<unsigned long long*>(smem);
+  int kind = A.a.phi_kind;
+  bool sm = A.use_smem != 0;
+  auto local = [&](int i, int j, int k) -> int {
+    return (i - base[0]) + A.R[0] * ((j - base[1]) + A.R[1] * (D == 3 ? (k - base[2]) : 0));
+  };
+  auto flush_index = [&](int q, const int stag[3]) -> long long {
+    int li = q % A.R[0];
+    int lj = (q / A.R[0]) % A.R[1];
+    int lk = q / (A.R[0] * A.R[1]);
+    int gi = kind_index(g, stag[0], 0, base[0] + li);
+    int gj = kind_index(g, stag[1], 1, base[1] + lj);
+    int gk = 0;
+    if (D == 3) gk = kind_index(g, stag[2], 2, base[2] + lk);
+    if (gi < 0 || gj < 0 || gk < 0) return -1;
+    return gidx(g, gi, gj, gk);
+  };
+  double winvD = 1.0 / (D == 3 ? A.a.omega * A.a.omega * A.a.omega : A.a.omega * A.a.omega);
+
+  // force and density on each face grid
+  for (int d = 0; d < D; ++d) {
+    int stag[3] = {1, 1, 1};
+    stag[d] = 0;
+    if (sm) {
+      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) {
+        accF[q] = 0.0;
+        accR[q] = 0.0;
+      }
+      __syncthreads();
+    }
+    for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
+      int s = A.N.perm[p];
+      const double* X = &A.N.X[3 * (long long)s];
+      double Fd = A.N.F[3 * (long long)s + d];
+      for_support<D>(g, stag, X, A.a.omega, kind,
+                     [&](int i, int j, int k, long long gi, double w) {
+                       double wt = winvD * w;
+                       if (sm) {
+                         int l = local(i, j, k);
+                         atomicAdd(&accF[l], Fd * wt);
+                         atomicAdd(&accR[l], A.a.amp_rho * wt);
+                       } else {
+                         atomicAdd(&A.P.frc[d][gi], Fd * wt);
+                         atomicAdd(&A.P.rho[d][gi], A.a.amp_rho * wt);
+                       }
+                     });
+    }
+    if (sm) {
+      __syncthreads();
+      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) {
+        double vf = accF[q], vr = accR[q];
+        if (vf == 0.0 && vr == 0.0) continue;
+        long long gi = flush_index(q, stag);
+        if (gi < 0) continue;
+        if (vf != 0.0) atomicAdd(&A.P.frc[d][gi], vf);
+        if (vr != 0.0) atomicAdd(&A.P.rho[d][gi], vr);
+      }
+      __syncthreads();
+    }
+  }
+
+  // viscosity maximum at centres and on edges (positive doubles order like
+  // their bit patterns, so an unsigned 64-bit max is a floating max)
+  double winvDm =
+      1.0 / (D == 3 ? A.a.omega_mu * A.a.omega_mu * A.a.omega_mu : A.a.omega_mu * A.a.omega_mu);
+  int nkinds = D == 3 ? 4 : 2;
+  for (int kk = 0; kk < nkinds; ++kk) {
+    int stag[3] = {1, 1, 1};
+    double* target = A.P.muc;
+    if (kk > 0) {
+      int e = kk - 1;  // 0: xy, 1: xz, 2: yz
+      int da = (e == 2) ? 1 : 0, db = (e == 0) ? 1 : 2;
+      stag[da] = 0;
+      stag[db] = 0;
+      target = A.P.mue[e];
+    }
+    if (sm) {
+      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) accM[q] = 0ull;
+      __syncthreads();
+    }
+    for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
+      int s = A.N.perm[p];
+      const double* X = &A.N.X[3 * (long long)s];
+      for_support<D>(g, stag, X, A.a.omega_mu, kind,
+                     [&](int i, int j, int k, long long gi, double w) {
+                       double cand = A.a.mu_coef * (winvDm * w) + A.a.mu_out;
+                       if (sm)
+                         atomicMax(&accM[local(i, j, k)], dbits(cand));
+                       else
+                         atomicMax(reinterpret_cast<unsigned long long*>(&target[gi]), dbits(cand));
+                     });
+    }
+    if (sm) {
+      __syncthreads();
+      unsigned long long floor_bits = dbits(A.a.mu_out);
+      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) {
+        unsigned long long v = accM[q];
+        if (v <= floor_bits) continue;
+        long long gi = flush_index(q, stag);
+        if (gi < 0) continue;
+        atomicMax(reinterpret_cast<unsigned long long*>(&target[gi]), v);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// U(s) = sum_x u_d(x) prod phi((x - X)/h) on each component's own grid
+// (Eq. discrVelCouple), then X += (dt/sigma) U with the periodic wrap and the
+// wall clamp.
+// ---------------------------------------------------------------------------
+struct Ptr3c {
+  const double* a[3];
+};
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_interp_advance(Geo g, NodeSet N, Ptr3c u, int kind,
+                                                           double c) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= N.eta) return;
+  double X[3] = {N.X[3 * s], N.X[3 * s + 1], N.X[3 * s + 2]};
+  double U[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int stag[3] = {1, 1, 1};
+    stag[d] = 0;
+    const double* __restrict__ ud = u.a[d];
+    double v = 0.0;
+    for_support<D>(g, stag, X, g.h, kind,
+                   [&](int, int, int, long long gi, double w) { v += ud[gi] * w; });
+    U[d] = v;
+  }
+  int clamped = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    N.U[3 * s + d] = U[d];
+    double x = X[d] + c * U[d];
+    double Lx = g.n[d] * g.h;
+    if (g.per[d]) {
+      if (x >= Lx) x -= Lx;
+      else if (x < 0.0) x += Lx;
+    } else {
+      if (x < 0.0) { x = 0.0; ++clamped; }
+      else if (x > Lx) { x = Lx; ++clamped; }
+    }
+    N.X[3 * s + d] = x;
+  }
+  if (clamped) atomicAdd(N.clamped, clamped);
+}
+
+__global__ void k_step_increment(long long* step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
+}
+
+inline dim3 blk3(int D) { return D == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1); }
+inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
+  return dim3((unsigned)((nx + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y),
+              (unsigned)((nz + b.z - 1) / b.z));
+}
+
+}  // namespace
+
+// ===========================================================================
+void launch_springs(int D, const Geo& g, const NodeSet& N, const SpringSet& S, cudaStream_t s) {
+  if (N.eta > 0) cudaMemsetAsync(N.F, 0, sizeof(double) * 3 * N.eta, s);
+  if (S.m <= 0) return;
+  unsigned nb = (unsigned)((S.m + kBlock - 1) / kBlock);
+  k_springs<<<nb, kBlock, 0, s>>>(D, g, N, S);
+}
+
+void launch_bin(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, cudaStream_t s) {
+  cudaMemsetAsync(N.count, 0, sizeof(int) * (tg.ntiles + 1), s);
+  if (N.eta > 0) {
+    unsigned nb = (unsigned)((N.eta + kBlock - 1) / kBlock);
+    k_bin_count<<<nb, kBlock, 0, s>>>(D, g, tg, N);
+  }
+  k_bin_scan<<<1, 1024, 0, s>>>(tg, N);
+  if (N.eta > 0) {
+    unsigned nb = (unsigned)((N.eta + kBlock - 1) / kBlock);
+    k_bin_scatter<<<nb, kBlock, 0, s>>>(N);
+  }
+}
+
+void launch_reset_fields(int D, const Geo& g, double* frc[3], double* rho[3], double* muc,
+                         double* mue[3], double rho_f, double mu_f, cudaStream_t s) {
+  FieldPtrs P;
+  for (int d = 0; d < 3; ++d) {
+    P.frc[d] = frc[d];
+    P.rho[d] = rho[d];
+    P.mue[d] = mue[d];
+  }
+  P.muc = muc;
+  dim3 b = blk3(D);
+  k_reset<<<grd3(g.s[0], g.s[1], g.s[2], b), b, 0, s>>>(D, g, P, rho_f, mu_f);
+}
+
+static void region(int D, const TileGeo& tg, int R[3], int& vol) {
+  vol = 1;
+  for (int a = 0; a < 3; ++a) {
+    R[a] = (a < D) ? tg.T[a] + 2 * tg.H : 1;
+    vol *= R[a];
+  }
+}
+
+size_t spread_smem_bytes(int D, const TileGeo& tg) {
+  int R[3], vol;
+  region(D, tg, R, vol);
+  return (size_t)2 * vol * sizeof(double);
+}
+
+void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, const SpreadArgs& a,
+                   double* frc[3], double* rho[3], double* muc, double* mue[3], cudaStream_t s) {
+  if (N.eta <= 0) return;
+  SpreadK A;
+  A.g = g;
+  A.tg = tg;
+  A.N = N;
+  A.a = a;
+  for (int d = 0; d < 3; ++d) {
+    A.P.frc[d] = frc[d];
+    A.P.rho[d] = rho[d];
+    A.P.mue[d] = mue[d];
+  }
+  A.P.muc = muc;
+  region(D, tg, A.R, A.vol);
+  size_t smem = spread_smem_bytes(D, tg);
+  A.use_smem = smem <= 96 * 1024 ? 1 : 0;
+  if (!A.use_smem) smem = 0;
+  if (D == 3) k_spread<3><<<tg.ntiles, kBlock, smem, s>>>(A);
+  else k_spread<2><<<tg.ntiles, kBlock, smem, s>>>(A);
+}
+
+cudaError_t spread_set_smem(int D, size_t bytes) {
+  if (D == 3)
+    return cudaFuncSetAttribute(k_spread<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(k_spread<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_interp_advance(int D, const Geo& g, const NodeSet& N, double* const uvel[3],
+                           int phi_kind, double dt_over_sigma, cudaStream_t s) {
+  if (N.eta <= 0) return;
+  Ptr3c u;
+  for (int d = 0; d < 3; ++d) u.a[d] = uvel[d];
+  unsigned nb = (unsigned)((N.eta + kBlock - 1) / kBlock);
+  if (D == 3) k_interp_advance<3><<<nb, kBlock, 0, s>>>(g, N, u, phi_kind, dt_over_sigma);
+  else k_interp_advance<2><<<nb, kBlock, 0, s>>>(g, N, u, phi_kind, dt_over_sigma);
+}
+
+void launch_step_increment(long long* step, cudaStream_t s) {
+  k_step_increment<<<1, 32, 0, s>>>(step);
+}
+
+}  // namespace bf

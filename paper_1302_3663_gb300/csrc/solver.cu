@@ -1,0 +1,1001 @@
+// Context, multigrid driver, time step and C ABI of libbfibm (include/bfibm.h).
+//
+// Host code here only orchestrates: it validates inputs, lays out device
+// memory, queues kernels on the context's stream (optionally as one CUDA
+// graph per time step) and copies data in and out. Every arithmetic step of
+// the method runs in the kernels of stencil.cu and lagrangian.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bfibm.h"
+#include "common.cuh"
+
+using namespace bf;
+
+namespace {
+
+struct Level {
+  Geo g;
+  LevelPtrs<double> d;
+};
+
+int edge_count(int D) { return D == 3 ? 3 : 1; }
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+Geo make_geo(const int n[3], const int per[3], int D, double h) {
+  Geo g;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = n[a];
+    g.per[a] = per[a];
+    g.s[a] = (a < D && !per[a]) ? n[a] + 1 : n[a];
+  }
+  if (D == 2) {
+    g.n[2] = 1;
+    g.s[2] = 1;
+    g.per[2] = 1;
+  }
+  long long pitch = round_up(g.s[0], 8);
+  g.st[0] = 1;
+  g.st[1] = pitch;
+  g.st[2] = pitch * g.s[1];
+  g.h = h;
+  return g;
+}
+
+long long level_elems(const Geo& g) { return g.st[2] * g.s[2]; }
+
+// arrays per level: p, pf, pr, beta[D], u[D], uf[D], ur[D], m[D], muc, mue[E]
+int arrays_per_level(int D) { return 3 + 5 * D + 1 + edge_count(D); }
+
+// Multigrid levels: halve while every axis is even, the halved minimum is at
+// least 2 and every halved periodic axis stays even (so that red-black
+// colouring is consistent across the periodic wrap), up to mg_levels_max.
+int build_levels(const bfibm_params& P, Geo out[kMaxLevels]) {
+  int D = P.dim;
+  int n[3] = {P.n[0], P.n[1], D == 3 ? P.n[2] : 1};
+  int per[3] = {P.periodic[0], P.periodic[1], D == 3 ? P.periodic[2] : 1};
+  int L = 0;
+  double h = P.h;
+  for (;;) {
+    out[L] = make_geo(n, per, D, h);
+    ++L;
+    if (L >= P.mg_levels_max || L >= kMaxLevels) break;
+    bool ok = true;
+    int mn = 1 << 30;
+    for (int a = 0; a < D; ++a) {
+      if (n[a] % 2) ok = false;
+      mn = std::min(mn, n[a] / 2);
+      if (per[a] && (n[a] / 2) % 2) ok = false;
+    }
+    if (!ok || mn < 2) break;
+    for (int a = 0; a < D; ++a) n[a] /= 2;
+    h *= 2.0;
+  }
+  return L;
+}
+
+size_t grid_pool_bytes(const bfibm_params& P, int* nlev = nullptr) {
+  Geo g[kMaxLevels];
+  int L = build_levels(P, g);
+  size_t bytes = 0;
+  for (int l = 0; l < L; ++l) {
+    size_t arr = (size_t)round_up(level_elems(g[l]) * 8, 256);
+    int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0);
+    bytes += arr * na;
+  }
+  bytes += 256 * 16;  // G and scalars
+  if (nlev) *nlev = L;
+  return bytes;
+}
+
+const char* validate(const bfibm_params* p) {
+  if (!p) return "params is NULL";
+  if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
+  for (int a = 0; a < p->dim; ++a) {
+    if (p->n[a] < 2) return "every n[a] must be >= 2";
+    if (p->periodic[a] && (p->n[a] % 2)) return "a periodic axis needs an even cell count";
+  }
+  if (p->dim == 2 && p->n[2] != 1) return "n[2] must be 1 when dim == 2";
+  if (p->flow_axis < 0 || p->flow_axis >= p->dim) return "flow_axis out of range";
+  if (!p->periodic[p->flow_axis]) return "the flow axis must be periodic";
+  for (int a = 0; a < p->dim; ++a)
+    if (a != p->flow_axis && p->periodic[a]) {
+      // laminar profile is defined between walls; periodic cross axes are allowed
+      // only with u_center <= 0 (explicit body force)
+      if (p->u_center > 0.0) return "u_center > 0 needs walls on every cross axis";
+    }
+  if (p->phi_kind != 1 && p->phi_kind != 2) return "phi_kind must be 1 or 2";
+  if (!(p->h > 0.0) || !(p->dt > 0.0) || !(p->sigma > 0.0) || !(p->euler > 0.0))
+    return "h, dt, sigma and euler must be positive";
+  if (!(p->rho_f > 0.0) || !(p->mu_f > 0.0) || p->rho_ratio < 1.0 || p->mu_ratio < 1.0)
+    return "rho_f, mu_f > 0 and ratios >= 1 required";
+  if (!(p->omega > 0.0) || !(p->omega_mu > 0.0)) return "omega and omega_mu must be positive";
+  if (p->mg_levels_max < 1 || p->nu1 < 0 || p->nu2 < 0 || p->coarse_sweeps < 1)
+    return "bad multigrid settings";
+  if (p->vc_visc < 0 || p->vc_p < 0 || (p->vc_visc == 0 || p->vc_p == 0) && p->max_cycles < 1)
+    return "bad V-cycle counts";
+  if (p->precision != 0) return "precision 1 is not available in this build";
+  if (!(p->inv_re >= 0.0)) return "inv_re must be >= 0";
+  return nullptr;
+}
+
+}  // namespace
+
+struct bfibm_ctx {
+  bfibm_params P;
+  int D = 0, L = 0;
+  Level lev[kMaxLevels];
+  double* uvel[3] = {nullptr, nullptr, nullptr};
+  double* rho[3] = {nullptr, nullptr, nullptr};
+  double* frc[3] = {nullptr, nullptr, nullptr};
+  double* G_dev = nullptr;
+  Scalars sc{};
+  double* host_sc = nullptr;  // pinned mirror of sc.out
+  char* pool = nullptr;
+  size_t pool_bytes = 0;
+  // Lagrangian state
+  NodeSet N{};
+  SpringSet S{};
+  TileGeo tg{};
+  long long* step_dev = nullptr;
+  int* counters = nullptr;    // [0] clamped, [1] event count
+  std::vector<void*> lag_allocs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t gexec = nullptr;
+  bool use_graph = true;
+  bool collect_stats = true;
+  bool dirty = true;
+  int poisoned = 0;
+  long long step_host = 0;
+  int cycles_visc = 0, cycles_p = 0;
+  long long graph_kernels = -1;   // kernel nodes in the captured step graph
+  std::string err;
+};
+
+namespace {
+
+bfibm_status set_err(bfibm_ctx* c, bfibm_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+bfibm_status cuda_fail(bfibm_ctx* c, cudaError_t e, const char* where) {
+  c->poisoned = 1;
+  return set_err(c, BFIBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);         \
+  } while (0)
+
+#define READY(c)                                                                       \
+  do {                                                                                 \
+    if (!(c)) return BFIBM_EINVAL;                                                     \
+    if ((c)->poisoned) return set_err((c), BFIBM_ESTATE, "context poisoned: " + (c)->err); \
+  } while (0)
+
+void drop_graph(bfibm_ctx* c) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+}
+
+
+// ----------------------------------------------------------------- multigrid
+void vcycle_p(bfibm_ctx* c, int l) {
+  Level& Lv = c->lev[l];
+  cudaStream_t s = c->stream;
+  if (l == c->L - 1) {
+    launch_coarse_p<double>(c->D, Lv.g, Lv.d, c->P.coarse_sweeps, s);
+    return;
+  }
+  for (int it = 0; it < c->P.nu1; ++it) {
+    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 0, s);
+    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 1, s);
+  }
+  launch_p_residual<double>(c->D, Lv.g, Lv.d, s);
+  Level& Lc = c->lev[l + 1];
+  launch_restrict_cell<double>(c->D, Lv.g, Lc.g, Lv.d.pr, Lc.d.pf, Lc.d.p, s);
+  vcycle_p(c, l + 1);
+  launch_prolong_cell<double>(c->D, Lv.g, Lc.g, Lc.d.p, Lv.d.p, s);
+  for (int it = 0; it < c->P.nu2; ++it) {
+    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 0, s);
+    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 1, s);
+  }
+}
+
+void v_sweep(bfibm_ctx* c, int l) {
+  Level& Lv = c->lev[l];
+  for (int d = 0; d < c->D; ++d) {
+    launch_v_rbgs<double>(c->D, Lv.g, Lv.d, d, 0, c->P.inv_re, c->stream);
+    launch_v_rbgs<double>(c->D, Lv.g, Lv.d, d, 1, c->P.inv_re, c->stream);
+  }
+}
+
+void vcycle_v(bfibm_ctx* c, int l) {
+  Level& Lv = c->lev[l];
+  cudaStream_t s = c->stream;
+  if (l == c->L - 1) {
+    launch_coarse_v<double>(c->D, Lv.g, Lv.d, c->P.coarse_sweeps, c->P.inv_re, s);
+    return;
+  }
+  for (int it = 0; it < c->P.nu1; ++it) v_sweep(c, l);
+  launch_v_residual<double>(c->D, Lv.g, Lv.d, c->P.inv_re, s);
+  Level& Lc = c->lev[l + 1];
+  for (int d = 0; d < c->D; ++d)
+    launch_restrict_face<double>(c->D, d, Lv.g, Lc.g, Lv.d.ur[d], Lc.d.uf[d], Lc.d.u[d], s);
+  vcycle_v(c, l + 1);
+  for (int d = 0; d < c->D; ++d)
+    launch_prolong_face<double>(c->D, d, Lv.g, Lc.g, Lc.d.u[d], Lv.d.u[d], s);
+  for (int it = 0; it < c->P.nu2; ++it) v_sweep(c, l);
+}
+
+// scalar slots: 0 scratch (means), 2/3 viscous |f|^2,|r|^2, 4/5 pressure, 6/7 div/KE
+enum { SL_VF = 2, SL_VR = 3, SL_PF = 4, SL_PR = 5, SL_DIV = 6 };
+
+bfibm_status read_scalars(bfibm_ctx* c) {
+  CK(cudaMemcpyAsync(c->host_sc, c->sc.out, 16 * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+// Solve on level 0. Fixed mode only queues work.
+bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
+  Level& L0 = c->lev[0];
+  cudaStream_t s = c->stream;
+  double* one[3] = {L0.d.pf, nullptr, nullptr};
+  double* res[3] = {L0.d.pr, nullptr, nullptr};
+  bool tol = ncycles <= 0;
+  if (tol || c->collect_stats) launch_norm2(c->D, L0.g, one, 0, c->sc, SL_PF, s);
+  if (!tol) {
+    for (int k = 0; k < ncycles; ++k) {
+      vcycle_p(c, 0);
+      launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
+    }
+    if (c->collect_stats) {
+      launch_p_residual<double>(c->D, L0.g, L0.d, s);
+      launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, s);
+    }
+    *used = ncycles;
+    return BFIBM_OK;
+  }
+  bfibm_status st = BFIBM_ENOCONV;
+  int k = 0;
+  for (k = 1; k <= c->P.max_cycles; ++k) {
+    vcycle_p(c, 0);
+    launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
+    launch_p_residual<double>(c->D, L0.g, L0.d, s);
+    launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, s);
+    bfibm_status rs = read_scalars(c);
+    if (rs != BFIBM_OK) return rs;
+    double fn = std::sqrt(c->host_sc[SL_PF]), rn = std::sqrt(c->host_sc[SL_PR]);
+    double rel = fn > 0.0 ? rn / fn : 0.0;
+    if (rel <= c->P.rtol) {
+      st = BFIBM_OK;
+      break;
+    }
+  }
+  *used = std::min(k, c->P.max_cycles);
+  return st;
+}
+
+bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
+  Level& L0 = c->lev[0];
+  cudaStream_t s = c->stream;
+  bool tol = ncycles <= 0;
+  if (tol || c->collect_stats) launch_norm2(c->D, L0.g, L0.d.uf, c->D, c->sc, SL_VF, s);
+  if (!tol) {
+    for (int k = 0; k < ncycles; ++k) vcycle_v(c, 0);
+    if (c->collect_stats) {
+      launch_v_residual<double>(c->D, L0.g, L0.d, c->P.inv_re, s);
+      launch_norm2(c->D, L0.g, L0.d.ur, c->D, c->sc, SL_VR, s);
+    }
+    *used = ncycles;
+    return BFIBM_OK;
+  }
+  bfibm_status st = BFIBM_ENOCONV;
+  int k = 0;
+  for (k = 1; k <= c->P.max_cycles; ++k) {
+    vcycle_v(c, 0);
+    launch_v_residual<double>(c->D, L0.g, L0.d, c->P.inv_re, s);
+    launch_norm2(c->D, L0.g, L0.d.ur, c->D, c->sc, SL_VR, s);
+    bfibm_status rs = read_scalars(c);
+    if (rs != BFIBM_OK) return rs;
+    double fn = std::sqrt(c->host_sc[SL_VF]), rn = std::sqrt(c->host_sc[SL_VR]);
+    double rel = fn > 0.0 ? rn / fn : 0.0;
+    if (rel <= c->P.rtol) {
+      st = BFIBM_OK;
+      break;
+    }
+  }
+  *used = std::min(k, c->P.max_cycles);
+  return st;
+}
+
+// ------------------------------------------------------------------ stages
+void stage_rhs(bfibm_ctx* c) {
+  launch_adv_rhs(c->D, c->lev[0].g, c->uvel, c->rho, c->frc, c->lev[0].d, c->P.c_force,
+                 c->P.flow_axis, c->G_dev, c->stream);
+}
+void stage_divergence(bfibm_ctx* c) {
+  double scale = c->P.sigma / c->P.euler / c->P.dt;
+  launch_divergence(c->D, c->lev[0].g, c->lev[0].d.u, c->lev[0].d.pf, scale, c->sc, c->stream);
+}
+void stage_project(bfibm_ctx* c) {
+  double coef = c->P.euler * c->P.dt / c->P.sigma;
+  launch_project(c->D, c->lev[0].g, c->lev[0].d.u, c->lev[0].d.p, c->lev[0].d.beta, c->uvel,
+                 coef, c->stream);
+}
+void stage_interp_advance(bfibm_ctx* c) {
+  launch_interp_advance(c->D, c->lev[0].g, c->N, c->uvel, c->P.phi_kind, c->P.dt / c->P.sigma,
+                        c->stream);
+}
+void stage_springs(bfibm_ctx* c) { launch_springs(c->D, c->lev[0].g, c->N, c->S, c->stream); }
+
+void build_coefficients(bfibm_ctx* c) {
+  Level& L0 = c->lev[0];
+  launch_coef_fine(c->D, L0.g, c->rho, L0.d.beta, L0.d.m, c->P.sigma / c->P.dt, c->stream);
+  for (int l = 1; l < c->L; ++l)
+    launch_coef_restrict(c->D, c->lev[l - 1].g, c->lev[l].g, c->lev[l - 1].d, c->lev[l].d,
+                         c->P.gamma_coarse, c->stream);
+}
+
+SpreadArgs spread_args(const bfibm_ctx* c) {
+  SpreadArgs a;
+  a.D = c->D;
+  a.phi_kind = c->P.phi_kind;
+  a.omega = c->P.omega;
+  a.omega_mu = c->P.omega_mu;
+  a.amp_rho = (c->P.rho_ratio - 1.0) * c->P.rho_f * c->P.d0_vol;
+  a.mu_out = c->P.mu_f;
+  double tw = 2.0 * c->P.omega_mu;
+  a.mu_coef = (c->D == 3 ? tw * tw * tw : tw * tw) * (c->P.mu_ratio * c->P.mu_f - c->P.mu_f);
+  return a;
+}
+
+// Break test and forces at the current nodes, then f, rho, mu and the
+// coefficient hierarchy.
+void refresh(bfibm_ctx* c) {
+  Level& L0 = c->lev[0];
+  stage_springs(c);
+  launch_reset_fields(c->D, L0.g, c->frc, c->rho, L0.d.muc, L0.d.mue, c->P.rho_f, c->P.mu_f,
+                      c->stream);
+  if (c->N.eta > 0) {
+    launch_bin(c->D, L0.g, c->tg, c->N, c->stream);
+    launch_spread(c->D, L0.g, c->tg, c->N, spread_args(c), c->frc, c->rho, L0.d.muc, L0.d.mue,
+                  c->stream);
+  }
+  build_coefficients(c);
+}
+
+// One time step (Sec. 3.4 order).
+bfibm_status queue_step(bfibm_ctx* c) {
+  stage_rhs(c);
+  bfibm_status st = solve_v(c, c->P.vc_visc, &c->cycles_visc);
+  if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
+  stage_divergence(c);
+  bfibm_status st2 = solve_p(c, c->P.vc_p, &c->cycles_p);
+  if (st2 != BFIBM_OK && st2 != BFIBM_ENOCONV) return st2;
+  stage_project(c);
+  stage_interp_advance(c);
+  launch_step_increment(c->step_dev, c->stream);
+  refresh(c);
+  return (st == BFIBM_ENOCONV || st2 == BFIBM_ENOCONV) ? BFIBM_ENOCONV : BFIBM_OK;
+}
+
+bool fixed_mode(const bfibm_ctx* c) { return c->P.vc_visc > 0 && c->P.vc_p > 0; }
+
+bfibm_status ensure_ready(bfibm_ctx* c) {
+  if (c->dirty) {
+    refresh(c);
+    c->dirty = false;
+    CK(cudaGetLastError());
+  }
+  return BFIBM_OK;
+}
+
+bfibm_status do_steps(bfibm_ctx* c, int nsteps) {
+  bfibm_status st = ensure_ready(c);
+  if (st != BFIBM_OK) return st;
+  bfibm_status agg = BFIBM_OK;
+  if (fixed_mode(c) && c->use_graph) {
+    if (!c->gexec) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      bfibm_status qs = queue_step(c);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+      if (qs != BFIBM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return qs;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      size_t nn = 0;
+      if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        long long nk = 0;
+        if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+          for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+          }
+        c->graph_kernels = nk;
+      }
+      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(c->gexec, c->stream));
+  } else {
+    for (int k = 0; k < nsteps; ++k) {
+      bfibm_status qs = queue_step(c);
+      if (qs == BFIBM_ENOCONV) agg = BFIBM_ENOCONV;
+      else if (qs != BFIBM_OK) return qs;
+    }
+  }
+  CK(cudaGetLastError());
+  c->step_host += nsteps;
+  return agg;
+}
+
+// ------------------------------------------------------------ field access
+double* field_ptr(bfibm_ctx* c, int which, int comp, int level) {
+  if (level < 0 || level >= c->L) return nullptr;
+  int D = c->D;
+  bool vec = (which == BFIBM_F_U || which == BFIBM_F_UT || which == BFIBM_F_URHS ||
+              which == BFIBM_F_RHO || which == BFIBM_F_FORCE || which == BFIBM_F_BETA ||
+              which == BFIBM_F_M || which == BFIBM_F_URES);
+  if (vec && (comp < 0 || comp >= D)) return nullptr;
+  if (which == BFIBM_F_MUE && (comp < 0 || comp >= edge_count(D))) return nullptr;
+  bool fine_only = which == BFIBM_F_U || which == BFIBM_F_RHO || which == BFIBM_F_FORCE;
+  if (fine_only && level != 0) return nullptr;
+  LevelPtrs<double>& L = c->lev[level].d;
+  switch (which) {
+    case BFIBM_F_U: return c->uvel[comp];
+    case BFIBM_F_UT: return L.u[comp];
+    case BFIBM_F_URHS: return L.uf[comp];
+    case BFIBM_F_P: return L.p;
+    case BFIBM_F_PRHS: return L.pf;
+    case BFIBM_F_RHO: return c->rho[comp];
+    case BFIBM_F_FORCE: return c->frc[comp];
+    case BFIBM_F_MUC: return L.muc;
+    case BFIBM_F_MUE: return L.mue[comp];
+    case BFIBM_F_BETA: return L.beta[comp];
+    case BFIBM_F_M: return L.m[comp];
+    case BFIBM_F_URES: return L.ur[comp];
+    case BFIBM_F_PRES: return L.pr;
+  }
+  return nullptr;
+}
+
+bfibm_status copy_field(bfibm_ctx* c, int which, int comp, int level, void* ext, bool to_ext,
+                        cudaMemcpyKind kind) {
+  double* p = field_ptr(c, which, comp, level);
+  if (!p || !ext) return set_err(c, BFIBM_EINVAL, "bad field selector or pointer");
+  const Geo& g = c->lev[level].g;
+  size_t row = (size_t)g.s[0] * sizeof(double);
+  size_t pitch = (size_t)g.st[1] * sizeof(double);
+  size_t rows = (size_t)g.s[1] * g.s[2];
+  if (to_ext)
+    CK(cudaMemcpy2DAsync(ext, row, p, pitch, row, rows, kind, c->stream));
+  else
+    CK(cudaMemcpy2DAsync(p, pitch, ext, row, row, rows, kind, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+void free_lag(bfibm_ctx* c, bool nodes, bool springs) {
+  if (nodes) {
+    for (void* q : {(void*)c->N.X, (void*)c->N.U, (void*)c->N.F, (void*)c->N.tile, (void*)c->N.perm,
+                    (void*)c->N.count, (void*)c->N.start, (void*)c->N.cursor})
+      if (q) cudaFree(q);
+    long long keep_eta = 0;
+    int* clamped = c->N.clamped;
+    c->N = NodeSet{};
+    c->N.eta = keep_eta;
+    c->N.clamped = clamped;
+  }
+  if (springs) {
+    for (void* q : {(void*)c->S.ab, (void*)c->S.rest, (void*)c->S.K, (void*)c->S.brk,
+                    (void*)c->S.broken, (void*)c->S.ev_id, (void*)c->S.ev_step})
+      if (q) cudaFree(q);
+    int* evc = c->S.ev_count;
+    long long* step = c->S.step;
+    c->S = SpringSet{};
+    c->S.ev_count = evc;
+    c->S.step = step;
+  }
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+}  // namespace
+
+// =========================================================================
+// C ABI
+// =========================================================================
+extern "C" {
+
+bfibm_status bfibm_footprint(const bfibm_params* p, int64_t eta, int64_t nsprings,
+                             int64_t* bytes) {
+  if (!bytes || validate(p)) return BFIBM_EINVAL;
+  size_t b = grid_pool_bytes(*p);
+  b += (size_t)eta * (3 * 3 * sizeof(double) + 2 * sizeof(int));
+  b += (size_t)nsprings * (2 * sizeof(int) + 3 * sizeof(double) + 3 * sizeof(int));
+  *bytes = (int64_t)b;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) {
+  if (!out) return BFIBM_EINVAL;
+  *out = nullptr;
+  if (validate(p)) return BFIBM_EINVAL;
+  bfibm_ctx* c = new (std::nothrow) bfibm_ctx();
+  if (!c) return BFIBM_ENOMEM;
+  c->P = *p;
+  c->D = p->dim;
+  Geo geos[kMaxLevels];
+  c->L = build_levels(*p, geos);
+  for (int l = 0; l < c->L; ++l) c->lev[l].g = geos[l];
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return BFIBM_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  c->pool_bytes = grid_pool_bytes(*p);
+  if (cudaMalloc((void**)&c->pool, c->pool_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    bfibm_destroy(c);
+    return BFIBM_ENOMEM;
+  }
+  // carve arrays
+  char* cur = c->pool;
+  auto take = [&](const Geo& g) {
+    double* q = (double*)cur;
+    cur += round_up(level_elems(g) * 8, 256);
+    return q;
+  };
+  int D = c->D, E = edge_count(D);
+  for (int l = 0; l < c->L; ++l) {
+    Level& Lv = c->lev[l];
+    LevelPtrs<double>& d = Lv.d;
+    std::memset(&d, 0, sizeof(d));
+    d.p = take(Lv.g);
+    d.pf = take(Lv.g);
+    d.pr = take(Lv.g);
+    for (int a = 0; a < D; ++a) {
+      d.beta[a] = take(Lv.g);
+      d.u[a] = take(Lv.g);
+      d.uf[a] = take(Lv.g);
+      d.ur[a] = take(Lv.g);
+      d.m[a] = take(Lv.g);
+    }
+    d.muc = take(Lv.g);
+    for (int e = 0; e < E; ++e) d.mue[e] = take(Lv.g);
+    if (l == 0)
+      for (int a = 0; a < D; ++a) {
+        c->uvel[a] = take(Lv.g);
+        c->rho[a] = take(Lv.g);
+        c->frc[a] = take(Lv.g);
+      }
+  }
+  c->G_dev = (double*)cur;
+  cur += 256;
+  c->sc.out = (double*)cur;
+  cur += 256;
+  // remaining scalar room
+  if (cudaMalloc((void**)&c->sc.partial, sizeof(double) * 4 * kRedBlocks) != cudaSuccess ||
+      cudaMalloc((void**)&c->step_dev, sizeof(long long)) != cudaSuccess ||
+      cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
+      cudaMallocHost((void**)&c->host_sc, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    bfibm_destroy(c);
+    return BFIBM_ENOMEM;
+  }
+  c->N.clamped = c->counters;
+  c->S.ev_count = c->counters + 1;
+  c->S.step = c->step_dev;
+  cudaStream_t s = c->stream;
+  bool ok = cudaMemsetAsync(c->pool, 0, c->pool_bytes, s) == cudaSuccess &&
+            cudaMemsetAsync(c->step_dev, 0, sizeof(long long), s) == cudaSuccess &&
+            cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, s) == cudaSuccess;
+  if (!ok) {
+    bfibm_destroy(c);
+    return BFIBM_ECUDA;
+  }
+  // tiles for binning: 8^3 cells in 3D, 16^2 in 2D
+  for (int a = 0; a < 3; ++a) {
+    c->tg.T[a] = (a < D) ? (D == 3 ? 8 : 16) : 1;
+    c->tg.nt[a] = (a < D) ? (p->n[a] + c->tg.T[a] - 1) / c->tg.T[a] : 1;
+  }
+  double wmax = std::max(p->omega, p->omega_mu);
+  c->tg.H = (int)std::ceil(2.0 * wmax / p->h) + 1;
+  c->tg.ntiles = c->tg.nt[0] * c->tg.nt[1] * c->tg.nt[2];
+  {
+    size_t smem = spread_smem_bytes(D, c->tg);
+    if (smem > 48 * 1024 && smem <= 96 * 1024 && spread_set_smem(D, smem) != cudaSuccess) {
+      cudaGetLastError();
+      bfibm_destroy(c);
+      return BFIBM_ECUDA;
+    }
+  }
+  // uniform fluid, laminar initial velocity
+  Level& L0 = c->lev[0];
+  double mu_eff = p->inv_re * p->mu_f;
+  launch_laminar(D, L0.g, p->flow_axis, mu_eff, p->u_center, p->body_force, p->ic_scale,
+                 c->uvel[p->flow_axis], c->G_dev, s);
+  launch_reset_fields(D, L0.g, c->frc, c->rho, L0.d.muc, L0.d.mue, p->rho_f, p->mu_f, s);
+  build_coefficients(c);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    bfibm_destroy(c);
+    return BFIBM_ECUDA;
+  }
+  c->dirty = true;
+  *out = c;
+  return BFIBM_OK;
+}
+
+void bfibm_destroy(bfibm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  free_lag(c, true, true);
+  if (c->pool) cudaFree(c->pool);
+  if (c->sc.partial) cudaFree(c->sc.partial);
+  if (c->step_dev) cudaFree(c->step_dev);
+  if (c->counters) cudaFree(c->counters);
+  if (c->host_sc) cudaFreeHost(c->host_sc);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* bfibm_last_error(const bfibm_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+bfibm_status bfibm_set_nodes(bfibm_ctx* c, int64_t eta, const double* X) {
+  READY(c);
+  if (eta < 0 || (eta > 0 && !X) || eta > (int64_t)0x7fffffff)
+    return set_err(c, BFIBM_EINVAL, "bad node count or pointer");
+  int D = c->D;
+  for (int64_t s = 0; s < eta; ++s)
+    for (int a = 0; a < D; ++a) {
+      double x = X[s * D + a], L = c->P.n[a] * c->P.h;
+      bool ok = std::isfinite(x) && x >= 0.0 && (c->P.periodic[a] ? x < L : x <= L);
+      if (!ok) return set_err(c, BFIBM_EINVAL, "node position outside the domain");
+    }
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  free_lag(c, true, false);
+  NodeSet& N = c->N;
+  N.eta = eta;
+  int nt = c->tg.ntiles;
+  if (dmalloc(&N.X, 3 * eta) || dmalloc(&N.U, 3 * eta) || dmalloc(&N.F, 3 * eta) ||
+      dmalloc(&N.tile, eta) || dmalloc(&N.perm, eta) || dmalloc(&N.count, nt + 1) ||
+      dmalloc(&N.start, nt + 1) || dmalloc(&N.cursor, nt + 1)) {
+    cudaGetLastError();
+    free_lag(c, true, false);
+    c->N.eta = 0;
+    return set_err(c, BFIBM_ENOMEM, "node buffers");
+  }
+  CK(cudaMemsetAsync(N.X, 0, sizeof(double) * 3 * std::max<int64_t>(eta, 1), c->stream));
+  CK(cudaMemsetAsync(N.U, 0, sizeof(double) * 3 * std::max<int64_t>(eta, 1), c->stream));
+  CK(cudaMemsetAsync(N.F, 0, sizeof(double) * 3 * std::max<int64_t>(eta, 1), c->stream));
+  if (eta > 0)
+    CK(cudaMemcpy2DAsync(N.X, 3 * sizeof(double), X, D * sizeof(double), D * sizeof(double),
+                         (size_t)eta, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->dirty = true;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_set_springs(bfibm_ctx* c, int64_t m, const int32_t* ab, const double* rest,
+                               const double* K, const double* brk) {
+  READY(c);
+  if (m < 0 || (m > 0 && (!ab || !rest || !K || !brk)) || m > (int64_t)0x7fffffff)
+    return set_err(c, BFIBM_EINVAL, "bad spring count or pointer");
+  for (int64_t q = 0; q < m; ++q) {
+    int a = ab[2 * q], b = ab[2 * q + 1];
+    if (a < 0 || b < 0 || a >= c->N.eta || b >= c->N.eta || a == b)
+      return set_err(c, BFIBM_EINVAL, "spring endpoint out of range (set nodes first)");
+    if (!(rest[q] >= 0.0) || !std::isfinite(K[q]) || !(brk[q] >= 0.0))
+      return set_err(c, BFIBM_EINVAL, "bad spring constants");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  free_lag(c, false, true);
+  SpringSet& S = c->S;
+  S.m = m;
+  if (dmalloc(&S.ab, 2 * m) || dmalloc(&S.rest, m) || dmalloc(&S.K, m) || dmalloc(&S.brk, m) ||
+      dmalloc(&S.broken, m) || dmalloc(&S.ev_id, m) || dmalloc(&S.ev_step, m)) {
+    cudaGetLastError();
+    free_lag(c, false, true);
+    c->S.m = 0;
+    return set_err(c, BFIBM_ENOMEM, "spring buffers");
+  }
+  if (m > 0) {
+    CK(cudaMemcpyAsync(S.ab, ab, sizeof(int) * 2 * m, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.rest, rest, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.K, K, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.brk, brk, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(S.broken, 0, sizeof(int) * m, c->stream));
+  }
+  CK(cudaMemsetAsync(S.ev_count, 0, sizeof(int), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->dirty = true;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_set_velocity(bfibm_ctx* c, int comp, const double* u) {
+  READY(c);
+  return copy_field(c, BFIBM_F_U, comp, 0, (void*)u, false, cudaMemcpyHostToDevice);
+}
+
+bfibm_status bfibm_step(bfibm_ctx* c, int nsteps) {
+  READY(c);
+  if (nsteps < 0) return set_err(c, BFIBM_EINVAL, "nsteps < 0");
+  return do_steps(c, nsteps);
+}
+
+bfibm_status bfibm_get_velocity(bfibm_ctx* c, int comp, double* out) {
+  READY(c);
+  return copy_field(c, BFIBM_F_U, comp, 0, out, true, cudaMemcpyDeviceToHost);
+}
+
+bfibm_status bfibm_get_pressure(bfibm_ctx* c, double* out) {
+  READY(c);
+  return copy_field(c, BFIBM_F_P, 0, 0, out, true, cudaMemcpyDeviceToHost);
+}
+
+bfibm_status bfibm_get_nodes(bfibm_ctx* c, double* X) {
+  READY(c);
+  if (!X && c->N.eta > 0) return set_err(c, BFIBM_EINVAL, "X is NULL");
+  if (c->N.eta > 0)
+    CK(cudaMemcpy2DAsync(X, c->D * sizeof(double), c->N.X, 3 * sizeof(double),
+                         c->D * sizeof(double), (size_t)c->N.eta, cudaMemcpyDeviceToHost,
+                         c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_get_node_forces(bfibm_ctx* c, double* F) {
+  READY(c);
+  if (!F && c->N.eta > 0) return set_err(c, BFIBM_EINVAL, "F is NULL");
+  if (c->N.eta > 0)
+    CK(cudaMemcpy2DAsync(F, c->D * sizeof(double), c->N.F, 3 * sizeof(double),
+                         c->D * sizeof(double), (size_t)c->N.eta, cudaMemcpyDeviceToHost,
+                         c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_get_broken(bfibm_ctx* c, int64_t cap, int64_t* n, int32_t* spring_id,
+                              int32_t* step) {
+  READY(c);
+  if (!n) return set_err(c, BFIBM_EINVAL, "n is NULL");
+  int cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, c->S.ev_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  cnt = (int)std::min<long long>(cnt, c->S.m);
+  *n = cnt;
+  if (cap <= 0 || cnt == 0) return BFIBM_OK;
+  if (!spring_id || !step) return set_err(c, BFIBM_EINVAL, "output arrays are NULL");
+  std::vector<int32_t> id(cnt), st(cnt);
+  CK(cudaMemcpyAsync(id.data(), c->S.ev_id, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(st.data(), c->S.ev_step, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<int> order(cnt);
+  for (int q = 0; q < cnt; ++q) order[q] = q;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return st[a] != st[b] ? st[a] < st[b] : id[a] < id[b];
+  });
+  int64_t w = std::min<int64_t>(cap, cnt);
+  for (int64_t q = 0; q < w; ++q) {
+    spring_id[q] = id[order[q]];
+    step[q] = st[order[q]];
+  }
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
+  READY(c);
+  if (!out) return set_err(c, BFIBM_EINVAL, "out is NULL");
+  launch_div_ke(c->D, c->lev[0].g, c->uvel, c->sc, SL_DIV, c->stream);
+  CK(cudaGetLastError());
+  bfibm_status rs = read_scalars(c);
+  if (rs != BFIBM_OK) return rs;
+  int cnt[4];
+  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof(*out));
+  out->cycles_visc = c->cycles_visc;
+  out->cycles_p = c->cycles_p;
+  out->broken_total = std::min<int>(cnt[1], (int)std::max<long long>(c->S.m, 0));
+  out->clamped_total = cnt[0];
+  auto rel = [](double f2, double r2) { return f2 > 0.0 ? std::sqrt(r2) / std::sqrt(f2) : 0.0; };
+  out->res_visc = rel(c->host_sc[SL_VF], c->host_sc[SL_VR]);
+  out->res_p = rel(c->host_sc[SL_PF], c->host_sc[SL_PR]);
+  out->div_max = c->host_sc[SL_DIV];
+  out->kinetic = c->host_sc[SL_DIV + 1];
+  out->step = c->step_host;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_get_field(bfibm_ctx* c, int which, int comp, int level, double* out) {
+  READY(c);
+  return copy_field(c, which, comp, level, out, true, cudaMemcpyDeviceToHost);
+}
+bfibm_status bfibm_set_field(bfibm_ctx* c, int which, int comp, int level, const double* in) {
+  READY(c);
+  return copy_field(c, which, comp, level, (void*)in, false, cudaMemcpyHostToDevice);
+}
+bfibm_status bfibm_get_field_dev(bfibm_ctx* c, int which, int comp, int level, double* dev) {
+  READY(c);
+  return copy_field(c, which, comp, level, dev, true, cudaMemcpyDeviceToDevice);
+}
+bfibm_status bfibm_set_field_dev(bfibm_ctx* c, int which, int comp, int level, const double* dev) {
+  READY(c);
+  return copy_field(c, which, comp, level, (void*)dev, false, cudaMemcpyDeviceToDevice);
+}
+
+bfibm_status bfibm_refresh(bfibm_ctx* c) {
+  READY(c);
+  refresh(c);
+  c->dirty = false;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_build_coefficients(bfibm_ctx* c) {
+  READY(c);
+  build_coefficients(c);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_stage(bfibm_ctx* c, int stage) {
+  READY(c);
+  switch (stage) {
+    case BFIBM_STAGE_RHS: stage_rhs(c); break;
+    case BFIBM_STAGE_DIVERGENCE: stage_divergence(c); break;
+    case BFIBM_STAGE_PROJECT: stage_project(c); break;
+    case BFIBM_STAGE_INTERP_ADVANCE: stage_interp_advance(c); break;
+    case BFIBM_STAGE_SPRINGS: stage_springs(c); break;
+    default: return set_err(c, BFIBM_EINVAL, "unknown stage");
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_solve_pressure(bfibm_ctx* c, int ncycles, int32_t* cycles) {
+  READY(c);
+  int used = 0;
+  bfibm_status st = solve_p(c, ncycles, &used);
+  if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
+  c->cycles_p = used;
+  if (cycles) *cycles = used;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles) {
+  READY(c);
+  int used = 0;
+  bfibm_status st = solve_v(c, ncycles, &used);
+  if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
+  c->cycles_visc = used;
+  if (cycles) *cycles = used;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+bfibm_status bfibm_smooth_pressure(bfibm_ctx* c, int level, int nsweeps) {
+  READY(c);
+  if (level < 0 || level >= c->L || nsweeps < 0) return set_err(c, BFIBM_EINVAL, "bad level");
+  for (int k = 0; k < nsweeps; ++k) {
+    launch_p_rbgs<double>(c->D, c->lev[level].g, c->lev[level].d, 0, c->stream);
+    launch_p_rbgs<double>(c->D, c->lev[level].g, c->lev[level].d, 1, c->stream);
+  }
+  CK(cudaGetLastError());
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_smooth_viscous(bfibm_ctx* c, int level, int nsweeps) {
+  READY(c);
+  if (level < 0 || level >= c->L || nsweeps < 0) return set_err(c, BFIBM_EINVAL, "bad level");
+  for (int k = 0; k < nsweeps; ++k) v_sweep(c, level);
+  CK(cudaGetLastError());
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_synchronize(bfibm_ctx* c) {
+  READY(c);
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_residual_pressure(bfibm_ctx* c, int level) {
+  READY(c);
+  if (level < 0 || level >= c->L) return set_err(c, BFIBM_EINVAL, "bad level");
+  launch_p_residual<double>(c->D, c->lev[level].g, c->lev[level].d, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_residual_viscous(bfibm_ctx* c, int level) {
+  READY(c);
+  if (level < 0 || level >= c->L) return set_err(c, BFIBM_EINVAL, "bad level");
+  launch_v_residual<double>(c->D, c->lev[level].g, c->lev[level].d, c->P.inv_re, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_levels(bfibm_ctx* c, int32_t* nlevels) {
+  if (!c || !nlevels) return BFIBM_EINVAL;
+  *nlevels = c->L;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_level_dims(bfibm_ctx* c, int level, int32_t n[3], int32_t s[3]) {
+  if (!c || !n || !s || level < 0 || level >= c->L) return BFIBM_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    n[a] = c->lev[level].g.n[a];
+    s[a] = c->lev[level].g.s[a];
+  }
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_body_force(bfibm_ctx* c, double* G) {
+  READY(c);
+  if (!G) return BFIBM_EINVAL;
+  CK(cudaMemcpyAsync(G, c->G_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n) {
+  READY(c);
+  if (!n) return BFIBM_EINVAL;
+  *n = c->gexec ? c->graph_kernels : -1;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
+  READY(c);
+  if (option == BFIBM_OPT_STATS) {
+    c->collect_stats = value != 0;
+  } else if (option == BFIBM_OPT_GRAPH) {
+    c->use_graph = value != 0;
+  } else {
+    return set_err(c, BFIBM_EINVAL, "unknown option");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  return BFIBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1064 @@
+// Eulerian grid kernels: red-black Gauss-Seidel smoothers, residuals, grid
+// transfers and coarse solves of the two multigrid solves (Sec. 3.5), the
+// explicit momentum right-hand side (Eq. NSdis1-1), the divergence and the
+// projection (Eq. NSdis2 - NSdis4), coefficient hierarchies (Eq.
+// ViscCoarseGrid) and deterministic reductions.
+//
+// Every array of a level shares one layout (see Geo): a wall axis stores one
+// extra plane so that the upper wall face/edge has a slot. All stencil
+// kernels map one thread to one grid point; the red-black kernels map one
+// thread to one point of the colour being updated, so a warp covers 64
+// consecutive x positions.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "common.cuh"
+
+namespace bf {
+
+namespace {
+
+constexpr int kBlock1D = 256;
+
+__host__ __device__ constexpr int edge_id(int d, int e) {
+  return (d < e ? d : e) + (d < e ? e : d) - 1;
+}
+
+inline dim3 blk3(int D) { return D == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1); }
+inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
+  return dim3((unsigned)((nx + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y),
+              (unsigned)((nz + b.z - 1) / b.z));
+}
+inline int red_grid(long long n) {
+  long long b = (n + kBlock1D - 1) / kBlock1D;
+  return (int)(b < kRedBlocks ? (b > 0 ? b : 1) : kRedBlocks);
+}
+
+// offset to the +1 / -1 neighbour along axis a (wrapping on periodic axes;
+// on wall axes the caller decides whether the neighbour exists)
+__device__ __forceinline__ long long offp(const Geo& g, int a, int ci) {
+  return (g.per[a] && ci == g.n[a] - 1) ? -(long long)(g.n[a] - 1) * g.st[a] : g.st[a];
+}
+__device__ __forceinline__ long long offm(const Geo& g, int a, int ci) {
+  return (g.per[a] && ci == 0) ? (long long)(g.n[a] - 1) * g.st[a] : -g.st[a];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// block-wide sum/max; the result is valid in thread 0
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+__device__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_max(v);
+  __syncthreads();
+  return v;
+}
+
+// decode a flattened cell index over n[0] x n[1] x n[2]
+__device__ __forceinline__ void decode(const Geo& g, long long idx, int& i, int& j, int& k) {
+  i = (int)(idx % g.n[0]);
+  long long r = idx / g.n[0];
+  j = (int)(r % g.n[1]);
+  k = (int)(r / g.n[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Pressure operator D.(beta D p), Eq. (divergenceGrad). num = sum of
+// beta_nb p_nb over the existing neighbours, dg = sum of beta_nb; then
+// (A p)(c) = (num - dg p(c)) / h^2. No flux crosses a wall.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ void p_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
+                                        long long c, T& num, T& dg) {
+  num = T(0);
+  dg = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const T* __restrict__ b = L.beta[a];
+    if (ci[a] > 0 || g.per[a]) {
+      long long cm = c + offm(g, a, ci[a]);
+      T bb = b[c];
+      num += bb * L.p[cm];
+      dg += bb;
+    }
+    if (ci[a] < g.n[a] - 1 || g.per[a]) {
+      long long cp = c + offp(g, a, ci[a]);
+      T bb = b[cp];
+      num += bb * L.p[cp];
+      dg += bb;
+    }
+  }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_p_rbgs(Geo g, LevelPtrs<T> L, int colour) {
+  int ih = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  int i = 2 * ih + ((j + k + colour) & 1);
+  if (i >= g.n[0]) return;
+  int ci[3] = {i, j, k};
+  long long c = gidx(g, i, j, k);
+  T num, dg;
+  p_terms<D, T>(g, L, ci, c, num, dg);
+  T h2 = (T)(g.h * g.h);
+  L.p[c] = (num - h2 * L.pf[c]) / dg;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long c = gidx(g, i, j, k);
+  T num, dg;
+  p_terms<D, T>(g, L, ci, c, num, dg);
+  T ih2 = (T)(1.0 / (g.h * g.h));
+  L.pr[c] = L.pf[c] - (num - dg * L.p[c]) * ih2;
+}
+
+// ---------------------------------------------------------------------------
+// Viscous operator for component d at face F (Eq. divergenceGrad +
+// Eq. divergencePartial on the staggered grid): tau_dd = 2 mu_c du_d/dx_d at
+// the cells beside F, tau_de = mu_de (du_d/dx_e + du_e/dx_d) on the edges
+// bounding F. Returns off and dgV with h^2 [div tau]_d = off - dgV u_d(F).
+// Beyond a wall along e the tangential u_d takes the mirror ghost -u_d(F),
+// which doubles that edge's weight in dgV; u_e on the wall is a stored 0.
+// ---------------------------------------------------------------------------
+template <int D, int d, typename T>
+__device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
+                                        long long F, T& off, T& dgV) {
+  const T* __restrict__ ud = L.u[d];
+  long long od_p = offp(g, d, ci[d]);
+  long long od_m = offm(g, d, ci[d]);
+  T mcp = L.muc[F], mcm = L.muc[F + od_m];
+  off = T(2) * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
+  dgV = T(2) * (mcp + mcm);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (e == d) continue;
+    const T* __restrict__ ue = L.u[e];
+    const T* __restrict__ me = L.mue[edge_id(d, e)];
+    bool pe = g.per[e] != 0;
+    bool wp = !pe && ci[e] == g.n[e] - 1;
+    bool wm = !pe && ci[e] == 0;
+    long long Ep = F + offp(g, e, ci[e]);   // e-face index ci[e] + 1
+    T mep = me[Ep], mem = me[F];
+    T cp = ue[Ep] - ue[Ep + od_m];
+    T cm = ue[F] - ue[F + od_m];
+    T udp = T(0), udm = T(0);
+    if (!wp) udp = ud[Ep];
+    if (!wm) udm = ud[F + offm(g, e, ci[e])];
+    off += mep * (udp + cp) + mem * (udm - cm);
+    dgV += (wp ? T(2) : T(1)) * mep + (wm ? T(2) : T(1)) * mem;
+  }
+}
+
+template <int D, int d, typename T>
+__global__ void __launch_bounds__(256) k_v_rbgs(Geo g, LevelPtrs<T> L, int colour, T ir) {
+  int ih = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  int i = 2 * ih + ((j + k + colour) & 1);
+  if (i >= g.n[0]) return;
+  int ci[3] = {i, j, k};
+  if (!g.per[d] && ci[d] == 0) return;   // wall face
+  long long F = gidx(g, i, j, k);
+  T off, dgV;
+  v_terms<D, d, T>(g, L, ci, F, off, dgV);
+  L.u[d][F] = (L.uf[d][F] + ir * off) / (L.m[d][F] + ir * dgV);
+}
+
+template <int D, int d, typename T>
+__device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T>& L,
+                                                 const int ci[3], long long F, T ir) {
+  if (!g.per[d] && ci[d] == 0) {
+    L.ur[d][F] = T(0);
+    return;
+  }
+  T off, dgV;
+  v_terms<D, d, T>(g, L, ci, F, off, dgV);
+  L.ur[d][F] = L.uf[d][F] - (L.m[d][F] + ir * dgV) * L.u[d][F] + ir * off;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long F = gidx(g, i, j, k);
+  v_residual_point<D, 0, T>(g, L, ci, F, ir);
+  v_residual_point<D, 1, T>(g, L, ci, F, ir);
+  if constexpr (D == 3) v_residual_point<D, 2, T>(g, L, ci, F, ir);
+}
+
+// ---------------------------------------------------------------------------
+// Grid transfers (Sec. 3.5).
+// Cell-centred restriction: mean of the 2^D children. Face restriction along
+// its own axis: (1/4, 1/2, 1/4) on the faces 2I-1, 2I, 2I+1; across the other
+// axes the mean of the two children. Both zero the coarse iterate.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_restrict_cell(Geo gf, Geo gc, const T* __restrict__ rf,
+                                                       T* __restrict__ fc, T* __restrict__ xc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  int K = blockIdx.z * blockDim.z + threadIdx.z;
+  if (I >= gc.n[0] || J >= gc.n[1] || K >= gc.n[2]) return;
+  long long f0 = gidx(gf, 2 * I, 2 * J, D == 3 ? 2 * K : 0);
+  long long sy = gf.st[1], sz = gf.st[2];
+  T s = rf[f0] + rf[f0 + 1];
+  s += rf[f0 + sy];
+  s += rf[f0 + sy + 1];
+  if constexpr (D == 3) {
+    s += rf[f0 + sz];
+    s += rf[f0 + sz + 1];
+    s += rf[f0 + sz + sy];
+    s += rf[f0 + sz + sy + 1];
+  }
+  long long c = gidx(gc, I, J, K);
+  fc[c] = s * (D == 3 ? T(0.125) : T(0.25));
+  xc[c] = T(0);
+}
+
+template <int D, int d, typename T>
+__global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* __restrict__ rf,
+                                                       T* __restrict__ fc, T* __restrict__ xc) {
+  int C[3];
+  C[0] = blockIdx.x * blockDim.x + threadIdx.x;
+  C[1] = blockIdx.y * blockDim.y + threadIdx.y;
+  C[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  // along d cover the stored faces (walls included), across d the cells
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int lim = (a == d && a < D) ? gc.s[a] : gc.n[a];
+    if (C[a] >= lim) return;
+  }
+  long long c = gidx(gc, C[0], C[1], C[2]);
+  xc[c] = T(0);
+  bool wallface = !gc.per[d] && (C[d] == 0 || C[d] == gc.n[d]);
+  if (wallface) {
+    fc[c] = T(0);
+    return;
+  }
+  constexpr int ta = (d == 0) ? 1 : 0;
+  constexpr int tb = (D == 3) ? ((d == 2) ? 1 : 2) : -1;
+  int nf = gf.n[d];
+  int f[3] = {0, 0, 0};
+  T s = T(0);
+#pragma unroll
+  for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2) {
+#pragma unroll
+    for (int t1 = 0; t1 < 2; ++t1) {
+      f[ta] = 2 * C[ta] + t1;
+      if constexpr (tb >= 0) f[tb] = 2 * C[tb] + t2;
+      T along = T(0);
+#pragma unroll
+      for (int o = -1; o <= 1; ++o) {
+        int q = 2 * C[d] + o;
+        if (gf.per[d]) q = (q + nf) % nf;
+        f[d] = q;
+        T w = (o == 0) ? T(0.5) : T(0.25);
+        along += w * rf[gidx(gf, f[0], f[1], f[2])];
+      }
+      s += along;
+    }
+  }
+  fc[c] = s * (D == 3 ? T(0.25) : T(0.5));
+}
+
+// 1D prolongation weights. Cell-centred axis: 3/4 on the parent, 1/4 on the
+// next coarse cell toward the child; beyond a wall the mirror ghost
+// (sign `mirror`) folds that 1/4 into the parent. Face axis: the coincident
+// coarse face, or the mean of the two coarse faces around a midway face.
+__device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, double mirror, int idx[2],
+                                            double w[2]) {
+  int I = i >> 1;
+  int J = I + ((i & 1) ? 1 : -1);
+  idx[0] = I;
+  w[0] = 0.75;
+  if (per) {
+    idx[1] = (J + nc) % nc;
+    w[1] = 0.25;
+    return 2;
+  }
+  if (J < 0 || J >= nc) {
+    w[0] = 0.75 + 0.25 * mirror;
+    return 1;
+  }
+  idx[1] = J;
+  w[1] = 0.25;
+  return 2;
+}
+__device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], double w[2]) {
+  int I = i >> 1;
+  if ((i & 1) == 0) {
+    idx[0] = per ? (I % nc) : I;
+    w[0] = 1.0;
+    return 1;
+  }
+  idx[0] = I;
+  w[0] = 0.5;
+  idx[1] = per ? ((I + 1) % nc) : I + 1;
+  w[1] = 0.5;
+  return 2;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* __restrict__ ec,
+                                                      T* __restrict__ xf) {
+  int fi[3];
+  fi[0] = blockIdx.x * blockDim.x + threadIdx.x;
+  fi[1] = blockIdx.y * blockDim.y + threadIdx.y;
+  fi[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
+  int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  double w[3][2] = {{1.0, 0.0}, {1.0, 0.0}, {1.0, 0.0}};
+  int cnt[3] = {1, 1, 1};
+#pragma unroll
+  for (int a = 0; a < D; ++a) cnt[a] = prol_cell_1d(fi[a], gc.n[a], gc.per[a], 1.0, idx[a], w[a]);
+  T v = T(0);
+  for (int c = 0; c < cnt[2]; ++c)
+    for (int b = 0; b < cnt[1]; ++b)
+      for (int a = 0; a < cnt[0]; ++a)
+        v += (T)(w[0][a] * w[1][b] * w[2][c]) * ec[gidx(gc, idx[0][a], idx[1][b], idx[2][c])];
+  xf[gidx(gf, fi[0], fi[1], fi[2])] += v;
+}
+
+template <int D, int d, typename T>
+__global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* __restrict__ ec,
+                                                      T* __restrict__ xf) {
+  int fi[3];
+  fi[0] = blockIdx.x * blockDim.x + threadIdx.x;
+  fi[1] = blockIdx.y * blockDim.y + threadIdx.y;
+  fi[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
+  if (!gf.per[d] && fi[d] == 0) return;
+  int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  double w[3][2] = {{1.0, 0.0}, {1.0, 0.0}, {1.0, 0.0}};
+  int cnt[3] = {1, 1, 1};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a == d)
+      cnt[a] = prol_face_1d(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
+    else
+      cnt[a] = prol_cell_1d(fi[a], gc.n[a], gc.per[a], -1.0, idx[a], w[a]);
+  }
+  T v = T(0);
+  for (int c = 0; c < cnt[2]; ++c)
+    for (int b = 0; b < cnt[1]; ++b)
+      for (int a = 0; a < cnt[0]; ++a)
+        v += (T)(w[0][a] * w[1][b] * w[2][c]) * ec[gidx(gc, idx[0][a], idx[1][b], idx[2][c])];
+  xf[gidx(gf, fi[0], fi[1], fi[2])] += v;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: one block does the whole solve (the grid holds at most a
+// few thousand points and stays in L2). Colour phases are separated by
+// block barriers.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> L, int sweeps) {
+  __shared__ double sh[32];
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  double s = 0.0;
+  for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
+    int i, j, k;
+    decode(g, q, i, j, k);
+    s += (double)L.pf[gidx(g, i, j, k)];
+  }
+  s = block_sum(s, sh);
+  __shared__ double mean;
+  if (threadIdx.x == 0) mean = s / (double)ncell;
+  __syncthreads();
+  for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
+    int i, j, k;
+    decode(g, q, i, j, k);
+    L.pf[gidx(g, i, j, k)] -= (T)mean;
+  }
+  __syncthreads();
+  int nh = (g.n[0] + 1) >> 1;
+  long long npts = (long long)nh * g.n[1] * g.n[2];
+  T h2 = (T)(g.h * g.h);
+  for (int it = 0; it < sweeps; ++it) {
+    for (int colour = 0; colour < 2; ++colour) {
+      for (long long q = threadIdx.x; q < npts; q += blockDim.x) {
+        int ih = (int)(q % nh);
+        long long r = q / nh;
+        int j = (int)(r % g.n[1]);
+        int k = (int)(r / g.n[1]);
+        int i = 2 * ih + ((j + k + colour) & 1);
+        if (i >= g.n[0]) continue;
+        int ci[3] = {i, j, k};
+        long long c = gidx(g, i, j, k);
+        T num, dg;
+        p_terms<D, T>(g, L, ci, c, num, dg);
+        L.p[c] = (num - h2 * L.pf[c]) / dg;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int D, int d, typename T>
+__device__ __forceinline__ void coarse_v_phase(const Geo& g, const LevelPtrs<T>& L, int colour,
+                                               T ir) {
+  int nh = (g.n[0] + 1) >> 1;
+  long long npts = (long long)nh * g.n[1] * g.n[2];
+  for (long long q = threadIdx.x; q < npts; q += blockDim.x) {
+    int ih = (int)(q % nh);
+    long long r = q / nh;
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+    int i = 2 * ih + ((j + k + colour) & 1);
+    if (i >= g.n[0]) continue;
+    int ci[3] = {i, j, k};
+    if (!g.per[d] && ci[d] == 0) continue;
+    long long F = gidx(g, i, j, k);
+    T off, dgV;
+    v_terms<D, d, T>(g, L, ci, F, off, dgV);
+    L.u[d][F] = (L.uf[d][F] + ir * off) / (L.m[d][F] + ir * dgV);
+  }
+  __syncthreads();
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> L, int sweeps, T ir) {
+  for (int it = 0; it < sweeps; ++it) {
+    coarse_v_phase<D, 0, T>(g, L, 0, ir);
+    coarse_v_phase<D, 0, T>(g, L, 1, ir);
+    coarse_v_phase<D, 1, T>(g, L, 0, ir);
+    coarse_v_phase<D, 1, T>(g, L, 1, ir);
+    if constexpr (D == 3) {
+      coarse_v_phase<D, 2, T>(g, L, 0, ir);
+      coarse_v_phase<D, 2, T>(g, L, 1, ir);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients: beta = 1/rho and m = rho sigma/dt on every stored fine face;
+// coarse levels average the fine faces on each coarse face, and the fine
+// points on each coarse centre/edge for mu, scaled by gamma (Eq.
+// ViscCoarseGrid).
+// ---------------------------------------------------------------------------
+struct Ptr3 {
+  double* a[3];
+};
+
+__global__ void __launch_bounds__(256) k_coef_fine(Geo g, int D, Ptr3 rho, Ptr3 beta, Ptr3 m,
+                                                   double msc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.s[0] || j >= g.s[1] || k >= g.s[2]) return;
+  long long c = gidx(g, i, j, k);
+  for (int d = 0; d < D; ++d) {
+    double r = rho.a[d][c];
+    beta.a[d][c] = r != 0.0 ? 1.0 / r : 0.0;
+    m.a[d][c] = r * msc;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_coef_restrict(Geo gf, Geo gc, LevelPtrs<double> F,
+                                                       LevelPtrs<double> Cc, double gamma) {
+  int C[3];
+  C[0] = blockIdx.x * blockDim.x + threadIdx.x;
+  C[1] = blockIdx.y * blockDim.y + threadIdx.y;
+  C[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  if (C[0] >= gc.s[0] || C[1] >= gc.s[1] || C[2] >= gc.s[2]) return;
+  long long c = gidx(gc, C[0], C[1], C[2]);
+  // faces
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (a == d) {
+        if (C[a] > (gc.per[a] ? gc.n[a] - 1 : gc.n[a])) ok = false;
+      } else if (C[a] >= gc.n[a]) {
+        ok = false;
+      }
+    }
+    double sb = 0.0, sm = 0.0;
+    if (ok) {
+      for (int z = 0; z < (D == 3 ? 2 : 1); ++z)
+        for (int y = 0; y < 2; ++y)
+          for (int x = 0; x < 2; ++x) {
+            int off[3] = {x, y, z};
+            if (off[d] != 0) continue;
+            long long f = gidx(gf, 2 * C[0] + x, 2 * C[1] + y, D == 3 ? 2 * C[2] + z : 0);
+            sb += F.beta[d][f];
+            sm += F.m[d][f];
+          }
+    }
+    double wt = (D == 3) ? 0.25 : 0.5;
+    Cc.beta[d][c] = ok ? sb * wt : 0.0;
+    Cc.m[d][c] = ok ? sm * wt : 0.0;
+  }
+  // centres
+  {
+    bool ok = C[0] < gc.n[0] && C[1] < gc.n[1] && C[2] < gc.n[2];
+    if (ok) {
+      long long f0 = gidx(gf, 2 * C[0], 2 * C[1], D == 3 ? 2 * C[2] : 0);
+      long long sy = gf.st[1], sz = gf.st[2];
+      double s = F.muc[f0] + F.muc[f0 + 1];
+      s += F.muc[f0 + sy];
+      s += F.muc[f0 + sy + 1];
+      if (D == 3) {
+        s += F.muc[f0 + sz];
+        s += F.muc[f0 + sz + 1];
+        s += F.muc[f0 + sz + sy];
+        s += F.muc[f0 + sz + sy + 1];
+      }
+      Cc.muc[c] = (s * (D == 3 ? 0.125 : 0.25)) * gamma;
+    } else {
+      Cc.muc[c] = 0.0;
+    }
+  }
+  // edges
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int e = d + 1; e < D; ++e) {
+      int t = 3 - d - e;
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        int lim = (a == d || a == e) ? (gc.per[a] ? gc.n[a] - 1 : gc.n[a]) : gc.n[a] - 1;
+        if (C[a] > lim) ok = false;
+      }
+      double v = 0.0;
+      if (ok) {
+        int f[3] = {2 * C[0], 2 * C[1], D == 3 ? 2 * C[2] : 0};
+        if (D == 3) {
+          double s = 0.0;
+          for (int q = 0; q < 2; ++q) {
+            int gi[3] = {f[0], f[1], f[2]};
+            gi[t] = 2 * C[t] + q;
+            s += F.mue[edge_id(d, e)][gidx(gf, gi[0], gi[1], gi[2])];
+          }
+          v = gamma * (s * 0.5);
+        } else {
+          v = gamma * (F.mue[edge_id(d, e)][gidx(gf, f[0], f[1], f[2])] * 1.0);
+        }
+      }
+      Cc.mue[edge_id(d, e)][c] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Momentum right-hand side, Eq. (NSdis1-1):
+//   rhs_d = m_d u_d - rho_d Adv_d(u) + c_f f_d + G [d = flow axis]
+// Adv_d = 1/2 (u.D u_d + D.(u u_d)): the advective half takes centred wide
+// differences with the velocity averaged to the d-face; the conservative half
+// differences fluxes at the cells (along d) and edges (other axes), each
+// factor a 2-point mean. The iterate u~ starts from u^n.
+// ---------------------------------------------------------------------------
+template <int D, int d>
+__device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, const Ptr3& rho,
+                                              const Ptr3& frc, const LevelPtrs<double>& L0,
+                                              const int ci[3], long long F, double c_force,
+                                              double gflow) {
+  if (!g.per[d] && ci[d] == 0) {
+    L0.uf[d][F] = 0.0;
+    L0.u[d][F] = 0.0;
+    return;
+  }
+  const double* __restrict__ ud = uv.a[d];
+  double h = g.h;
+  long long od_p = offp(g, d, ci[d]), od_m = offm(g, d, ci[d]);
+  double udF = ud[F], udp = ud[F + od_p], udm = ud[F + od_m];
+  double adv = udF * (udp - udm) / (2.0 * h);
+  double cp = 0.5 * (udF + udp), cm = 0.5 * (udm + udF);
+  double cons = (cp * cp - cm * cm) / h;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (e == d) continue;
+    const double* __restrict__ ue = uv.a[e];
+    bool pe = g.per[e] != 0;
+    long long oe_p = offp(g, e, ci[e]);
+    double up = -udF, um = -udF;   // mirror ghosts beyond a wall
+    if (pe || ci[e] != g.n[e] - 1) up = ud[F + oe_p];
+    if (pe || ci[e] != 0) um = ud[F + offm(g, e, ci[e])];
+    double ue_lo = 0.5 * (ue[F + od_m] + ue[F]);
+    double ue_hi = 0.5 * (ue[F + oe_p + od_m] + ue[F + oe_p]);
+    double ubar = 0.5 * (ue_lo + ue_hi);
+    adv += ubar * (up - um) / (2.0 * h);
+    double flux_hi = ue_hi * 0.5 * (udF + up);
+    double flux_lo = ue_lo * 0.5 * (um + udF);
+    cons += (flux_hi - flux_lo) / h;
+  }
+  double A = 0.5 * (adv + cons);
+  L0.uf[d][F] = L0.m[d][F] * udF - rho.a[d][F] * A + c_force * frc.a[d][F] + gflow;
+  L0.u[d][F] = udF;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_adv_rhs(Geo g, Ptr3 uv, Ptr3 rho, Ptr3 frc,
+                                                 LevelPtrs<double> L0, double c_force, int flow,
+                                                 const double* __restrict__ G_dev) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long F = gidx(g, i, j, k);
+  double G = *G_dev;
+  adv_rhs_point<D, 0>(g, uv, rho, frc, L0, ci, F, c_force, flow == 0 ? G : 0.0);
+  adv_rhs_point<D, 1>(g, uv, rho, frc, L0, ci, F, c_force, flow == 1 ? G : 0.0);
+  if constexpr (D == 3) adv_rhs_point<D, 2>(g, uv, rho, frc, L0, ci, F, c_force, flow == 2 ? G : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Divergence, projection and reductions.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ double div_at(const Geo& g, const Ptr3& u, const int ci[3],
+                                         long long c) {
+  double s = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) s += (u.a[a][c + offp(g, a, ci[a])] - u.a[a][c]) / g.h;
+  return s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_divergence(Geo g, Ptr3 u, double* __restrict__ b,
+                                                    double scale, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  double acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int ci[3];
+    decode(g, q, ci[0], ci[1], ci[2]);
+    long long c = gidx(g, ci[0], ci[1], ci[2]);
+    double v = scale * div_at<D>(g, u, ci, c);
+    b[c] = v;
+    acc += v;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_partial_sum(Geo g, const double* __restrict__ a,
+                                                     double* __restrict__ partial) {
+  __shared__ double sh[32];
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  double acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, q, i, j, k);
+    acc += a[gidx(g, i, j, k)];
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// out[slot] = scale * (sum or max of partial[0..nb)), in a fixed order
+__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ partial, int nb,
+                                                   double* __restrict__ out, int slot,
+                                                   double scale, int is_max) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) v = is_max ? fmax(v, partial[q]) : v + partial[q];
+  v = is_max ? block_max(v, sh) : block_sum(v, sh);
+  if (threadIdx.x == 0) out[slot] = v * scale;
+}
+
+__global__ void __launch_bounds__(256) k_sub_scalar(Geo g, double* __restrict__ a,
+                                                    const double* __restrict__ s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  a[gidx(g, i, j, k)] -= *s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* __restrict__ p,
+                                                 Ptr3 beta, Ptr3 uv, double coef) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long F = gidx(g, i, j, k);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    if (!g.per[d] && ci[d] == 0) {
+      uv.a[d][F] = 0.0;
+      continue;
+    }
+    double gp = (p[F] - p[F + offm(g, d, ci[d])]) / g.h;
+    uv.a[d][F] = ut.a[d][F] - coef * beta.a[d][F] * gp;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_norm2(Geo g, Ptr3 a, int ncomp,
+                                               double* __restrict__ partial) {
+  __shared__ double sh[32];
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  double acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int ci[3];
+    decode(g, q, ci[0], ci[1], ci[2]);
+    long long c = gidx(g, ci[0], ci[1], ci[2]);
+    if (ncomp == 0) {
+      double v = a.a[0][c];
+      acc += v * v;
+    } else {
+      for (int d = 0; d < ncomp; ++d) {
+        if (!g.per[d] && ci[d] == 0) continue;
+        double v = a.a[d][c];
+        acc += v * v;
+      }
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_div_ke(Geo g, Ptr3 u, double* __restrict__ pmax,
+                                                double* __restrict__ psum) {
+  __shared__ double sh[32];
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  double mx = 0.0, acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int ci[3];
+    decode(g, q, ci[0], ci[1], ci[2]);
+    long long c = gidx(g, ci[0], ci[1], ci[2]);
+    mx = fmax(mx, fabs(div_at<D>(g, u, ci, c)));
+    for (int d = 0; d < D; ++d) {
+      if (!g.per[d] && ci[d] == 0) continue;
+      double v = u.a[d][c];
+      acc += v * v;
+    }
+  }
+  mx = block_max(mx, sh);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    pmax[blockIdx.x] = mx;
+    psum[blockIdx.x] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Laminar profile (Eq. 2DlaminarSoln, Eq. 3DlaminarFlow) for G = 1 and an
+// effective viscosity of 1. In 3D the double series of Eq. (3DlaminarFlow)
+// is summed over one index in closed form: x(A-x)/2 minus a single series in
+// cosh, summed over the odd n below 1000.
+// ---------------------------------------------------------------------------
+__device__ double laminar_unit(int D, double A, double B, double x, double y) {
+  if (D == 2) return 0.5 * x * (A - x);
+  double sum = 0.0;
+  for (int n = 1; n <= 999; n += 2) {
+    double k = n * CUDART_PI / A;
+    double t1 = exp(k * (y - B)) + exp(-k * y);
+    double t2 = 1.0 + exp(-k * B);
+    sum += sin(k * x) * (t1 / t2) / ((double)n * n * n);
+  }
+  return 0.5 * x * (A - x) - 4.0 * A * A / (CUDART_PI * CUDART_PI * CUDART_PI) * sum;
+}
+
+__global__ void k_body_force(int D, double A, double B, double mu_eff, double u_center,
+                             double body_force, double* G_dev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (u_center > 0.0)
+    *G_dev = u_center * mu_eff / laminar_unit(D, A, B, 0.5 * A, 0.5 * B);
+  else
+    *G_dev = body_force;
+}
+
+// one thread per column across the flow axis; the value is copied along it
+__global__ void k_laminar(Geo g, int D, int fa, int ta0, int ta1, double mu_eff, double ic_scale,
+                          const double* __restrict__ G_dev, double* __restrict__ u) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y * blockDim.y + threadIdx.y;
+  int n0 = g.n[ta0], n1 = (D == 3) ? g.n[ta1] : 1;
+  if (a >= n0 || b >= n1) return;
+  double A = g.n[ta0] * g.h, B = (D == 3) ? g.n[ta1] * g.h : 0.0;
+  double v = ic_scale * (*G_dev) / mu_eff *
+             laminar_unit(D, A, B, (a + 0.5) * g.h, (b + 0.5) * g.h);
+  int lo = g.per[fa] ? 0 : 1;
+  for (int q = lo; q < g.n[fa]; ++q) {
+    int c[3] = {0, 0, 0};
+    c[fa] = q;
+    c[ta0] = a;
+    if (D == 3) c[ta1] = b;
+    u[gidx(g, c[0], c[1], c[2])] = v;
+  }
+}
+
+__global__ void k_fill(double* a, long long n, double v) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    a[q] = v;
+}
+
+}  // namespace
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+template <typename T>
+void launch_p_rbgs(int D, const Geo& g, const LevelPtrs<T>& L, int colour, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3((g.n[0] + 1) / 2, g.n[1], g.n[2], b);
+  if (D == 3) k_p_rbgs<3, T><<<gr, b, 0, s>>>(g, L, colour);
+  else k_p_rbgs<2, T><<<gr, b, 0, s>>>(g, L, colour);
+}
+
+template <typename T>
+void launch_p_residual(int D, const Geo& g, const LevelPtrs<T>& L, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  if (D == 3) k_p_residual<3, T><<<gr, b, 0, s>>>(g, L);
+  else k_p_residual<2, T><<<gr, b, 0, s>>>(g, L);
+}
+
+template <typename T>
+void launch_v_rbgs(int D, const Geo& g, const LevelPtrs<T>& L, int d, int colour, double inv_re,
+                   cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3((g.n[0] + 1) / 2, g.n[1], g.n[2], b);
+  T ir = (T)(inv_re / (g.h * g.h));
+  if (D == 3) {
+    if (d == 0) k_v_rbgs<3, 0, T><<<gr, b, 0, s>>>(g, L, colour, ir);
+    else if (d == 1) k_v_rbgs<3, 1, T><<<gr, b, 0, s>>>(g, L, colour, ir);
+    else k_v_rbgs<3, 2, T><<<gr, b, 0, s>>>(g, L, colour, ir);
+  } else {
+    if (d == 0) k_v_rbgs<2, 0, T><<<gr, b, 0, s>>>(g, L, colour, ir);
+    else k_v_rbgs<2, 1, T><<<gr, b, 0, s>>>(g, L, colour, ir);
+  }
+}
+
+template <typename T>
+void launch_v_residual(int D, const Geo& g, const LevelPtrs<T>& L, double inv_re, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  T ir = (T)(inv_re / (g.h * g.h));
+  if (D == 3) k_v_residual<3, T><<<gr, b, 0, s>>>(g, L, ir);
+  else k_v_residual<2, T><<<gr, b, 0, s>>>(g, L, ir);
+}
+
+template <typename T>
+void launch_restrict_cell(int D, const Geo& gf, const Geo& gc, const T* rf, T* fc, T* xc,
+                          cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(gc.n[0], gc.n[1], gc.n[2], b);
+  if (D == 3) k_restrict_cell<3, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+  else k_restrict_cell<2, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+}
+
+template <typename T>
+void launch_restrict_face(int D, int d, const Geo& gf, const Geo& gc, const T* rf, T* fc, T* xc,
+                          cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(gc.s[0], gc.s[1], gc.s[2], b);
+  if (D == 3) {
+    if (d == 0) k_restrict_face<3, 0, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+    else if (d == 1) k_restrict_face<3, 1, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+    else k_restrict_face<3, 2, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+  } else {
+    if (d == 0) k_restrict_face<2, 0, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+    else k_restrict_face<2, 1, T><<<gr, b, 0, s>>>(gf, gc, rf, fc, xc);
+  }
+}
+
+template <typename T>
+void launch_prolong_cell(int D, const Geo& gf, const Geo& gc, const T* ec, T* xf, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(gf.n[0], gf.n[1], gf.n[2], b);
+  if (D == 3) k_prolong_cell<3, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+  else k_prolong_cell<2, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+}
+
+template <typename T>
+void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec, T* xf,
+                         cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(gf.n[0], gf.n[1], gf.n[2], b);
+  if (D == 3) {
+    if (d == 0) k_prolong_face<3, 0, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+    else if (d == 1) k_prolong_face<3, 1, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+    else k_prolong_face<3, 2, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+  } else {
+    if (d == 0) k_prolong_face<2, 0, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+    else k_prolong_face<2, 1, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
+  }
+}
+
+template <typename T>
+void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cudaStream_t s) {
+  if (D == 3) k_coarse_p<3, T><<<1, 1024, 0, s>>>(g, L, sweeps);
+  else k_coarse_p<2, T><<<1, 1024, 0, s>>>(g, L, sweeps);
+}
+
+template <typename T>
+void launch_coarse_v(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, double inv_re,
+                     cudaStream_t s) {
+  T ir = (T)(inv_re / (g.h * g.h));
+  if (D == 3) k_coarse_v<3, T><<<1, 1024, 0, s>>>(g, L, sweeps, ir);
+  else k_coarse_v<2, T><<<1, 1024, 0, s>>>(g, L, sweeps, ir);
+}
+
+#define BF_INST(T)                                                                           \
+  template void launch_p_rbgs<T>(int, const Geo&, const LevelPtrs<T>&, int, cudaStream_t);   \
+  template void launch_p_residual<T>(int, const Geo&, const LevelPtrs<T>&, cudaStream_t);    \
+  template void launch_v_rbgs<T>(int, const Geo&, const LevelPtrs<T>&, int, int, double,     \
+                                 cudaStream_t);                                              \
+  template void launch_v_residual<T>(int, const Geo&, const LevelPtrs<T>&, double,           \
+                                     cudaStream_t);                                          \
+  template void launch_restrict_cell<T>(int, const Geo&, const Geo&, const T*, T*, T*,       \
+                                        cudaStream_t);                                       \
+  template void launch_restrict_face<T>(int, int, const Geo&, const Geo&, const T*, T*, T*,  \
+                                        cudaStream_t);                                       \
+  template void launch_prolong_cell<T>(int, const Geo&, const Geo&, const T*, T*,            \
+                                       cudaStream_t);                                        \
+  template void launch_prolong_face<T>(int, int, const Geo&, const Geo&, const T*, T*,       \
+                                       cudaStream_t);                                        \
+  template void launch_coarse_p<T>(int, const Geo&, const LevelPtrs<T>&, int, cudaStream_t); \
+  template void launch_coarse_v<T>(int, const Geo&, const LevelPtrs<T>&, int, double,        \
+                                   cudaStream_t);
+BF_INST(double)
+BF_INST(float)
+#undef BF_INST
+
+static Ptr3 ptr3(double* const a[3]) {
+  Ptr3 p;
+  for (int d = 0; d < 3; ++d) p.a[d] = a[d];
+  return p;
+}
+
+void launch_coef_fine(int D, const Geo& g, double* const rho[3], double* beta[3], double* m[3],
+                      double msc, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.s[0], g.s[1], g.s[2], b);
+  k_coef_fine<<<gr, b, 0, s>>>(g, D, ptr3(rho), ptr3(beta), ptr3(m), msc);
+}
+
+void launch_coef_restrict(int D, const Geo& gf, const Geo& gc, const LevelPtrs<double>& F,
+                          const LevelPtrs<double>& C, double gamma, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(gc.s[0], gc.s[1], gc.s[2], b);
+  if (D == 3) k_coef_restrict<3><<<gr, b, 0, s>>>(gf, gc, F, C, gamma);
+  else k_coef_restrict<2><<<gr, b, 0, s>>>(gf, gc, F, C, gamma);
+}
+
+void launch_adv_rhs(int D, const Geo& g, double* const uvel[3], double* const rho[3],
+                    double* const frc[3], const LevelPtrs<double>& L0, double c_force,
+                    int flow_axis, const double* G_dev, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  if (D == 3)
+    k_adv_rhs<3><<<gr, b, 0, s>>>(g, ptr3(uvel), ptr3(rho), ptr3(frc), L0, c_force, flow_axis, G_dev);
+  else
+    k_adv_rhs<2><<<gr, b, 0, s>>>(g, ptr3(uvel), ptr3(rho), ptr3(frc), L0, c_force, flow_axis, G_dev);
+}
+
+void launch_divergence(int D, const Geo& g, double* const u[3], double* b, double scale,
+                       Scalars sc, cudaStream_t s) {
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  int nb = red_grid(ncell);
+  if (D == 3) k_divergence<3><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), b, scale, sc.partial);
+  else k_divergence<2><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), b, scale, sc.partial);
+  k_finalize<<<1, 1024, 0, s>>>(sc.partial, nb, sc.out, 0, 1.0 / (double)ncell, 0);
+  dim3 bb = blk3(D);
+  k_sub_scalar<<<grd3(g.n[0], g.n[1], g.n[2], bb), bb, 0, s>>>(g, b, sc.out);
+}
+
+void launch_sub_mean(int D, const Geo& g, double* a, Scalars sc, cudaStream_t s) {
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  int nb = red_grid(ncell);
+  k_partial_sum<<<nb, kBlock1D, 0, s>>>(g, a, sc.partial);
+  k_finalize<<<1, 1024, 0, s>>>(sc.partial, nb, sc.out, 0, 1.0 / (double)ncell, 0);
+  dim3 bb = blk3(D);
+  k_sub_scalar<<<grd3(g.n[0], g.n[1], g.n[2], bb), bb, 0, s>>>(g, a, sc.out);
+}
+
+void launch_project(int D, const Geo& g, double* const ut[3], const double* p,
+                    double* const beta[3], double* uvel[3], double coef, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  if (D == 3) k_project<3><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef);
+  else k_project<2><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef);
+}
+
+void launch_norm2(int D, const Geo& g, double* const a[3], int ncomp, Scalars sc, int slot,
+                  cudaStream_t s) {
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  int nb = red_grid(ncell);
+  if (D == 3) k_norm2<3><<<nb, kBlock1D, 0, s>>>(g, ptr3(a), ncomp, sc.partial);
+  else k_norm2<2><<<nb, kBlock1D, 0, s>>>(g, ptr3(a), ncomp, sc.partial);
+  k_finalize<<<1, 1024, 0, s>>>(sc.partial, nb, sc.out, slot, 1.0, 0);
+}
+
+void launch_div_ke(int D, const Geo& g, double* const u[3], Scalars sc, int slot, cudaStream_t s) {
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  int nb = red_grid(ncell);
+  double* pmax = sc.partial;
+  double* psum = sc.partial + kRedBlocks;
+  if (D == 3) k_div_ke<3><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), pmax, psum);
+  else k_div_ke<2><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), pmax, psum);
+  double hD = D == 3 ? g.h * g.h * g.h : g.h * g.h;
+  k_finalize<<<1, 1024, 0, s>>>(pmax, nb, sc.out, slot, 1.0, 1);
+  k_finalize<<<1, 1024, 0, s>>>(psum, nb, sc.out, slot + 1, hD, 0);
+}
+
+void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_center,
+                    double body_force, double ic_scale, double* ucomp, double* G_dev,
+                    cudaStream_t s) {
+  int ta[2] = {0, 0}, q = 0;
+  for (int a = 0; a < D; ++a)
+    if (a != flow_axis) ta[q++] = a;
+  double A = g.n[ta[0]] * g.h, B = (D == 3) ? g.n[ta[1]] * g.h : 0.0;
+  k_body_force<<<1, 32, 0, s>>>(D, A, B, mu_eff, u_center, body_force, G_dev);
+  int n0 = g.n[ta[0]], n1 = (D == 3) ? g.n[ta[1]] : 1;
+  dim3 b(32, 8, 1);
+  dim3 gr((n0 + 31) / 32, (n1 + 7) / 8, 1);
+  k_laminar<<<gr, b, 0, s>>>(g, D, flow_axis, ta[0], ta[1], mu_eff, ic_scale, G_dev, ucomp);
+}
+
+void launch_fill(double* a, long long n, double v, cudaStream_t s) {
+  if (n <= 0) return;
+  int nb = red_grid(n);
+  k_fill<<<nb, kBlock1D, 0, s>>>(a, n, v);
+}
+
+}  // namespace bf

@@ -1,0 +1,50 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h
+declares; parameter validation and footprints need no GPU."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1302_3663_gb300 import bfibm, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(bfibm_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    bfibm.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", bfibm.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    missing = declared() - exported
+    assert not missing, missing
+    assert len(declared()) >= 30
+
+
+def test_binding_covers_every_symbol():
+    assert declared() == set(bfibm.SIGNATURES)
+
+
+def test_footprint_and_validation_without_gpu():
+    prm = W.c3()["params"]
+    fp = bfibm.footprint(dict(prm, precision=0), 20000, 150000)
+    cells = 128 * 128 * 256
+    assert 25 * 8 * cells < fp < 60 * 8 * cells
+    bad = dict(W.c1()["params"], phi_kind=3)
+    with pytest.raises(bfibm.BfibmError) as e:
+        bfibm.footprint(bad)
+    assert e.value.status == bfibm.EINVAL
+    for key, val in (("dim", 4), ("n", [63, 32, 1]), ("dt", 0.0), ("flow_axis", 1),
+                     ("mu_ratio", 0.5)):
+        with pytest.raises(bfibm.BfibmError):
+            bfibm.footprint(dict(W.c1()["params"], **{key: val}))

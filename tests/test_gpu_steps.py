@@ -1,0 +1,127 @@
+"""GPU parity over whole time steps: the CUDA library against the FP64 oracle
+on the same seeded workloads. Tolerances (FP64 path): relative L2 of u and p
+at most 1e-10, node positions within 1e-12, identical spring-break events
+(springs within 1e-12 of the break threshold in the oracle are reported and
+excluded)."""
+import numpy as np
+import pytest
+
+from paper_1302_3663_gb300 import bfibm, workloads as W
+
+from helpers import assert_close, pair
+from test_gpu_stages import ragged_duct
+
+pytestmark = pytest.mark.gpu
+
+U_TOL = 1e-10
+X_TOL = 1e-12
+
+
+def near_threshold(o, inst, tol=1e-12):
+    """Springs whose length is within tol (relative) of the break length."""
+    X = o.nodes()
+    prm = inst["params"]
+    d = X[inst["ab"][:, 1]] - X[inst["ab"][:, 0]]
+    for a in range(prm["dim"]):
+        if prm["periodic"][a]:
+            L = prm["n"][a] * prm["h"]
+            d[:, a] -= L * np.round(d[:, a] / L)
+    ratio = np.linalg.norm(d, axis=1) / ((1 + inst["brk"]) * inst["rest"])
+    return set(np.flatnonzero(np.abs(ratio - 1) < tol))
+
+
+def compare_state(g, o, inst, what):
+    D = g.dim
+    for d in range(D):
+        assert_close(g.get_velocity(d), o.get("u", d), U_TOL, "%s u%d" % (what, d))
+    assert_close(g.get_pressure(), o.get("p"), U_TOL, "%s p" % what)
+    Xg, Xo = g.get_nodes(), o.nodes()
+    assert np.abs(Xg - Xo).max() <= X_TOL, "%s nodes %.3e" % (what, np.abs(Xg - Xo).max())
+
+
+def run_pair(inst, steps, override=None, chunk=1):
+    g, o = pair(inst, override)
+    skip = set()
+    done = 0
+    while done < steps:
+        k = min(chunk, steps - done)
+        g.step(k)
+        o.step(k)
+        done += k
+        skip |= near_threshold(o, inst)
+    ig, sg = g.get_broken()
+    io, so = o.broken()
+    ev_g = {(int(i), int(s)) for i, s in zip(ig, sg) if i not in skip}
+    ev_o = {(int(i), int(s)) for i, s in zip(io, so) if i not in skip}
+    assert ev_g == ev_o, (sorted(ev_g ^ ev_o)[:10], len(skip))
+    compare_state(g, o, inst, inst["name"])
+    return g, o, skip
+
+
+def test_c1_full_run():
+    inst = W.c1()
+    g, o, skip = run_pair(inst, inst["steps"])
+    st_g, st_o = g.get_stats(), o.stats()
+    assert st_g["cycles_visc"] == st_o["cycles_visc"] == 3
+    assert abs(st_g["kinetic"] - st_o["kinetic"]) <= 1e-12 * st_o["kinetic"]
+    assert abs(st_g["res_p"] - st_o["res_p"]) <= 1e-6 * st_o["res_p"]
+    assert st_g["step"] == inst["steps"]
+
+
+def test_c1_breaking_springs():
+    # weak springs (break strain 0.02) break within a few steps
+    inst = W.c1()
+    inst["brk"] = np.full(len(inst["rest"]), 0.02)
+    inst["K"] = np.full(len(inst["rest"]), 5.0)
+    g, o, skip = run_pair(inst, 12, {"dt": 4e-3})
+    assert len(o.broken()[0]) > 5
+
+
+def test_ragged_duct_run():
+    inst = ragged_duct()
+    g, o, skip = run_pair(inst, inst["steps"], chunk=5)
+
+
+def test_c2_ten_steps():
+    inst = W.c2()
+    run_pair(inst, 10, chunk=5)
+
+
+def test_no_nodes_duct():
+    inst = ragged_duct(nodes=0)
+    inst["X"] = np.zeros((0, 3))
+    inst["ab"] = np.zeros((0, 2), np.int32)
+    inst["rest"] = inst["K"] = inst["brk"] = np.zeros(0)
+    run_pair(inst, 5, chunk=5)
+
+
+def test_tolerance_mode_matches():
+    inst = W.c1()
+    g, o = pair(inst, {"vc_visc": 0, "vc_p": 0, "rtol": 1e-9, "max_cycles": 40})
+    for k in range(3):
+        g.step(1)
+        o.step(1)
+    sg, so = g.get_stats(), o.stats()
+    assert abs(sg["cycles_p"] - so["cycles_p"]) <= 1 and abs(sg["cycles_visc"] - so["cycles_visc"]) <= 1
+    assert sg["res_p"] <= 1e-9 and sg["res_visc"] <= 1e-9
+    for d in range(2):
+        assert_close(g.get_velocity(d), o.get("u", d), 1e-8, "u%d" % d)
+
+
+def test_graph_replay_equals_direct_launches():
+    inst = W.c1()
+    a = bfibm.load_instance(inst)
+    b = bfibm.load_instance(inst)
+    b.set_option(bfibm.OPT_GRAPH, 0)
+    a.step(6)
+    b.step(6)
+    for d in range(2):
+        assert_close(a.get_velocity(d), b.get_velocity(d), 1e-13, "graph u%d" % d)
+    assert np.abs(a.get_nodes() - b.get_nodes()).max() < 1e-14
+
+
+@pytest.mark.slow
+def test_c3_full_size_two_steps_fp64():
+    # the benchmark's grid (128 x 128 x 256, 20,000 nodes) at full size
+    inst = W.c3(precision=0)
+    run_pair(inst, 2, chunk=2)
