@@ -195,8 +195,9 @@ bfibm_status bfibm_level_dims(bfibm_ctx* c, int level, int32_t n[3], int32_t s[3
 bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
 /* Options: BFIBM_OPT_STATS (1: residual norms after every fixed-count solve,
    default 1), BFIBM_OPT_GRAPH (1: replay fixed-count steps as a CUDA graph,
-   default 1). */
-enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1 };
+   default 1), BFIBM_OPT_FUSED (1: one-pass red-black sweeps, default 1; 0:
+   one kernel per colour). Every option gives the same results to rounding. */
+enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Kernel launches in one replayed time step (the kernel nodes of the captured
    step graph), or -1 when no graph has been captured yet. */

@@ -40,6 +40,12 @@ struct LevelPtrs {
   T* m[3];       // rho sigma / dt on faces
   T* muc;        // mu at centres
   T* mue[3];     // mu on edges: xy, xz, yz
+  T* p2;         // second buffer of p for out-of-place sweeps
+  T* u2[3];      // second buffers of u
+};
+
+struct Ptr3d {
+  double* a[3];
 };
 
 struct Scalars {
@@ -77,6 +83,30 @@ void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cud
 template <typename T>
 void launch_coarse_v(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, double inv_re,
                      cudaStream_t s);
+
+// Fused sweeps (smooth.cu): both colours in one pass, read L.p / L.u[d],
+// write `out`.
+template <typename T>
+void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s);
+template <typename T>
+void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
+                       cudaStream_t s);
+
+// Mixed precision (mixed.cu).
+int red_blocks_3d(int D, const Geo& g);
+void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* r32,
+                             float* e32, double* partial, cudaStream_t s);
+void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
+                             float* const e32[3], double inv_re, double* partial, cudaStream_t s);
+void launch_add_correction(int D, const Geo& g, double* const x[3], float* const e[3], int ncomp,
+                           cudaStream_t s);
+void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
+void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
+void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
+                        const LevelPtrs<float>& L32, cudaStream_t s);
+// out[slot] = scale * sum(partial[0..nb))
+void launch_finalize_sum(const double* partial, int nb, double* out, int slot, double scale,
+                         cudaStream_t s);
 
 // FP64-only grid stages.
 void launch_coef_fine(int D, const Geo& g, double* const rho[3], double* beta[3], double* m[3],

@@ -1,0 +1,276 @@
+// Mixed-precision pieces of the defect-correction solves: each outer
+// iteration computes the fine-grid residual r = f - A x in FP64, hands it to
+// an FP32 V-cycle as the right-hand side of A e = r (e starts at 0), and adds
+// the FP32 correction back into the FP64 iterate. The coarsest grid is solved
+// in FP64 (its right-hand side and solution are converted at the boundary).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bf {
+
+namespace {
+
+constexpr int kBlock1D = 256;
+
+__host__ __device__ constexpr int edge_id(int d, int e) {
+  return (d < e ? d : e) + (d < e ? e : d) - 1;
+}
+__device__ __forceinline__ long long offp(const Geo& g, int a, int ci) {
+  return (g.per[a] && ci == g.n[a] - 1) ? -(long long)(g.n[a] - 1) * g.st[a] : g.st[a];
+}
+__device__ __forceinline__ long long offm(const Geo& g, int a, int ci) {
+  return (g.per[a] && ci == 0) ? (long long)(g.n[a] - 1) * g.st[a] : -g.st[a];
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// sum over a block whose size is a multiple of 32; valid in thread 0
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  int nt = blockDim.x * blockDim.y * blockDim.z;
+  int lane = t & 31, w = t >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (t < (nt + 31) / 32) ? sh[t] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+inline dim3 blk3(int D) { return D == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1); }
+inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
+  return dim3((unsigned)((nx + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y),
+              (unsigned)((nz + b.z - 1) / b.z));
+}
+__device__ __forceinline__ int block_linear() {
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+// FP64 pressure residual written as the FP32 right-hand side of the
+// correction equation; the FP32 correction is zeroed; per-block partial sums
+// of r^2 (for the relative-residual test).
+template <int D>
+__global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<double> L, float* r32,
+                                                          float* e32, double* partial) {
+  __shared__ double sh[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double r2 = 0.0;
+  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+    int ci[3] = {i, j, k};
+    long long c = gidx(g, i, j, k);
+    double num = 0.0, dg = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double* __restrict__ b = L.beta[a];
+      if (ci[a] > 0 || g.per[a]) {
+        double bb = b[c];
+        num += bb * L.p[c + offm(g, a, ci[a])];
+        dg += bb;
+      }
+      if (ci[a] < g.n[a] - 1 || g.per[a]) {
+        long long cp = c + offp(g, a, ci[a]);
+        double bb = b[cp];
+        num += bb * L.p[cp];
+        dg += bb;
+      }
+    }
+    double r = L.pf[c] - (num - dg * L.p[c]) * (1.0 / (g.h * g.h));
+    r32[c] = (float)r;
+    e32[c] = 0.0f;
+    r2 = r * r;
+  }
+  if (partial) {
+    r2 = block_sum(r2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) partial[block_linear()] = r2;
+  }
+}
+
+// FP64 viscous residual of component d at face F (same arithmetic as the
+// FP64 residual kernel)
+template <int D, int d>
+__device__ __forceinline__ double v_res64(const Geo& g, const LevelPtrs<double>& L,
+                                          const int ci[3], long long F, double ir) {
+  const double* __restrict__ ud = L.u[d];
+  long long od_p = offp(g, d, ci[d]);
+  long long od_m = offm(g, d, ci[d]);
+  double mcp = L.muc[F], mcm = L.muc[F + od_m];
+  double off = 2.0 * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
+  double dgV = 2.0 * (mcp + mcm);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (e == d) continue;
+    const double* __restrict__ ue = L.u[e];
+    const double* __restrict__ me = L.mue[edge_id(d, e)];
+    bool pe = g.per[e] != 0;
+    bool wp = !pe && ci[e] == g.n[e] - 1;
+    bool wm = !pe && ci[e] == 0;
+    long long Ep = F + offp(g, e, ci[e]);
+    double mep = me[Ep], mem = me[F];
+    double cp = ue[Ep] - ue[Ep + od_m];
+    double cm = ue[F] - ue[F + od_m];
+    double udp = 0.0, udm = 0.0;
+    if (!wp) udp = ud[Ep];
+    if (!wm) udm = ud[F + offm(g, e, ci[e])];
+    off += mep * (udp + cp) + mem * (udm - cm);
+    dgV += (wp ? 2.0 : 1.0) * mep + (wm ? 2.0 : 1.0) * mem;
+  }
+  return L.uf[d][F] - (L.m[d][F] + ir * dgV) * ud[F] + ir * off;
+}
+
+struct F32x3 {
+  float* a[3];
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
+                                                          F32x3 e32, double ir, double* partial) {
+  __shared__ double sh[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double r2 = 0.0;
+  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+    int ci[3] = {i, j, k};
+    long long F = gidx(g, i, j, k);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double r = 0.0;
+      if (g.per[d] || ci[d] != 0) {
+        if (d == 0) r = v_res64<D, 0>(g, L, ci, F, ir);
+        else if (d == 1) r = v_res64<D, 1>(g, L, ci, F, ir);
+        else r = v_res64<D, (D == 3 ? 2 : 1)>(g, L, ci, F, ir);
+      }
+      r32.a[d][F] = (float)r;
+      e32.a[d][F] = 0.0f;
+      r2 += r * r;
+    }
+  }
+  if (partial) {
+    r2 = block_sum(r2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) partial[block_linear()] = r2;
+  }
+}
+
+// x += e over the unknowns of ncomp face components (ncomp = 0: cells)
+template <int D>
+__global__ void __launch_bounds__(256) k_add_correction(Geo g, Ptr3d x, F32x3 e, int ncomp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long c = gidx(g, i, j, k);
+  if (ncomp == 0) {
+    x.a[0][c] += (double)e.a[0][c];
+    return;
+  }
+  for (int d = 0; d < ncomp; ++d)
+    if (g.per[d] || ci[d] != 0) x.a[d][c] += (double)e.a[d][c];
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_convert(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                 long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    out[q] = (Tout)in[q];
+}
+
+struct ConvList {
+  const double* in[12];
+  float* out[12];
+  int n;
+};
+
+__global__ void __launch_bounds__(256) k_convert_list(ConvList L, long long elems) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < elems;
+       q += (long long)gridDim.x * blockDim.x)
+    for (int a = 0; a < L.n; ++a) L.out[a][q] = (float)L.in[a][q];
+}
+
+}  // namespace
+
+int red_blocks_3d(int D, const Geo& g) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  return (int)(gr.x * gr.y * gr.z);
+}
+
+void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* r32,
+                             float* e32, double* partial, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  if (D == 3) k_p_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r32, e32, partial);
+  else k_p_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r32, e32, partial);
+}
+
+void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
+                             float* const e32[3], double inv_re, double* partial, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  F32x3 r, e;
+  for (int d = 0; d < 3; ++d) {
+    r.a[d] = r32[d];
+    e.a[d] = e32[d];
+  }
+  double ir = inv_re / (g.h * g.h);
+  if (D == 3) k_v_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r, e, ir, partial);
+  else k_v_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r, e, ir, partial);
+}
+
+void launch_add_correction(int D, const Geo& g, double* const x[3], float* const e[3], int ncomp,
+                           cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  Ptr3d xx;
+  F32x3 ee;
+  for (int d = 0; d < 3; ++d) {
+    xx.a[d] = x[d];
+    ee.a[d] = e[d];
+  }
+  if (D == 3) k_add_correction<3><<<gr, b, 0, s>>>(g, xx, ee, ncomp);
+  else k_add_correction<2><<<gr, b, 0, s>>>(g, xx, ee, ncomp);
+}
+
+void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s) {
+  long long nb = (n + kBlock1D - 1) / kBlock1D;
+  if (nb > 4096) nb = 4096;
+  if (nb < 1) nb = 1;
+  k_convert<float, double><<<(unsigned)nb, kBlock1D, 0, s>>>(in, out, n);
+}
+
+void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s) {
+  long long nb = (n + kBlock1D - 1) / kBlock1D;
+  if (nb > 4096) nb = 4096;
+  if (nb < 1) nb = 1;
+  k_convert<double, float><<<(unsigned)nb, kBlock1D, 0, s>>>(in, out, n);
+}
+
+void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
+                        const LevelPtrs<float>& L32, cudaStream_t s) {
+  ConvList cl;
+  cl.n = 0;
+  for (int d = 0; d < D; ++d) {
+    cl.in[cl.n] = L64.beta[d];
+    cl.out[cl.n++] = L32.beta[d];
+    cl.in[cl.n] = L64.m[d];
+    cl.out[cl.n++] = L32.m[d];
+  }
+  cl.in[cl.n] = L64.muc;
+  cl.out[cl.n++] = L32.muc;
+  for (int e = 0; e < (D == 3 ? 3 : 1); ++e) {
+    cl.in[cl.n] = L64.mue[e];
+    cl.out[cl.n++] = L32.mue[e];
+  }
+  long long n = g.st[2] * g.s[2];
+  long long nb = (n + kBlock1D - 1) / kBlock1D;
+  if (nb > 4096) nb = 4096;
+  k_convert_list<<<(unsigned)nb, kBlock1D, 0, s>>>(cl, n);
+}
+
+}  // namespace bf

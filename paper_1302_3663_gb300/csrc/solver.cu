@@ -23,7 +23,8 @@ namespace {
 
 struct Level {
   Geo g;
-  LevelPtrs<double> d;
+  LevelPtrs<double> d;   // FP64 arrays
+  LevelPtrs<float> f;    // FP32 arrays of the mixed-precision V-cycles
 };
 
 int edge_count(int D) { return D == 3 ? 3 : 1; }
@@ -52,8 +53,8 @@ Geo make_geo(const int n[3], const int per[3], int D, double h) {
 
 long long level_elems(const Geo& g) { return g.st[2] * g.s[2]; }
 
-// arrays per level: p, pf, pr, beta[D], u[D], uf[D], ur[D], m[D], muc, mue[E]
-int arrays_per_level(int D) { return 3 + 5 * D + 1 + edge_count(D); }
+// arrays per level: p, p2, pf, pr, beta[D], u[D], u2[D], uf[D], ur[D], m[D], muc, mue[E]
+int arrays_per_level(int D) { return 4 + 6 * D + 1 + edge_count(D); }
 
 // Multigrid levels: halve while every axis is even, the halved minimum is at
 // least 2 and every halved periodic axis stays even (so that red-black
@@ -90,6 +91,8 @@ size_t grid_pool_bytes(const bfibm_params& P, int* nlev = nullptr) {
     size_t arr = (size_t)round_up(level_elems(g[l]) * 8, 256);
     int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0);
     bytes += arr * na;
+    if (P.precision == 1)
+      bytes += (size_t)round_up(level_elems(g[l]) * 4, 256) * arrays_per_level(P.dim);
   }
   bytes += 256 * 16;  // G and scalars
   if (nlev) *nlev = L;
@@ -122,7 +125,7 @@ const char* validate(const bfibm_params* p) {
     return "bad multigrid settings";
   if (p->vc_visc < 0 || p->vc_p < 0 || (p->vc_visc == 0 || p->vc_p == 0) && p->max_cycles < 1)
     return "bad V-cycle counts";
-  if (p->precision != 0) return "precision 1 is not available in this build";
+  if (p->precision != 0 && p->precision != 1) return "precision must be 0 or 1";
   if (!(p->inv_re >= 0.0)) return "inv_re must be >= 0";
   return nullptr;
 }
@@ -152,12 +155,14 @@ struct bfibm_ctx {
   bool own_stream = false;
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
+  bool fused = true;             // one-pass red-black sweeps
   bool collect_stats = true;
   bool dirty = true;
   int poisoned = 0;
   long long step_host = 0;
   int cycles_visc = 0, cycles_p = 0;
   long long graph_kernels = -1;   // kernel nodes in the captured step graph
+  long long partial_cap = 0;      // doubles in sc.partial
   std::string err;
 };
 
@@ -170,6 +175,7 @@ bfibm_status set_err(bfibm_ctx* c, bfibm_status st, const std::string& msg) {
 
 bfibm_status cuda_fail(bfibm_ctx* c, cudaError_t e, const char* where) {
   c->poisoned = 1;
+  cudaGetLastError();  // do not leave the error for the next caller
   return set_err(c, BFIBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -194,6 +200,53 @@ void drop_graph(bfibm_ctx* c) {
 
 
 // ----------------------------------------------------------------- multigrid
+// n red-black sweeps of the pressure iterate on level l. The fused sweep is
+// out of place: the level's two p buffers swap after every sweep and, after
+// an odd count, the result is copied back so that the iterate always ends in
+// its own buffer (a replayed step graph then sees the same buffers).
+void smooth_p(bfibm_ctx* c, int l, int n) {
+  Level& Lv = c->lev[l];
+  cudaStream_t s = c->stream;
+  if (!c->fused) {
+    for (int it = 0; it < n; ++it) {
+      launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 0, s);
+      launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 1, s);
+    }
+    return;
+  }
+  for (int it = 0; it < n; ++it) {
+    launch_p_rb_fused<double>(c->D, Lv.g, Lv.d, Lv.d.p2, s);
+    std::swap(Lv.d.p, Lv.d.p2);
+  }
+  if (n & 1) {
+    cudaMemcpyAsync(Lv.d.p2, Lv.d.p, (size_t)level_elems(Lv.g) * sizeof(double),
+                    cudaMemcpyDeviceToDevice, s);
+    std::swap(Lv.d.p, Lv.d.p2);
+  }
+}
+
+// n block sweeps (component x, y, z in turn) of the viscous iterate.
+void smooth_v(bfibm_ctx* c, int l, int n) {
+  Level& Lv = c->lev[l];
+  cudaStream_t s = c->stream;
+  for (int it = 0; it < n; ++it)
+    for (int d = 0; d < c->D; ++d) {
+      if (!c->fused) {
+        launch_v_rbgs<double>(c->D, Lv.g, Lv.d, d, 0, c->P.inv_re, s);
+        launch_v_rbgs<double>(c->D, Lv.g, Lv.d, d, 1, c->P.inv_re, s);
+      } else {
+        launch_v_rb_fused<double>(c->D, Lv.g, Lv.d, d, Lv.d.u2[d], c->P.inv_re, s);
+        std::swap(Lv.d.u[d], Lv.d.u2[d]);
+      }
+    }
+  if (c->fused && (n & 1))
+    for (int d = 0; d < c->D; ++d) {
+      cudaMemcpyAsync(Lv.d.u2[d], Lv.d.u[d], (size_t)level_elems(Lv.g) * sizeof(double),
+                      cudaMemcpyDeviceToDevice, s);
+      std::swap(Lv.d.u[d], Lv.d.u2[d]);
+    }
+}
+
 void vcycle_p(bfibm_ctx* c, int l) {
   Level& Lv = c->lev[l];
   cudaStream_t s = c->stream;
@@ -201,27 +254,13 @@ void vcycle_p(bfibm_ctx* c, int l) {
     launch_coarse_p<double>(c->D, Lv.g, Lv.d, c->P.coarse_sweeps, s);
     return;
   }
-  for (int it = 0; it < c->P.nu1; ++it) {
-    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 0, s);
-    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 1, s);
-  }
+  smooth_p(c, l, c->P.nu1);
   launch_p_residual<double>(c->D, Lv.g, Lv.d, s);
   Level& Lc = c->lev[l + 1];
   launch_restrict_cell<double>(c->D, Lv.g, Lc.g, Lv.d.pr, Lc.d.pf, Lc.d.p, s);
   vcycle_p(c, l + 1);
   launch_prolong_cell<double>(c->D, Lv.g, Lc.g, Lc.d.p, Lv.d.p, s);
-  for (int it = 0; it < c->P.nu2; ++it) {
-    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 0, s);
-    launch_p_rbgs<double>(c->D, Lv.g, Lv.d, 1, s);
-  }
-}
-
-void v_sweep(bfibm_ctx* c, int l) {
-  Level& Lv = c->lev[l];
-  for (int d = 0; d < c->D; ++d) {
-    launch_v_rbgs<double>(c->D, Lv.g, Lv.d, d, 0, c->P.inv_re, c->stream);
-    launch_v_rbgs<double>(c->D, Lv.g, Lv.d, d, 1, c->P.inv_re, c->stream);
-  }
+  smooth_p(c, l, c->P.nu2);
 }
 
 void vcycle_v(bfibm_ctx* c, int l) {
@@ -231,7 +270,7 @@ void vcycle_v(bfibm_ctx* c, int l) {
     launch_coarse_v<double>(c->D, Lv.g, Lv.d, c->P.coarse_sweeps, c->P.inv_re, s);
     return;
   }
-  for (int it = 0; it < c->P.nu1; ++it) v_sweep(c, l);
+  smooth_v(c, l, c->P.nu1);
   launch_v_residual<double>(c->D, Lv.g, Lv.d, c->P.inv_re, s);
   Level& Lc = c->lev[l + 1];
   for (int d = 0; d < c->D; ++d)
@@ -239,7 +278,7 @@ void vcycle_v(bfibm_ctx* c, int l) {
   vcycle_v(c, l + 1);
   for (int d = 0; d < c->D; ++d)
     launch_prolong_face<double>(c->D, d, Lv.g, Lc.g, Lc.d.u[d], Lv.d.u[d], s);
-  for (int it = 0; it < c->P.nu2; ++it) v_sweep(c, l);
+  smooth_v(c, l, c->P.nu2);
 }
 
 // scalar slots: 0 scratch (means), 2/3 viscous |f|^2,|r|^2, 4/5 pressure, 6/7 div/KE
@@ -325,6 +364,159 @@ bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
   return st;
 }
 
+// ------------------------------------------------------ mixed precision
+// FP32 sweeps on level l (out of place, copied back after an odd count).
+void smooth_p32(bfibm_ctx* c, int l, int n) {
+  Level& Lv = c->lev[l];
+  for (int it = 0; it < n; ++it) {
+    launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream);
+    std::swap(Lv.f.p, Lv.f.p2);
+  }
+  if (n & 1) {
+    cudaMemcpyAsync(Lv.f.p2, Lv.f.p, (size_t)level_elems(Lv.g) * sizeof(float),
+                    cudaMemcpyDeviceToDevice, c->stream);
+    std::swap(Lv.f.p, Lv.f.p2);
+  }
+}
+
+void smooth_v32(bfibm_ctx* c, int l, int n) {
+  Level& Lv = c->lev[l];
+  for (int it = 0; it < n; ++it)
+    for (int d = 0; d < c->D; ++d) {
+      launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream);
+      std::swap(Lv.f.u[d], Lv.f.u2[d]);
+    }
+  if (n & 1)
+    for (int d = 0; d < c->D; ++d) {
+      cudaMemcpyAsync(Lv.f.u2[d], Lv.f.u[d], (size_t)level_elems(Lv.g) * sizeof(float),
+                      cudaMemcpyDeviceToDevice, c->stream);
+      std::swap(Lv.f.u[d], Lv.f.u2[d]);
+    }
+}
+
+// FP32 V-cycle for the correction e of A e = r on level l; the coarsest
+// level is solved in FP64.
+void vcycle_p32(bfibm_ctx* c, int l) {
+  Level& Lv = c->lev[l];
+  cudaStream_t s = c->stream;
+  if (l == c->L - 1) {
+    long long n = level_elems(Lv.g);
+    launch_f32_to_f64(Lv.f.pf, Lv.d.pf, n, s);
+    cudaMemsetAsync(Lv.d.p, 0, n * sizeof(double), s);
+    launch_coarse_p<double>(c->D, Lv.g, Lv.d, c->P.coarse_sweeps, s);
+    launch_f64_to_f32(Lv.d.p, Lv.f.p, n, s);
+    return;
+  }
+  smooth_p32(c, l, c->P.nu1);
+  launch_p_residual<float>(c->D, Lv.g, Lv.f, s);
+  Level& Lc = c->lev[l + 1];
+  launch_restrict_cell<float>(c->D, Lv.g, Lc.g, Lv.f.pr, Lc.f.pf, Lc.f.p, s);
+  vcycle_p32(c, l + 1);
+  launch_prolong_cell<float>(c->D, Lv.g, Lc.g, Lc.f.p, Lv.f.p, s);
+  smooth_p32(c, l, c->P.nu2);
+}
+
+void vcycle_v32(bfibm_ctx* c, int l) {
+  Level& Lv = c->lev[l];
+  cudaStream_t s = c->stream;
+  if (l == c->L - 1) {
+    long long n = level_elems(Lv.g);
+    for (int d = 0; d < c->D; ++d) {
+      launch_f32_to_f64(Lv.f.uf[d], Lv.d.uf[d], n, s);
+      cudaMemsetAsync(Lv.d.u[d], 0, n * sizeof(double), s);
+    }
+    launch_coarse_v<double>(c->D, Lv.g, Lv.d, c->P.coarse_sweeps, c->P.inv_re, s);
+    for (int d = 0; d < c->D; ++d) launch_f64_to_f32(Lv.d.u[d], Lv.f.u[d], n, s);
+    return;
+  }
+  smooth_v32(c, l, c->P.nu1);
+  launch_v_residual<float>(c->D, Lv.g, Lv.f, c->P.inv_re, s);
+  Level& Lc = c->lev[l + 1];
+  for (int d = 0; d < c->D; ++d)
+    launch_restrict_face<float>(c->D, d, Lv.g, Lc.g, Lv.f.ur[d], Lc.f.uf[d], Lc.f.u[d], s);
+  vcycle_v32(c, l + 1);
+  for (int d = 0; d < c->D; ++d)
+    launch_prolong_face<float>(c->D, d, Lv.g, Lc.g, Lc.f.u[d], Lv.f.u[d], s);
+  smooth_v32(c, l, c->P.nu2);
+}
+
+// Defect correction: r = f - A x in FP64 (handed to FP32), one FP32 V-cycle
+// for the correction, x += e in FP64; ncycles > 0 fixed, else until rtol.
+bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
+  Level& L0 = c->lev[0];
+  cudaStream_t s = c->stream;
+  double* one[3] = {L0.d.pf, nullptr, nullptr};
+  bool tol = ncycles <= 0;
+  int nb = red_blocks_3d(c->D, L0.g);
+  if (tol || c->collect_stats) launch_norm2(c->D, L0.g, one, 0, c->sc, SL_PF, s);
+  int maxc = tol ? c->P.max_cycles : ncycles;
+  bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
+  double* xs[3] = {L0.d.p, nullptr, nullptr};
+  float* es[3] = {L0.f.p, nullptr, nullptr};
+  int k = 0;
+  for (k = 1; k <= maxc; ++k) {
+    launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, tol ? c->sc.partial : nullptr, s);
+    if (tol) {
+      launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, s);
+      bfibm_status rs = read_scalars(c);
+      if (rs != BFIBM_OK) return rs;
+      double fn = std::sqrt(c->host_sc[SL_PF]), rn = std::sqrt(c->host_sc[SL_PR]);
+      if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) {
+        st = BFIBM_OK;
+        k -= 1;
+        break;
+      }
+    }
+    vcycle_p32(c, 0);
+    xs[0] = L0.d.p;
+    es[0] = L0.f.p;
+    launch_add_correction(c->D, L0.g, xs, es, 0, s);
+    launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
+  }
+  if (k > maxc) k = maxc;
+  if (c->collect_stats || tol) {
+    launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, c->sc.partial, s);
+    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, s);
+  }
+  *used = k;
+  return st;
+}
+
+bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
+  Level& L0 = c->lev[0];
+  cudaStream_t s = c->stream;
+  bool tol = ncycles <= 0;
+  int nb = red_blocks_3d(c->D, L0.g);
+  if (tol || c->collect_stats) launch_norm2(c->D, L0.g, L0.d.uf, c->D, c->sc, SL_VF, s);
+  int maxc = tol ? c->P.max_cycles : ncycles;
+  bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
+  int k = 0;
+  for (k = 1; k <= maxc; ++k) {
+    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re,
+                            tol ? c->sc.partial : nullptr, s);
+    if (tol) {
+      launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
+      bfibm_status rs = read_scalars(c);
+      if (rs != BFIBM_OK) return rs;
+      double fn = std::sqrt(c->host_sc[SL_VF]), rn = std::sqrt(c->host_sc[SL_VR]);
+      if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) {
+        st = BFIBM_OK;
+        k -= 1;
+        break;
+      }
+    }
+    vcycle_v32(c, 0);
+    launch_add_correction(c->D, L0.g, L0.d.u, L0.f.u, c->D, s);
+  }
+  if (k > maxc) k = maxc;
+  if (c->collect_stats || tol) {
+    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, c->sc.partial, s);
+    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
+  }
+  *used = k;
+  return st;
+}
+
 // ------------------------------------------------------------------ stages
 void stage_rhs(bfibm_ctx* c) {
   launch_adv_rhs(c->D, c->lev[0].g, c->uvel, c->rho, c->frc, c->lev[0].d, c->P.c_force,
@@ -351,6 +543,9 @@ void build_coefficients(bfibm_ctx* c) {
   for (int l = 1; l < c->L; ++l)
     launch_coef_restrict(c->D, c->lev[l - 1].g, c->lev[l].g, c->lev[l - 1].d, c->lev[l].d,
                          c->P.gamma_coarse, c->stream);
+  if (c->P.precision == 1)
+    for (int l = 0; l < c->L; ++l)
+      launch_coef_to_f32(c->D, c->lev[l].g, c->lev[l].d, c->lev[l].f, c->stream);
 }
 
 SpreadArgs spread_args(const bfibm_ctx* c) {
@@ -384,10 +579,13 @@ void refresh(bfibm_ctx* c) {
 // One time step (Sec. 3.4 order).
 bfibm_status queue_step(bfibm_ctx* c) {
   stage_rhs(c);
-  bfibm_status st = solve_v(c, c->P.vc_visc, &c->cycles_visc);
+  bool mixed = c->P.precision == 1;
+  bfibm_status st = mixed ? solve_v_mixed(c, c->P.vc_visc, &c->cycles_visc)
+                          : solve_v(c, c->P.vc_visc, &c->cycles_visc);
   if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
   stage_divergence(c);
-  bfibm_status st2 = solve_p(c, c->P.vc_p, &c->cycles_p);
+  bfibm_status st2 = mixed ? solve_p_mixed(c, c->P.vc_p, &c->cycles_p)
+                           : solve_p(c, c->P.vc_p, &c->cycles_p);
   if (st2 != BFIBM_OK && st2 != BFIBM_ENOCONV) return st2;
   stage_project(c);
   stage_interp_advance(c);
@@ -545,6 +743,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   if (!out) return BFIBM_EINVAL;
   *out = nullptr;
   if (validate(p)) return BFIBM_EINVAL;
+  cudaGetLastError();  // a stale error of an earlier call is not ours
   bfibm_ctx* c = new (std::nothrow) bfibm_ctx();
   if (!c) return BFIBM_ENOMEM;
   c->P = *p;
@@ -580,11 +779,13 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
     LevelPtrs<double>& d = Lv.d;
     std::memset(&d, 0, sizeof(d));
     d.p = take(Lv.g);
+    d.p2 = take(Lv.g);
     d.pf = take(Lv.g);
     d.pr = take(Lv.g);
     for (int a = 0; a < D; ++a) {
       d.beta[a] = take(Lv.g);
       d.u[a] = take(Lv.g);
+      d.u2[a] = take(Lv.g);
       d.uf[a] = take(Lv.g);
       d.ur[a] = take(Lv.g);
       d.m[a] = take(Lv.g);
@@ -598,12 +799,39 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
         c->frc[a] = take(Lv.g);
       }
   }
+  if (p->precision == 1) {
+    auto take32 = [&](const Geo& g) {
+      float* q = (float*)cur;
+      cur += round_up(level_elems(g) * 4, 256);
+      return q;
+    };
+    for (int l = 0; l < c->L; ++l) {
+      Level& Lv = c->lev[l];
+      LevelPtrs<float>& f = Lv.f;
+      std::memset(&f, 0, sizeof(f));
+      f.p = take32(Lv.g);
+      f.p2 = take32(Lv.g);
+      f.pf = take32(Lv.g);
+      f.pr = take32(Lv.g);
+      for (int a = 0; a < D; ++a) {
+        f.beta[a] = take32(Lv.g);
+        f.u[a] = take32(Lv.g);
+        f.u2[a] = take32(Lv.g);
+        f.uf[a] = take32(Lv.g);
+        f.ur[a] = take32(Lv.g);
+        f.m[a] = take32(Lv.g);
+      }
+      f.muc = take32(Lv.g);
+      for (int e = 0; e < E; ++e) f.mue[e] = take32(Lv.g);
+    }
+  }
   c->G_dev = (double*)cur;
   cur += 256;
   c->sc.out = (double*)cur;
   cur += 256;
   // remaining scalar room
-  if (cudaMalloc((void**)&c->sc.partial, sizeof(double) * 4 * kRedBlocks) != cudaSuccess ||
+  c->partial_cap = std::max<long long>(4 * kRedBlocks, red_blocks_3d(D, c->lev[0].g) + 64);
+  if (cudaMalloc((void**)&c->sc.partial, sizeof(double) * c->partial_cap) != cudaSuccess ||
       cudaMalloc((void**)&c->step_dev, sizeof(long long)) != cudaSuccess ||
       cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
       cudaMallocHost((void**)&c->host_sc, 16 * sizeof(double)) != cudaSuccess) {
@@ -687,7 +915,8 @@ bfibm_status bfibm_set_nodes(bfibm_ctx* c, int64_t eta, const double* X) {
   NodeSet& N = c->N;
   N.eta = eta;
   int nt = c->tg.ntiles;
-  if (dmalloc(&N.X, 3 * eta) || dmalloc(&N.U, 3 * eta) || dmalloc(&N.F, 3 * eta) ||
+  long long e3 = 3 * std::max<long long>(eta, 1);
+  if (dmalloc(&N.X, e3) || dmalloc(&N.U, e3) || dmalloc(&N.F, e3) ||
       dmalloc(&N.tile, eta) || dmalloc(&N.perm, eta) || dmalloc(&N.count, nt + 1) ||
       dmalloc(&N.start, nt + 1) || dmalloc(&N.cursor, nt + 1)) {
     cudaGetLastError();
@@ -914,10 +1143,7 @@ bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles) {
 bfibm_status bfibm_smooth_pressure(bfibm_ctx* c, int level, int nsweeps) {
   READY(c);
   if (level < 0 || level >= c->L || nsweeps < 0) return set_err(c, BFIBM_EINVAL, "bad level");
-  for (int k = 0; k < nsweeps; ++k) {
-    launch_p_rbgs<double>(c->D, c->lev[level].g, c->lev[level].d, 0, c->stream);
-    launch_p_rbgs<double>(c->D, c->lev[level].g, c->lev[level].d, 1, c->stream);
-  }
+  smooth_p(c, level, nsweeps);
   CK(cudaGetLastError());
   return BFIBM_OK;
 }
@@ -925,7 +1151,7 @@ bfibm_status bfibm_smooth_pressure(bfibm_ctx* c, int level, int nsweeps) {
 bfibm_status bfibm_smooth_viscous(bfibm_ctx* c, int level, int nsweeps) {
   READY(c);
   if (level < 0 || level >= c->L || nsweeps < 0) return set_err(c, BFIBM_EINVAL, "bad level");
-  for (int k = 0; k < nsweeps; ++k) v_sweep(c, level);
+  smooth_v(c, level, nsweeps);
   CK(cudaGetLastError());
   return BFIBM_OK;
 }
@@ -990,6 +1216,8 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
     c->collect_stats = value != 0;
   } else if (option == BFIBM_OPT_GRAPH) {
     c->use_graph = value != 0;
+  } else if (option == BFIBM_OPT_FUSED) {
+    c->fused = value != 0;
   } else {
     return set_err(c, BFIBM_EINVAL, "unknown option");
   }

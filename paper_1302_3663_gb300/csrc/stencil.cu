@@ -1055,6 +1055,11 @@ void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_
   k_laminar<<<gr, b, 0, s>>>(g, D, flow_axis, ta[0], ta[1], mu_eff, ic_scale, G_dev, ucomp);
 }
 
+void launch_finalize_sum(const double* partial, int nb, double* out, int slot, double scale,
+                         cudaStream_t s) {
+  k_finalize<<<1, 1024, 0, s>>>(partial, nb, out, slot, scale, 0);
+}
+
 void launch_fill(double* a, long long n, double v, cudaStream_t s) {
   if (n <= 0) return;
   int nb = red_grid(n);
