@@ -202,6 +202,28 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Kernel launches in one replayed time step (the kernel nodes of the captured
    step graph), or -1 when no graph has been captured yet. */
 bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n);
+/* Allocation-free divergence stage (the paper has no counterpart: this exists
+   for callers that cannot let a library allocate device memory, such as
+   programs whose device memory is already held by another allocator, services
+   that must not hit an out-of-memory error after start-up, or loops that
+   cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+   cause). Computes what BFIBM_STAGE_DIVERGENCE computes, from the caller's
+   buffers: b = (sigma/euler) D.u / dt at every cell, mean removed.
+   u0, u1, u2: device pointers to the velocity components in the dense field
+   layout above (u2 ignored when dim == 2); b: device pointer, same layout,
+   only the cell entries are written. p supplies dim, n, periodic, h, dt,
+   sigma and euler. stream: the stream to queue on (NULL = legacy default).
+   Returns once the kernels are queued.
+   Scratch: a fixed device array in the library (512 KB per GPU, held until
+   the process exits); grids of more than 2^24 cells are rejected with
+   BFIBM_EINVAL. No cudaMalloc, cudaFree or allocating library call is made.
+   The first call on a device looks up that array's device address
+   (cudaGetSymbolAddress) with the device current; make that first call before
+   any stream capture. Every call shares the array, so calls that overlap on
+   the GPU (other streams, other threads) race and must be serialised by the
+   caller. BFIBM_ECUDA if the lookup or a launch fails. */
+bfibm_status bfibm_divergence_noalloc(const bfibm_params* p, const double* u0, const double* u1,
+                                      const double* u2, double* b, void* stream);
 /* Device bytes a context with these parameters allocates for its grids. */
 bfibm_status bfibm_footprint(const bfibm_params* p, int64_t eta, int64_t nsprings,
                              int64_t* bytes);

@@ -92,6 +92,7 @@ SIGNATURES = {
     "bfibm_set_option": [_V, _i, _L],
     "bfibm_launches_per_step": [_V, C.POINTER(_L)],
     "bfibm_footprint": [C.POINTER(bfibm_params), _L, _L, C.POINTER(_L)],
+    "bfibm_divergence_noalloc": [C.POINTER(bfibm_params), _V, _V, _V, _V, _V],
 }
 _RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None}
 
@@ -145,6 +146,16 @@ def footprint(prm, eta=0, nsprings=0):
     if st != OK:
         raise BfibmError(st, "bfibm_footprint")
     return out.value
+
+
+def divergence_noalloc(prm, u_ptrs, b_ptr, stream=None):
+    """bfibm_divergence_noalloc on device pointers (ints); queues only."""
+    P = make_params(prm)
+    u = list(u_ptrs) + [None] * (3 - len(u_ptrs))
+    st = lib().bfibm_divergence_noalloc(C.byref(P), u[0], u[1], u[2], b_ptr,
+                                        _stream_handle(stream))
+    if st != OK:
+        raise BfibmError(st, "bfibm_divergence_noalloc")
 
 
 def _stream_handle(stream):
