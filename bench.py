@@ -41,8 +41,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c3")
-    ap.add_argument("--precision", type=int, default=0,
-                    help="0: FP64; 1: FP32 V-cycles in FP64 defect correction")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="0: FP64; 1: FP32 V-cycles in FP64 defect correction "
+                         "(default: the workload's own, 1 for c3)")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain FP64 single-instance comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -174,11 +177,10 @@ def max_over_ranks(world, v):
     return float(t.item())
 
 
-def alg_bytes_visc_launch(dim, cells):
-    # one colour of one component: u_d (read + write), rhs_d, m_d, mu_c, and
-    # per other axis one edge-mu array and one cross component: (5 + 2(D-1)) x
-    # 8 B per cell for a full sweep, half of it per colour
-    return (5 + 2 * (dim - 1)) * 8 * cells / 2.0
+def alg_bytes_visc_sweep(dim, cells, elem):
+    # one sweep of one component: u_d (read + write), rhs_d, m_d, mu_c, and per
+    # other axis one edge-mu array and one cross component
+    return (5 + 2 * (dim - 1)) * elem * cells
 
 
 def cpu_baseline(inst, max_seconds=30.0):
@@ -235,24 +237,35 @@ def run_ours(args):
     value = cells * args.steps * world / (ms / 1e3)
     st = ctx.get_stats()
 
-    # dominant kernel: viscous red-black sweep on the finest grid, timed alone
+    # dominant kernel: the viscous red-black sweep on the finest grid, timed
+    # alone with events on the context's stream
+    peak, peak_src = measured_peak()
     sweeps = 10
-    ctx.smooth_viscous(0, 2, sync=True)
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    ctx.smooth_viscous(0, sweeps, sync=False)
-    k1.record(stream)
-    k1.synchronize()
-    nlaunch = sweeps * 2 * prm["dim"]
+    if prm.get("precision", 0) == 1:
+        ctx.smooth_f32(1, 0, 2, sync=True)
+        k0.record(stream)
+        ctx.smooth_f32(1, 0, sweeps, sync=False)
+        k1.record(stream)
+        k1.synchronize()
+        nlaunch = sweeps * prm["dim"]
+        alg = alg_bytes_visc_sweep(prm["dim"], cells, 4)
+        kname = ("k_v_rb_fused<float> (one-pass red-black sweep of one viscous component, "
+                 "FP32, finest grid)")
+    else:
+        ctx.smooth_viscous(0, 2, sync=True)
+        k0.record(stream)
+        ctx.smooth_viscous(0, sweeps, sync=False)
+        k1.record(stream)
+        k1.synchronize()
+        nlaunch = sweeps * 2 * prm["dim"]
+        alg = alg_bytes_visc_sweep(prm["dim"], cells, 8) / 2.0
+        kname = "k_v_rbgs<double> (one colour of one viscous component, FP64, finest grid)"
     launch_s = k0.elapsed_time(k1) / 1e3 / nlaunch
-    peak, peak_src = measured_peak()
-    alg = alg_bytes_visc_launch(prm["dim"], cells)
     achieved = alg / launch_s / 1e9
-    roof = {"kernel": "k_v_rbgs (viscous red-black sweep, one colour of one component, "
-                      "finest grid)",
-            "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+    roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
             "alg_bytes_per_launch": alg, "launch_us": round(launch_s * 1e6, 2),
             "peak_source": peak_src}
     ctx.close()
@@ -271,6 +284,8 @@ def run_ours(args):
            "final_stats": {"div_max": st["div_max"], "kinetic": st["kinetic"],
                            "broken": st["broken_total"]}}
 
+    if not args.no_fp64 and prm.get("precision", 0) == 1:
+        out["fp64_single_instance"] = run_fp64(inst, args, world, stream)
     if not args.no_e2e:
         out["e2e"] = run_e2e(inst, args, world, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -280,6 +295,30 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_fp64(inst, args, world, stream):
+    """The plain FP64 path on the same workload and step count, for comparison."""
+    import torch
+
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+    prm = dict(inst["params"], precision=0)
+    ctx = bfibm.load_instance(dict(inst, params=prm), stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = max_over_ranks(world, e0.elapsed_time(e1))
+    st = ctx.get_stats()
+    ctx.close()
+    return {"value": W.cells(prm) * args.steps * world / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "div_max": st["div_max"]}
 
 
 def run_e2e(inst, args, world, stream):

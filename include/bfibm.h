@@ -186,6 +186,10 @@ bfibm_status bfibm_smooth_viscous(bfibm_ctx* c, int level, int nsweeps);
 /* Residual on one level (synchronous). */
 bfibm_status bfibm_residual_pressure(bfibm_ctx* c, int level);
 bfibm_status bfibm_residual_viscous(bfibm_ctx* c, int level);
+/* nsweeps FP32 red-black sweeps of the correction iterate of a mixed-precision
+   context (which: 0 pressure, 1 viscous) on one level; asynchronous.
+   BFIBM_ESTATE for an FP64 context. */
+bfibm_status bfibm_smooth_f32(bfibm_ctx* c, int which, int level, int nsweeps);
 /* Wait for all work queued on the context's stream. */
 bfibm_status bfibm_synchronize(bfibm_ctx* c);
 /* Number of multigrid levels and their cell counts / storage extents. */
@@ -195,8 +199,10 @@ bfibm_status bfibm_level_dims(bfibm_ctx* c, int level, int32_t n[3], int32_t s[3
 bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
 /* Options: BFIBM_OPT_STATS (1: residual norms after every fixed-count solve,
    default 1), BFIBM_OPT_GRAPH (1: replay fixed-count steps as a CUDA graph,
-   default 1), BFIBM_OPT_FUSED (1: one-pass red-black sweeps, default 1; 0:
-   one kernel per colour). Every option gives the same results to rounding. */
+   default 1), BFIBM_OPT_FUSED (1: one-pass FP64 red-black sweeps; 0, the
+   default: one kernel per colour, faster where FP64 arithmetic rather than
+   memory bounds the sweep; FP32 sweeps are always one-pass). Every option
+   gives the same results to rounding. */
 enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Kernel launches in one replayed time step (the kernel nodes of the captured

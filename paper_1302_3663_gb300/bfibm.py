@@ -84,6 +84,7 @@ SIGNATURES = {
     "bfibm_smooth_pressure": [_V, _i, _i],
     "bfibm_smooth_viscous": [_V, _i, _i],
     "bfibm_synchronize": [_V],
+    "bfibm_smooth_f32": [_V, _i, _i, _i],
     "bfibm_residual_pressure": [_V, _i],
     "bfibm_residual_viscous": [_V, _i],
     "bfibm_levels": [_V, _IP],
@@ -320,6 +321,11 @@ class Context:
 
     def smooth_viscous(self, level=0, nsweeps=1, sync=True):
         self._chk(self.lib.bfibm_smooth_viscous(self.h, level, nsweeps), "bfibm_smooth_viscous")
+        if sync:
+            self.synchronize()
+
+    def smooth_f32(self, which, level=0, nsweeps=1, sync=True):
+        self._chk(self.lib.bfibm_smooth_f32(self.h, which, level, nsweeps), "bfibm_smooth_f32")
         if sync:
             self.synchronize()
 

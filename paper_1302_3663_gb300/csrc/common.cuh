@@ -108,6 +108,12 @@ void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
 void launch_finalize_sum(const double* partial, int nb, double* out, int slot, double scale,
                          cudaStream_t s);
 
+// allow the coarsest-level kernels up to 160 KB of shared memory (call once,
+// outside stream capture)
+cudaError_t coarse_set_smem();
+
+cudaError_t fused_set_carveout();
+
 // FP64-only grid stages.
 void launch_coef_fine(int D, const Geo& g, double* const rho[3], double* beta[3], double* m[3],
                       double msc, cudaStream_t s);
@@ -133,6 +139,9 @@ void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_
                     double body_force, double ic_scale, double* ucomp, double* G_dev,
                     cudaStream_t s);
 void launch_fill(double* a, long long n, double v, cudaStream_t s);
+// device side of a relative-residual while loop in a graph (see solver.cu)
+void launch_tol_check(cudaGraphConditionalHandle h, const double* out, int sf, int sr,
+                      double rtol, int maxc, int* counter, cudaStream_t s);
 
 // ------------------------------------------------------------ lagrangian.cu
 struct NodeSet {
@@ -146,6 +155,8 @@ struct NodeSet {
   int* start;   // ntiles + 1
   int* cursor;  // ntiles
   int* clamped; // 1 counter
+  double* tw;   // eta x 2 widths x 2 staggers x 3 axes x 4: 1D delta weights
+  int* tlo;     // eta x 2 x 2 x 3 x (first index, count)
 };
 struct SpringSet {
   long long m;
@@ -186,5 +197,6 @@ size_t spread_smem_bytes(int D, const TileGeo& tg);
 // opt the spread kernel into more than 48 KB of dynamic shared memory (call
 // once, outside stream capture)
 cudaError_t spread_set_smem(int D, size_t bytes);
+size_t spread_smem_limit();
 
 }  // namespace bf

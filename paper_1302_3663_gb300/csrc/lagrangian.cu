@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <cmath>
+
 #include "common.cuh"
 
 namespace bf {
@@ -203,7 +205,95 @@ __global__ void __launch_bounds__(kBlock) k_reset(int D, Geo g, FieldPtrs P, dou
 }
 
 // ---------------------------------------------------------------------------
-// Tile spread. Shared region per axis: [t T - H, t T + T + H).
+// The width-w delta is a product of 1D factors, so each node evaluates phi
+// once per axis and grid stagger (face: coordinate i h, centre: (i+1/2) h) and
+// every grid point takes the product of three table entries, in the same
+// order (x * y, then * z) as a direct evaluation.
+// ---------------------------------------------------------------------------
+constexpr int kP = 4;   // points per axis held in a table (support width <= 4 cells)
+
+struct W1 {
+  int lo, cnt;
+  double w[kP];
+};
+
+__device__ __forceinline__ void weights1d(const Geo& g, int stag, int a, double X, double wid,
+                                          int kind, W1& o) {
+  int lo, hi;
+  support(g, stag, X, wid, lo, hi);
+  o.lo = lo;
+  o.cnt = hi - lo + 1;
+#pragma unroll
+  for (int q = 0; q < kP; ++q)
+    o.w[q] = (q < o.cnt) ? phi(kind, ((lo + q + 0.5 * stag) * g.h - X) / wid) : 0.0;
+}
+
+// Visit the points of a grid kind inside the support, with tabulated
+// weights: fn(i, j, k unwrapped, global index, prod of phi).
+template <int D, typename Fn>
+__device__ __forceinline__ void for_table(const Geo& g, const int stag[3], const W1* wx,
+                                          const W1* wy, const W1* wz, Fn fn) {
+  int kcnt = (D == 3) ? wz->cnt : 1;
+  for (int kq = 0; kq < kcnt; ++kq) {
+    int k = 0, kk = 0;
+    double pz = 1.0;
+    if constexpr (D == 3) {
+      k = wz->lo + kq;
+      kk = kind_index(g, stag[2], 2, k);
+      if (kk < 0) continue;
+      pz = wz->w[kq];
+    }
+    for (int jq = 0; jq < wy->cnt; ++jq) {
+      int j = wy->lo + jq;
+      int jj = kind_index(g, stag[1], 1, j);
+      if (jj < 0) continue;
+      double py = wy->w[jq];
+      for (int iq = 0; iq < wx->cnt; ++iq) {
+        int i = wx->lo + iq;
+        int ii = kind_index(g, stag[0], 0, i);
+        if (ii < 0) continue;
+        double px = wx->w[iq];
+        fn(i, j, k, gidx(g, ii, jj, kk), px * py * pz);
+      }
+    }
+  }
+}
+
+// Per-node visitor: with TAB (support of at most kP points per axis, i.e.
+// width <= h) the 1D tables are filled once; otherwise phi is evaluated per
+// point.
+template <int D, bool TAB>
+struct NodeVisit {
+  W1 wf[3], wc[3];
+  const double* X;
+  double wid;
+  int kind;
+  __device__ __forceinline__ void init(const Geo& g, const double* X_, double w_, int kind_) {
+    X = X_;
+    wid = w_;
+    kind = kind_;
+    if constexpr (TAB) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        weights1d(g, 0, a, X[a], wid, kind, wf[a]);
+        weights1d(g, 1, a, X[a], wid, kind, wc[a]);
+      }
+    }
+  }
+  template <typename Fn>
+  __device__ __forceinline__ void visit(const Geo& g, const int stag[3], Fn fn) {
+    if constexpr (TAB)
+      for_table<D>(g, stag, stag[0] ? &wc[0] : &wf[0], stag[1] ? &wc[1] : &wf[1],
+                   stag[2] ? &wc[2] : &wf[2], fn);
+    else
+      for_support<D>(g, stag, X, wid, kind, fn);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Tile spread. Shared region per axis: [t T - H, t T + T + H). Pass 1 holds
+// f_d and rho_d of every face grid at once; pass 2 the viscosity maximum of
+// the centres and edges.
 // ---------------------------------------------------------------------------
 struct SpreadK {
   Geo g;
@@ -212,6 +302,8 @@ struct SpreadK {
   SpreadArgs a;
   FieldPtrs P;
   int use_smem;
+  int cmax;        // support points per axis at most
+  int same_width;  // omega_mu == omega: the viscosity pass reuses table 0
   int R[3];
   int vol;
 };
@@ -220,21 +312,63 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
   return (unsigned long long)__double_as_longlong(v);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kBlock) k_spread(SpreadK A) {
+// ---------------------------------------------------------------------------
+// Per-node 1D weight tables, one thread per (node, width, stagger, axis):
+// lo/cnt of the support and phi at its points. Width 0 is omega (force and
+// density), width 1 omega_mu (viscosity).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tab_index(long long s, int wid, int stag, int a) {
+  return (int)(((s * 2 + wid) * 2 + stag) * 3 + a);
+}
+
+__global__ void __launch_bounds__(kBlock) k_node_tables(int D, Geo g, NodeSet N, double w0,
+                                                        double w1, int kind) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= N.eta * 12) return;
+  int a = (int)(q % 3);
+  int stag = (int)((q / 3) % 2);
+  int wid = (int)((q / 6) % 2);
+  long long s = q / 12;
+  if (a >= D) return;
+  double w = wid ? w1 : w0;
+  double X = N.X[3 * s + a];
+  int lo, hi;
+  support(g, stag, X, w, lo, hi);
+  int t = tab_index(s, wid, stag, a);
+  N.tlo[2 * t] = lo;
+  N.tlo[2 * t + 1] = hi - lo + 1;
+#pragma unroll
+  for (int k = 0; k < kP; ++k)
+    N.tw[kP * t + k] = (k <= hi - lo) ? phi(kind, ((lo + k + 0.5 * stag) * g.h - X) / w) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Tile spread: one block per cell tile, one grid kind at a time. Work items
+// are (node, support point) pairs, so dense tiles keep every thread busy;
+// contributions meet in shared memory over the tile region [t T - H,
+// t T + T + H) and leave with one global atomic per non-zero entry.
+// With TAB the weights come from the node tables, otherwise phi is evaluated
+// per point (supports wider than the tables).
+// ---------------------------------------------------------------------------
+constexpr int kSpreadThreads = 512;
+
+template <int D, bool TAB>
+__global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadK A) {
   extern __shared__ double smem[];
   const Geo& g = A.g;
-  int t = blockIdx.x;
-  int s0 = A.N.start[t], s1 = A.N.start[t + 1];
+  const int t = blockIdx.x;
+  const int s0 = A.N.start[t], s1 = A.N.start[t + 1];
   if (s0 == s1) return;
-  int tc[3] = {t % A.tg.nt[0], (t / A.tg.nt[0]) % A.tg.nt[1], t / (A.tg.nt[0] * A.tg.nt[1])};
+  const int nn = s1 - s0;
+  const int tc[3] = {t % A.tg.nt[0], (t / A.tg.nt[0]) % A.tg.nt[1],
+                     t / (A.tg.nt[0] * A.tg.nt[1])};
   int base[3];
   for (int a = 0; a < 3; ++a) base[a] = (a < D) ? tc[a] * A.tg.T[a] - A.tg.H : 0;
-  double* accF = smem;
-  double* accR = smem + A.vol;
-  unsigned long long* accM = reinterpret_cast<unsigned long long*>(smem);
-  int kind = A.a.phi_kind;
-  bool sm = A.use_smem != 0;
+  const int vol = A.vol;
+  const bool sm = A.use_smem != 0;
+  const int kind = A.a.phi_kind;
+  const int C = A.cmax;                       // support points per axis at most
+  const int slots = (D == 3) ? C * C * C : C * C;
   auto local = [&](int i, int j, int k) -> int {
     return (i - base[0]) + A.R[0] * ((j - base[1]) + A.R[1] * (D == 3 ? (k - base[2]) : 0));
   };
@@ -249,39 +383,73 @@ __global__ void __launch_bounds__(kBlock) k_spread(SpreadK A) {
     if (gi < 0 || gj < 0 || gk < 0) return -1;
     return gidx(g, gi, gj, gk);
   };
-  double winvD = 1.0 / (D == 3 ? A.a.omega * A.a.omega * A.a.omega : A.a.omega * A.a.omega);
+  // visit item (node p, slot) of grid kind `stag` at width index wid:
+  // fn(local index or -1, global index, prod of phi)
+  auto item = [&](int p, int slot, const int stag[3], int wid, double w, auto fn) {
+    int sidx = A.N.perm[p];
+    const double* X = &A.N.X[3 * (long long)sidx];
+    (void)X;
+    int off[3] = {slot % C, (slot / C) % C, D == 3 ? slot / (C * C) : 0};
+    int idx[3] = {0, 0, 0}, gl[3] = {0, 0, 0};
+    double pr[3] = {1.0, 1.0, 1.0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int lo, cnt;
+      double wt;
+      if constexpr (TAB) {
+        int ti = tab_index(sidx, wid, stag[a], a);
+        lo = A.N.tlo[2 * ti];
+        cnt = A.N.tlo[2 * ti + 1];
+        if (off[a] >= cnt) return;
+        wt = A.N.tw[kP * ti + off[a]];
+      } else {
+        int hi;
+        support(g, stag[a], X[a], w, lo, hi);
+        cnt = hi - lo + 1;
+        if (off[a] >= cnt) return;
+        wt = phi(kind, ((lo + off[a] + 0.5 * stag[a]) * g.h - X[a]) / w);
+      }
+      idx[a] = lo + off[a];
+      gl[a] = kind_index(g, stag[a], a, idx[a]);
+      if (gl[a] < 0) return;
+      pr[a] = wt;
+    }
+    fn(sm ? local(idx[0], idx[1], idx[2]) : -1, gidx(g, gl[0], gl[1], gl[2]),
+       pr[0] * pr[1] * pr[2]);
+  };
+  const double winvD =
+      1.0 / (D == 3 ? A.a.omega * A.a.omega * A.a.omega : A.a.omega * A.a.omega);
+  const double winvDm =
+      1.0 / (D == 3 ? A.a.omega_mu * A.a.omega_mu * A.a.omega_mu : A.a.omega_mu * A.a.omega_mu);
+  const long long items = (long long)nn * slots;
 
-  // force and density on each face grid
+  // force and density, one face grid at a time
   for (int d = 0; d < D; ++d) {
     int stag[3] = {1, 1, 1};
     stag[d] = 0;
+    double* accF = smem;
+    double* accR = smem + vol;
     if (sm) {
-      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) {
-        accF[q] = 0.0;
-        accR[q] = 0.0;
-      }
+      for (int q = threadIdx.x; q < 2 * vol; q += blockDim.x) smem[q] = 0.0;
       __syncthreads();
     }
-    for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
-      int s = A.N.perm[p];
-      const double* X = &A.N.X[3 * (long long)s];
-      double Fd = A.N.F[3 * (long long)s + d];
-      for_support<D>(g, stag, X, A.a.omega, kind,
-                     [&](int i, int j, int k, long long gi, double w) {
-                       double wt = winvD * w;
-                       if (sm) {
-                         int l = local(i, j, k);
-                         atomicAdd(&accF[l], Fd * wt);
-                         atomicAdd(&accR[l], A.a.amp_rho * wt);
-                       } else {
-                         atomicAdd(&A.P.frc[d][gi], Fd * wt);
-                         atomicAdd(&A.P.rho[d][gi], A.a.amp_rho * wt);
-                       }
-                     });
+    for (long long it = threadIdx.x; it < items; it += blockDim.x) {
+      int p = s0 + (int)(it / slots), slot = (int)(it % slots);
+      double Fd = A.N.F[3 * (long long)A.N.perm[p] + d];
+      item(p, slot, stag, 0, A.a.omega, [&](int l, long long gi, double w) {
+        double wt = winvD * w;
+        if (l >= 0) {
+          atomicAdd(&accF[l], Fd * wt);
+          atomicAdd(&accR[l], A.a.amp_rho * wt);
+        } else {
+          atomicAdd(&A.P.frc[d][gi], Fd * wt);
+          atomicAdd(&A.P.rho[d][gi], A.a.amp_rho * wt);
+        }
+      });
     }
     if (sm) {
       __syncthreads();
-      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) {
+      for (int q = threadIdx.x; q < vol; q += blockDim.x) {
         double vf = accF[q], vr = accR[q];
         if (vf == 0.0 && vr == 0.0) continue;
         long long gi = flush_index(q, stag);
@@ -293,41 +461,35 @@ __global__ void __launch_bounds__(kBlock) k_spread(SpreadK A) {
     }
   }
 
-  // viscosity maximum at centres and on edges (positive doubles order like
-  // their bit patterns, so an unsigned 64-bit max is a floating max)
-  double winvDm =
-      1.0 / (D == 3 ? A.a.omega_mu * A.a.omega_mu * A.a.omega_mu : A.a.omega_mu * A.a.omega_mu);
-  int nkinds = D == 3 ? 4 : 2;
+  // viscosity maximum, one grid at a time (positive doubles order like their
+  // bit patterns, so an unsigned 64-bit max is a floating max)
+  unsigned long long* accM = reinterpret_cast<unsigned long long*>(smem);
+  const unsigned long long floor_bits = dbits(A.a.mu_out);
+  const int nkinds = D == 3 ? 4 : 2;
   for (int kk = 0; kk < nkinds; ++kk) {
     int stag[3] = {1, 1, 1};
     double* target = A.P.muc;
     if (kk > 0) {
       int e = kk - 1;  // 0: xy, 1: xz, 2: yz
-      int da = (e == 2) ? 1 : 0, db = (e == 0) ? 1 : 2;
-      stag[da] = 0;
-      stag[db] = 0;
+      stag[(e == 2) ? 1 : 0] = 0;
+      stag[(e == 0) ? 1 : 2] = 0;
       target = A.P.mue[e];
     }
     if (sm) {
-      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) accM[q] = 0ull;
+      for (int q = threadIdx.x; q < vol; q += blockDim.x) accM[q] = 0ull;
       __syncthreads();
     }
-    for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
-      int s = A.N.perm[p];
-      const double* X = &A.N.X[3 * (long long)s];
-      for_support<D>(g, stag, X, A.a.omega_mu, kind,
-                     [&](int i, int j, int k, long long gi, double w) {
-                       double cand = A.a.mu_coef * (winvDm * w) + A.a.mu_out;
-                       if (sm)
-                         atomicMax(&accM[local(i, j, k)], dbits(cand));
-                       else
-                         atomicMax(reinterpret_cast<unsigned long long*>(&target[gi]), dbits(cand));
-                     });
+    for (long long it = threadIdx.x; it < items; it += blockDim.x) {
+      int p = s0 + (int)(it / slots), slot = (int)(it % slots);
+      item(p, slot, stag, A.same_width ? 0 : 1, A.a.omega_mu, [&](int l, long long gi, double w) {
+        double cand = A.a.mu_coef * (winvDm * w) + A.a.mu_out;
+        if (l >= 0) atomicMax(&accM[l], dbits(cand));
+        else atomicMax(reinterpret_cast<unsigned long long*>(&target[gi]), dbits(cand));
+      });
     }
     if (sm) {
       __syncthreads();
-      unsigned long long floor_bits = dbits(A.a.mu_out);
-      for (int q = threadIdx.x; q < A.vol; q += blockDim.x) {
+      for (int q = threadIdx.x; q < vol; q += blockDim.x) {
         unsigned long long v = accM[q];
         if (v <= floor_bits) continue;
         long long gi = flush_index(q, stag);
@@ -355,14 +517,15 @@ __global__ void __launch_bounds__(kBlock) k_interp_advance(Geo g, NodeSet N, Ptr
   if (s >= N.eta) return;
   double X[3] = {N.X[3 * s], N.X[3 * s + 1], N.X[3 * s + 2]};
   double U[3] = {0.0, 0.0, 0.0};
+  NodeVisit<D, true> nv;   // width h: at most 4 points per axis
+  nv.init(g, X, g.h, kind);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     int stag[3] = {1, 1, 1};
     stag[d] = 0;
     const double* __restrict__ ud = u.a[d];
     double v = 0.0;
-    for_support<D>(g, stag, X, g.h, kind,
-                   [&](int, int, int, long long gi, double w) { v += ud[gi] * w; });
+    nv.visit(g, stag, [&](int, int, int, long long gi, double w) { v += ud[gi] * w; });
     U[d] = v;
   }
   int clamped = 0;
@@ -437,10 +600,20 @@ static void region(int D, const TileGeo& tg, int R[3], int& vol) {
   }
 }
 
+// one grid kind at a time: f and rho of one face grid, or one mu grid
 size_t spread_smem_bytes(int D, const TileGeo& tg) {
   int R[3], vol;
   region(D, tg, R, vol);
   return (size_t)2 * vol * sizeof(double);
+}
+
+size_t spread_smem_limit() { return 200 * 1024; }
+
+bool spread_fits_tables(double omega, double omega_mu, double h) {
+  // a width-w support covers fewer than 4 w / h + 1 points per axis: at most 4
+  // when w <= h
+  double w = omega > omega_mu ? omega : omega_mu;
+  return w <= h;
 }
 
 void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, const SpreadArgs& a,
@@ -459,16 +632,39 @@ void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, con
   A.P.muc = muc;
   region(D, tg, A.R, A.vol);
   size_t smem = spread_smem_bytes(D, tg);
-  A.use_smem = smem <= 96 * 1024 ? 1 : 0;
+  A.use_smem = smem <= spread_smem_limit() ? 1 : 0;
   if (!A.use_smem) smem = 0;
-  if (D == 3) k_spread<3><<<tg.ntiles, kBlock, smem, s>>>(A);
-  else k_spread<2><<<tg.ntiles, kBlock, smem, s>>>(A);
+  bool tab = spread_fits_tables(a.omega, a.omega_mu, g.h);
+  double Rw = (a.omega > a.omega_mu ? a.omega : a.omega_mu) / g.h;
+  A.cmax = (int)std::floor(4.0 * Rw) + 1;
+  if (tab && A.cmax > kP) A.cmax = kP;
+  A.same_width = a.omega == a.omega_mu;
+  if (tab) {
+    long long q = N.eta * 12;
+    k_node_tables<<<(unsigned)((q + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        D, g, N, a.omega, a.omega_mu, a.phi_kind);
+  }
+  if (D == 3) {
+    if (tab) k_spread<3, true><<<tg.ntiles, kSpreadThreads, smem, s>>>(A);
+    else k_spread<3, false><<<tg.ntiles, kSpreadThreads, smem, s>>>(A);
+  } else {
+    if (tab) k_spread<2, true><<<tg.ntiles, kSpreadThreads, smem, s>>>(A);
+    else k_spread<2, false><<<tg.ntiles, kSpreadThreads, smem, s>>>(A);
+  }
 }
 
 cudaError_t spread_set_smem(int D, size_t bytes) {
-  if (D == 3)
-    return cudaFuncSetAttribute(k_spread<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaFuncSetAttribute(k_spread<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e;
+  if (D == 3) {
+    e = cudaFuncSetAttribute(k_spread<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_spread<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
+  }
+  e = cudaFuncSetAttribute(k_spread<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_spread<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
 }
 
 void launch_interp_advance(int D, const Geo& g, const NodeSet& N, double* const uvel[3],

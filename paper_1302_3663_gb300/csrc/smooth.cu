@@ -25,12 +25,6 @@ __host__ __device__ constexpr int edge_id(int d, int e) {
   return (d < e ? d : e) + (d < e ? e : d) - 1;
 }
 
-__device__ __forceinline__ long long offp(const Geo& g, int a, int ci) {
-  return (g.per[a] && ci == g.n[a] - 1) ? -(long long)(g.n[a] - 1) * g.st[a] : g.st[a];
-}
-__device__ __forceinline__ long long offm(const Geo& g, int a, int ci) {
-  return (g.per[a] && ci == 0) ? (long long)(g.n[a] - 1) * g.st[a] : -g.st[a];
-}
 __device__ __forceinline__ int wrapi(int i, int n) { return ((i % n) + n) % n; }
 
 template <int D>
@@ -50,70 +44,96 @@ struct Ring {
 
 __device__ __forceinline__ int slot_of(int k) { return ((k % 3) + 3) % 3; }
 
+// Offsets (32-bit, within one level array) of a point's six neighbours and
+// its wall flags, computed once per point update. op/om wrap on periodic
+// axes; on a wall axis om of the first and op of the last index point beyond
+// the grid and are flagged by wm/wp.
+struct Pt {
+  int F;
+  int op[3], om[3];
+  bool wp[3], wm[3];
+};
+
+template <int D>
+__device__ __forceinline__ void make_pt(const Geo& g, const int ci[3], Pt& q) {
+  const int st[3] = {1, (int)g.st[1], (int)g.st[2]};
+  q.F = ci[0] + st[1] * ci[1] + st[2] * ci[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= D) {
+      q.op[a] = q.om[a] = 0;
+      q.wp[a] = q.wm[a] = true;
+      continue;
+    }
+    bool last = ci[a] == g.n[a] - 1, first = ci[a] == 0;
+    bool per = g.per[a] != 0;
+    q.op[a] = (per && last) ? -(g.n[a] - 1) * st[a] : st[a];
+    q.om[a] = (per && first) ? (g.n[a] - 1) * st[a] : -st[a];
+    q.wp[a] = !per && last;
+    q.wm[a] = !per && first;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pressure: red from the old black values (global), black from the new red
 // values (shared). Neighbours are summed axis 0, 1, 2, lower then upper, as
 // in the two-kernel sweep.
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__device__ __forceinline__ T p_red(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
-                                   long long c, T h2) {
+__device__ __forceinline__ T p_red(const LevelPtrs<T>& L, const Pt& q, T h2) {
   T num = T(0), dg = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const T* __restrict__ b = L.beta[a];
-    if (ci[a] > 0 || g.per[a]) {
-      T bb = b[c];
-      num += bb * L.p[c + offm(g, a, ci[a])];
+    if (!q.wm[a]) {
+      T bb = b[q.F];
+      num += bb * L.p[q.F + q.om[a]];
       dg += bb;
     }
-    if (ci[a] < g.n[a] - 1 || g.per[a]) {
-      long long cp = c + offp(g, a, ci[a]);
-      T bb = b[cp];
-      num += bb * L.p[cp];
+    if (!q.wp[a]) {
+      T bb = b[q.F + q.op[a]];
+      num += bb * L.p[q.F + q.op[a]];
       dg += bb;
     }
   }
-  return (num - h2 * L.pf[c]) / dg;
+  return (num - h2 * L.pf[q.F]) / dg;
+}
+
+// the new red value of a neighbour of the black point: from the ring row of
+// this plane (x, row axis) or of the planes before and after (streaming axis)
+template <int D, typename T>
+__device__ __forceinline__ T ring_nb(const Ring<T>& rg, const Pt& q, int i, int n0, int a,
+                                     int side, int r, int sl_m, int sl_0, int sl_p) {
+  constexpr int RA = Ax<D>::R;
+  if (a == 0) {
+    int ii = i + side;
+    if (ii < 0) ii += n0;
+    else if (ii >= n0 && q.op[0] < 0) ii -= n0;   // periodic wrap (op < 0 only then)
+    return rg.row(sl_0, r)[ii];
+  }
+  if (a == RA) return rg.row(sl_0, r + side)[i];
+  return rg.row(side > 0 ? sl_p : sl_m, r)[i];
 }
 
 template <int D, typename T>
-__device__ __forceinline__ T p_black(const Geo& g, const LevelPtrs<T>& L, const Ring<T>& rg,
-                                     const int ci[3], long long c, int r, int sl_m, int sl_0,
-                                     int sl_p, T h2) {
-  constexpr int RA = Ax<D>::R, SA = Ax<D>::S;
+__device__ __forceinline__ T p_black(const LevelPtrs<T>& L, const Ring<T>& rg, const Pt& q,
+                                     int i, int n0, int r, int sl_m, int sl_0, int sl_p, T h2) {
   T num = T(0), dg = T(0);
-  const T* here = rg.row(sl_0, r);
-  int i = ci[0], n0 = g.n[0];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const T* __restrict__ b = L.beta[a];
-    bool hm = ci[a] > 0 || g.per[a];
-    bool hp = ci[a] < g.n[a] - 1 || g.per[a];
-    T vm = T(0), vp = T(0);
-    if (a == 0) {
-      if (hm) vm = here[i > 0 ? i - 1 : n0 - 1];
-      if (hp) vp = here[i < n0 - 1 ? i + 1 : 0];
-    } else if (a == RA) {
-      if (hm) vm = rg.row(sl_0, r - 1)[i];
-      if (hp) vp = rg.row(sl_0, r + 1)[i];
-    } else {  // a == SA
-      if (hm) vm = rg.row(sl_m, r)[i];
-      if (hp) vp = rg.row(sl_p, r)[i];
-    }
-    if (hm) {
-      T bb = b[c];
-      num += bb * vm;
+    if (!q.wm[a]) {
+      T bb = b[q.F];
+      num += bb * ring_nb<D, T>(rg, q, i, n0, a, -1, r, sl_m, sl_0, sl_p);
       dg += bb;
     }
-    if (hp) {
-      T bb = b[c + offp(g, a, ci[a])];
-      num += bb * vp;
+    if (!q.wp[a]) {
+      T bb = b[q.F + q.op[a]];
+      num += bb * ring_nb<D, T>(rg, q, i, n0, a, +1, r, sl_m, sl_0, sl_p);
       dg += bb;
     }
   }
-  (void)SA;
-  return (num - h2 * L.pf[c]) / dg;
+  return (num - h2 * L.pf[q.F]) / dg;
 }
 
 template <int D, typename T>
@@ -149,9 +169,12 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
         int ci[3];
         ci[RA] = jw;
         ci[SA] = kw;
-        int par = (ci[1] + ci[2]) & 1;
-        ci[0] = 2 * ip + par;          // the red point of this pair
-        if (ci[0] < n0) row[ci[0]] = p_red<D, T>(g, L, ci, gidx(g, ci[0], ci[1], ci[2]), h2);
+        ci[0] = 2 * ip + ((ci[1] + ci[2]) & 1);   // the red point of this pair
+        if (ci[0] < n0) {
+          Pt q;
+          make_pt<D>(g, ci, q);
+          row[ci[0]] = p_red<D, T>(L, q, h2);
+        }
       }
     } else {
       for (int i = threadIdx.x; i < rg.W; i += blockDim.x) row[i] = T(0);
@@ -168,11 +191,12 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
         ci[SA] = kb;
         int par = (ci[1] + ci[2]) & 1;
         int ir = 2 * ip + par, ib = 2 * ip + (par ^ 1);
-        if (ir < n0) out[gidx(g, ir, ci[1], ci[2])] = here[ir];
+        if (ir < n0) out[ir + (int)g.st[1] * ci[1] + (int)g.st[2] * ci[2]] = here[ir];
         if (ib < n0) {
           ci[0] = ib;
-          long long c = gidx(g, ib, ci[1], ci[2]);
-          out[c] = p_black<D, T>(g, L, rg, ci, c, r, sl_m, sl_0, sl_p, h2);
+          Pt q;
+          make_pt<D>(g, ci, q);
+          out[q.F] = p_black<D, T>(L, rg, q, ib, n0, r, sl_m, sl_0, sl_p, h2);
         }
       }
     }
@@ -189,90 +213,68 @@ template <int D, int d, typename T>
 struct VC {
   T cdp, cdm;          // 2 mu_c on the cells beside the face
   T cep[2], cem[2];    // edge mu per other axis (the neighbour beyond a wall is unused)
-  bool wp[2], wm[2];   // that neighbour lies beyond a wall (mirror ghost)
   T cross, diag;
 };
 
 template <int D, int d, typename T>
-__device__ __forceinline__ void v_coef(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
-                                       long long F, T ir, VC<D, d, T>& v) {
-  long long od_m = offm(g, d, ci[d]);
+__device__ __forceinline__ void v_coef(const LevelPtrs<T>& L, const Pt& q, T ir, VC<D, d, T>& v) {
+  const int F = q.F, od_m = q.om[d];
   T mcp = L.muc[F], mcm = L.muc[F + od_m];
   v.cdp = T(2) * mcp;
   v.cdm = T(2) * mcm;
   T dgV = T(2) * (mcp + mcm);
   v.cross = T(0);
-  int q = 0;
+  int k = 0;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
     const T* __restrict__ ue = L.u[e];
     const T* __restrict__ me = L.mue[edge_id(d, e)];
-    bool pe = g.per[e] != 0;
-    bool wp = !pe && ci[e] == g.n[e] - 1;
-    bool wm = !pe && ci[e] == 0;
-    long long Ep = F + offp(g, e, ci[e]);
+    const int Ep = F + q.op[e];
     T mep = me[Ep], mem = me[F];
     v.cross += mep * (ue[Ep] - ue[Ep + od_m]) - mem * (ue[F] - ue[F + od_m]);
-    v.cep[q] = mep;
-    v.cem[q] = mem;
-    v.wp[q] = wp;
-    v.wm[q] = wm;
-    dgV += (wp ? T(2) : T(1)) * mep + (wm ? T(2) : T(1)) * mem;
-    ++q;
+    v.cep[k] = mep;
+    v.cem[k] = mem;
+    dgV += (q.wp[e] ? T(2) : T(1)) * mep + (q.wm[e] ? T(2) : T(1)) * mem;
+    ++k;
   }
   v.diag = L.m[d][F] + ir * dgV;
 }
 
 template <int D, int d, typename T>
-__device__ __forceinline__ T v_red(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
-                                   long long F, T ir) {
+__device__ __forceinline__ T v_red(const LevelPtrs<T>& L, const Pt& q, T ir) {
   VC<D, d, T> v;
-  v_coef<D, d, T>(g, L, ci, F, ir, v);
+  v_coef<D, d, T>(L, q, ir, v);
   const T* __restrict__ ud = L.u[d];
-  T off = v.cross + v.cdp * ud[F + offp(g, d, ci[d])] + v.cdm * ud[F + offm(g, d, ci[d])];
-  int q = 0;
+  T off = v.cross + v.cdp * ud[q.F + q.op[d]] + v.cdm * ud[q.F + q.om[d]];
+  int k = 0;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
-    if (!v.wp[q]) off += v.cep[q] * ud[F + offp(g, e, ci[e])];
-    if (!v.wm[q]) off += v.cem[q] * ud[F + offm(g, e, ci[e])];
-    ++q;
+    if (!q.wp[e]) off += v.cep[k] * ud[q.F + q.op[e]];
+    if (!q.wm[e]) off += v.cem[k] * ud[q.F + q.om[e]];
+    ++k;
   }
-  return (L.uf[d][F] + ir * off) / v.diag;
-}
-
-// u_d at the neighbour of ci one step along axis a (side +1/-1) from the ring
-template <int D, typename T>
-__device__ __forceinline__ T ring_nb(const Geo& g, const Ring<T>& rg, const int ci[3], int a,
-                                     int side, int r, int sl_m, int sl_0, int sl_p) {
-  constexpr int RA = Ax<D>::R;
-  if (a == 0) {
-    int i = ci[0] + side;
-    if (g.per[0]) i = wrapi(i, g.n[0]);
-    return rg.row(sl_0, r)[i];
-  }
-  if (a == RA) return rg.row(sl_0, r + side)[ci[0]];
-  return rg.row(side > 0 ? sl_p : sl_m, r)[ci[0]];
+  return (L.uf[d][q.F] + ir * off) / v.diag;
 }
 
 template <int D, int d, typename T>
-__device__ __forceinline__ T v_black(const Geo& g, const LevelPtrs<T>& L, const Ring<T>& rg,
-                                     const int ci[3], long long F, T ir, int r, int sl_m,
-                                     int sl_0, int sl_p) {
+__device__ __forceinline__ T v_black(const LevelPtrs<T>& L, const Ring<T>& rg, const Pt& q,
+                                     int i, int n0, T ir, int r, int sl_m, int sl_0, int sl_p) {
   VC<D, d, T> v;
-  v_coef<D, d, T>(g, L, ci, F, ir, v);
-  T off = v.cross + v.cdp * ring_nb<D, T>(g, rg, ci, d, +1, r, sl_m, sl_0, sl_p) +
-          v.cdm * ring_nb<D, T>(g, rg, ci, d, -1, r, sl_m, sl_0, sl_p);
-  int q = 0;
+  v_coef<D, d, T>(L, q, ir, v);
+  // along d a wall neighbour is the stored zero face: the ring holds 0 there
+  T off = v.cross + v.cdp * ring_nb<D, T>(rg, q, i, n0, d, +1, r, sl_m, sl_0, sl_p) +
+          v.cdm * ring_nb<D, T>(rg, q, i, n0, d, -1, r, sl_m, sl_0, sl_p);
+  int k = 0;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
-    if (!v.wp[q]) off += v.cep[q] * ring_nb<D, T>(g, rg, ci, e, +1, r, sl_m, sl_0, sl_p);
-    if (!v.wm[q]) off += v.cem[q] * ring_nb<D, T>(g, rg, ci, e, -1, r, sl_m, sl_0, sl_p);
-    ++q;
+    if (!q.wp[e]) off += v.cep[k] * ring_nb<D, T>(rg, q, i, n0, e, +1, r, sl_m, sl_0, sl_p);
+    if (!q.wm[e]) off += v.cem[k] * ring_nb<D, T>(rg, q, i, n0, e, -1, r, sl_m, sl_0, sl_p);
+    ++k;
   }
-  return (L.uf[d][F] + ir * off) / v.diag;
+  return (L.uf[d][q.F] + ir * off) / v.diag;
 }
 
 template <int D, int d, typename T>
@@ -307,11 +309,14 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
         int ci[3];
         ci[RA] = jw;
         ci[SA] = kw;
-        int par = (ci[1] + ci[2]) & 1;
-        ci[0] = 2 * ip + par;
+        ci[0] = 2 * ip + ((ci[1] + ci[2]) & 1);
         if (ci[0] >= n0) continue;
         T v = T(0);   // wall faces hold 0
-        if (!(wall_d && ci[d] == 0)) v = v_red<D, d, T>(g, L, ci, gidx(g, ci[0], ci[1], ci[2]), ir);
+        if (!(wall_d && ci[d] == 0)) {
+          Pt q;
+          make_pt<D>(g, ci, q);
+          v = v_red<D, d, T>(L, q, ir);
+        }
         row[ci[0]] = v;
       }
     } else {
@@ -328,13 +333,14 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
         ci[SA] = kb;
         int par = (ci[1] + ci[2]) & 1;
         int irr = 2 * ip + par, ib = 2 * ip + (par ^ 1);
-        if (irr < n0) out[gidx(g, irr, ci[1], ci[2])] = here[irr];
+        if (irr < n0) out[irr + (int)g.st[1] * ci[1] + (int)g.st[2] * ci[2]] = here[irr];
         if (ib < n0) {
           ci[0] = ib;
-          long long F = gidx(g, ib, ci[1], ci[2]);
+          Pt q;
+          make_pt<D>(g, ci, q);
           T v = T(0);
-          if (!(wall_d && ci[d] == 0)) v = v_black<D, d, T>(g, L, rg, ci, F, ir, r, sl_m, sl_0, sl_p);
-          out[F] = v;
+          if (!(wall_d && ci[d] == 0)) v = v_black<D, d, T>(L, rg, q, ib, n0, ir, r, sl_m, sl_0, sl_p);
+          out[q.F] = v;
         }
       }
     }
@@ -356,15 +362,17 @@ FusedShape fused_shape(int D, const Geo& g) {
   int npairs = (g.n[0] + 1) / 2;
   int bx = ((npairs + 31) / 32) * 32;
   if (bx > 128) bx = 128;
-  f.TY = (D == 3) ? (g.n[RA] >= 8 ? 8 : g.n[RA]) : 1;
+  // 4 rows (+2 ring rows) keep blocks small enough for several per SM
+  f.TY = (D == 3) ? (g.n[RA] >= 4 ? 4 : g.n[RA]) : 1;
   while (bx * (f.TY + 2 * ring) > 1024 && f.TY > 1) --f.TY;
   while ((size_t)3 * (f.TY + 2 * ring) * g.s[0] * sizeof(T) > 48 * 1024 && f.TY > 1) --f.TY;
   int nrt = (g.n[RA] + f.TY - 1) / f.TY;
-  // aim for several blocks per SM while keeping the recomputed first plane of
-  // each chunk a small fraction of the work
-  long long want = 4LL * 152;
+  // about three blocks per SM in flight, with chunks of at most 16 planes so
+  // that the recomputed first plane of a chunk stays a small fraction
+  long long want = 3LL * 152;
   int KC = (int)((long long)g.n[SA] * nrt / want);
   if (KC < 4) KC = 4;
+  if (KC > 16) KC = 16;
   if (KC > g.n[SA]) KC = g.n[SA];
   f.KC = KC;
   f.block = dim3(bx, f.TY + 2 * ring, 1);
@@ -395,6 +403,31 @@ void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out
     if (d == 0) k_v_rb_fused<2, 0, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
     else k_v_rb_fused<2, 1, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
   }
+}
+
+// Let the fused sweeps run several blocks per SM: ask for a shared-memory
+// carveout of a quarter of the unified L1/shared storage (call once, outside
+// stream capture).
+cudaError_t fused_set_carveout() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+  };
+  set((const void*)k_p_rb_fused<3, float>);
+  set((const void*)k_p_rb_fused<2, float>);
+  set((const void*)k_p_rb_fused<3, double>);
+  set((const void*)k_p_rb_fused<2, double>);
+  set((const void*)k_v_rb_fused<3, 0, float>);
+  set((const void*)k_v_rb_fused<3, 1, float>);
+  set((const void*)k_v_rb_fused<3, 2, float>);
+  set((const void*)k_v_rb_fused<2, 0, float>);
+  set((const void*)k_v_rb_fused<2, 1, float>);
+  set((const void*)k_v_rb_fused<3, 0, double>);
+  set((const void*)k_v_rb_fused<3, 1, double>);
+  set((const void*)k_v_rb_fused<3, 2, double>);
+  set((const void*)k_v_rb_fused<2, 0, double>);
+  set((const void*)k_v_rb_fused<2, 1, double>);
+  return e;
 }
 
 size_t fused_smem_bytes(int D, const Geo& g, int elem) {

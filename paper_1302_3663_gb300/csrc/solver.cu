@@ -152,10 +152,13 @@ struct bfibm_ctx {
   int* counters = nullptr;    // [0] clamped, [1] event count
   std::vector<void*> lag_allocs;
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;     // captures the bodies of device-side loops
   bool own_stream = false;
+  bool capturing = false;         // a step graph is being captured
+  int* dev_cycles = nullptr;      // V-cycles used by the last solves (visc, p)
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
-  bool fused = true;             // one-pass red-black sweeps
+  bool fused = false;            // one-pass FP64 red-black sweeps (FP32 sweeps always are)
   bool collect_stats = true;
   bool dirty = true;
   int poisoned = 0;
@@ -291,7 +294,43 @@ bfibm_status read_scalars(bfibm_ctx* c) {
   return BFIBM_OK;
 }
 
-// Solve on level 0. Fixed mode only queues work.
+// Records into the step graph being captured on c->stream a device-side
+// loop: a conditional WHILE node whose body (queued by `body` on c->stream,
+// redirected to the auxiliary stream while the body is captured) ends with
+// launch_tol_check, which decides whether the body runs again.
+template <typename Body>
+bfibm_status capture_while(bfibm_ctx* c, Body body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &np));
+  CK(cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1,
+                                         cudaStreamSetCaptureDependencies));
+  cudaGraph_t bg = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->aux, bg, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  cudaStream_t main = c->stream;
+  c->stream = c->aux;
+  body(h);
+  c->stream = main;
+  cudaGraph_t out = nullptr;
+  CK(cudaStreamEndCapture(c->aux, &out));
+  return BFIBM_OK;
+}
+
+// Solve on level 0. Fixed mode only queues work; relative-residual mode
+// either loops on the device (inside a captured step graph) or reads the
+// residual norm back after every cycle.
 bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
   Level& L0 = c->lev[0];
   cudaStream_t s = c->stream;
@@ -310,6 +349,19 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
     }
     *used = ncycles;
     return BFIBM_OK;
+  }
+  if (c->capturing) {
+    cudaMemsetAsync(c->dev_cycles + 1, 0, sizeof(int), s);
+    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+      vcycle_p(c, 0);
+      launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, c->stream);
+      launch_p_residual<double>(c->D, L0.g, L0.d, c->stream);
+      launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, c->stream);
+      launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1,
+                       c->stream);
+    });
+    *used = -1;
+    return cs;
   }
   bfibm_status st = BFIBM_ENOCONV;
   int k = 0;
@@ -344,6 +396,18 @@ bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
     }
     *used = ncycles;
     return BFIBM_OK;
+  }
+  if (c->capturing) {
+    cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
+    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+      vcycle_v(c, 0);
+      launch_v_residual<double>(c->D, L0.g, L0.d, c->P.inv_re, c->stream);
+      launch_norm2(c->D, L0.g, L0.d.ur, c->D, c->sc, SL_VR, c->stream);
+      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles,
+                       c->stream);
+    });
+    *used = -1;
+    return cs;
   }
   bfibm_status st = BFIBM_ENOCONV;
   int k = 0;
@@ -453,6 +517,23 @@ bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
   bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
   double* xs[3] = {L0.d.p, nullptr, nullptr};
   float* es[3] = {L0.f.p, nullptr, nullptr};
+  if (tol && c->capturing) {
+    cudaMemsetAsync(c->dev_cycles + 1, 0, sizeof(int), s);
+    launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, nullptr, s);
+    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+      cudaStream_t b = c->stream;
+      vcycle_p32(c, 0);
+      xs[0] = L0.d.p;
+      es[0] = L0.f.p;
+      launch_add_correction(c->D, L0.g, xs, es, 0, b);
+      launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, b);
+      launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, c->sc.partial, b);
+      launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, b);
+      launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1, b);
+    });
+    *used = -1;
+    return cs;
+  }
   int k = 0;
   for (k = 1; k <= maxc; ++k) {
     launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, tol ? c->sc.partial : nullptr, s);
@@ -490,6 +571,20 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   if (tol || c->collect_stats) launch_norm2(c->D, L0.g, L0.d.uf, c->D, c->sc, SL_VF, s);
   int maxc = tol ? c->P.max_cycles : ncycles;
   bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
+  if (tol && c->capturing) {
+    cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
+    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, nullptr, s);
+    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+      cudaStream_t b = c->stream;
+      vcycle_v32(c, 0);
+      launch_add_correction(c->D, L0.g, L0.d.u, L0.f.u, c->D, b);
+      launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, c->sc.partial, b);
+      launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
+      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles, b);
+    });
+    *used = -1;
+    return cs;
+  }
   int k = 0;
   for (k = 1; k <= maxc; ++k) {
     launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re,
@@ -609,11 +704,13 @@ bfibm_status do_steps(bfibm_ctx* c, int nsteps) {
   bfibm_status st = ensure_ready(c);
   if (st != BFIBM_OK) return st;
   bfibm_status agg = BFIBM_OK;
-  if (fixed_mode(c) && c->use_graph) {
+  if (c->use_graph) {
     if (!c->gexec) {
       cudaGraph_t graph = nullptr;
       CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      c->capturing = true;
       bfibm_status qs = queue_step(c);
+      c->capturing = false;
       cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
       if (qs != BFIBM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -697,7 +794,8 @@ bfibm_status copy_field(bfibm_ctx* c, int which, int comp, int level, void* ext,
 void free_lag(bfibm_ctx* c, bool nodes, bool springs) {
   if (nodes) {
     for (void* q : {(void*)c->N.X, (void*)c->N.U, (void*)c->N.F, (void*)c->N.tile, (void*)c->N.perm,
-                    (void*)c->N.count, (void*)c->N.start, (void*)c->N.cursor})
+                    (void*)c->N.count, (void*)c->N.start, (void*)c->N.cursor, (void*)c->N.tw,
+                    (void*)c->N.tlo})
       if (q) cudaFree(q);
     long long keep_eta = 0;
     int* clamped = c->N.clamped;
@@ -834,6 +932,8 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   if (cudaMalloc((void**)&c->sc.partial, sizeof(double) * c->partial_cap) != cudaSuccess ||
       cudaMalloc((void**)&c->step_dev, sizeof(long long)) != cudaSuccess ||
       cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc((void**)&c->dev_cycles, sizeof(int) * 2) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost((void**)&c->host_sc, 16 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     bfibm_destroy(c);
@@ -845,7 +945,8 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   cudaStream_t s = c->stream;
   bool ok = cudaMemsetAsync(c->pool, 0, c->pool_bytes, s) == cudaSuccess &&
             cudaMemsetAsync(c->step_dev, 0, sizeof(long long), s) == cudaSuccess &&
-            cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, s) == cudaSuccess;
+            cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, s) == cudaSuccess &&
+            cudaMemsetAsync(c->dev_cycles, 0, sizeof(int) * 2, s) == cudaSuccess;
   if (!ok) {
     bfibm_destroy(c);
     return BFIBM_ECUDA;
@@ -860,11 +961,16 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   c->tg.ntiles = c->tg.nt[0] * c->tg.nt[1] * c->tg.nt[2];
   {
     size_t smem = spread_smem_bytes(D, c->tg);
-    if (smem > 48 * 1024 && smem <= 96 * 1024 && spread_set_smem(D, smem) != cudaSuccess) {
+    if (smem > 48 * 1024 && smem <= spread_smem_limit() && spread_set_smem(D, smem) != cudaSuccess) {
       cudaGetLastError();
       bfibm_destroy(c);
       return BFIBM_ECUDA;
     }
+  }
+  if (coarse_set_smem() != cudaSuccess || fused_set_carveout() != cudaSuccess) {
+    cudaGetLastError();
+    bfibm_destroy(c);
+    return BFIBM_ECUDA;
   }
   // uniform fluid, laminar initial velocity
   Level& L0 = c->lev[0];
@@ -891,6 +997,8 @@ void bfibm_destroy(bfibm_ctx* c) {
   if (c->sc.partial) cudaFree(c->sc.partial);
   if (c->step_dev) cudaFree(c->step_dev);
   if (c->counters) cudaFree(c->counters);
+  if (c->dev_cycles) cudaFree(c->dev_cycles);
+  if (c->aux) cudaStreamDestroy(c->aux);
   if (c->host_sc) cudaFreeHost(c->host_sc);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -918,7 +1026,8 @@ bfibm_status bfibm_set_nodes(bfibm_ctx* c, int64_t eta, const double* X) {
   long long e3 = 3 * std::max<long long>(eta, 1);
   if (dmalloc(&N.X, e3) || dmalloc(&N.U, e3) || dmalloc(&N.F, e3) ||
       dmalloc(&N.tile, eta) || dmalloc(&N.perm, eta) || dmalloc(&N.count, nt + 1) ||
-      dmalloc(&N.start, nt + 1) || dmalloc(&N.cursor, nt + 1)) {
+      dmalloc(&N.start, nt + 1) || dmalloc(&N.cursor, nt + 1) || dmalloc(&N.tw, 48 * (e3 / 3)) ||
+      dmalloc(&N.tlo, 24 * (e3 / 3))) {
     cudaGetLastError();
     free_lag(c, true, false);
     c->N.eta = 0;
@@ -1056,6 +1165,13 @@ bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
   std::memset(out, 0, sizeof(*out));
   out->cycles_visc = c->cycles_visc;
   out->cycles_p = c->cycles_p;
+  if (c->cycles_visc < 0 || c->cycles_p < 0) {   // counted on the device
+    int cyc[2];
+    CK(cudaMemcpyAsync(cyc, c->dev_cycles, sizeof(cyc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->cycles_visc < 0) out->cycles_visc = cyc[0];
+    if (c->cycles_p < 0) out->cycles_p = cyc[1];
+  }
   out->broken_total = std::min<int>(cnt[1], (int)std::max<long long>(c->S.m, 0));
   out->clamped_total = cnt[0];
   auto rel = [](double f2, double r2) { return f2 > 0.0 ? std::sqrt(r2) / std::sqrt(f2) : 0.0; };
@@ -1152,6 +1268,17 @@ bfibm_status bfibm_smooth_viscous(bfibm_ctx* c, int level, int nsweeps) {
   READY(c);
   if (level < 0 || level >= c->L || nsweeps < 0) return set_err(c, BFIBM_EINVAL, "bad level");
   smooth_v(c, level, nsweeps);
+  CK(cudaGetLastError());
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_smooth_f32(bfibm_ctx* c, int which, int level, int nsweeps) {
+  READY(c);
+  if (c->P.precision != 1) return set_err(c, BFIBM_ESTATE, "not a mixed-precision context");
+  if (level < 0 || level >= c->L || nsweeps < 0 || (which != 0 && which != 1))
+    return set_err(c, BFIBM_EINVAL, "bad level, count or selector");
+  if (which == 0) smooth_p32(c, level, nsweeps);
+  else smooth_v32(c, level, nsweeps);
   CK(cudaGetLastError());
   return BFIBM_OK;
 }

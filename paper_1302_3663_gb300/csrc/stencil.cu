@@ -300,37 +300,59 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* 
 // next coarse cell toward the child; beyond a wall the mirror ghost
 // (sign `mirror`) folds that 1/4 into the parent. Face axis: the coincident
 // coarse face, or the mean of the two coarse faces around a midway face.
-__device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, double mirror, int idx[2],
-                                            double w[2]) {
+// The weights are exact binary fractions in any precision.
+template <typename T>
+__device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, int mirror, int idx[2], T w[2]) {
   int I = i >> 1;
   int J = I + ((i & 1) ? 1 : -1);
   idx[0] = I;
-  w[0] = 0.75;
+  w[0] = T(0.75);
+  w[1] = T(0);
   if (per) {
     idx[1] = (J + nc) % nc;
-    w[1] = 0.25;
+    w[1] = T(0.25);
     return 2;
   }
   if (J < 0 || J >= nc) {
-    w[0] = 0.75 + 0.25 * mirror;
+    w[0] = mirror > 0 ? T(1) : T(0.5);
     return 1;
   }
   idx[1] = J;
-  w[1] = 0.25;
+  w[1] = T(0.25);
   return 2;
 }
-__device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], double w[2]) {
+template <typename T>
+__device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], T w[2]) {
   int I = i >> 1;
+  w[1] = T(0);
   if ((i & 1) == 0) {
     idx[0] = per ? (I % nc) : I;
-    w[0] = 1.0;
+    w[0] = T(1);
     return 1;
   }
   idx[0] = I;
-  w[0] = 0.5;
+  w[0] = T(0.5);
   idx[1] = per ? ((I + 1) % nc) : I + 1;
-  w[1] = 0.5;
+  w[1] = T(0.5);
   return 2;
+}
+
+// separable tensor-product sum: x-rows first, then y, then z
+template <typename T>
+__device__ __forceinline__ T prol_sum(const Geo& gc, const T* __restrict__ ec, const int idx[3][2],
+                                      const T w[3][2], const int cnt[3]) {
+  T v = T(0);
+  for (int c = 0; c < cnt[2]; ++c) {
+    T col = T(0);
+    for (int b = 0; b < cnt[1]; ++b) {
+      long long r = gidx(gc, 0, idx[1][b], idx[2][c]);
+      T row = w[0][0] * ec[r + idx[0][0]];
+      if (cnt[0] == 2) row += w[0][1] * ec[r + idx[0][1]];
+      col += w[1][b] * row;
+    }
+    v += w[2][c] * col;
+  }
+  return v;
 }
 
 template <int D, typename T>
@@ -342,16 +364,11 @@ __global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* _
   fi[2] = blockIdx.z * blockDim.z + threadIdx.z;
   if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  double w[3][2] = {{1.0, 0.0}, {1.0, 0.0}, {1.0, 0.0}};
+  T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
   int cnt[3] = {1, 1, 1};
 #pragma unroll
-  for (int a = 0; a < D; ++a) cnt[a] = prol_cell_1d(fi[a], gc.n[a], gc.per[a], 1.0, idx[a], w[a]);
-  T v = T(0);
-  for (int c = 0; c < cnt[2]; ++c)
-    for (int b = 0; b < cnt[1]; ++b)
-      for (int a = 0; a < cnt[0]; ++a)
-        v += (T)(w[0][a] * w[1][b] * w[2][c]) * ec[gidx(gc, idx[0][a], idx[1][b], idx[2][c])];
-  xf[gidx(gf, fi[0], fi[1], fi[2])] += v;
+  for (int a = 0; a < D; ++a) cnt[a] = prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, idx[a], w[a]);
+  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w, cnt);
 }
 
 template <int D, int d, typename T>
@@ -364,21 +381,16 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
   if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
   if (!gf.per[d] && fi[d] == 0) return;
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  double w[3][2] = {{1.0, 0.0}, {1.0, 0.0}, {1.0, 0.0}};
+  T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
   int cnt[3] = {1, 1, 1};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     if (a == d)
-      cnt[a] = prol_face_1d(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
+      cnt[a] = prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
     else
-      cnt[a] = prol_cell_1d(fi[a], gc.n[a], gc.per[a], -1.0, idx[a], w[a]);
+      cnt[a] = prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, idx[a], w[a]);
   }
-  T v = T(0);
-  for (int c = 0; c < cnt[2]; ++c)
-    for (int b = 0; b < cnt[1]; ++b)
-      for (int a = 0; a < cnt[0]; ++a)
-        v += (T)(w[0][a] * w[1][b] * w[2][c]) * ec[gidx(gc, idx[0][a], idx[1][b], idx[2][c])];
-  xf[gidx(gf, fi[0], fi[1], fi[2])] += v;
+  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,9 +398,35 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
 // few thousand points and stays in L2). Colour phases are separated by
 // block barriers.
 // ---------------------------------------------------------------------------
+// The coarsest level's arrays are copied to shared memory when they fit
+// (nel elements each); the sweeps then run on the copies.
+template <typename T>
+__device__ __forceinline__ void stage_in(T* dst, const T* src, long long nel) {
+  for (long long q = threadIdx.x; q < nel; q += blockDim.x) dst[q] = src[q];
+}
+template <typename T>
+__device__ __forceinline__ void stage_out(T* dst, const T* src, long long nel) {
+  for (long long q = threadIdx.x; q < nel; q += blockDim.x) dst[q] = src[q];
+}
+
 template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> L, int sweeps) {
+__global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int sweeps,
+                                                   long long nel, int use_smem) {
+  extern __shared__ __align__(16) unsigned char csm[];
   __shared__ double sh[32];
+  LevelPtrs<T> L = Lg;
+  if (use_smem) {
+    T* b = reinterpret_cast<T*>(csm);
+    L.p = b;
+    L.pf = b + nel;
+    stage_in(L.p, Lg.p, nel);
+    stage_in(L.pf, Lg.pf, nel);
+    for (int a = 0; a < D; ++a) {
+      L.beta[a] = b + (2 + a) * nel;
+      stage_in(L.beta[a], Lg.beta[a], nel);
+    }
+    __syncthreads();
+  }
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   double s = 0.0;
   for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
@@ -427,6 +465,10 @@ __global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> L, int sw
       __syncthreads();
     }
   }
+  if (use_smem) {
+    stage_out(Lg.p, L.p, nel);
+    stage_out(Lg.pf, L.pf, nel);
+  }
 }
 
 template <int D, int d, typename T>
@@ -452,7 +494,29 @@ __device__ __forceinline__ void coarse_v_phase(const Geo& g, const LevelPtrs<T>&
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> L, int sweeps, T ir) {
+__global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> Lg, int sweeps, T ir,
+                                                   long long nel, int use_smem) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  LevelPtrs<T> L = Lg;
+  if (use_smem) {
+    T* b = reinterpret_cast<T*>(csm);
+    int q = 0;
+    for (int d = 0; d < D; ++d) {
+      L.u[d] = b + (q++) * nel;
+      stage_in(L.u[d], Lg.u[d], nel);
+      L.uf[d] = b + (q++) * nel;
+      stage_in(L.uf[d], Lg.uf[d], nel);
+      L.m[d] = b + (q++) * nel;
+      stage_in(L.m[d], Lg.m[d], nel);
+    }
+    L.muc = b + (q++) * nel;
+    stage_in(L.muc, Lg.muc, nel);
+    for (int e = 0; e < (D == 3 ? 3 : 1); ++e) {
+      L.mue[e] = b + (q++) * nel;
+      stage_in(L.mue[e], Lg.mue[e], nel);
+    }
+    __syncthreads();
+  }
   for (int it = 0; it < sweeps; ++it) {
     coarse_v_phase<D, 0, T>(g, L, 0, ir);
     coarse_v_phase<D, 0, T>(g, L, 1, ir);
@@ -463,6 +527,8 @@ __global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> L, int sw
       coarse_v_phase<D, 2, T>(g, L, 1, ir);
     }
   }
+  if (use_smem)
+    for (int d = 0; d < D; ++d) stage_out(Lg.u[d], L.u[d], nel);
 }
 
 // ---------------------------------------------------------------------------
@@ -585,23 +651,25 @@ __global__ void __launch_bounds__(256) k_coef_restrict(Geo gf, Geo gc, LevelPtrs
 // differences fluxes at the cells (along d) and edges (other axes), each
 // factor a 2-point mean. The iterate u~ starts from u^n.
 // ---------------------------------------------------------------------------
+// The constant factors (1/2 of each mean, 1/(2h), 1/h) are folded into two
+// products so that a point costs no division: FP64 throughput is scarce.
 template <int D, int d>
 __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, const Ptr3& rho,
                                               const Ptr3& frc, const LevelPtrs<double>& L0,
                                               const int ci[3], long long F, double c_force,
-                                              double gflow) {
+                                              double gflow, double c_adv, double c_cons) {
   if (!g.per[d] && ci[d] == 0) {
     L0.uf[d][F] = 0.0;
     L0.u[d][F] = 0.0;
     return;
   }
   const double* __restrict__ ud = uv.a[d];
-  double h = g.h;
   long long od_p = offp(g, d, ci[d]), od_m = offm(g, d, ci[d]);
   double udF = ud[F], udp = ud[F + od_p], udm = ud[F + od_m];
-  double adv = udF * (udp - udm) / (2.0 * h);
-  double cp = 0.5 * (udF + udp), cm = 0.5 * (udm + udF);
-  double cons = (cp * cp - cm * cm) / h;
+  // 4 x (advective half) and 4 x (conservative half), scaled at the end
+  double adv4 = 4.0 * udF * (udp - udm);
+  double sp = udF + udp, sm = udm + udF;
+  double cons4 = sp * sp - sm * sm;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
@@ -611,15 +679,12 @@ __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, cons
     double up = -udF, um = -udF;   // mirror ghosts beyond a wall
     if (pe || ci[e] != g.n[e] - 1) up = ud[F + oe_p];
     if (pe || ci[e] != 0) um = ud[F + offm(g, e, ci[e])];
-    double ue_lo = 0.5 * (ue[F + od_m] + ue[F]);
-    double ue_hi = 0.5 * (ue[F + oe_p + od_m] + ue[F + oe_p]);
-    double ubar = 0.5 * (ue_lo + ue_hi);
-    adv += ubar * (up - um) / (2.0 * h);
-    double flux_hi = ue_hi * 0.5 * (udF + up);
-    double flux_lo = ue_lo * 0.5 * (um + udF);
-    cons += (flux_hi - flux_lo) / h;
+    double s_lo = ue[F + od_m] + ue[F];                 // 2 x u_e on the lower edge
+    double s_hi = ue[F + oe_p + od_m] + ue[F + oe_p];   // 2 x u_e on the upper edge
+    adv4 += (s_lo + s_hi) * (up - um);
+    cons4 += s_hi * (udF + up) - s_lo * (um + udF);
   }
-  double A = 0.5 * (adv + cons);
+  double A = c_adv * adv4 + c_cons * cons4;
   L0.uf[d][F] = L0.m[d][F] * udF - rho.a[d][F] * A + c_force * frc.a[d][F] + gflow;
   L0.u[d][F] = udF;
 }
@@ -635,9 +700,13 @@ __global__ void __launch_bounds__(256) k_adv_rhs(Geo g, Ptr3 uv, Ptr3 rho, Ptr3 
   int ci[3] = {i, j, k};
   long long F = gidx(g, i, j, k);
   double G = *G_dev;
-  adv_rhs_point<D, 0>(g, uv, rho, frc, L0, ci, F, c_force, flow == 0 ? G : 0.0);
-  adv_rhs_point<D, 1>(g, uv, rho, frc, L0, ci, F, c_force, flow == 1 ? G : 0.0);
-  if constexpr (D == 3) adv_rhs_point<D, 2>(g, uv, rho, frc, L0, ci, F, c_force, flow == 2 ? G : 0.0);
+  // Adv = 1/2 (adv4 / (8 h) + cons4 / (4 h)): the 4-point mean is 1/4 of a
+  // sum, the wide difference 1/(2h), the flux means 1/4 of sums over 1/h
+  const double c_adv = 0.0625 / g.h, c_cons = 0.125 / g.h;
+  adv_rhs_point<D, 0>(g, uv, rho, frc, L0, ci, F, c_force, flow == 0 ? G : 0.0, c_adv, c_cons);
+  adv_rhs_point<D, 1>(g, uv, rho, frc, L0, ci, F, c_force, flow == 1 ? G : 0.0, c_adv, c_cons);
+  if constexpr (D == 3)
+    adv_rhs_point<D, 2>(g, uv, rho, frc, L0, ci, F, c_force, flow == 2 ? G : 0.0, c_adv, c_cons);
 }
 
 // ---------------------------------------------------------------------------
@@ -825,6 +894,17 @@ __global__ void k_laminar(Geo g, int D, int fa, int ta0, int ta1, double mu_eff,
   }
 }
 
+// One iteration of a device-side relative-residual loop has finished:
+// count it and keep looping while ||r||/||f|| > rtol and the cap is not hit.
+__global__ void k_tol_check(cudaGraphConditionalHandle h, const double* __restrict__ out, int sf,
+                            int sr, double rtol, int maxc, int* __restrict__ counter) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int n = ++(*counter);
+  double f2 = out[sf], r2 = out[sr];
+  double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
+  cudaGraphSetConditional(h, (rel > rtol && n < maxc) ? 1u : 0u);
+}
+
 __global__ void k_fill(double* a, long long n, double v) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x)
@@ -924,18 +1004,51 @@ void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec
   }
 }
 
+size_t coarse_smem_bytes(int D, const Geo& g, int elem, bool viscous) {
+  long long nel = g.st[2] * g.s[2];
+  int narr = viscous ? 3 * D + 1 + (D == 3 ? 3 : 1) : 2 + D;
+  return (size_t)narr * nel * elem;
+}
+
+static const size_t kCoarseSmemMax = 160 * 1024;
+
 template <typename T>
 void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cudaStream_t s) {
-  if (D == 3) k_coarse_p<3, T><<<1, 1024, 0, s>>>(g, L, sweeps);
-  else k_coarse_p<2, T><<<1, 1024, 0, s>>>(g, L, sweeps);
+  long long nel = g.st[2] * g.s[2];
+  size_t smem = coarse_smem_bytes(D, g, sizeof(T), false);
+  int use = smem <= kCoarseSmemMax;
+  if (!use) smem = 0;
+  if (D == 3) k_coarse_p<3, T><<<1, 1024, smem, s>>>(g, L, sweeps, nel, use);
+  else k_coarse_p<2, T><<<1, 1024, smem, s>>>(g, L, sweeps, nel, use);
 }
 
 template <typename T>
 void launch_coarse_v(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, double inv_re,
                      cudaStream_t s) {
   T ir = (T)(inv_re / (g.h * g.h));
-  if (D == 3) k_coarse_v<3, T><<<1, 1024, 0, s>>>(g, L, sweeps, ir);
-  else k_coarse_v<2, T><<<1, 1024, 0, s>>>(g, L, sweeps, ir);
+  long long nel = g.st[2] * g.s[2];
+  size_t smem = coarse_smem_bytes(D, g, sizeof(T), true);
+  int use = smem <= kCoarseSmemMax;
+  if (!use) smem = 0;
+  if (D == 3) k_coarse_v<3, T><<<1, 1024, smem, s>>>(g, L, sweeps, ir, nel, use);
+  else k_coarse_v<2, T><<<1, 1024, smem, s>>>(g, L, sweeps, ir, nel, use);
+}
+
+cudaError_t coarse_set_smem() {
+  cudaError_t e = cudaSuccess;
+  int b = (int)kCoarseSmemMax;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  };
+  set((const void*)k_coarse_p<3, double>);
+  set((const void*)k_coarse_p<2, double>);
+  set((const void*)k_coarse_v<3, double>);
+  set((const void*)k_coarse_v<2, double>);
+  set((const void*)k_coarse_p<3, float>);
+  set((const void*)k_coarse_p<2, float>);
+  set((const void*)k_coarse_v<3, float>);
+  set((const void*)k_coarse_v<2, float>);
+  return e;
 }
 
 #define BF_INST(T)                                                                           \
@@ -1058,6 +1171,11 @@ void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_
 void launch_finalize_sum(const double* partial, int nb, double* out, int slot, double scale,
                          cudaStream_t s) {
   k_finalize<<<1, 1024, 0, s>>>(partial, nb, out, slot, scale, 0);
+}
+
+void launch_tol_check(cudaGraphConditionalHandle h, const double* out, int sf, int sr,
+                      double rtol, int maxc, int* counter, cudaStream_t s) {
+  k_tol_check<<<1, 32, 0, s>>>(h, out, sf, sr, rtol, maxc, counter);
 }
 
 void launch_fill(double* a, long long n, double v, cudaStream_t s) {

@@ -40,7 +40,7 @@ def base_params(dim, n, periodic, flow_axis, h, **kw):
     periodic = list(periodic) + [1] * (3 - len(periodic))
     prm = dict(dim=dim, n=n, periodic=periodic, flow_axis=flow_axis, phi_kind=PHI_COSINE,
                mg_levels_max=6, nu1=2, nu2=2, vc_visc=3, vc_p=3, max_cycles=60,
-               coarse_sweeps=40, h=float(h), rho_f=1.0, mu_f=0.01, rho_ratio=1.0,
+               coarse_sweeps=16, h=float(h), rho_f=1.0, mu_f=0.01, rho_ratio=1.0,
                mu_ratio=1.0, omega=2.0 * h, omega_mu=2.0 * h, d0_vol=h ** dim,
                dt=0.1 * h, sigma=1.0, euler=1.0, inv_re=1.0, c_force=1.0, body_force=0.0,
                u_center=1.0, ic_scale=1.0, rtol=1e-9, gamma_coarse=1.0, precision=0)
