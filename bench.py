@@ -46,6 +46,13 @@ def parse():
                          "(default: the workload's own, 1 for c3)")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the plain FP64 single-instance comparison run")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served-stream block of the default run")
+    ap.add_argument("--instances", type=int, default=64, help="c4: batched instances")
+    ap.add_argument("--requests", type=int, default=None, help="c5: requests served")
+    ap.add_argument("--request-steps", type=int, default=None, help="c5: steps per request")
+    ap.add_argument("--budget-frac", type=float, default=0.05,
+                    help="c5: admission budget as a fraction of free device memory")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -288,6 +295,9 @@ def run_ours(args):
         out["fp64_single_instance"] = run_fp64(inst, args, world, stream)
     if not args.no_e2e:
         out["e2e"] = run_e2e(inst, args, world, stream)
+    if not args.no_served:
+        out["served"] = run_served_stream(args.requests or 8, args.request_steps or 10,
+                                          args.budget_frac, fp64_subset=8)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst)
     if world > 1:
@@ -396,10 +406,108 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_served_stream(nreq, steps, budget_frac, fp64_subset=None):
+    """A bounded Poisson stream of duct requests through the continuous-
+    batching service, and the same requests run serially in plain FP64."""
+    import torch
+
+    from paper_1302_3663_gb300 import serve, workloads as W
+    arr = W.c5_arrivals(count=nreq)
+    reqs = [serve.Request(i, W.c5_request(i), steps, float(arr[i])) for i in range(nreq)]
+    free, _ = torch.cuda.mem_get_info()
+    budget = max(int(budget_frac * free), max(int(1.05 * r.footprint) + 1 for r in reqs))
+    srv = serve.Server(budget, keep_results=False)
+    done = srv.run(reqs)
+    srv.close()
+    out = serve.summarize(done, srv.elapsed)
+    out["budget_bytes"] = budget
+    out["steps_per_request"] = steps
+    sub = reqs[:fp64_subset] if fp64_subset else reqs
+    v, ms = serve.serial(sub, precision=0)
+    out["serial_fp64"] = {"cell_steps_per_s": v, "requests": len(sub), "device_ms": ms}
+    v32, ms32 = serve.serial(sub, precision=None)
+    out["serial_mixed"] = {"cell_steps_per_s": v32, "requests": len(sub), "device_ms": ms32}
+    return out
+
+
+def run_batched(args):
+    """c4: independent ducts of uneven sizes stepped together."""
+    import torch
+
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+    world, rank, local = dist_setup(args)
+    insts = [W.c4_instance(i) for i in range(args.instances)]
+    ctxs = []
+    batch = bfibm.Batch()
+    for inst in insts:
+        c = bfibm.load_instance(inst)
+        c.set_option(bfibm.OPT_STATS, 0)
+        ctxs.append(c)
+        batch.add(c)
+    for _ in range(args.warmup):
+        batch.step()
+    batch.wait()
+    barrier(world)
+    cells = sum(W.cells(i["params"]) for i in insts)
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            batch.step()
+        batch.wait()
+        el = time.perf_counter() - t0
+    el = max_over_ranks(world, el)
+    value = cells * args.steps * world / el
+    # the plain FP64 path, each instance alone, on the first 8 instances
+    from paper_1302_3663_gb300 import serve
+    sub = [serve.Request(i, insts[i], args.steps, 0.0) for i in range(min(8, len(insts)))]
+    v64, _ = serve.serial(sub, precision=0)
+    v32, _ = serve.serial(sub, precision=None)
+    batch.close()
+    for c in ctxs:
+        c.close()
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+           "data": "synthetic", "config": {
+               "workload": "c4: %d independent ducts (edges 32-96, length 2 edges), 500-8,000 "
+                           "nodes each, all stepped together" % len(insts),
+               "cells": cells, "precision": "fp32 V-cycles in fp64 defect correction",
+               "parallelism": "one stream per instance, step graphs replayed together"},
+           "clocks": clk.summary(),
+           "fp64_single_instance_serial": {"cell_steps_per_s": v64, "instances": len(sub)},
+           "mixed_single_instance_serial": {"cell_steps_per_s": v32, "instances": len(sub)}}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_served(args):
+    from paper_1302_3663_gb300 import workloads as W
+    world, rank, local = dist_setup(args)
+    nreq = args.requests or 32
+    steps = args.request_steps or 20
+    with Clocks(local) as clk:
+        res = run_served_stream(nreq, steps, args.budget_frac, fp64_subset=8)
+    out = {"metric": METRIC, "value": res["cell_steps_per_s"], "unit": UNIT, "n_gpus": world,
+           "steps": steps, "warmup": 0, "ms_per_step": res["step_ms_p50"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+           "data": "synthetic", "config": {
+               "workload": "c5: Poisson stream (mean 4 requests/s) of %d duct simulations, "
+                           "edges 48-160, 500-50,000 nodes, %d steps each" % (nreq, steps),
+               "admission": "device-memory footprint within %.0f%% of free memory" %
+                            (100 * args.budget_frac)},
+           "served": res, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c4":
+        run_batched(args)
+    elif args.config == "c5":
+        run_served(args)
     else:
         run_ours(args)
 

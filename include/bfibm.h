@@ -91,6 +91,11 @@ typedef struct {
   double div_max;                    /* max |D.u| of the current velocity */
   double kinetic;                    /* sum over faces of u_d^2 h^D (Sec. 4.3.4) */
   int64_t step;                      /* completed time steps */
+  int32_t nonfinite_total;           /* non-finite node coordinates met (a run that
+                                        has blown up, e.g. a time step above the
+                                        stability limit of Sec. 4.3.4); each is reset
+                                        to 0 so that every kernel stays in bounds */
+  int32_t reserved;
 } bfibm_stats;
 
 /* Field selectors for bfibm_get_field / bfibm_set_field (see layout above). */
@@ -230,6 +235,24 @@ bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n);
    caller. BFIBM_ECUDA if the lookup or a launch fails. */
 bfibm_status bfibm_divergence_noalloc(const bfibm_params* p, const double* u0, const double* u1,
                                       const double* u2, double* b, void* stream);
+/* Batches: step many independent contexts together. Every member replays its
+   own step graph on its own stream (create members with stream NULL so that
+   each has one), so uneven simulations overlap on the device. A batch does
+   not own its members; removing or destroying it leaves them intact. */
+typedef struct bfibm_batch bfibm_batch;
+bfibm_status bfibm_batch_create(bfibm_batch** out);
+/* Add a context; *slot receives its index (freed slots are reused). */
+bfibm_status bfibm_batch_add(bfibm_batch* b, bfibm_ctx* c, int32_t* slot);
+bfibm_status bfibm_batch_remove(bfibm_batch* b, int32_t slot);
+/* Queue nsteps[slot] time steps for every member (NULL: one each; 0 skips a
+   member) without waiting, bracketing each member's steps with events. */
+bfibm_status bfibm_batch_step(bfibm_batch* b, const int32_t* nsteps);
+/* Wait until every member's queued work is done. */
+bfibm_status bfibm_batch_wait(bfibm_batch* b);
+/* Device time of a member's steps in the last bfibm_batch_step (waits for
+   them); BFIBM_ESTATE if the member was not stepped. */
+bfibm_status bfibm_batch_slot_ms(bfibm_batch* b, int32_t slot, float* ms);
+void bfibm_batch_destroy(bfibm_batch* b);
 /* Device bytes a context with these parameters allocates for its grids. */
 bfibm_status bfibm_footprint(const bfibm_params* p, int64_t eta, int64_t nsprings,
                              int64_t* bytes);

@@ -48,7 +48,8 @@ class bfibm_stats(C.Structure):
     _fields_ = [("cycles_visc", C.c_int32), ("cycles_p", C.c_int32),
                 ("broken_total", C.c_int32), ("clamped_total", C.c_int32),
                 ("res_visc", C.c_double), ("res_p", C.c_double), ("div_max", C.c_double),
-                ("kinetic", C.c_double), ("step", C.c_int64)]
+                ("kinetic", C.c_double), ("step", C.c_int64),
+                ("nonfinite_total", C.c_int32), ("reserved", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -94,8 +95,15 @@ SIGNATURES = {
     "bfibm_launches_per_step": [_V, C.POINTER(_L)],
     "bfibm_footprint": [C.POINTER(bfibm_params), _L, _L, C.POINTER(_L)],
     "bfibm_divergence_noalloc": [C.POINTER(bfibm_params), _V, _V, _V, _V, _V],
+    "bfibm_batch_create": [C.POINTER(_V)],
+    "bfibm_batch_add": [_V, _V, _IP],
+    "bfibm_batch_remove": [_V, C.c_int32],
+    "bfibm_batch_step": [_V, _IP],
+    "bfibm_batch_wait": [_V],
+    "bfibm_batch_slot_ms": [_V, C.c_int32, C.POINTER(C.c_float)],
+    "bfibm_batch_destroy": [_V],
 }
-_RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None}
+_RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None, "bfibm_batch_destroy": None}
 
 _LIB = None
 
@@ -358,3 +366,74 @@ def load_instance(inst, stream=None, prm_override=None):
     ctx.set_nodes(inst["X"])
     ctx.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
     return ctx
+
+
+class Batch:
+    """Independent contexts stepped together (see bfibm_batch_*)."""
+
+    def __init__(self):
+        self.lib = lib()
+        h = _V()
+        st = self.lib.bfibm_batch_create(C.byref(h))
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_create")
+        self.h = h
+        self.members = {}
+
+    def add(self, ctx):
+        slot = C.c_int32(-1)
+        st = self.lib.bfibm_batch_add(self.h, ctx.h, C.byref(slot))
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_add")
+        self.members[slot.value] = ctx
+        return slot.value
+
+    def remove(self, slot):
+        st = self.lib.bfibm_batch_remove(self.h, int(slot))
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_remove")
+        return self.members.pop(slot)
+
+    def step(self, nsteps=None):
+        arr = None
+        if nsteps is not None:
+            n = max(self.members) + 1 if self.members else 0
+            a = np.zeros(max(n, 1), dtype=np.int32)
+            for k, v in nsteps.items():
+                a[k] = v
+            arr = a.ctypes.data_as(_IP)
+            self._keep = a
+        st = self.lib.bfibm_batch_step(self.h, arr)
+        if st not in (OK, ENOCONV):
+            raise BfibmError(st, "bfibm_batch_step: " + self._member_errors())
+
+    def _member_errors(self):
+        msgs = []
+        for slot, ctx in self.members.items():
+            m = self.lib.bfibm_last_error(ctx.h)
+            if m:
+                msgs.append("slot %d: %s" % (slot, m.decode()))
+        return "; ".join(msgs)
+
+    def wait(self):
+        st = self.lib.bfibm_batch_wait(self.h)
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_wait: " + self._member_errors())
+
+    def slot_ms(self, slot):
+        ms = C.c_float(0)
+        st = self.lib.bfibm_batch_slot_ms(self.h, int(slot), C.byref(ms))
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_slot_ms")
+        return ms.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bfibm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -155,6 +155,7 @@ struct NodeSet {
   int* start;   // ntiles + 1
   int* cursor;  // ntiles
   int* clamped; // 1 counter
+  int* nonfinite;  // 1 counter: non-finite coordinates reset to 0
   double* tw;   // eta x 2 widths x 2 staggers x 3 axes x 4: 1D delta weights
   int* tlo;     // eta x 2 x 2 x 3 x (first index, count)
 };

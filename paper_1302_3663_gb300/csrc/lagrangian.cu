@@ -13,6 +13,7 @@
 #include <math_constants.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -369,8 +370,14 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadK A) {
   const int kind = A.a.phi_kind;
   const int C = A.cmax;                       // support points per axis at most
   const int slots = (D == 3) ? C * C * C : C * C;
+  // index in the tile region, or -1 (global atomic) for a point outside it,
+  // which only a node outside the domain can reach
   auto local = [&](int i, int j, int k) -> int {
-    return (i - base[0]) + A.R[0] * ((j - base[1]) + A.R[1] * (D == 3 ? (k - base[2]) : 0));
+    int li = i - base[0], lj = j - base[1], lk = D == 3 ? k - base[2] : 0;
+    if ((unsigned)li >= (unsigned)A.R[0] || (unsigned)lj >= (unsigned)A.R[1] ||
+        (D == 3 && (unsigned)lk >= (unsigned)A.R[2]))
+      return -1;
+    return li + A.R[0] * (lj + A.R[1] * lk);
   };
   auto flush_index = [&](int q, const int stag[3]) -> long long {
     int li = q % A.R[0];
@@ -528,15 +535,24 @@ __global__ void __launch_bounds__(kBlock) k_interp_advance(Geo g, NodeSet N, Ptr
     nv.visit(g, stag, [&](int, int, int, long long gi, double w) { v += ud[gi] * w; });
     U[d] = v;
   }
-  int clamped = 0;
+  int clamped = 0, bad = 0;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     N.U[3 * s + d] = U[d];
     double x = X[d] + c * U[d];
     double Lx = g.n[d] * g.h;
-    if (g.per[d]) {
+    if (!isfinite(x)) {
+      // a run that has blown up: keep the node inside the grid so that every
+      // later kernel stays in bounds, and count it
+      x = 0.0;
+      ++bad;
+    } else if (g.per[d]) {
       if (x >= Lx) x -= Lx;
       else if (x < 0.0) x += Lx;
+      if (!(x >= 0.0 && x < Lx)) {   // moved by more than one period
+        x -= Lx * floor(x / Lx);
+        if (!(x >= 0.0 && x < Lx)) x = 0.0;
+      }
     } else {
       if (x < 0.0) { x = 0.0; ++clamped; }
       else if (x > Lx) { x = Lx; ++clamped; }
@@ -544,6 +560,7 @@ __global__ void __launch_bounds__(kBlock) k_interp_advance(Geo g, NodeSet N, Ptr
     N.X[3 * s + d] = x;
   }
   if (clamped) atomicAdd(N.clamped, clamped);
+  if (bad) atomicAdd(N.nonfinite, bad);
 }
 
 __global__ void k_step_increment(long long* step) {
@@ -653,17 +670,25 @@ void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, con
   }
 }
 
+// The limit is a property of the kernel, shared by every context of the
+// process: it only ever grows, so that a context needing less never lowers it
+// below what another context's captured launches use.
 cudaError_t spread_set_smem(int D, size_t bytes) {
+  static std::mutex mu;
+  static size_t granted[4] = {0, 0, 0, 0};
+  std::lock_guard<std::mutex> lock(mu);
+  if (bytes <= granted[D]) return cudaSuccess;
   cudaError_t e;
   if (D == 3) {
     e = cudaFuncSetAttribute(k_spread<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_spread<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return e;
+  } else {
+    e = cudaFuncSetAttribute(k_spread<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_spread<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
-  e = cudaFuncSetAttribute(k_spread<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_spread<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) granted[D] = bytes;
   return e;
 }
 

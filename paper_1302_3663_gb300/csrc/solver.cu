@@ -149,7 +149,7 @@ struct bfibm_ctx {
   SpringSet S{};
   TileGeo tg{};
   long long* step_dev = nullptr;
-  int* counters = nullptr;    // [0] clamped, [1] event count
+  int* counters = nullptr;    // [0] clamped, [1] event count, [2] non-finite
   std::vector<void*> lag_allocs;
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;     // captures the bodies of device-side loops
@@ -799,9 +799,11 @@ void free_lag(bfibm_ctx* c, bool nodes, bool springs) {
       if (q) cudaFree(q);
     long long keep_eta = 0;
     int* clamped = c->N.clamped;
+    int* nonfinite = c->N.nonfinite;
     c->N = NodeSet{};
     c->N.eta = keep_eta;
     c->N.clamped = clamped;
+    c->N.nonfinite = nonfinite;
   }
   if (springs) {
     for (void* q : {(void*)c->S.ab, (void*)c->S.rest, (void*)c->S.K, (void*)c->S.brk,
@@ -940,6 +942,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
     return BFIBM_ENOMEM;
   }
   c->N.clamped = c->counters;
+  c->N.nonfinite = c->counters + 2;
   c->S.ev_count = c->counters + 1;
   c->S.step = c->step_dev;
   cudaStream_t s = c->stream;
@@ -1174,6 +1177,7 @@ bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
   }
   out->broken_total = std::min<int>(cnt[1], (int)std::max<long long>(c->S.m, 0));
   out->clamped_total = cnt[0];
+  out->nonfinite_total = cnt[2];
   auto rel = [](double f2, double r2) { return f2 > 0.0 ? std::sqrt(r2) / std::sqrt(f2) : 0.0; };
   out->res_visc = rel(c->host_sc[SL_VF], c->host_sc[SL_VR]);
   out->res_p = rel(c->host_sc[SL_PF], c->host_sc[SL_PR]);
@@ -1351,6 +1355,107 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
   CK(cudaStreamSynchronize(c->stream));
   drop_graph(c);
   return BFIBM_OK;
+}
+
+// ------------------------------------------------------------------ batches
+struct bfibm_batch {
+  struct Slot {
+    bfibm_ctx* c = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool timed = false;
+  };
+  std::vector<Slot> slots;
+};
+
+bfibm_status bfibm_batch_create(bfibm_batch** out) {
+  if (!out) return BFIBM_EINVAL;
+  *out = new (std::nothrow) bfibm_batch();
+  return *out ? BFIBM_OK : BFIBM_ENOMEM;
+}
+
+bfibm_status bfibm_batch_add(bfibm_batch* b, bfibm_ctx* c, int32_t* slot) {
+  if (!b || !c || !slot) return BFIBM_EINVAL;
+  READY(c);
+  int k = -1;
+  for (size_t q = 0; q < b->slots.size(); ++q)
+    if (!b->slots[q].c) {
+      k = (int)q;
+      break;
+    }
+  if (k < 0) {
+    k = (int)b->slots.size();
+    b->slots.emplace_back();
+  }
+  bfibm_batch::Slot& s = b->slots[k];
+  if (!s.e0 && (cudaEventCreate(&s.e0) != cudaSuccess || cudaEventCreate(&s.e1) != cudaSuccess)) {
+    cudaGetLastError();
+    return BFIBM_ECUDA;
+  }
+  s.c = c;
+  s.timed = false;
+  *slot = k;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_batch_remove(bfibm_batch* b, int32_t slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].c) return BFIBM_EINVAL;
+  b->slots[slot].c = nullptr;
+  b->slots[slot].timed = false;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_batch_step(bfibm_batch* b, const int32_t* nsteps) {
+  if (!b) return BFIBM_EINVAL;
+  bfibm_status agg = BFIBM_OK;
+  for (size_t q = 0; q < b->slots.size(); ++q) {
+    bfibm_batch::Slot& s = b->slots[q];
+    if (!s.c) continue;
+    int n = nsteps ? nsteps[q] : 1;
+    if (n <= 0) {
+      s.timed = false;
+      continue;
+    }
+    bfibm_ctx* c = s.c;
+    READY(c);
+    CK(cudaEventRecord(s.e0, c->stream));
+    bfibm_status st = do_steps(c, n);
+    if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
+    if (st == BFIBM_ENOCONV) agg = st;
+    CK(cudaEventRecord(s.e1, c->stream));
+    s.timed = true;
+  }
+  return agg;
+}
+
+bfibm_status bfibm_batch_wait(bfibm_batch* b) {
+  if (!b) return BFIBM_EINVAL;
+  for (auto& s : b->slots) {
+    if (!s.c) continue;
+    bfibm_ctx* c = s.c;
+    READY(c);
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_batch_slot_ms(bfibm_batch* b, int32_t slot, float* ms) {
+  if (!b || !ms || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].c)
+    return BFIBM_EINVAL;
+  bfibm_batch::Slot& s = b->slots[slot];
+  if (!s.timed) return BFIBM_ESTATE;
+  bfibm_ctx* c = s.c;
+  CK(cudaEventSynchronize(s.e1));
+  CK(cudaEventElapsedTime(ms, s.e0, s.e1));
+  return BFIBM_OK;
+}
+
+void bfibm_batch_destroy(bfibm_batch* b) {
+  if (!b) return;
+  for (auto& s : b->slots) {
+    if (s.e0) cudaEventDestroy(s.e0);
+    if (s.e1) cudaEventDestroy(s.e1);
+  }
+  delete b;
 }
 
 }  // extern "C"
