@@ -33,6 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-steps/s & V-cycle HBM roofline frac; served p50/p99 step latency vs FP64"
 UNIT = "cell-steps/s"
 
+# Solves run to a relative residual of 1e-11, which leaves max |div u| below
+# 1e-10 after every projection; coarse-grid viscosity scaled by gamma = 0.8
+# (Eq. ViscCoarseGrid, inside the recommended [0.7, 1]); V(3,3) cycles.
+TOL_SOLVER = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 100, "gamma_coarse": 0.8,
+              "nu1": 3, "nu2": 3}
+DIV_TARGET = 1e-10
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -53,16 +60,29 @@ def parse():
     ap.add_argument("--request-steps", type=int, default=None, help="c5: steps per request")
     ap.add_argument("--budget-frac", type=float, default=0.05,
                     help="c5: admission budget as a fraction of free device memory")
+    ap.add_argument("--solver", choices=["tol", "fixed"], default="tol",
+                    help="tol: V-cycles until max |div u| <= 1e-10 (relative residual "
+                         "1e-11); fixed: the workload's own fixed V-cycle counts")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel directly instead of replaying the step graph "
+                         "(same kernels; for profilers that cannot enter graphs with "
+                         "conditional nodes)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def load_workload(name, precision):
+def solver_override(args):
+    return dict(TOL_SOLVER) if args.solver == "tol" else {}
+
+
+def load_workload(name, precision, args=None):
     from paper_1302_3663_gb300 import workloads as W
     inst = W.CONFIGS[name]()
     if precision is not None:
         inst["params"]["precision"] = precision
+    if args is not None:
+        inst["params"].update(solver_override(args))
     return inst
 
 
@@ -73,7 +93,8 @@ def describe(inst):
     prec = "fp64" if p.get("precision", 0) == 0 else "fp32 V-cycles in fp64 defect correction"
     vc = ("%d viscous + %d pressure V(%d,%d) cycles per step" %
           (p["vc_visc"], p["vc_p"], p["nu1"], p["nu2"]) if p["vc_visc"] > 0
-          else "V-cycles to relative residual %.0e" % p["rtol"])
+          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %g"
+          % (p["nu1"], p["nu2"], p["rtol"], p["gamma_coarse"]))
     return {
         "workload": "%s: %s grid, %d nodes, %d springs, density ratio %g, viscosity ratio %g"
                     % (inst["name"], "x".join(map(str, n)), inst["X"].shape[0],
@@ -215,37 +236,40 @@ def cpu_baseline(inst, max_seconds=30.0):
                       % (steps, inst["name"], el)}
 
 
-def run_ours(args):
-    import numpy as np
+def timed_steps(ctx, stream, steps, world, label="timed"):
+    """Device time (ms) of `steps` time steps replayed on `stream` (inside an
+    NVTX range named `label`, so a profiler can select exactly these)."""
     import torch
-
-    from paper_1302_3663_gb300 import bfibm, workloads as W
-
-    world, rank, local = dist_setup(args)
-    inst = load_workload(args.config, args.precision)
-    prm = inst["params"]
-    cells = W.cells(prm)
-    stream = torch.cuda.Stream()
-    ctx = bfibm.load_instance(inst, stream=stream)
-    ctx.set_option(bfibm.OPT_STATS, 0)
-    ctx.step(args.warmup)
-    ctx.synchronize()
-    launches = ctx.launches_per_step()
-    barrier(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        e0.record(stream)
-        ctx.step(args.steps)
-        e1.record(stream)
-        e1.synchronize()
     barrier(world)
-    ms = max_over_ranks(world, e0.elapsed_time(e1))
-    value = cells * args.steps * world / (ms / 1e3)
-    st = ctx.get_stats()
+    torch.cuda.nvtx.range_push(label)
+    e0.record(stream)
+    ctx.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.nvtx.range_pop()
+    return max_over_ranks(world, e0.elapsed_time(e1))
 
-    # dominant kernel: the viscous red-black sweep on the finest grid, timed
-    # alone with events on the context's stream
+
+def final_stats(ctx):
+    """One more (untimed) step with statistics on: V-cycles of each solve,
+    relative residuals and max |div u| after the projection."""
+    from paper_1302_3663_gb300 import bfibm
+    ctx.set_option(bfibm.OPT_STATS, 1)
+    ctx.step(1)
+    st = ctx.get_stats()
+    return {"div_max": st["div_max"], "cycles_visc": st["cycles_visc"],
+            "cycles_p": st["cycles_p"], "res_visc": st["res_visc"], "res_p": st["res_p"],
+            "kinetic": st["kinetic"], "broken": st["broken_total"],
+            "wait_timeouts": st["wait_timeouts"]}
+
+
+def sweep_roofline(ctx, stream, prm, cells):
+    """The dominant kernel: one red-black sweep of one viscous component on
+    the finest grid (FP32 in the mixed path, FP64 otherwise), timed alone with
+    events on the context's stream."""
+    import torch
     peak, peak_src = measured_peak()
     sweeps = 10
     k0 = torch.cuda.Event(enable_timing=True)
@@ -258,8 +282,13 @@ def run_ours(args):
         k1.synchronize()
         nlaunch = sweeps * prm["dim"]
         alg = alg_bytes_visc_sweep(prm["dim"], cells, 4)
-        kname = ("k_v_rb_fused<float> (one-pass red-black sweep of one viscous component, "
-                 "FP32, finest grid)")
+        plans = [ctx.tma_plan(0, d) for d in range(prm["dim"])]
+        if all(p is None for p in plans):
+            kname = ("k_v_rb_fused<float> (one-pass red-black sweep of one viscous component, "
+                     "FP32, finest grid, inputs read from global memory)")
+        else:
+            kname = ("k_rb_tma / k_v_rb_fused<float> (one-pass red-black sweep of one viscous "
+                     "component, FP32, finest grid; per component the autotuned choice)")
     else:
         ctx.smooth_viscous(0, 2, sync=True)
         k0.record(stream)
@@ -268,6 +297,7 @@ def run_ours(args):
         k1.synchronize()
         nlaunch = sweeps * 2 * prm["dim"]
         alg = alg_bytes_visc_sweep(prm["dim"], cells, 8) / 2.0
+        plans = None
         kname = "k_v_rbgs<double> (one colour of one viscous component, FP64, finest grid)"
     launch_s = k0.elapsed_time(k1) / 1e3 / nlaunch
     achieved = alg / launch_s / 1e9
@@ -275,6 +305,42 @@ def run_ours(args):
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
             "alg_bytes_per_launch": alg, "launch_us": round(launch_s * 1e6, 2),
             "peak_source": peak_src}
+    if plans is not None:
+        roof["tma_plans"] = {"viscous_%d" % d: p for d, p in enumerate(plans)}
+        roof["tma_plans"]["pressure"] = ctx.tma_plan(0, 3)
+    return roof
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+
+    world, rank, local = dist_setup(args)
+    inst = load_workload(args.config, args.precision, args)
+    prm = inst["params"]
+    cells = W.cells(prm)
+    stream = torch.cuda.Stream()
+    ctx = bfibm.load_instance(inst, stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    if args.no_graph:
+        ctx.set_option(bfibm.OPT_GRAPH, 0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    lc0 = ctx.launch_counts()
+    with Clocks(local) as clk:
+        ms = timed_steps(ctx, stream, args.steps, world)
+    lc1 = ctx.launch_counts()
+    value = cells * args.steps * world / (ms / 1e3)
+    # kernels launched in the timed region: top-level graph nodes per step plus
+    # the loop bodies times the iterations the device ran
+    launches = None
+    if lc1["top"] > 0:
+        launches = (args.steps * lc1["top"] +
+                    (lc1["iters_visc"] - lc0["iters_visc"]) * lc1["body_visc"] +
+                    (lc1["iters_p"] - lc0["iters_p"]) * lc1["body_p"])
+    roof = sweep_roofline(ctx, stream, prm, cells)
+    fin = final_stats(ctx)
     ctx.close()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -287,17 +353,22 @@ def run_ours(args):
                           "no flush" % (bfibm.footprint(prm, inst['X'].shape[0],
                                                         inst['ab'].shape[0]) / 1e9)),
            "roofline": roof, "clocks": clk.summary(),
-           "gpu_launches": launches * args.steps if launches > 0 else None,
-           "final_stats": {"div_max": st["div_max"], "kinetic": st["kinetic"],
-                           "broken": st["broken_total"]}}
+           "gpu_launches": launches,
+           "final_stats": fin}
+    if args.solver == "tol":
+        out["config"]["div_target"] = DIV_TARGET
+        out["div_target_met"] = fin["div_max"] <= DIV_TARGET
 
     if not args.no_fp64 and prm.get("precision", 0) == 1:
         out["fp64_single_instance"] = run_fp64(inst, args, world, stream)
+    if args.solver == "tol":
+        out["fixed_3_vcycles"] = run_fixed(inst, args, world, stream)
     if not args.no_e2e:
         out["e2e"] = run_e2e(inst, args, world, stream)
     if not args.no_served:
         out["served"] = run_served_stream(args.requests or 8, args.request_steps or 10,
-                                          args.budget_frac, fp64_subset=8)
+                                          args.budget_frac, fp64_subset=8,
+                                          solver=solver_override(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst)
     if world > 1:
@@ -307,28 +378,38 @@ def run_ours(args):
         print(json.dumps(out))
 
 
-def run_fp64(inst, args, world, stream):
-    """The plain FP64 path on the same workload and step count, for comparison."""
-    import torch
+def run_fixed(inst, args, world, stream):
+    """The same workload with 3 V-cycles per solve (no convergence check): the
+    throughput of the loosest setting, for context."""
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+    prm = dict(inst["params"], vc_visc=3, vc_p=3, nu1=2, nu2=2, gamma_coarse=1.0)
+    ctx = bfibm.load_instance(dict(inst, params=prm), stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    steps = max(args.steps, 10)
+    ms = timed_steps(ctx, stream, steps, world, "timed_fixed")
+    fin = final_stats(ctx)
+    ctx.close()
+    return {"value": W.cells(prm) * steps * world / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / steps, "div_max": fin["div_max"]}
 
+
+def run_fp64(inst, args, world, stream):
+    """The plain FP64 single-instance path on the same workload, solver
+    settings and step count, for comparison at equal final divergence."""
     from paper_1302_3663_gb300 import bfibm, workloads as W
     prm = dict(inst["params"], precision=0)
     ctx = bfibm.load_instance(dict(inst, params=prm), stream=stream)
     ctx.set_option(bfibm.OPT_STATS, 0)
     ctx.step(args.warmup)
     ctx.synchronize()
-    barrier(world)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    ms = max_over_ranks(world, e0.elapsed_time(e1))
-    st = ctx.get_stats()
+    ms = timed_steps(ctx, stream, args.steps, world, "timed_fp64")
+    fin = final_stats(ctx)
     ctx.close()
     return {"value": W.cells(prm) * args.steps * world / (ms / 1e3), "unit": UNIT,
-            "ms_per_step": ms / args.steps, "div_max": st["div_max"]}
+            "ms_per_step": ms / args.steps, "div_max": fin["div_max"],
+            "cycles_visc": fin["cycles_visc"], "cycles_p": fin["cycles_p"]}
 
 
 def run_e2e(inst, args, world, stream):
@@ -371,7 +452,7 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_1302_3663_gb300 import workloads as W
-    inst = load_workload(args.config, 0)
+    inst = load_workload(args.config, 0, args)
     prm = inst["params"]
     cells = W.cells(prm)
     o = O.Oracle(prm, omp=True)
@@ -406,20 +487,25 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def run_served_stream(nreq, steps, budget_frac, fp64_subset=None):
+def run_served_stream(nreq, steps, budget_frac, fp64_subset=None, solver=None):
     """A bounded Poisson stream of duct requests through the continuous-
-    batching service, and the same requests run serially in plain FP64."""
+    batching service, and the same requests run one after another alone in
+    plain FP64 and in mixed precision (same solver settings)."""
     import torch
 
     from paper_1302_3663_gb300 import serve, workloads as W
     arr = W.c5_arrivals(count=nreq)
-    reqs = [serve.Request(i, W.c5_request(i), steps, float(arr[i])) for i in range(nreq)]
+    reqs = []
+    for i in range(nreq):
+        inst = W.c5_request(i)
+        inst["params"].update(solver or {})
+        reqs.append(serve.Request(i, inst, steps, float(arr[i])))
     free, _ = torch.cuda.mem_get_info()
     budget = max(int(budget_frac * free), max(int(1.05 * r.footprint) + 1 for r in reqs))
     srv = serve.Server(budget, keep_results=False)
     done = srv.run(reqs)
     srv.close()
-    out = serve.summarize(done, srv.elapsed)
+    out = serve.summarize(done, srv.elapsed, srv.busy)
     out["budget_bytes"] = budget
     out["steps_per_request"] = steps
     sub = reqs[:fp64_subset] if fp64_subset else reqs
@@ -437,6 +523,8 @@ def run_batched(args):
     from paper_1302_3663_gb300 import bfibm, workloads as W
     world, rank, local = dist_setup(args)
     insts = [W.c4_instance(i) for i in range(args.instances)]
+    for inst in insts:
+        inst["params"].update(solver_override(args))
     ctxs = []
     batch = bfibm.Batch()
     for inst in insts:
@@ -457,9 +545,9 @@ def run_batched(args):
         el = time.perf_counter() - t0
     el = max_over_ranks(world, el)
     value = cells * args.steps * world / el
-    # the plain FP64 path, each instance alone, on the first 8 instances
+    # every instance alone, one after another: plain FP64, then mixed precision
     from paper_1302_3663_gb300 import serve
-    sub = [serve.Request(i, insts[i], args.steps, 0.0) for i in range(min(8, len(insts)))]
+    sub = [serve.Request(i, insts[i], args.steps, 0.0) for i in range(len(insts))]
     v64, _ = serve.serial(sub, precision=0)
     v32, _ = serve.serial(sub, precision=None)
     batch.close()
@@ -486,7 +574,8 @@ def run_served(args):
     nreq = args.requests or 32
     steps = args.request_steps or 20
     with Clocks(local) as clk:
-        res = run_served_stream(nreq, steps, args.budget_frac, fp64_subset=8)
+        res = run_served_stream(nreq, steps, args.budget_frac, fp64_subset=8,
+                                solver=solver_override(args))
     out = {"metric": METRIC, "value": res["cell_steps_per_s"], "unit": UNIT, "n_gpus": world,
            "steps": steps, "warmup": 0, "ms_per_step": res["step_ms_p50"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",

@@ -95,7 +95,9 @@ typedef struct {
                                         has blown up, e.g. a time step above the
                                         stability limit of Sec. 4.3.4); each is reset
                                         to 0 so that every kernel stays in bounds */
-  int32_t reserved;
+  int32_t wait_timeouts;             /* bounded device waits that ran out (0 unless
+                                        the device misbehaves); the affected sweep
+                                        stops early and its result is not valid */
 } bfibm_stats;
 
 /* Field selectors for bfibm_get_field / bfibm_set_field (see layout above). */
@@ -173,6 +175,13 @@ bfibm_status bfibm_set_field(bfibm_ctx* c, int which, int comp, int level, const
 /* Device-to-device variants: `dev` is a device pointer to a dense field array. */
 bfibm_status bfibm_get_field_dev(bfibm_ctx* c, int which, int comp, int level, double* dev);
 bfibm_status bfibm_set_field_dev(bfibm_ctx* c, int which, int comp, int level, const double* dev);
+/* FP32 copies of the multigrid arrays used by the mixed-precision V-cycles
+   (precision 1 only): which is one of BFIBM_F_UT, URHS, P, PRHS, MUC, MUE,
+   BETA, M, URES, PRES (on level 0, UT/URHS/P/PRHS hold the FP32 correction
+   and its right-hand side). Same layout as bfibm_get_field, in floats; host
+   buffers; BFIBM_EINVAL for another selector or an FP64-only context. */
+bfibm_status bfibm_get_field_f32(bfibm_ctx* c, int which, int comp, int level, float* out);
+bfibm_status bfibm_set_field_f32(bfibm_ctx* c, int which, int comp, int level, const float* in);
 /* Node forces F (eta x dim, host) from the last spring stage. */
 bfibm_status bfibm_get_node_forces(bfibm_ctx* c, double* F);
 /* Break test, forces, spreads and coefficient hierarchy at the current nodes. */
@@ -206,13 +215,32 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
    default 1), BFIBM_OPT_GRAPH (1: replay fixed-count steps as a CUDA graph,
    default 1), BFIBM_OPT_FUSED (1: one-pass FP64 red-black sweeps; 0, the
    default: one kernel per colour, faster where FP64 arithmetic rather than
-   memory bounds the sweep; FP32 sweeps are always one-pass). Every option
-   gives the same results to rounding. */
-enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2 };
+   memory bounds the sweep; FP32 sweeps are always one-pass), BFIBM_OPT_TMA
+   (3D FP32 sweeps that stage their inputs in shared memory with
+   tensor-memory-accelerator copies: 0 never, the one-pass sweep reads them
+   from global memory; 1, the default, on the levels and components where the
+   autotuner timed them faster; 2 on every level that allows them; all give
+   bit-identical results). Every option gives the same results to rounding. */
+enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2, BFIBM_OPT_TMA = 3 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
+/* Tile plan the autotuner chose for the TMA-staged FP32 sweep of one level
+   (kind 0..D-1: viscous component, 3: pressure): out = {tile rows, planes per
+   chunk, planes prefetched, grid blocks}. Plans are timed once per level
+   shape when a mixed-precision context is created. BFIBM_EINVAL when the
+   level does not use the TMA sweep (not allowed, or the one-pass sweep timed
+   faster). No counterpart in the paper. */
+bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[4]);
 /* Kernel launches in one replayed time step (the kernel nodes of the captured
    step graph), or -1 when no graph has been captured yet. */
 bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n);
+/* Kernel launch accounting of the replayed step graph: out = {kernel nodes
+   at the top level of the step graph (-1 before the first capture), kernel
+   nodes of one iteration of the viscous and of the pressure relative-residual
+   loop (0 in fixed-cycle mode), iterations of the viscous and of the pressure
+   loop run on the device since the context was created}. Kernels launched
+   over n replayed steps = n * out[0] + (growth of out[3]) * out[1] + (growth
+   of out[4]) * out[2]. No counterpart in the paper. */
+bfibm_status bfibm_launch_counts(bfibm_ctx* c, int64_t out[5]);
 /* Allocation-free divergence stage (the paper has no counterpart: this exists
    for callers that cannot let a library allocate device memory, such as
    programs whose device memory is already held by another allocator, services

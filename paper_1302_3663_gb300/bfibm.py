@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTAT
 FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
          "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
-OPT_STATS, OPT_GRAPH, OPT_FUSED = 0, 1, 2
+OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA = 0, 1, 2, 3
 
 
 class BfibmError(RuntimeError):
@@ -49,7 +49,7 @@ class bfibm_stats(C.Structure):
                 ("broken_total", C.c_int32), ("clamped_total", C.c_int32),
                 ("res_visc", C.c_double), ("res_p", C.c_double), ("div_max", C.c_double),
                 ("kinetic", C.c_double), ("step", C.c_int64),
-                ("nonfinite_total", C.c_int32), ("reserved", C.c_int32)]
+                ("nonfinite_total", C.c_int32), ("wait_timeouts", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -74,6 +74,9 @@ SIGNATURES = {
     "bfibm_destroy": [_V],
     "bfibm_get_field": [_V, _i, _i, _i, _DP],
     "bfibm_set_field": [_V, _i, _i, _i, _DP],
+    "bfibm_tma_plan": [_V, _i, _i, _IP],
+    "bfibm_get_field_f32": [_V, _i, _i, _i, C.POINTER(C.c_float)],
+    "bfibm_set_field_f32": [_V, _i, _i, _i, C.POINTER(C.c_float)],
     "bfibm_get_field_dev": [_V, _i, _i, _i, _V],
     "bfibm_set_field_dev": [_V, _i, _i, _i, _V],
     "bfibm_get_node_forces": [_V, _DP],
@@ -93,6 +96,7 @@ SIGNATURES = {
     "bfibm_body_force": [_V, _DP],
     "bfibm_set_option": [_V, _i, _L],
     "bfibm_launches_per_step": [_V, C.POINTER(_L)],
+    "bfibm_launch_counts": [_V, C.POINTER(_L)],
     "bfibm_footprint": [C.POINTER(bfibm_params), _L, _L, C.POINTER(_L)],
     "bfibm_divergence_noalloc": [C.POINTER(bfibm_params), _V, _V, _V, _V, _V],
     "bfibm_batch_create": [C.POINTER(_V)],
@@ -293,6 +297,26 @@ class Context:
         self._chk(self.lib.bfibm_set_field(self.h, FIELD[which], comp, level, _dp(a)),
                   "bfibm_set_field")
 
+    def tma_plan(self, level=0, kind=0):
+        """(tile rows, planes per chunk, planes prefetched, grid) of the tuned
+        TMA sweep on a level, or None where the level does not use it."""
+        out = (C.c_int32 * 4)()
+        st = self.lib.bfibm_tma_plan(self.h, level, kind, out)
+        return tuple(out) if st == OK else None
+
+    def get_field_f32(self, which, comp=0, level=0):
+        out = np.empty(self.shape(level), dtype=np.float32)
+        self._chk(self.lib.bfibm_get_field_f32(self.h, FIELD[which], comp, level,
+                                               out.ctypes.data_as(C.POINTER(C.c_float))),
+                  "bfibm_get_field_f32")
+        return out
+
+    def set_field_f32(self, which, arr, comp=0, level=0):
+        a = np.ascontiguousarray(arr, dtype=np.float32).reshape(self.shape(level))
+        self._chk(self.lib.bfibm_set_field_f32(self.h, FIELD[which], comp, level,
+                                               a.ctypes.data_as(C.POINTER(C.c_float))),
+                  "bfibm_set_field_f32")
+
     def get_field_dev(self, which, dev_ptr, comp=0, level=0):
         self._chk(self.lib.bfibm_get_field_dev(self.h, FIELD[which], comp, level, int(dev_ptr)),
                   "bfibm_get_field_dev")
@@ -347,6 +371,12 @@ class Context:
     def residual_viscous(self, level=0):
         self._chk(self.lib.bfibm_residual_viscous(self.h, level), "bfibm_residual_viscous")
         return [self.get_field("ures", d, level) for d in range(self.dim)]
+
+    def launch_counts(self):
+        """{top, body_visc, body_p, iters_visc, iters_p}: see bfibm_launch_counts."""
+        out = (_L * 5)()
+        self._chk(self.lib.bfibm_launch_counts(self.h, out), "bfibm_launch_counts")
+        return dict(zip(("top", "body_visc", "body_p", "iters_visc", "iters_p"), out))
 
     def launches_per_step(self):
         n = _L(0)

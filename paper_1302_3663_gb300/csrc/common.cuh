@@ -114,6 +114,21 @@ cudaError_t coarse_set_smem();
 
 cudaError_t fused_set_carveout();
 
+// ---------------------------------------------------------------- smooth_tma.cu
+// 3D FP32 red-black sweeps with TMA-staged inputs. Kind K: 0..2 viscous
+// component, 3 pressure; coef = inv_re / h^2 (viscous) or h^2 (pressure);
+// err counts bounded waits that ran out.
+bool tma_eligible(int D, const Geo& g);
+cudaError_t tma_set_smem();
+cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, float* out,
+                         int* err, double coef, cudaStream_t s);
+cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K, float* out,
+                          int* err, double coef, cudaStream_t s);
+// whether the tuner found the TMA sweep faster than the one-pass sweep
+bool tma_chosen(int K, const Geo& g);
+// tuned plan of a level shape: tile rows, chunk planes, prefetch planes, grid
+bool tma_plan_of(int K, const Geo& g, int out[4]);
+
 // FP64-only grid stages.
 void launch_coef_fine(int D, const Geo& g, double* const rho[3], double* beta[3], double* m[3],
                       double msc, cudaStream_t s);
@@ -141,7 +156,7 @@ void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_
 void launch_fill(double* a, long long n, double v, cudaStream_t s);
 // device side of a relative-residual while loop in a graph (see solver.cu)
 void launch_tol_check(cudaGraphConditionalHandle h, const double* out, int sf, int sr,
-                      double rtol, int maxc, int* counter, cudaStream_t s);
+                      double rtol, int maxc, int* counter, long long* total, cudaStream_t s);
 
 // ------------------------------------------------------------ lagrangian.cu
 struct NodeSet {

@@ -149,16 +149,20 @@ struct bfibm_ctx {
   SpringSet S{};
   TileGeo tg{};
   long long* step_dev = nullptr;
-  int* counters = nullptr;    // [0] clamped, [1] event count, [2] non-finite
+  int* counters = nullptr;    // [0] clamped, [1] event count, [2] non-finite, [3] wait timeouts
   std::vector<void*> lag_allocs;
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;     // captures the bodies of device-side loops
   bool own_stream = false;
   bool capturing = false;         // a step graph is being captured
   int* dev_cycles = nullptr;      // V-cycles used by the last solves (visc, p)
+  long long* loop_total = nullptr;   // device-loop iterations so far (visc, p)
+  long long body_kernels[2] = {0, 0};   // kernel nodes of one iteration of each loop
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
   bool fused = false;            // one-pass FP64 red-black sweeps (FP32 sweeps always are)
+  int tma = 1;                   // 3D FP32 sweeps with TMA-staged inputs: 0 never, 1 where
+                                 // the tuner timed them faster, 2 wherever a level allows
   bool collect_stats = true;
   bool dirty = true;
   int poisoned = 0;
@@ -294,12 +298,28 @@ bfibm_status read_scalars(bfibm_ctx* c) {
   return BFIBM_OK;
 }
 
+long long count_kernel_nodes(cudaGraph_t graph) {
+  size_t nn = 0;
+  long long nk = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+  return nk;
+}
+
 // Records into the step graph being captured on c->stream a device-side
 // loop: a conditional WHILE node whose body (queued by `body` on c->stream,
 // redirected to the auxiliary stream while the body is captured) ends with
 // launch_tol_check, which decides whether the body runs again.
 template <typename Body>
-bfibm_status capture_while(bfibm_ctx* c, Body body) {
+bfibm_status capture_while(bfibm_ctx* c, int which, Body body) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -325,6 +345,7 @@ bfibm_status capture_while(bfibm_ctx* c, Body body) {
   c->stream = main;
   cudaGraph_t out = nullptr;
   CK(cudaStreamEndCapture(c->aux, &out));
+  c->body_kernels[which] = count_kernel_nodes(bg);
   return BFIBM_OK;
 }
 
@@ -352,13 +373,13 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
   }
   if (c->capturing) {
     cudaMemsetAsync(c->dev_cycles + 1, 0, sizeof(int), s);
-    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+    bfibm_status cs = capture_while(c, 1, [&](cudaGraphConditionalHandle h) {
       vcycle_p(c, 0);
       launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, c->stream);
       launch_p_residual<double>(c->D, L0.g, L0.d, c->stream);
       launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, c->stream);
       launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1,
-                       c->stream);
+                       c->loop_total + 1, c->stream);
     });
     *used = -1;
     return cs;
@@ -399,12 +420,12 @@ bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
   }
   if (c->capturing) {
     cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
-    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+    bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
       vcycle_v(c, 0);
       launch_v_residual<double>(c->D, L0.g, L0.d, c->P.inv_re, c->stream);
       launch_norm2(c->D, L0.g, L0.d.ur, c->D, c->sc, SL_VR, c->stream);
       launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles,
-                       c->stream);
+                       c->loop_total, c->stream);
     });
     *used = -1;
     return cs;
@@ -430,10 +451,19 @@ bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
 
 // ------------------------------------------------------ mixed precision
 // FP32 sweeps on level l (out of place, copied back after an odd count).
+bool use_tma(bfibm_ctx* c, int l) { return c->tma && tma_eligible(c->D, c->lev[l].g); }
+bool tma_for(bfibm_ctx* c, int l, int K) {
+  return use_tma(c, l) && (c->tma == 2 || tma_chosen(K, c->lev[l].g));
+}
+
 void smooth_p32(bfibm_ctx* c, int l, int n) {
   Level& Lv = c->lev[l];
+  const bool tma = tma_for(c, l, 3);
   for (int it = 0; it < n; ++it) {
-    launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream);
+    if (tma)
+      launch_rb_tma(c->D, Lv.g, Lv.f, 3, Lv.f.p2, c->counters + 3, Lv.g.h * Lv.g.h, c->stream);
+    else
+      launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream);
     std::swap(Lv.f.p, Lv.f.p2);
   }
   if (n & 1) {
@@ -447,7 +477,11 @@ void smooth_v32(bfibm_ctx* c, int l, int n) {
   Level& Lv = c->lev[l];
   for (int it = 0; it < n; ++it)
     for (int d = 0; d < c->D; ++d) {
-      launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream);
+      if (tma_for(c, l, d))
+        launch_rb_tma(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->counters + 3,
+                      c->P.inv_re / (Lv.g.h * Lv.g.h), c->stream);
+      else
+        launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream);
       std::swap(Lv.f.u[d], Lv.f.u2[d]);
     }
   if (n & 1)
@@ -520,7 +554,7 @@ bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
   if (tol && c->capturing) {
     cudaMemsetAsync(c->dev_cycles + 1, 0, sizeof(int), s);
     launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, nullptr, s);
-    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+    bfibm_status cs = capture_while(c, 1, [&](cudaGraphConditionalHandle h) {
       cudaStream_t b = c->stream;
       vcycle_p32(c, 0);
       xs[0] = L0.d.p;
@@ -529,7 +563,8 @@ bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
       launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, b);
       launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, b);
-      launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1, b);
+      launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1,
+                       c->loop_total + 1, b);
     });
     *used = -1;
     return cs;
@@ -574,13 +609,14 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   if (tol && c->capturing) {
     cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
     launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, nullptr, s);
-    bfibm_status cs = capture_while(c, [&](cudaGraphConditionalHandle h) {
+    bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
       cudaStream_t b = c->stream;
       vcycle_v32(c, 0);
       launch_add_correction(c->D, L0.g, L0.d.u, L0.f.u, c->D, b);
       launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
-      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles, b);
+      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles,
+                       c->loop_total, b);
     });
     *used = -1;
     return cs;
@@ -717,17 +753,7 @@ bfibm_status do_steps(bfibm_ctx* c, int nsteps) {
         return qs;
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-      size_t nn = 0;
-      if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess) {
-        std::vector<cudaGraphNode_t> nodes(nn);
-        long long nk = 0;
-        if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
-          for (auto nd : nodes) {
-            cudaGraphNodeType t;
-            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
-          }
-        c->graph_kernels = nk;
-      }
+      c->graph_kernels = count_kernel_nodes(graph);
       e = cudaGraphInstantiate(&c->gexec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
@@ -773,6 +799,44 @@ double* field_ptr(bfibm_ctx* c, int which, int comp, int level) {
     case BFIBM_F_PRES: return L.pr;
   }
   return nullptr;
+}
+
+float* field_ptr32(bfibm_ctx* c, int which, int comp, int level) {
+  if (c->P.precision != 1 || level < 0 || level >= c->L) return nullptr;
+  int D = c->D;
+  bool vec = (which == BFIBM_F_UT || which == BFIBM_F_URHS || which == BFIBM_F_BETA ||
+              which == BFIBM_F_M || which == BFIBM_F_URES);
+  if (vec && (comp < 0 || comp >= D)) return nullptr;
+  if (which == BFIBM_F_MUE && (comp < 0 || comp >= edge_count(D))) return nullptr;
+  LevelPtrs<float>& L = c->lev[level].f;
+  switch (which) {
+    case BFIBM_F_UT: return L.u[comp];
+    case BFIBM_F_URHS: return L.uf[comp];
+    case BFIBM_F_P: return L.p;
+    case BFIBM_F_PRHS: return L.pf;
+    case BFIBM_F_MUC: return L.muc;
+    case BFIBM_F_MUE: return L.mue[comp];
+    case BFIBM_F_BETA: return L.beta[comp];
+    case BFIBM_F_M: return L.m[comp];
+    case BFIBM_F_URES: return L.ur[comp];
+    case BFIBM_F_PRES: return L.pr;
+  }
+  return nullptr;
+}
+
+bfibm_status copy_field32(bfibm_ctx* c, int which, int comp, int level, void* ext, bool to_ext) {
+  float* p = field_ptr32(c, which, comp, level);
+  if (!p || !ext) return set_err(c, BFIBM_EINVAL, "bad FP32 field selector or pointer");
+  const Geo& g = c->lev[level].g;
+  size_t row = (size_t)g.s[0] * sizeof(float);
+  size_t pitch = (size_t)g.st[1] * sizeof(float);
+  size_t rows = (size_t)g.s[1] * g.s[2];
+  if (to_ext)
+    CK(cudaMemcpy2DAsync(ext, row, p, pitch, row, rows, cudaMemcpyDeviceToHost, c->stream));
+  else
+    CK(cudaMemcpy2DAsync(p, pitch, ext, row, row, rows, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
 }
 
 bfibm_status copy_field(bfibm_ctx* c, int which, int comp, int level, void* ext, bool to_ext,
@@ -935,6 +999,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
       cudaMalloc((void**)&c->step_dev, sizeof(long long)) != cudaSuccess ||
       cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
       cudaMalloc((void**)&c->dev_cycles, sizeof(int) * 2) != cudaSuccess ||
+      cudaMalloc((void**)&c->loop_total, sizeof(long long) * 2) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost((void**)&c->host_sc, 16 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -949,7 +1014,8 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   bool ok = cudaMemsetAsync(c->pool, 0, c->pool_bytes, s) == cudaSuccess &&
             cudaMemsetAsync(c->step_dev, 0, sizeof(long long), s) == cudaSuccess &&
             cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, s) == cudaSuccess &&
-            cudaMemsetAsync(c->dev_cycles, 0, sizeof(int) * 2, s) == cudaSuccess;
+            cudaMemsetAsync(c->dev_cycles, 0, sizeof(int) * 2, s) == cudaSuccess &&
+            cudaMemsetAsync(c->loop_total, 0, sizeof(long long) * 2, s) == cudaSuccess;
   if (!ok) {
     bfibm_destroy(c);
     return BFIBM_ECUDA;
@@ -986,6 +1052,25 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
     bfibm_destroy(c);
     return BFIBM_ECUDA;
   }
+  // tile shapes of the TMA-staged FP32 sweeps, timed once per level shape
+  // (out of place into the spare buffers, before any stream capture)
+  if (c->P.precision == 1 && D == 3) {
+    bool ok = tma_set_smem() == cudaSuccess;
+    for (int l = 0; ok && l < c->L; ++l) {
+      Level& Lv = c->lev[l];
+      if (!tma_eligible(D, Lv.g)) continue;
+      double hh = Lv.g.h * Lv.g.h;
+      ok = tma_autotune(D, Lv.g, Lv.f, 3, Lv.f.p2, c->counters + 3, hh, s) == cudaSuccess;
+      for (int d = 0; ok && d < D; ++d)
+        ok = tma_autotune(D, Lv.g, Lv.f, d, Lv.f.u2[d], c->counters + 3, p->inv_re / hh, s) ==
+             cudaSuccess;
+    }
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      bfibm_destroy(c);
+      return BFIBM_ECUDA;
+    }
+  }
   c->dirty = true;
   *out = c;
   return BFIBM_OK;
@@ -1001,6 +1086,7 @@ void bfibm_destroy(bfibm_ctx* c) {
   if (c->step_dev) cudaFree(c->step_dev);
   if (c->counters) cudaFree(c->counters);
   if (c->dev_cycles) cudaFree(c->dev_cycles);
+  if (c->loop_total) cudaFree(c->loop_total);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->host_sc) cudaFreeHost(c->host_sc);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1178,6 +1264,7 @@ bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
   out->broken_total = std::min<int>(cnt[1], (int)std::max<long long>(c->S.m, 0));
   out->clamped_total = cnt[0];
   out->nonfinite_total = cnt[2];
+  out->wait_timeouts = cnt[3];
   auto rel = [](double f2, double r2) { return f2 > 0.0 ? std::sqrt(r2) / std::sqrt(f2) : 0.0; };
   out->res_visc = rel(c->host_sc[SL_VF], c->host_sc[SL_VR]);
   out->res_p = rel(c->host_sc[SL_PF], c->host_sc[SL_PR]);
@@ -1194,6 +1281,14 @@ bfibm_status bfibm_get_field(bfibm_ctx* c, int which, int comp, int level, doubl
 bfibm_status bfibm_set_field(bfibm_ctx* c, int which, int comp, int level, const double* in) {
   READY(c);
   return copy_field(c, which, comp, level, (void*)in, false, cudaMemcpyHostToDevice);
+}
+bfibm_status bfibm_get_field_f32(bfibm_ctx* c, int which, int comp, int level, float* out) {
+  READY(c);
+  return copy_field32(c, which, comp, level, out, true);
+}
+bfibm_status bfibm_set_field_f32(bfibm_ctx* c, int which, int comp, int level, const float* in) {
+  READY(c);
+  return copy_field32(c, which, comp, level, (void*)in, false);
 }
 bfibm_status bfibm_get_field_dev(bfibm_ctx* c, int which, int comp, int level, double* dev) {
   READY(c);
@@ -1334,10 +1429,35 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G) {
   return BFIBM_OK;
 }
 
+bfibm_status bfibm_launch_counts(bfibm_ctx* c, int64_t out[5]) {
+  READY(c);
+  if (!out) return set_err(c, BFIBM_EINVAL, "out is NULL");
+  long long tot[2] = {0, 0};
+  CK(cudaMemcpyAsync(tot, c->loop_total, sizeof(tot), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  out[0] = c->gexec ? c->graph_kernels : -1;
+  out[1] = c->body_kernels[0];
+  out[2] = c->body_kernels[1];
+  out[3] = tot[0];
+  out[4] = tot[1];
+  return BFIBM_OK;
+}
+
 bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n) {
   READY(c);
   if (!n) return BFIBM_EINVAL;
   *n = c->gexec ? c->graph_kernels : -1;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[4]) {
+  READY(c);
+  if (!out || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
+      (kind < 3 && kind >= c->D) || c->P.precision != 1 || !use_tma(c, level))
+    return set_err(c, BFIBM_EINVAL, "no TMA sweep on this level");
+  int v[4];
+  if (!tma_plan_of(kind, c->lev[level].g, v)) return set_err(c, BFIBM_EINVAL, "level not tuned");
+  for (int q = 0; q < 4; ++q) out[q] = v[q];
   return BFIBM_OK;
 }
 
@@ -1349,6 +1469,9 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
     c->use_graph = value != 0;
   } else if (option == BFIBM_OPT_FUSED) {
     c->fused = value != 0;
+  } else if (option == BFIBM_OPT_TMA) {
+    if (value < 0 || value > 2) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_TMA takes 0, 1 or 2");
+    c->tma = (int)value;
   } else {
     return set_err(c, BFIBM_EINVAL, "unknown option");
   }

@@ -897,9 +897,11 @@ __global__ void k_laminar(Geo g, int D, int fa, int ta0, int ta1, double mu_eff,
 // One iteration of a device-side relative-residual loop has finished:
 // count it and keep looping while ||r||/||f|| > rtol and the cap is not hit.
 __global__ void k_tol_check(cudaGraphConditionalHandle h, const double* __restrict__ out, int sf,
-                            int sr, double rtol, int maxc, int* __restrict__ counter) {
+                            int sr, double rtol, int maxc, int* __restrict__ counter,
+                            long long* __restrict__ total) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int n = ++(*counter);
+  ++(*total);
   double f2 = out[sf], r2 = out[sr];
   double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
   cudaGraphSetConditional(h, (rel > rtol && n < maxc) ? 1u : 0u);
@@ -1174,8 +1176,8 @@ void launch_finalize_sum(const double* partial, int nb, double* out, int slot, d
 }
 
 void launch_tol_check(cudaGraphConditionalHandle h, const double* out, int sf, int sr,
-                      double rtol, int maxc, int* counter, cudaStream_t s) {
-  k_tol_check<<<1, 32, 0, s>>>(h, out, sf, sr, rtol, maxc, counter);
+                      double rtol, int maxc, int* counter, long long* total, cudaStream_t s) {
+  k_tol_check<<<1, 32, 0, s>>>(h, out, sf, sr, rtol, maxc, counter, total);
 }
 
 void launch_fill(double* a, long long n, double v, cudaStream_t s) {

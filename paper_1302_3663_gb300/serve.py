@@ -44,6 +44,7 @@ class Server:
         self.used = 0
         self.active = {}          # slot -> (request, context)
         self.ticks = 0
+        self.busy = 0.0           # seconds from each tick's launch to its completion
 
     def _admit(self, req, now):
         ctx = bfibm.load_instance(req.inst)
@@ -84,9 +85,11 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(0.05, pending[0].arrival - now)))
                 continue
+            tb = clock()
             self.batch.step()
             self.batch.wait()
             self.ticks += 1
+            self.busy += clock() - tb
             now = clock() - t0
             for slot in list(self.active):
                 req, _ = self.active[slot]
@@ -106,33 +109,44 @@ class Server:
         self.batch.close()
 
 
-def summarize(finished, elapsed):
+def summarize(finished, elapsed, busy=None):
+    """Throughput over the wall-clock span of the stream (arrival gaps
+    included) and, given the server's busy time, over the ticks alone."""
     lat = np.concatenate([np.asarray(r.step_ms) for r in finished]) if finished else np.zeros(1)
     cell_steps = sum(r.cells * r.done for r in finished)
     turnaround = [r.finished - r.arrival for r in finished]
     queued = [r.admitted - r.arrival for r in finished]
-    return {"requests": len(finished), "cell_steps": cell_steps,
+    out = {"requests": len(finished), "cell_steps": cell_steps,
             "cell_steps_per_s": cell_steps / elapsed if elapsed > 0 else 0.0,
             "step_ms_p50": float(np.percentile(lat, 50)),
             "step_ms_p99": float(np.percentile(lat, 99)),
             "turnaround_s_p50": float(np.percentile(turnaround, 50)) if turnaround else 0.0,
             "queue_s_max": float(max(queued)) if queued else 0.0,
             "elapsed_s": elapsed}
+    if busy is not None:
+        out["busy_s"] = busy
+        out["cell_steps_per_busy_s"] = cell_steps / busy if busy > 0 else 0.0
+    return out
 
 
-def serial(requests, precision=None):
+def serial(requests, precision=None, params=None):
     """The same requests one after another, each alone (the baseline the
-    service is compared with). Returns cell-steps per second of device time."""
+    service is compared with): one untimed step (it captures the step graph),
+    then the request's steps timed on the device. Returns cell-steps per
+    second of device time and the total device milliseconds."""
     import torch
     total_ms = 0.0
     cell_steps = 0
     for r in requests:
         prm = dict(r.inst["params"])
+        if params:
+            prm.update(params)
         if precision is not None:
             prm["precision"] = precision
         s = torch.cuda.Stream()
         ctx = bfibm.load_instance(r.inst, stream=s, prm_override=prm)
         ctx.set_option(bfibm.OPT_STATS, 0)
+        ctx.step(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s)

@@ -157,3 +157,21 @@ def test_device_loop_equals_host_loop_tolerance_mode(precision):
     for d in range(3):
         assert_close(a.get_velocity(d), b.get_velocity(d), 1e-12, "u%d" % d)
     assert_close(a.get_pressure(), b.get_pressure(), 1e-12, "p")
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_accounting_of_device_loops(precision):
+    # the step graph of the relative-residual mode loops on the device: its
+    # loop bodies and the iterations they ran are counted
+    inst = W.c2()
+    over = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-9, "max_cycles": 60, "precision": precision}
+    c = bfibm.load_instance(inst, prm_override=over)
+    c.step(1)
+    a = c.launch_counts()
+    c.step(2)
+    b = c.launch_counts()
+    st = c.get_stats()
+    assert a["top"] > 0 and a["body_visc"] > 0 and a["body_p"] > 0
+    assert b["iters_visc"] - a["iters_visc"] >= 2 * 3
+    assert b["iters_p"] - a["iters_p"] >= 2
+    assert b["iters_visc"] - a["iters_visc"] >= st["cycles_visc"]

@@ -1,0 +1,89 @@
+"""The 3D FP32 red-black sweeps with TMA-staged inputs against the one-pass
+sweep that reads global memory: on the same FP32 inputs both must give
+bit-identical iterates (the per-point arithmetic is the same; only the data
+movement differs). Shapes cover ragged row tiles and plane chunks, periodic
+and wall x and z axes, and the 128 x 128 x 256 grid of the mixed-precision
+benchmark."""
+import numpy as np
+import pytest
+
+from paper_1302_3663_gb300 import bfibm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def context(n, periodic, flow_axis=2):
+    h = 1.0 / n[0]
+    prm = W.base_params(3, n, periodic, flow_axis, h, rho_ratio=1.5, mu_ratio=300.0,
+                        omega=0.8 * h, omega_mu=0.8 * h, precision=1, u_center=0.0,
+                        body_force=1.0)
+    c = bfibm.Context(prm)
+    c.set_nodes(np.zeros((0, 3)))
+    c.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+    return c
+
+
+def random_inputs(c, rng):
+    f = {}
+    for d in range(3):
+        f[("ut", d)] = rng.standard_normal(c.shape(0))
+        f[("urhs", d)] = rng.standard_normal(c.shape(0))
+        f[("m", d)] = rng.uniform(0.5, 2.0, c.shape(0))
+        f[("beta", d)] = rng.uniform(0.2, 1.0, c.shape(0))
+        f[("mue", d)] = np.exp(rng.uniform(np.log(0.01), np.log(10.0), c.shape(0)))
+    f[("muc", 0)] = np.exp(rng.uniform(np.log(0.01), np.log(10.0), c.shape(0)))
+    f[("p", 0)] = rng.standard_normal(c.shape(0))
+    f[("prhs", 0)] = rng.standard_normal(c.shape(0))
+    for (name, comp), v in f.items():
+        c.set_field_f32(name, v, comp, 0)
+    return f
+
+
+def sweep(c, f, which, tma, nsweeps):
+    c.set_option(bfibm.OPT_TMA, 2 if tma else 0)
+    for (name, comp), v in f.items():
+        c.set_field_f32(name, v, comp, 0)
+    c.smooth_f32(which, 0, nsweeps)
+    if which == 0:
+        return [c.get_field_f32("p", 0, 0)]
+    return [c.get_field_f32("ut", d, 0) for d in range(3)]
+
+
+SHAPES = [((48, 20, 40), (0, 0, 1), 2),    # ragged row tiles and chunks, periodic z
+          ((40, 22, 44), (1, 0, 1), 2),    # periodic x and z
+          ((32, 36, 30), (1, 0, 0), 0),    # wall z (flow along periodic x)
+          ((64, 64, 64), (0, 0, 1), 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=["ragged", "per_x", "wall_z", "c2"])
+@pytest.mark.parametrize("which", [0, 1], ids=["pressure", "viscous"])
+def test_tma_sweep_bit_identical(shape, which):
+    n, per, fa = shape
+    c = context(n, per, fa)
+    f = random_inputs(c, np.random.default_rng(31))
+    a = sweep(c, f, which, True, 3)
+    b = sweep(c, f, which, False, 3)
+    for x, y in zip(a, b):
+        assert np.isfinite(x).all()
+        assert np.array_equal(x, y), "max |diff| %.3e" % np.abs(x - y).max()
+    assert c.get_stats()["wait_timeouts"] == 0
+    c.close()
+
+
+def test_tma_sweep_bit_identical_on_the_benchmark_grid():
+    inst = W.c3()
+    c = bfibm.load_instance(inst)
+    c.step(1)
+    f = {}
+    for d in range(3):
+        for name in ("ut", "urhs", "m", "beta", "mue"):
+            f[(name, d)] = c.get_field_f32(name, d, 0)
+    for name in ("muc", "p", "prhs"):
+        f[(name, 0)] = c.get_field_f32(name, 0, 0)
+    for which in (0, 1):
+        a = sweep(c, f, which, True, 2)
+        b = sweep(c, f, which, False, 2)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert c.get_stats()["wait_timeouts"] == 0
+    c.close()
