@@ -67,6 +67,9 @@ def parse():
                     help="launch every kernel directly instead of replaying the step graph "
                          "(same kernels; for profilers that cannot enter graphs with "
                          "conditional nodes)")
+    ap.add_argument("--tma", type=int, choices=[0, 1, 2], default=1,
+                    help="FP32 sweeps with TMA-staged inputs: 0 never, 1 where the autotuner "
+                         "timed them faster (default), 2 wherever a level allows")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -276,10 +279,12 @@ def sweep_roofline(ctx, stream, prm, cells):
     k1 = torch.cuda.Event(enable_timing=True)
     if prm.get("precision", 0) == 1:
         ctx.smooth_f32(1, 0, 2, sync=True)
+        torch.cuda.nvtx.range_push("sweep")
         k0.record(stream)
         ctx.smooth_f32(1, 0, sweeps, sync=False)
         k1.record(stream)
         k1.synchronize()
+        torch.cuda.nvtx.range_pop()
         nlaunch = sweeps * prm["dim"]
         alg = alg_bytes_visc_sweep(prm["dim"], cells, 4)
         plans = [ctx.tma_plan(0, d) for d in range(prm["dim"])]
@@ -291,10 +296,12 @@ def sweep_roofline(ctx, stream, prm, cells):
                      "component, FP32, finest grid; per component the autotuned choice)")
     else:
         ctx.smooth_viscous(0, 2, sync=True)
+        torch.cuda.nvtx.range_push("sweep")
         k0.record(stream)
         ctx.smooth_viscous(0, sweeps, sync=False)
         k1.record(stream)
         k1.synchronize()
+        torch.cuda.nvtx.range_pop()
         nlaunch = sweeps * 2 * prm["dim"]
         alg = alg_bytes_visc_sweep(prm["dim"], cells, 8) / 2.0
         plans = None
@@ -325,6 +332,7 @@ def run_ours(args):
     ctx.set_option(bfibm.OPT_STATS, 0)
     if args.no_graph:
         ctx.set_option(bfibm.OPT_GRAPH, 0)
+    ctx.set_option(bfibm.OPT_TMA, args.tma)
     ctx.step(args.warmup)
     ctx.synchronize()
     lc0 = ctx.launch_counts()
