@@ -225,11 +225,19 @@ enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2, BFIBM_OPT_
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Tile plan the autotuner chose for the TMA-staged FP32 sweep of one level
    (kind 0..D-1: viscous component, 3: pressure): out = {tile rows, planes per
-   chunk, planes prefetched, grid blocks}. Plans are timed once per level
+   chunk, planes prefetched, columns per strip, grid blocks}. Plans are timed once per level
    shape when a mixed-precision context is created. BFIBM_EINVAL when the
    level does not use the TMA sweep (not allowed, or the one-pass sweep timed
    faster). No counterpart in the paper. */
-bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[4]);
+bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]);
+/* Pin the TMA sweep's plan {tile rows, planes per chunk, planes prefetched
+   (1..3), columns per strip (>= n[0]: whole rows), grid blocks (0: as many as
+   fit at once)} for the shape of one level, process-wide, in place of the
+   tuned one (for example to reuse plans tuned in another process). Takes
+   effect for step graphs captured afterwards. BFIBM_EINVAL when the level
+   does not allow the TMA sweep or the plan does not fit. No counterpart in
+   the paper. */
+bfibm_status bfibm_tma_set_plan(bfibm_ctx* c, int level, int kind, const int32_t plan[5]);
 /* Kernel launches in one replayed time step (the kernel nodes of the captured
    step graph), or -1 when no graph has been captured yet. */
 bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n);

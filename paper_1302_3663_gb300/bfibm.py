@@ -75,6 +75,7 @@ SIGNATURES = {
     "bfibm_get_field": [_V, _i, _i, _i, _DP],
     "bfibm_set_field": [_V, _i, _i, _i, _DP],
     "bfibm_tma_plan": [_V, _i, _i, _IP],
+    "bfibm_tma_set_plan": [_V, _i, _i, _IP],
     "bfibm_get_field_f32": [_V, _i, _i, _i, C.POINTER(C.c_float)],
     "bfibm_set_field_f32": [_V, _i, _i, _i, C.POINTER(C.c_float)],
     "bfibm_get_field_dev": [_V, _i, _i, _i, _V],
@@ -298,11 +299,18 @@ class Context:
                   "bfibm_set_field")
 
     def tma_plan(self, level=0, kind=0):
-        """(tile rows, planes per chunk, planes prefetched, grid) of the tuned
-        TMA sweep on a level, or None where the level does not use it."""
-        out = (C.c_int32 * 4)()
+        """(tile rows, planes per chunk, planes prefetched, strip columns, grid)
+        of the tuned TMA sweep on a level, or None where the level does not
+        use it."""
+        out = (C.c_int32 * 5)()
         st = self.lib.bfibm_tma_plan(self.h, level, kind, out)
         return tuple(out) if st == OK else None
+
+    def tma_set_plan(self, level, kind, plan):
+        """Pin (tile rows, planes per chunk, planes prefetched, strip columns,
+        grid) for the shape of a level; see bfibm_tma_set_plan."""
+        arr = (C.c_int32 * 5)(*plan)
+        self._chk(self.lib.bfibm_tma_set_plan(self.h, level, kind, arr), "bfibm_tma_set_plan")
 
     def get_field_f32(self, which, comp=0, level=0):
         out = np.empty(self.shape(level), dtype=np.float32)

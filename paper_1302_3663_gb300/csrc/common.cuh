@@ -124,10 +124,13 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
                          int* err, double coef, cudaStream_t s);
 cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K, float* out,
                           int* err, double coef, cudaStream_t s);
+// pin a plan {TY, KC, PD, SW, grid (0: resident blocks)} for a level shape
+bool tma_set_plan(int K, const Geo& g, const int in[5]);
 // whether the tuner found the TMA sweep faster than the one-pass sweep
 bool tma_chosen(int K, const Geo& g);
-// tuned plan of a level shape: tile rows, chunk planes, prefetch planes, grid
-bool tma_plan_of(int K, const Geo& g, int out[4]);
+// tuned plan of a level shape: tile rows, chunk planes, prefetch planes,
+// strip columns, grid
+bool tma_plan_of(int K, const Geo& g, int out[5]);
 
 // FP64-only grid stages.
 void launch_coef_fine(int D, const Geo& g, double* const rho[3], double* beta[3], double* m[3],

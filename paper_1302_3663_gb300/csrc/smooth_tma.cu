@@ -39,7 +39,8 @@ namespace {
 
 constexpr int kNB = 8;                  // mbarriers (planes in flight <= PD + 1 <= 4)
 constexpr int kMaxPD = 3;               // prefetch distance in planes, at most
-constexpr int kTmaThreads = 512;        // threads per block at most
+constexpr int kRing = 4;                // ring planes of red values: k-3 .. k
+constexpr int kTmaThreads = 1024;       // threads per block at most
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr size_t kSmemMax = 225 * 1024;   // dynamic, leaving room for the static words
 
@@ -48,10 +49,11 @@ constexpr size_t kSmemMax = 225 * 1024;   // dynamic, leaving room for the stati
 // e2). Pressure (kind 3): old p, rhs, beta_x, beta_y, beta_z.
 __host__ __device__ constexpr int n_staged(int K) { return K == 3 ? 5 : 8; }
 
-// Plane slots: the planes a block still reads (k-1 .. k+1 around the red
-// plane k; k-2 as well for the z component, whose stencil reaches one plane
-// below the point) plus the PD planes in flight.
-__host__ __device__ constexpr int win(int K, int PD) { return (K == 2 ? 4 : 3) + PD; }
+// Plane slots: the planes a block still reads at iteration k (k-2 .. k+1:
+// the red plane k with its neighbours and the black plane k-2 with its
+// neighbours; k-3 as well for the z component, whose stencil reaches one
+// plane below the point) plus the PD planes in flight.
+__host__ __device__ constexpr int win(int K, int PD) { return (K == 2 ? 5 : 4) + PD; }
 __host__ __device__ constexpr int total_slots(int K, int PD) { return win(K, PD) * n_staged(K); }
 
 struct TmaArgs {
@@ -59,10 +61,11 @@ struct TmaArgs {
   Geo g;
   float* out;
   int* err;
-  int TY, KC, nrt, items, pitch;
+  int TY, KC, nrt, ns, items;
+  int SW, BW, RW;        // strip columns, box columns (SW + 8), ring row floats
   int PD;                // planes issued ahead of the red plane's last need
   int tile;              // floats between array tiles (multiple of 32)
-  unsigned box_bytes;    // bytes of one box: (TY + 4) rows of pitch floats
+  unsigned box_bytes;    // bytes of one box: (TY + 4) rows of BW floats
   float c;               // viscous: inv_re / h^2; pressure: h^2
 };
 
@@ -130,8 +133,10 @@ __host__ __device__ constexpr int edge_id(int d, int e) {
 
 // ------------------------------------------------------------------ kernel
 // Shared memory: W plane slots, each holding one tile per staged array
-// (tile = TY + 4 rows of pitch floats); then the three-plane ring; then the
-// mbarriers. Plane p of a chunk lives in slot (p - pbase) % W.
+// (tile = TY + 4 rows of BW = SW + 8 floats: the strip's columns with four
+// halo columns each side); then the three-plane ring of red values (TY + 2
+// rows of RW floats, column c holding x = xs - 1 + c); then the mbarriers.
+// Plane p of a chunk lives in slot (p - pbase) % W.
 template <int K>
 __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ TmaArgs A) {
   constexpr int NS = n_staged(K);
@@ -139,63 +144,86 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ int abort_flag;
   const Geo& g = A.g;
-  const int TY = A.TY, pitch = A.pitch, tile = A.tile;
+  const int TY = A.TY, BW = A.BW, RW = A.RW, SW = A.SW, tile = A.tile;
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const bool per0 = g.per[0] != 0, per2 = g.per[2] != 0;
   const long long st1 = g.st[1], st2 = g.st[2];
   float* tiles = reinterpret_cast<float*>(sm);
   float* ring = tiles + (size_t)W * NS * tile;
-  const int ringplane = (TY + 2) * pitch;
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(ring + 3 * ringplane);
+  const int ringplane = (TY + 2) * RW;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(ring + kRing * ringplane);
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int q = tid; q < 3 * ringplane; q += nthr) ring[q] = 0.f;
+  for (int q = tid; q < kRing * ringplane; q += nthr) ring[q] = 0.f;
   if (tid == 0) {
     abort_flag = 0;
     for (int b = 0; b < kNB; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const int npairs = (n0 + 1) / 2;
   const float c = A.c;
+  // this thread's red item (row r of TY + 2, pair q of SW / 2 + 2, the first
+  // one left of the strip) and black item (row r of TY, pair q of SW / 2)
+  const int rpairs = SW / 2 + 2, bpairs = SW / 2;
+  const bool has_red = tid < (TY + 2) * rpairs, has_blk = tid < TY * bpairs;
+  const int r_red = tid / rpairs, q_red = tid - r_red * rpairs;
+  const int r_blk = tid / bpairs, q_blk = tid - r_blk * bpairs;
   unsigned seq = 0, waited = 0;   // planes issued / waited for by this block
 
   for (int item = blockIdx.x; item < A.items; item += gridDim.x) {
-    const int t = item % A.nrt, ch = item / A.nrt;
-    const int j0 = t * TY, k0 = ch * A.KC, k1 = min(k0 + A.KC, n2);
+    const int strip = item % A.ns, rest = item / A.ns;
+    const int t = rest % A.nrt, ch = rest / A.nrt;
+    const int xs = strip * SW, j0 = t * TY, k0 = ch * A.KC, k1 = min(k0 + A.KC, n2);
     const int pbase = k0 - 2;   // plane in slot 0 at the start of the chunk
     const unsigned sbase = seq;
-    auto plane_tiles = [&](int p) -> float* { return tiles + (size_t)((p - pbase) % W) * NS * tile; };
-    auto ring_plane = [&](int p) -> float* { return ring + ((p - pbase) % 3) * ringplane; };
-    if (tid == 0) {
-      for (int p = pbase; p <= min(pbase + 1 + PD, k1 + 1); ++p) {
-        unsigned long long* b = &bar[(sbase + (unsigned)(p - pbase)) % kNB];
-        mbar_expect_tx(b, (unsigned)NS * A.box_bytes);
-        int z = per2 ? wrapi(p, n2) : p;
-        float* dst = plane_tiles(p);
+    auto plane_tiles = [&](int p) -> float* {
+      return tiles + (size_t)((p - pbase) % W) * NS * tile;
+    };
+    auto issue = [&](int p) {   // one thread: plane p of every staged array
+      unsigned long long* b = &bar[(sbase + (unsigned)(p - pbase)) % kNB];
+      fence_proxy_async();
+      mbar_expect_tx(b, (unsigned)NS * A.box_bytes);
+      int z = per2 ? wrapi(p, n2) : p;
+      float* dst = plane_tiles(p);
 #pragma unroll
-        for (int a = 0; a < NS; ++a) tma_load_3d(dst + a * tile, &A.map[a], b, 0, j0 - 2, z);
-      }
-    }
-    seq += (unsigned)(min(pbase + 1 + PD, k1 + 1) - pbase + 1);
+      for (int a = 0; a < NS; ++a)
+        tma_load_3d(dst + a * tile, &A.map[a], b, xs - 4, j0 - 2, z);
+    };
+    const int last0 = min(pbase + 1 + PD, k1 + 1);
+    if (tid == 0)
+      for (int p = pbase; p <= last0; ++p) issue(p);
+    seq += (unsigned)(last0 - pbase + 1);
 
-    // One point update of the plane whose tiles are P0 (neighbours Pm, Pp)
-    // at tile offset o; x neighbours at o + dxp / o + dxm. BLACK takes the
-    // u_d (or p) neighbours from the ring (planes Rm, R0, Rp at ring offset
-    // ro, x neighbours at ro + rxp / ro + rxm), red from the staged old
-    // values. Same operation order as the two-kernel sweep.
-    auto update = [&](auto black_tag, const float* Pm, const float* P0, const float* Pp, int o,
-                      int dxp, int dxm, const float* Rm, const float* R0, const float* Rp,
-                      int ro, int rxp, int rxm, const bool* wm, const bool* wp) -> float {
+    // One point update. P0 (Pm, Pp) are the tiles of the point's plane (and
+    // of the planes below and above), o its offset in a tile, dxp / dxm the
+    // offsets of its x neighbours; BLACK reads the iterate's neighbours from
+    // the ring (planes Rm, R0, Rp; offset ro; x neighbours at ro + rxp /
+    // ro + rxm), red from the staged old values. INTERIOR: no neighbour lies
+    // beyond a wall or across a periodic seam, so every flag is false and
+    // every x offset is +-1 (the same arithmetic with the branches removed).
+    auto update = [&](auto black_tag, auto interior_tag, const float* Pm, const float* P0,
+                      const float* Pp, int o, int dxp, int dxm, const float* Rm,
+                      const float* R0, const float* Rp, int ro, int rxp, int rxm,
+                      const bool* wmv, const bool* wpv) -> float {
       constexpr bool BLACK = decltype(black_tag)::value;
-      // neighbour of the iterate (array 0) along axis ax, side +-1
-      auto nb = [&](int ax, int side) -> float {
+      constexpr bool INTERIOR = decltype(interior_tag)::value;
+      auto wm = [&](int a) -> bool {
+        if constexpr (INTERIOR) return false;
+        else return wmv[a];
+      };
+      auto wp = [&](int a) -> bool {
+        if constexpr (INTERIOR) return false;
+        else return wpv[a];
+      };
+      const int xp = INTERIOR ? 1 : dxp, xm = INTERIOR ? -1 : dxm;
+      const int rp = INTERIOR ? 1 : rxp, rm = INTERIOR ? -1 : rxm;
+      auto nb = [&](int ax, int side) -> float {   // neighbour of the iterate (array 0)
         if constexpr (BLACK) {
-          if (ax == 0) return R0[ro + (side > 0 ? rxp : rxm)];
-          if (ax == 1) return R0[ro + side * pitch];
+          if (ax == 0) return R0[ro + (side > 0 ? rp : rm)];
+          if (ax == 1) return R0[ro + side * RW];
           return (side > 0 ? Rp : Rm)[ro];
         } else {
-          if (ax == 0) return P0[o + (side > 0 ? dxp : dxm)];
-          if (ax == 1) return P0[o + side * pitch];
+          if (ax == 0) return P0[o + (side > 0 ? xp : xm)];
+          if (ax == 1) return P0[o + side * BW];
           return (side > 0 ? Pp : Pm)[o];
         }
       };
@@ -204,13 +232,13 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
         const float* P = P0;
         int off = o + a * tile;
         if (s1 != 0) {
-          if (ax1 == 0) off += s1 > 0 ? dxp : dxm;
-          else if (ax1 == 1) off += s1 * pitch;
+          if (ax1 == 0) off += s1 > 0 ? xp : xm;
+          else if (ax1 == 1) off += s1 * BW;
           else P = s1 > 0 ? Pp : Pm;
         }
         if (s2 != 0) {
-          if (ax2 == 0) off += s2 > 0 ? dxp : dxm;
-          else if (ax2 == 1) off += s2 * pitch;
+          if (ax2 == 0) off += s2 > 0 ? xp : xm;
+          else if (ax2 == 1) off += s2 * BW;
           else P = s2 > 0 ? Pp : Pm;
         }
         return P[off];
@@ -220,12 +248,12 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
         float num = 0.f, dg = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          if (!wm[a]) {
+          if (!wm(a)) {
             float bb = at(2 + a);
             num += bb * nb(a, -1);
             dg += bb;
           }
-          if (!wp[a]) {
+          if (!wp(a)) {
             float bb = sh(2 + a, a, +1, 0, 0);
             num += bb * nb(a, +1);
             dg += bb;
@@ -249,15 +277,15 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
                    mem * (at(ue) - sh(ue, d, -1, 0, 0));
           cep[q] = mep;
           cem[q] = mem;
-          dgV += (wp[e] ? 2.f : 1.f) * mep + (wm[e] ? 2.f : 1.f) * mem;
+          dgV += (wp(e) ? 2.f : 1.f) * mep + (wm(e) ? 2.f : 1.f) * mem;
         }
         float diag = at(2) + c * dgV;
         float off = cross + cdp * nb(d, +1) + cdm * nb(d, -1);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int e = q == 0 ? e1 : e2;
-          if (!wp[e]) off += cep[q] * nb(e, +1);
-          if (!wm[e]) off += cem[q] * nb(e, -1);
+          if (!wp(e)) off += cep[q] * nb(e, +1);
+          if (!wm(e)) off += cem[q] * nb(e, -1);
         }
         return (at(1) + c * off) / diag;
       }
@@ -268,33 +296,45 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
       else if constexpr (K == 2) return !per2 && kw == 0;
       return false;
     };
-    // tile offsets of the x neighbours (periodic wrap; beyond a wall: the
-    // stored wall face or an unused slot)
-    auto xdeltas = [&](int i, int& dxp, int& dxm) {
-      dxp = (i == n0 - 1 && per0) ? -(n0 - 1) : 1;
-      dxm = (i == 0 && per0) ? (n0 - 1) : -1;
-    };
-    auto rdeltas = [&](int i, int& rxp, int& rxm) {   // as the ring-fused sweep wraps
-      rxp = (i == n0 - 1 && per0) ? -(n0 - 1) : 1;
-      rxm = (i == 0) ? (n0 - 1) : -1;
+    // the point update with the flags and offsets of (i, j, kw)
+    auto point = [&](auto black_tag, const float* Pm, const float* P0, const float* Pp,
+                     const float* Rm, const float* R0, const float* Rp, int i, int j, int kw,
+                     int o, int ro) -> float {
+      const bool xin = i > 0 && i < n0 - 1;
+      const bool zin = per2 || (kw > 0 && kw < n2 - 1);
+      if (xin && j > 0 && j < n1 - 1 && zin)
+        return update(black_tag, std::integral_constant<bool, true>{}, Pm, P0, Pp, o, 1, -1, Rm,
+                      R0, Rp, ro, 1, -1, nullptr, nullptr);
+      const bool wmv[3] = {!per0 && i == 0, j == 0, !per2 && kw == 0};
+      const bool wpv[3] = {!per0 && i == n0 - 1, j == n1 - 1, !per2 && kw == n2 - 1};
+      const int dxp = (i == n0 - 1 && per0) ? -(n0 - 1) : 1;
+      const int dxm = (i == 0 && per0) ? (n0 - 1) : -1;
+      const int rxp = (i == n0 - 1 && per0) ? -(n0 - 1) : 1;
+      const int rxm = (i == 0 && per0) ? (n0 - 1) : -1;
+      return update(black_tag, std::integral_constant<bool, false>{}, Pm, P0, Pp, o, dxp, dxm,
+                    Rm, R0, Rp, ro, rxp, rxm, wmv, wpv);
     };
 
-    for (int k = k0 - 1; k <= k1; ++k) {
+    // One phase per plane: the red values of plane k and the black values of
+    // plane k - 2 (whose red neighbours, planes k - 3 .. k - 1, are complete)
+    // are independent, so each thread runs both updates between two barriers.
+    // Tile slots of the planes k - 3 .. k + 1, ring slots of k - 3 .. k and the
+    // wrapped index of plane k advance by one plane per iteration.
+    int sM3 = W - 2, sM2 = W - 1, sM1 = 0, s0 = 1, sP1 = 2;
+    int rM3 = 2, rM2 = 3, rM1 = 0, r0 = 1;
+    int kw = per2 ? wrapi(k0 - 1, n2) : k0 - 1;
+    const int j_red = j0 - 1 + r_red, j_blk = j0 + r_blk;
+    const bool row_red = has_red && j_red >= 0 && j_red < n1;
+    const int i0_red = xs - 2 + 2 * q_red, i0_blk = xs + 2 * q_blk;
+    const bool row_blk = has_blk && j_blk < n1 && i0_blk < n0;
+    const size_t plane_floats = (size_t)NS * tile;
+    for (int k = k0 - 1; k <= k1 + 1; ++k) {
       if (k + 1 + PD <= k1 + 1) {
-        if (tid == 0) {
-          const int p = k + 1 + PD;
-          unsigned long long* b = &bar[(sbase + (unsigned)(p - pbase)) % kNB];
-          fence_proxy_async();
-          mbar_expect_tx(b, (unsigned)NS * A.box_bytes);
-          int z = per2 ? wrapi(p, n2) : p;
-          float* dst = plane_tiles(p);
-#pragma unroll
-          for (int a = 0; a < NS; ++a) tma_load_3d(dst + a * tile, &A.map[a], b, 0, j0 - 2, z);
-        }
+        if (tid == 0) issue(k + 1 + PD);
         ++seq;
       }
       bool ok = true;
-      const unsigned need = sbase + (unsigned)(k + 1 - pbase);   // plane k + 1
+      const unsigned need = sbase + (unsigned)(min(k + 1, k1 + 1) - pbase);
       while (waited <= need) {
         ok = ok && wait_seq(bar, waited, kWaitNs);
         ++waited;
@@ -303,73 +343,58 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
         abort_flag = 1;
         atomicExch(A.err, 1);
       }
-      // red values of plane k on the rows j0 - 1 .. j0 + TY
-      {
+      // red values of plane k on the rows j0 - 1 .. j0 + TY and the columns
+      // xs - 1 .. xs + SW; zeros where the point does not exist
+      if (has_red && k <= k1) {
         const bool planevalid = per2 || (k >= 0 && k < n2);
-        const int kw = per2 ? wrapi(k, n2) : k;
-        const float* Pm = plane_tiles(k - 1);
-        const float* P0 = plane_tiles(k);
-        const float* Pp = plane_tiles(k + 1);
-        float* R0 = ring_plane(k);
-        for (int q = tid; q < (TY + 2) * npairs; q += nthr) {
-          const int r = q / npairs, ip = q - r * npairs;
-          const int j = j0 - 1 + r;
-          float* row = R0 + r * pitch;
-          if (!(planevalid && j >= 0 && j < n1)) {
-            row[2 * ip] = 0.f;
-            if (2 * ip + 1 < n0) row[2 * ip + 1] = 0.f;
-            continue;
+        float* row = ring + r0 * ringplane + r_red * RW;
+        if (!(planevalid && row_red)) {
+          if (i0_red >= xs - 1) row[i0_red - xs + 1] = 0.f;
+          if (i0_red + 1 <= xs + SW) row[i0_red - xs + 2] = 0.f;
+        } else {
+          const int i = i0_red + ((j_red + kw) & 1);
+          if (i >= xs - 1 && i <= xs + SW) {
+            float v = 0.f;
+            if (i >= 0 && i < n0 && !on_wall_face(i, j_red, kw))
+              v = point(std::integral_constant<bool, false>{}, tiles + sM1 * plane_floats,
+                        tiles + s0 * plane_floats, tiles + sP1 * plane_floats, nullptr, nullptr,
+                        nullptr, i, j_red, kw, (r_red + 1) * BW + (i - xs + 4), 0);
+            row[i - xs + 1] = v;
           }
-          const int i = 2 * ip + ((j + kw) & 1);
-          if (i >= n0) continue;
+        }
+      }
+      // black values of plane k - 2 on the block's rows and columns; both
+      // colours out
+      const int kb = k - 2;
+      if (kb >= k0 && row_blk) {
+        const int par = (j_blk + kb) & 1;
+        const int ir = i0_blk + par, ib = i0_blk + (par ^ 1);
+        float* o = A.out + st1 * j_blk + st2 * kb;
+        const float* RB = ring + rM2 * ringplane;
+        const int rrow = (r_blk + 1) * RW;
+        if (ir < n0) o[ir] = RB[rrow + ir - xs + 1];
+        if (ib < n0) {
           float v = 0.f;
-          if (!on_wall_face(i, j, kw)) {
-            const bool wm[3] = {!per0 && i == 0, j == 0, !per2 && kw == 0};
-            const bool wp[3] = {!per0 && i == n0 - 1, j == n1 - 1, !per2 && kw == n2 - 1};
-            int dxp, dxm;
-            xdeltas(i, dxp, dxm);
-            v = update(std::integral_constant<bool, false>{}, Pm, P0, Pp, (r + 1) * pitch + i,
-                       dxp, dxm, nullptr, nullptr, nullptr, 0, 0, 0, wm, wp);
-          }
-          row[i] = v;
+          if (!on_wall_face(ib, j_blk, kb))
+            v = point(std::integral_constant<bool, true>{}, tiles + sM3 * plane_floats,
+                      tiles + sM2 * plane_floats, tiles + sM1 * plane_floats,
+                      ring + rM3 * ringplane, RB, ring + rM1 * ringplane, ib, j_blk, kb,
+                      (r_blk + 2) * BW + (ib - xs + 4), rrow + ib - xs + 1);
+          o[ib] = v;
         }
       }
       __syncthreads();
       if (abort_flag) break;
-      // black values of plane k - 1 on the block's own rows; both colours out
-      const int kb = k - 1;
-      if (kb >= k0) {
-        const float* Pm = plane_tiles(kb - 1);
-        const float* P0 = plane_tiles(kb);
-        const float* Pp = plane_tiles(kb + 1);
-        const float* Rm = ring_plane(kb - 1);
-        const float* R0 = ring_plane(kb);
-        const float* Rp = ring_plane(kb + 1);
-        for (int q = tid; q < TY * npairs; q += nthr) {
-          const int r = q / npairs, ip = q - r * npairs;
-          const int j = j0 + r;
-          if (j >= n1) continue;
-          const int par = (j + kb) & 1;
-          const int ir = 2 * ip + par, ib = 2 * ip + (par ^ 1);
-          float* o = A.out + st1 * j + st2 * kb;
-          const int rrow = (r + 1) * pitch;
-          if (ir < n0) o[ir] = R0[rrow + ir];
-          if (ib < n0) {
-            float v = 0.f;
-            if (!on_wall_face(ib, j, kb)) {
-              const bool wm[3] = {!per0 && ib == 0, j == 0, !per2 && kb == 0};
-              const bool wp[3] = {!per0 && ib == n0 - 1, j == n1 - 1, !per2 && kb == n2 - 1};
-              int dxp, dxm, rxp, rxm;
-              xdeltas(ib, dxp, dxm);
-              rdeltas(ib, rxp, rxm);
-              v = update(std::integral_constant<bool, true>{}, Pm, P0, Pp, (r + 2) * pitch + ib,
-                         dxp, dxm, Rm, R0, Rp, rrow + ib, rxp, rxm, wm, wp);
-            }
-            o[ib] = v;
-          }
-        }
-      }
-      __syncthreads();
+      sM3 = sM2;
+      sM2 = sM1;
+      sM1 = s0;
+      s0 = sP1;
+      sP1 = (sP1 + 1 == W) ? 0 : sP1 + 1;
+      rM3 = rM2;
+      rM2 = rM1;
+      rM1 = r0;
+      r0 = (r0 + 1 == kRing) ? 0 : r0 + 1;
+      kw = (per2 && kw + 1 == n2) ? 0 : kw + 1;
     }
     if (abort_flag) break;
   }
@@ -400,12 +425,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor maps are pure host descriptors: cached by (address, geometry, rows).
-using MapKey = std::tuple<const void*, long long, int, int, int>;
+using MapKey = std::tuple<const void*, long long, int, int, int, int>;
 std::mutex g_map_mu;
 std::map<MapKey, CUtensorMap> g_maps;
 
-bool make_map(const Geo& g, const float* base, int TY, CUtensorMap* out) {
-  MapKey key{base, g.st[1], g.s[1], g.s[2], TY};
+bool make_map(const Geo& g, const float* base, int TY, int BW, CUtensorMap* out) {
+  MapKey key{base, g.st[1], g.s[1], g.s[2], TY, BW};
   std::lock_guard<std::mutex> lock(g_map_mu);
   auto it = g_maps.find(key);
   if (it != g_maps.end()) {
@@ -416,7 +441,7 @@ bool make_map(const Geo& g, const float* base, int TY, CUtensorMap* out) {
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)g.st[1], (cuuint64_t)g.s[1], (cuuint64_t)g.s[2]};
   cuuint64_t strides[2] = {(cuuint64_t)g.st[1] * 4, (cuuint64_t)g.st[2] * 4};
-  cuuint32_t box[3] = {(cuuint32_t)g.st[1], (cuuint32_t)(TY + 4), 1};
+  cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)(TY + 4), 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUtensorMap m;
   CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
@@ -429,21 +454,35 @@ bool make_map(const Geo& g, const float* base, int TY, CUtensorMap* out) {
   return true;
 }
 
-int tile_of(const Geo& g, int TY) {   // floats, rounded to 128 bytes
-  int f = (int)((TY + 4) * g.st[1]);
+// strip geometry: SW columns per strip (a multiple of 4; a whole row when
+// SW >= n0), boxes of BW = SW + 8 columns, ring rows of RW floats
+int full_strip(const Geo& g) { return (g.n[0] + 3) / 4 * 4; }
+int box_cols(int SW) { return SW + 8; }
+int ring_cols(int SW) { return SW + 4; }
+
+int tile_of(int TY, int SW) {   // floats, rounded to 128 bytes
+  int f = (TY + 4) * box_cols(SW);
   return (f + 31) / 32 * 32;
 }
 
-size_t smem_of(int K, const Geo& g, int TY, int PD) {
-  return (size_t)total_slots(K, PD) * tile_of(g, TY) * 4 + (size_t)3 * (TY + 2) * g.st[1] * 4 +
-         kNB * 8;
+size_t smem_of(int K, int TY, int PD, int SW) {
+  return (size_t)total_slots(K, PD) * tile_of(TY, SW) * 4 +
+         (size_t)kRing * (TY + 2) * ring_cols(SW) * 4 + kNB * 8;
 }
 
-int threads_of(const Geo& g, int TY) {
-  int npairs = (g.n[0] + 1) / 2;
-  int t = (TY + 2) * npairs;
-  if (t > kTmaThreads) t = kTmaThreads;
+int threads_of(int TY, int SW) {
+  int red = (TY + 2) * (SW / 2 + 2), blk = TY * (SW / 2);
+  int t = red > blk ? red : blk;
   return (t + 31) / 32 * 32;
+}
+
+// a plan the kernel can run: one item per thread, boxes within TMA limits,
+// shared memory within the limit, strips only where x has walls
+bool plan_fits(int K, const Geo& g, int TY, int PD, int SW) {
+  if (TY < 1 || TY + 4 > 256 || box_cols(SW) > 256 || SW % 4) return false;
+  if (SW < g.n[0] && g.per[0]) return false;
+  if (threads_of(TY, SW) > kTmaThreads) return false;
+  return smem_of(K, TY, PD, SW) <= kSmemMax;
 }
 
 const void* kernel_of(int K) {
@@ -456,7 +495,7 @@ const void* kernel_of(int K) {
 }
 
 struct Plan {
-  int TY = 4, KC = 16, PD = 1, grid = 0;
+  int TY = 4, KC = 16, PD = 1, SW = 0, grid = 0;
   bool tma = false;    // the TMA sweep timed faster than the one-pass global-memory sweep
 };
 
@@ -484,7 +523,8 @@ int sm_count() {
 
 // Fill the launch arguments for kind K with tile height TY and chunk KC.
 bool fill_args(int K, const Geo& g, const LevelPtrs<float>& L, float* out, int* err,
-               double coef, int TY, int KC, int PD, TmaArgs& A) {
+               double coef, int TY, int KC, int PD, int SW, TmaArgs& A) {
+  if (SW >= g.n[0]) SW = full_strip(g);
   std::memset(&A, 0, sizeof(A));
   const float* src[8] = {nullptr};
   if (K == 3) {
@@ -503,7 +543,7 @@ bool fill_args(int K, const Geo& g, const LevelPtrs<float>& L, float* out, int* 
     src[7] = L.u[e2];
   }
   for (int a = 0; a < n_staged(K); ++a)
-    if (!src[a] || !make_map(g, src[a], TY, &A.map[a])) return false;
+    if (!src[a] || !make_map(g, src[a], TY, box_cols(SW), &A.map[a])) return false;
   A.g = g;
   A.out = out;
   A.err = err;
@@ -511,17 +551,20 @@ bool fill_args(int K, const Geo& g, const LevelPtrs<float>& L, float* out, int* 
   A.KC = KC;
   A.PD = PD;
   A.nrt = (g.n[1] + TY - 1) / TY;
-  A.items = A.nrt * ((g.n[2] + KC - 1) / KC);
-  A.pitch = (int)g.st[1];
-  A.tile = tile_of(g, TY);
-  A.box_bytes = (unsigned)((TY + 4) * g.st[1] * 4);
+  A.ns = (g.n[0] + SW - 1) / SW;
+  A.items = A.ns * A.nrt * ((g.n[2] + KC - 1) / KC);
+  A.SW = SW;
+  A.BW = box_cols(SW);
+  A.RW = ring_cols(SW);
+  A.tile = tile_of(TY, SW);
+  A.box_bytes = (unsigned)((TY + 4) * A.BW * 4);
   A.c = (float)coef;
   return true;
 }
 
-cudaError_t launch_args(int K, const Geo& g, const TmaArgs& A, int grid, cudaStream_t s) {
-  size_t smem = smem_of(K, g, A.TY, A.PD);
-  dim3 blk(threads_of(g, A.TY));
+cudaError_t launch_args(int K, const TmaArgs& A, int grid, cudaStream_t s) {
+  size_t smem = smem_of(K, A.TY, A.PD, A.SW);
+  dim3 blk(threads_of(A.TY, A.SW));
   switch (K) {
     case 0: k_rb_tma<0><<<grid, blk, smem, s>>>(A); break;
     case 1: k_rb_tma<1><<<grid, blk, smem, s>>>(A); break;
@@ -531,10 +574,10 @@ cudaError_t launch_args(int K, const Geo& g, const TmaArgs& A, int grid, cudaStr
   return cudaGetLastError();
 }
 
-int resident_grid(int K, const Geo& g, int TY, int PD, int items) {
+int resident_grid(int K, int TY, int PD, int SW, int items) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of(K), threads_of(g, TY),
-                                                    smem_of(K, g, TY, PD)) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of(K), threads_of(TY, SW),
+                                                    smem_of(K, TY, PD, SW)) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -547,10 +590,11 @@ int resident_grid(int K, const Geo& g, int TY, int PD, int items) {
 
 bool tma_eligible(int D, const Geo& g) {
   if (D != 3 || g.per[1]) return false;
-  if (g.st[1] > 256 || g.n[0] < 8 || g.n[1] < 2 || g.n[2] < 2) return false;
+  if (g.n[0] < 8 || g.n[1] < 2 || g.n[2] < 2) return false;
   if ((long long)g.n[0] * g.n[1] * g.n[2] < 32768) return false;
+  const int SW = g.per[0] ? full_strip(g) : (g.n[0] > 64 ? 64 : full_strip(g));
   for (int K = 0; K < 4; ++K)
-    if (smem_of(K, g, 2, 1) > kSmemMax) return false;
+    if (!plan_fits(K, g, 2, 1, SW)) return false;
   return encode_fn() != nullptr;
 }
 
@@ -598,19 +642,22 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
   }
   const int tys[] = {2, 4, 6, 8};
   const int kcs[] = {16, 32, 64};
+  const int sws[] = {64, full_strip(g)};
+  for (int SW : sws) {
+  if (SW == 64 && g.n[0] <= 64) continue;
   for (int TY : tys) {
     if (TY > g.n[1]) continue;
     for (int PD = 1; PD <= kMaxPD; ++PD) {
-    if (smem_of(K, g, TY, PD) > kSmemMax) continue;
+    if (!plan_fits(K, g, TY, PD, SW)) continue;
     for (int KC : kcs) {
       if (KC > g.n[2] && KC != kcs[0]) continue;
       TmaArgs A;
-      if (!fill_args(K, g, L, out, err, coef, TY, KC, PD, A)) continue;
-      int grid = resident_grid(K, g, TY, PD, A.items);
-      status = launch_args(K, g, A, grid, s);
+      if (!fill_args(K, g, L, out, err, coef, TY, KC, PD, SW, A)) continue;
+      int grid = resident_grid(K, TY, PD, A.SW, A.items);
+      status = launch_args(K, A, grid, s);
       if (status != cudaSuccess) break;
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) launch_args(K, g, A, grid, s);
+      for (int r = 0; r < 3; ++r) launch_args(K, A, grid, s);
       cudaEventRecord(e1, s);
       status = cudaEventSynchronize(e1);
       if (status != cudaSuccess) break;
@@ -622,12 +669,15 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
         best.TY = TY;
         best.KC = KC;
         best.PD = PD;
+        best.SW = A.SW;
         best.grid = grid;
       }
     }
     if (status != cudaSuccess) break;
     }
     if (status != cudaSuccess) break;
+  }
+  if (status != cudaSuccess) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -650,12 +700,29 @@ cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K,
     auto it = g_plans.find(plan_key(K, g));
     if (it != g_plans.end()) pl = it->second;
   }
+  if (pl.SW <= 0) pl.SW = (g.per[0] || g.n[0] <= 64) ? full_strip(g) : 64;
   if (pl.TY > g.n[1]) pl.TY = g.n[1];
-  while (pl.TY > 2 && smem_of(K, g, pl.TY, pl.PD) > kSmemMax) --pl.TY;
+  while (pl.TY > 2 && !plan_fits(K, g, pl.TY, pl.PD, pl.SW)) --pl.TY;
   TmaArgs A;
-  if (!fill_args(K, g, L, out, err, coef, pl.TY, pl.KC, pl.PD, A)) return cudaErrorInvalidValue;
-  int grid = pl.grid > 0 ? pl.grid : resident_grid(K, g, pl.TY, pl.PD, A.items);
-  return launch_args(K, g, A, grid, s);
+  if (!fill_args(K, g, L, out, err, coef, pl.TY, pl.KC, pl.PD, pl.SW, A))
+    return cudaErrorInvalidValue;
+  int grid = pl.grid > 0 ? pl.grid : resident_grid(K, pl.TY, pl.PD, A.SW, A.items);
+  return launch_args(K, A, grid, s);
+}
+
+bool tma_set_plan(int K, const Geo& g, const int in[5]) {
+  Plan pl;
+  pl.tma = true;
+  pl.TY = in[0];
+  pl.KC = in[1];
+  pl.PD = in[2];
+  pl.SW = in[3] >= g.n[0] ? full_strip(g) : in[3];
+  pl.grid = in[4];
+  if (pl.KC < 1 || pl.PD < 1 || pl.PD > kMaxPD || pl.grid < 0 || !plan_fits(K, g, pl.TY, pl.PD, pl.SW))
+    return false;
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  g_plans[plan_key(K, g)] = pl;
+  return true;
 }
 
 bool tma_chosen(int K, const Geo& g) {
@@ -664,14 +731,15 @@ bool tma_chosen(int K, const Geo& g) {
   return it != g_plans.end() && it->second.tma;
 }
 
-bool tma_plan_of(int K, const Geo& g, int out[4]) {
+bool tma_plan_of(int K, const Geo& g, int out[5]) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   auto it = g_plans.find(plan_key(K, g));
   if (it == g_plans.end() || !it->second.tma) return false;
   out[0] = it->second.TY;
   out[1] = it->second.KC;
   out[2] = it->second.PD;
-  out[3] = it->second.grid;
+  out[3] = it->second.SW;
+  out[4] = it->second.grid;
   return true;
 }
 

@@ -1450,14 +1450,24 @@ bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n) {
   return BFIBM_OK;
 }
 
-bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[4]) {
+bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]) {
   READY(c);
   if (!out || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
       (kind < 3 && kind >= c->D) || c->P.precision != 1 || !use_tma(c, level))
     return set_err(c, BFIBM_EINVAL, "no TMA sweep on this level");
-  int v[4];
+  int v[5];
   if (!tma_plan_of(kind, c->lev[level].g, v)) return set_err(c, BFIBM_EINVAL, "level not tuned");
-  for (int q = 0; q < 4; ++q) out[q] = v[q];
+  for (int q = 0; q < 5; ++q) out[q] = v[q];
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_tma_set_plan(bfibm_ctx* c, int level, int kind, const int32_t plan[5]) {
+  READY(c);
+  if (!plan || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
+      (kind < 3 && kind >= c->D) || !tma_eligible(c->D, c->lev[level].g))
+    return set_err(c, BFIBM_EINVAL, "no TMA sweep on this level");
+  int v[5] = {plan[0], plan[1], plan[2], plan[3], plan[4]};
+  if (!tma_set_plan(kind, c->lev[level].g, v)) return set_err(c, BFIBM_EINVAL, "plan does not fit");
   return BFIBM_OK;
 }
 
