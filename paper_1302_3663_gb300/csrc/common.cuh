@@ -97,7 +97,11 @@ int red_blocks_3d(int D, const Geo& g);
 void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* r32,
                              float* e32, double* partial, cudaStream_t s);
 void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
-                             float* const e32[3], double inv_re, double* partial, cudaStream_t s);
+                             float* const e32[3], double* const diag[3], double inv_re,
+                             double* partial, cudaStream_t s);
+// diagonal of the FP64 viscous operator on one level (formed once per step)
+void launch_v_diag(int D, const Geo& g, const LevelPtrs<double>& L, double* const diag[3],
+                   double inv_re, cudaStream_t s);
 void launch_add_correction(int D, const Geo& g, double* const x[3], float* const e[3], int ncomp,
                            cudaStream_t s);
 void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);

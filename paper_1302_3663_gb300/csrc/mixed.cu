@@ -90,45 +90,106 @@ __global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<doubl
   }
 }
 
-// FP64 viscous residual of component d at face F (same arithmetic as the
-// FP64 residual kernel)
+// Diagonal of the FP64 viscous operator of component d at face F:
+// m_d + (inv_re / h^2) * (2 mu_c on both cells + the edge viscosities, an edge
+// beyond a wall counted twice for the mirrored tangential neighbour). The
+// coefficients stay fixed through a time step's solves, so the diagonal is
+// formed once per step instead of in every defect-correction cycle.
 template <int D, int d>
-__device__ __forceinline__ double v_res64(const Geo& g, const LevelPtrs<double>& L,
-                                          const int ci[3], long long F, double ir) {
-  const double* __restrict__ ud = L.u[d];
-  long long od_p = offp(g, d, ci[d]);
+__device__ __forceinline__ double v_diag64(const Geo& g, const LevelPtrs<double>& L,
+                                           const int ci[3], long long F, double ir) {
   long long od_m = offm(g, d, ci[d]);
   double mcp = L.muc[F], mcm = L.muc[F + od_m];
-  double off = 2.0 * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
   double dgV = 2.0 * (mcp + mcm);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (e == d) continue;
+    const double* __restrict__ me = L.mue[edge_id(d, e)];
+    bool pe = g.per[e] != 0;
+    bool wp = !pe && ci[e] == g.n[e] - 1;
+    bool wm = !pe && ci[e] == 0;
+    double mep = me[F + offp(g, e, ci[e])], mem = me[F];
+    dgV += (wp ? 2.0 : 1.0) * mep + (wm ? 2.0 : 1.0) * mem;
+  }
+  return L.m[d][F] + ir * dgV;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_v_diag(Geo g, LevelPtrs<double> L, Ptr3d diag,
+                                                double ir) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long F = gidx(g, i, j, k);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    double v = 0.0;
+    if (g.per[d] || ci[d] != 0) {
+      if (d == 0) v = v_diag64<D, 0>(g, L, ci, F, ir);
+      else if (d == 1) v = v_diag64<D, 1>(g, L, ci, F, ir);
+      else v = v_diag64<D, (D == 3 ? 2 : 1)>(g, L, ci, F, ir);
+    }
+    diag.a[d][F] = v;
+  }
+}
+
+// FP64 viscous residual of component d at face F with the diagonal read from
+// `diag` (the same arithmetic as the FP64 residual kernel). INTERIOR: no
+// neighbour lies beyond a wall or across a periodic seam, so the offsets are
+// the plain strides and no flag is tested.
+template <int D, int d, bool INTERIOR>
+__device__ __forceinline__ double v_res64d(const Geo& g, const LevelPtrs<double>& L,
+                                           const double* __restrict__ diag, const int ci[3],
+                                           long long F, double ir) {
+  const double* __restrict__ ud = L.u[d];
+  const long long od_p = INTERIOR ? g.st[d] : offp(g, d, ci[d]);
+  const long long od_m = INTERIOR ? -g.st[d] : offm(g, d, ci[d]);
+  double mcp = L.muc[F], mcm = L.muc[F + od_m];
+  double off = 2.0 * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
     const double* __restrict__ ue = L.u[e];
     const double* __restrict__ me = L.mue[edge_id(d, e)];
-    bool pe = g.per[e] != 0;
-    bool wp = !pe && ci[e] == g.n[e] - 1;
-    bool wm = !pe && ci[e] == 0;
-    long long Ep = F + offp(g, e, ci[e]);
+    bool wp = false, wm = false;
+    if (!INTERIOR) {
+      bool pe = g.per[e] != 0;
+      wp = !pe && ci[e] == g.n[e] - 1;
+      wm = !pe && ci[e] == 0;
+    }
+    const long long oep = INTERIOR ? g.st[e] : offp(g, e, ci[e]);
+    const long long oem = INTERIOR ? -g.st[e] : offm(g, e, ci[e]);
+    long long Ep = F + oep;
     double mep = me[Ep], mem = me[F];
     double cp = ue[Ep] - ue[Ep + od_m];
     double cm = ue[F] - ue[F + od_m];
     double udp = 0.0, udm = 0.0;
     if (!wp) udp = ud[Ep];
-    if (!wm) udm = ud[F + offm(g, e, ci[e])];
+    if (!wm) udm = ud[F + oem];
     off += mep * (udp + cp) + mem * (udm - cm);
-    dgV += (wp ? 2.0 : 1.0) * mep + (wm ? 2.0 : 1.0) * mem;
   }
-  return L.uf[d][F] - (L.m[d][F] + ir * dgV) * ud[F] + ir * off;
+  return L.uf[d][F] - diag[F] * ud[F] + ir * off;
 }
 
 struct F32x3 {
   float* a[3];
 };
 
+template <int D, bool INTERIOR>
+__device__ __forceinline__ double v_res_any(const Geo& g, const LevelPtrs<double>& L,
+                                            const Ptr3d& diag, int d, const int ci[3],
+                                            long long F, double ir) {
+  if (d == 0) return v_res64d<D, 0, INTERIOR>(g, L, diag.a[0], ci, F, ir);
+  if (d == 1) return v_res64d<D, 1, INTERIOR>(g, L, diag.a[1], ci, F, ir);
+  return v_res64d<D, (D == 3 ? 2 : 1), INTERIOR>(g, L, diag.a[D == 3 ? 2 : 1], ci, F, ir);
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
-                                                          F32x3 e32, double ir, double* partial) {
+                                                          F32x3 e32, Ptr3d diag, double ir,
+                                                          double* partial) {
   __shared__ double sh[32];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -137,14 +198,14 @@ __global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<doubl
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
     int ci[3] = {i, j, k};
     long long F = gidx(g, i, j, k);
+    bool interior = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) interior = interior && ci[a] > 0 && ci[a] < g.n[a] - 1;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       double r = 0.0;
-      if (g.per[d] || ci[d] != 0) {
-        if (d == 0) r = v_res64<D, 0>(g, L, ci, F, ir);
-        else if (d == 1) r = v_res64<D, 1>(g, L, ci, F, ir);
-        else r = v_res64<D, (D == 3 ? 2 : 1)>(g, L, ci, F, ir);
-      }
+      if (interior) r = v_res_any<D, true>(g, L, diag, d, ci, F, ir);
+      else if (g.per[d] || ci[d] != 0) r = v_res_any<D, false>(g, L, diag, d, ci, F, ir);
       r32.a[d][F] = (float)r;
       e32.a[d][F] = 0.0f;
       r2 += r * r;
@@ -210,17 +271,31 @@ void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, fl
 }
 
 void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
-                             float* const e32[3], double inv_re, double* partial, cudaStream_t s) {
+                             float* const e32[3], double* const diag[3], double inv_re,
+                             double* partial, cudaStream_t s) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
   F32x3 r, e;
+  Ptr3d dg;
   for (int d = 0; d < 3; ++d) {
     r.a[d] = r32[d];
     e.a[d] = e32[d];
+    dg.a[d] = diag[d];
   }
   double ir = inv_re / (g.h * g.h);
-  if (D == 3) k_v_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r, e, ir, partial);
-  else k_v_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r, e, ir, partial);
+  if (D == 3) k_v_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r, e, dg, ir, partial);
+  else k_v_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r, e, dg, ir, partial);
+}
+
+void launch_v_diag(int D, const Geo& g, const LevelPtrs<double>& L, double* const diag[3],
+                   double inv_re, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  Ptr3d dg;
+  for (int d = 0; d < 3; ++d) dg.a[d] = diag[d];
+  double ir = inv_re / (g.h * g.h);
+  if (D == 3) k_v_diag<3><<<gr, b, 0, s>>>(g, L, dg, ir);
+  else k_v_diag<2><<<gr, b, 0, s>>>(g, L, dg, ir);
 }
 
 void launch_add_correction(int D, const Geo& g, double* const x[3], float* const e[3], int ncomp,

@@ -157,13 +157,14 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
   const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int q = tid; q < 3 * rg.nrow * rg.W; q += nthr) rg.buf[q] = T(0);
   __syncthreads();
+  // ring slots of the planes k, k - 1, k - 2 and the wrapped index of plane
+  // k, advanced by one plane per iteration (no division per point)
+  int s0 = slot_of(k0 - 1), s1 = slot_of(k0 - 2), s2 = slot_of(k0 - 3);
+  int kw = g.per[SA] ? wrapi(k0 - 1, nS) : k0 - 1;
   for (int k = k0 - 1; k <= k1; ++k) {
     // new red values of plane k on every row of the block (ring included)
-    T* row = rg.row(slot_of(k), r);
-    int kw = k;
-    bool planevalid = true;
-    if (g.per[SA]) kw = wrapi(k, nS);
-    else planevalid = (k >= 0 && k < nS);
+    T* row = rg.row(s0, r);
+    const bool planevalid = g.per[SA] || (k >= 0 && k < nS);
     if (planevalid && rowvalid) {
       for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
         int ci[3];
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
     // black values of plane k - 1 on the block's own rows; both colours out
     const int kb = k - 1;
     if (kb >= k0 && tilerow) {
-      const int sl_m = slot_of(kb - 1), sl_0 = slot_of(kb), sl_p = slot_of(kb + 1);
+      const int sl_m = s2, sl_0 = s1, sl_p = s0;
       const T* here = rg.row(sl_0, r);
       for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
         int ci[3];
@@ -201,6 +202,11 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
       }
     }
     __syncthreads();
+    const int sn = s2;   // plane k + 1 takes the slot of plane k - 2
+    s2 = s1;
+    s1 = s0;
+    s0 = sn;
+    kw = (g.per[SA] && kw + 1 == nS) ? 0 : kw + 1;
   }
 }
 
@@ -298,12 +304,11 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
   const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int q = tid; q < 3 * rg.nrow * rg.W; q += nthr) rg.buf[q] = T(0);
   __syncthreads();
+  int s0 = slot_of(k0 - 1), s1 = slot_of(k0 - 2), s2 = slot_of(k0 - 3);
+  int kw = g.per[SA] ? wrapi(k0 - 1, nS) : k0 - 1;
   for (int k = k0 - 1; k <= k1; ++k) {
-    T* row = rg.row(slot_of(k), r);
-    int kw = k;
-    bool planevalid = true;
-    if (g.per[SA]) kw = wrapi(k, nS);
-    else planevalid = (k >= 0 && k < nS);
+    T* row = rg.row(s0, r);
+    const bool planevalid = g.per[SA] || (k >= 0 && k < nS);
     if (planevalid && rowvalid) {
       for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
         int ci[3];
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
     __syncthreads();
     const int kb = k - 1;
     if (kb >= k0 && tilerow) {
-      const int sl_m = slot_of(kb - 1), sl_0 = slot_of(kb), sl_p = slot_of(kb + 1);
+      const int sl_m = s2, sl_0 = s1, sl_p = s0;
       const T* here = rg.row(sl_0, r);
       for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
         int ci[3];
@@ -345,6 +350,11 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
       }
     }
     __syncthreads();
+    const int sn = s2;   // plane k + 1 takes the slot of plane k - 2
+    s2 = s1;
+    s1 = s0;
+    s0 = sn;
+    kw = (g.per[SA] && kw + 1 == nS) ? 0 : kw + 1;
   }
 }
 

@@ -89,7 +89,8 @@ size_t grid_pool_bytes(const bfibm_params& P, int* nlev = nullptr) {
   size_t bytes = 0;
   for (int l = 0; l < L; ++l) {
     size_t arr = (size_t)round_up(level_elems(g[l]) * 8, 256);
-    int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0);
+    int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0) +
+             (l == 0 && P.precision == 1 ? P.dim : 0);
     bytes += arr * na;
     if (P.precision == 1)
       bytes += (size_t)round_up(level_elems(g[l]) * 4, 256) * arrays_per_level(P.dim);
@@ -137,6 +138,7 @@ struct bfibm_ctx {
   int D = 0, L = 0;
   Level lev[kMaxLevels];
   double* uvel[3] = {nullptr, nullptr, nullptr};
+  double* vdiag[3] = {nullptr, nullptr, nullptr};   // FP64 viscous diagonal (mixed precision)
   double* rho[3] = {nullptr, nullptr, nullptr};
   double* frc[3] = {nullptr, nullptr, nullptr};
   double* G_dev = nullptr;
@@ -608,12 +610,12 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
   if (tol && c->capturing) {
     cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
-    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, nullptr, s);
+    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, nullptr, s);
     bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
       cudaStream_t b = c->stream;
       vcycle_v32(c, 0);
       launch_add_correction(c->D, L0.g, L0.d.u, L0.f.u, c->D, b);
-      launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, c->sc.partial, b);
+      launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
       launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles,
                        c->loop_total, b);
@@ -623,7 +625,7 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   }
   int k = 0;
   for (k = 1; k <= maxc; ++k) {
-    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re,
+    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re,
                             tol ? c->sc.partial : nullptr, s);
     if (tol) {
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
@@ -641,7 +643,7 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   }
   if (k > maxc) k = maxc;
   if (c->collect_stats || tol) {
-    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->P.inv_re, c->sc.partial, s);
+    launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, c->sc.partial, s);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
   }
   *used = k;
@@ -674,9 +676,11 @@ void build_coefficients(bfibm_ctx* c) {
   for (int l = 1; l < c->L; ++l)
     launch_coef_restrict(c->D, c->lev[l - 1].g, c->lev[l].g, c->lev[l - 1].d, c->lev[l].d,
                          c->P.gamma_coarse, c->stream);
-  if (c->P.precision == 1)
+  if (c->P.precision == 1) {
+    launch_v_diag(c->D, L0.g, L0.d, c->vdiag, c->P.inv_re, c->stream);
     for (int l = 0; l < c->L; ++l)
       launch_coef_to_f32(c->D, c->lev[l].g, c->lev[l].d, c->lev[l].f, c->stream);
+  }
 }
 
 SpreadArgs spread_args(const bfibm_ctx* c) {
@@ -961,6 +965,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
         c->uvel[a] = take(Lv.g);
         c->rho[a] = take(Lv.g);
         c->frc[a] = take(Lv.g);
+        if (p->precision == 1) c->vdiag[a] = take(Lv.g);
       }
   }
   if (p->precision == 1) {

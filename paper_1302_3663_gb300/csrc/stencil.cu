@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* 
 #pragma unroll
       for (int o = -1; o <= 1; ++o) {
         int q = 2 * C[d] + o;
-        if (gf.per[d]) q = (q + nf) % nf;
+        if (gf.per[d]) q = q < 0 ? q + nf : (q >= nf ? q - nf : q);
         f[d] = q;
         T w = (o == 0) ? T(0.5) : T(0.25);
         along += w * rf[gidx(gf, f[0], f[1], f[2])];
@@ -309,7 +309,7 @@ __device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, int mirror, 
   w[0] = T(0.75);
   w[1] = T(0);
   if (per) {
-    idx[1] = (J + nc) % nc;
+    idx[1] = J < 0 ? J + nc : (J >= nc ? J - nc : J);
     w[1] = T(0.25);
     return 2;
   }
@@ -326,13 +326,13 @@ __device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], 
   int I = i >> 1;
   w[1] = T(0);
   if ((i & 1) == 0) {
-    idx[0] = per ? (I % nc) : I;
+    idx[0] = I;   // a fine face index is below 2 nc, so I < nc
     w[0] = T(1);
     return 1;
   }
   idx[0] = I;
   w[0] = T(0.5);
-  idx[1] = per ? ((I + 1) % nc) : I + 1;
+  idx[1] = (per && I + 1 == nc) ? 0 : I + 1;
   w[1] = T(0.5);
   return 2;
 }
