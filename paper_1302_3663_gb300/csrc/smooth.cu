@@ -364,8 +364,10 @@ struct FusedShape {
   size_t smem;
 };
 
+// Tile rows TYo and chunk planes KCo (3D) come from the autotuner when it
+// has timed this level shape; 0 selects the built-in heuristic.
 template <typename T>
-FusedShape fused_shape(int D, const Geo& g) {
+FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0) {
   FusedShape f;
   int RA = (D == 3) ? 1 : 2, SA = (D == 3) ? 2 : 1;
   int ring = (D == 3) ? 1 : 0;
@@ -374,6 +376,7 @@ FusedShape fused_shape(int D, const Geo& g) {
   if (bx > 128) bx = 128;
   // 4 rows (+2 ring rows) keep blocks small enough for several per SM
   f.TY = (D == 3) ? (g.n[RA] >= 4 ? 4 : g.n[RA]) : 1;
+  if (D == 3 && TYo > 0) f.TY = TYo < g.n[RA] ? TYo : g.n[RA];
   while (bx * (f.TY + 2 * ring) > 1024 && f.TY > 1) --f.TY;
   while ((size_t)3 * (f.TY + 2 * ring) * g.s[0] * sizeof(T) > 48 * 1024 && f.TY > 1) --f.TY;
   int nrt = (g.n[RA] + f.TY - 1) / f.TY;
@@ -383,6 +386,7 @@ FusedShape fused_shape(int D, const Geo& g) {
   int KC = (int)((long long)g.n[SA] * nrt / want);
   if (KC < 4) KC = 4;
   if (KC > 16) KC = 16;
+  if (D == 3 && KCo > 0) KC = KCo;
   if (KC > g.n[SA]) KC = g.n[SA];
   f.KC = KC;
   f.block = dim3(bx, f.TY + 2 * ring, 1);
@@ -394,16 +398,17 @@ FusedShape fused_shape(int D, const Geo& g) {
 }  // namespace
 
 template <typename T>
-void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s) {
-  FusedShape f = fused_shape<T>(D, g);
+void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s, int TYo,
+                       int KCo) {
+  FusedShape f = fused_shape<T>(D, g, TYo, KCo);
   if (D == 3) k_p_rb_fused<3, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
   else k_p_rb_fused<2, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
 }
 
 template <typename T>
 void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
-                       cudaStream_t s) {
-  FusedShape f = fused_shape<T>(D, g);
+                       cudaStream_t s, int TYo, int KCo) {
+  FusedShape f = fused_shape<T>(D, g, TYo, KCo);
   T ir = (T)(inv_re / (g.h * g.h));
   if (D == 3) {
     if (d == 0) k_v_rb_fused<3, 0, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
@@ -445,12 +450,12 @@ size_t fused_smem_bytes(int D, const Geo& g, int elem) {
 }
 
 template void launch_p_rb_fused<double>(int, const Geo&, const LevelPtrs<double>&, double*,
-                                        cudaStream_t);
+                                        cudaStream_t, int, int);
 template void launch_p_rb_fused<float>(int, const Geo&, const LevelPtrs<float>&, float*,
-                                       cudaStream_t);
+                                       cudaStream_t, int, int);
 template void launch_v_rb_fused<double>(int, const Geo&, const LevelPtrs<double>&, int, double*,
-                                        double, cudaStream_t);
+                                        double, cudaStream_t, int, int);
 template void launch_v_rb_fused<float>(int, const Geo&, const LevelPtrs<float>&, int, float*,
-                                       double, cudaStream_t);
+                                       double, cudaStream_t, int, int);
 
 }  // namespace bf

@@ -497,6 +497,7 @@ const void* kernel_of(int K) {
 struct Plan {
   int TY = 4, KC = 16, PD = 1, SW = 0, grid = 0;
   bool tma = false;    // the TMA sweep timed faster than the one-pass global-memory sweep
+  int rTY = 0, rKC = 0;   // fastest tile rows / chunk planes of the one-pass sweep
 };
 
 using PlanKey = std::tuple<int, int, int, int, int, long long, int>;
@@ -627,18 +628,38 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
   Plan best;
   float best_ms = 1e30f;
   cudaError_t status = cudaSuccess;
-  // the one-pass sweep that reads global memory is the first candidate
-  {
-    auto ring = [&]() {
-      if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s);
-      else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s);
-    };
-    ring();
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 3; ++r) ring();
-    cudaEventRecord(e1, s);
-    status = cudaEventSynchronize(e1);
-    if (status == cudaSuccess) cudaEventElapsedTime(&best_ms, e0, e1);
+  // the one-pass sweep that reads global memory: tile rows and chunk planes
+  const int npairs = (g.n[0] + 1) / 2;
+  const int bx = npairs >= 128 ? 128 : (npairs + 31) / 32 * 32;
+  // shapes are searched on large levels only: on small ones a launch lasts a
+  // few microseconds and the timing cannot tell the candidates apart
+  const bool search = (long long)g.n[0] * g.n[1] * g.n[2] >= (1 << 19);
+  for (int rTY : {0, 2, 4, 6, 8}) {
+    if ((rTY == 0) == search) continue;
+    if (rTY > g.n[1] || bx * (rTY + 2) > 1024) continue;
+    for (int rKC : {8, 16, 32}) {
+      if (!search && rKC != 8) continue;
+      if (search && rKC > g.n[2] && rKC != 8) continue;
+      auto ring = [&]() {
+        if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s, rTY, rKC);
+        else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s, rTY, rKC);
+      };
+      ring();
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 5; ++r) ring();
+      cudaEventRecord(e1, s);
+      status = cudaEventSynchronize(e1);
+      if (status != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms *= 3.0f / 5.0f;   // the TMA candidates below are timed over 3 launches
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.rTY = rTY;
+        best.rKC = search ? rKC : 0;
+      }
+    }
+    if (status != cudaSuccess) break;
   }
   const int tys[] = {2, 4, 6, 8};
   const int kcs[] = {16, 32, 64};
@@ -721,7 +742,21 @@ bool tma_set_plan(int K, const Geo& g, const int in[5]) {
   if (pl.KC < 1 || pl.PD < 1 || pl.PD > kMaxPD || pl.grid < 0 || !plan_fits(K, g, pl.TY, pl.PD, pl.SW))
     return false;
   std::lock_guard<std::mutex> lock(g_plan_mu);
+  auto it = g_plans.find(plan_key(K, g));
+  if (it != g_plans.end()) {
+    pl.rTY = it->second.rTY;
+    pl.rKC = it->second.rKC;
+  }
   g_plans[plan_key(K, g)] = pl;
+  return true;
+}
+
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  auto it = g_plans.find(plan_key(K, g));
+  if (it == g_plans.end() || it->second.rTY <= 0) return false;
+  *TY = it->second.rTY;
+  *KC = it->second.rKC;
   return true;
 }
 

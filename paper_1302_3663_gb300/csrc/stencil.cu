@@ -315,6 +315,7 @@ __device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, int mirror, 
   }
   if (J < 0 || J >= nc) {
     w[0] = mirror > 0 ? T(1) : T(0.5);
+    idx[1] = I;   // weight 0: any valid index
     return 1;
   }
   idx[1] = J;
@@ -327,6 +328,7 @@ __device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], 
   w[1] = T(0);
   if ((i & 1) == 0) {
     idx[0] = I;   // a fine face index is below 2 nc, so I < nc
+    idx[1] = I;   // weight 0: any valid index
     w[0] = T(1);
     return 1;
   }
@@ -337,17 +339,22 @@ __device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], 
   return 2;
 }
 
-// separable tensor-product sum: x-rows first, then y, then z
+// separable tensor-product sum: x-rows first, then y, then z. Every axis
+// takes two terms; a missing term has weight 0 and a valid index, and adding
+// its exact zero leaves the sum unchanged, so the loops unroll fully and the
+// index and weight arrays stay in registers.
 template <typename T>
 __device__ __forceinline__ T prol_sum(const Geo& gc, const T* __restrict__ ec, const int idx[3][2],
-                                      const T w[3][2], const int cnt[3]) {
+                                      const T w[3][2]) {
   T v = T(0);
-  for (int c = 0; c < cnt[2]; ++c) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
     T col = T(0);
-    for (int b = 0; b < cnt[1]; ++b) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
       long long r = gidx(gc, 0, idx[1][b], idx[2][c]);
       T row = w[0][0] * ec[r + idx[0][0]];
-      if (cnt[0] == 2) row += w[0][1] * ec[r + idx[0][1]];
+      row += w[0][1] * ec[r + idx[0][1]];
       col += w[1][b] * row;
     }
     v += w[2][c] * col;
@@ -365,10 +372,9 @@ __global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* _
   if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
-  int cnt[3] = {1, 1, 1};
 #pragma unroll
-  for (int a = 0; a < D; ++a) cnt[a] = prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, idx[a], w[a]);
-  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w, cnt);
+  for (int a = 0; a < D; ++a) prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, idx[a], w[a]);
+  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
 }
 
 template <int D, int d, typename T>
@@ -382,15 +388,14 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
   if (!gf.per[d] && fi[d] == 0) return;
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
-  int cnt[3] = {1, 1, 1};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     if (a == d)
-      cnt[a] = prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
+      prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
     else
-      cnt[a] = prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, idx[a], w[a]);
+      prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, idx[a], w[a]);
   }
-  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w, cnt);
+  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
 }
 
 // ---------------------------------------------------------------------------
