@@ -88,10 +88,10 @@ void launch_coarse_v(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, dou
 // write `out`.
 template <typename T>
 void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s,
-                       int TYo = 0, int KCo = 0);
+                       int TYo = 0, int KCo = 0, int NPo = 1);
 template <typename T>
 void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
-                       cudaStream_t s, int TYo = 0, int KCo = 0);
+                       cudaStream_t s, int TYo = 0, int KCo = 0, int NPo = 1);
 
 // Mixed precision (mixed.cu).
 int red_blocks_3d(int D, const Geo& g);
@@ -132,7 +132,7 @@ cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K,
 // pin a plan {TY, KC, PD, SW, grid (0: resident blocks)} for a level shape
 bool tma_set_plan(int K, const Geo& g, const int in[5]);
 // the one-pass sweep's tuned tile rows and chunk planes for a level shape
-bool ring_shape_of(int K, const Geo& g, int* TY, int* KC);
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP);
 // whether the tuner found the TMA sweep faster than the one-pass sweep
 bool tma_chosen(int K, const Geo& g);
 // tuned plan of a level shape: tile rows, chunk planes, prefetch planes,

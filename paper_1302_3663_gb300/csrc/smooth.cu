@@ -136,10 +136,19 @@ __device__ __forceinline__ T p_black(const LevelPtrs<T>& L, const Ring<T>& rg, c
   return (num - h2 * L.pf[q.F]) / dg;
 }
 
-template <int D, typename T>
+// NP planes per iteration: the red values of planes k .. k+NP-1 (independent
+// of one another, so their loads overlap), a barrier, then the black values
+// of planes k-1 .. k+NP-2; the ring holds NP + 2 planes.
+__device__ __forceinline__ int add_mod(int s, int o, int R) {
+  int v = s + o;
+  return v >= R ? v - R : (v < 0 ? v + R : v);
+}
+
+template <int D, typename T, int NP>
 __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* __restrict__ out,
                                                      int TY, int KC) {
   constexpr int RA = Ax<D>::R, SA = Ax<D>::S, RING = Ax<D>::RING;
+  constexpr int R = NP + 2;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   Ring<T> rg{reinterpret_cast<T*>(sm_raw), TY + 2 * RING, g.s[0]};
   const int n0 = g.n[0], nR = g.n[RA], nS = g.n[SA];
@@ -155,58 +164,72 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
   const bool tilerow = (r >= RING && r < RING + TY && j < nR);
   const T h2 = (T)(g.h * g.h);
   const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int q = tid; q < 3 * rg.nrow * rg.W; q += nthr) rg.buf[q] = T(0);
+  for (int q = tid; q < R * rg.nrow * rg.W; q += nthr) rg.buf[q] = T(0);
   __syncthreads();
-  // ring slots of the planes k, k - 1, k - 2 and the wrapped index of plane
-  // k, advanced by one plane per iteration (no division per point)
-  int s0 = slot_of(k0 - 1), s1 = slot_of(k0 - 2), s2 = slot_of(k0 - 3);
+  // ring slot and wrapped index of plane k, advanced by NP planes per
+  // iteration (no division per point); plane k0 - 2 sits in slot 0
+  int sk = 1;
   int kw = g.per[SA] ? wrapi(k0 - 1, nS) : k0 - 1;
-  for (int k = k0 - 1; k <= k1; ++k) {
-    // new red values of plane k on every row of the block (ring included)
-    T* row = rg.row(s0, r);
-    const bool planevalid = g.per[SA] || (k >= 0 && k < nS);
-    if (planevalid && rowvalid) {
-      for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
+  for (int k = k0 - 1; k <= k1; k += NP) {
+    // new red values of planes k .. k + NP - 1 on every row of the block
+    bool live[NP];
+    int kwo[NP];
+#pragma unroll
+    for (int o = 0; o < NP; ++o) {
+      const int p = k + o;
+      kwo[o] = (g.per[SA] && kw + o >= nS) ? kw + o - nS : kw + o;
+      live[o] = p <= k1 && rowvalid && (g.per[SA] || (p >= 0 && p < nS));
+      if (p <= k1 && !live[o]) {
+        T* row = rg.row(add_mod(sk, o, R), r);
+        for (int i = threadIdx.x; i < rg.W; i += blockDim.x) row[i] = T(0);
+      }
+    }
+    for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
+#pragma unroll
+      for (int o = 0; o < NP; ++o) {
+        if (!live[o]) continue;
         int ci[3];
         ci[RA] = jw;
-        ci[SA] = kw;
+        ci[SA] = kwo[o];
         ci[0] = 2 * ip + ((ci[1] + ci[2]) & 1);   // the red point of this pair
         if (ci[0] < n0) {
           Pt q;
           make_pt<D>(g, ci, q);
-          row[ci[0]] = p_red<D, T>(L, q, h2);
+          rg.row(add_mod(sk, o, R), r)[ci[0]] = p_red<D, T>(L, q, h2);
         }
       }
-    } else {
-      for (int i = threadIdx.x; i < rg.W; i += blockDim.x) row[i] = T(0);
     }
     __syncthreads();
-    // black values of plane k - 1 on the block's own rows; both colours out
-    const int kb = k - 1;
-    if (kb >= k0 && tilerow) {
-      const int sl_m = s2, sl_0 = s1, sl_p = s0;
-      const T* here = rg.row(sl_0, r);
+    // black values of planes k - 1 .. k + NP - 2 on the block's own rows;
+    // both colours out
+    if (tilerow) {
       for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
-        int ci[3];
-        ci[RA] = jw;
-        ci[SA] = kb;
-        int par = (ci[1] + ci[2]) & 1;
-        int ir = 2 * ip + par, ib = 2 * ip + (par ^ 1);
-        if (ir < n0) out[ir + (int)g.st[1] * ci[1] + (int)g.st[2] * ci[2]] = here[ir];
-        if (ib < n0) {
-          ci[0] = ib;
-          Pt q;
-          make_pt<D>(g, ci, q);
-          out[q.F] = p_black<D, T>(L, rg, q, ib, n0, r, sl_m, sl_0, sl_p, h2);
+#pragma unroll
+        for (int o = 0; o < NP; ++o) {
+          const int kb = k - 1 + o;
+          if (kb < k0 || kb >= k1) continue;
+          const int sl_m = add_mod(sk, o - 2, R), sl_0 = add_mod(sk, o - 1, R),
+                    sl_p = add_mod(sk, o, R);
+          const T* here = rg.row(sl_0, r);
+          int ci[3];
+          ci[RA] = jw;
+          ci[SA] = kb;
+          int par = (ci[1] + ci[2]) & 1;
+          int ir = 2 * ip + par, ib = 2 * ip + (par ^ 1);
+          if (ir < n0) out[ir + (int)g.st[1] * ci[1] + (int)g.st[2] * ci[2]] = here[ir];
+          if (ib < n0) {
+            ci[0] = ib;
+            Pt q;
+            make_pt<D>(g, ci, q);
+            out[q.F] = p_black<D, T>(L, rg, q, ib, n0, r, sl_m, sl_0, sl_p, h2);
+          }
         }
       }
     }
     __syncthreads();
-    const int sn = s2;   // plane k + 1 takes the slot of plane k - 2
-    s2 = s1;
-    s1 = s0;
-    s0 = sn;
-    kw = (g.per[SA] && kw + 1 == nS) ? 0 : kw + 1;
+    sk = add_mod(sk, NP, R);
+    kw += NP;
+    if (g.per[SA] && kw >= nS) kw -= nS;
   }
 }
 
@@ -283,10 +306,11 @@ __device__ __forceinline__ T v_black(const LevelPtrs<T>& L, const Ring<T>& rg, c
   return (L.uf[d][q.F] + ir * off) / v.diag;
 }
 
-template <int D, int d, typename T>
+template <int D, int d, typename T, int NP>
 __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* __restrict__ out,
                                                      int TY, int KC, T ir) {
   constexpr int RA = Ax<D>::R, SA = Ax<D>::S, RING = Ax<D>::RING;
+  constexpr int R = NP + 2;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   Ring<T> rg{reinterpret_cast<T*>(sm_raw), TY + 2 * RING, g.s[0]};
   const int n0 = g.n[0], nR = g.n[RA], nS = g.n[SA];
@@ -302,18 +326,30 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
   const bool tilerow = (r >= RING && r < RING + TY && j < nR);
   const bool wall_d = !g.per[d];
   const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int q = tid; q < 3 * rg.nrow * rg.W; q += nthr) rg.buf[q] = T(0);
+  for (int q = tid; q < R * rg.nrow * rg.W; q += nthr) rg.buf[q] = T(0);
   __syncthreads();
-  int s0 = slot_of(k0 - 1), s1 = slot_of(k0 - 2), s2 = slot_of(k0 - 3);
+  int sk = 1;
   int kw = g.per[SA] ? wrapi(k0 - 1, nS) : k0 - 1;
-  for (int k = k0 - 1; k <= k1; ++k) {
-    T* row = rg.row(s0, r);
-    const bool planevalid = g.per[SA] || (k >= 0 && k < nS);
-    if (planevalid && rowvalid) {
-      for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
+  for (int k = k0 - 1; k <= k1; k += NP) {
+    bool live[NP];
+    int kwo[NP];
+#pragma unroll
+    for (int o = 0; o < NP; ++o) {
+      const int p = k + o;
+      kwo[o] = (g.per[SA] && kw + o >= nS) ? kw + o - nS : kw + o;
+      live[o] = p <= k1 && rowvalid && (g.per[SA] || (p >= 0 && p < nS));
+      if (p <= k1 && !live[o]) {
+        T* row = rg.row(add_mod(sk, o, R), r);
+        for (int i = threadIdx.x; i < rg.W; i += blockDim.x) row[i] = T(0);
+      }
+    }
+    for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
+#pragma unroll
+      for (int o = 0; o < NP; ++o) {
+        if (!live[o]) continue;
         int ci[3];
         ci[RA] = jw;
-        ci[SA] = kw;
+        ci[SA] = kwo[o];
         ci[0] = 2 * ip + ((ci[1] + ci[2]) & 1);
         if (ci[0] >= n0) continue;
         T v = T(0);   // wall faces hold 0
@@ -322,39 +358,41 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
           make_pt<D>(g, ci, q);
           v = v_red<D, d, T>(L, q, ir);
         }
-        row[ci[0]] = v;
+        rg.row(add_mod(sk, o, R), r)[ci[0]] = v;
       }
-    } else {
-      for (int i = threadIdx.x; i < rg.W; i += blockDim.x) row[i] = T(0);
     }
     __syncthreads();
-    const int kb = k - 1;
-    if (kb >= k0 && tilerow) {
-      const int sl_m = s2, sl_0 = s1, sl_p = s0;
-      const T* here = rg.row(sl_0, r);
+    if (tilerow) {
       for (int ip = threadIdx.x; 2 * ip < n0; ip += blockDim.x) {
-        int ci[3];
-        ci[RA] = jw;
-        ci[SA] = kb;
-        int par = (ci[1] + ci[2]) & 1;
-        int irr = 2 * ip + par, ib = 2 * ip + (par ^ 1);
-        if (irr < n0) out[irr + (int)g.st[1] * ci[1] + (int)g.st[2] * ci[2]] = here[irr];
-        if (ib < n0) {
-          ci[0] = ib;
-          Pt q;
-          make_pt<D>(g, ci, q);
-          T v = T(0);
-          if (!(wall_d && ci[d] == 0)) v = v_black<D, d, T>(L, rg, q, ib, n0, ir, r, sl_m, sl_0, sl_p);
-          out[q.F] = v;
+#pragma unroll
+        for (int o = 0; o < NP; ++o) {
+          const int kb = k - 1 + o;
+          if (kb < k0 || kb >= k1) continue;
+          const int sl_m = add_mod(sk, o - 2, R), sl_0 = add_mod(sk, o - 1, R),
+                    sl_p = add_mod(sk, o, R);
+          const T* here = rg.row(sl_0, r);
+          int ci[3];
+          ci[RA] = jw;
+          ci[SA] = kb;
+          int par = (ci[1] + ci[2]) & 1;
+          int irr = 2 * ip + par, ib = 2 * ip + (par ^ 1);
+          if (irr < n0) out[irr + (int)g.st[1] * ci[1] + (int)g.st[2] * ci[2]] = here[irr];
+          if (ib < n0) {
+            ci[0] = ib;
+            Pt q;
+            make_pt<D>(g, ci, q);
+            T v = T(0);
+            if (!(wall_d && ci[d] == 0))
+              v = v_black<D, d, T>(L, rg, q, ib, n0, ir, r, sl_m, sl_0, sl_p);
+            out[q.F] = v;
+          }
         }
       }
     }
     __syncthreads();
-    const int sn = s2;   // plane k + 1 takes the slot of plane k - 2
-    s2 = s1;
-    s1 = s0;
-    s0 = sn;
-    kw = (g.per[SA] && kw + 1 == nS) ? 0 : kw + 1;
+    sk = add_mod(sk, NP, R);
+    kw += NP;
+    if (g.per[SA] && kw >= nS) kw -= nS;
   }
 }
 
@@ -367,7 +405,7 @@ struct FusedShape {
 // Tile rows TYo and chunk planes KCo (3D) come from the autotuner when it
 // has timed this level shape; 0 selects the built-in heuristic.
 template <typename T>
-FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0) {
+FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0, int NP = 1) {
   FusedShape f;
   int RA = (D == 3) ? 1 : 2, SA = (D == 3) ? 2 : 1;
   int ring = (D == 3) ? 1 : 0;
@@ -378,7 +416,7 @@ FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0) {
   f.TY = (D == 3) ? (g.n[RA] >= 4 ? 4 : g.n[RA]) : 1;
   if (D == 3 && TYo > 0) f.TY = TYo < g.n[RA] ? TYo : g.n[RA];
   while (bx * (f.TY + 2 * ring) > 1024 && f.TY > 1) --f.TY;
-  while ((size_t)3 * (f.TY + 2 * ring) * g.s[0] * sizeof(T) > 48 * 1024 && f.TY > 1) --f.TY;
+  while ((size_t)(NP + 2) * (f.TY + 2 * ring) * g.s[0] * sizeof(T) > 48 * 1024 && f.TY > 1) --f.TY;
   int nrt = (g.n[RA] + f.TY - 1) / f.TY;
   // about three blocks per SM in flight, with chunks of at most 16 planes so
   // that the recomputed first plane of a chunk stays a small fraction
@@ -391,7 +429,7 @@ FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0) {
   f.KC = KC;
   f.block = dim3(bx, f.TY + 2 * ring, 1);
   f.grid = dim3(nrt, (g.n[SA] + KC - 1) / KC, 1);
-  f.smem = (size_t)3 * (f.TY + 2 * ring) * g.s[0] * sizeof(T);
+  f.smem = (size_t)(NP + 2) * (f.TY + 2 * ring) * g.s[0] * sizeof(T);
   return f;
 }
 
@@ -399,24 +437,33 @@ FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0) {
 
 template <typename T>
 void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s, int TYo,
-                       int KCo) {
-  FusedShape f = fused_shape<T>(D, g, TYo, KCo);
-  if (D == 3) k_p_rb_fused<3, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
-  else k_p_rb_fused<2, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
+                       int KCo, int NPo) {
+  const int NP = (D == 3 && NPo == 2) ? 2 : 1;
+  FusedShape f = fused_shape<T>(D, g, TYo, KCo, NP);
+  if (D == 3 && NP == 2) k_p_rb_fused<3, T, 2><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
+  else if (D == 3) k_p_rb_fused<3, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
+  else k_p_rb_fused<2, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
 }
 
 template <typename T>
 void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
-                       cudaStream_t s, int TYo, int KCo) {
-  FusedShape f = fused_shape<T>(D, g, TYo, KCo);
+                       cudaStream_t s, int TYo, int KCo, int NPo) {
+  const int NP = (D == 3 && NPo == 2) ? 2 : 1;
+  FusedShape f = fused_shape<T>(D, g, TYo, KCo, NP);
   T ir = (T)(inv_re / (g.h * g.h));
   if (D == 3) {
-    if (d == 0) k_v_rb_fused<3, 0, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
-    else if (d == 1) k_v_rb_fused<3, 1, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
-    else k_v_rb_fused<3, 2, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+    if (NP == 2) {
+      if (d == 0) k_v_rb_fused<3, 0, T, 2><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+      else if (d == 1) k_v_rb_fused<3, 1, T, 2><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+      else k_v_rb_fused<3, 2, T, 2><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+    } else {
+      if (d == 0) k_v_rb_fused<3, 0, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+      else if (d == 1) k_v_rb_fused<3, 1, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+      else k_v_rb_fused<3, 2, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+    }
   } else {
-    if (d == 0) k_v_rb_fused<2, 0, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
-    else k_v_rb_fused<2, 1, T><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+    if (d == 0) k_v_rb_fused<2, 0, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
+    else k_v_rb_fused<2, 1, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC, ir);
   }
 }
 
@@ -428,20 +475,28 @@ cudaError_t fused_set_carveout() {
   auto set = [&](const void* f) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
   };
-  set((const void*)k_p_rb_fused<3, float>);
-  set((const void*)k_p_rb_fused<2, float>);
-  set((const void*)k_p_rb_fused<3, double>);
-  set((const void*)k_p_rb_fused<2, double>);
-  set((const void*)k_v_rb_fused<3, 0, float>);
-  set((const void*)k_v_rb_fused<3, 1, float>);
-  set((const void*)k_v_rb_fused<3, 2, float>);
-  set((const void*)k_v_rb_fused<2, 0, float>);
-  set((const void*)k_v_rb_fused<2, 1, float>);
-  set((const void*)k_v_rb_fused<3, 0, double>);
-  set((const void*)k_v_rb_fused<3, 1, double>);
-  set((const void*)k_v_rb_fused<3, 2, double>);
-  set((const void*)k_v_rb_fused<2, 0, double>);
-  set((const void*)k_v_rb_fused<2, 1, double>);
+  set((const void*)k_p_rb_fused<3, float, 1>);
+  set((const void*)k_p_rb_fused<3, float, 2>);
+  set((const void*)k_p_rb_fused<2, float, 1>);
+  set((const void*)k_p_rb_fused<3, double, 1>);
+  set((const void*)k_p_rb_fused<3, double, 2>);
+  set((const void*)k_p_rb_fused<2, double, 1>);
+  set((const void*)k_v_rb_fused<3, 0, float, 1>);
+  set((const void*)k_v_rb_fused<3, 1, float, 1>);
+  set((const void*)k_v_rb_fused<3, 2, float, 1>);
+  set((const void*)k_v_rb_fused<3, 0, float, 2>);
+  set((const void*)k_v_rb_fused<3, 1, float, 2>);
+  set((const void*)k_v_rb_fused<3, 2, float, 2>);
+  set((const void*)k_v_rb_fused<2, 0, float, 1>);
+  set((const void*)k_v_rb_fused<2, 1, float, 1>);
+  set((const void*)k_v_rb_fused<3, 0, double, 1>);
+  set((const void*)k_v_rb_fused<3, 1, double, 1>);
+  set((const void*)k_v_rb_fused<3, 2, double, 1>);
+  set((const void*)k_v_rb_fused<3, 0, double, 2>);
+  set((const void*)k_v_rb_fused<3, 1, double, 2>);
+  set((const void*)k_v_rb_fused<3, 2, double, 2>);
+  set((const void*)k_v_rb_fused<2, 0, double, 1>);
+  set((const void*)k_v_rb_fused<2, 1, double, 1>);
   return e;
 }
 
@@ -450,12 +505,12 @@ size_t fused_smem_bytes(int D, const Geo& g, int elem) {
 }
 
 template void launch_p_rb_fused<double>(int, const Geo&, const LevelPtrs<double>&, double*,
-                                        cudaStream_t, int, int);
+                                        cudaStream_t, int, int, int);
 template void launch_p_rb_fused<float>(int, const Geo&, const LevelPtrs<float>&, float*,
-                                       cudaStream_t, int, int);
+                                       cudaStream_t, int, int, int);
 template void launch_v_rb_fused<double>(int, const Geo&, const LevelPtrs<double>&, int, double*,
-                                        double, cudaStream_t, int, int);
+                                        double, cudaStream_t, int, int, int);
 template void launch_v_rb_fused<float>(int, const Geo&, const LevelPtrs<float>&, int, float*,
-                                       double, cudaStream_t, int, int);
+                                       double, cudaStream_t, int, int, int);
 
 }  // namespace bf

@@ -497,7 +497,7 @@ const void* kernel_of(int K) {
 struct Plan {
   int TY = 4, KC = 16, PD = 1, SW = 0, grid = 0;
   bool tma = false;    // the TMA sweep timed faster than the one-pass global-memory sweep
-  int rTY = 0, rKC = 0;   // fastest tile rows / chunk planes of the one-pass sweep
+  int rTY = 0, rKC = 0, rNP = 1;   // fastest rows / chunk planes / planes per phase of the one-pass sweep
 };
 
 using PlanKey = std::tuple<int, int, int, int, int, long long, int>;
@@ -628,12 +628,33 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
   Plan best;
   float best_ms = 1e30f;
   cudaError_t status = cudaSuccess;
+  // per-launch time of a candidate: the better of two rounds of four launches
+  auto per_launch_ms = [&](auto&& launch) -> float {
+    float t = 1e30f;
+    for (int round = 0; round < 2 && status == cudaSuccess; ++round) {
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 4; ++r) launch();
+      cudaEventRecord(e1, s);
+      status = cudaEventSynchronize(e1);
+      if (status != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 4 < t) t = ms / 4;
+    }
+    return t;
+  };
   // the one-pass sweep that reads global memory: tile rows and chunk planes
   const int npairs = (g.n[0] + 1) / 2;
   const int bx = npairs >= 128 ? 128 : (npairs + 31) / 32 * 32;
   // shapes are searched on large levels only: on small ones a launch lasts a
   // few microseconds and the timing cannot tell the candidates apart
   const bool search = (long long)g.n[0] * g.n[1] * g.n[2] >= (1 << 19);
+  // bring the clocks up before the first candidate is timed
+  for (int r = 0; r < 10; ++r) {
+    if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s);
+    else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s);
+  }
+  for (int rNP : {1, 2}) {
   for (int rTY : {0, 2, 4, 6, 8}) {
     if ((rTY == 0) == search) continue;
     if (rTY > g.n[1] || bx * (rTY + 2) > 1024) continue;
@@ -641,25 +662,22 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
       if (!search && rKC != 8) continue;
       if (search && rKC > g.n[2] && rKC != 8) continue;
       auto ring = [&]() {
-        if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s, rTY, rKC);
-        else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s, rTY, rKC);
+        if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s, rTY, rKC, rNP);
+        else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s, rTY, rKC, rNP);
       };
       ring();
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < 5; ++r) ring();
-      cudaEventRecord(e1, s);
-      status = cudaEventSynchronize(e1);
+      float ms = per_launch_ms(ring);
       if (status != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms *= 3.0f / 5.0f;   // the TMA candidates below are timed over 3 launches
       if (ms < best_ms) {
         best_ms = ms;
         best.rTY = rTY;
         best.rKC = search ? rKC : 0;
+        best.rNP = rNP;
       }
     }
     if (status != cudaSuccess) break;
+  }
+  if (status != cudaSuccess) break;
   }
   const int tys[] = {2, 4, 6, 8};
   const int kcs[] = {16, 32, 64};
@@ -677,13 +695,8 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
       int grid = resident_grid(K, TY, PD, A.SW, A.items);
       status = launch_args(K, A, grid, s);
       if (status != cudaSuccess) break;
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) launch_args(K, A, grid, s);
-      cudaEventRecord(e1, s);
-      status = cudaEventSynchronize(e1);
+      float ms = per_launch_ms([&]() { launch_args(K, A, grid, s); });
       if (status != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best_ms) {
         best_ms = ms;
         best.tma = true;
@@ -746,17 +759,19 @@ bool tma_set_plan(int K, const Geo& g, const int in[5]) {
   if (it != g_plans.end()) {
     pl.rTY = it->second.rTY;
     pl.rKC = it->second.rKC;
+    pl.rNP = it->second.rNP;
   }
   g_plans[plan_key(K, g)] = pl;
   return true;
 }
 
-bool ring_shape_of(int K, const Geo& g, int* TY, int* KC) {
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   auto it = g_plans.find(plan_key(K, g));
-  if (it == g_plans.end() || it->second.rTY <= 0) return false;
+  if (it == g_plans.end()) return false;
   *TY = it->second.rTY;
   *KC = it->second.rKC;
+  *NP = it->second.rNP;
   return true;
 }
 

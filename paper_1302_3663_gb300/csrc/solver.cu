@@ -465,9 +465,9 @@ void smooth_p32(bfibm_ctx* c, int l, int n) {
     if (tma)
       launch_rb_tma(c->D, Lv.g, Lv.f, 3, Lv.f.p2, c->counters + 3, Lv.g.h * Lv.g.h, c->stream);
     else {
-      int ty = 0, kc = 0;
-      ring_shape_of(3, Lv.g, &ty, &kc);
-      launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc);
+      int ty = 0, kc = 0, np = 1;
+      ring_shape_of(3, Lv.g, &ty, &kc, &np);
+      launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc, np);
     }
     std::swap(Lv.f.p, Lv.f.p2);
   }
@@ -486,9 +486,10 @@ void smooth_v32(bfibm_ctx* c, int l, int n) {
         launch_rb_tma(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->counters + 3,
                       c->P.inv_re / (Lv.g.h * Lv.g.h), c->stream);
       else {
-        int ty = 0, kc = 0;
-        ring_shape_of(d, Lv.g, &ty, &kc);
-        launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream, ty, kc);
+        int ty = 0, kc = 0, np = 1;
+        ring_shape_of(d, Lv.g, &ty, &kc, &np);
+        launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream, ty, kc,
+                                 np);
       }
       std::swap(Lv.f.u[d], Lv.f.u2[d]);
     }
