@@ -135,8 +135,8 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out);
 
 /* Load eta node positions X (eta x dim doubles, row-major, host). Every
    coordinate must lie in [0, L) on a periodic axis and in [0, L] on a wall
-   axis (L = n h), else BFIBM_EINVAL and nothing changes. Replaces the
-   springs' endpoints' meaning: load springs after nodes. */
+   axis (L = n h), else BFIBM_EINVAL and nothing changes. Load springs after
+   nodes: loading a different number of nodes drops the springs. */
 bfibm_status bfibm_set_nodes(bfibm_ctx* c, int64_t eta, const double* X);
 
 /* Load m springs: node pairs ab (m x 2 int32), rest lengths, Hookean

@@ -195,6 +195,10 @@ struct SpringSet {
   int* ev_step;
   int* ev_count;    // 1 counter
   long long* step;  // device step counter
+  double* fvec;     // m x 3: the force each spring puts on its first node
+  int* adj_start;   // eta + 1: springs of node s are adj[adj_start[s] .. adj_start[s+1])
+  int* adj;         // 2 m: 2 * spring + (0: first node, 1: second node), springs ascending
+  long long adj_eta;   // node count the adjacency was built for
 };
 struct TileGeo {
   int T[3];         // cells per tile and axis
@@ -208,6 +212,8 @@ struct SpreadArgs {
   double omega, omega_mu;
   double amp_rho;     // rho_b d0^D
   double mu_out, mu_coef;   // (2 w)^D (mu_max - mu_out)
+  double rho_f;       // background density
+  double* scale;      // device [2]: fixed-point scales of the force and density sums
 };
 
 void launch_springs(int D, const Geo& g, const NodeSet& N, const SpringSet& S, cudaStream_t s);
@@ -216,6 +222,11 @@ void launch_reset_fields(int D, const Geo& g, double* frc[3], double* rho[3], do
                          double* mue[3], double rho_f, double mu_f, cudaStream_t s);
 void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, const SpreadArgs& a,
                    double* frc[3], double* rho[3], double* muc, double* mue[3], cudaStream_t s);
+// f and rho leave the spread as 64-bit fixed-point sums (see lagrangian.cu);
+// this converts them to doubles (run after every spread, and after a reset
+// without nodes)
+void launch_spread_finish(int D, const Geo& g, const SpreadArgs& a, double* frc[3], double* rho[3],
+                          cudaStream_t s);
 void launch_interp_advance(int D, const Geo& g, const NodeSet& N, double* const uvel[3],
                            int phi_kind, double dt_over_sigma, cudaStream_t s);
 void launch_step_increment(long long* step, cudaStream_t s);

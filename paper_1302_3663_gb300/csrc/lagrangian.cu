@@ -88,11 +88,16 @@ __device__ __forceinline__ void for_support(const Geo& g, const int stag[3], con
 // ---------------------------------------------------------------------------
 // Springs: break test on the squared length without fused multiply-adds (so
 // the decision matches a plain IEEE evaluation), then the tension
-// T = K (|d| - r) pulls both nodes along d (Eq. springF).
+// T = K (|d| - r) pulls both nodes along d (Eq. springF). Each spring stores
+// the force on its first node; every node then sums the forces of its
+// springs in ascending spring order (a fixed order, so the sums do not depend
+// on thread scheduling).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_springs(int D, Geo g, NodeSet N, SpringSet S) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= S.m) return;
+  double* fq = &S.fvec[3 * q];
+  fq[0] = fq[1] = fq[2] = 0.0;
   if (S.broken[q]) return;
   int a = S.ab[2 * q], b = S.ab[2 * q + 1];
   double dv[3] = {0.0, 0.0, 0.0};
@@ -120,11 +125,24 @@ __global__ void __launch_bounds__(kBlock) k_springs(int D, Geo g, NodeSet N, Spr
   double len = sqrt(len2);
   if (len == 0.0) return;
   double T = S.K[q] * (len - S.rest[q]);
-  for (int ax = 0; ax < D; ++ax) {
-    double f = T * dv[ax] / len;
-    atomicAdd(&N.F[3 * (long long)a + ax], f);
-    atomicAdd(&N.F[3 * (long long)b + ax], -f);
+  for (int ax = 0; ax < D; ++ax) fq[ax] = T * dv[ax] / len;
+}
+
+__global__ void __launch_bounds__(kBlock) k_node_force(NodeSet N, SpringSet S) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= N.eta) return;
+  double F[3] = {0.0, 0.0, 0.0};
+  for (int e = S.adj_start[s]; e < S.adj_start[s + 1]; ++e) {
+    const int q = S.adj[e] >> 1;
+    const bool second = (S.adj[e] & 1) != 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      double f = S.fvec[3 * (long long)q + ax];
+      F[ax] += second ? -f : f;
+    }
   }
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) N.F[3 * s + ax] = F[ax];
 }
 
 // ---------------------------------------------------------------------------
@@ -180,7 +198,8 @@ __global__ void __launch_bounds__(kBlock) k_bin_scatter(NodeSet N) {
 }
 
 // ---------------------------------------------------------------------------
-// Field reset before spreading: f = 0, rho = rho_f, mu = mu_f everywhere.
+// Field reset before spreading: the f and rho sums start at zero, mu = mu_f
+// everywhere.
 // ---------------------------------------------------------------------------
 struct FieldPtrs {
   double* frc[3];
@@ -196,9 +215,10 @@ __global__ void __launch_bounds__(kBlock) k_reset(int D, Geo g, FieldPtrs P, dou
   int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= g.s[0] || j >= g.s[1] || k >= g.s[2]) return;
   long long c = gidx(g, i, j, k);
+  (void)rho_f;   // added back when the density sums are converted
   for (int d = 0; d < D; ++d) {
-    P.frc[d][c] = 0.0;
-    P.rho[d][c] = rho_f;
+    P.frc[d][c] = 0.0;   // the bit pattern of the fixed-point zero
+    P.rho[d][c] = 0.0;
   }
   P.muc[c] = mu_f;
   int ne = D == 3 ? 3 : 1;
@@ -430,39 +450,47 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadK A) {
       1.0 / (D == 3 ? A.a.omega_mu * A.a.omega_mu * A.a.omega_mu : A.a.omega_mu * A.a.omega_mu);
   const long long items = (long long)nn * slots;
 
-  // force and density, one face grid at a time
+  // force and density, one face grid at a time, summed as 64-bit fixed-point
+  // integers (every contribution rounded once, at the scale of the step's
+  // bound on the sums): integer addition is associative, so the result does
+  // not depend on the order in which threads and blocks add
+  const double sf = A.a.scale[0], sr = A.a.scale[1];
   for (int d = 0; d < D; ++d) {
     int stag[3] = {1, 1, 1};
     stag[d] = 0;
-    double* accF = smem;
-    double* accR = smem + vol;
+    unsigned long long* accF = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* accR = accF + vol;
     if (sm) {
-      for (int q = threadIdx.x; q < 2 * vol; q += blockDim.x) smem[q] = 0.0;
+      for (int q = threadIdx.x; q < 2 * vol; q += blockDim.x) accF[q] = 0ull;
       __syncthreads();
     }
+    unsigned long long* gF = reinterpret_cast<unsigned long long*>(A.P.frc[d]);
+    unsigned long long* gR = reinterpret_cast<unsigned long long*>(A.P.rho[d]);
     for (long long it = threadIdx.x; it < items; it += blockDim.x) {
       int p = s0 + (int)(it / slots), slot = (int)(it % slots);
       double Fd = A.N.F[3 * (long long)A.N.perm[p] + d];
       item(p, slot, stag, 0, A.a.omega, [&](int l, long long gi, double w) {
         double wt = winvD * w;
+        const unsigned long long cf = (unsigned long long)llrint(Fd * wt * sf);
+        const unsigned long long cr = (unsigned long long)llrint(A.a.amp_rho * wt * sr);
         if (l >= 0) {
-          atomicAdd(&accF[l], Fd * wt);
-          atomicAdd(&accR[l], A.a.amp_rho * wt);
+          if (cf) atomicAdd(&accF[l], cf);
+          if (cr) atomicAdd(&accR[l], cr);
         } else {
-          atomicAdd(&A.P.frc[d][gi], Fd * wt);
-          atomicAdd(&A.P.rho[d][gi], A.a.amp_rho * wt);
+          if (cf) atomicAdd(&gF[gi], cf);
+          if (cr) atomicAdd(&gR[gi], cr);
         }
       });
     }
     if (sm) {
       __syncthreads();
       for (int q = threadIdx.x; q < vol; q += blockDim.x) {
-        double vf = accF[q], vr = accR[q];
-        if (vf == 0.0 && vr == 0.0) continue;
+        unsigned long long vf = accF[q], vr = accR[q];
+        if (vf == 0ull && vr == 0ull) continue;
         long long gi = flush_index(q, stag);
         if (gi < 0) continue;
-        if (vf != 0.0) atomicAdd(&A.P.frc[d][gi], vf);
-        if (vr != 0.0) atomicAdd(&A.P.rho[d][gi], vr);
+        if (vf) atomicAdd(&gF[gi], vf);
+        if (vr) atomicAdd(&gR[gi], vr);
       }
       __syncthreads();
     }
@@ -577,10 +605,14 @@ inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
 
 // ===========================================================================
 void launch_springs(int D, const Geo& g, const NodeSet& N, const SpringSet& S, cudaStream_t s) {
-  if (N.eta > 0) cudaMemsetAsync(N.F, 0, sizeof(double) * 3 * N.eta, s);
-  if (S.m <= 0) return;
+  if (N.eta <= 0) return;
+  if (S.m <= 0 || S.adj_eta != N.eta) {
+    cudaMemsetAsync(N.F, 0, sizeof(double) * 3 * N.eta, s);
+    return;
+  }
   unsigned nb = (unsigned)((S.m + kBlock - 1) / kBlock);
   k_springs<<<nb, kBlock, 0, s>>>(D, g, N, S);
+  k_node_force<<<(unsigned)((N.eta + kBlock - 1) / kBlock), kBlock, 0, s>>>(N, S);
 }
 
 void launch_bin(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, cudaStream_t s) {
@@ -633,9 +665,75 @@ bool spread_fits_tables(double omega, double omega_mu, double h) {
   return w <= h;
 }
 
+namespace {
+
+// Scales of the fixed-point sums: the largest power of two S with
+// S * bound < 2^61, where bound >= |any partial sum| (the sum over nodes of
+// the largest force component times the delta's peak omega^-D, and eta times
+// rho_b d0^D omega^-D). One block sums in a fixed order, so the scales, and
+// with them every rounded contribution, are the same in every run.
+__global__ void __launch_bounds__(1024) k_spread_scale(NodeSet N, int D, double winvD, double amp,
+                                                       double* scale) {
+  __shared__ double part[1024];
+  double v = 0.0;
+  for (long long s = threadIdx.x; s < N.eta; s += blockDim.x) {
+    double m = 0.0;
+    for (int a = 0; a < D; ++a) m = fmax(m, fabs(N.F[3 * s + a]));
+    v += m;
+  }
+  part[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) part[threadIdx.x] += part[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double bound[2] = {part[0] * winvD, (double)N.eta * fabs(amp) * winvD};
+    for (int k = 0; k < 2; ++k) {
+      int e = 0;
+      frexp(bound[k], &e);   // bound < 2^e
+      scale[k] = (bound[k] > 0.0 && isfinite(bound[k])) ? ldexp(1.0, 61 - e) : 1.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_spread_finish(int D, Geo g, Ptr3d frc, Ptr3d rho,
+                                                          const double* __restrict__ scale,
+                                                          double rho_f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.s[0] || j >= g.s[1] || k >= g.s[2]) return;
+  long long c = gidx(g, i, j, k);
+  const double inv_f = 1.0 / scale[0], inv_r = 1.0 / scale[1];   // powers of two: exact
+  for (int d = 0; d < D; ++d) {
+    long long vf = (long long)__double_as_longlong(frc.a[d][c]);
+    long long vr = (long long)__double_as_longlong(rho.a[d][c]);
+    frc.a[d][c] = vf ? (double)vf * inv_f : 0.0;
+    rho.a[d][c] = rho_f + (vr ? (double)vr * inv_r : 0.0);
+  }
+}
+
+}  // namespace
+
+void launch_spread_finish(int D, const Geo& g, const SpreadArgs& a, double* frc[3], double* rho[3],
+                          cudaStream_t s) {
+  Ptr3d F, R;
+  for (int d = 0; d < 3; ++d) {
+    F.a[d] = frc[d];
+    R.a[d] = rho[d];
+  }
+  dim3 b = blk3(D);
+  k_spread_finish<<<grd3(g.s[0], g.s[1], g.s[2], b), b, 0, s>>>(D, g, F, R, a.scale, a.rho_f);
+}
+
 void launch_spread(int D, const Geo& g, const TileGeo& tg, const NodeSet& N, const SpreadArgs& a,
                    double* frc[3], double* rho[3], double* muc, double* mue[3], cudaStream_t s) {
   if (N.eta <= 0) return;
+  {
+    const double w = a.omega;
+    k_spread_scale<<<1, 1024, 0, s>>>(N, D, 1.0 / (D == 3 ? w * w * w : w * w), a.amp_rho, a.scale);
+  }
   SpreadK A;
   A.g = g;
   A.tg = tg;

@@ -152,6 +152,7 @@ struct bfibm_ctx {
   TileGeo tg{};
   long long* step_dev = nullptr;
   int* counters = nullptr;    // [0] clamped, [1] event count, [2] non-finite, [3] wait timeouts
+  double* spread_scale = nullptr;   // fixed-point scales of the force and density sums
   std::vector<void*> lag_allocs;
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;     // captures the bodies of device-side loops
@@ -700,6 +701,8 @@ SpreadArgs spread_args(const bfibm_ctx* c) {
   a.mu_out = c->P.mu_f;
   double tw = 2.0 * c->P.omega_mu;
   a.mu_coef = (c->D == 3 ? tw * tw * tw : tw * tw) * (c->P.mu_ratio * c->P.mu_f - c->P.mu_f);
+  a.rho_f = c->P.rho_f;
+  a.scale = c->spread_scale;
   return a;
 }
 
@@ -715,6 +718,7 @@ void refresh(bfibm_ctx* c) {
     launch_spread(c->D, L0.g, c->tg, c->N, spread_args(c), c->frc, c->rho, L0.d.muc, L0.d.mue,
                   c->stream);
   }
+  launch_spread_finish(c->D, L0.g, spread_args(c), c->frc, c->rho, c->stream);
   build_coefficients(c);
 }
 
@@ -882,7 +886,8 @@ void free_lag(bfibm_ctx* c, bool nodes, bool springs) {
   }
   if (springs) {
     for (void* q : {(void*)c->S.ab, (void*)c->S.rest, (void*)c->S.K, (void*)c->S.brk,
-                    (void*)c->S.broken, (void*)c->S.ev_id, (void*)c->S.ev_step})
+                    (void*)c->S.broken, (void*)c->S.ev_id, (void*)c->S.ev_step,
+                    (void*)c->S.fvec, (void*)c->S.adj_start, (void*)c->S.adj})
       if (q) cudaFree(q);
     int* evc = c->S.ev_count;
     long long* step = c->S.step;
@@ -1012,6 +1017,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
       cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
       cudaMalloc((void**)&c->dev_cycles, sizeof(int) * 2) != cudaSuccess ||
       cudaMalloc((void**)&c->loop_total, sizeof(long long) * 2) != cudaSuccess ||
+      cudaMalloc((void**)&c->spread_scale, sizeof(double) * 2) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost((void**)&c->host_sc, 16 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -1028,6 +1034,11 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
             cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, s) == cudaSuccess &&
             cudaMemsetAsync(c->dev_cycles, 0, sizeof(int) * 2, s) == cudaSuccess &&
             cudaMemsetAsync(c->loop_total, 0, sizeof(long long) * 2, s) == cudaSuccess;
+  {
+    static const double one[2] = {1.0, 1.0};
+    ok = ok && cudaMemcpyAsync(c->spread_scale, one, sizeof(one), cudaMemcpyHostToDevice, s) ==
+                   cudaSuccess;
+  }
   if (!ok) {
     bfibm_destroy(c);
     return BFIBM_ECUDA;
@@ -1097,6 +1108,7 @@ void bfibm_destroy(bfibm_ctx* c) {
   if (c->sc.partial) cudaFree(c->sc.partial);
   if (c->step_dev) cudaFree(c->step_dev);
   if (c->counters) cudaFree(c->counters);
+  if (c->spread_scale) cudaFree(c->spread_scale);
   if (c->dev_cycles) cudaFree(c->dev_cycles);
   if (c->loop_total) cudaFree(c->loop_total);
   if (c->aux) cudaStreamDestroy(c->aux);
@@ -1121,6 +1133,10 @@ bfibm_status bfibm_set_nodes(bfibm_ctx* c, int64_t eta, const double* X) {
   CK(cudaStreamSynchronize(c->stream));
   drop_graph(c);
   free_lag(c, true, false);
+  if (c->S.m > 0 && c->S.adj_eta != eta) {   // the springs refer to the old node count
+    free_lag(c, false, true);
+    c->S.m = 0;
+  }
   NodeSet& N = c->N;
   N.eta = eta;
   int nt = c->tg.ntiles;
@@ -1162,8 +1178,10 @@ bfibm_status bfibm_set_springs(bfibm_ctx* c, int64_t m, const int32_t* ab, const
   free_lag(c, false, true);
   SpringSet& S = c->S;
   S.m = m;
+  const long long eta = c->N.eta;
   if (dmalloc(&S.ab, 2 * m) || dmalloc(&S.rest, m) || dmalloc(&S.K, m) || dmalloc(&S.brk, m) ||
-      dmalloc(&S.broken, m) || dmalloc(&S.ev_id, m) || dmalloc(&S.ev_step, m)) {
+      dmalloc(&S.broken, m) || dmalloc(&S.ev_id, m) || dmalloc(&S.ev_step, m) ||
+      dmalloc(&S.fvec, 3 * m) || dmalloc(&S.adj_start, eta + 1) || dmalloc(&S.adj, 2 * m)) {
     cudaGetLastError();
     free_lag(c, false, true);
     c->S.m = 0;
@@ -1175,6 +1193,28 @@ bfibm_status bfibm_set_springs(bfibm_ctx* c, int64_t m, const int32_t* ab, const
     CK(cudaMemcpyAsync(S.K, K, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(S.brk, brk, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(S.broken, 0, sizeof(int) * m, c->stream));
+  }
+  // springs of each node in ascending order (the order the node force sums
+  // them in): a counting sort of the 2 m endpoints
+  {
+    std::vector<int> start(eta + 1, 0), adj(2 * std::max<int64_t>(m, 1));
+    for (int64_t q = 0; q < m; ++q) {
+      ++start[ab[2 * q] + 1];
+      ++start[ab[2 * q + 1] + 1];
+    }
+    for (long long s = 0; s < eta; ++s) start[s + 1] += start[s];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int64_t q = 0; q < m; ++q) {
+      adj[fill[ab[2 * q]]++] = (int)(2 * q);
+      adj[fill[ab[2 * q + 1]]++] = (int)(2 * q + 1);
+    }
+    CK(cudaMemcpyAsync(S.adj_start, start.data(), sizeof(int) * (eta + 1), cudaMemcpyHostToDevice,
+                       c->stream));
+    if (m > 0)
+      CK(cudaMemcpyAsync(S.adj, adj.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice,
+                         c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    S.adj_eta = eta;
   }
   CK(cudaMemsetAsync(S.ev_count, 0, sizeof(int), c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -175,3 +175,35 @@ def test_launch_accounting_of_device_loops(precision):
     assert b["iters_visc"] - a["iters_visc"] >= 2 * 3
     assert b["iters_p"] - a["iters_p"] >= 2
     assert b["iters_visc"] - a["iters_visc"] >= st["cycles_visc"]
+
+
+def breaking_c1():
+    inst = W.c1()
+    inst["brk"] = np.full(len(inst["rest"]), 0.02)
+    inst["K"] = np.full(len(inst["rest"]), 5.0)
+    return inst, {"dt": 4e-3}, 12
+
+
+def c2_plain():
+    return W.c2(), {}, 6
+
+
+@pytest.mark.parametrize("case", [breaking_c1, c2_plain], ids=["c1_breaking", "c2"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_repeated_runs_bit_identical(case, precision):
+    # two runs of the same input agree bit for bit (node forces summed per node
+    # in a fixed order, spread sums in fixed point)
+    inst, over, steps = case()
+    over = dict(over, precision=precision)
+    runs = []
+    for _ in range(2):
+        c = bfibm.load_instance(inst, prm_override=over)
+        c.step(steps)
+        runs.append([c.get_velocity(d) for d in range(c.dim)] +
+                    [c.get_pressure(), c.get_nodes(), c.get_node_forces(),
+                     np.sort(c.get_broken()[0])])
+        c.close()
+    if case is breaking_c1:
+        assert len(runs[0][-1]) > 5
+    for x, y in zip(*runs):
+        assert np.array_equal(x, y)
