@@ -223,6 +223,22 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
    bit-identical results). Every option gives the same results to rounding. */
 enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2, BFIBM_OPT_TMA = 3 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
+/* Checkpoint and resume. The state a time step starts from (Sec. 3.4): the
+   velocity u^n, the pressure (the next projection's initial guess), the node
+   positions X^n, the broken springs with their break events, and the step
+   count; forces, spreads and coefficients follow from it. bfibm_state_bytes
+   gives the buffer size; bfibm_save_state writes the state into a host
+   buffer; bfibm_load_state restores it into a context created with the same
+   parameters and the same node and spring counts (BFIBM_EINVAL otherwise).
+   Because no part of a step depends on the order of atomic operations, a
+   resumed run continues bit for bit as the original would have. The buffer
+   starts with a header (magic, version, dim, n, precision, counts) followed
+   by the raw level-0 arrays in their padded layout; it is meant for the same
+   library version. Checkpoints are not in the paper. */
+bfibm_status bfibm_state_bytes(bfibm_ctx* c, int64_t* bytes);
+bfibm_status bfibm_save_state(bfibm_ctx* c, void* buf, int64_t bytes);
+bfibm_status bfibm_load_state(bfibm_ctx* c, const void* buf, int64_t bytes);
+
 /* Tile plan the autotuner chose for the TMA-staged FP32 sweep of one level
    (kind 0..D-1: viscous component, 3: pressure): out = {tile rows, planes per
    chunk, planes prefetched, columns per strip, grid blocks}. Plans are timed once per level

@@ -75,6 +75,9 @@ SIGNATURES = {
     "bfibm_get_field": [_V, _i, _i, _i, _DP],
     "bfibm_set_field": [_V, _i, _i, _i, _DP],
     "bfibm_tma_plan": [_V, _i, _i, _IP],
+    "bfibm_state_bytes": [_V, C.POINTER(_L)],
+    "bfibm_save_state": [_V, _V, _L],
+    "bfibm_load_state": [_V, _V, _L],
     "bfibm_tma_set_plan": [_V, _i, _i, _IP],
     "bfibm_get_field_f32": [_V, _i, _i, _i, C.POINTER(C.c_float)],
     "bfibm_set_field_f32": [_V, _i, _i, _i, C.POINTER(C.c_float)],
@@ -297,6 +300,19 @@ class Context:
         a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape(level))
         self._chk(self.lib.bfibm_set_field(self.h, FIELD[which], comp, level, _dp(a)),
                   "bfibm_set_field")
+
+    def save_state(self):
+        """The checkpoint of the evolving state as a uint8 array (see
+        bfibm_save_state)."""
+        n = _L()
+        self._chk(self.lib.bfibm_state_bytes(self.h, C.byref(n)), "bfibm_state_bytes")
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._chk(self.lib.bfibm_save_state(self.h, buf.ctypes.data, n.value), "bfibm_save_state")
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._chk(self.lib.bfibm_load_state(self.h, buf.ctypes.data, buf.size), "bfibm_load_state")
 
     def tma_plan(self, level=0, kind=0):
         """(tile rows, planes per chunk, planes prefetched, strip columns, grid)

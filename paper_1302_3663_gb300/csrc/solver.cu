@@ -1502,6 +1502,102 @@ bfibm_status bfibm_launches_per_step(bfibm_ctx* c, int64_t* n) {
   return BFIBM_OK;
 }
 
+// ------------------------------------------------------------------ checkpoints
+namespace {
+struct CkptHeader {
+  uint64_t magic;
+  int32_t version, dim, n[3], precision;
+  int64_t eta, m, step, events, elems;
+};
+constexpr uint64_t kCkptMagic = 0x31544b504d424942ull;   // "BIBMPKT1"
+
+int64_t ckpt_bytes(const bfibm_ctx* c) {
+  const int64_t elems = level_elems(c->lev[0].g);
+  return (int64_t)sizeof(CkptHeader) + (int64_t)(c->D + 1) * elems * 8 + c->N.eta * 3 * 8 +
+         c->S.m * 3 * 4;
+}
+}  // namespace
+
+bfibm_status bfibm_state_bytes(bfibm_ctx* c, int64_t* bytes) {
+  READY(c);
+  if (!bytes) return set_err(c, BFIBM_EINVAL, "bytes is NULL");
+  *bytes = ckpt_bytes(c);
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_save_state(bfibm_ctx* c, void* buf, int64_t bytes) {
+  READY(c);
+  if (!buf || bytes < ckpt_bytes(c)) return set_err(c, BFIBM_EINVAL, "buffer too small");
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kCkptMagic;
+  h.version = 1;
+  h.dim = c->D;
+  for (int a = 0; a < 3; ++a) h.n[a] = c->P.n[a];
+  h.precision = c->P.precision;
+  h.eta = c->N.eta;
+  h.m = c->S.m;
+  h.step = c->step_host;
+  h.elems = level_elems(c->lev[0].g);
+  int cnt[4];
+  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  h.events = std::min<int64_t>(cnt[1], c->S.m);
+  unsigned char* q = (unsigned char*)buf;
+  std::memcpy(q, &h, sizeof(h));
+  q += sizeof(h);
+  const size_t fb = (size_t)h.elems * 8;
+  for (int d = 0; d < c->D; ++d, q += fb)
+    CK(cudaMemcpyAsync(q, c->uvel[d], fb, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(q, c->lev[0].d.p, fb, cudaMemcpyDeviceToHost, c->stream));
+  q += fb;
+  if (h.eta > 0) CK(cudaMemcpyAsync(q, c->N.X, h.eta * 24, cudaMemcpyDeviceToHost, c->stream));
+  q += h.eta * 24;
+  if (h.m > 0) {
+    CK(cudaMemcpyAsync(q, c->S.broken, h.m * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(q + h.m * 4, c->S.ev_id, h.m * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(q + h.m * 8, c->S.ev_step, h.m * 4, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_load_state(bfibm_ctx* c, const void* buf, int64_t bytes) {
+  READY(c);
+  if (!buf || bytes < (int64_t)sizeof(CkptHeader)) return set_err(c, BFIBM_EINVAL, "buffer too small");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  bool same = h.magic == kCkptMagic && h.version == 1 && h.dim == c->D &&
+              h.precision == c->P.precision && h.eta == c->N.eta && h.m == c->S.m &&
+              h.elems == level_elems(c->lev[0].g) && h.step >= 0 && h.events >= 0 &&
+              h.events <= h.m;
+  for (int a = 0; a < 3; ++a) same = same && h.n[a] == c->P.n[a];
+  if (!same) return set_err(c, BFIBM_EINVAL, "checkpoint does not match this context");
+  if (bytes < ckpt_bytes(c)) return set_err(c, BFIBM_EINVAL, "checkpoint truncated");
+  CK(cudaStreamSynchronize(c->stream));
+  const unsigned char* q = (const unsigned char*)buf + sizeof(h);
+  const size_t fb = (size_t)h.elems * 8;
+  for (int d = 0; d < c->D; ++d, q += fb)
+    CK(cudaMemcpyAsync(c->uvel[d], q, fb, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->lev[0].d.p, q, fb, cudaMemcpyHostToDevice, c->stream));
+  q += fb;
+  if (h.eta > 0) CK(cudaMemcpyAsync(c->N.X, q, h.eta * 24, cudaMemcpyHostToDevice, c->stream));
+  q += h.eta * 24;
+  if (h.m > 0) {
+    CK(cudaMemcpyAsync(c->S.broken, q, h.m * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->S.ev_id, q + h.m * 4, h.m * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->S.ev_step, q + h.m * 8, h.m * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  long long step = h.step;
+  int events = (int)h.events;
+  CK(cudaMemcpyAsync(c->step_dev, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->counters + 1, &events, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->step_host = h.step;
+  c->dirty = true;   // forces, spreads and coefficients follow from X on the next step
+  return BFIBM_OK;
+}
+
 bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]) {
   READY(c);
   if (!out || level < 0 || level >= c->L || kind < 0 || kind > 3 ||

@@ -253,7 +253,33 @@ def c5_arrivals(count=128, rate=4.0, seed=999):
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
 
 
-CONFIGS = {"c1": c1, "c2": c2, "c3": c3}
+# The paper's scaling (Appendix, "Scaling Parameters"): L = 50 um, u0 = 1 mm/s,
+# T = 1 s, pressure drop 0.8144 Pa, rho0 = 998 kg/m^3, mu = 1e-3 kg/(m s).
+PAPER_SIGMA = 50e-6 / (1.0 * 1e-3)                 # L / (T u0) = 0.05
+PAPER_EULER = 0.8144 / (998.0 * 1e-3 ** 2)         # dp / (rho0 u0^2), about 816
+PAPER_RE = 998.0 * 1e-3 * 50e-6 / 1e-3             # rho0 u0 L / mu, about 0.0499
+
+
+def paper_units_duct(e=64, nodes=1500, f_max=0.5, seed=7):
+    """A 3D duct in the paper's nondimensional units (sigma = 0.05, Euler
+    number about 816, Re about 0.05, fluid viscosity 1 = that of water): the
+    hemispherical mound of the 64^3 duct, springs with K = F_max / r that break
+    at twice their rest length (Eq. defineK, break strain 1), and
+    dt = 0.1 h sigma (a node moves a tenth of a cell per step at unit speed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = 0.008
+    R = 0.15
+    X = _hemisphere_points(rng, nodes, (0.5, 0.0, 0.5), R, 3)
+    h = 1.0 / e
+    prm = _duct_params(e, e, r, 1.5, 1e3, (2.0 / 3.0 * math.pi * R ** 3) / nodes,
+                       sigma=PAPER_SIGMA, euler=PAPER_EULER, inv_re=1.0 / PAPER_RE, mu_f=1.0,
+                       dt=0.1 * h * PAPER_SIGMA)
+    ab, rest = springs_within(X, 2.5 * r)
+    return dict(name="paper_units", params=prm, X=np.ascontiguousarray(X), ab=ab, rest=rest,
+                K=f_max / np.maximum(rest, 1e-12), brk=np.full(len(rest), 1.0), steps=20)
+
+
+CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "paper_units": paper_units_duct}
 
 
 def cells(prm):

@@ -207,3 +207,42 @@ def test_repeated_runs_bit_identical(case, precision):
         assert len(runs[0][-1]) > 5
     for x, y in zip(*runs):
         assert np.array_equal(x, y)
+
+
+def test_paper_units_parity():
+    # the paper's nondimensional units (sigma 0.05, Euler ~816, Re ~0.05)
+    inst = W.paper_units_duct(e=32, nodes=800)
+    run_pair(inst, 8, chunk=4)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_bit_identical(precision):
+    # save the state mid-run, restore it into a fresh context: the resumed run
+    # continues bit for bit (breaking springs included)
+    inst, over, _ = breaking_c1()
+    over = dict(over, precision=precision)
+    a = bfibm.load_instance(inst, prm_override=over)
+    a.step(5)
+    ck = a.save_state()
+    a.step(7)
+    b = bfibm.load_instance(inst, prm_override=over)
+    b.load_state(ck)
+    assert b.get_stats()["step"] == 5
+    b.step(7)
+    assert b.get_stats()["step"] == a.get_stats()["step"] == 12
+    for d in range(a.dim):
+        assert np.array_equal(a.get_velocity(d), b.get_velocity(d))
+    assert np.array_equal(a.get_pressure(), b.get_pressure())
+    assert np.array_equal(a.get_nodes(), b.get_nodes())
+    ea, eb = a.get_broken(), b.get_broken()
+    assert len(ea[0]) > 5
+    assert sorted(zip(*ea)) == sorted(zip(*eb))
+    # a truncated checkpoint, or one of another grid, is refused
+    with pytest.raises(bfibm.BfibmError):
+        b.load_state(ck[:100])
+    other = bfibm.load_instance(ragged_duct(), prm_override={"precision": precision})
+    with pytest.raises(bfibm.BfibmError):
+        other.load_state(ck)
+    a.close()
+    b.close()
+    other.close()

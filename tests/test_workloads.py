@@ -45,3 +45,29 @@ def test_c4_c5_draws():
     t = W.c5_arrivals()
     assert t.shape == (128,) and np.all(np.diff(t) > 0)
     assert 15 < t[-1] < 50   # mean gap 0.25 s
+
+
+def test_paper_units_duct():
+    # the paper's scaling table: sigma = L / (T u0), Euler = dp / (rho0 u0^2),
+    # Re = rho0 u0 L / mu; springs K = F_max / r breaking at 2 r (Eq. defineK)
+    inst = W.paper_units_duct(e=32, nodes=600, f_max=0.5)
+    p = inst["params"]
+    assert abs(p["sigma"] - 0.05) < 1e-15
+    assert abs(p["euler"] - 816.0320641282565) < 1e-9
+    assert abs(1.0 / p["inv_re"] - 0.0499) < 1e-15
+    assert np.allclose(inst["K"] * inst["rest"], 0.5) and np.all(inst["brk"] == 1.0)
+    assert abs(p["dt"] - 0.1 / 32 * 0.05) < 1e-18
+
+
+def test_paper_units_duct_stable_in_the_oracle():
+    # kinetic energy without extreme growth (the stability notion of Sec. 4.3.4)
+    from oracle.oracle import Oracle
+    inst = W.paper_units_duct(e=32, nodes=600)
+    o = Oracle(inst["params"], omp=True)
+    o.set_nodes(inst["X"])
+    o.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+    ke = []
+    for _ in range(8):
+        o.step(1)
+        ke.append(o.stats()["kinetic"])
+    assert max(ke) < 1.1 * ke[0] and min(ke) > 0.8 * ke[0]
