@@ -70,6 +70,14 @@ def parse():
     ap.add_argument("--tma", type=int, choices=[0, 1, 2], default=1,
                     help="FP32 sweeps with TMA-staged inputs: 0 never, 1 where the autotuner "
                          "timed them faster (default), 2 wherever a level allows")
+    ap.add_argument("--study", choices=["gamma", "work_units"], default=None,
+                    help="gamma: tune the coarse viscosity scaling per level (Eq. "
+                         "ViscCoarseGrid) on the workload and time a step before and after; "
+                         "work_units: cycles and work units of one solve against the number "
+                         "of multigrid levels (Sec. 4.3.1)")
+    ap.add_argument("--no-tune-gamma", action="store_true",
+                    help="keep one coarse viscosity scaling for every level instead of tuning "
+                         "it per level before the timed region")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -94,10 +102,12 @@ def describe(inst):
     p = inst["params"]
     n = p["n"][:p["dim"]]
     prec = "fp64" if p.get("precision", 0) == 0 else "fp32 V-cycles in fp64 defect correction"
+    gl = [g for g in p.get("gamma_levels", [])[1:] if g > 0]
     vc = ("%d viscous + %d pressure V(%d,%d) cycles per step" %
           (p["vc_visc"], p["vc_p"], p["nu1"], p["nu2"]) if p["vc_visc"] > 0
-          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %g"
-          % (p["nu1"], p["nu2"], p["rtol"], p["gamma_coarse"]))
+          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %s"
+          % (p["nu1"], p["nu2"], p["rtol"],
+             ("%s per level (tuned)" % gl) if gl else "%g" % p["gamma_coarse"]))
     return {
         "workload": "%s: %s grid, %d nodes, %d springs, density ratio %g, viscosity ratio %g"
                     % (inst["name"], "x".join(map(str, n)), inst["X"].shape[0],
@@ -335,6 +345,18 @@ def run_ours(args):
     ctx.set_option(bfibm.OPT_TMA, args.tma)
     ctx.step(args.warmup)
     ctx.synchronize()
+    if args.solver == "tol" and not args.no_tune_gamma:
+        # gamma_lh of Eq. (ViscCoarseGrid) per coarse level, tuned on this
+        # state before the timed region (the plain FP64 comparison reuses it)
+        from paper_1302_3663_gb300 import tuning
+        ctx.set_option(bfibm.OPT_GRAPH, 0)
+        gl, _, _ = tuning.tune_gamma(ctx)
+        ctx.set_option(bfibm.OPT_GRAPH, 0 if args.no_graph else 1)
+        ctx.set_option(bfibm.OPT_STATS, 0)
+        prm["gamma_levels"] = gl
+        inst["params"]["gamma_levels"] = gl
+        ctx.step(1)
+        ctx.synchronize()
     lc0 = ctx.launch_counts()
     with Clocks(local) as clk:
         ms = timed_steps(ctx, stream, args.steps, world)
@@ -390,7 +412,8 @@ def run_fixed(inst, args, world, stream):
     """The same workload with 3 V-cycles per solve (no convergence check): the
     throughput of the loosest setting, for context."""
     from paper_1302_3663_gb300 import bfibm, workloads as W
-    prm = dict(inst["params"], vc_visc=3, vc_p=3, nu1=2, nu2=2, gamma_coarse=1.0)
+    prm = dict(inst["params"], vc_visc=3, vc_p=3, nu1=2, nu2=2, gamma_coarse=1.0,
+               gamma_levels=[])
     ctx = bfibm.load_instance(dict(inst, params=prm), stream=stream)
     ctx.set_option(bfibm.OPT_STATS, 0)
     ctx.step(args.warmup)
@@ -597,8 +620,51 @@ def run_served(args):
         print(json.dumps(out))
 
 
+def run_study(args):
+    """Solver studies (not the benchmark line): one JSON line each."""
+    import torch
+
+    from paper_1302_3663_gb300 import bfibm, tuning, workloads as W
+    dist_setup(args)
+    if args.study == "work_units":
+        out = {"study": "work_units", "rtol": 1e-10, "rows": {}}
+        for name, levels in (("c1", range(1, 6)), ("c2", range(3, 7))):
+            inst = W.CONFIGS[name]()
+            for which in ("pressure", "viscous"):
+                out["rows"]["%s_%s" % (name, which)] = tuning.work_units_vs_levels(
+                    inst, levels, which=which)
+        print(json.dumps(out))
+        return
+    inst = load_workload(args.config, args.precision, args)
+    cells = W.cells(inst["params"])
+    stream = torch.cuda.Stream()
+    ctx = bfibm.load_instance(inst, stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    ms0 = timed_steps(ctx, stream, args.steps, 1, "timed_gamma0")
+    fin0 = final_stats(ctx)
+    ctx.set_option(bfibm.OPT_GRAPH, 0)
+    g, before, after = tuning.tune_gamma(ctx)
+    ctx.set_option(bfibm.OPT_GRAPH, 1)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.step(1)
+    ms1 = timed_steps(ctx, stream, args.steps, 1, "timed_gamma1")
+    fin1 = final_stats(ctx)
+    ctx.close()
+    print(json.dumps({"study": "gamma", "config": describe(inst), "gamma_levels": g,
+                      "viscous_cycles_trial": [before, after],
+                      "before": {"ms_per_step": ms0 / args.steps,
+                                 "cell_steps_per_s": cells * args.steps / (ms0 / 1e3), **fin0},
+                      "after": {"ms_per_step": ms1 / args.steps,
+                                "cell_steps_per_s": cells * args.steps / (ms1 / 1e3), **fin1}}))
+
+
 def main():
     args = parse()
+    if args.study:
+        run_study(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "c4":

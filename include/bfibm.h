@@ -80,7 +80,10 @@ typedef struct {
   double u_center;        /* > 0: G chosen so the laminar centreline speed is u_center */
   double ic_scale;        /* initial velocity = ic_scale * laminar profile */
   double rtol;            /* relative residual target (Sec. 4.1 uses 1e-9) */
-  double gamma_coarse;    /* gamma of Eq. (ViscCoarseGrid) on every coarse level */
+  double gamma_coarse;    /* gamma of Eq. (ViscCoarseGrid) on every coarse level ... */
+  double gamma_levels[8]; /* ... unless gamma_levels[l] > 0: gamma_lh of coarse level l
+                             (l = 1 is the grid 2h); entries 0 and past the last level
+                             are ignored */
 } bfibm_params;
 
 typedef struct {
@@ -189,8 +192,10 @@ bfibm_status bfibm_refresh(bfibm_ctx* c);
 /* beta = 1/rho and m = rho sigma/dt on the fine faces, then every coarse level. */
 bfibm_status bfibm_build_coefficients(bfibm_ctx* c);
 bfibm_status bfibm_stage(bfibm_ctx* c, int stage);
-/* Multigrid solves on level 0 (ncycles > 0 fixed, 0 = until rtol); the cycles
-   used are written to *cycles when cycles is not NULL. */
+/* Multigrid solves on level 0 (ncycles > 0 fixed, 0 = until rtol), in the
+   context's precision (FP64 V-cycles, or FP32 V-cycles inside FP64 defect
+   correction); the cycles used are written to *cycles when cycles is not
+   NULL. */
 bfibm_status bfibm_solve_pressure(bfibm_ctx* c, int ncycles, int32_t* cycles);
 bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles);
 /* nsweeps red-black sweeps on one level (Sec. 3.5). Asynchronous: returns
@@ -206,6 +211,11 @@ bfibm_status bfibm_residual_viscous(bfibm_ctx* c, int level);
 bfibm_status bfibm_smooth_f32(bfibm_ctx* c, int which, int level, int nsweeps);
 /* Wait for all work queued on the context's stream. */
 bfibm_status bfibm_synchronize(bfibm_ctx* c);
+/* Replace the coarse-grid viscosity scaling of Eq. (ViscCoarseGrid):
+   gamma_levels[l] > 0 sets gamma_lh of coarse level l (others fall back to
+   gamma_coarse). Rebuilds the coefficient hierarchy; the next step captures a
+   new step graph. BFIBM_EINVAL for a negative or non-finite entry. */
+bfibm_status bfibm_set_gamma(bfibm_ctx* c, const double gamma_levels[8]);
 /* Number of multigrid levels and their cell counts / storage extents. */
 bfibm_status bfibm_levels(bfibm_ctx* c, int32_t* nlevels);
 bfibm_status bfibm_level_dims(bfibm_ctx* c, int level, int32_t n[3], int32_t s[3]);

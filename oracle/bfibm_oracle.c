@@ -80,7 +80,8 @@ typedef struct {
   double u_center;        /* > 0: G such that the laminar centreline speed is u_center */
   double ic_scale;        /* initial velocity = ic_scale * laminar profile */
   double rtol;            /* relative residual target, 1e-9 in Sec. 4.1 */
-  double gamma_coarse;    /* gamma of Eq. (ViscCoarseGrid), one value for all levels */
+  double gamma_coarse;    /* gamma of Eq. (ViscCoarseGrid) on every coarse level ... */
+  double gamma_levels[8]; /* ... unless gamma_levels[l] > 0: gamma_lh of coarse level l */
 } or_params;
 
 typedef struct {
@@ -684,11 +685,12 @@ static void build_coefficients(or_sim* S) {
       restrict_face_coef(S, Lf, Lc, d, Lf->beta[d], Lc->beta[d]);
       restrict_face_coef(S, Lf, Lc, d, Lf->m[d], Lc->m[d]);
     }
-    restrict_cell_coef(S, Lf, Lc, Lf->muc, Lc->muc, S->P.gamma_coarse);
+    /* Eq. (ViscCoarseGrid): gamma_lh may differ per coarse grid lh */
+    double gam = (l < 8 && S->P.gamma_levels[l] > 0.0) ? S->P.gamma_levels[l] : S->P.gamma_coarse;
+    restrict_cell_coef(S, Lf, Lc, Lf->muc, Lc->muc, gam);
     for (int d = 0; d < S->D; ++d)
       for (int e = d + 1; e < S->D; ++e)
-        restrict_edge_coef(S, Lf, Lc, d, e, Lf->mue[edge_id(d, e)], Lc->mue[edge_id(d, e)],
-                           S->P.gamma_coarse);
+        restrict_edge_coef(S, Lf, Lc, d, e, Lf->mue[edge_id(d, e)], Lc->mue[edge_id(d, e)], gam);
   }
 }
 

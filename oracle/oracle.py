@@ -32,7 +32,8 @@ class OrParams(C.Structure):
                 ("omega_mu", C.c_double), ("d0_vol", C.c_double), ("dt", C.c_double),
                 ("sigma", C.c_double), ("euler", C.c_double), ("inv_re", C.c_double),
                 ("c_force", C.c_double), ("body_force", C.c_double), ("u_center", C.c_double),
-                ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double)]
+                ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double),
+                ("gamma_levels", C.c_double * 8)]
 
 
 class OrStats(C.Structure):
@@ -111,6 +112,8 @@ def make_params(prm):
               "dt", "sigma", "euler", "inv_re", "c_force", "body_force", "u_center", "ic_scale",
               "rtol", "gamma_coarse"):
         setattr(P, k, float(prm[k]))
+    for l, v in enumerate(prm.get("gamma_levels", [])[:8]):
+        P.gamma_levels[l] = float(v)
     return P
 
 

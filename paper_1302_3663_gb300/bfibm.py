@@ -41,7 +41,8 @@ class bfibm_params(C.Structure):
                 ("omega_mu", C.c_double), ("d0_vol", C.c_double), ("dt", C.c_double),
                 ("sigma", C.c_double), ("euler", C.c_double), ("inv_re", C.c_double),
                 ("c_force", C.c_double), ("body_force", C.c_double), ("u_center", C.c_double),
-                ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double)]
+                ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double),
+                ("gamma_levels", C.c_double * 8)]
 
 
 class bfibm_stats(C.Structure):
@@ -75,6 +76,7 @@ SIGNATURES = {
     "bfibm_get_field": [_V, _i, _i, _i, _DP],
     "bfibm_set_field": [_V, _i, _i, _i, _DP],
     "bfibm_tma_plan": [_V, _i, _i, _IP],
+    "bfibm_set_gamma": [_V, _DP],
     "bfibm_state_bytes": [_V, C.POINTER(_L)],
     "bfibm_save_state": [_V, _V, _L],
     "bfibm_load_state": [_V, _V, _L],
@@ -149,6 +151,8 @@ def make_params(prm):
               "sigma", "euler", "inv_re", "c_force", "body_force", "u_center", "ic_scale", "rtol",
               "gamma_coarse"):
         setattr(P, k, float(prm[k]))
+    for l, v in enumerate(prm.get("gamma_levels", [])[:8]):
+        P.gamma_levels[l] = float(v)
     return P
 
 
@@ -300,6 +304,13 @@ class Context:
         a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape(level))
         self._chk(self.lib.bfibm_set_field(self.h, FIELD[which], comp, level, _dp(a)),
                   "bfibm_set_field")
+
+    def set_gamma(self, gamma_levels):
+        """gamma_lh per coarse level (index 1 = grid 2h; 0 falls back to
+        gamma_coarse); see bfibm_set_gamma."""
+        g = np.zeros(8)
+        g[:len(gamma_levels)] = gamma_levels
+        self._chk(self.lib.bfibm_set_gamma(self.h, _dp(g)), "bfibm_set_gamma")
 
     def save_state(self):
         """The checkpoint of the evolving state as a uint8 array (see

@@ -128,6 +128,10 @@ const char* validate(const bfibm_params* p) {
     return "bad V-cycle counts";
   if (p->precision != 0 && p->precision != 1) return "precision must be 0 or 1";
   if (!(p->inv_re >= 0.0)) return "inv_re must be >= 0";
+  if (!(p->gamma_coarse > 0.0) || !std::isfinite(p->gamma_coarse)) return "gamma_coarse must be > 0";
+  for (int l = 0; l < 8; ++l)
+    if (!(p->gamma_levels[l] >= 0.0) || !std::isfinite(p->gamma_levels[l]))
+      return "gamma_levels entries must be >= 0";
   return nullptr;
 }
 
@@ -681,9 +685,13 @@ void stage_springs(bfibm_ctx* c) { launch_springs(c->D, c->lev[0].g, c->N, c->S,
 void build_coefficients(bfibm_ctx* c) {
   Level& L0 = c->lev[0];
   launch_coef_fine(c->D, L0.g, c->rho, L0.d.beta, L0.d.m, c->P.sigma / c->P.dt, c->stream);
-  for (int l = 1; l < c->L; ++l)
-    launch_coef_restrict(c->D, c->lev[l - 1].g, c->lev[l].g, c->lev[l - 1].d, c->lev[l].d,
-                         c->P.gamma_coarse, c->stream);
+  for (int l = 1; l < c->L; ++l) {
+    // Eq. (ViscCoarseGrid): gamma_lh may differ per coarse grid
+    const double gam = (l < 8 && c->P.gamma_levels[l] > 0.0) ? c->P.gamma_levels[l]
+                                                              : c->P.gamma_coarse;
+    launch_coef_restrict(c->D, c->lev[l - 1].g, c->lev[l].g, c->lev[l - 1].d, c->lev[l].d, gam,
+                         c->stream);
+  }
   if (c->P.precision == 1) {
     launch_v_diag(c->D, L0.g, L0.d, c->vdiag, c->P.inv_re, c->stream);
     for (int l = 0; l < c->L; ++l)
@@ -1386,7 +1394,8 @@ bfibm_status bfibm_stage(bfibm_ctx* c, int stage) {
 bfibm_status bfibm_solve_pressure(bfibm_ctx* c, int ncycles, int32_t* cycles) {
   READY(c);
   int used = 0;
-  bfibm_status st = solve_p(c, ncycles, &used);
+  bfibm_status st = c->P.precision == 1 ? solve_p_mixed(c, ncycles, &used)
+                                        : solve_p(c, ncycles, &used);
   if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
   c->cycles_p = used;
   if (cycles) *cycles = used;
@@ -1395,10 +1404,26 @@ bfibm_status bfibm_solve_pressure(bfibm_ctx* c, int ncycles, int32_t* cycles) {
   return st;
 }
 
+bfibm_status bfibm_set_gamma(bfibm_ctx* c, const double gamma_levels[8]) {
+  READY(c);
+  if (!gamma_levels) return set_err(c, BFIBM_EINVAL, "gamma_levels is NULL");
+  for (int l = 0; l < 8; ++l)
+    if (!(gamma_levels[l] >= 0.0) || !std::isfinite(gamma_levels[l]))
+      return set_err(c, BFIBM_EINVAL, "gamma_levels entries must be >= 0");
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  for (int l = 0; l < 8; ++l) c->P.gamma_levels[l] = gamma_levels[l];
+  build_coefficients(c);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return BFIBM_OK;
+}
+
 bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles) {
   READY(c);
   int used = 0;
-  bfibm_status st = solve_v(c, ncycles, &used);
+  bfibm_status st = c->P.precision == 1 ? solve_v_mixed(c, ncycles, &used)
+                                        : solve_v(c, ncycles, &used);
   if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
   c->cycles_visc = used;
   if (cycles) *cycles = used;

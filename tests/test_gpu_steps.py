@@ -246,3 +246,24 @@ def test_checkpoint_resume_bit_identical(precision):
     a.close()
     b.close()
     other.close()
+
+
+def test_per_level_gamma_parity():
+    # Eq. (ViscCoarseGrid) with a different gamma_lh on each coarse grid
+    inst = W.c2()
+    run_pair(inst, 4, {"gamma_levels": [0.0, 0.7, 0.9, 0.8, 1.0, 0.75]}, chunk=2)
+
+
+def test_gamma_tuner_never_needs_more_cycles():
+    from paper_1302_3663_gb300 import tuning
+    inst = W.c2()
+    c = bfibm.load_instance(inst, prm_override={"vc_visc": 0, "vc_p": 0, "rtol": 1e-9,
+                                                "max_cycles": 80, "precision": 1})
+    c.set_option(bfibm.OPT_GRAPH, 0)
+    c.step(1)
+    g, before, after = tuning.tune_gamma(c, candidates=(0.7, 1.0))
+    assert after <= before
+    assert all(0.0 < x <= 1.0 for x in g[1:c.levels])
+    c.step(1)   # the tuned hierarchy steps on
+    assert c.get_stats()["res_visc"] <= 1e-9
+    c.close()

@@ -205,3 +205,21 @@ def test_paper_break_rule_twice_rest_length():
     assert abs(np.linalg.norm(o.node_forces()[0]) - Fmax) < 1e-14
     o = two_node(np.array([2 * r * (1 + 1e-9), 0.0]), rest=r, K=Fmax / r, brk=1.0)
     assert len(o.broken()[0]) == 1
+
+
+def test_per_level_gamma_scales_coarse_viscosity():
+    # Eq. (ViscCoarseGrid): mu_lh = gamma_lh I(mu_(l/2)h). Restriction is
+    # linear, so halving gamma on the grid 2h alone halves mu_c there and on
+    # every coarser grid (whose own gamma stays 1).
+    inst = W.c2()
+    mu = []
+    for gl in ([], [0.0, 0.5]):
+        prm = dict(inst["params"], gamma_coarse=1.0, gamma_levels=gl)
+        o = O.Oracle(prm)
+        o.set_nodes(inst["X"])
+        o.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+        o.refresh()
+        mu.append([o.get("muc", 0, l) for l in range(3)])
+    assert np.array_equal(mu[0][0], mu[1][0])
+    for l in (1, 2):
+        assert np.max(np.abs(mu[1][l] - 0.5 * mu[0][l])) <= 1e-15 * np.max(np.abs(mu[0][l]))
