@@ -3,12 +3,13 @@
 // once per colour.
 //
 // A block owns full x rows, TY rows of the row axis (y in 3D) and a chunk of
-// planes along the streaming axis (z in 3D, y in 2D). It walks the chunk
-// plane by plane: first the new red values of plane k on its rows plus one
-// ring row on each side (red points depend only on old black values), kept in
-// a three-plane shared-memory ring; then the black values of plane k-1, which
-// need the new red values of planes k-2, k-1, k. The sweep is out of place:
-// old values are read from one buffer and both colours are written to
+// planes along the streaming axis (z in 3D, y in 2D). It walks the chunk NP
+// planes at a time: first the new red values of NP planes on its rows plus
+// one ring row on each side (red points depend only on old black values, so
+// the NP updates are independent), kept in a ring of NP + 2 planes in shared
+// memory; then the black values of the NP planes one behind, which need the
+// new red values of the planes below, at and above them. The sweep is out of
+// place: old values are read from one buffer and both colours are written to
 // another, so neighbouring blocks (which recompute the shared ring rows and
 // the first plane of a chunk) never read a value another block has already
 // replaced. The arithmetic of every point update is that of the two-kernel

@@ -1,22 +1,25 @@
 // Red-black Gauss-Seidel sweeps (Sec. 3.5) with their inputs staged in
-// shared memory by the Tensor Memory Accelerator: the 3D FP32 smoother of the
-// mixed-precision V-cycles.
+// shared memory by the Tensor Memory Accelerator: an alternative 3D FP32
+// smoother of the mixed-precision V-cycles, and the autotuner that chooses,
+// per level shape and sweep kind, between it and the one-pass sweep of
+// smooth.cu (and the one-pass sweep's tile shape).
 //
 // The arithmetic of every point update is that of the two-kernel sweep in
-// stencil.cu and of the ring-fused sweep in smooth.cu; only the data movement
-// differs. A block owns TY full x rows of the y axis and walks a chunk of
-// planes along z. For every plane one elected thread issues one tiled TMA copy
-// per input array (a box of TY + 4 rows of one plane: two halo rows on each
-// side) into a window of plane slots, two planes ahead of the computation;
-// completion is tracked by transaction-count mbarriers. Red values of a plane
-// (on the block's rows plus one ring row each side) depend only on old black
-// values and go to a three-plane ring; the black values of the plane before
-// then read their red neighbours from the ring. The sweep is out of place.
+// stencil.cu and of the one-pass sweep; only the data movement differs. A
+// block owns a strip of x (64 columns or whole rows), TY rows of y and a
+// chunk of planes along z. For every plane one elected thread issues one
+// tiled TMA copy per input array (a box of TY + 4 rows and the strip plus
+// four halo columns each side) into a window of plane slots, up to three
+// planes ahead of the computation; completion is tracked by
+// transaction-count mbarriers. Each phase computes the red values of plane k
+// (on the block's rows and columns plus one ring row / column each side,
+// from old black values) into a four-plane ring and, independently, the black
+// values of plane k - 2 from the ring; one barrier separates phases. The
+// sweep is out of place.
 //
-// Blocks are persistent: block b takes the work items (row tile, plane chunk)
-// b, b + G, b + 2G, ..., so the items in flight at any moment are neighbours
-// and share their halo rows through L2. Tile height, chunk length and grid
-// size come from a timing autotuner run once per level shape.
+// Blocks are persistent: block b takes the work items (strip, row tile,
+// plane chunk) b, b + G, b + 2G, ..., so the items in flight at any moment are
+// neighbours and share their halo rows through L2.
 //
 // Every wait on an mbarrier is bounded (2 s of the global timer); a block
 // whose wait runs out raises the error word, drains its own copies in flight

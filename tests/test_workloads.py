@@ -1,4 +1,4 @@
-"""The seeded input generators: deterministic, and shaped as the configs state."""
+"""The seeded input generators: deterministic, and shaped as the workloads are defined."""
 import numpy as np
 from scipy.spatial import cKDTree
 
