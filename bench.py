@@ -70,11 +70,12 @@ def parse():
     ap.add_argument("--tma", type=int, choices=[0, 1, 2], default=1,
                     help="FP32 sweeps with TMA-staged inputs: 0 never, 1 where the autotuner "
                          "timed them faster (default), 2 wherever a level allows")
-    ap.add_argument("--study", choices=["gamma", "work_units"], default=None,
+    ap.add_argument("--study", choices=["gamma", "work_units", "refinement"], default=None,
                     help="gamma: tune the coarse viscosity scaling per level (Eq. "
                          "ViscCoarseGrid) on the workload and time a step before and after; "
                          "work_units: cycles and work units of one solve against the number "
-                         "of multigrid levels (Sec. 4.3.1)")
+                         "of multigrid levels (Sec. 4.3.1); refinement: convergence rates in "
+                         "time and space (Sec. 4.3.2-4.3.3) on the GPU")
     ap.add_argument("--no-tune-gamma", action="store_true",
                     help="keep one coarse viscosity scaling for every level instead of tuning "
                          "it per level before the timed region")
@@ -633,6 +634,18 @@ def run_study(args):
             for which in ("pressure", "viscous"):
                 out["rows"]["%s_%s" % (name, which)] = tuning.work_units_vs_levels(
                     inst, levels, which=which)
+        print(json.dumps(out))
+        return
+    if args.study == "refinement":
+        from paper_1302_3663_gb300 import refinement as R
+        solver = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-12, "max_cycles": 300, "precision": 0}
+        out = {"study": "refinement", "solver": solver,
+               "spin_up_time_256x128": R.temporal_rates(W.spin_up_channel(256), T=0.02,
+                                                        dt0=2e-3, nruns=5, solver=solver),
+               "spin_up_space": R.spatial_rates(W.spin_up_channel, [32, 64, 128, 256, 512],
+                                                T=0.02, dt=1e-3, solver=solver),
+               "biofilm_c1_time": R.temporal_rates(W.c1(), T=0.02, dt0=2e-3, nruns=5,
+                                                   solver=solver)}
         print(json.dumps(out))
         return
     inst = load_workload(args.config, args.precision, args)

@@ -279,6 +279,17 @@ def paper_units_duct(e=64, nodes=1500, f_max=0.5, seed=7):
                 K=f_max / np.maximum(rest, 1e-12), brk=np.full(len(rest), 1.0), steps=20)
 
 
+def spin_up_channel(n=64):
+    """2D channel of n x n/2 cells (periodic along the flow, walls across),
+    started from half the Poiseuille profile and driven by the body force
+    towards the full one; uniform fluid, no nodes. Smooth in space and time:
+    the flow of the refinement studies (Sec. 4.3.2-4.3.3)."""
+    h = 1.0 / n
+    prm = base_params(2, (n, n // 2), (1, 0), 0, h, rho_ratio=1.5, mu_ratio=100.0,
+                      omega=0.01, omega_mu=0.01, ic_scale=0.5, mu_f=1.0)
+    return _instance(prm, np.zeros((0, 2)), 0.01, 1.0, 0.5, 20, "spin_up")
+
+
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "paper_units": paper_units_duct}
 
 
