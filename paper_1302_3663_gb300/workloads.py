@@ -290,6 +290,22 @@ def spin_up_channel(n=64):
     return _instance(prm, np.zeros((0, 2)), 0.01, 1.0, 0.5, 20, "spin_up")
 
 
+def mound_2d(n=64, rho_ratio=1.0, mu_ratio=1.0, omega=0.02, seed=0):
+    """The refinement-study mound (Sec. 4.3.3): the 2D channel of c1 on an
+    n x n/2 grid with the same 150 nodes in every resolution (the Lagrangian
+    points are not refined with the grid), delta width omega = 1/50, and a
+    biofilm that is fluid-like (ratios 1), twice as dense (rho_ratio 2) or
+    500 times as viscous (mu_ratio 500)."""
+    h = 1.0 / n
+    r = 0.01
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X, spacing = dart_throw(rng, 150, 2, (0.5, 0.0), 0.1, 2 * r)
+    area = math.pi * 0.1 ** 2 / 2.0
+    prm = base_params(2, (n, n // 2), (1, 0), 0, h, rho_ratio=rho_ratio, mu_ratio=mu_ratio,
+                      omega=omega, omega_mu=omega, d0_vol=area / 150)
+    return _instance(prm, X, r, 1.0, 0.5, 20, "mound_2d", dict(spacing=spacing))
+
+
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "paper_units": paper_units_duct}
 
 

@@ -110,6 +110,19 @@ def test_spatial_rate_of_the_spin_up_is_second_order():
     assert 1.6 <= x["u_inf"] <= 2.2, r["rates"]
 
 
+def test_mound_converges_under_grid_refinement():
+    """The mound with the same nodes on every grid (Sec. 4.3.3): the errors in
+    u and X fall as h halves, at least first order in X for the L2 norm, as
+    in the paper's constant-coefficient refinement table."""
+    r = R.spatial_rates(W.mound_2d, [16, 32, 64, 128], T=0.01, dt=1e-4,
+                        backend=oracle_backend, solver=SOLVER)
+    e = r["errors"]
+    for a, b in zip(e[:-1], e[1:]):
+        assert b["u_2"] < a["u_2"] and b["X_2"] < a["X_2"], e
+    for x in r["rates"]:
+        assert 1.0 <= x["X_2"] <= 2.5, r["rates"]
+
+
 def _same_study(a, b, rel):
     for ea, eb in zip(a["errors"], b["errors"]):
         for k in ("u_2", "u_inf", "X_2", "X_inf"):
