@@ -36,8 +36,10 @@ UNIT = "cell-steps/s"
 # Solves run to a relative residual of 1e-11, which leaves max |div u| below
 # 1e-10 after every projection; coarse-grid viscosity scaled by gamma = 0.8
 # (Eq. ViscCoarseGrid, inside the recommended [0.7, 1]); V(3,3) cycles.
+# inner_cycles: FP32 V-cycles per FP64 residual in mixed precision (ignored by
+# the FP64 path)
 TOL_SOLVER = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 100, "gamma_coarse": 0.8,
-              "nu1": 3, "nu2": 3}
+              "nu1": 3, "nu2": 3, "inner_cycles": 3}
 DIV_TARGET = 1e-10
 
 
@@ -106,9 +108,11 @@ def describe(inst):
     gl = [g for g in p.get("gamma_levels", [])[1:] if g > 0]
     vc = ("%d viscous + %d pressure V(%d,%d) cycles per step" %
           (p["vc_visc"], p["vc_p"], p["nu1"], p["nu2"]) if p["vc_visc"] > 0
-          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %s"
+          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %s%s"
           % (p["nu1"], p["nu2"], p["rtol"],
-             ("%s per level (tuned)" % gl) if gl else "%g" % p["gamma_coarse"]))
+             ("%s per level (tuned)" % gl) if gl else "%g" % p["gamma_coarse"],
+             (", %d FP32 V-cycles per FP64 residual" % p["inner_cycles"])
+             if p.get("precision", 0) == 1 and p.get("inner_cycles", 1) > 1 else ""))
     return {
         "workload": "%s: %s grid, %d nodes, %d springs, density ratio %g, viscosity ratio %g"
                     % (inst["name"], "x".join(map(str, n)), inst["X"].shape[0],

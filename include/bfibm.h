@@ -230,8 +230,20 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
    tensor-memory-accelerator copies: 0 never, the one-pass sweep reads them
    from global memory; 1, the default, on the levels and components where the
    autotuner timed them faster; 2 on every level that allows them; all give
-   bit-identical results). Every option gives the same results to rounding. */
-enum { BFIBM_OPT_STATS = 0, BFIBM_OPT_GRAPH = 1, BFIBM_OPT_FUSED = 2, BFIBM_OPT_TMA = 3 };
+   bit-identical results), BFIBM_OPT_INNER (mixed precision: FP32 V-cycles per
+   FP64 defect-correction iteration, 1 to 16, default 1; each FP64 residual is
+   then followed by that many V-cycles on the FP32 correction equation, so a
+   solve computes fewer FP64 residuals for the same V-cycles; a tolerance
+   solve stops after a multiple of it). Every option but BFIBM_OPT_INNER gives
+   the same results to rounding; BFIBM_OPT_INNER changes the iterates within
+   the solver tolerance. */
+enum {
+  BFIBM_OPT_STATS = 0,
+  BFIBM_OPT_GRAPH = 1,
+  BFIBM_OPT_FUSED = 2,
+  BFIBM_OPT_TMA = 3,
+  BFIBM_OPT_INNER = 4
+};
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Checkpoint and resume. The state a time step starts from (Sec. 3.4): the
    velocity u^n, the pressure (the next projection's initial guess), the node

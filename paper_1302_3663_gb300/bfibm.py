@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTAT
 FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
          "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
-OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA = 0, 1, 2, 3
+OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER = 0, 1, 2, 3, 4
 
 
 class BfibmError(RuntimeError):
@@ -204,6 +204,10 @@ class Context:
         nl = C.c_int32(0)
         self.lib.bfibm_levels(self.h, C.byref(nl))
         self.levels = nl.value
+        # FP32 V-cycles per FP64 defect-correction iteration (an option of the
+        # context, not a field of bfibm_params)
+        if int(prm.get("inner_cycles", 1)) != 1:
+            self.set_option(OPT_INNER, int(prm["inner_cycles"]))
 
     def _chk(self, st, what, allow=(OK,)):
         if st not in allow:

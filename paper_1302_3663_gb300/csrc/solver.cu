@@ -174,7 +174,9 @@ struct bfibm_ctx {
   bool dirty = true;
   int poisoned = 0;
   long long step_host = 0;
+  int inner = 1;                 // FP32 V-cycles per FP64 defect-correction iteration
   int cycles_visc = 0, cycles_p = 0;
+  int loop_inner[2] = {1, 1};    // V-cycles per device-loop iteration (visc, p) when captured
   long long graph_kernels = -1;   // kernel nodes in the captured step graph
   long long partial_cap = 0;      // doubles in sc.partial
   std::string err;
@@ -380,6 +382,7 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
   }
   if (c->capturing) {
     cudaMemsetAsync(c->dev_cycles + 1, 0, sizeof(int), s);
+    c->loop_inner[1] = 1;
     bfibm_status cs = capture_while(c, 1, [&](cudaGraphConditionalHandle h) {
       vcycle_p(c, 0);
       launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, c->stream);
@@ -427,6 +430,7 @@ bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
   }
   if (c->capturing) {
     cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
+    c->loop_inner[0] = 1;
     bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
       vcycle_v(c, 0);
       launch_v_residual<double>(c->D, L0.g, L0.d, c->P.inv_re, c->stream);
@@ -552,38 +556,47 @@ void vcycle_v32(bfibm_ctx* c, int l) {
   smooth_v32(c, l, c->P.nu2);
 }
 
-// Defect correction: r = f - A x in FP64 (handed to FP32), one FP32 V-cycle
-// for the correction, x += e in FP64; ncycles > 0 fixed, else until rtol.
+// Defect correction: r = f - A x in FP64 (handed to FP32), c->inner FP32
+// V-cycles for the correction of A e = r (the first from e = 0, each next one
+// from the last iterate: the same V-cycles in exact arithmetic, one FP64
+// residual per `inner` of them), x += e in FP64. ncycles > 0: that many
+// V-cycles; else until rtol, with max_cycles V-cycles at most. Returns the
+// V-cycles used (a multiple of c->inner in tolerance mode).
+inline int dc_iterations(int vcycles, int inner) { return (vcycles + inner - 1) / inner; }
+
 bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
   Level& L0 = c->lev[0];
   cudaStream_t s = c->stream;
   double* one[3] = {L0.d.pf, nullptr, nullptr};
   bool tol = ncycles <= 0;
+  const int inner = c->inner;
   int nb = red_blocks_3d(c->D, L0.g);
   if (tol || c->collect_stats) launch_norm2(c->D, L0.g, one, 0, c->sc, SL_PF, s);
-  int maxc = tol ? c->P.max_cycles : ncycles;
+  int vmax = tol ? c->P.max_cycles : ncycles;
+  int maxc = dc_iterations(vmax, inner);
   bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
   double* xs[3] = {L0.d.p, nullptr, nullptr};
   float* es[3] = {L0.f.p, nullptr, nullptr};
   if (tol && c->capturing) {
     cudaMemsetAsync(c->dev_cycles + 1, 0, sizeof(int), s);
     launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, nullptr, s);
+    c->loop_inner[1] = inner;
     bfibm_status cs = capture_while(c, 1, [&](cudaGraphConditionalHandle h) {
       cudaStream_t b = c->stream;
-      vcycle_p32(c, 0);
+      for (int q = 0; q < inner; ++q) vcycle_p32(c, 0);
       xs[0] = L0.d.p;
       es[0] = L0.f.p;
       launch_add_correction(c->D, L0.g, xs, es, 0, b);
       launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, b);
       launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, b);
-      launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1,
+      launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, maxc, c->dev_cycles + 1,
                        c->loop_total + 1, b);
     });
     *used = -1;
     return cs;
   }
-  int k = 0;
+  int k = 0, vdone = 0;
   for (k = 1; k <= maxc; ++k) {
     launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, tol ? c->sc.partial : nullptr, s);
     if (tol) {
@@ -593,22 +606,22 @@ bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
       double fn = std::sqrt(c->host_sc[SL_PF]), rn = std::sqrt(c->host_sc[SL_PR]);
       if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) {
         st = BFIBM_OK;
-        k -= 1;
         break;
       }
     }
-    vcycle_p32(c, 0);
+    const int nv = tol ? inner : std::min(inner, ncycles - vdone);
+    for (int q = 0; q < nv; ++q) vcycle_p32(c, 0);
+    vdone += nv;
     xs[0] = L0.d.p;
     es[0] = L0.f.p;
     launch_add_correction(c->D, L0.g, xs, es, 0, s);
     launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
   }
-  if (k > maxc) k = maxc;
   if (c->collect_stats || tol) {
     launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, c->sc.partial, s);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, s);
   }
-  *used = k;
+  *used = vdone;
   return st;
 }
 
@@ -616,26 +629,29 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   Level& L0 = c->lev[0];
   cudaStream_t s = c->stream;
   bool tol = ncycles <= 0;
+  const int inner = c->inner;
   int nb = red_blocks_3d(c->D, L0.g);
   if (tol || c->collect_stats) launch_norm2(c->D, L0.g, L0.d.uf, c->D, c->sc, SL_VF, s);
-  int maxc = tol ? c->P.max_cycles : ncycles;
+  int vmax = tol ? c->P.max_cycles : ncycles;
+  int maxc = dc_iterations(vmax, inner);
   bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
   if (tol && c->capturing) {
     cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
     launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, nullptr, s);
+    c->loop_inner[0] = inner;
     bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
       cudaStream_t b = c->stream;
-      vcycle_v32(c, 0);
+      for (int q = 0; q < inner; ++q) vcycle_v32(c, 0);
       launch_add_correction(c->D, L0.g, L0.d.u, L0.f.u, c->D, b);
       launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
-      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles,
+      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, maxc, c->dev_cycles,
                        c->loop_total, b);
     });
     *used = -1;
     return cs;
   }
-  int k = 0;
+  int k = 0, vdone = 0;
   for (k = 1; k <= maxc; ++k) {
     launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re,
                             tol ? c->sc.partial : nullptr, s);
@@ -646,19 +662,19 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
       double fn = std::sqrt(c->host_sc[SL_VF]), rn = std::sqrt(c->host_sc[SL_VR]);
       if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) {
         st = BFIBM_OK;
-        k -= 1;
         break;
       }
     }
-    vcycle_v32(c, 0);
+    const int nv = tol ? inner : std::min(inner, ncycles - vdone);
+    for (int q = 0; q < nv; ++q) vcycle_v32(c, 0);
+    vdone += nv;
     launch_add_correction(c->D, L0.g, L0.d.u, L0.f.u, c->D, s);
   }
-  if (k > maxc) k = maxc;
   if (c->collect_stats || tol) {
     launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, c->sc.partial, s);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
   }
-  *used = k;
+  *used = vdone;
   return st;
 }
 
@@ -1318,8 +1334,8 @@ bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
     int cyc[2];
     CK(cudaMemcpyAsync(cyc, c->dev_cycles, sizeof(cyc), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (c->cycles_visc < 0) out->cycles_visc = cyc[0];
-    if (c->cycles_p < 0) out->cycles_p = cyc[1];
+    if (c->cycles_visc < 0) out->cycles_visc = cyc[0] * c->loop_inner[0];
+    if (c->cycles_p < 0) out->cycles_p = cyc[1] * c->loop_inner[1];
   }
   out->broken_total = std::min<int>(cnt[1], (int)std::max<long long>(c->S.m, 0));
   out->clamped_total = cnt[0];
@@ -1655,6 +1671,10 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
   } else if (option == BFIBM_OPT_TMA) {
     if (value < 0 || value > 2) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_TMA takes 0, 1 or 2");
     c->tma = (int)value;
+  } else if (option == BFIBM_OPT_INNER) {
+    if (value < 1 || value > 16)
+      return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_INNER takes 1 to 16");
+    c->inner = (int)value;
   } else {
     return set_err(c, BFIBM_EINVAL, "unknown option");
   }

@@ -32,6 +32,10 @@ def tune_gamma(ctx, candidates=GAMMA_CANDIDATES, passes=1):
     g = [0.0] * 8
     for l in range(1, nlev):
         g[l] = float(given[l]) if given[l] > 0 else base
+    # count single V-cycles (several per FP64 residual would round the counts
+    # up to their multiple)
+    inner = int(ctx.prm.get("inner_cycles", 1))
+    ctx.set_option(bfibm.OPT_INNER, 1)
     ctx.stage("rhs")
     u0 = [ctx.get_velocity(d) for d in range(ctx.dim)]
     ctx.set_gamma(g)
@@ -48,6 +52,7 @@ def tune_gamma(ctx, candidates=GAMMA_CANDIDATES, passes=1):
                 if cyc < best:
                     best, g = cyc, trial
     ctx.set_gamma(g)
+    ctx.set_option(bfibm.OPT_INNER, inner)
     # leave the viscous iterate as the step would find it
     for d in range(ctx.dim):
         ctx.set_field("ut", u0[d], d, 0)
