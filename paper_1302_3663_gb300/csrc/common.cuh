@@ -92,6 +92,8 @@ void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaS
 template <typename T>
 void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
                        cudaStream_t s, int TYo = 0, int KCo = 0, int NPo = 1);
+// chunk planes filling `waves` waves of resident blocks (3D FP32 sweeps; 0: none)
+int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int waves);
 
 // Mixed precision (mixed.cu).
 int red_blocks_3d(int D, const Geo& g);

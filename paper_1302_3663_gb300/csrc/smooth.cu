@@ -501,6 +501,31 @@ cudaError_t fused_set_carveout() {
   return e;
 }
 
+// Chunk planes that give `waves` full waves of resident blocks for the 3D
+// FP32 sweep of kind K (0..2 viscous components, 3 pressure) with TY tile
+// rows; 0 where the occupancy cannot be had.
+int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int waves) {
+  if (D != 3) return 0;
+  FusedShape f = fused_shape<float>(D, g, TY, 0, NP);
+  const void* fn;
+  if (K == 3) fn = NP == 2 ? (const void*)k_p_rb_fused<3, float, 2> : (const void*)k_p_rb_fused<3, float, 1>;
+  else if (K == 0) fn = NP == 2 ? (const void*)k_v_rb_fused<3, 0, float, 2> : (const void*)k_v_rb_fused<3, 0, float, 1>;
+  else if (K == 1) fn = NP == 2 ? (const void*)k_v_rb_fused<3, 1, float, 2> : (const void*)k_v_rb_fused<3, 1, float, 1>;
+  else fn = NP == 2 ? (const void*)k_v_rb_fused<3, 2, float, 2> : (const void*)k_v_rb_fused<3, 2, float, 1>;
+  int bps = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, (int)(f.block.x * f.block.y * f.block.z),
+                                                    f.smem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  long long chunks = (long long)waves * nsm * bps / (long long)f.grid.x;
+  if (chunks < 1) return 0;
+  int KC = (int)((g.n[2] + chunks - 1) / chunks);
+  return KC < 2 ? 2 : KC;
+}
+
 size_t fused_smem_bytes(int D, const Geo& g, int elem) {
   return elem == 8 ? fused_shape<double>(D, g).smem : fused_shape<float>(D, g).smem;
 }

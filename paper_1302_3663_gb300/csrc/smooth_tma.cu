@@ -661,7 +661,19 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
   for (int rTY : {0, 2, 4, 6, 8}) {
     if ((rTY == 0) == search) continue;
     if (rTY > g.n[1] || bx * (rTY + 2) > 1024) continue;
-    for (int rKC : {8, 16, 32}) {
+    // fixed chunk sizes, and the sizes that fill one or two waves of resident
+    // blocks exactly
+    int kcs_ring[5] = {8, 16, 32, 0, 0};
+    if (search && rTY > 0) {
+      kcs_ring[3] = ring_fill_kc(D, K, g, rTY, rNP, 1);
+      kcs_ring[4] = ring_fill_kc(D, K, g, rTY, rNP, 2);
+    }
+    for (int ci = 0; ci < 5; ++ci) {
+      const int rKC = kcs_ring[ci];
+      if (rKC <= 0) continue;
+      bool seen = false;
+      for (int cj = 0; cj < ci; ++cj) seen = seen || kcs_ring[cj] == rKC;
+      if (seen) continue;
       if (!search && rKC != 8) continue;
       if (search && rKC > g.n[2] && rKC != 8) continue;
       auto ring = [&]() {
