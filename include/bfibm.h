@@ -117,7 +117,10 @@ enum {
   BFIBM_F_BETA = 9,    /* 1/rho on the comp-faces (restricted on coarse levels) */
   BFIBM_F_M = 10,      /* rho sigma / dt on the comp-faces */
   BFIBM_F_URES = 11,   /* viscous residual, component comp */
-  BFIBM_F_PRES = 12    /* pressure residual */
+  BFIBM_F_PRES = 12,   /* pressure residual */
+  BFIBM_F_IDG = 13     /* FP32 only: 1 / diagonal of the viscous operator, component
+                          comp (formed from the FP64 coefficients when they are built;
+                          0 on the fixed wall faces) */
 };
 
 /* Stage selectors for bfibm_stage. */
@@ -180,7 +183,7 @@ bfibm_status bfibm_get_field_dev(bfibm_ctx* c, int which, int comp, int level, d
 bfibm_status bfibm_set_field_dev(bfibm_ctx* c, int which, int comp, int level, const double* dev);
 /* FP32 copies of the multigrid arrays used by the mixed-precision V-cycles
    (precision 1 only): which is one of BFIBM_F_UT, URHS, P, PRHS, MUC, MUE,
-   BETA, M, URES, PRES (on level 0, UT/URHS/P/PRHS hold the FP32 correction
+   BETA, M, URES, PRES, IDG (on level 0, UT/URHS/P/PRHS hold the FP32 correction
    and its right-hand side). Same layout as bfibm_get_field, in floats; host
    buffers; BFIBM_EINVAL for another selector or an FP64-only context. */
 bfibm_status bfibm_get_field_f32(bfibm_ctx* c, int which, int comp, int level, float* out);

@@ -19,7 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTATE"]
 
 FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
-         "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12}
+         "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12, "idg": 13}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
 OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER = 0, 1, 2, 3, 4
 

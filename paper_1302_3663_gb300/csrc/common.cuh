@@ -42,6 +42,7 @@ struct LevelPtrs {
   T* mue[3];     // mu on edges: xy, xz, yz
   T* p2;         // second buffer of p for out-of-place sweeps
   T* u2[3];      // second buffers of u
+  T* idg[3];     // FP32 sweeps: 1 / diagonal of the viscous operator of component d
 };
 
 struct Ptr3d {
@@ -109,6 +110,10 @@ void launch_add_correction(int D, const Geo& g, double* const x[3], float* const
                            cudaStream_t s);
 void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
 void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
+// 1 / diagonal of the viscous operator per face component, from the FP64
+// coefficients of one level, stored in L32.idg (0 on the fixed wall faces)
+void launch_v_idg32(int D, const Geo& g, const LevelPtrs<double>& L64,
+                    const LevelPtrs<float>& L32, double ir, cudaStream_t s);
 void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
                         const LevelPtrs<float>& L32, cudaStream_t s);
 // out[slot] = scale * sum(partial[0..nb))

@@ -135,6 +135,35 @@ __global__ void __launch_bounds__(256) k_v_diag(Geo g, LevelPtrs<double> L, Ptr3
   }
 }
 
+struct F32x3 {
+  float* a[3];
+};
+
+// 1 / diagonal per face component for the FP32 sweeps: formed in FP64 from
+// the level's FP64 coefficients, rounded once to FP32.
+template <int D>
+__global__ void __launch_bounds__(256) k_v_idg32(Geo g, LevelPtrs<double> L, F32x3 idg,
+                                                 double ir) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  int ci[3] = {i, j, k};
+  long long F = gidx(g, i, j, k);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    float v = 0.f;
+    if (g.per[d] || ci[d] != 0) {
+      double dg;
+      if (d == 0) dg = v_diag64<D, 0>(g, L, ci, F, ir);
+      else if (d == 1) dg = v_diag64<D, 1>(g, L, ci, F, ir);
+      else dg = v_diag64<D, (D == 3 ? 2 : 1)>(g, L, ci, F, ir);
+      v = (float)(1.0 / dg);
+    }
+    idg.a[d][F] = v;
+  }
+}
+
 // FP64 viscous residual of component d at face F with the diagonal read from
 // `diag` (the same arithmetic as the FP64 residual kernel). INTERIOR: no
 // neighbour lies beyond a wall or across a periodic seam, so the offsets are
@@ -172,10 +201,6 @@ __device__ __forceinline__ double v_res64d(const Geo& g, const LevelPtrs<double>
   }
   return L.uf[d][F] - diag[F] * ud[F] + ir * off;
 }
-
-struct F32x3 {
-  float* a[3];
-};
 
 template <int D, bool INTERIOR>
 __device__ __forceinline__ double v_res_any(const Geo& g, const LevelPtrs<double>& L,
@@ -324,6 +349,16 @@ void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s
   if (nb > 4096) nb = 4096;
   if (nb < 1) nb = 1;
   k_convert<double, float><<<(unsigned)nb, kBlock1D, 0, s>>>(in, out, n);
+}
+
+void launch_v_idg32(int D, const Geo& g, const LevelPtrs<double>& L64,
+                    const LevelPtrs<float>& L32, double ir, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  F32x3 o;
+  for (int d = 0; d < 3; ++d) o.a[d] = L32.idg[d];
+  if (D == 3) k_v_idg32<3><<<gr, b, 0, s>>>(g, L64, o, ir);
+  else k_v_idg32<2><<<gr, b, 0, s>>>(g, L64, o, ir);
 }
 
 void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,

@@ -13,7 +13,8 @@
 // another, so neighbouring blocks (which recompute the shared ring rows and
 // the first plane of a chunk) never read a value another block has already
 // replaced. The arithmetic of every point update is that of the two-kernel
-// sweep in stencil.cu.
+// sweep in stencil.cu, except that FP32 viscous updates multiply by a
+// precomputed inverse diagonal instead of dividing by the diagonal.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -239,11 +240,17 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
 // come from the coefficient arrays and the (fixed) other components; the u_d
 // neighbours come from the old buffer (red) or the ring (black).
 // ---------------------------------------------------------------------------
+// FP32 sweeps multiply by the precomputed 1 / diagonal (L.idg, formed in
+// FP64 once per step); FP64 sweeps form the diagonal and divide, as the
+// two-kernel sweep does.
+template <typename T>
+constexpr bool kIdg = sizeof(T) == 4;
+
 template <int D, int d, typename T>
 struct VC {
   T cdp, cdm;          // 2 mu_c on the cells beside the face
   T cep[2], cem[2];    // edge mu per other axis (the neighbour beyond a wall is unused)
-  T cross, diag;
+  T cross, diag;       // diag: the diagonal (FP64) or its inverse (FP32)
 };
 
 template <int D, int d, typename T>
@@ -265,10 +272,17 @@ __device__ __forceinline__ void v_coef(const LevelPtrs<T>& L, const Pt& q, T ir,
     v.cross += mep * (ue[Ep] - ue[Ep + od_m]) - mem * (ue[F] - ue[F + od_m]);
     v.cep[k] = mep;
     v.cem[k] = mem;
-    dgV += (q.wp[e] ? T(2) : T(1)) * mep + (q.wm[e] ? T(2) : T(1)) * mem;
+    if constexpr (!kIdg<T>) dgV += (q.wp[e] ? T(2) : T(1)) * mep + (q.wm[e] ? T(2) : T(1)) * mem;
     ++k;
   }
-  v.diag = L.m[d][F] + ir * dgV;
+  if constexpr (kIdg<T>) v.diag = L.idg[d][F];
+  else v.diag = L.m[d][F] + ir * dgV;
+}
+
+template <typename T>
+__device__ __forceinline__ T v_solve(T num, T diag) {
+  if constexpr (kIdg<T>) return num * diag;
+  else return num / diag;
 }
 
 template <int D, int d, typename T>
@@ -285,7 +299,7 @@ __device__ __forceinline__ T v_red(const LevelPtrs<T>& L, const Pt& q, T ir) {
     if (!q.wm[e]) off += v.cem[k] * ud[q.F + q.om[e]];
     ++k;
   }
-  return (L.uf[d][q.F] + ir * off) / v.diag;
+  return v_solve<T>(L.uf[d][q.F] + ir * off, v.diag);
 }
 
 template <int D, int d, typename T>
@@ -304,7 +318,7 @@ __device__ __forceinline__ T v_black(const LevelPtrs<T>& L, const Ring<T>& rg, c
     if (!q.wm[e]) off += v.cem[k] * ring_nb<D, T>(rg, q, i, n0, e, -1, r, sl_m, sl_0, sl_p);
     ++k;
   }
-  return (L.uf[d][q.F] + ir * off) / v.diag;
+  return v_solve<T>(L.uf[d][q.F] + ir * off, v.diag);
 }
 
 template <int D, int d, typename T, int NP>

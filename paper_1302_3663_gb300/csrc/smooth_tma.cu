@@ -4,8 +4,9 @@
 // per level shape and sweep kind, between it and the one-pass sweep of
 // smooth.cu (and the one-pass sweep's tile shape).
 //
-// The arithmetic of every point update is that of the two-kernel sweep in
-// stencil.cu and of the one-pass sweep; only the data movement differs. A
+// The arithmetic of every point update is that of the one-pass sweep (FP32
+// viscous updates multiply by the precomputed inverse diagonal); only the
+// data movement differs. A
 // block owns a strip of x (64 columns or whole rows), TY rows of y and a
 // chunk of planes along z. For every plane one elected thread issues one
 // tiled TMA copy per input array (a box of TY + 4 rows and the strip plus
@@ -47,9 +48,9 @@ constexpr int kTmaThreads = 1024;       // threads per block at most
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr size_t kSmemMax = 225 * 1024;   // dynamic, leaving room for the static words
 
-// Staged arrays. Viscous component d (kinds 0, 1, 2): old u_d, rhs_d, m_d,
-// mu_c, the two edge viscosities of d and the two other components (axes e1 <
-// e2). Pressure (kind 3): old p, rhs, beta_x, beta_y, beta_z.
+// Staged arrays. Viscous component d (kinds 0, 1, 2): old u_d, rhs_d, the
+// inverse diagonal of component d, mu_c, the two edge viscosities of d and the
+// two other components (axes e1 < e2). Pressure (kind 3): old p, rhs, beta_x, beta_y, beta_z.
 __host__ __device__ constexpr int n_staged(int K) { return K == 3 ? 5 : 8; }
 
 // Plane slots: the planes a block still reads at iteration k (k-2 .. k+1:
@@ -268,7 +269,6 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
         constexpr int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
         float mcp = at(3), mcm = sh(3, d, -1, 0, 0);
         float cdp = 2.f * mcp, cdm = 2.f * mcm;
-        float dgV = 2.f * (mcp + mcm);
         float cross = 0.f;
         float cep[2], cem[2];
 #pragma unroll
@@ -280,9 +280,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
                    mem * (at(ue) - sh(ue, d, -1, 0, 0));
           cep[q] = mep;
           cem[q] = mem;
-          dgV += (wp(e) ? 2.f : 1.f) * mep + (wm(e) ? 2.f : 1.f) * mem;
         }
-        float diag = at(2) + c * dgV;
         float off = cross + cdp * nb(d, +1) + cdm * nb(d, -1);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -290,7 +288,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
           if (!wp(e)) off += cep[q] * nb(e, +1);
           if (!wm(e)) off += cem[q] * nb(e, -1);
         }
-        return (at(1) + c * off) / diag;
+        return (at(1) + c * off) * at(2);   // slot 2: 1 / diagonal
       }
     };
     auto on_wall_face = [&](int i, int j, int kw) -> bool {   // fixed zero face of u_d
@@ -539,7 +537,7 @@ bool fill_args(int K, const Geo& g, const LevelPtrs<float>& L, float* out, int* 
     const int d = K, e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
     src[0] = L.u[d];
     src[1] = L.uf[d];
-    src[2] = L.m[d];
+    src[2] = L.idg[d];
     src[3] = L.muc;
     src[4] = L.mue[edge_id(d, e1)];
     src[5] = L.mue[edge_id(d, e2)];

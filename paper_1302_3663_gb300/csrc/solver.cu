@@ -92,8 +92,8 @@ size_t grid_pool_bytes(const bfibm_params& P, int* nlev = nullptr) {
     int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0) +
              (l == 0 && P.precision == 1 ? P.dim : 0);
     bytes += arr * na;
-    if (P.precision == 1)
-      bytes += (size_t)round_up(level_elems(g[l]) * 4, 256) * arrays_per_level(P.dim);
+    if (P.precision == 1)   // the level's arrays and the inverse viscous diagonals
+      bytes += (size_t)round_up(level_elems(g[l]) * 4, 256) * (arrays_per_level(P.dim) + P.dim);
   }
   bytes += 256 * 16;  // G and scalars
   if (nlev) *nlev = L;
@@ -710,8 +710,11 @@ void build_coefficients(bfibm_ctx* c) {
   }
   if (c->P.precision == 1) {
     launch_v_diag(c->D, L0.g, L0.d, c->vdiag, c->P.inv_re, c->stream);
-    for (int l = 0; l < c->L; ++l)
+    for (int l = 0; l < c->L; ++l) {
       launch_coef_to_f32(c->D, c->lev[l].g, c->lev[l].d, c->lev[l].f, c->stream);
+      const double h = c->lev[l].g.h;
+      launch_v_idg32(c->D, c->lev[l].g, c->lev[l].d, c->lev[l].f, c->P.inv_re / (h * h), c->stream);
+    }
   }
 }
 
@@ -844,10 +847,11 @@ float* field_ptr32(bfibm_ctx* c, int which, int comp, int level) {
   if (c->P.precision != 1 || level < 0 || level >= c->L) return nullptr;
   int D = c->D;
   bool vec = (which == BFIBM_F_UT || which == BFIBM_F_URHS || which == BFIBM_F_BETA ||
-              which == BFIBM_F_M || which == BFIBM_F_URES);
+              which == BFIBM_F_M || which == BFIBM_F_URES || which == BFIBM_F_IDG);
   if (vec && (comp < 0 || comp >= D)) return nullptr;
   if (which == BFIBM_F_MUE && (comp < 0 || comp >= edge_count(D))) return nullptr;
   LevelPtrs<float>& L = c->lev[level].f;
+  if (which == BFIBM_F_IDG) return L.idg[comp];
   switch (which) {
     case BFIBM_F_UT: return L.u[comp];
     case BFIBM_F_URHS: return L.uf[comp];
@@ -1025,6 +1029,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
         f.uf[a] = take32(Lv.g);
         f.ur[a] = take32(Lv.g);
         f.m[a] = take32(Lv.g);
+        f.idg[a] = take32(Lv.g);
       }
       f.muc = take32(Lv.g);
       for (int e = 0; e < E; ++e) f.mue[e] = take32(Lv.g);

@@ -31,6 +31,10 @@ def random_inputs(c, rng):
         f[("m", d)] = rng.uniform(0.5, 2.0, c.shape(0))
         f[("beta", d)] = rng.uniform(0.2, 1.0, c.shape(0))
         f[("mue", d)] = np.exp(rng.uniform(np.log(0.01), np.log(10.0), c.shape(0)))
+        # inverse diagonals small enough that every update is a contraction
+        # (|off| <= 80 max|u| for these coefficients; ir = inv_re / h^2)
+        ir = c.prm["inv_re"] / c.prm["h"] ** 2
+        f[("idg", d)] = rng.uniform(0.5, 1.0, c.shape(0)) / (200.0 * ir)
     f[("muc", 0)] = np.exp(rng.uniform(np.log(0.01), np.log(10.0), c.shape(0)))
     f[("p", 0)] = rng.standard_normal(c.shape(0))
     f[("prhs", 0)] = rng.standard_normal(c.shape(0))
@@ -76,7 +80,7 @@ def test_tma_sweep_bit_identical_on_the_benchmark_grid():
     c.step(1)
     f = {}
     for d in range(3):
-        for name in ("ut", "urhs", "m", "beta", "mue"):
+        for name in ("ut", "urhs", "m", "beta", "mue", "idg"):
             f[(name, d)] = c.get_field_f32(name, d, 0)
     for name in ("muc", "p", "prhs"):
         f[(name, 0)] = c.get_field_f32(name, 0, 0)
