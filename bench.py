@@ -330,6 +330,10 @@ def sweep_roofline(ctx, stream, prm, cells):
     if plans is not None:
         roof["tma_plans"] = {"viscous_%d" % d: p for d, p in enumerate(plans)}
         roof["tma_plans"]["pressure"] = ctx.tma_plan(0, 3)
+        # (tile rows, planes per chunk, planes per phase, threads per row)
+        roof["sweep_shapes"] = {"viscous_%d" % d: ctx.sweep_shape(0, d)
+                                for d in range(prm["dim"])}
+        roof["sweep_shapes"]["pressure"] = ctx.sweep_shape(0, 3)
     return roof
 
 

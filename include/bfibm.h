@@ -271,6 +271,13 @@ bfibm_status bfibm_load_state(bfibm_ctx* c, const void* buf, int64_t bytes);
    level does not use the TMA sweep (not allowed, or the one-pass sweep timed
    faster). No counterpart in the paper. */
 bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]);
+/* Launch shape the autotuner chose for the one-pass FP32 sweep (the kernel
+   that reads its inputs from global memory) of one level and kind (0..D-1:
+   viscous component, 3: pressure), mixed-precision contexts only: out = {tile
+   rows, planes per chunk, planes per phase, threads per row}; 0 stands for
+   the built-in choice. BFIBM_EINVAL for an FP64 context, a bad level or kind,
+   or a level shape the tuner has not timed. No counterpart in the paper. */
+bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[4]);
 /* Pin the TMA sweep's plan {tile rows, planes per chunk, planes prefetched
    (1..3), columns per strip (>= n[0]: whole rows), grid blocks (0: as many as
    fit at once)} for the shape of one level, process-wide, in place of the

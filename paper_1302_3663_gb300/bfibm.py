@@ -76,6 +76,7 @@ SIGNATURES = {
     "bfibm_get_field": [_V, _i, _i, _i, _DP],
     "bfibm_set_field": [_V, _i, _i, _i, _DP],
     "bfibm_tma_plan": [_V, _i, _i, _IP],
+    "bfibm_sweep_shape": [_V, _i, _i, _IP],
     "bfibm_set_gamma": [_V, _DP],
     "bfibm_state_bytes": [_V, C.POINTER(_L)],
     "bfibm_save_state": [_V, _V, _L],
@@ -335,6 +336,14 @@ class Context:
         use it."""
         out = (C.c_int32 * 5)()
         st = self.lib.bfibm_tma_plan(self.h, level, kind, out)
+        return tuple(out) if st == OK else None
+
+    def sweep_shape(self, level=0, kind=0):
+        """(tile rows, planes per chunk, planes per phase, threads per row) of
+        the tuned one-pass FP32 sweep on a level (0: built-in choice), or None
+        where the level has not been tuned."""
+        out = (C.c_int32 * 4)()
+        st = self.lib.bfibm_sweep_shape(self.h, level, kind, out)
         return tuple(out) if st == OK else None
 
     def tma_set_plan(self, level, kind, plan):

@@ -89,12 +89,12 @@ void launch_coarse_v(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, dou
 // write `out`.
 template <typename T>
 void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s,
-                       int TYo = 0, int KCo = 0, int NPo = 1);
+                       int TYo = 0, int KCo = 0, int NPo = 1, int BXo = 0);
 template <typename T>
 void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
-                       cudaStream_t s, int TYo = 0, int KCo = 0, int NPo = 1);
+                       cudaStream_t s, int TYo = 0, int KCo = 0, int NPo = 1, int BXo = 0);
 // chunk planes filling `waves` waves of resident blocks (3D FP32 sweeps; 0: none)
-int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int waves);
+int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int BX, int waves);
 
 // Mixed precision (mixed.cu).
 int red_blocks_3d(int D, const Geo& g);
@@ -139,7 +139,7 @@ cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K,
 // pin a plan {TY, KC, PD, SW, grid (0: resident blocks)} for a level shape
 bool tma_set_plan(int K, const Geo& g, const int in[5]);
 // the one-pass sweep's tuned tile rows and chunk planes for a level shape
-bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP);
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX);
 // whether the tuner found the TMA sweep faster than the one-pass sweep
 bool tma_chosen(int K, const Geo& g);
 // tuned plan of a level shape: tile rows, chunk planes, prefetch planes,

@@ -417,16 +417,19 @@ struct FusedShape {
   size_t smem;
 };
 
-// Tile rows TYo and chunk planes KCo (3D) come from the autotuner when it
-// has timed this level shape; 0 selects the built-in heuristic.
+// Tile rows TYo, chunk planes KCo and threads per row BXo (3D) come from the
+// autotuner when it has timed this level shape; 0 selects the built-in
+// heuristic. A row of fewer threads than point pairs has each thread update
+// several pairs per phase.
 template <typename T>
-FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0, int NP = 1) {
+FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0, int NP = 1, int BXo = 0) {
   FusedShape f;
   int RA = (D == 3) ? 1 : 2, SA = (D == 3) ? 2 : 1;
   int ring = (D == 3) ? 1 : 0;
   int npairs = (g.n[0] + 1) / 2;
   int bx = ((npairs + 31) / 32) * 32;
   if (bx > 128) bx = 128;
+  if (D == 3 && BXo >= 32 && BXo < bx) bx = BXo / 32 * 32;
   // 4 rows (+2 ring rows) keep blocks small enough for several per SM
   f.TY = (D == 3) ? (g.n[RA] >= 4 ? 4 : g.n[RA]) : 1;
   if (D == 3 && TYo > 0) f.TY = TYo < g.n[RA] ? TYo : g.n[RA];
@@ -452,9 +455,9 @@ FusedShape fused_shape(int D, const Geo& g, int TYo = 0, int KCo = 0, int NP = 1
 
 template <typename T>
 void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaStream_t s, int TYo,
-                       int KCo, int NPo) {
+                       int KCo, int NPo, int BXo) {
   const int NP = (D == 3 && NPo == 2) ? 2 : 1;
-  FusedShape f = fused_shape<T>(D, g, TYo, KCo, NP);
+  FusedShape f = fused_shape<T>(D, g, TYo, KCo, NP, BXo);
   if (D == 3 && NP == 2) k_p_rb_fused<3, T, 2><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
   else if (D == 3) k_p_rb_fused<3, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
   else k_p_rb_fused<2, T, 1><<<f.grid, f.block, f.smem, s>>>(g, L, out, f.TY, f.KC);
@@ -462,9 +465,9 @@ void launch_p_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, T* out, cudaS
 
 template <typename T>
 void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out, double inv_re,
-                       cudaStream_t s, int TYo, int KCo, int NPo) {
+                       cudaStream_t s, int TYo, int KCo, int NPo, int BXo) {
   const int NP = (D == 3 && NPo == 2) ? 2 : 1;
-  FusedShape f = fused_shape<T>(D, g, TYo, KCo, NP);
+  FusedShape f = fused_shape<T>(D, g, TYo, KCo, NP, BXo);
   T ir = (T)(inv_re / (g.h * g.h));
   if (D == 3) {
     if (NP == 2) {
@@ -483,12 +486,22 @@ void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out
 }
 
 // Let the fused sweeps run several blocks per SM: ask for a shared-memory
-// carveout of a quarter of the unified L1/shared storage (call once, outside
-// stream capture).
+// carveout of a quarter of the unified L1/shared storage for the FP64 sweeps
+// and half of it for the FP32 sweeps, whose taller tiles (up to 18 ring rows)
+// need more (call once, outside stream capture).
 cudaError_t fused_set_carveout() {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+    const bool f32 = f == (const void*)k_p_rb_fused<3, float, 1> ||
+                     f == (const void*)k_p_rb_fused<3, float, 2> ||
+                     f == (const void*)k_v_rb_fused<3, 0, float, 1> ||
+                     f == (const void*)k_v_rb_fused<3, 1, float, 1> ||
+                     f == (const void*)k_v_rb_fused<3, 2, float, 1> ||
+                     f == (const void*)k_v_rb_fused<3, 0, float, 2> ||
+                     f == (const void*)k_v_rb_fused<3, 1, float, 2> ||
+                     f == (const void*)k_v_rb_fused<3, 2, float, 2>;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, f32 ? 50 : 25);
   };
   set((const void*)k_p_rb_fused<3, float, 1>);
   set((const void*)k_p_rb_fused<3, float, 2>);
@@ -518,9 +531,9 @@ cudaError_t fused_set_carveout() {
 // Chunk planes that give `waves` full waves of resident blocks for the 3D
 // FP32 sweep of kind K (0..2 viscous components, 3 pressure) with TY tile
 // rows; 0 where the occupancy cannot be had.
-int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int waves) {
+int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int BX, int waves) {
   if (D != 3) return 0;
-  FusedShape f = fused_shape<float>(D, g, TY, 0, NP);
+  FusedShape f = fused_shape<float>(D, g, TY, 0, NP, BX);
   const void* fn;
   if (K == 3) fn = NP == 2 ? (const void*)k_p_rb_fused<3, float, 2> : (const void*)k_p_rb_fused<3, float, 1>;
   else if (K == 0) fn = NP == 2 ? (const void*)k_v_rb_fused<3, 0, float, 2> : (const void*)k_v_rb_fused<3, 0, float, 1>;
@@ -545,12 +558,12 @@ size_t fused_smem_bytes(int D, const Geo& g, int elem) {
 }
 
 template void launch_p_rb_fused<double>(int, const Geo&, const LevelPtrs<double>&, double*,
-                                        cudaStream_t, int, int, int);
+                                        cudaStream_t, int, int, int, int);
 template void launch_p_rb_fused<float>(int, const Geo&, const LevelPtrs<float>&, float*,
-                                       cudaStream_t, int, int, int);
+                                       cudaStream_t, int, int, int, int);
 template void launch_v_rb_fused<double>(int, const Geo&, const LevelPtrs<double>&, int, double*,
-                                        double, cudaStream_t, int, int, int);
+                                        double, cudaStream_t, int, int, int, int);
 template void launch_v_rb_fused<float>(int, const Geo&, const LevelPtrs<float>&, int, float*,
-                                       double, cudaStream_t, int, int, int);
+                                       double, cudaStream_t, int, int, int, int);
 
 }  // namespace bf

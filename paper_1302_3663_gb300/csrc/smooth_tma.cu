@@ -499,6 +499,7 @@ struct Plan {
   int TY = 4, KC = 16, PD = 1, SW = 0, grid = 0;
   bool tma = false;    // the TMA sweep timed faster than the one-pass global-memory sweep
   int rTY = 0, rKC = 0, rNP = 1;   // fastest rows / chunk planes / planes per phase of the one-pass sweep
+  int rBX = 0;                     // and threads per row (0: one per point pair, up to 128)
 };
 
 using PlanKey = std::tuple<int, int, int, int, int, long long, int>;
@@ -655,16 +656,22 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
     if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s);
     else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s);
   }
+  // (rows, threads per row): one thread per point pair on up to 8 rows, or
+  // 32 threads per row (several pairs each) on taller tiles, where the ring
+  // rows recomputed by neighbouring blocks are a smaller share
+  const int shapes[8][2] = {{0, 0}, {2, 0}, {4, 0}, {6, 0}, {8, 0}, {8, 32}, {12, 32}, {16, 32}};
   for (int rNP : {1, 2}) {
-  for (int rTY : {0, 2, 4, 6, 8}) {
+  for (const auto& shp : shapes) {
+    const int rTY = shp[0], rBX = shp[1];
     if ((rTY == 0) == search) continue;
-    if (rTY > g.n[1] || bx * (rTY + 2) > 1024) continue;
+    if (rBX > 0 && rBX >= bx) continue;
+    if (rTY > g.n[1] || (rBX > 0 ? rBX : bx) * (rTY + 2) > 1024) continue;
     // fixed chunk sizes, and the sizes that fill one or two waves of resident
     // blocks exactly
     int kcs_ring[5] = {8, 16, 32, 0, 0};
     if (search && rTY > 0) {
-      kcs_ring[3] = ring_fill_kc(D, K, g, rTY, rNP, 1);
-      kcs_ring[4] = ring_fill_kc(D, K, g, rTY, rNP, 2);
+      kcs_ring[3] = ring_fill_kc(D, K, g, rTY, rNP, rBX, 1);
+      kcs_ring[4] = ring_fill_kc(D, K, g, rTY, rNP, rBX, 2);
     }
     for (int ci = 0; ci < 5; ++ci) {
       const int rKC = kcs_ring[ci];
@@ -675,8 +682,8 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
       if (!search && rKC != 8) continue;
       if (search && rKC > g.n[2] && rKC != 8) continue;
       auto ring = [&]() {
-        if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s, rTY, rKC, rNP);
-        else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s, rTY, rKC, rNP);
+        if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s, rTY, rKC, rNP, rBX);
+        else launch_v_rb_fused<float>(D, g, L, K, out, coef * g.h * g.h, s, rTY, rKC, rNP, rBX);
       };
       ring();
       float ms = per_launch_ms(ring);
@@ -686,6 +693,7 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
         best.rTY = rTY;
         best.rKC = search ? rKC : 0;
         best.rNP = rNP;
+        best.rBX = rBX;
       }
     }
     if (status != cudaSuccess) break;
@@ -773,18 +781,20 @@ bool tma_set_plan(int K, const Geo& g, const int in[5]) {
     pl.rTY = it->second.rTY;
     pl.rKC = it->second.rKC;
     pl.rNP = it->second.rNP;
+    pl.rBX = it->second.rBX;
   }
   g_plans[plan_key(K, g)] = pl;
   return true;
 }
 
-bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP) {
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   auto it = g_plans.find(plan_key(K, g));
   if (it == g_plans.end()) return false;
   *TY = it->second.rTY;
   *KC = it->second.rKC;
   *NP = it->second.rNP;
+  *BX = it->second.rBX;
   return true;
 }
 

@@ -474,9 +474,9 @@ void smooth_p32(bfibm_ctx* c, int l, int n) {
     if (tma)
       launch_rb_tma(c->D, Lv.g, Lv.f, 3, Lv.f.p2, c->counters + 3, Lv.g.h * Lv.g.h, c->stream);
     else {
-      int ty = 0, kc = 0, np = 1;
-      ring_shape_of(3, Lv.g, &ty, &kc, &np);
-      launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc, np);
+      int ty = 0, kc = 0, np = 1, bx = 0;
+      ring_shape_of(3, Lv.g, &ty, &kc, &np, &bx);
+      launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc, np, bx);
     }
     std::swap(Lv.f.p, Lv.f.p2);
   }
@@ -495,10 +495,10 @@ void smooth_v32(bfibm_ctx* c, int l, int n) {
         launch_rb_tma(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->counters + 3,
                       c->P.inv_re / (Lv.g.h * Lv.g.h), c->stream);
       else {
-        int ty = 0, kc = 0, np = 1;
-        ring_shape_of(d, Lv.g, &ty, &kc, &np);
+        int ty = 0, kc = 0, np = 1, bx = 0;
+        ring_shape_of(d, Lv.g, &ty, &kc, &np, &bx);
         launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream, ty, kc,
-                                 np);
+                                 np, bx);
       }
       std::swap(Lv.f.u[d], Lv.f.u2[d]);
     }
@@ -1652,6 +1652,21 @@ bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]) {
   int v[5];
   if (!tma_plan_of(kind, c->lev[level].g, v)) return set_err(c, BFIBM_EINVAL, "level not tuned");
   for (int q = 0; q < 5; ++q) out[q] = v[q];
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[4]) {
+  READY(c);
+  if (!out || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
+      (kind < 3 && kind >= c->D) || c->P.precision != 1)
+    return set_err(c, BFIBM_EINVAL, "no FP32 sweep of this kind on this level");
+  int ty = 0, kc = 0, np = 1, bx = 0;
+  if (!ring_shape_of(kind, c->lev[level].g, &ty, &kc, &np, &bx))
+    return set_err(c, BFIBM_EINVAL, "level not tuned");
+  out[0] = ty;
+  out[1] = kc;
+  out[2] = np;
+  out[3] = bx;
   return BFIBM_OK;
 }
 
