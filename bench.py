@@ -36,10 +36,13 @@ UNIT = "cell-steps/s"
 # Solves run to a relative residual of 1e-11, which leaves max |div u| below
 # 1e-10 after every projection; coarse-grid viscosity scaled by gamma = 0.8
 # (Eq. ViscCoarseGrid, inside the recommended [0.7, 1]); V(3,3) cycles.
-# inner_cycles: FP32 V-cycles per FP64 residual in mixed precision (ignored by
-# the FP64 path)
+# Mixed precision only (the FP64 path ignores both): inner_cycles FP32
+# V-cycles per FP64 residual, and krylov = 1 puts the viscous solve's FP32
+# V-cycles inside a flexible conjugate-gradient iteration in FP64
 TOL_SOLVER = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 100, "gamma_coarse": 0.8,
-              "nu1": 3, "nu2": 3, "inner_cycles": 3}
+              "nu1": 2, "nu2": 2, "inner_cycles": 2, "krylov": 1}
+# the same with plain defect correction (3 V(3,3) cycles per FP64 residual)
+DC_SOLVER = dict(TOL_SOLVER, nu1=3, nu2=3, inner_cycles=3, krylov=0)
 DIV_TARGET = 1e-10
 
 
@@ -108,11 +111,13 @@ def describe(inst):
     gl = [g for g in p.get("gamma_levels", [])[1:] if g > 0]
     vc = ("%d viscous + %d pressure V(%d,%d) cycles per step" %
           (p["vc_visc"], p["vc_p"], p["nu1"], p["nu2"]) if p["vc_visc"] > 0
-          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %s%s"
+          else "V(%d,%d) cycles until the relative residual is %.0e, coarse viscosity x %s%s%s"
           % (p["nu1"], p["nu2"], p["rtol"],
              ("%s per level (tuned)" % gl) if gl else "%g" % p["gamma_coarse"],
              (", %d FP32 V-cycles per FP64 residual" % p["inner_cycles"])
-             if p.get("precision", 0) == 1 and p.get("inner_cycles", 1) > 1 else ""))
+             if p.get("precision", 0) == 1 and p.get("inner_cycles", 1) > 1 else "",
+             ", viscous solve: flexible CG in FP64 preconditioned by the FP32 V-cycles"
+             if p.get("precision", 0) == 1 and p.get("krylov", 0) else ""))
     return {
         "workload": "%s: %s grid, %d nodes, %d springs, density ratio %g, viscosity ratio %g"
                     % (inst["name"], "x".join(map(str, n)), inst["X"].shape[0],
@@ -400,6 +405,8 @@ def run_ours(args):
 
     if not args.no_fp64 and prm.get("precision", 0) == 1:
         out["fp64_single_instance"] = run_fp64(inst, args, world, stream)
+    if args.solver == "tol" and prm.get("precision", 0) == 1 and prm.get("krylov", 0):
+        out["mixed_defect_correction"] = run_dc(inst, args, world, stream)
     if args.solver == "tol":
         out["fixed_3_vcycles"] = run_fixed(inst, args, world, stream)
     if not args.no_e2e:
@@ -422,7 +429,7 @@ def run_fixed(inst, args, world, stream):
     throughput of the loosest setting, for context."""
     from paper_1302_3663_gb300 import bfibm, workloads as W
     prm = dict(inst["params"], vc_visc=3, vc_p=3, nu1=2, nu2=2, gamma_coarse=1.0,
-               gamma_levels=[])
+               gamma_levels=[], inner_cycles=1, krylov=0)
     ctx = bfibm.load_instance(dict(inst, params=prm), stream=stream)
     ctx.set_option(bfibm.OPT_STATS, 0)
     ctx.step(args.warmup)
@@ -433,6 +440,25 @@ def run_fixed(inst, args, world, stream):
     ctx.close()
     return {"value": W.cells(prm) * steps * world / (ms / 1e3), "unit": UNIT,
             "ms_per_step": ms / steps, "div_max": fin["div_max"]}
+
+
+def run_dc(inst, args, world, stream):
+    """Mixed precision with plain defect correction (no conjugate gradients)
+    on the same workload, tolerance and coarse scaling."""
+    from paper_1302_3663_gb300 import bfibm, workloads as W
+    prm = dict(inst["params"], **{k: DC_SOLVER[k] for k in ("nu1", "nu2", "inner_cycles",
+                                                             "krylov")})
+    ctx = bfibm.load_instance(dict(inst, params=prm), stream=stream)
+    ctx.set_option(bfibm.OPT_STATS, 0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    ms = timed_steps(ctx, stream, args.steps, world, "timed_dc")
+    fin = final_stats(ctx)
+    ctx.close()
+    return {"value": W.cells(prm) * args.steps * world / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "div_max": fin["div_max"],
+            "cycles_visc": fin["cycles_visc"], "cycles_p": fin["cycles_p"],
+            "solver": "V(3,3), 3 FP32 V-cycles per FP64 residual, no conjugate gradients"}
 
 
 def run_fp64(inst, args, world, stream):

@@ -239,13 +239,19 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
    solve computes fewer FP64 residuals for the same V-cycles; a tolerance
    solve stops after a multiple of it). Every option but BFIBM_OPT_INNER gives
    the same results to rounding; BFIBM_OPT_INNER changes the iterates within
-   the solver tolerance. */
+   the solver tolerance), BFIBM_OPT_KRYLOV (mixed precision, viscous solve:
+   0, the default, FP64 defect correction around the FP32 V-cycles; 1, a
+   flexible conjugate-gradient iteration in FP64 with the FP32 V-cycles as
+   preconditioner, which needs fewer V-cycles where the viscosity contrast
+   slows the V-cycle down; the same discrete system and stopping test, so
+   tolerance solves agree within the tolerance). */
 enum {
   BFIBM_OPT_STATS = 0,
   BFIBM_OPT_GRAPH = 1,
   BFIBM_OPT_FUSED = 2,
   BFIBM_OPT_TMA = 3,
-  BFIBM_OPT_INNER = 4
+  BFIBM_OPT_INNER = 4,
+  BFIBM_OPT_KRYLOV = 5
 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Checkpoint and resume. The state a time step starts from (Sec. 3.4): the

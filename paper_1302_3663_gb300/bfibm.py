@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTAT
 FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
          "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12, "idg": 13}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
-OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER = 0, 1, 2, 3, 4
+OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER, OPT_KRYLOV = 0, 1, 2, 3, 4, 5
 
 
 class BfibmError(RuntimeError):
@@ -209,6 +209,9 @@ class Context:
         # context, not a field of bfibm_params)
         if int(prm.get("inner_cycles", 1)) != 1:
             self.set_option(OPT_INNER, int(prm["inner_cycles"]))
+        # flexible CG around the FP32 V-cycles for the viscous solve
+        if int(prm.get("krylov", 0)) != 0:
+            self.set_option(OPT_KRYLOV, int(prm["krylov"]))
 
     def _chk(self, st, what, allow=(OK,)):
         if st not in allow:

@@ -168,19 +168,18 @@ __global__ void __launch_bounds__(256) k_v_idg32(Geo g, LevelPtrs<double> L, F32
 // `diag` (the same arithmetic as the FP64 residual kernel). INTERIOR: no
 // neighbour lies beyond a wall or across a periodic seam, so the offsets are
 // the plain strides and no flag is tested.
-template <int D, int d, bool INTERIOR>
-__device__ __forceinline__ double v_res64d(const Geo& g, const LevelPtrs<double>& L,
-                                           const double* __restrict__ diag, const int ci[3],
-                                           long long F, double ir) {
-  const double* __restrict__ ud = L.u[d];
+template <int D, int d, bool INTERIOR, typename V>
+__device__ __forceinline__ double v_off64(const Geo& g, const LevelPtrs<double>& L,
+                                          const V* const vec[3], const int ci[3], long long F) {
+  const V* __restrict__ ud = vec[d];
   const long long od_p = INTERIOR ? g.st[d] : offp(g, d, ci[d]);
   const long long od_m = INTERIOR ? -g.st[d] : offm(g, d, ci[d]);
   double mcp = L.muc[F], mcm = L.muc[F + od_m];
-  double off = 2.0 * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
+  double off = 2.0 * (mcp * (double)ud[F + od_p] + mcm * (double)ud[F + od_m]);
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
-    const double* __restrict__ ue = L.u[e];
+    const V* __restrict__ ue = vec[e];
     const double* __restrict__ me = L.mue[edge_id(d, e)];
     bool wp = false, wm = false;
     if (!INTERIOR) {
@@ -192,14 +191,25 @@ __device__ __forceinline__ double v_res64d(const Geo& g, const LevelPtrs<double>
     const long long oem = INTERIOR ? -g.st[e] : offm(g, e, ci[e]);
     long long Ep = F + oep;
     double mep = me[Ep], mem = me[F];
-    double cp = ue[Ep] - ue[Ep + od_m];
-    double cm = ue[F] - ue[F + od_m];
+    double cp = (double)ue[Ep] - (double)ue[Ep + od_m];
+    double cm = (double)ue[F] - (double)ue[F + od_m];
     double udp = 0.0, udm = 0.0;
-    if (!wp) udp = ud[Ep];
-    if (!wm) udm = ud[F + oem];
+    if (!wp) udp = (double)ud[Ep];
+    if (!wm) udm = (double)ud[F + oem];
     off += mep * (udp + cp) + mem * (udm - cm);
   }
-  return L.uf[d][F] - diag[F] * ud[F] + ir * off;
+  return off;
+}
+
+// The off-diagonal part of the FP64 viscous operator of component d at face
+// F applied to `vec` (FP64 or FP32 components, summed in FP64).
+template <int D, int d, bool INTERIOR>
+__device__ __forceinline__ double v_res64d(const Geo& g, const LevelPtrs<double>& L,
+                                           const double* __restrict__ diag, const int ci[3],
+                                           long long F, double ir) {
+  const double* const vec[3] = {L.u[0], L.u[1], L.u[2]};
+  double off = v_off64<D, d, INTERIOR, double>(g, L, vec, ci, F);
+  return L.uf[d][F] - diag[F] * L.u[d][F] + ir * off;
 }
 
 template <int D, bool INTERIOR>
@@ -214,7 +224,7 @@ __device__ __forceinline__ double v_res_any(const Geo& g, const LevelPtrs<double
 template <int D>
 __global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
                                                           F32x3 e32, Ptr3d diag, double ir,
-                                                          double* partial) {
+                                                          double* partial, Ptr3d r64) {
   __shared__ double sh[32];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -233,6 +243,7 @@ __global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<doubl
       else if (g.per[d] || ci[d] != 0) r = v_res_any<D, false>(g, L, diag, d, ci, F, ir);
       r32.a[d][F] = (float)r;
       e32.a[d][F] = 0.0f;
+      if (r64.a[0]) r64.a[d][F] = r;
       r2 += r * r;
     }
   }
@@ -297,19 +308,191 @@ void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, fl
 
 void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
                              float* const e32[3], double* const diag[3], double inv_re,
-                             double* partial, cudaStream_t s) {
+                             double* partial, cudaStream_t s, double* const r64[3]) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
   F32x3 r, e;
-  Ptr3d dg;
+  Ptr3d dg, rr;
   for (int d = 0; d < 3; ++d) {
     r.a[d] = r32[d];
     e.a[d] = e32[d];
     dg.a[d] = diag[d];
+    rr.a[d] = r64 ? r64[d] : nullptr;
   }
   double ir = inv_re / (g.h * g.h);
-  if (D == 3) k_v_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r, e, dg, ir, partial);
-  else k_v_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r, e, dg, ir, partial);
+  if (D == 3) k_v_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r, e, dg, ir, partial, rr);
+  else k_v_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r, e, dg, ir, partial, rr);
+}
+
+// ------------------------------------------------------------ flexible CG
+// Flexible conjugate gradients for the viscous solve, in FP64 around the
+// FP32 V-cycle as preconditioner M (the viscous operator A is symmetric
+// positive definite; M is neither symmetric nor fixed, so the update of the
+// search direction uses the flexible form, with one previous direction):
+//   z = M r,  w = A z,  beta = -(z.q) / (p.q)  (0 at the first iteration),
+//   p = z + beta p,  q = w + beta q,  alpha = (p.r) / (p.q),
+//   x += alpha p,  r -= alpha q.
+// Scalars travel between the kernels in device memory (slots of `out`).
+template <int D, int d, bool INTERIOR>
+__device__ __forceinline__ double v_apply_z(const Geo& g, const LevelPtrs<double>& L,
+                                            const F32x3& z, const double* __restrict__ diag,
+                                            const int ci[3], long long F, double ir) {
+  const float* const vec[3] = {z.a[0], z.a[1], z.a[2]};
+  double off = v_off64<D, d, INTERIOR, float>(g, L, vec, ci, F);
+  return diag[F] * (double)z.a[d][F] - ir * off;
+}
+
+template <int D, bool INTERIOR>
+__device__ __forceinline__ double v_apply_any(const Geo& g, const LevelPtrs<double>& L,
+                                              const F32x3& z, const Ptr3d& diag, int d,
+                                              const int ci[3], long long F, double ir) {
+  if (d == 0) return v_apply_z<D, 0, INTERIOR>(g, L, z, diag.a[0], ci, F, ir);
+  if (d == 1) return v_apply_z<D, 1, INTERIOR>(g, L, z, diag.a[1], ci, F, ir);
+  return v_apply_z<D, (D == 3 ? 2 : 1), INTERIOR>(g, L, z, diag.a[D == 3 ? 2 : 1], ci, F, ir);
+}
+
+__device__ __forceinline__ bool block_leader() {
+  return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+}
+
+// w = A z on every unknown face (0 on the fixed wall faces); partial sums of z.q
+template <int D>
+__global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, F32x3 z,
+                                                   Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
+                                                   double* partial) {
+  __shared__ double sh[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double zq = 0.0;
+  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+    int ci[3] = {i, j, k};
+    long long F = gidx(g, i, j, k);
+    bool interior = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) interior = interior && ci[a] > 0 && ci[a] < g.n[a] - 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double v = 0.0;
+      if (interior) v = v_apply_any<D, true>(g, L, z, diag, d, ci, F, ir);
+      else if (g.per[d] || ci[d] != 0) v = v_apply_any<D, false>(g, L, z, diag, d, ci, F, ir);
+      w.a[d][F] = v;
+      zq += (double)z.a[d][F] * q.a[d][F];
+    }
+  }
+  zq = block_sum(zq, sh);
+  if (block_leader()) partial[block_linear()] = zq;
+}
+
+// p = z + beta p, q = w + beta q; partial sums of p.q (first nb) and p.r (next nb)
+template <int D>
+__global__ void __launch_bounds__(256) k_fcg_dir(Geo g, F32x3 z, Ptr3d w, Ptr3d p, Ptr3d q,
+                                                 Ptr3d r, const double* __restrict__ out,
+                                                 int sl_zq, int sl_pq, double* partial, int nb) {
+  __shared__ double sh[32];
+  const double pq_old = out[sl_pq];
+  const double beta = pq_old != 0.0 ? -out[sl_zq] / pq_old : 0.0;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double pq = 0.0, pr = 0.0;
+  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+    long long F = gidx(g, i, j, k);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double pv = (double)z.a[d][F] + beta * p.a[d][F];
+      double qv = w.a[d][F] + beta * q.a[d][F];
+      p.a[d][F] = pv;
+      q.a[d][F] = qv;
+      pq += pv * qv;
+      pr += pv * r.a[d][F];
+    }
+  }
+  pq = block_sum(pq, sh);
+  pr = block_sum(pr, sh);
+  if (block_leader()) {
+    partial[block_linear()] = pq;
+    partial[nb + block_linear()] = pr;
+  }
+}
+
+// x += alpha p, r -= alpha q; the new residual as the FP32 right-hand side of
+// the next preconditioning (correction zeroed); partial sums of r.r
+template <int D>
+__global__ void __launch_bounds__(256) k_fcg_update(Geo g, Ptr3d x, Ptr3d p, Ptr3d q, Ptr3d r,
+                                                    F32x3 r32, F32x3 e32,
+                                                    const double* __restrict__ out, int sl_pq,
+                                                    int sl_pr, double* partial) {
+  __shared__ double sh[32];
+  const double pq = out[sl_pq];
+  const double alpha = pq != 0.0 ? out[sl_pr] / pq : 0.0;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double rr = 0.0;
+  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+    long long F = gidx(g, i, j, k);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      x.a[d][F] += alpha * p.a[d][F];
+      double rv = r.a[d][F] - alpha * q.a[d][F];
+      r.a[d][F] = rv;
+      r32.a[d][F] = (float)rv;
+      e32.a[d][F] = 0.0f;
+      rr += rv * rv;
+    }
+  }
+  rr = block_sum(rr, sh);
+  if (block_leader()) partial[block_linear()] = rr;
+}
+
+namespace {
+Ptr3d p3(double* const a[3]) {
+  Ptr3d o;
+  for (int d = 0; d < 3; ++d) o.a[d] = a[d];
+  return o;
+}
+F32x3 f3(float* const a[3]) {
+  F32x3 o;
+  for (int d = 0; d < 3; ++d) o.a[d] = a[d];
+  return o;
+}
+}  // namespace
+
+void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, float* const z[3],
+                      double* const diag[3], double inv_re, double* const w[3],
+                      double* const q[3], double* partial, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  double ir = inv_re / (g.h * g.h);
+  if (D == 3) k_fcg_apply<3><<<gr, b, 0, s>>>(g, L, f3(z), p3(diag), ir, p3(w), p3(q), partial);
+  else k_fcg_apply<2><<<gr, b, 0, s>>>(g, L, f3(z), p3(diag), ir, p3(w), p3(q), partial);
+}
+
+void launch_fcg_dir(int D, const Geo& g, float* const z[3], double* const w[3], double* const p[3],
+                    double* const q[3], double* const r[3], const double* out, int sl_zq,
+                    int sl_pq, double* partial, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  int nb = (int)(gr.x * gr.y * gr.z);
+  if (D == 3)
+    k_fcg_dir<3><<<gr, b, 0, s>>>(g, f3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
+  else
+    k_fcg_dir<2><<<gr, b, 0, s>>>(g, f3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
+}
+
+void launch_fcg_update(int D, const Geo& g, double* const x[3], double* const p[3],
+                       double* const q[3], double* const r[3], float* const r32[3],
+                       float* const e32[3], const double* out, int sl_pq, int sl_pr,
+                       double* partial, cudaStream_t s) {
+  dim3 b = blk3(D);
+  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  if (D == 3)
+    k_fcg_update<3><<<gr, b, 0, s>>>(g, p3(x), p3(p), p3(q), p3(r), f3(r32), f3(e32), out, sl_pq,
+                                     sl_pr, partial);
+  else
+    k_fcg_update<2><<<gr, b, 0, s>>>(g, p3(x), p3(p), p3(q), p3(r), f3(r32), f3(e32), out, sl_pq,
+                                     sl_pr, partial);
 }
 
 void launch_v_diag(int D, const Geo& g, const LevelPtrs<double>& L, double* const diag[3],

@@ -89,8 +89,10 @@ size_t grid_pool_bytes(const bfibm_params& P, int* nlev = nullptr) {
   size_t bytes = 0;
   for (int l = 0; l < L; ++l) {
     size_t arr = (size_t)round_up(level_elems(g[l]) * 8, 256);
+    // level 0: velocity, density, force; mixed precision adds the FP64
+    // viscous diagonal and the flexible-CG directions p and q
     int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0) +
-             (l == 0 && P.precision == 1 ? P.dim : 0);
+             (l == 0 && P.precision == 1 ? 3 * P.dim : 0);
     bytes += arr * na;
     if (P.precision == 1)   // the level's arrays and the inverse viscous diagonals
       bytes += (size_t)round_up(level_elems(g[l]) * 4, 256) * (arrays_per_level(P.dim) + P.dim);
@@ -143,6 +145,8 @@ struct bfibm_ctx {
   Level lev[kMaxLevels];
   double* uvel[3] = {nullptr, nullptr, nullptr};
   double* vdiag[3] = {nullptr, nullptr, nullptr};   // FP64 viscous diagonal (mixed precision)
+  double* cg_p[3] = {nullptr, nullptr, nullptr};    // flexible-CG direction and A times it
+  double* cg_q[3] = {nullptr, nullptr, nullptr};
   double* rho[3] = {nullptr, nullptr, nullptr};
   double* frc[3] = {nullptr, nullptr, nullptr};
   double* G_dev = nullptr;
@@ -175,6 +179,7 @@ struct bfibm_ctx {
   int poisoned = 0;
   long long step_host = 0;
   int inner = 1;                 // FP32 V-cycles per FP64 defect-correction iteration
+  int krylov = 0;                // 1: flexible CG around the FP32 V-cycle (viscous, mixed)
   int cycles_visc = 0, cycles_p = 0;
   int loop_inner[2] = {1, 1};    // V-cycles per device-loop iteration (visc, p) when captured
   long long graph_kernels = -1;   // kernel nodes in the captured step graph
@@ -298,7 +303,7 @@ void vcycle_v(bfibm_ctx* c, int l) {
 }
 
 // scalar slots: 0 scratch (means), 2/3 viscous |f|^2,|r|^2, 4/5 pressure, 6/7 div/KE
-enum { SL_VF = 2, SL_VR = 3, SL_PF = 4, SL_PR = 5, SL_DIV = 6 };
+enum { SL_VF = 2, SL_VR = 3, SL_PF = 4, SL_PR = 5, SL_DIV = 6, SL_ZQ = 8, SL_PQ = 9, SL_PRR = 10 };
 
 bfibm_status read_scalars(bfibm_ctx* c) {
   CK(cudaMemcpyAsync(c->host_sc, c->sc.out, 16 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -678,6 +683,87 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
   return st;
 }
 
+// Flexible CG for the mixed-precision viscous solve: the FP32 V-cycle (c->inner
+// of them) preconditions an FP64 conjugate-gradient iteration on A x = f. The
+// residual r is kept in FP64 (recurrence r -= alpha q) and its norm decides
+// convergence; a tolerance solve stops after max_cycles V-cycles at most, a
+// fixed one runs ncycles V-cycles. Returns V-cycles used.
+bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
+  Level& L0 = c->lev[0];
+  cudaStream_t s = c->stream;
+  const int D = c->D;
+  const bool tol = ncycles <= 0;
+  const int inner = c->inner;
+  const int nb = red_blocks_3d(D, L0.g);
+  double* w[3] = {L0.d.u2[0], L0.d.u2[1], L0.d.u2[2]};
+  double* r[3] = {L0.d.ur[0], L0.d.ur[1], L0.d.ur[2]};
+  if (tol || c->collect_stats) launch_norm2(D, L0.g, L0.d.uf, D, c->sc, SL_VF, s);
+  const int maxc = dc_iterations(tol ? c->P.max_cycles : ncycles, inner);
+  // r = f - A x in FP64 (and as the FP32 right-hand side), the first
+  // direction flagged by p.q = 0
+  launch_v_residual_mixed(D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, c->sc.partial,
+                          s, r);
+  launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
+  CK(cudaMemsetAsync(c->sc.out + SL_PQ, 0, sizeof(double), s));
+  auto iteration = [&](cudaStream_t b, int nv) {
+    for (int q = 0; q < nv; ++q) vcycle_v32(c, 0);
+    launch_fcg_apply(D, L0.g, L0.d, L0.f.u, c->vdiag, c->P.inv_re, w, c->cg_q, c->sc.partial, b);
+    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_ZQ, 1.0, b);
+    launch_fcg_dir(D, L0.g, L0.f.u, w, c->cg_p, c->cg_q, r, c->sc.out, SL_ZQ, SL_PQ,
+                   c->sc.partial, b);
+    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PQ, 1.0, b);
+    launch_finalize_sum(c->sc.partial + nb, nb, c->sc.out, SL_PRR, 1.0, b);
+    launch_fcg_update(D, L0.g, L0.d.u, c->cg_p, c->cg_q, r, L0.f.uf, L0.f.u, c->sc.out, SL_PQ,
+                      SL_PRR, c->sc.partial, b);
+    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
+  };
+  if (tol && c->capturing) {
+    cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
+    c->loop_inner[0] = inner;
+    bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
+      iteration(c->stream, inner);
+      launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, maxc, c->dev_cycles, c->loop_total,
+                       c->stream);
+    });
+    if (cs == BFIBM_OK && c->collect_stats) {   // the true FP64 residual of the final iterate
+      launch_v_residual_mixed(D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re,
+                              c->sc.partial, s);
+      launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
+    }
+    *used = -1;
+    return cs;
+  }
+  bfibm_status st = tol ? BFIBM_ENOCONV : BFIBM_OK;
+  int vdone = 0;
+  for (int k = 1; k <= maxc; ++k) {
+    if (tol) {
+      bfibm_status rs = read_scalars(c);
+      if (rs != BFIBM_OK) return rs;
+      double fn = std::sqrt(c->host_sc[SL_VF]), rn = std::sqrt(c->host_sc[SL_VR]);
+      if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) {
+        st = BFIBM_OK;
+        break;
+      }
+    }
+    const int nv = tol ? inner : std::min(inner, ncycles - vdone);
+    iteration(s, nv);
+    vdone += nv;
+  }
+  if (tol && st != BFIBM_OK) {
+    bfibm_status rs = read_scalars(c);
+    if (rs != BFIBM_OK) return rs;
+    double fn = std::sqrt(c->host_sc[SL_VF]), rn = std::sqrt(c->host_sc[SL_VR]);
+    if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) st = BFIBM_OK;
+  }
+  if (c->collect_stats || tol) {   // the true FP64 residual of the final iterate
+    launch_v_residual_mixed(D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re,
+                            c->sc.partial, s);
+    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
+  }
+  *used = vdone;
+  return st;
+}
+
 // ------------------------------------------------------------------ stages
 void stage_rhs(bfibm_ctx* c) {
   launch_adv_rhs(c->D, c->lev[0].g, c->uvel, c->rho, c->frc, c->lev[0].d, c->P.c_force,
@@ -753,7 +839,8 @@ void refresh(bfibm_ctx* c) {
 bfibm_status queue_step(bfibm_ctx* c) {
   stage_rhs(c);
   bool mixed = c->P.precision == 1;
-  bfibm_status st = mixed ? solve_v_mixed(c, c->P.vc_visc, &c->cycles_visc)
+  bfibm_status st = mixed ? (c->krylov ? solve_v_fcg(c, c->P.vc_visc, &c->cycles_visc)
+                                        : solve_v_mixed(c, c->P.vc_visc, &c->cycles_visc))
                           : solve_v(c, c->P.vc_visc, &c->cycles_visc);
   if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
   stage_divergence(c);
@@ -1005,7 +1092,11 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
         c->uvel[a] = take(Lv.g);
         c->rho[a] = take(Lv.g);
         c->frc[a] = take(Lv.g);
-        if (p->precision == 1) c->vdiag[a] = take(Lv.g);
+        if (p->precision == 1) {
+          c->vdiag[a] = take(Lv.g);
+          c->cg_p[a] = take(Lv.g);
+          c->cg_q[a] = take(Lv.g);
+        }
       }
   }
   if (p->precision == 1) {
@@ -1040,7 +1131,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   c->sc.out = (double*)cur;
   cur += 256;
   // remaining scalar room
-  c->partial_cap = std::max<long long>(4 * kRedBlocks, red_blocks_3d(D, c->lev[0].g) + 64);
+  c->partial_cap = std::max<long long>(4 * kRedBlocks, 2LL * red_blocks_3d(D, c->lev[0].g) + 64);
   if (cudaMalloc((void**)&c->sc.partial, sizeof(double) * c->partial_cap) != cudaSuccess ||
       cudaMalloc((void**)&c->step_dev, sizeof(long long)) != cudaSuccess ||
       cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
@@ -1443,7 +1534,8 @@ bfibm_status bfibm_set_gamma(bfibm_ctx* c, const double gamma_levels[8]) {
 bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles) {
   READY(c);
   int used = 0;
-  bfibm_status st = c->P.precision == 1 ? solve_v_mixed(c, ncycles, &used)
+  bfibm_status st = c->P.precision == 1 ? (c->krylov ? solve_v_fcg(c, ncycles, &used)
+                                                     : solve_v_mixed(c, ncycles, &used))
                                         : solve_v(c, ncycles, &used);
   if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
   c->cycles_visc = used;
@@ -1691,6 +1783,9 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
   } else if (option == BFIBM_OPT_TMA) {
     if (value < 0 || value > 2) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_TMA takes 0, 1 or 2");
     c->tma = (int)value;
+  } else if (option == BFIBM_OPT_KRYLOV) {
+    if (value < 0 || value > 1) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_KRYLOV takes 0 or 1");
+    c->krylov = (int)value;
   } else if (option == BFIBM_OPT_INNER) {
     if (value < 1 || value > 16)
       return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_INNER takes 1 to 16");

@@ -106,6 +106,45 @@ def test_inner_vcycles_per_defect_correction(inner):
         c.close()
 
 
+@pytest.mark.parametrize("inner", [1, 2])
+def test_flexible_cg_viscous_solve(inner):
+    """Flexible CG around the FP32 V-cycle for the viscous solve: the same
+    discrete system and stopping test as defect correction, so at rtol 1e-11
+    it agrees with the oracle to 1e-10; it needs fewer V-cycles than defect
+    correction on the same state; the device loop and the host loop take
+    the same iterations and give the same bits; a fixed count runs exactly
+    that many V-cycles."""
+    inst = W.c2()
+    over = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 80, "inner_cycles": inner}
+    g, o = mixed_pair(inst, 2, dict(over, krylov=1))
+    sg = g.get_stats()
+    print("fcg inner %d: cycles %d/%d res %.2e %.2e div %.2e" % (
+        inner, sg["cycles_visc"], sg["cycles_p"], sg["res_visc"], sg["res_p"], sg["div_max"]))
+    assert sg["res_visc"] <= 1e-11 and sg["res_p"] <= 1e-11
+    assert sg["cycles_visc"] % inner == 0
+    du, dp, dx = report(g, o, "c2 mixed fcg inner %d" % inner)
+    assert du <= 1e-10 and dp <= 1e-10
+    dc, _ = mixed_pair(inst, 2, over)
+    sd = dc.get_stats()
+    print("defect correction cycles %d, flexible CG %d" % (sd["cycles_visc"], sg["cycles_visc"]))
+    assert sg["cycles_visc"] < sd["cycles_visc"]
+    h = bfibm.load_instance(inst, prm_override=dict(inst["params"], precision=1, krylov=1, **over))
+    h.set_option(bfibm.OPT_GRAPH, 0)
+    h.step(2)
+    sh = h.get_stats()
+    assert sh["cycles_visc"] == sg["cycles_visc"]
+    for d in range(3):
+        assert np.array_equal(h.get_velocity(d), g.get_velocity(d))
+    f = bfibm.load_instance(inst, prm_override=dict(inst["params"], precision=1, krylov=1,
+                                                    inner_cycles=inner))
+    f.step(2)
+    sf = f.get_stats()
+    assert sf["cycles_visc"] == inst["params"]["vc_visc"]
+    assert all(np.isfinite(f.get_velocity(d)).all() for d in range(3))
+    for c in (g, dc, h, f):
+        c.close()
+
+
 @pytest.mark.slow
 def test_c3_mixed_two_steps():
     inst = W.c3(precision=1)
