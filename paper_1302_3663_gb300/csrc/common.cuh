@@ -103,14 +103,15 @@ void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, fl
 void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
                              float* const e32[3], double* const diag[3], double inv_re,
                              double* partial, cudaStream_t s, double* const r64[3] = nullptr);
-// Flexible CG around the FP32 V-cycle (mixed.cu): w = A z with partial z.q;
+// Flexible CG around the FP32 V-cycle (mixed.cu): z is the V-cycle's result
+// converted to FP64; w = A z with partial z.q;
 // p = z + beta p, q = w + beta q with partials p.q, p.r (2 nb entries);
 // x += alpha p, r -= alpha q, r32 = r, e32 = 0 with partial r.r. beta and
 // alpha are read from out[] slots on the device.
-void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, float* const z[3],
+void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, double* const z[3],
                       double* const diag[3], double inv_re, double* const w[3],
                       double* const q[3], double* partial, cudaStream_t s);
-void launch_fcg_dir(int D, const Geo& g, float* const z[3], double* const w[3], double* const p[3],
+void launch_fcg_dir(int D, const Geo& g, double* const z[3], double* const w[3], double* const p[3],
                     double* const q[3], double* const r[3], const double* out, int sl_zq,
                     int sl_pq, double* partial, cudaStream_t s);
 void launch_fcg_update(int D, const Geo& g, double* const x[3], double* const p[3],

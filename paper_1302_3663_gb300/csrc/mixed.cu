@@ -333,18 +333,20 @@ void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, fl
 //   p = z + beta p,  q = w + beta q,  alpha = (p.r) / (p.q),
 //   x += alpha p,  r -= alpha q.
 // Scalars travel between the kernels in device memory (slots of `out`).
+// (z arrives in FP64: converting each FP32 neighbour at every use would put
+// about fifteen conversions per face on GB300's small FP64 pipe)
 template <int D, int d, bool INTERIOR>
 __device__ __forceinline__ double v_apply_z(const Geo& g, const LevelPtrs<double>& L,
-                                            const F32x3& z, const double* __restrict__ diag,
+                                            const Ptr3d& z, const double* __restrict__ diag,
                                             const int ci[3], long long F, double ir) {
-  const float* const vec[3] = {z.a[0], z.a[1], z.a[2]};
-  double off = v_off64<D, d, INTERIOR, float>(g, L, vec, ci, F);
-  return diag[F] * (double)z.a[d][F] - ir * off;
+  const double* const vec[3] = {z.a[0], z.a[1], z.a[2]};
+  double off = v_off64<D, d, INTERIOR, double>(g, L, vec, ci, F);
+  return diag[F] * z.a[d][F] - ir * off;
 }
 
 template <int D, bool INTERIOR>
 __device__ __forceinline__ double v_apply_any(const Geo& g, const LevelPtrs<double>& L,
-                                              const F32x3& z, const Ptr3d& diag, int d,
+                                              const Ptr3d& z, const Ptr3d& diag, int d,
                                               const int ci[3], long long F, double ir) {
   if (d == 0) return v_apply_z<D, 0, INTERIOR>(g, L, z, diag.a[0], ci, F, ir);
   if (d == 1) return v_apply_z<D, 1, INTERIOR>(g, L, z, diag.a[1], ci, F, ir);
@@ -357,7 +359,7 @@ __device__ __forceinline__ bool block_leader() {
 
 // w = A z on every unknown face (0 on the fixed wall faces); partial sums of z.q
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, F32x3 z,
+__global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, Ptr3d z,
                                                    Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
                                                    double* partial) {
   __shared__ double sh[32];
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, F
       if (interior) v = v_apply_any<D, true>(g, L, z, diag, d, ci, F, ir);
       else if (g.per[d] || ci[d] != 0) v = v_apply_any<D, false>(g, L, z, diag, d, ci, F, ir);
       w.a[d][F] = v;
-      zq += (double)z.a[d][F] * q.a[d][F];
+      zq += z.a[d][F] * q.a[d][F];
     }
   }
   zq = block_sum(zq, sh);
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, F
 
 // p = z + beta p, q = w + beta q; partial sums of p.q (first nb) and p.r (next nb)
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_dir(Geo g, F32x3 z, Ptr3d w, Ptr3d p, Ptr3d q,
+__global__ void __launch_bounds__(256) k_fcg_dir(Geo g, Ptr3d z, Ptr3d w, Ptr3d p, Ptr3d q,
                                                  Ptr3d r, const double* __restrict__ out,
                                                  int sl_zq, int sl_pq, double* partial, int nb) {
   __shared__ double sh[32];
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(256) k_fcg_dir(Geo g, F32x3 z, Ptr3d w, Ptr3d 
     long long F = gidx(g, i, j, k);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      double pv = (double)z.a[d][F] + beta * p.a[d][F];
+      double pv = z.a[d][F] + beta * p.a[d][F];
       double qv = w.a[d][F] + beta * q.a[d][F];
       p.a[d][F] = pv;
       q.a[d][F] = qv;
@@ -459,26 +461,26 @@ F32x3 f3(float* const a[3]) {
 }
 }  // namespace
 
-void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, float* const z[3],
+void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, double* const z[3],
                       double* const diag[3], double inv_re, double* const w[3],
                       double* const q[3], double* partial, cudaStream_t s) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
   double ir = inv_re / (g.h * g.h);
-  if (D == 3) k_fcg_apply<3><<<gr, b, 0, s>>>(g, L, f3(z), p3(diag), ir, p3(w), p3(q), partial);
-  else k_fcg_apply<2><<<gr, b, 0, s>>>(g, L, f3(z), p3(diag), ir, p3(w), p3(q), partial);
+  if (D == 3) k_fcg_apply<3><<<gr, b, 0, s>>>(g, L, p3(z), p3(diag), ir, p3(w), p3(q), partial);
+  else k_fcg_apply<2><<<gr, b, 0, s>>>(g, L, p3(z), p3(diag), ir, p3(w), p3(q), partial);
 }
 
-void launch_fcg_dir(int D, const Geo& g, float* const z[3], double* const w[3], double* const p[3],
+void launch_fcg_dir(int D, const Geo& g, double* const z[3], double* const w[3], double* const p[3],
                     double* const q[3], double* const r[3], const double* out, int sl_zq,
                     int sl_pq, double* partial, cudaStream_t s) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
   int nb = (int)(gr.x * gr.y * gr.z);
   if (D == 3)
-    k_fcg_dir<3><<<gr, b, 0, s>>>(g, f3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
+    k_fcg_dir<3><<<gr, b, 0, s>>>(g, p3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
   else
-    k_fcg_dir<2><<<gr, b, 0, s>>>(g, f3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
+    k_fcg_dir<2><<<gr, b, 0, s>>>(g, p3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
 }
 
 void launch_fcg_update(int D, const Geo& g, double* const x[3], double* const p[3],

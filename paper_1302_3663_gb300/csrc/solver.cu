@@ -90,9 +90,9 @@ size_t grid_pool_bytes(const bfibm_params& P, int* nlev = nullptr) {
   for (int l = 0; l < L; ++l) {
     size_t arr = (size_t)round_up(level_elems(g[l]) * 8, 256);
     // level 0: velocity, density, force; mixed precision adds the FP64
-    // viscous diagonal and the flexible-CG directions p and q
+    // viscous diagonal and the flexible-CG vectors p, q and z
     int na = arrays_per_level(P.dim) + (l == 0 ? 3 * P.dim : 0) +
-             (l == 0 && P.precision == 1 ? 3 * P.dim : 0);
+             (l == 0 && P.precision == 1 ? 4 * P.dim : 0);
     bytes += arr * na;
     if (P.precision == 1)   // the level's arrays and the inverse viscous diagonals
       bytes += (size_t)round_up(level_elems(g[l]) * 4, 256) * (arrays_per_level(P.dim) + P.dim);
@@ -147,6 +147,7 @@ struct bfibm_ctx {
   double* vdiag[3] = {nullptr, nullptr, nullptr};   // FP64 viscous diagonal (mixed precision)
   double* cg_p[3] = {nullptr, nullptr, nullptr};    // flexible-CG direction and A times it
   double* cg_q[3] = {nullptr, nullptr, nullptr};
+  double* cg_z[3] = {nullptr, nullptr, nullptr};    // the preconditioned residual in FP64
   double* rho[3] = {nullptr, nullptr, nullptr};
   double* frc[3] = {nullptr, nullptr, nullptr};
   double* G_dev = nullptr;
@@ -707,9 +708,10 @@ bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
   CK(cudaMemsetAsync(c->sc.out + SL_PQ, 0, sizeof(double), s));
   auto iteration = [&](cudaStream_t b, int nv) {
     for (int q = 0; q < nv; ++q) vcycle_v32(c, 0);
-    launch_fcg_apply(D, L0.g, L0.d, L0.f.u, c->vdiag, c->P.inv_re, w, c->cg_q, c->sc.partial, b);
+    for (int d = 0; d < D; ++d) launch_f32_to_f64(L0.f.u[d], c->cg_z[d], level_elems(L0.g), b);
+    launch_fcg_apply(D, L0.g, L0.d, c->cg_z, c->vdiag, c->P.inv_re, w, c->cg_q, c->sc.partial, b);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_ZQ, 1.0, b);
-    launch_fcg_dir(D, L0.g, L0.f.u, w, c->cg_p, c->cg_q, r, c->sc.out, SL_ZQ, SL_PQ,
+    launch_fcg_dir(D, L0.g, c->cg_z, w, c->cg_p, c->cg_q, r, c->sc.out, SL_ZQ, SL_PQ,
                    c->sc.partial, b);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PQ, 1.0, b);
     launch_finalize_sum(c->sc.partial + nb, nb, c->sc.out, SL_PRR, 1.0, b);
@@ -1096,6 +1098,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
           c->vdiag[a] = take(Lv.g);
           c->cg_p[a] = take(Lv.g);
           c->cg_q[a] = take(Lv.g);
+          c->cg_z[a] = take(Lv.g);
         }
       }
   }

@@ -476,16 +476,19 @@ __global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int s
   }
 }
 
-template <int D, int d, typename T>
+// One colour of component d on the coarsest grid. INV: L.m[d] holds the
+// inverse of the whole diagonal (formed once per solve in shared memory), so
+// the update multiplies instead of forming the diagonal and dividing.
+template <int D, int d, typename T, bool INV>
 __device__ __forceinline__ void coarse_v_phase(const Geo& g, const LevelPtrs<T>& L, int colour,
                                                T ir) {
-  int nh = (g.n[0] + 1) >> 1;
-  long long npts = (long long)nh * g.n[1] * g.n[2];
-  for (long long q = threadIdx.x; q < npts; q += blockDim.x) {
-    int ih = (int)(q % nh);
-    long long r = q / nh;
-    int j = (int)(r % g.n[1]);
-    int k = (int)(r / g.n[1]);
+  const int nh = (g.n[0] + 1) >> 1;
+  const int npts = nh * g.n[1] * g.n[2];   // a few thousand at most on the coarsest grid
+  for (int q = threadIdx.x; q < npts; q += blockDim.x) {
+    int ih = q % nh;
+    int r = q / nh;
+    int j = r % g.n[1];
+    int k = r / g.n[1];
     int i = 2 * ih + ((j + k + colour) & 1);
     if (i >= g.n[0]) continue;
     int ci[3] = {i, j, k};
@@ -493,9 +496,29 @@ __device__ __forceinline__ void coarse_v_phase(const Geo& g, const LevelPtrs<T>&
     long long F = gidx(g, i, j, k);
     T off, dgV;
     v_terms<D, d, T>(g, L, ci, F, off, dgV);
-    L.u[d][F] = (L.uf[d][F] + ir * off) / (L.m[d][F] + ir * dgV);
+    if constexpr (INV) L.u[d][F] = (L.uf[d][F] + ir * off) * L.m[d][F];
+    else L.u[d][F] = (L.uf[d][F] + ir * off) / (L.m[d][F] + ir * dgV);
   }
   __syncthreads();
+}
+
+// m_d -> 1 / (m_d + ir dgV) in place on the staged copy (each point reads
+// only its own m_d)
+template <int D, int d, typename T>
+__device__ __forceinline__ void coarse_v_invert(const Geo& g, const LevelPtrs<T>& L, T ir) {
+  const int ncell = g.n[0] * g.n[1] * g.n[2];
+  for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
+    int i = q % g.n[0];
+    int r = q / g.n[0];
+    int j = r % g.n[1];
+    int k = r / g.n[1];
+    int ci[3] = {i, j, k};
+    if (!g.per[d] && ci[d] == 0) continue;
+    long long F = gidx(g, i, j, k);
+    T off, dgV;
+    v_terms<D, d, T>(g, L, ci, F, off, dgV);
+    L.m[d][F] = T(1) / (L.m[d][F] + ir * dgV);
+  }
 }
 
 template <int D, typename T>
@@ -521,19 +544,34 @@ __global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> Lg, int s
       stage_in(L.mue[e], Lg.mue[e], nel);
     }
     __syncthreads();
+    // the coefficients are fixed through the solve: invert each diagonal once
+    coarse_v_invert<D, 0, T>(g, L, ir);
+    coarse_v_invert<D, 1, T>(g, L, ir);
+    if constexpr (D == 3) coarse_v_invert<D, 2, T>(g, L, ir);
+    __syncthreads();
+    for (int it = 0; it < sweeps; ++it) {
+      coarse_v_phase<D, 0, T, true>(g, L, 0, ir);
+      coarse_v_phase<D, 0, T, true>(g, L, 1, ir);
+      coarse_v_phase<D, 1, T, true>(g, L, 0, ir);
+      coarse_v_phase<D, 1, T, true>(g, L, 1, ir);
+      if constexpr (D == 3) {
+        coarse_v_phase<D, 2, T, true>(g, L, 0, ir);
+        coarse_v_phase<D, 2, T, true>(g, L, 1, ir);
+      }
+    }
+    for (int d = 0; d < D; ++d) stage_out(Lg.u[d], L.u[d], nel);
+    return;
   }
   for (int it = 0; it < sweeps; ++it) {
-    coarse_v_phase<D, 0, T>(g, L, 0, ir);
-    coarse_v_phase<D, 0, T>(g, L, 1, ir);
-    coarse_v_phase<D, 1, T>(g, L, 0, ir);
-    coarse_v_phase<D, 1, T>(g, L, 1, ir);
+    coarse_v_phase<D, 0, T, false>(g, L, 0, ir);
+    coarse_v_phase<D, 0, T, false>(g, L, 1, ir);
+    coarse_v_phase<D, 1, T, false>(g, L, 0, ir);
+    coarse_v_phase<D, 1, T, false>(g, L, 1, ir);
     if constexpr (D == 3) {
-      coarse_v_phase<D, 2, T>(g, L, 0, ir);
-      coarse_v_phase<D, 2, T>(g, L, 1, ir);
+      coarse_v_phase<D, 2, T, false>(g, L, 0, ir);
+      coarse_v_phase<D, 2, T, false>(g, L, 1, ir);
     }
   }
-  if (use_smem)
-    for (int d = 0; d < D; ++d) stage_out(Lg.u[d], L.u[d], nel);
 }
 
 // ---------------------------------------------------------------------------
