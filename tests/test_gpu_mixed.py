@@ -145,6 +145,24 @@ def test_flexible_cg_viscous_solve(inner):
         c.close()
 
 
+def test_flexible_cg_2d_matches_the_oracle():
+    """The 2D biofilm case with the benchmark's solver settings (flexible CG
+    around two FP32 V(2,2) cycles, rtol 1e-11): u and p agree with the FP64
+    oracle to 1e-10 over several steps, spring breaks included."""
+    inst = W.c1()
+    over = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 100, "nu1": 2, "nu2": 2,
+            "inner_cycles": 2, "krylov": 1}
+    g, o = mixed_pair(inst, 6, over)
+    sg = g.get_stats()
+    assert sg["res_visc"] <= 1e-11 and sg["res_p"] <= 1e-11
+    du, dp, dx = report(g, o, "c1 mixed fcg")
+    assert du <= 1e-10 and dp <= 1e-10 and dx <= 1e-10
+    ig, _ = g.get_broken()
+    io, _ = o.broken()
+    assert set(ig) == set(io)
+    g.close()
+
+
 @pytest.mark.slow
 def test_c3_mixed_two_steps():
     inst = W.c3(precision=1)

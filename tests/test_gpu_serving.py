@@ -113,12 +113,21 @@ def test_contexts_with_different_spread_regions():
     b.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_alone_and_in_batch_bit_identical(precision):
+# the served benchmark's solver: relative residual 1e-11, flexible CG around
+# two FP32 V(2,2) cycles for the viscous solve
+TOL_CG = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 100, "gamma_coarse": 0.8,
+          "nu1": 2, "nu2": 2, "inner_cycles": 2, "krylov": 1}
+
+
+@pytest.mark.parametrize("precision,solver", [(0, None), (1, None), (1, TOL_CG)],
+                         ids=["fp64", "mixed", "mixed_tolerance_cg"])
+def test_alone_and_in_batch_bit_identical(precision, solver):
     # node forces are summed per node in a fixed order and the spread sums f
     # and rho as fixed-point integers, so nothing depends on the order of
     # atomic additions: a simulation gives the same bits alone and in a batch
     insts = [small_instance(i, e=(32 if i % 2 else 48), precision=precision) for i in range(3)]
+    for inst in insts:
+        inst["params"].update(solver or {})
     alone = []
     for inst in insts:
         c = bfibm.load_instance(inst)
