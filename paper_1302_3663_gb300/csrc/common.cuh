@@ -114,6 +114,8 @@ void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, double* c
 void launch_fcg_dir(int D, const Geo& g, double* const z[3], double* const w[3], double* const p[3],
                     double* const q[3], double* const r[3], const double* out, int sl_zq,
                     int sl_pq, double* partial, cudaStream_t s);
+// blocks of the flat direction and update passes (their partial sums)
+int fcg_flat_blocks(const Geo& g);
 void launch_fcg_update(int D, const Geo& g, double* const x[3], double* const p[3],
                        double* const q[3], double* const r[3], float* const r32[3],
                        float* const e32[3], const double* out, int sl_pq, int sl_pr,

@@ -386,66 +386,83 @@ __global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, P
   if (block_leader()) partial[block_linear()] = zq;
 }
 
+// The direction and update passes touch every stored element of the level
+// arrays (pads and fixed wall faces hold 0 in every vector, so they add
+// nothing): flat grid-stride loops over pairs of doubles.
+constexpr int kFlatBlocks = 1216;   // 8 blocks of 256 threads per SM on 152 SMs
+
 // p = z + beta p, q = w + beta q; partial sums of p.q (first nb) and p.r (next nb)
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_dir(Geo g, Ptr3d z, Ptr3d w, Ptr3d p, Ptr3d q,
-                                                 Ptr3d r, const double* __restrict__ out,
-                                                 int sl_zq, int sl_pq, double* partial, int nb) {
+__global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d w, Ptr3d p,
+                                                 Ptr3d q, Ptr3d r, const double* __restrict__ out,
+                                                 int sl_zq, int sl_pq, double* partial) {
   __shared__ double sh[32];
   const double pq_old = out[sl_pq];
   const double beta = pq_old != 0.0 ? -out[sl_zq] / pq_old : 0.0;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
   double pq = 0.0, pr = 0.0;
-  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
-    long long F = gidx(g, i, j, k);
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      double pv = z.a[d][F] + beta * p.a[d][F];
-      double qv = w.a[d][F] + beta * q.a[d][F];
-      p.a[d][F] = pv;
-      q.a[d][F] = qv;
-      pq += pv * qv;
-      pr += pv * r.a[d][F];
+  for (int d = 0; d < D; ++d) {
+    const double2* __restrict__ zz = reinterpret_cast<const double2*>(z.a[d]);
+    const double2* __restrict__ ww = reinterpret_cast<const double2*>(w.a[d]);
+    const double2* __restrict__ rr = reinterpret_cast<const double2*>(r.a[d]);
+    double2* pp = reinterpret_cast<double2*>(p.a[d]);
+    double2* qq = reinterpret_cast<double2*>(q.a[d]);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < npair;
+         k += (long long)gridDim.x * blockDim.x) {
+      double2 zv = zz[k], wv = ww[k], pv = pp[k], qv = qq[k], rv = rr[k];
+      pv.x = zv.x + beta * pv.x;
+      pv.y = zv.y + beta * pv.y;
+      qv.x = wv.x + beta * qv.x;
+      qv.y = wv.y + beta * qv.y;
+      pp[k] = pv;
+      qq[k] = qv;
+      pq += pv.x * qv.x + pv.y * qv.y;
+      pr += pv.x * rv.x + pv.y * rv.y;
     }
   }
   pq = block_sum(pq, sh);
   pr = block_sum(pr, sh);
-  if (block_leader()) {
-    partial[block_linear()] = pq;
-    partial[nb + block_linear()] = pr;
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = pq;
+    partial[gridDim.x + blockIdx.x] = pr;
   }
 }
 
 // x += alpha p, r -= alpha q; the new residual as the FP32 right-hand side of
 // the next preconditioning (correction zeroed); partial sums of r.r
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_update(Geo g, Ptr3d x, Ptr3d p, Ptr3d q, Ptr3d r,
-                                                    F32x3 r32, F32x3 e32,
+__global__ void __launch_bounds__(256) k_fcg_update(long long npair, Ptr3d x, Ptr3d p, Ptr3d q,
+                                                    Ptr3d r, F32x3 r32, F32x3 e32,
                                                     const double* __restrict__ out, int sl_pq,
                                                     int sl_pr, double* partial) {
   __shared__ double sh[32];
   const double pq = out[sl_pq];
   const double alpha = pq != 0.0 ? out[sl_pr] / pq : 0.0;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
-  double rr = 0.0;
-  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
-    long long F = gidx(g, i, j, k);
+  double rs = 0.0;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      x.a[d][F] += alpha * p.a[d][F];
-      double rv = r.a[d][F] - alpha * q.a[d][F];
-      r.a[d][F] = rv;
-      r32.a[d][F] = (float)rv;
-      e32.a[d][F] = 0.0f;
-      rr += rv * rv;
+  for (int d = 0; d < D; ++d) {
+    double2* xx = reinterpret_cast<double2*>(x.a[d]);
+    const double2* __restrict__ pp = reinterpret_cast<const double2*>(p.a[d]);
+    const double2* __restrict__ qq = reinterpret_cast<const double2*>(q.a[d]);
+    double2* rr = reinterpret_cast<double2*>(r.a[d]);
+    float2* r2 = reinterpret_cast<float2*>(r32.a[d]);
+    float2* e2 = reinterpret_cast<float2*>(e32.a[d]);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < npair;
+         k += (long long)gridDim.x * blockDim.x) {
+      double2 xv = xx[k], pv = pp[k], qv = qq[k], rv = rr[k];
+      xv.x += alpha * pv.x;
+      xv.y += alpha * pv.y;
+      rv.x -= alpha * qv.x;
+      rv.y -= alpha * qv.y;
+      xx[k] = xv;
+      rr[k] = rv;
+      r2[k] = make_float2((float)rv.x, (float)rv.y);
+      e2[k] = make_float2(0.f, 0.f);
+      rs += rv.x * rv.x + rv.y * rv.y;
     }
   }
-  rr = block_sum(rr, sh);
-  if (block_leader()) partial[block_linear()] = rr;
+  rs = block_sum(rs, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = rs;
 }
 
 namespace {
@@ -471,30 +488,39 @@ void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, double* c
   else k_fcg_apply<2><<<gr, b, 0, s>>>(g, L, p3(z), p3(diag), ir, p3(w), p3(q), partial);
 }
 
+// flat loops run over pairs: the level arrays hold an even number of
+// elements (rows padded to a multiple of 8) and start on 256-byte boundaries
+long long flat_elems(const Geo& g) { return g.st[2] * g.s[2]; }
+
+int fcg_flat_blocks(const Geo& g) {
+  long long npair = flat_elems(g) / 2;
+  long long nb = (npair + 255) / 256;
+  return (int)(nb < kFlatBlocks ? (nb < 1 ? 1 : nb) : kFlatBlocks);
+}
+
 void launch_fcg_dir(int D, const Geo& g, double* const z[3], double* const w[3], double* const p[3],
                     double* const q[3], double* const r[3], const double* out, int sl_zq,
                     int sl_pq, double* partial, cudaStream_t s) {
-  dim3 b = blk3(D);
-  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
-  int nb = (int)(gr.x * gr.y * gr.z);
+  const long long npair = flat_elems(g) / 2;
+  const int nb = fcg_flat_blocks(g);
   if (D == 3)
-    k_fcg_dir<3><<<gr, b, 0, s>>>(g, p3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
+    k_fcg_dir<3><<<nb, 256, 0, s>>>(npair, p3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial);
   else
-    k_fcg_dir<2><<<gr, b, 0, s>>>(g, p3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial, nb);
+    k_fcg_dir<2><<<nb, 256, 0, s>>>(npair, p3(z), p3(w), p3(p), p3(q), p3(r), out, sl_zq, sl_pq, partial);
 }
 
 void launch_fcg_update(int D, const Geo& g, double* const x[3], double* const p[3],
                        double* const q[3], double* const r[3], float* const r32[3],
                        float* const e32[3], const double* out, int sl_pq, int sl_pr,
                        double* partial, cudaStream_t s) {
-  dim3 b = blk3(D);
-  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  const long long npair = flat_elems(g) / 2;
+  const int nb = fcg_flat_blocks(g);
   if (D == 3)
-    k_fcg_update<3><<<gr, b, 0, s>>>(g, p3(x), p3(p), p3(q), p3(r), f3(r32), f3(e32), out, sl_pq,
-                                     sl_pr, partial);
+    k_fcg_update<3><<<nb, 256, 0, s>>>(npair, p3(x), p3(p), p3(q), p3(r), f3(r32), f3(e32), out,
+                                       sl_pq, sl_pr, partial);
   else
-    k_fcg_update<2><<<gr, b, 0, s>>>(g, p3(x), p3(p), p3(q), p3(r), f3(r32), f3(e32), out, sl_pq,
-                                     sl_pr, partial);
+    k_fcg_update<2><<<nb, 256, 0, s>>>(npair, p3(x), p3(p), p3(q), p3(r), f3(r32), f3(e32), out,
+                                       sl_pq, sl_pr, partial);
 }
 
 void launch_v_diag(int D, const Geo& g, const LevelPtrs<double>& L, double* const diag[3],

@@ -696,6 +696,7 @@ bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
   const bool tol = ncycles <= 0;
   const int inner = c->inner;
   const int nb = red_blocks_3d(D, L0.g);
+  const int nbf = fcg_flat_blocks(L0.g);
   double* w[3] = {L0.d.u2[0], L0.d.u2[1], L0.d.u2[2]};
   double* r[3] = {L0.d.ur[0], L0.d.ur[1], L0.d.ur[2]};
   if (tol || c->collect_stats) launch_norm2(D, L0.g, L0.d.uf, D, c->sc, SL_VF, s);
@@ -713,11 +714,11 @@ bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_ZQ, 1.0, b);
     launch_fcg_dir(D, L0.g, c->cg_z, w, c->cg_p, c->cg_q, r, c->sc.out, SL_ZQ, SL_PQ,
                    c->sc.partial, b);
-    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PQ, 1.0, b);
-    launch_finalize_sum(c->sc.partial + nb, nb, c->sc.out, SL_PRR, 1.0, b);
+    launch_finalize_sum(c->sc.partial, nbf, c->sc.out, SL_PQ, 1.0, b);
+    launch_finalize_sum(c->sc.partial + nbf, nbf, c->sc.out, SL_PRR, 1.0, b);
     launch_fcg_update(D, L0.g, L0.d.u, c->cg_p, c->cg_q, r, L0.f.uf, L0.f.u, c->sc.out, SL_PQ,
                       SL_PRR, c->sc.partial, b);
-    launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
+    launch_finalize_sum(c->sc.partial, nbf, c->sc.out, SL_VR, 1.0, b);
   };
   if (tol && c->capturing) {
     cudaMemsetAsync(c->dev_cycles, 0, sizeof(int), s);
