@@ -196,9 +196,10 @@ bfibm_status bfibm_refresh(bfibm_ctx* c);
 bfibm_status bfibm_build_coefficients(bfibm_ctx* c);
 bfibm_status bfibm_stage(bfibm_ctx* c, int stage);
 /* Multigrid solves on level 0 (ncycles > 0 fixed, 0 = until rtol), in the
-   context's precision (FP64 V-cycles, or FP32 V-cycles inside FP64 defect
-   correction); the cycles used are written to *cycles when cycles is not
-   NULL. */
+   context's precision and solver options (FP64 V-cycles; or FP32 V-cycles
+   inside FP64 defect correction, BFIBM_OPT_INNER of them per FP64 residual,
+   and for the viscous solve inside flexible CG with BFIBM_OPT_KRYLOV); the
+   V-cycles used are written to *cycles when cycles is not NULL. */
 bfibm_status bfibm_solve_pressure(bfibm_ctx* c, int ncycles, int32_t* cycles);
 bfibm_status bfibm_solve_viscous(bfibm_ctx* c, int ncycles, int32_t* cycles);
 /* nsweeps red-black sweeps on one level (Sec. 3.5). Asynchronous: returns

@@ -398,7 +398,9 @@ __global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d
                                                  int sl_zq, int sl_pq, double* partial) {
   __shared__ double sh[32];
   const double pq_old = out[sl_pq];
-  const double beta = pq_old != 0.0 ? -out[sl_zq] / pq_old : 0.0;
+  // the first direction is z itself: the previous solve's p and q are not read
+  const bool first = pq_old == 0.0;
+  const double beta = first ? 0.0 : -out[sl_zq] / pq_old;
   double pq = 0.0, pr = 0.0;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -409,11 +411,14 @@ __global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d
     double2* qq = reinterpret_cast<double2*>(q.a[d]);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < npair;
          k += (long long)gridDim.x * blockDim.x) {
-      double2 zv = zz[k], wv = ww[k], pv = pp[k], qv = qq[k], rv = rr[k];
-      pv.x = zv.x + beta * pv.x;
-      pv.y = zv.y + beta * pv.y;
-      qv.x = wv.x + beta * qv.x;
-      qv.y = wv.y + beta * qv.y;
+      double2 zv = zz[k], wv = ww[k], rv = rr[k], pv = zv, qv = wv;
+      if (!first) {
+        const double2 po = pp[k], qo = qq[k];
+        pv.x += beta * po.x;
+        pv.y += beta * po.y;
+        qv.x += beta * qo.x;
+        qv.y += beta * qo.y;
+      }
       pp[k] = pv;
       qq[k] = qv;
       pq += pv.x * qv.x + pv.y * qv.y;
