@@ -189,7 +189,10 @@ def _stream_handle(stream):
 
 
 class Context:
-    """One simulation on the current CUDA device (see bfibm_create)."""
+    """One simulation on the current CUDA device (see bfibm_create). `prm`
+    holds the fields of bfibm_params and, for mixed precision, two solver
+    options: `inner_cycles` (FP32 V-cycles per FP64 residual) and `krylov`
+    (1: flexible CG around the V-cycles for the viscous solve)."""
 
     def __init__(self, prm, stream=None):
         self.lib = lib()
