@@ -203,15 +203,20 @@ class Clocks:
 
 
 def dist_setup(args):
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE): NCCL on
+    GPUs; gloo where no GPU is visible (the host-side logic of the replica
+    runs, which the CPU tests exercise)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    gpu = torch.cuda.is_available()
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
+        if gpu:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if gpu else "gloo")
+    elif gpu:
         torch.cuda.set_device(0)
     return world, rank, local
 
@@ -221,17 +226,26 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
 
 def max_over_ranks(world, v):
+    """The slowest rank's value (every rank gets it)."""
     import torch
     if world == 1:
         return v
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(cells, steps, world, ms_max):
+    """Whole-job cell-steps per second of `world` independent replicas: the
+    units every rank processed over the slowest rank's time."""
+    return cells * steps * world / (ms_max / 1e3)
 
 
 def alg_bytes_visc_sweep(dim, cells, elem):
@@ -386,7 +400,7 @@ def run_ours(args):
     with Clocks(local) as clk:
         ms = timed_steps(ctx, stream, args.steps, world)
     lc1 = ctx.launch_counts()
-    value = cells * args.steps * world / (ms / 1e3)
+    value = replica_throughput(cells, args.steps, world, ms)
     # kernels launched in the timed region: top-level graph nodes per step plus
     # the loop bodies times the iterations the device ran
     launches = None
