@@ -87,6 +87,12 @@ def parse():
                          "work_units: cycles and work units of one solve against the number "
                          "of multigrid levels (Sec. 4.3.1); refinement: convergence rates in "
                          "time and space (Sec. 4.3.2-4.3.3) on the GPU")
+    ap.add_argument("--save-plans", default=None,
+                    help="write the FP32 sweep choices the autotuner made (JSON) after the "
+                         "context is created")
+    ap.add_argument("--load-plans", default=None,
+                    help="pin FP32 sweep choices written by --save-plans instead of this "
+                         "process's own tuning (a profiler distorts the tuner's timings)")
     ap.add_argument("--no-tune-gamma", action="store_true",
                     help="keep one coarse viscosity scaling for every level instead of tuning "
                          "it per level before the timed region")
@@ -382,6 +388,12 @@ def run_ours(args):
     if args.no_graph:
         ctx.set_option(bfibm.OPT_GRAPH, 0)
     ctx.set_option(bfibm.OPT_TMA, args.tma)
+    if args.load_plans:
+        with open(args.load_plans) as f:
+            ctx.pin_sweep_plans(json.load(f))
+    if args.save_plans:
+        with open(args.save_plans, "w") as f:
+            json.dump(ctx.sweep_plans(), f)
     ctx.step(args.warmup)
     ctx.synchronize()
     if args.solver == "tol" and not args.no_tune_gamma:

@@ -285,6 +285,14 @@ bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]);
    the built-in choice. BFIBM_EINVAL for an FP64 context, a bad level or kind,
    or a level shape the tuner has not timed. No counterpart in the paper. */
 bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[4]);
+/* Pin the one-pass FP32 sweep with shape {tile rows (0: built-in), planes per
+   chunk (0: built-in), planes per phase (1 or 2), threads per row (0 or a
+   multiple of 32 up to 128)} for the shape of one level and kind, process-wide,
+   in place of the autotuner's choice (the TMA sweep is no longer used there);
+   the next step captures a new step graph. 3D mixed-precision contexts only;
+   BFIBM_EINVAL otherwise or for a shape outside those ranges. Same results to
+   the bit as any other shape. No counterpart in the paper. */
+bfibm_status bfibm_sweep_set_shape(bfibm_ctx* c, int level, int kind, const int32_t shape[4]);
 /* Pin the TMA sweep's plan {tile rows, planes per chunk, planes prefetched
    (1..3), columns per strip (>= n[0]: whole rows), grid blocks (0: as many as
    fit at once)} for the shape of one level, process-wide, in place of the

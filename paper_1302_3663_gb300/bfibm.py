@@ -77,6 +77,7 @@ SIGNATURES = {
     "bfibm_set_field": [_V, _i, _i, _i, _DP],
     "bfibm_tma_plan": [_V, _i, _i, _IP],
     "bfibm_sweep_shape": [_V, _i, _i, _IP],
+    "bfibm_sweep_set_shape": [_V, _i, _i, _IP],
     "bfibm_set_gamma": [_V, _DP],
     "bfibm_state_bytes": [_V, C.POINTER(_L)],
     "bfibm_save_state": [_V, _V, _L],
@@ -351,6 +352,34 @@ class Context:
         out = (C.c_int32 * 4)()
         st = self.lib.bfibm_sweep_shape(self.h, level, kind, out)
         return tuple(out) if st == OK else None
+
+    def sweep_set_shape(self, level, kind, shape):
+        """Pin (tile rows, planes per chunk, planes per phase, threads per
+        row) of the one-pass FP32 sweep for the shape of a level; see
+        bfibm_sweep_set_shape."""
+        arr = (C.c_int32 * 4)(*[int(v) for v in shape])
+        self._chk(self.lib.bfibm_sweep_set_shape(self.h, level, kind, arr),
+                  "bfibm_sweep_set_shape")
+
+    def sweep_plans(self):
+        """Every tuned FP32 sweep choice of this context's levels: a list of
+        (level, kind, TMA plan or None, one-pass shape)."""
+        out = []
+        for level in range(self.levels):
+            for kind in list(range(self.dim)) + [3]:
+                shape = self.sweep_shape(level, kind)
+                if shape is not None:
+                    out.append((level, kind, self.tma_plan(level, kind), shape))
+        return out
+
+    def pin_sweep_plans(self, plans):
+        """Pin choices recorded by sweep_plans (of a context with the same
+        level shapes), so that another process runs the same kernels."""
+        for level, kind, tma, shape in plans:
+            if tma is not None:
+                self.tma_set_plan(level, kind, tma)
+            else:
+                self.sweep_set_shape(level, kind, shape)
 
     def tma_set_plan(self, level, kind, plan):
         """Pin (tile rows, planes per chunk, planes prefetched, strip columns,

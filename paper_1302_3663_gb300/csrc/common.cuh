@@ -157,6 +157,7 @@ cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K,
 bool tma_set_plan(int K, const Geo& g, const int in[5]);
 // the one-pass sweep's tuned tile rows and chunk planes for a level shape
 bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX);
+bool ring_set_shape(int K, const Geo& g, const int in[4]);
 // whether the tuner found the TMA sweep faster than the one-pass sweep
 bool tma_chosen(int K, const Geo& g);
 // tuned plan of a level shape: tile rows, chunk planes, prefetch planes,

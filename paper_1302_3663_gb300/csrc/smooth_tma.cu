@@ -787,6 +787,25 @@ bool tma_set_plan(int K, const Geo& g, const int in[5]) {
   return true;
 }
 
+// Pin the one-pass sweep (not the TMA one) with shape {TY, KC, NP, BX} for
+// the level shape of g, process-wide.
+bool ring_set_shape(int K, const Geo& g, const int in[4]) {
+  if (in[0] < 0 || in[1] < 0 || (in[2] != 1 && in[2] != 2) || in[3] < 0 || in[3] > 128 ||
+      in[3] % 32 != 0)
+    return false;
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  Plan pl;
+  auto it = g_plans.find(plan_key(K, g));
+  if (it != g_plans.end()) pl = it->second;
+  pl.tma = false;
+  pl.rTY = in[0];
+  pl.rKC = in[1];
+  pl.rNP = in[2];
+  pl.rBX = in[3];
+  g_plans[plan_key(K, g)] = pl;
+  return true;
+}
+
 bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   auto it = g_plans.find(plan_key(K, g));

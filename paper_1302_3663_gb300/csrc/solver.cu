@@ -1766,6 +1766,18 @@ bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[4]
   return BFIBM_OK;
 }
 
+bfibm_status bfibm_sweep_set_shape(bfibm_ctx* c, int level, int kind, const int32_t shape[4]) {
+  READY(c);
+  if (!shape || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
+      (kind < 3 && kind >= c->D) || c->P.precision != 1 || c->D != 3)
+    return set_err(c, BFIBM_EINVAL, "no FP32 sweep of this kind on this level");
+  int v[4] = {shape[0], shape[1], shape[2], shape[3]};
+  if (!ring_set_shape(kind, c->lev[level].g, v)) return set_err(c, BFIBM_EINVAL, "bad shape");
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  return BFIBM_OK;
+}
+
 bfibm_status bfibm_tma_set_plan(bfibm_ctx* c, int level, int kind, const int32_t plan[5]) {
   READY(c);
   if (!plan || level < 0 || level >= c->L || kind < 0 || kind > 3 ||

@@ -91,3 +91,24 @@ def test_tma_sweep_bit_identical_on_the_benchmark_grid():
             assert np.array_equal(x, y)
     assert c.get_stats()["wait_timeouts"] == 0
     c.close()
+
+
+def test_pinned_sweep_shape_gives_the_same_bits():
+    """A one-pass sweep shape pinned in place of the tuner's choice (what a
+    profiled run does to reproduce a live run's kernels) changes only the
+    launch shape, never a bit of the result; shapes outside the documented
+    ranges are refused."""
+    c = context((48, 40, 64), (0, 0, 1), 2)
+    f = random_inputs(c, np.random.default_rng(7))
+    a = sweep(c, f, 1, False, 2)
+    for d in range(3):
+        c.sweep_set_shape(0, d, (4, 8, 2, 32))
+        assert c.sweep_shape(0, d) == (4, 8, 2, 32)
+    b = sweep(c, f, 1, False, 2)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    with pytest.raises(bfibm.BfibmError):
+        c.sweep_set_shape(0, 0, (4, 8, 3, 32))
+    with pytest.raises(bfibm.BfibmError):
+        c.sweep_set_shape(0, 0, (4, 8, 1, 48))
+    c.close()
