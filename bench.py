@@ -119,7 +119,9 @@ def describe(inst):
     from paper_1302_3663_gb300 import workloads as W
     p = inst["params"]
     n = p["n"][:p["dim"]]
-    prec = "fp64" if p.get("precision", 0) == 0 else "fp32 V-cycles in fp64 defect correction"
+    prec = ("fp64" if p.get("precision", 0) == 0 else
+            "fp32 V-cycles in fp64 flexible CG (viscous) and defect correction (pressure)"
+            if p.get("krylov", 0) else "fp32 V-cycles in fp64 defect correction")
     gl = [g for g in p.get("gamma_levels", [])[1:] if g > 0]
     vc = ("%d viscous + %d pressure V(%d,%d) cycles per step" %
           (p["vc_visc"], p["vc_p"], p["nu1"], p["nu2"]) if p["vc_visc"] > 0
