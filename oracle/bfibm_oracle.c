@@ -800,6 +800,19 @@ static int solve_v(or_sim* S, int ncycles) {
   return cyc;
 }
 
+/* Grid transfers between level l and l+1 (for the pins of the transfers): comp < 0 is the
+   cell-centred (pressure) pair, comp = d the face pair of velocity component d. The
+   restriction overwrites `coarse`; the prolongation adds into `fine`. */
+void or_restrict(void* sim, int l, int comp, const double* fine, double* coarse) {
+  or_sim* S = (or_sim*)sim;
+  if (comp < 0) restrict_cell(S, &S->lev[l], &S->lev[l + 1], fine, coarse);
+  else restrict_face(S, &S->lev[l], &S->lev[l + 1], comp, fine, coarse);
+}
+void or_prolong_add(void* sim, int l, int comp, const double* coarse, double* fine) {
+  or_sim* S = (or_sim*)sim;
+  if (comp < 0) prolong_add_cell(S, &S->lev[l], &S->lev[l + 1], coarse, fine);
+  else prolong_add_face(S, &S->lev[l], &S->lev[l + 1], comp, coarse, fine);
+}
 int or_solve_p(void* sim, int ncycles) { return solve_p((or_sim*)sim, ncycles); }
 int or_solve_visc(void* sim, int ncycles) { return solve_v((or_sim*)sim, ncycles); }
 void or_vcycle_p(void* sim) { vcycle_p((or_sim*)sim, 0); }
@@ -812,10 +825,13 @@ void or_residual_visc(void* sim, int l) { v_residual((or_sim*)sim, l); }
 /* ------------------------------------------------------------------------- */
 /* Momentum right-hand side, Eq. (NSdis1-1), explicit part:                    */
 /*   rhs_d = (rho_d sigma/dt) u_d - rho_d Adv_d(u) + c_f f_d + G [d = flow]     */
-/* Adv_d = 1/2 (u . D u_d + D . (u u_d)): the advective half uses centred wide */
-/* differences of u_d with the velocity averaged to the d-face (4 points for  */
-/* the other components); the conservative half differences the fluxes at the */
-/* cell centres (d) and edges (e != d), where each factor is a 2-point average.*/
+/* Adv_d = 1/2 (u . D u_d + D . (u u_d)). On the paper's collocated grid D0 is  */
+/* antisymmetric, so this skew form gives sum_x u_k Adv_k = 0 for every field.  */
+/* The staggered reading keeps that: along each axis e, the advecting velocity */
+/* U_e sits at the two flux points of the d-face (cell centres for e = d, the  */
+/* (d,e)-edges otherwise) as a 2-point mean; the conservative half differences */
+/* the fluxes U_e * (2-point mean of u_d); the advective half averages the two  */
+/* one-sided products U_e * (one-sided difference of u_d).                      */
 /* ------------------------------------------------------------------------- */
 static double ue_avg_at_face(const or_sim* S, const or_level* L, const double* ue, int d, int e,
                              const int F[3], int qoff) {
@@ -836,27 +852,25 @@ static double advection_point(const or_sim* S, const or_level* L, double* const 
   const double* ud = u[d];
   int nd = L->n[d], perd = S->P.periodic[d];
   double udF = ud[LIc(L, F)];
-  int Fp[3] = {F[0], F[1], F[2]}, Fm[3] = {F[0], F[1], F[2]};
-  Fp[d] = perd ? wrapi(F[d] + 1, nd) : F[d] + 1;
-  Fm[d] = perd ? wrapi(F[d] - 1, nd) : F[d] - 1;
-  double udp = ud[LIc(L, Fp)], udm = ud[LIc(L, Fm)];
-  /* advective half */
-  double adv = udF * (udp - udm) / (2.0 * h);
-  /* conservative half, along d: fluxes at the two cells */
-  double cp = 0.5 * (udF + udp), cm = 0.5 * (udm + udF);
-  double cons = (cp * cp - cm * cm) / h;
+  double adv = 0.0, cons = 0.0;
   for (int e = 0; e < S->D; ++e) {
-    if (e == d) continue;
-    const double* ue = u[e];
-    double up = ud_at(S, L, ud, d, F, e, F[e] + 1);
-    double um = ud_at(S, L, ud, d, F, e, F[e] - 1);
-    double ue_lo = ue_avg_at_face(S, L, ue, d, e, F, 0);
-    double ue_hi = ue_avg_at_face(S, L, ue, d, e, F, 1);
-    double ubar = 0.5 * (ue_lo + ue_hi);
-    adv += ubar * (up - um) / (2.0 * h);
-    double flux_hi = ue_hi * 0.5 * (udF + up);
-    double flux_lo = ue_lo * 0.5 * (um + udF);
-    cons += (flux_hi - flux_lo) / h;
+    double up, um, Uhi, Ulo;   /* u_d one step up/down along e; U_e at the flux points */
+    if (e == d) {
+      int Fp[3] = {F[0], F[1], F[2]}, Fm[3] = {F[0], F[1], F[2]};
+      Fp[d] = perd ? wrapi(F[d] + 1, nd) : F[d] + 1;
+      Fm[d] = perd ? wrapi(F[d] - 1, nd) : F[d] - 1;
+      up = ud[LIc(L, Fp)];
+      um = ud[LIc(L, Fm)];
+      Uhi = 0.5 * (udF + up);   /* u_d at the cell centres beside the face */
+      Ulo = 0.5 * (um + udF);
+    } else {
+      up = ud_at(S, L, ud, d, F, e, F[e] + 1);
+      um = ud_at(S, L, ud, d, F, e, F[e] - 1);
+      Uhi = ue_avg_at_face(S, L, u[e], d, e, F, 1);   /* u_e on the (d,e)-edges */
+      Ulo = ue_avg_at_face(S, L, u[e], d, e, F, 0);
+    }
+    adv += 0.5 * (Uhi * (up - udF) / h + Ulo * (udF - um) / h);
+    cons += (Uhi * 0.5 * (udF + up) - Ulo * 0.5 * (um + udF)) / h;
   }
   return 0.5 * (adv + cons);
 }

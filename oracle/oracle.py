@@ -69,6 +69,7 @@ def _lib(omp=False):
         "or_apply_p": (v, [p, i, _DP, _DP]),
         "or_apply_visc": (v, [p, i, C.POINTER(_DP), C.POINTER(_DP)]),
         "or_advection": (v, [p, C.POINTER(_DP), C.POINTER(_DP)]),
+        "or_restrict": (v, [p, i, i, _DP, _DP]), "or_prolong_add": (v, [p, i, i, _DP, _DP]),
         "or_visc_diag": (d, [p, i, i, i, i, i]), "or_p_diag": (d, [p, i, i, i, i]),
         "or_solve_p": (i, [p, i]), "or_solve_visc": (i, [p, i]),
         "or_vcycle_p": (v, [p]), "or_vcycle_visc": (v, [p]),
@@ -243,6 +244,21 @@ class Oracle:
         outs, optr = self._vec3([np.zeros(self.shape(0)) for _ in range(3)], 0)
         self.lib.or_advection(self.h, ptr, optr)
         return [outs[d].copy() for d in range(self.dim)]
+
+    def restrict(self, fine, level=0, comp=-1):
+        """Restriction from `level` to `level + 1`: comp < 0 cell-centred, else the
+        faces of velocity component comp."""
+        f = np.ascontiguousarray(fine, dtype=np.float64).reshape(self.shape(level))
+        out = np.zeros(self.shape(level + 1))
+        self.lib.or_restrict(self.h, level, int(comp), _dp(f), _dp(out))
+        return out
+
+    def prolong_add(self, coarse, fine, level=0, comp=-1):
+        """fine (on `level`) plus the prolongation of coarse (on `level + 1`)."""
+        c = np.ascontiguousarray(coarse, dtype=np.float64).reshape(self.shape(level + 1))
+        out = np.array(fine, dtype=np.float64).reshape(self.shape(level)).copy()
+        self.lib.or_prolong_add(self.h, level, int(comp), _dp(c), _dp(out))
+        return out
 
     def visc_diag(self, level, d, i, j, k=0):
         return self.lib.or_visc_diag(self.h, level, d, i, j, k)
