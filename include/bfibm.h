@@ -47,7 +47,8 @@ typedef enum {
   BFIBM_EINVAL = 1,   /* bad argument; nothing changed */
   BFIBM_ENOMEM = 2,   /* device or host allocation failed; nothing changed */
   BFIBM_ECUDA = 3,    /* a CUDA call failed; the context is poisoned */
-  BFIBM_ENOCONV = 4,  /* relative-residual mode hit max_cycles; state is valid */
+  BFIBM_ENOCONV = 4,  /* a solve stopped above its tolerance or a projection above
+                         div_tol; state is valid */
   BFIBM_ETIMEOUT = 5, /* a bounded device wait gave up; the context is poisoned */
   BFIBM_ESTATE = 6    /* the context is poisoned or not ready for the call */
 } bfibm_status;
@@ -84,6 +85,9 @@ typedef struct {
   double gamma_levels[8]; /* ... unless gamma_levels[l] > 0: gamma_lh of coarse level l
                              (l = 1 is the grid 2h); entries 0 and past the last level
                              are ignored */
+  double div_tol;         /* > 0: every projection (Eq. NSdis2) checks max |D.u| in FP64
+                             on the device against it (Eq. NSdis4 makes D.u vanish) and
+                             counts a violation; 0: the maximum is still recorded */
 } bfibm_params;
 
 typedef struct {
@@ -99,8 +103,17 @@ typedef struct {
                                         stability limit of Sec. 4.3.4); each is reset
                                         to 0 so that every kernel stays in bounds */
   int32_t wait_timeouts;             /* bounded device waits that ran out (0 unless
-                                        the device misbehaves); the affected sweep
-                                        stops early and its result is not valid */
+                                        the device misbehaves or BFIBM_OPT_WAIT_NS is
+                                        set very short); the affected sweep stops early
+                                        and its result is not valid */
+  int32_t nonconv_total;             /* relative-residual solves that stopped above
+                                        their tolerance (at max_cycles, or a flexible-CG
+                                        solve whose true FP64 residual exceeds twice
+                                        rtol), counted on the device */
+  int32_t div_violations;            /* projections whose max |D.u| exceeded div_tol */
+  double div_max_step;               /* max |D.u| of the last step's projection,
+                                        computed inside the step (FP64) */
+  double div_max_steps;              /* the largest such value over all steps */
 } bfibm_stats;
 
 /* Field selectors for bfibm_get_field / bfibm_set_field (see layout above). */
@@ -157,9 +170,12 @@ bfibm_status bfibm_set_velocity(bfibm_ctx* c, int comp, const double* u);
 /* Advance nsteps time steps in the order of Sec. 3.4: u~ (Eq. NSdis1-1), p
    (Eq. NSdis4), u (Eq. NSdis2), U (Eq. discrVelCouple), X, then springs,
    f, rho, mu (Eq. discrForceCouple, discrDensCouple, ViscExp) at the new
-   positions. Returns once the work is queued (fixed V-cycle mode) or done
-   (rtol mode, which reads residual norms back). BFIBM_ENOCONV if a solve
-   stopped at max_cycles. */
+   positions. Every projection also records max |D.u| in FP64 on the device
+   (bfibm_stats.div_max_step). Returns once the steps are done: it waits for
+   the context's stream and reads the device status words. BFIBM_ENOCONV
+   (the state is valid) if, since the last report, a relative-residual solve
+   stopped above its tolerance or a projection exceeded div_tol;
+   BFIBM_ETIMEOUT (the context is poisoned) if a bounded device wait ran out. */
 bfibm_status bfibm_step(bfibm_ctx* c, int nsteps);
 
 /* Read results into host buffers (field layout; X as eta x dim). */
@@ -245,14 +261,20 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
    flexible conjugate-gradient iteration in FP64 with the FP32 V-cycles as
    preconditioner, which needs fewer V-cycles where the viscosity contrast
    slows the V-cycle down; the same discrete system and stopping test, so
-   tolerance solves agree within the tolerance). */
+   tolerance solves agree within the tolerance), BFIBM_OPT_WAIT_NS (the
+   limit in nanoseconds of each wait of the TMA sweep for its staged copies,
+   default 2e9; 0 tests the barrier once without waiting. A sweep whose wait
+   runs out drains its copies in flight, stops and raises
+   bfibm_stats.wait_timeouts; the step then reports BFIBM_ETIMEOUT. Short
+   limits exist to exercise that path). */
 enum {
   BFIBM_OPT_STATS = 0,
   BFIBM_OPT_GRAPH = 1,
   BFIBM_OPT_FUSED = 2,
   BFIBM_OPT_TMA = 3,
   BFIBM_OPT_INNER = 4,
-  BFIBM_OPT_KRYLOV = 5
+  BFIBM_OPT_KRYLOV = 5,
+  BFIBM_OPT_WAIT_NS = 6
 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Checkpoint and resume. The state a time step starts from (Sec. 3.4): the
@@ -346,7 +368,10 @@ bfibm_status bfibm_batch_remove(bfibm_batch* b, int32_t slot);
 /* Queue nsteps[slot] time steps for every member (NULL: one each; 0 skips a
    member) without waiting, bracketing each member's steps with events. */
 bfibm_status bfibm_batch_step(bfibm_batch* b, const int32_t* nsteps);
-/* Wait until every member's queued work is done. */
+/* Wait until every member's queued work is done and read each member's
+   device status words as bfibm_step does: BFIBM_ENOCONV if any member
+   reports it (bfibm_get_stats tells which), BFIBM_ETIMEOUT for the first
+   member whose bounded wait ran out. */
 bfibm_status bfibm_batch_wait(bfibm_batch* b);
 /* Device time of a member's steps in the last bfibm_batch_step (waits for
    them); BFIBM_ESTATE if the member was not stepped. */

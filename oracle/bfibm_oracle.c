@@ -82,6 +82,8 @@ typedef struct {
   double rtol;            /* relative residual target, 1e-9 in Sec. 4.1 */
   double gamma_coarse;    /* gamma of Eq. (ViscCoarseGrid) on every coarse level ... */
   double gamma_levels[8]; /* ... unless gamma_levels[l] > 0: gamma_lh of coarse level l */
+  double div_tol;         /* > 0: relative-residual pressure solves also run until the
+                             divergence the projection will leave is at most div_tol */
 } or_params;
 
 typedef struct {
@@ -756,21 +758,38 @@ static double norm2_faces(const or_sim* S, const or_level* L, double* const a[3]
   return s;
 }
 
-/* Pressure solve on level 0: ncycles > 0 fixed, else until ||r||/||f|| <= rtol.
-   The mean of p is re-zeroed after every cycle. Returns cycles used. */
+static double maxabs_cells(const or_sim* S, const or_level* L, const double* a) {
+  int nz = S->D == 3 ? L->n[2] : 1;
+  double m = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < L->n[1]; ++j)
+      for (int i = 0; i < L->n[0]; ++i) {
+        double v = fabs(a[LI(L, i, j, k)]);
+        if (!(v <= m)) m = v;   /* a NaN propagates */
+      }
+  return m;
+}
+
+/* Pressure solve on level 0: ncycles > 0 fixed, else until ||r||/||f|| <= rtol
+   and, when div_tol > 0, (euler dt / sigma) max |r| <= div_tol: after the
+   projection, Eq. (NSdis2), D.u equals (euler dt / sigma) times the residual of
+   Eq. (NSdis4), so this bounds max |D.u| by div_tol. The mean of p is
+   re-zeroed after every cycle. Returns cycles used. */
 static int solve_p(or_sim* S, int ncycles) {
   or_level* L = &S->lev[0];
   double fn = sqrt(norm2_cells(S, L, L->pf));
   int cyc = 0;
   double rel = 0.0;
   int maxc = ncycles > 0 ? ncycles : S->P.max_cycles;
+  double dscale = S->P.euler * S->P.dt / S->P.sigma;
   for (cyc = 1; cyc <= maxc; ++cyc) {
     vcycle_p(S, 0);
     cell_sub(S, L, L->p, cell_mean(S, L, L->p));
     if (ncycles <= 0) {
       p_residual(S, 0);
       rel = fn > 0.0 ? sqrt(norm2_cells(S, L, L->pr)) / fn : 0.0;
-      if (rel <= S->P.rtol) break;
+      int div_ok = S->P.div_tol <= 0.0 || dscale * maxabs_cells(S, L, L->pr) <= S->P.div_tol;
+      if (rel <= S->P.rtol && div_ok) break;
     }
   }
   if (cyc > maxc) cyc = maxc;

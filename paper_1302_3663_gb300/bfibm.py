@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTAT
 FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
          "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12, "idg": 13}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
-OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER, OPT_KRYLOV = 0, 1, 2, 3, 4, 5
+OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER, OPT_KRYLOV, OPT_WAIT_NS = range(7)
 
 
 class BfibmError(RuntimeError):
@@ -42,7 +42,7 @@ class bfibm_params(C.Structure):
                 ("sigma", C.c_double), ("euler", C.c_double), ("inv_re", C.c_double),
                 ("c_force", C.c_double), ("body_force", C.c_double), ("u_center", C.c_double),
                 ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double),
-                ("gamma_levels", C.c_double * 8)]
+                ("gamma_levels", C.c_double * 8), ("div_tol", C.c_double)]
 
 
 class bfibm_stats(C.Structure):
@@ -50,7 +50,9 @@ class bfibm_stats(C.Structure):
                 ("broken_total", C.c_int32), ("clamped_total", C.c_int32),
                 ("res_visc", C.c_double), ("res_p", C.c_double), ("div_max", C.c_double),
                 ("kinetic", C.c_double), ("step", C.c_int64),
-                ("nonfinite_total", C.c_int32), ("wait_timeouts", C.c_int32)]
+                ("nonfinite_total", C.c_int32), ("wait_timeouts", C.c_int32),
+                ("nonconv_total", C.c_int32), ("div_violations", C.c_int32),
+                ("div_max_step", C.c_double), ("div_max_steps", C.c_double)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -155,6 +157,7 @@ def make_params(prm):
         setattr(P, k, float(prm[k]))
     for l, v in enumerate(prm.get("gamma_levels", [])[:8]):
         P.gamma_levels[l] = float(v)
+    P.div_tol = float(prm.get("div_tol", 0.0))
     return P
 
 
@@ -529,9 +532,12 @@ class Batch:
         return "; ".join(msgs)
 
     def wait(self):
+        """Wait for every member; returns ENOCONV when a member reports it
+        (its statistics say which) and raises on any other failure."""
         st = self.lib.bfibm_batch_wait(self.h)
-        if st != OK:
+        if st not in (OK, ENOCONV):
             raise BfibmError(st, "bfibm_batch_wait: " + self._member_errors())
+        return st
 
     def slot_ms(self, slot):
         ms = C.c_float(0)

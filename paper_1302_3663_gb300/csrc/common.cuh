@@ -98,6 +98,8 @@ int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int BX, int waves);
 
 // Mixed precision (mixed.cu).
 int red_blocks_3d(int D, const Geo& g);
+// (partial, when not null, receives the blocks' sums of r^2 and then their
+// maxima of |r|: 2 red_blocks_3d entries)
 void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* r32,
                              float* e32, double* partial, cudaStream_t s);
 void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
@@ -147,12 +149,16 @@ cudaError_t fused_set_carveout();
 // 3D FP32 red-black sweeps with TMA-staged inputs. Kind K: 0..2 viscous
 // component, 3 pressure; coef = inv_re / h^2 (viscous) or h^2 (pressure);
 // err counts bounded waits that ran out.
+// default limit of the TMA sweep's bounded waits (a context may set its own;
+// 0 tests each barrier once without waiting)
+constexpr unsigned long long kTmaWaitNs = 2000000000ull;
 bool tma_eligible(int D, const Geo& g);
 cudaError_t tma_set_smem();
 cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, float* out,
                          int* err, double coef, cudaStream_t s);
 cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K, float* out,
-                          int* err, double coef, cudaStream_t s);
+                          int* err, double coef, cudaStream_t s,
+                          unsigned long long wait_ns = kTmaWaitNs);
 // pin a plan {TY, KC, PD, SW, grid (0: resident blocks)} for a level shape
 bool tma_set_plan(int K, const Geo& g, const int in[5]);
 // the one-pass sweep's tuned tile rows and chunk planes for a level shape
@@ -174,8 +180,20 @@ void launch_adv_rhs(int D, const Geo& g, double* const uvel[3], double* const rh
                     int flow_axis, const double* G_dev, cudaStream_t s);
 void launch_divergence(int D, const Geo& g, double* const u[3], double* b, double scale,
                        Scalars sc, cudaStream_t s);
+// The divergence check fused into the projection: out[acc] accumulates the
+// max |D.u| of the projected velocity (bit pattern of a double); a small
+// kernel then copies it to out[step], folds it into out[all] (max over all
+// steps), counts a violation in *viol when it exceeds tol (> 0) and clears
+// out[acc].
+struct DivCheck {
+  double* out;
+  int acc, step, all;
+  double tol;
+  int* viol;
+};
 void launch_project(int D, const Geo& g, double* const ut[3], const double* p,
-                    double* const beta[3], double* uvel[3], double coef, cudaStream_t s);
+                    double* const beta[3], double* uvel[3], double coef, const DivCheck& dc,
+                    cudaStream_t s);
 // mean over cells of a (deterministic two-pass) subtracted from a
 void launch_sub_mean(int D, const Geo& g, double* a, Scalars sc, cudaStream_t s);
 // sum of squares over the unknowns (cells if ncomp == 0, else the faces of
@@ -190,8 +208,19 @@ void launch_laminar(int D, const Geo& g, int flow_axis, double mu_eff, double u_
                     cudaStream_t s);
 void launch_fill(double* a, long long n, double v, cudaStream_t s);
 // device side of a relative-residual while loop in a graph (see solver.cu)
+// (smax >= 0 adds a second test, mscale * out[smax] <= mtol when mtol > 0; a
+// loop that stops at the cap with a test unmet is counted in *nonconv)
 void launch_tol_check(cudaGraphConditionalHandle h, const double* out, int sf, int sr,
-                      double rtol, int maxc, int* counter, long long* total, cudaStream_t s);
+                      double rtol, int maxc, int* counter, long long* total, int* nonconv,
+                      cudaStream_t s, int smax = -1, double mscale = 0.0, double mtol = 0.0);
+// out[slot] = max of partial[0..nb)
+void launch_finalize_max(const double* partial, int nb, double* out, int slot, cudaStream_t s);
+// out[slot] = max over the cells of |a|
+void launch_absmax_cells(int D, const Geo& g, const double* a, Scalars sc, int slot,
+                         cudaStream_t s);
+// counts ||r||/||f|| (from out[sr], out[sf]) above thresh in *nonconv
+void launch_res_check(const double* out, int sf, int sr, double thresh, int* nonconv,
+                      cudaStream_t s);
 
 // ------------------------------------------------------------ lagrangian.cu
 struct NodeSet {

@@ -4,6 +4,7 @@
 // the FP32 correction back into the FP64 iterate. The coarsest grid is solved
 // in FP64 (its right-hand side and solution are converted at the boundary).
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "common.cuh"
 
@@ -40,6 +41,23 @@ __device__ double block_sum(double v, double* sh) {
   __syncthreads();
   return v;
 }
+// maximum over a block whose size is a multiple of 32; valid in thread 0
+__device__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  int nt = blockDim.x * blockDim.y * blockDim.z;
+  int lane = t & 31, w = t >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (t < (nt + 31) / 32) ? sh[t] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  __syncthreads();
+  return v;
+}
 inline dim3 blk3(int D) { return D == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1); }
 inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
   return dim3((unsigned)((nx + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y),
@@ -51,7 +69,10 @@ __device__ __forceinline__ int block_linear() {
 
 // FP64 pressure residual written as the FP32 right-hand side of the
 // correction equation; the FP32 correction is zeroed; per-block partial sums
-// of r^2 (for the relative-residual test).
+// of r^2 (for the relative-residual test) in partial[0 .. nb) and per-block
+// maxima of |r| (for the divergence the projection will leave, Eq. NSdis2 -
+// NSdis4: max |D.u| = (euler dt / sigma) max |r|) in partial[nb .. 2 nb),
+// nb the launch's blocks; a non-finite residual counts as infinity.
 template <int D>
 __global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<double> L, float* r32,
                                                           float* e32, double* partial) {
@@ -59,7 +80,7 @@ __global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<doubl
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z * blockDim.z + threadIdx.z;
-  double r2 = 0.0;
+  double r2 = 0.0, ra = 0.0;
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
     int ci[3] = {i, j, k};
     long long c = gidx(g, i, j, k);
@@ -83,10 +104,17 @@ __global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<doubl
     r32[c] = (float)r;
     e32[c] = 0.0f;
     r2 = r * r;
+    ra = fabs(r);
+    if (!(ra <= CUDART_INF)) ra = CUDART_INF;
   }
   if (partial) {
     r2 = block_sum(r2, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) partial[block_linear()] = r2;
+    ra = block_max(ra, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+      const int nb = gridDim.x * gridDim.y * gridDim.z;
+      partial[block_linear()] = r2;
+      partial[nb + block_linear()] = ra;
+    }
   }
 }
 

@@ -22,9 +22,11 @@
 // plane chunk) b, b + G, b + 2G, ..., so the items in flight at any moment are
 // neighbours and share their halo rows through L2.
 //
-// Every wait on an mbarrier is bounded (2 s of the global timer); a block
-// whose wait runs out raises the error word, drains its own copies in flight
-// (again bounded) and returns.
+// Every wait on an mbarrier is bounded (2 s of the global timer by default;
+// a context may set a shorter limit, 0 testing each barrier once without
+// waiting). A block whose wait runs out raises the error word, drains its own
+// copies in flight from the first one it has not seen complete (bounded by
+// the default limit, whatever the context's) and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -45,7 +47,7 @@ constexpr int kNB = 8;                  // mbarriers (planes in flight <= PD + 1
 constexpr int kMaxPD = 3;               // prefetch distance in planes, at most
 constexpr int kRing = 4;                // ring planes of red values: k-3 .. k
 constexpr int kTmaThreads = 1024;       // threads per block at most
-constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned long long kWaitNs = kTmaWaitNs;   // the drain's limit
 constexpr size_t kSmemMax = 225 * 1024;   // dynamic, leaving room for the static words
 
 // Staged arrays. Viscous component d (kinds 0, 1, 2): old u_d, rhs_d, the
@@ -71,6 +73,7 @@ struct TmaArgs {
   int tile;              // floats between array tiles (multiple of 32)
   unsigned box_bytes;    // bytes of one box: (TY + 4) rows of BW floats
   float c;               // viscous: inv_re / h^2; pressure: h^2
+  unsigned long long wait_ns;   // limit of each main-loop wait (0: test once)
 };
 
 // ------------------------------------------------------------------ PTX
@@ -103,6 +106,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned pa
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map,
                                             unsigned long long* b, int x, int y, int z) {
   asm volatile(
@@ -117,11 +131,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 // bounded wait for the completion of sequence number s (barrier s % kNB,
-// phase parity (s / kNB) & 1)
+// phase parity (s / kNB) & 1); limit 0 tests the barrier once
 __device__ __forceinline__ bool wait_seq(unsigned long long* bar, unsigned s,
                                          unsigned long long limit_ns) {
   unsigned long long* b = &bar[s % kNB];
   unsigned par = (s / kNB) & 1u;
+  if (limit_ns == 0) return mbar_test_wait(b, par);
   if (mbar_try_wait(b, par)) return true;
   unsigned long long t0 = global_ns();
   while (!mbar_try_wait(b, par))
@@ -336,8 +351,11 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
       }
       bool ok = true;
       const unsigned need = sbase + (unsigned)(min(k + 1, k1 + 1) - pbase);
-      while (waited <= need) {
-        ok = ok && wait_seq(bar, waited, kWaitNs);
+      while (waited <= need) {   // `waited` stops at the first copy not seen complete
+        if (!wait_seq(bar, waited, A.wait_ns)) {
+          ok = false;
+          break;
+        }
         ++waited;
       }
       if (!ok) {
@@ -400,7 +418,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
     if (abort_flag) break;
   }
   if (abort_flag && tid == 0) {
-    // drain the copies still in flight into this block's shared memory
+    // drain the copies still in flight into this block's shared memory, from
+    // the first one this thread has not seen complete
     while (waited < seq) {
       wait_seq(bar, waited, kWaitNs / 2);
       ++waited;
@@ -562,6 +581,7 @@ bool fill_args(int K, const Geo& g, const LevelPtrs<float>& L, float* out, int* 
   A.tile = tile_of(TY, SW);
   A.box_bytes = (unsigned)((TY + 4) * A.BW * 4);
   A.c = (float)coef;
+  A.wait_ns = kWaitNs;
   return true;
 }
 
@@ -748,7 +768,7 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
 // pressure, else viscous component K). Uses the tuned plan of the level shape,
 // or a default one before tuning.
 cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K, float* out,
-                          int* err, double coef, cudaStream_t s) {
+                          int* err, double coef, cudaStream_t s, unsigned long long wait_ns) {
   Plan pl;
   {
     std::lock_guard<std::mutex> lock(g_plan_mu);
@@ -761,6 +781,7 @@ cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K,
   TmaArgs A;
   if (!fill_args(K, g, L, out, err, coef, pl.TY, pl.KC, pl.PD, pl.SW, A))
     return cudaErrorInvalidValue;
+  A.wait_ns = wait_ns;
   int grid = pl.grid > 0 ? pl.grid : resident_grid(K, pl.TY, pl.PD, A.SW, A.items);
   return launch_args(K, A, grid, s);
 }

@@ -134,8 +134,11 @@ const char* validate(const bfibm_params* p) {
   for (int l = 0; l < 8; ++l)
     if (!(p->gamma_levels[l] >= 0.0) || !std::isfinite(p->gamma_levels[l]))
       return "gamma_levels entries must be >= 0";
+  if (!(p->div_tol >= 0.0) || !std::isfinite(p->div_tol)) return "div_tol must be >= 0";
   return nullptr;
 }
+
+constexpr int kCounters = 8;
 
 }  // namespace
 
@@ -160,7 +163,10 @@ struct bfibm_ctx {
   SpringSet S{};
   TileGeo tg{};
   long long* step_dev = nullptr;
-  int* counters = nullptr;    // [0] clamped, [1] event count, [2] non-finite, [3] wait timeouts
+  int* counters = nullptr;    // [0] clamped, [1] event count, [2] non-finite, [3] wait timeouts,
+                              // [4] solves stopped above their tolerance, [5] projections
+                              // above div_tol
+  int seen[kCounters] = {0};  // counters as last reported by a step or a batch wait
   double* spread_scale = nullptr;   // fixed-point scales of the force and density sums
   std::vector<void*> lag_allocs;
   cudaStream_t stream = nullptr;
@@ -173,6 +179,7 @@ struct bfibm_ctx {
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
   bool fused = false;            // one-pass FP64 red-black sweeps (FP32 sweeps always are)
+  unsigned long long tma_wait_ns = kTmaWaitNs;   // limit of the TMA sweep's waits
   int tma = 1;                   // 3D FP32 sweeps with TMA-staged inputs: 0 never, 1 where
                                  // the tuner timed them faster, 2 wherever a level allows
   bool collect_stats = true;
@@ -303,8 +310,30 @@ void vcycle_v(bfibm_ctx* c, int l) {
   smooth_v(c, l, c->P.nu2);
 }
 
-// scalar slots: 0 scratch (means), 2/3 viscous |f|^2,|r|^2, 4/5 pressure, 6/7 div/KE
-enum { SL_VF = 2, SL_VR = 3, SL_PF = 4, SL_PR = 5, SL_DIV = 6, SL_ZQ = 8, SL_PQ = 9, SL_PRR = 10 };
+// scalar slots: 0 scratch (means), 2/3 viscous |f|^2,|r|^2, 4/5 pressure, 6/7 div/KE,
+// 8-10 flexible CG, 11-13 the divergence check of every projection (accumulator,
+// this step's max |D.u|, the max over all steps)
+// 14 the max |r| of the pressure residual
+enum { SL_VF = 2, SL_VR = 3, SL_PF = 4, SL_PR = 5, SL_DIV = 6, SL_ZQ = 8, SL_PQ = 9, SL_PRR = 10,
+       SL_DIVACC = 11, SL_DIVSTEP = 12, SL_DIVALL = 13, SL_PRMAX = 14 };
+
+// The projection leaves D.u = (euler dt / sigma) r_p (Eq. NSdis2 - NSdis4, the
+// pressure right-hand side having zero mean), so a pressure solve in
+// relative-residual mode with div_tol > 0 also runs until
+// (euler dt / sigma) max |r_p| <= div_tol: the divergence target then holds
+// after every projection, not only on average.
+double div_scale(const bfibm_ctx* c) { return c->P.euler * c->P.dt / c->P.sigma; }
+
+bool p_converged(const bfibm_ctx* c, const double* hs) {
+  double fn = std::sqrt(hs[SL_PF]), rn = std::sqrt(hs[SL_PR]);
+  double rel = fn > 0.0 ? rn / fn : 0.0;
+  return rel <= c->P.rtol && (c->P.div_tol <= 0.0 || div_scale(c) * hs[SL_PRMAX] <= c->P.div_tol);
+}
+
+// The true FP64 residual of a flexible-CG solve may drift from the recurrence
+// that stops the loop; a solve whose true relative residual exceeds this many
+// times rtol is reported as not converged.
+constexpr double kTrueResidualSlack = 2.0;
 
 bfibm_status read_scalars(bfibm_ctx* c) {
   CK(cudaMemcpyAsync(c->host_sc, c->sc.out, 16 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -394,8 +423,10 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
       launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, c->stream);
       launch_p_residual<double>(c->D, L0.g, L0.d, c->stream);
       launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, c->stream);
+      if (c->P.div_tol > 0.0) launch_absmax_cells(c->D, L0.g, L0.d.pr, c->sc, SL_PRMAX, c->stream);
       launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, c->P.max_cycles, c->dev_cycles + 1,
-                       c->loop_total + 1, c->stream);
+                       c->loop_total + 1, c->counters + 4, c->stream, SL_PRMAX, div_scale(c),
+                       c->P.div_tol);
     });
     *used = -1;
     return cs;
@@ -407,11 +438,10 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
     launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
     launch_p_residual<double>(c->D, L0.g, L0.d, s);
     launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, s);
+    if (c->P.div_tol > 0.0) launch_absmax_cells(c->D, L0.g, L0.d.pr, c->sc, SL_PRMAX, s);
     bfibm_status rs = read_scalars(c);
     if (rs != BFIBM_OK) return rs;
-    double fn = std::sqrt(c->host_sc[SL_PF]), rn = std::sqrt(c->host_sc[SL_PR]);
-    double rel = fn > 0.0 ? rn / fn : 0.0;
-    if (rel <= c->P.rtol) {
+    if (p_converged(c, c->host_sc)) {
       st = BFIBM_OK;
       break;
     }
@@ -442,7 +472,7 @@ bfibm_status solve_v(bfibm_ctx* c, int ncycles, int* used) {
       launch_v_residual<double>(c->D, L0.g, L0.d, c->P.inv_re, c->stream);
       launch_norm2(c->D, L0.g, L0.d.ur, c->D, c->sc, SL_VR, c->stream);
       launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, c->P.max_cycles, c->dev_cycles,
-                       c->loop_total, c->stream);
+                       c->loop_total, c->counters + 4, c->stream);
     });
     *used = -1;
     return cs;
@@ -478,7 +508,8 @@ void smooth_p32(bfibm_ctx* c, int l, int n) {
   const bool tma = tma_for(c, l, 3);
   for (int it = 0; it < n; ++it) {
     if (tma)
-      launch_rb_tma(c->D, Lv.g, Lv.f, 3, Lv.f.p2, c->counters + 3, Lv.g.h * Lv.g.h, c->stream);
+      launch_rb_tma(c->D, Lv.g, Lv.f, 3, Lv.f.p2, c->counters + 3, Lv.g.h * Lv.g.h, c->stream,
+                    c->tma_wait_ns);
     else {
       int ty = 0, kc = 0, np = 1, bx = 0;
       ring_shape_of(3, Lv.g, &ty, &kc, &np, &bx);
@@ -499,7 +530,7 @@ void smooth_v32(bfibm_ctx* c, int l, int n) {
     for (int d = 0; d < c->D; ++d) {
       if (tma_for(c, l, d))
         launch_rb_tma(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->counters + 3,
-                      c->P.inv_re / (Lv.g.h * Lv.g.h), c->stream);
+                      c->P.inv_re / (Lv.g.h * Lv.g.h), c->stream, c->tma_wait_ns);
       else {
         int ty = 0, kc = 0, np = 1, bx = 0;
         ring_shape_of(d, Lv.g, &ty, &kc, &np, &bx);
@@ -596,8 +627,10 @@ bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
       launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, b);
       launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, b);
+      if (c->P.div_tol > 0.0) launch_finalize_max(c->sc.partial + nb, nb, c->sc.out, SL_PRMAX, b);
       launch_tol_check(h, c->sc.out, SL_PF, SL_PR, c->P.rtol, maxc, c->dev_cycles + 1,
-                       c->loop_total + 1, b);
+                       c->loop_total + 1, c->counters + 4, b, SL_PRMAX, div_scale(c),
+                       c->P.div_tol);
     });
     *used = -1;
     return cs;
@@ -607,10 +640,10 @@ bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
     launch_p_residual_mixed(c->D, L0.g, L0.d, L0.f.pf, L0.f.p, tol ? c->sc.partial : nullptr, s);
     if (tol) {
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_PR, 1.0, s);
+      launch_finalize_max(c->sc.partial + nb, nb, c->sc.out, SL_PRMAX, s);
       bfibm_status rs = read_scalars(c);
       if (rs != BFIBM_OK) return rs;
-      double fn = std::sqrt(c->host_sc[SL_PF]), rn = std::sqrt(c->host_sc[SL_PR]);
-      if ((fn > 0.0 ? rn / fn : 0.0) <= c->P.rtol) {
+      if (p_converged(c, c->host_sc)) {
         st = BFIBM_OK;
         break;
       }
@@ -652,7 +685,7 @@ bfibm_status solve_v_mixed(bfibm_ctx* c, int ncycles, int* used) {
       launch_v_residual_mixed(c->D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re, c->sc.partial, b);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, b);
       launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, maxc, c->dev_cycles,
-                       c->loop_total, b);
+                       c->loop_total, c->counters + 4, b);
     });
     *used = -1;
     return cs;
@@ -726,12 +759,14 @@ bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
     bfibm_status cs = capture_while(c, 0, [&](cudaGraphConditionalHandle h) {
       iteration(c->stream, inner);
       launch_tol_check(h, c->sc.out, SL_VF, SL_VR, c->P.rtol, maxc, c->dev_cycles, c->loop_total,
-                       c->stream);
+                       c->counters + 4, c->stream);
     });
-    if (cs == BFIBM_OK && c->collect_stats) {   // the true FP64 residual of the final iterate
+    if (cs == BFIBM_OK) {   // the true FP64 residual of the final iterate, checked
       launch_v_residual_mixed(D, L0.g, L0.d, L0.f.uf, L0.f.u, c->vdiag, c->P.inv_re,
                               c->sc.partial, s);
       launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
+      launch_res_check(c->sc.out, SL_VF, SL_VR, kTrueResidualSlack * c->P.rtol, c->counters + 4,
+                       s);
     }
     *used = -1;
     return cs;
@@ -763,6 +798,12 @@ bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
                             c->sc.partial, s);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_VR, 1.0, s);
   }
+  if (tol && st == BFIBM_OK) {
+    bfibm_status rs = read_scalars(c);
+    if (rs != BFIBM_OK) return rs;
+    double fn = std::sqrt(c->host_sc[SL_VF]), rn = std::sqrt(c->host_sc[SL_VR]);
+    if (!((fn > 0.0 ? rn / fn : 0.0) <= kTrueResidualSlack * c->P.rtol)) st = BFIBM_ENOCONV;
+  }
   *used = vdone;
   return st;
 }
@@ -778,8 +819,9 @@ void stage_divergence(bfibm_ctx* c) {
 }
 void stage_project(bfibm_ctx* c) {
   double coef = c->P.euler * c->P.dt / c->P.sigma;
+  DivCheck dc{c->sc.out, SL_DIVACC, SL_DIVSTEP, SL_DIVALL, c->P.div_tol, c->counters + 5};
   launch_project(c->D, c->lev[0].g, c->lev[0].d.u, c->lev[0].d.p, c->lev[0].d.beta, c->uvel,
-                 coef, c->stream);
+                 coef, dc, c->stream);
 }
 void stage_interp_advance(bfibm_ctx* c) {
   launch_interp_advance(c->D, c->lev[0].g, c->N, c->uvel, c->P.phi_kind, c->P.dt / c->P.sigma,
@@ -868,7 +910,33 @@ bfibm_status ensure_ready(bfibm_ctx* c) {
   return BFIBM_OK;
 }
 
-bfibm_status do_steps(bfibm_ctx* c, int nsteps) {
+// Reads the device status words (waits for the context's stream) and reports
+// what happened since the last report: BFIBM_ETIMEOUT (the context is
+// poisoned) when a bounded device wait ran out, BFIBM_ENOCONV when a solve
+// stopped above its tolerance or a projection left max |D.u| above div_tol.
+bfibm_status check_status(bfibm_ctx* c) {
+  int cnt[kCounters];
+  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const bool timeout = cnt[3] != c->seen[3];
+  const bool nonconv = cnt[4] != c->seen[4];
+  const bool div = cnt[5] != c->seen[5];
+  for (int q = 0; q < kCounters; ++q) c->seen[q] = cnt[q];
+  if (timeout) {
+    c->poisoned = 1;
+    return set_err(c, BFIBM_ETIMEOUT, "a bounded device wait of the TMA sweep ran out");
+  }
+  if (nonconv || div)
+    return set_err(c, BFIBM_ENOCONV,
+                   nonconv ? "a solve stopped above its relative-residual tolerance"
+                           : "max |D.u| after a projection exceeded div_tol");
+  return BFIBM_OK;
+}
+
+// Queues nsteps time steps; with `report` it then waits for them and returns
+// what check_status reports (a batch step queues only and reports in
+// bfibm_batch_wait).
+bfibm_status do_steps(bfibm_ctx* c, int nsteps, bool report) {
   bfibm_status st = ensure_ready(c);
   if (st != BFIBM_OK) return st;
   bfibm_status agg = BFIBM_OK;
@@ -900,6 +968,10 @@ bfibm_status do_steps(bfibm_ctx* c, int nsteps) {
   }
   CK(cudaGetLastError());
   c->step_host += nsteps;
+  if (report) {
+    bfibm_status cs = check_status(c);
+    if (cs != BFIBM_OK) return cs;
+  }
   return agg;
 }
 
@@ -1138,7 +1210,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   c->partial_cap = std::max<long long>(4 * kRedBlocks, 2LL * red_blocks_3d(D, c->lev[0].g) + 64);
   if (cudaMalloc((void**)&c->sc.partial, sizeof(double) * c->partial_cap) != cudaSuccess ||
       cudaMalloc((void**)&c->step_dev, sizeof(long long)) != cudaSuccess ||
-      cudaMalloc((void**)&c->counters, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc((void**)&c->counters, sizeof(int) * kCounters) != cudaSuccess ||
       cudaMalloc((void**)&c->dev_cycles, sizeof(int) * 2) != cudaSuccess ||
       cudaMalloc((void**)&c->loop_total, sizeof(long long) * 2) != cudaSuccess ||
       cudaMalloc((void**)&c->spread_scale, sizeof(double) * 2) != cudaSuccess ||
@@ -1155,7 +1227,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   cudaStream_t s = c->stream;
   bool ok = cudaMemsetAsync(c->pool, 0, c->pool_bytes, s) == cudaSuccess &&
             cudaMemsetAsync(c->step_dev, 0, sizeof(long long), s) == cudaSuccess &&
-            cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, s) == cudaSuccess &&
+            cudaMemsetAsync(c->counters, 0, sizeof(int) * kCounters, s) == cudaSuccess &&
             cudaMemsetAsync(c->dev_cycles, 0, sizeof(int) * 2, s) == cudaSuccess &&
             cudaMemsetAsync(c->loop_total, 0, sizeof(long long) * 2, s) == cudaSuccess;
   {
@@ -1354,7 +1426,7 @@ bfibm_status bfibm_set_velocity(bfibm_ctx* c, int comp, const double* u) {
 bfibm_status bfibm_step(bfibm_ctx* c, int nsteps) {
   READY(c);
   if (nsteps < 0) return set_err(c, BFIBM_EINVAL, "nsteps < 0");
-  return do_steps(c, nsteps);
+  return do_steps(c, nsteps, true);
 }
 
 bfibm_status bfibm_get_velocity(bfibm_ctx* c, int comp, double* out) {
@@ -1424,8 +1496,8 @@ bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
   CK(cudaGetLastError());
   bfibm_status rs = read_scalars(c);
   if (rs != BFIBM_OK) return rs;
-  int cnt[4];
-  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+  int cnt[kCounters];
+  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   std::memset(out, 0, sizeof(*out));
   out->cycles_visc = c->cycles_visc;
@@ -1446,6 +1518,10 @@ bfibm_status bfibm_get_stats(bfibm_ctx* c, bfibm_stats* out) {
   out->res_p = rel(c->host_sc[SL_PF], c->host_sc[SL_PR]);
   out->div_max = c->host_sc[SL_DIV];
   out->kinetic = c->host_sc[SL_DIV + 1];
+  out->nonconv_total = cnt[4];
+  out->div_violations = cnt[5];
+  out->div_max_step = c->host_sc[SL_DIVSTEP];
+  out->div_max_steps = c->host_sc[SL_DIVALL];
   out->step = c->step_host;
   return BFIBM_OK;
 }
@@ -1681,7 +1757,7 @@ bfibm_status bfibm_save_state(bfibm_ctx* c, void* buf, int64_t bytes) {
   h.m = c->S.m;
   h.step = c->step_host;
   h.elems = level_elems(c->lev[0].g);
-  int cnt[4];
+  int cnt[kCounters];
   CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   h.events = std::min<int64_t>(cnt[1], c->S.m);
@@ -1802,6 +1878,9 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
   } else if (option == BFIBM_OPT_KRYLOV) {
     if (value < 0 || value > 1) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_KRYLOV takes 0 or 1");
     c->krylov = (int)value;
+  } else if (option == BFIBM_OPT_WAIT_NS) {
+    if (value < 0) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_WAIT_NS takes a value >= 0");
+    c->tma_wait_ns = (unsigned long long)value;
   } else if (option == BFIBM_OPT_INNER) {
     if (value < 1 || value > 16)
       return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_INNER takes 1 to 16");
@@ -1875,7 +1954,7 @@ bfibm_status bfibm_batch_step(bfibm_batch* b, const int32_t* nsteps) {
     bfibm_ctx* c = s.c;
     READY(c);
     CK(cudaEventRecord(s.e0, c->stream));
-    bfibm_status st = do_steps(c, n);
+    bfibm_status st = do_steps(c, n, false);
     if (st != BFIBM_OK && st != BFIBM_ENOCONV) return st;
     if (st == BFIBM_ENOCONV) agg = st;
     CK(cudaEventRecord(s.e1, c->stream));
@@ -1886,13 +1965,16 @@ bfibm_status bfibm_batch_step(bfibm_batch* b, const int32_t* nsteps) {
 
 bfibm_status bfibm_batch_wait(bfibm_batch* b) {
   if (!b) return BFIBM_EINVAL;
+  bfibm_status agg = BFIBM_OK;
   for (auto& s : b->slots) {
     if (!s.c) continue;
     bfibm_ctx* c = s.c;
     READY(c);
-    CK(cudaStreamSynchronize(c->stream));
+    bfibm_status st = check_status(c);
+    if (st == BFIBM_ENOCONV) agg = BFIBM_ENOCONV;
+    else if (st != BFIBM_OK) return st;
   }
-  return BFIBM_OK;
+  return agg;
 }
 
 bfibm_status bfibm_batch_slot_ms(bfibm_batch* b, int32_t slot, float* ms) {

@@ -689,18 +689,22 @@ __global__ void __launch_bounds__(256) k_coef_restrict(Geo gf, Geo gc, LevelPtrs
 // ---------------------------------------------------------------------------
 // Momentum right-hand side, Eq. (NSdis1-1):
 //   rhs_d = m_d u_d - rho_d Adv_d(u) + c_f f_d + G [d = flow axis]
-// Adv_d = 1/2 (u.D u_d + D.(u u_d)): the advective half takes centred wide
-// differences with the velocity averaged to the d-face; the conservative half
-// differences fluxes at the cells (along d) and edges (other axes), each
-// factor a 2-point mean. The iterate u~ starts from u^n.
+// Adv_d = 1/2 (u.D u_d + D.(u u_d)) in the staggered skew form that keeps the
+// property of the paper's D0 form, sum over faces of u_d Adv_d = 0: along each
+// axis e the advecting velocity U_e is a 2-point mean at the two flux points
+// of the face (cell centres for e = d, edges otherwise), and the mean of the
+// conservative half (fluxes U_e x 2-point mean of u_d) and the advective half
+// (mean of U_e x one-sided differences) collapses to
+//   Adv_d = sum_e (U_e+ u_d(F + e) - U_e- u_d(F - e)) / (2h).
+// The iterate u~ starts from u^n.
 // ---------------------------------------------------------------------------
-// The constant factors (1/2 of each mean, 1/(2h), 1/h) are folded into two
-// products so that a point costs no division: FP64 throughput is scarce.
+// U_e = s / 2 with s a sum of two values, so each term is s u / (4h): one
+// product per point (FP64 throughput is scarce).
 template <int D, int d>
 __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, const Ptr3& rho,
                                               const Ptr3& frc, const LevelPtrs<double>& L0,
                                               const int ci[3], long long F, double c_force,
-                                              double gflow, double c_adv, double c_cons) {
+                                              double gflow, double c4) {
   if (!g.per[d] && ci[d] == 0) {
     L0.uf[d][F] = 0.0;
     L0.u[d][F] = 0.0;
@@ -709,25 +713,22 @@ __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, cons
   const double* __restrict__ ud = uv.a[d];
   long long od_p = offp(g, d, ci[d]), od_m = offm(g, d, ci[d]);
   double udF = ud[F], udp = ud[F + od_p], udm = ud[F + od_m];
-  // 4 x (advective half) and 4 x (conservative half), scaled at the end
-  double adv4 = 4.0 * udF * (udp - udm);
-  double sp = udF + udp, sm = udm + udF;
-  double cons4 = sp * sp - sm * sm;
+  // 4 h Adv_d, one axis at a time
+  double a4 = (udF + udp) * udp - (udm + udF) * udm;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     if (e == d) continue;
     const double* __restrict__ ue = uv.a[e];
     bool pe = g.per[e] != 0;
     long long oe_p = offp(g, e, ci[e]);
-    double up = -udF, um = -udF;   // mirror ghosts beyond a wall
+    double up = -udF, um = -udF;   // mirror ghosts beyond a wall (U_e = 0 there)
     if (pe || ci[e] != g.n[e] - 1) up = ud[F + oe_p];
     if (pe || ci[e] != 0) um = ud[F + offm(g, e, ci[e])];
     double s_lo = ue[F + od_m] + ue[F];                 // 2 x u_e on the lower edge
     double s_hi = ue[F + oe_p + od_m] + ue[F + oe_p];   // 2 x u_e on the upper edge
-    adv4 += (s_lo + s_hi) * (up - um);
-    cons4 += s_hi * (udF + up) - s_lo * (um + udF);
+    a4 += s_hi * up - s_lo * um;
   }
-  double A = c_adv * adv4 + c_cons * cons4;
+  double A = c4 * a4;
   L0.uf[d][F] = L0.m[d][F] * udF - rho.a[d][F] * A + c_force * frc.a[d][F] + gflow;
   L0.u[d][F] = udF;
 }
@@ -743,13 +744,11 @@ __global__ void __launch_bounds__(256) k_adv_rhs(Geo g, Ptr3 uv, Ptr3 rho, Ptr3 
   int ci[3] = {i, j, k};
   long long F = gidx(g, i, j, k);
   double G = *G_dev;
-  // Adv = 1/2 (adv4 / (8 h) + cons4 / (4 h)): the 4-point mean is 1/4 of a
-  // sum, the wide difference 1/(2h), the flux means 1/4 of sums over 1/h
-  const double c_adv = 0.0625 / g.h, c_cons = 0.125 / g.h;
-  adv_rhs_point<D, 0>(g, uv, rho, frc, L0, ci, F, c_force, flow == 0 ? G : 0.0, c_adv, c_cons);
-  adv_rhs_point<D, 1>(g, uv, rho, frc, L0, ci, F, c_force, flow == 1 ? G : 0.0, c_adv, c_cons);
+  const double c4 = 0.25 / g.h;
+  adv_rhs_point<D, 0>(g, uv, rho, frc, L0, ci, F, c_force, flow == 0 ? G : 0.0, c4);
+  adv_rhs_point<D, 1>(g, uv, rho, frc, L0, ci, F, c_force, flow == 1 ? G : 0.0, c4);
   if constexpr (D == 3)
-    adv_rhs_point<D, 2>(g, uv, rho, frc, L0, ci, F, c_force, flow == 2 ? G : 0.0, c_adv, c_cons);
+    adv_rhs_point<D, 2>(g, uv, rho, frc, L0, ci, F, c_force, flow == 2 ? G : 0.0, c4);
 }
 
 // ---------------------------------------------------------------------------
@@ -818,24 +817,78 @@ __global__ void __launch_bounds__(256) k_sub_scalar(Geo g, double* __restrict__ 
   a[gidx(g, i, j, k)] -= *s;
 }
 
+// u_d on one face after the projection, Eq. (NSdis2); pM is p of the cell
+// below the face along d. One function for the face a thread owns and for
+// the upper faces it recomputes, so both round alike.
+__device__ __forceinline__ double proj_face(double ut, double beta, double pF, double pM,
+                                            double coef, double h) {
+  return ut - coef * beta * ((pF - pM) / h);
+}
+
+// Projection, Eq. (NSdis2), with the check of Eq. (NSdis4) fused in: each
+// thread owns the lower faces of its cell, writes them, recomputes the upper
+// ones (owned by the neighbours) and takes |D.u| of its cell in FP64. The
+// block maximum goes to *divacc as the bit pattern of a non-negative double
+// (unsigned max: order-independent, hence deterministic); a non-finite
+// divergence counts as infinity.
 template <int D>
 __global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* __restrict__ p,
-                                                 Ptr3 beta, Ptr3 uv, double coef) {
+                                                 Ptr3 beta, Ptr3 uv, double coef,
+                                                 unsigned long long* __restrict__ divacc) {
+  __shared__ double sh[32];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
-  int ci[3] = {i, j, k};
-  long long F = gidx(g, i, j, k);
+  double mx = 0.0;
+  if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+    int ci[3] = {i, j, k};
+    long long F = gidx(g, i, j, k);
+    const double pF = p[F];
+    double s = 0.0;
 #pragma unroll
-  for (int d = 0; d < D; ++d) {
-    if (!g.per[d] && ci[d] == 0) {
-      uv.a[d][F] = 0.0;
-      continue;
+    for (int d = 0; d < D; ++d) {
+      double lo = 0.0;
+      if (!g.per[d] && ci[d] == 0) {
+        uv.a[d][F] = 0.0;
+      } else {
+        lo = proj_face(ut.a[d][F], beta.a[d][F], pF, p[F + offm(g, d, ci[d])], coef, g.h);
+        uv.a[d][F] = lo;
+      }
+      double hi = 0.0;   // the upper wall face holds 0
+      if (g.per[d] || ci[d] != g.n[d] - 1) {
+        long long Fu = F + offp(g, d, ci[d]);
+        hi = proj_face(ut.a[d][Fu], beta.a[d][Fu], p[Fu], pF, coef, g.h);
+      }
+      s += (hi - lo) / g.h;
     }
-    double gp = (p[F] - p[F + offm(g, d, ci[d])]) / g.h;
-    uv.a[d][F] = ut.a[d][F] - coef * beta.a[d][F] * gp;
+    mx = fabs(s);
+    if (!(mx <= CUDART_INF)) mx = CUDART_INF;
   }
+  // block maximum over the linear thread index (a 3D block)
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  mx = warp_max(mx);
+  if ((t & 31) == 0) sh[t >> 5] = mx;
+  __syncthreads();
+  if (t < 32) {
+    mx = t < ((nt + 31) >> 5) ? sh[t] : 0.0;
+    mx = warp_max(mx);
+    if (t == 0 && mx > 0.0) atomicMax(divacc, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// After a projection: this step's max |D.u| to out[step], the maximum over
+// all steps to out[all], a violation counted when it exceeds tol (> 0), and
+// the accumulator cleared for the next projection.
+__global__ void k_div_check(double* __restrict__ out, int acc, int step, int all, double tol,
+                            int* __restrict__ viol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(out + acc);
+  const double v = __longlong_as_double((long long)*a);
+  out[step] = v;
+  out[all] = fmax(out[all], v);
+  if (tol > 0.0 && !(v <= tol)) ++(*viol);
+  *a = 0ull;
 }
 
 template <int D>
@@ -938,16 +991,48 @@ __global__ void k_laminar(Geo g, int D, int fa, int ta0, int ta1, double mu_eff,
 }
 
 // One iteration of a device-side relative-residual loop has finished:
-// count it and keep looping while ||r||/||f|| > rtol and the cap is not hit.
+// count it and keep looping while ||r||/||f|| > rtol (or, with mtol > 0,
+// mscale * out[smax] > mtol) and the cap is not hit. A loop that stops at
+// the cap with either test unmet is counted in *nonconv.
 __global__ void k_tol_check(cudaGraphConditionalHandle h, const double* __restrict__ out, int sf,
                             int sr, double rtol, int maxc, int* __restrict__ counter,
-                            long long* __restrict__ total) {
+                            long long* __restrict__ total, int* __restrict__ nonconv, int smax,
+                            double mscale, double mtol) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int n = ++(*counter);
   ++(*total);
   double f2 = out[sf], r2 = out[sr];
   double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
-  cudaGraphSetConditional(h, (rel > rtol && n < maxc) ? 1u : 0u);
+  const bool met = rel <= rtol && (mtol <= 0.0 || mscale * out[smax] <= mtol);
+  const bool again = !met && n < maxc;
+  if (!again && !met) ++(*nonconv);
+  cudaGraphSetConditional(h, again ? 1u : 0u);
+}
+
+// max over cells of |a| (a non-finite value counts as infinity), per block
+__global__ void __launch_bounds__(256) k_absmax_cells(Geo g, const double* __restrict__ a,
+                                                      double* __restrict__ partial) {
+  __shared__ double sh[32];
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  double mx = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, q, i, j, k);
+    double v = fabs(a[gidx(g, i, j, k)]);
+    mx = (v <= CUDART_INF) ? fmax(mx, v) : CUDART_INF;
+  }
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = mx;
+}
+
+// ||r||/||f|| from out[sr], out[sf]: counted in *nonconv when above thresh
+__global__ void k_res_check(const double* __restrict__ out, int sf, int sr, double thresh,
+                            int* __restrict__ nonconv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double f2 = out[sf], r2 = out[sr];
+  double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
+  if (!(rel <= thresh)) ++(*nonconv);
 }
 
 __global__ void k_fill(double* a, long long n, double v) {
@@ -1171,11 +1256,14 @@ void launch_sub_mean(int D, const Geo& g, double* a, Scalars sc, cudaStream_t s)
 }
 
 void launch_project(int D, const Geo& g, double* const ut[3], const double* p,
-                    double* const beta[3], double* uvel[3], double coef, cudaStream_t s) {
+                    double* const beta[3], double* uvel[3], double coef, const DivCheck& dc,
+                    cudaStream_t s) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
-  if (D == 3) k_project<3><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef);
-  else k_project<2><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef);
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(dc.out + dc.acc);
+  if (D == 3) k_project<3><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef, acc);
+  else k_project<2><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef, acc);
+  k_div_check<<<1, 32, 0, s>>>(dc.out, dc.acc, dc.step, dc.all, dc.tol, dc.viol);
 }
 
 void launch_norm2(int D, const Geo& g, double* const a[3], int ncomp, Scalars sc, int slot,
@@ -1219,8 +1307,28 @@ void launch_finalize_sum(const double* partial, int nb, double* out, int slot, d
 }
 
 void launch_tol_check(cudaGraphConditionalHandle h, const double* out, int sf, int sr,
-                      double rtol, int maxc, int* counter, long long* total, cudaStream_t s) {
-  k_tol_check<<<1, 32, 0, s>>>(h, out, sf, sr, rtol, maxc, counter, total);
+                      double rtol, int maxc, int* counter, long long* total, int* nonconv,
+                      cudaStream_t s, int smax, double mscale, double mtol) {
+  k_tol_check<<<1, 32, 0, s>>>(h, out, sf, sr, rtol, maxc, counter, total, nonconv,
+                               smax < 0 ? 0 : smax, mscale, smax < 0 ? 0.0 : mtol);
+}
+
+void launch_finalize_max(const double* partial, int nb, double* out, int slot,
+                         cudaStream_t s) {
+  k_finalize<<<1, 1024, 0, s>>>(partial, nb, out, slot, 1.0, 1);
+}
+
+void launch_absmax_cells(int D, const Geo& g, const double* a, Scalars sc, int slot,
+                         cudaStream_t s) {
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  int nb = red_grid(ncell);
+  k_absmax_cells<<<nb, kBlock1D, 0, s>>>(g, a, sc.partial);
+  k_finalize<<<1, 1024, 0, s>>>(sc.partial, nb, sc.out, slot, 1.0, 1);
+}
+
+void launch_res_check(const double* out, int sf, int sr, double thresh, int* nonconv,
+                      cudaStream_t s) {
+  k_res_check<<<1, 32, 0, s>>>(out, sf, sr, thresh, nonconv);
 }
 
 void launch_fill(double* a, long long n, double v, cudaStream_t s) {

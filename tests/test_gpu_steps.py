@@ -121,6 +121,24 @@ def test_tolerance_mode_matches():
         assert_close(g.get_velocity(d), o.get("u", d), 1e-8, "u%d" % d)
 
 
+def test_divergence_stop_rule_matches_the_oracle():
+    # rtol 1e-9 alone leaves max |D.u| above 1e-10 on c1; with div_tol the
+    # pressure solves run until (euler dt / sigma) max |r_p| <= div_tol on
+    # both sides, so both take the same V-cycles and every projection of the
+    # run stays within div_tol
+    inst = W.c1()
+    g, o = pair(inst, {"vc_visc": 0, "vc_p": 0, "rtol": 1e-9, "max_cycles": 60,
+                       "div_tol": 1e-10})
+    for k in range(3):
+        assert g.step(1) == bfibm.OK
+        o.step(1)
+        sg, so = g.get_stats(), o.stats()
+        assert sg["cycles_p"] == so["cycles_p"], (k, sg["cycles_p"], so["cycles_p"])
+        assert sg["div_max_step"] <= 1e-10 and so["div_max"] <= 1e-10
+    assert g.get_stats()["div_violations"] == 0
+    compare_state(g, o, inst, "c1 with the divergence stop rule")
+
+
 def test_graph_replay_equals_direct_launches():
     inst = W.c1()
     a = bfibm.load_instance(inst)

@@ -112,3 +112,26 @@ def test_c1_kinetic_energy_stable():
     X = o.nodes()
     assert np.all(np.isfinite(X))
     assert np.abs(X - c["X"]).max() > 1e-4      # the biofilm moves with the flow
+
+
+def test_divergence_target_holds_after_every_projection():
+    # the relative-residual test alone (rtol 1e-9) leaves max |D.u| above
+    # 1e-10; adding (euler dt / sigma) max |r_p| <= div_tol to the pressure
+    # solve's stopping test holds it below div_tol after every projection
+    c = W.c1()
+    divs = {}
+    cyc = {}
+    for tol in (0.0, 1e-10):
+        prm = dict(c["params"], vc_visc=0, vc_p=0, rtol=1e-9, max_cycles=100, div_tol=tol)
+        o = O.Oracle(prm)
+        o.set_nodes(c["X"])
+        o.set_springs(c["ab"], c["rest"], c["K"], c["brk"])
+        divs[tol], cyc[tol] = [], []
+        for _ in range(3):
+            o.step(1)
+            st = o.stats()
+            divs[tol].append(st["div_max"])
+            cyc[tol].append(st["cycles_p"])
+    assert max(divs[0.0]) > 1e-10
+    assert max(divs[1e-10]) <= 1e-10
+    assert sum(cyc[1e-10]) > sum(cyc[0.0])
