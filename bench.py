@@ -46,9 +46,9 @@ DC_SOLVER = dict(TOL_SOLVER, nu1=3, nu2=3, inner_cycles=3, krylov=0)
 DIV_TARGET = 1e-10
 # ncu capture of the FP32 viscous sweep on the 128x128x256 grid (mean of the
 # three components' dram__bytes_read.sum + dram__bytes_write.sum per launch)
-# in the shape the autotuner chose: 16 rows, 7 planes per chunk, 2 planes per
-# phase, 32 threads per row
-PROFILED_SWEEP_SHAPE = (16, 7, 2, 32)
+# in the shape the autotuner chose (tile rows, planes per chunk, planes per
+# phase, threads per row, kernel); claimed only while the tuner picks it
+PROFILED_SWEEP_SHAPE = (16, 7, 2, 32, 0)
 PROFILED_SWEEP_TRAFFIC = 229.5e6
 
 
@@ -345,12 +345,16 @@ def sweep_roofline(ctx, stream, prm, cells):
         nlaunch = sweeps * prm["dim"]
         alg = alg_bytes_visc_sweep(prm["dim"], cells, 4)
         plans = [ctx.tma_plan(0, d) for d in range(prm["dim"])]
-        if all(p is None for p in plans):
+        kinds = {(ctx.sweep_shape(0, d) or (0,) * 5)[4] for d in range(prm["dim"])}
+        if any(p is not None for p in plans) or len(kinds) > 1:
+            kname = ("k_rb_tma / k_v_rb_fused<float> / k_v_rb_pair (red-black sweep of one "
+                     "viscous component, FP32, finest grid; per component the autotuned choice)")
+        elif kinds == {1}:
+            kname = ("k_v_rb_pair (pair red-black sweep of one viscous component, FP32, finest "
+                     "grid: a thread per (red, black) pair of a row marching over the planes)")
+        else:
             kname = ("k_v_rb_fused<float> (one-pass red-black sweep of one viscous component, "
                      "FP32, finest grid, inputs read from global memory)")
-        else:
-            kname = ("k_rb_tma / k_v_rb_fused<float> (one-pass red-black sweep of one viscous "
-                     "component, FP32, finest grid; per component the autotuned choice)")
     else:
         ctx.smooth_viscous(0, 2, sync=True)
         torch.cuda.nvtx.range_push("sweep")

@@ -300,21 +300,29 @@ bfibm_status bfibm_load_state(bfibm_ctx* c, const void* buf, int64_t bytes);
    level does not use the TMA sweep (not allowed, or the one-pass sweep timed
    faster). No counterpart in the paper. */
 bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]);
-/* Launch shape the autotuner chose for the one-pass FP32 sweep (the kernel
-   that reads its inputs from global memory) of one level and kind (0..D-1:
-   viscous component, 3: pressure), mixed-precision contexts only: out = {tile
-   rows, planes per chunk, planes per phase, threads per row}; 0 stands for
-   the built-in choice. BFIBM_EINVAL for an FP64 context, a bad level or kind,
+/* Launch shape the autotuner chose for the one-pass FP32 sweep (the kernels
+   that read their inputs from global memory) of one level and kind (0..D-1:
+   viscous component, 3: pressure), mixed-precision contexts only: out =
+   {tile rows, planes per chunk, planes per phase, threads per row, kernel};
+   kernel 0 is the ring sweep (a thread per point pair or per 32-thread row
+   group, a ring of new red planes, 0 in the first four fields standing for the
+   built-in choice), kernel 1 the pair sweep of a viscous component (a thread
+   per (red, black) pair of a row marching over the planes, two float2 row
+   loads per array and plane; planes per phase 1, threads per row 0). Both
+   give the same bits. BFIBM_EINVAL for an FP64 context, a bad level or kind,
    or a level shape the tuner has not timed. No counterpart in the paper. */
-bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[4]);
+bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[5]);
 /* Pin the one-pass FP32 sweep with shape {tile rows (0: built-in), planes per
    chunk (0: built-in), planes per phase (1 or 2), threads per row (0 or a
-   multiple of 32 up to 128)} for the shape of one level and kind, process-wide,
-   in place of the autotuner's choice (the TMA sweep is no longer used there);
+   multiple of 32 up to 128), kernel (0 ring sweep; 1 pair sweep, which takes
+   tile rows >= 1, planes per chunk >= 1, planes per phase 1, threads per row
+   0, a viscous kind and a level with walls in x and y and an even row of at
+   most 256 points)} for the shape of one level and kind, process-wide, in
+   place of the autotuner's choice (the TMA sweep is no longer used there);
    the next step captures a new step graph. 3D mixed-precision contexts only;
    BFIBM_EINVAL otherwise or for a shape outside those ranges. Same results to
    the bit as any other shape. No counterpart in the paper. */
-bfibm_status bfibm_sweep_set_shape(bfibm_ctx* c, int level, int kind, const int32_t shape[4]);
+bfibm_status bfibm_sweep_set_shape(bfibm_ctx* c, int level, int kind, const int32_t shape[5]);
 /* Pin the TMA sweep's plan {tile rows, planes per chunk, planes prefetched
    (1..3), columns per strip (>= n[0]: whole rows), grid blocks (0: as many as
    fit at once)} for the shape of one level, process-wide, in place of the

@@ -349,18 +349,20 @@ class Context:
         return tuple(out) if st == OK else None
 
     def sweep_shape(self, level=0, kind=0):
-        """(tile rows, planes per chunk, planes per phase, threads per row) of
-        the tuned one-pass FP32 sweep on a level (0: built-in choice), or None
+        """(tile rows, planes per chunk, planes per phase, threads per row,
+        kernel) of the tuned one-pass FP32 sweep on a level (kernel 0: ring
+        sweep, 1: pair sweep; 0 in the first four: built-in choice), or None
         where the level has not been tuned."""
-        out = (C.c_int32 * 4)()
+        out = (C.c_int32 * 5)()
         st = self.lib.bfibm_sweep_shape(self.h, level, kind, out)
         return tuple(out) if st == OK else None
 
     def sweep_set_shape(self, level, kind, shape):
         """Pin (tile rows, planes per chunk, planes per phase, threads per
-        row) of the one-pass FP32 sweep for the shape of a level; see
-        bfibm_sweep_set_shape."""
-        arr = (C.c_int32 * 4)(*[int(v) for v in shape])
+        row, kernel) of the one-pass FP32 sweep for the shape of a level (a
+        4-tuple pins the ring sweep); see bfibm_sweep_set_shape."""
+        shape = list(shape) + [0] * (5 - len(shape))
+        arr = (C.c_int32 * 5)(*[int(v) for v in shape])
         self._chk(self.lib.bfibm_sweep_set_shape(self.h, level, kind, arr),
                   "bfibm_sweep_set_shape")
 

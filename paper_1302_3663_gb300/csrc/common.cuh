@@ -49,6 +49,27 @@ struct Ptr3d {
   double* a[3];
 };
 
+// The FP32 viscous point update, Eq. (NSdis1-1) with Eq. (divergenceGrad) /
+// (divergencePartial) on the staggered grid, with every rounding written out
+// (each product, difference and fused multiply-add explicit), so that every
+// FP32 sweep kernel (ring, pair and TMA-staged) gives the same bits whatever
+// the compiler would otherwise contract:
+//   cross += mep (u_e(F+e) - u_e(F+e-d)) - mem (u_e(F) - u_e(F-d))
+//   off = cross + cdp u_d(F+d) + cdm u_d(F-d) + sum_e (cep u_d(F+e) + cem u_d(F-e))
+//   u_d(F) = (rhs + ir off) / diag, with 1 / diag precomputed
+__device__ __forceinline__ float vx_cross(float cross, float mep, float uEp, float uEpm, float mem,
+                                          float uF, float uFm) {
+  return __fadd_rn(cross,
+                   __fmaf_rn(mep, __fsub_rn(uEp, uEpm), -__fmul_rn(mem, __fsub_rn(uF, uFm))));
+}
+__device__ __forceinline__ float vx_off(float cross, float cdp, float up, float cdm, float um) {
+  return __fmaf_rn(cdm, um, __fmaf_rn(cdp, up, cross));
+}
+__device__ __forceinline__ float vx_acc(float off, float w, float u) { return __fmaf_rn(w, u, off); }
+__device__ __forceinline__ float vx_final(float rhs, float ir, float off, float idg) {
+  return __fmul_rn(__fmaf_rn(ir, off, rhs), idg);
+}
+
 struct Scalars {
   double* partial;   // kRedBlocks partial results
   double* out;       // 16 finalized scalars
@@ -95,6 +116,13 @@ void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out
                        cudaStream_t s, int TYo = 0, int KCo = 0, int NPo = 1, int BXo = 0);
 // chunk planes filling `waves` waves of resident blocks (3D FP32 sweeps; 0: none)
 int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int BX, int waves);
+// The pair sweep of a 3D FP32 viscous component (smooth.cu): one thread per
+// (red, black) pair of a row, TY rows per block plus two ring rows, KC planes
+// per chunk; same arithmetic as the one-pass sweep
+bool pair_eligible(int D, const Geo& g, int TY);
+void launch_v_rb_pair(const Geo& g, const LevelPtrs<float>& L, int d, float* out, double inv_re,
+                      cudaStream_t s, int TY, int KC);
+int pair_fill_kc(const Geo& g, int d, int TY, int waves);
 
 // Mixed precision (mixed.cu).
 int red_blocks_3d(int D, const Geo& g);
@@ -161,9 +189,10 @@ cudaError_t launch_rb_tma(int D, const Geo& g, const LevelPtrs<float>& L, int K,
                           unsigned long long wait_ns = kTmaWaitNs);
 // pin a plan {TY, KC, PD, SW, grid (0: resident blocks)} for a level shape
 bool tma_set_plan(int K, const Geo& g, const int in[5]);
-// the one-pass sweep's tuned tile rows and chunk planes for a level shape
-bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX);
-bool ring_set_shape(int K, const Geo& g, const int in[4]);
+// the one-pass sweep's tuned tile rows, chunk planes, planes per phase,
+// threads per row and kernel (0 ring sweep, 1 pair sweep) for a level shape
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX, int* KERN = nullptr);
+bool ring_set_shape(int K, const Geo& g, const int in[5]);
 // whether the tuner found the TMA sweep faster than the one-pass sweep
 bool tma_chosen(int K, const Geo& g);
 // tuned plan of a level shape: tile rows, chunk planes, prefetch planes,

@@ -269,7 +269,10 @@ __device__ __forceinline__ void v_coef(const LevelPtrs<T>& L, const Pt& q, T ir,
     const T* __restrict__ me = L.mue[edge_id(d, e)];
     const int Ep = F + q.op[e];
     T mep = me[Ep], mem = me[F];
-    v.cross += mep * (ue[Ep] - ue[Ep + od_m]) - mem * (ue[F] - ue[F + od_m]);
+    if constexpr (kIdg<T>)
+      v.cross = vx_cross(v.cross, mep, ue[Ep], ue[Ep + od_m], mem, ue[F], ue[F + od_m]);
+    else
+      v.cross += mep * (ue[Ep] - ue[Ep + od_m]) - mem * (ue[F] - ue[F + od_m]);
     v.cep[k] = mep;
     v.cem[k] = mem;
     if constexpr (!kIdg<T>) dgV += (q.wp[e] ? T(2) : T(1)) * mep + (q.wm[e] ? T(2) : T(1)) * mem;
@@ -290,16 +293,29 @@ __device__ __forceinline__ T v_red(const LevelPtrs<T>& L, const Pt& q, T ir) {
   VC<D, d, T> v;
   v_coef<D, d, T>(L, q, ir, v);
   const T* __restrict__ ud = L.u[d];
-  T off = v.cross + v.cdp * ud[q.F + q.op[d]] + v.cdm * ud[q.F + q.om[d]];
-  int k = 0;
+  if constexpr (kIdg<T>) {
+    float off = vx_off(v.cross, v.cdp, ud[q.F + q.op[d]], v.cdm, ud[q.F + q.om[d]]);
+    int k = 0;
 #pragma unroll
-  for (int e = 0; e < D; ++e) {
-    if (e == d) continue;
-    if (!q.wp[e]) off += v.cep[k] * ud[q.F + q.op[e]];
-    if (!q.wm[e]) off += v.cem[k] * ud[q.F + q.om[e]];
-    ++k;
+    for (int e = 0; e < D; ++e) {
+      if (e == d) continue;
+      if (!q.wp[e]) off = vx_acc(off, v.cep[k], ud[q.F + q.op[e]]);
+      if (!q.wm[e]) off = vx_acc(off, v.cem[k], ud[q.F + q.om[e]]);
+      ++k;
+    }
+    return vx_final(L.uf[d][q.F], ir, off, v.diag);
+  } else {
+    T off = v.cross + v.cdp * ud[q.F + q.op[d]] + v.cdm * ud[q.F + q.om[d]];
+    int k = 0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      if (e == d) continue;
+      if (!q.wp[e]) off += v.cep[k] * ud[q.F + q.op[e]];
+      if (!q.wm[e]) off += v.cem[k] * ud[q.F + q.om[e]];
+      ++k;
+    }
+    return v_solve<T>(L.uf[d][q.F] + ir * off, v.diag);
   }
-  return v_solve<T>(L.uf[d][q.F] + ir * off, v.diag);
 }
 
 template <int D, int d, typename T>
@@ -308,17 +324,33 @@ __device__ __forceinline__ T v_black(const LevelPtrs<T>& L, const Ring<T>& rg, c
   VC<D, d, T> v;
   v_coef<D, d, T>(L, q, ir, v);
   // along d a wall neighbour is the stored zero face: the ring holds 0 there
-  T off = v.cross + v.cdp * ring_nb<D, T>(rg, q, i, n0, d, +1, r, sl_m, sl_0, sl_p) +
-          v.cdm * ring_nb<D, T>(rg, q, i, n0, d, -1, r, sl_m, sl_0, sl_p);
-  int k = 0;
+  if constexpr (kIdg<T>) {
+    float off = vx_off(v.cross, v.cdp, ring_nb<D, T>(rg, q, i, n0, d, +1, r, sl_m, sl_0, sl_p),
+                       v.cdm, ring_nb<D, T>(rg, q, i, n0, d, -1, r, sl_m, sl_0, sl_p));
+    int k = 0;
 #pragma unroll
-  for (int e = 0; e < D; ++e) {
-    if (e == d) continue;
-    if (!q.wp[e]) off += v.cep[k] * ring_nb<D, T>(rg, q, i, n0, e, +1, r, sl_m, sl_0, sl_p);
-    if (!q.wm[e]) off += v.cem[k] * ring_nb<D, T>(rg, q, i, n0, e, -1, r, sl_m, sl_0, sl_p);
-    ++k;
+    for (int e = 0; e < D; ++e) {
+      if (e == d) continue;
+      if (!q.wp[e])
+        off = vx_acc(off, v.cep[k], ring_nb<D, T>(rg, q, i, n0, e, +1, r, sl_m, sl_0, sl_p));
+      if (!q.wm[e])
+        off = vx_acc(off, v.cem[k], ring_nb<D, T>(rg, q, i, n0, e, -1, r, sl_m, sl_0, sl_p));
+      ++k;
+    }
+    return vx_final(L.uf[d][q.F], ir, off, v.diag);
+  } else {
+    T off = v.cross + v.cdp * ring_nb<D, T>(rg, q, i, n0, d, +1, r, sl_m, sl_0, sl_p) +
+            v.cdm * ring_nb<D, T>(rg, q, i, n0, d, -1, r, sl_m, sl_0, sl_p);
+    int k = 0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      if (e == d) continue;
+      if (!q.wp[e]) off += v.cep[k] * ring_nb<D, T>(rg, q, i, n0, e, +1, r, sl_m, sl_0, sl_p);
+      if (!q.wm[e]) off += v.cem[k] * ring_nb<D, T>(rg, q, i, n0, e, -1, r, sl_m, sl_0, sl_p);
+      ++k;
+    }
+    return v_solve<T>(L.uf[d][q.F] + ir * off, v.diag);
   }
-  return v_solve<T>(L.uf[d][q.F] + ir * off, v.diag);
 }
 
 template <int D, int d, typename T, int NP>
@@ -411,6 +443,376 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pair sweep (3D FP32 viscous component d, walls in x and y). One thread owns
+// the two points (x0, x0 + 1), x0 = 2 ip, of a row: one red, one black. It
+// walks the planes of a chunk. Every input row is read as one float2, plus
+// the value left (x0 - 1) or right (x0 + 2) of the pair where a stencil
+// reaches there. Rows that the next planes need again (the plane above
+// becomes the plane itself, then the plane below) stay in registers, so a
+// pair costs 15 to 17 loads per plane.
+//
+// At plane k the thread computes the coefficient sets of both points, that
+// is, everything of the update but the u_d neighbours. The red point is then
+// solved from the old u_d values, and the black point's set is kept. After
+// one barrier the black point of plane k - 1 is solved from its kept set and
+// the ring of new red values. The ring has four plane slots, so the next
+// plane's red values never overwrite a slot still being read. Then the pair
+// of plane k - 1 is stored. The expressions and their order are those of
+// v_red / v_black; a term the ring sweep skips at a wall gets a zero weight
+// here (adding 0 * x changes no bit).
+// ---------------------------------------------------------------------------
+struct PRow {        // a row at the pair: v = (x0, x0 + 1), l = x0 - 1, r = x0 + 2
+  float2 v;
+  float l, r;
+};
+
+template <int o>     // the value at x0 + o, o in -1 .. 2
+__device__ __forceinline__ float pe(const PRow& q) {
+  if constexpr (o == -1) return q.l;
+  else if constexpr (o == 0) return q.v.x;
+  else if constexpr (o == 1) return q.v.y;
+  else return q.r;
+}
+
+__device__ __forceinline__ float2 ldp(const float* __restrict__ a, int o) {
+  return __ldg(reinterpret_cast<const float2*>(a + o));
+}
+// bring a line towards L1 for the next plane's load (no register is tied up)
+__device__ __forceinline__ void pf1(const float* a, int o) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a + o));
+}
+
+struct PSet {
+  float cross, cdp, cdm, cep0, cem0, cep1, cem1, uf, idg;
+};
+
+// The coefficient set of element e from the rows of its plane: pc (u_d's own
+// centre row is not needed here), for every e2 != d pairs of rows at F and at
+// F + e, each with the row shifted by -d.
+template <int d, int e>
+__device__ __forceinline__ PSet pset(const PRow& mc, const PRow& mcm, const PRow& me0_F,
+                                     const PRow& me0_P, const PRow& ue0_F, const PRow& ue0_Fm,
+                                     const PRow& ue0_P, const PRow& ue0_Pm, const PRow& me1_F,
+                                     const PRow& me1_P, const PRow& ue1_F, const PRow& ue1_Fm,
+                                     const PRow& ue1_P, const PRow& ue1_Pm, const PRow& uf,
+                                     const PRow& idg, bool wp0, bool wm0, bool wp1, bool wm1) {
+  constexpr int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  constexpr int sd = d == 0 ? -1 : 0;        // x shift of F - d
+  constexpr int s1 = e1 == 0 ? 1 : 0, s2 = e2 == 0 ? 1 : 0;   // x shift of F + e
+  PSet c;
+  float mcp = pe<e>(mc), mcmv = pe<e + sd>(mcm);
+  c.cdp = 2.f * mcp;
+  c.cdm = 2.f * mcmv;
+  c.cross = 0.f;
+  {
+    float mep = pe<e + s1>(me0_P), mem = pe<e>(me0_F);
+    c.cross = vx_cross(c.cross, mep, pe<e + s1>(ue0_P), pe<e + s1 + sd>(ue0_Pm), mem, pe<e>(ue0_F),
+                       pe<e + sd>(ue0_Fm));
+    c.cep0 = wp0 ? 0.f : mep;
+    c.cem0 = wm0 ? 0.f : mem;
+  }
+  {
+    float mep = pe<e + s2>(me1_P), mem = pe<e>(me1_F);
+    c.cross = vx_cross(c.cross, mep, pe<e + s2>(ue1_P), pe<e + s2 + sd>(ue1_Pm), mem, pe<e>(ue1_F),
+                       pe<e + sd>(ue1_Fm));
+    c.cep1 = wp1 ? 0.f : mep;
+    c.cem1 = wm1 ? 0.f : mem;
+  }
+  c.uf = pe<e>(uf);
+  c.idg = pe<e>(idg);
+  return c;
+}
+
+__device__ __forceinline__ float psolve(const PSet& c, float ir, float up_d, float um_d,
+                                        float up_1, float um_1, float up_2, float um_2) {
+  float off = vx_off(c.cross, c.cdp, up_d, c.cdm, um_d);
+  off = vx_acc(off, c.cep0, up_1);
+  off = vx_acc(off, c.cem0, um_1);
+  off = vx_acc(off, c.cep1, up_2);
+  off = vx_acc(off, c.cem1, um_2);
+  return vx_final(c.uf, ir, off, c.idg);
+}
+
+__device__ __forceinline__ PSet psel(bool t, const PSet& a, const PSet& b) {
+  PSet c;
+  c.cross = t ? a.cross : b.cross;
+  c.cdp = t ? a.cdp : b.cdp;
+  c.cdm = t ? a.cdm : b.cdm;
+  c.cep0 = t ? a.cep0 : b.cep0;
+  c.cem0 = t ? a.cem0 : b.cem0;
+  c.cep1 = t ? a.cep1 : b.cep1;
+  c.cem1 = t ? a.cem1 : b.cem1;
+  c.uf = t ? a.uf : b.uf;
+  c.idg = t ? a.idg : b.idg;
+  return c;
+}
+
+template <int d, bool PERZ>
+__global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
+                                                   float* __restrict__ out, int TY, int KC,
+                                                   float ir) {
+  constexpr int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* ring = reinterpret_cast<float*>(sm_raw);
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int W = n0;                        // ring row pitch
+  const int plane = (TY + 2) * W;
+  const int x0 = 2 * threadIdx.x, r = threadIdx.y;
+  const int j0 = blockIdx.x * TY;
+  const int k0 = blockIdx.y * KC, k1 = min(k0 + KC, n2);
+  const int j = j0 - 1 + r;
+  const bool lane_ok = x0 < n0;
+  const bool rowvalid = lane_ok && j >= 0 && j < n1;
+  const bool own = rowvalid && r >= 1 && r <= TY;
+  const int st1 = (int)g.st[1], st2 = (int)g.st[2];
+  const int xl = x0 > 0 ? x0 - 1 : 0;     // left of the pair (clamped at the wall: zero weight)
+  // wall flags of the row and of the two x positions
+  const bool wpy = j == n1 - 1, wmy = j == 0;
+  const bool wmx0 = x0 == 0, wpx1 = x0 + 1 == n0 - 1;
+  for (int q = threadIdx.y * blockDim.x + threadIdx.x; q < 4 * plane; q += blockDim.x * blockDim.y)
+    ring[q] = 0.f;
+  const float* __restrict__ ud = L.u[d];
+  const float* __restrict__ ua = L.u[e1];
+  const float* __restrict__ ub = L.u[e2];
+  const float* __restrict__ ma = L.mue[edge_id(d, e1)];
+  const float* __restrict__ mb = L.mue[edge_id(d, e2)];
+  const float* __restrict__ mc = L.muc;
+  const float* __restrict__ uf = L.uf[d];
+  const float* __restrict__ ig = L.idg[d];
+  // row offsets (elements, x0 included): this row, the rows below and above
+  const int jm = j > 0 ? j - 1 : j;
+  const int oy0 = j * st1 + x0, oym = jm * st1 + x0, oyp = (j + 1) * st1 + x0;
+  // plane index of plane k (wrapped on a periodic axis, clamped into the
+  // storage on a wall axis: planes outside are never used)
+  auto pz = [&](int k) -> int {
+    if constexpr (PERZ) return k < 0 ? k + n2 : (k >= n2 ? k - n2 : k);
+    else return k < 0 ? 0 : (k > n2 ? n2 : k);
+  };
+  auto row = [&](const float* __restrict__ a, int oy, int kz, bool left, bool right) -> PRow {
+    PRow q;
+    const int o = oy + kz * st2;
+    q.v = ldp(a, o);
+    q.l = left ? __ldg(a + o - x0 + xl) : 0.f;
+    q.r = right ? __ldg(a + o + 2) : 0.f;
+    return q;
+  };
+  // register queues along z: rows of plane k - 1 and k
+  PRow UDm{}, UDc{};
+  PRow Q0c{}, Q1c{}, Q2c{};     // the component-specific rows of plane k (see below)
+  const bool ld = rowvalid;
+  {
+    const int km = pz(k0 - 2), kc = pz(k0 - 1);
+    if (ld) {
+      UDm = row(ud, oy0, km, false, false);
+      UDc = row(ud, oy0, kc, false, false);
+      if constexpr (d == 0) {          // u_z and mu_xz at F (plane k)
+        Q0c = row(ub, oy0, kc, true, false);
+        Q1c = row(mb, oy0, kc, false, false);
+      } else if constexpr (d == 1) {   // u_z at F and F - y, mu_yz at F (plane k)
+        Q0c = row(ub, oy0, kc, false, false);
+        Q1c = row(ub, oym, kc, false, false);
+        Q2c = row(mb, oy0, kc, false, false);
+      } else {                         // u_x at F, u_y at F and F + y, mu_c at F (plane k - 1)
+        Q0c = row(ua, oy0, km, false, true);
+        Q1c = row(ub, oy0, km, false, false);
+        Q2c = row(ub, oyp, km, false, false);
+      }
+    }
+  }
+  PRow MCzm{};
+  if constexpr (d == 2) {
+    if (ld) MCzm = row(mc, oy0, pz(k0 - 2), false, false);
+  }
+  __syncthreads();
+  int sk = 0;                                // ring slot of plane k
+  PSet keep{};                               // the black point's set of plane k - 1
+  float red_prev = 0.f;
+  int par_prev = 0;
+  for (int k = k0 - 1; k <= k1; ++k) {
+    const bool planevalid = PERZ || (k >= 0 && k < n2);
+    const int kw = pz(k), kp = pz(k + 1);
+    const int par = (j + kw) & 1;            // element index of the red point
+    const bool wpz = !PERZ && kw == n2 - 1, wmz = !PERZ && kw == 0;
+    float redv = 0.f;
+    PSet blk{};
+    PRow UDp{};
+    if (ld) UDp = row(ud, oy0, kp, false, false);
+    if (ld && k < k1) {
+      // the rows the next plane loads: one plane further along z
+      const int kn = pz(k + 1) * st2, kn2 = pz(k + 2) * st2;
+      pf1(ud, oy0 + kn2);
+      pf1(ud, oym + kn);
+      pf1(ud, oyp + kn);
+      pf1(mc, oy0 + kn);
+      pf1(uf, oy0 + kn);
+      pf1(ig, oy0 + kn);
+      if constexpr (d == 0) {
+        pf1(ma, oy0 + kn);
+        pf1(ma, oyp + kn);
+        pf1(ua, oy0 + kn);
+        pf1(ua, oyp + kn);
+        pf1(ub, oy0 + kn2);
+        pf1(mb, oy0 + kn2);
+      } else if constexpr (d == 1) {
+        pf1(mc, oym + kn);
+        pf1(ma, oy0 + kn);
+        pf1(ua, oy0 + kn);
+        pf1(ua, oym + kn);
+        pf1(ub, oy0 + kn2);
+        pf1(ub, oym + kn2);
+        pf1(mb, oy0 + kn2);
+      } else {
+        pf1(ma, oy0 + kn);
+        pf1(ua, oy0 + kn);
+        pf1(mb, oy0 + kn);
+        pf1(mb, oyp + kn);
+        pf1(ub, oy0 + kn);
+        pf1(ub, oyp + kn);
+      }
+    }
+    PRow N0{}, N1{}, N2{}, N3{};
+    if (ld && planevalid) {
+      // u_d at the rows beside (old values) and one value beside the pair
+      const PRow UDym = row(ud, oym, kw, false, false), UDyp = row(ud, oyp, kw, false, false);
+      PRow UDx = UDc;
+      const int ox = oy0 + kw * st2;
+      if (par) UDx.r = __ldg(ud + ox + 2);
+      else UDx.l = __ldg(ud + ox - x0 + xl);
+      PSet c0, c1;
+      if constexpr (d == 0) {
+        // e1 = y: mu_xy at F, F + y; u_y at F, F + y (and x - 1)
+        // e2 = z: mu_xz at F, F + z; u_z at F, F + z (and x - 1)
+        const PRow MC = row(mc, oy0, kw, true, false);
+        const PRow MAF = row(ma, oy0, kw, false, false), MAP = row(ma, oyp, kw, false, false);
+        const PRow UAF = row(ua, oy0, kw, true, false), UAP = row(ua, oyp, kw, true, false);
+        const PRow UBP = row(ub, oy0, kp, true, false), MBP = row(mb, oy0, kp, false, false);
+        const PRow UF = row(uf, oy0, kw, false, false), IG = row(ig, oy0, kw, false, false);
+        c0 = pset<0, 0>(MC, MC, MAF, MAP, UAF, UAF, UAP, UAP, Q1c, MBP, Q0c, Q0c, UBP, UBP, UF, IG,
+                        wpy, wmy, wpz, wmz);
+        c1 = pset<0, 1>(MC, MC, MAF, MAP, UAF, UAF, UAP, UAP, Q1c, MBP, Q0c, Q0c, UBP, UBP, UF, IG,
+                        wpy, wmy, wpz, wmz);
+        N0 = UBP;
+        N1 = MBP;
+      } else if constexpr (d == 1) {
+        // e1 = x: mu_xy at F, F + x; u_x at F, F + x and the row below
+        // e2 = z: mu_yz at F, F + z; u_z at F, F + z and the row below
+        const PRow MC = row(mc, oy0, kw, false, false), MCm = row(mc, oym, kw, false, false);
+        const PRow MA = row(ma, oy0, kw, false, true);
+        const PRow UA = row(ua, oy0, kw, false, true), UAm = row(ua, oym, kw, false, true);
+        const PRow UBP = row(ub, oy0, kp, false, false), UBPm = row(ub, oym, kp, false, false);
+        const PRow MBP = row(mb, oy0, kp, false, false);
+        const PRow UF = row(uf, oy0, kw, false, false), IG = row(ig, oy0, kw, false, false);
+        c0 = pset<1, 0>(MC, MCm, MA, MA, UA, UAm, UA, UAm, Q2c, MBP, Q0c, Q1c, UBP, UBPm, UF, IG,
+                        false, wmx0, wpz, wmz);
+        c1 = pset<1, 1>(MC, MCm, MA, MA, UA, UAm, UA, UAm, Q2c, MBP, Q0c, Q1c, UBP, UBPm, UF, IG,
+                        wpx1, false, wpz, wmz);
+        N0 = UBP;
+        N1 = UBPm;
+        N2 = MBP;
+      } else {
+        // e1 = x: mu_xz at F, F + x; u_x at F, F + x and the plane below
+        // e2 = y: mu_yz at F, F + y; u_y at F, F + y and the plane below
+        const PRow MC = row(mc, oy0, kw, false, false);
+        const PRow MA = row(ma, oy0, kw, false, true);
+        const PRow UA = row(ua, oy0, kw, false, true);
+        const PRow MBF = row(mb, oy0, kw, false, false), MBP = row(mb, oyp, kw, false, false);
+        const PRow UBF = row(ub, oy0, kw, false, false), UBP = row(ub, oyp, kw, false, false);
+        const PRow UF = row(uf, oy0, kw, false, false), IG = row(ig, oy0, kw, false, false);
+        c0 = pset<2, 0>(MC, MCzm, MA, MA, UA, Q0c, UA, Q0c, MBF, MBP, UBF, Q1c, UBP, Q2c, UF, IG,
+                        false, wmx0, wpy, wmy);
+        c1 = pset<2, 1>(MC, MCzm, MA, MA, UA, Q0c, UA, Q0c, MBF, MBP, UBF, Q1c, UBP, Q2c, UF, IG,
+                        wpx1, false, wpy, wmy);
+        N0 = UA;
+        N1 = UBF;
+        N2 = UBP;
+        N3 = MC;
+      }
+      // the red point: its set and its old neighbours along d, e1, e2
+      const PSet cr = psel(par != 0, c1, c0);
+      float np_[3], nm_[3];
+      np_[0] = par ? pe<2>(UDx) : pe<1>(UDx);
+      nm_[0] = par ? pe<0>(UDx) : pe<-1>(UDx);
+      np_[1] = par ? pe<1>(UDyp) : pe<0>(UDyp);
+      nm_[1] = par ? pe<1>(UDym) : pe<0>(UDym);
+      np_[2] = par ? pe<1>(UDp) : pe<0>(UDp);
+      nm_[2] = par ? pe<1>(UDm) : pe<0>(UDm);
+      redv = psolve(cr, ir, np_[d], nm_[d], np_[e1], nm_[e1], np_[e2], nm_[e2]);
+      const bool wall_red = (d == 0 && x0 + par == 0) || (d == 1 && j == 0) ||
+                            (d == 2 && !PERZ && kw == 0);
+      if (wall_red) redv = 0.f;
+      blk = psel(par != 0, c0, c1);
+    }
+    if (lane_ok) {
+      const float2 rv = make_float2(par ? 0.f : redv, par ? redv : 0.f);
+      *reinterpret_cast<float2*>(ring + sk * plane + r * W + x0) = rv;
+    }
+    __syncthreads();
+    // the black point of plane k - 1 on the block's own rows; the pair out
+    const int kb = k - 1;
+    if (own && kb >= k0 && kb < k1) {
+      const int kbw = pz(kb);
+      const int s_m = (sk + 2) & 3, s_0 = (sk + 3) & 3;   // planes k - 2, k - 1 (k: sk)
+      const int eb = par_prev ^ 1;
+      const int xb = x0 + eb;
+      const float* R0 = ring + s_0 * plane + r * W;
+      float np_[3], nm_[3];
+      np_[0] = xb + 1 < n0 ? R0[xb + 1] : 0.f;
+      nm_[0] = xb > 0 ? R0[xb - 1] : 0.f;
+      np_[1] = R0[W + xb];
+      nm_[1] = R0[-W + xb];
+      np_[2] = ring[sk * plane + r * W + xb];
+      nm_[2] = ring[s_m * plane + r * W + xb];
+      float bv = psolve(keep, ir, np_[d], nm_[d], np_[e1], nm_[e1], np_[e2], nm_[e2]);
+      const bool wall_blk = (d == 0 && xb == 0) || (d == 1 && j == 0) ||
+                            (d == 2 && !PERZ && kbw == 0);
+      if (wall_blk) bv = 0.f;
+      const float2 o = eb ? make_float2(red_prev, bv) : make_float2(bv, red_prev);
+      *reinterpret_cast<float2*>(out + oy0 + kbw * st2) = o;
+    }
+    // advance the queues by one plane
+    keep = blk;
+    red_prev = redv;
+    par_prev = par;
+    sk = (sk + 1) & 3;
+    UDm = UDc;
+    UDc = UDp;
+    if (ld) {
+      if constexpr (d == 0) {
+        if (planevalid) {
+          Q0c = N0;
+          Q1c = N1;
+        } else {
+          Q0c = row(ub, oy0, kp, true, false);
+          Q1c = row(mb, oy0, kp, false, false);
+        }
+      } else if constexpr (d == 1) {
+        if (planevalid) {
+          Q0c = N0;
+          Q1c = N1;
+          Q2c = N2;
+        } else {
+          Q0c = row(ub, oy0, kp, false, false);
+          Q1c = row(ub, oym, kp, false, false);
+          Q2c = row(mb, oy0, kp, false, false);
+        }
+      } else {
+        if (planevalid) {
+          Q0c = N0;
+          Q1c = N1;
+          Q2c = N2;
+          MCzm = N3;
+        } else {
+          Q0c = row(ua, oy0, kw, false, true);
+          Q1c = row(ub, oy0, kw, false, false);
+          Q2c = row(ub, oyp, kw, false, false);
+          MCzm = row(mc, oy0, kw, false, false);
+        }
+      }
+    }
+  }
+}
+
 struct FusedShape {
   dim3 grid, block;
   int TY, KC;
@@ -485,6 +887,65 @@ void launch_v_rb_fused(int D, const Geo& g, const LevelPtrs<T>& L, int d, T* out
   }
 }
 
+// Pair sweep: blocks of (pairs of a row rounded up to 32) x (TY + 2) threads
+// over (row tiles, plane chunks); 3D, walls in x and y, an even row of at
+// most 256 points.
+bool pair_eligible(int D, const Geo& g, int TY) {
+  if (D != 3 || g.per[0] || g.per[1] || (g.n[0] & 1) || g.n[0] < 4 || g.n[0] > 256) return false;
+  const int bx = ((g.n[0] / 2 + 31) / 32) * 32;
+  return TY >= 1 && TY <= g.n[1] && bx * (TY + 2) <= 512;
+}
+
+const void* pair_kernel(int d, bool perz) {
+  if (perz)
+    return d == 0 ? (const void*)k_v_rb_pair<0, true>
+                  : (d == 1 ? (const void*)k_v_rb_pair<1, true> : (const void*)k_v_rb_pair<2, true>);
+  return d == 0 ? (const void*)k_v_rb_pair<0, false>
+                : (d == 1 ? (const void*)k_v_rb_pair<1, false> : (const void*)k_v_rb_pair<2, false>);
+}
+
+size_t pair_smem(const Geo& g, int TY) { return (size_t)4 * (TY + 2) * g.n[0] * sizeof(float); }
+
+void launch_v_rb_pair(const Geo& g, const LevelPtrs<float>& L, int d, float* out, double inv_re,
+                      cudaStream_t s, int TY, int KC) {
+  const int bx = ((g.n[0] / 2 + 31) / 32) * 32;
+  if (KC < 1) KC = 1;
+  dim3 block(bx, TY + 2, 1);
+  dim3 grid((g.n[1] + TY - 1) / TY, (g.n[2] + KC - 1) / KC, 1);
+  const float ir = (float)(inv_re / (g.h * g.h));
+  const size_t sm = pair_smem(g, TY);
+  if (g.per[2]) {
+    if (d == 0) k_v_rb_pair<0, true><<<grid, block, sm, s>>>(g, L, out, TY, KC, ir);
+    else if (d == 1) k_v_rb_pair<1, true><<<grid, block, sm, s>>>(g, L, out, TY, KC, ir);
+    else k_v_rb_pair<2, true><<<grid, block, sm, s>>>(g, L, out, TY, KC, ir);
+  } else {
+    if (d == 0) k_v_rb_pair<0, false><<<grid, block, sm, s>>>(g, L, out, TY, KC, ir);
+    else if (d == 1) k_v_rb_pair<1, false><<<grid, block, sm, s>>>(g, L, out, TY, KC, ir);
+    else k_v_rb_pair<2, false><<<grid, block, sm, s>>>(g, L, out, TY, KC, ir);
+  }
+}
+
+// Chunk planes giving `waves` full waves of resident pair-sweep blocks; 0
+// where the occupancy cannot be had.
+int pair_fill_kc(const Geo& g, int d, int TY, int waves) {
+  if (!pair_eligible(3, g, TY)) return 0;
+  const void* fn = pair_kernel(d, g.per[2] != 0);
+  const int bx = ((g.n[0] / 2 + 31) / 32) * 32;
+  int bps = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, bx * (TY + 2), pair_smem(g, TY)) !=
+          cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const long long tiles = (g.n[1] + TY - 1) / TY;
+  long long chunks = (long long)waves * nsm * bps / tiles;
+  if (chunks < 1) return 0;
+  int KC = (int)((g.n[2] + chunks - 1) / chunks);
+  return KC < 2 ? 2 : KC;
+}
+
 // Let the fused sweeps run several blocks per SM: ask for a shared-memory
 // carveout of a quarter of the unified L1/shared storage for the FP64 sweeps
 // and half of it for the FP32 sweeps, whose taller tiles (up to 18 ring rows)
@@ -525,6 +986,13 @@ cudaError_t fused_set_carveout() {
   set((const void*)k_v_rb_fused<3, 2, double, 2>);
   set((const void*)k_v_rb_fused<2, 0, double, 1>);
   set((const void*)k_v_rb_fused<2, 1, double, 1>);
+  // the pair sweeps keep most of the unified storage as L1: their row loads
+  // are reused by neighbouring rows and by the next plane
+  for (int d = 0; d < 3; ++d)
+    for (bool perz : {false, true})
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pair_kernel(d, perz), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 25);
   return e;
 }
 

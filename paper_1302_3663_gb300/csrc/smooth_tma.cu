@@ -291,19 +291,19 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
           const int e = q == 0 ? e1 : e2;
           const int me = 4 + q, ue = 6 + q;
           float mep = sh(me, e, +1, 0, 0), mem = at(me);
-          cross += mep * (sh(ue, e, +1, 0, 0) - sh(ue, e, +1, d, -1)) -
-                   mem * (at(ue) - sh(ue, d, -1, 0, 0));
+          cross = vx_cross(cross, mep, sh(ue, e, +1, 0, 0), sh(ue, e, +1, d, -1), mem, at(ue),
+                           sh(ue, d, -1, 0, 0));
           cep[q] = mep;
           cem[q] = mem;
         }
-        float off = cross + cdp * nb(d, +1) + cdm * nb(d, -1);
+        float off = vx_off(cross, cdp, nb(d, +1), cdm, nb(d, -1));
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int e = q == 0 ? e1 : e2;
-          if (!wp(e)) off += cep[q] * nb(e, +1);
-          if (!wm(e)) off += cem[q] * nb(e, -1);
+          if (!wp(e)) off = vx_acc(off, cep[q], nb(e, +1));
+          if (!wm(e)) off = vx_acc(off, cem[q], nb(e, -1));
         }
-        return (at(1) + c * off) * at(2);   // slot 2: 1 / diagonal
+        return vx_final(at(1), c, off, at(2));   // slot 2: 1 / diagonal
       }
     };
     auto on_wall_face = [&](int i, int j, int kw) -> bool {   // fixed zero face of u_d
@@ -519,6 +519,7 @@ struct Plan {
   bool tma = false;    // the TMA sweep timed faster than the one-pass global-memory sweep
   int rTY = 0, rKC = 0, rNP = 1;   // fastest rows / chunk planes / planes per phase of the one-pass sweep
   int rBX = 0;                     // and threads per row (0: one per point pair, up to 128)
+  int rK = 0;                      // which one-pass sweep: 0 the ring sweep, 1 the pair sweep
 };
 
 using PlanKey = std::tuple<int, int, int, int, int, long long, int>;
@@ -714,11 +715,39 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
         best.rKC = search ? rKC : 0;
         best.rNP = rNP;
         best.rBX = rBX;
+        best.rK = 0;
       }
     }
     if (status != cudaSuccess) break;
   }
   if (status != cudaSuccess) break;
+  }
+  // the pair sweep (viscous components): tile rows and chunk planes
+  if (K < 3 && search && status == cudaSuccess) {
+    for (int pTY : {2, 4, 6, 8, 10, 14}) {
+      if (!pair_eligible(D, g, pTY)) continue;
+      int kcs_pair[5] = {8, 16, 32, pair_fill_kc(g, K, pTY, 1), pair_fill_kc(g, K, pTY, 2)};
+      for (int ci = 0; ci < 5; ++ci) {
+        const int pKC = kcs_pair[ci];
+        if (pKC <= 0 || pKC > g.n[2]) continue;
+        bool seen = false;
+        for (int cj = 0; cj < ci; ++cj) seen = seen || kcs_pair[cj] == pKC;
+        if (seen) continue;
+        auto pr = [&]() { launch_v_rb_pair(g, L, K, out, coef * g.h * g.h, s, pTY, pKC); };
+        pr();
+        float ms = per_launch_ms(pr);
+        if (status != cudaSuccess) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.rTY = pTY;
+          best.rKC = pKC;
+          best.rNP = 1;
+          best.rBX = 0;
+          best.rK = 1;
+        }
+      }
+      if (status != cudaSuccess) break;
+    }
   }
   const int tys[] = {2, 4, 6, 8};
   const int kcs[] = {16, 32, 64};
@@ -803,16 +832,21 @@ bool tma_set_plan(int K, const Geo& g, const int in[5]) {
     pl.rKC = it->second.rKC;
     pl.rNP = it->second.rNP;
     pl.rBX = it->second.rBX;
+    pl.rK = it->second.rK;
   }
   g_plans[plan_key(K, g)] = pl;
   return true;
 }
 
-// Pin the one-pass sweep (not the TMA one) with shape {TY, KC, NP, BX} for
-// the level shape of g, process-wide.
-bool ring_set_shape(int K, const Geo& g, const int in[4]) {
+// Pin the one-pass sweep (not the TMA one) with shape {TY, KC, NP, BX, kernel}
+// for the level shape of g, process-wide (kernel 1, the pair sweep, takes
+// TY > 0, KC > 0, NP 1 and BX 0).
+bool ring_set_shape(int K, const Geo& g, const int in[5]) {
   if (in[0] < 0 || in[1] < 0 || (in[2] != 1 && in[2] != 2) || in[3] < 0 || in[3] > 128 ||
-      in[3] % 32 != 0)
+      in[3] % 32 != 0 || (in[4] != 0 && in[4] != 1))
+    return false;
+  if (in[4] == 1 && (K == 3 || in[0] < 1 || in[1] < 1 || in[2] != 1 || in[3] != 0 ||
+                     !pair_eligible(3, g, in[0])))
     return false;
   std::lock_guard<std::mutex> lock(g_plan_mu);
   Plan pl;
@@ -823,11 +857,12 @@ bool ring_set_shape(int K, const Geo& g, const int in[4]) {
   pl.rKC = in[1];
   pl.rNP = in[2];
   pl.rBX = in[3];
+  pl.rK = in[4];
   g_plans[plan_key(K, g)] = pl;
   return true;
 }
 
-bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX) {
+bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX, int* KERN) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   auto it = g_plans.find(plan_key(K, g));
   if (it == g_plans.end()) return false;
@@ -835,6 +870,7 @@ bool ring_shape_of(int K, const Geo& g, int* TY, int* KC, int* NP, int* BX) {
   *KC = it->second.rKC;
   *NP = it->second.rNP;
   *BX = it->second.rBX;
+  if (KERN) *KERN = it->second.rK;
   return true;
 }
 

@@ -532,10 +532,13 @@ void smooth_v32(bfibm_ctx* c, int l, int n) {
         launch_rb_tma(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->counters + 3,
                       c->P.inv_re / (Lv.g.h * Lv.g.h), c->stream, c->tma_wait_ns);
       else {
-        int ty = 0, kc = 0, np = 1, bx = 0;
-        ring_shape_of(d, Lv.g, &ty, &kc, &np, &bx);
-        launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream, ty, kc,
-                                 np, bx);
+        int ty = 0, kc = 0, np = 1, bx = 0, kern = 0;
+        ring_shape_of(d, Lv.g, &ty, &kc, &np, &bx, &kern);
+        if (kern == 1)
+          launch_v_rb_pair(Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream, ty, kc);
+        else
+          launch_v_rb_fused<float>(c->D, Lv.g, Lv.f, d, Lv.f.u2[d], c->P.inv_re, c->stream, ty,
+                                   kc, np, bx);
       }
       std::swap(Lv.f.u[d], Lv.f.u2[d]);
     }
@@ -1827,27 +1830,28 @@ bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]) {
   return BFIBM_OK;
 }
 
-bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[4]) {
+bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[5]) {
   READY(c);
   if (!out || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
       (kind < 3 && kind >= c->D) || c->P.precision != 1)
     return set_err(c, BFIBM_EINVAL, "no FP32 sweep of this kind on this level");
-  int ty = 0, kc = 0, np = 1, bx = 0;
-  if (!ring_shape_of(kind, c->lev[level].g, &ty, &kc, &np, &bx))
+  int ty = 0, kc = 0, np = 1, bx = 0, kern = 0;
+  if (!ring_shape_of(kind, c->lev[level].g, &ty, &kc, &np, &bx, &kern))
     return set_err(c, BFIBM_EINVAL, "level not tuned");
   out[0] = ty;
   out[1] = kc;
   out[2] = np;
   out[3] = bx;
+  out[4] = kern;
   return BFIBM_OK;
 }
 
-bfibm_status bfibm_sweep_set_shape(bfibm_ctx* c, int level, int kind, const int32_t shape[4]) {
+bfibm_status bfibm_sweep_set_shape(bfibm_ctx* c, int level, int kind, const int32_t shape[5]) {
   READY(c);
   if (!shape || level < 0 || level >= c->L || kind < 0 || kind > 3 ||
       (kind < 3 && kind >= c->D) || c->P.precision != 1 || c->D != 3)
     return set_err(c, BFIBM_EINVAL, "no FP32 sweep of this kind on this level");
-  int v[4] = {shape[0], shape[1], shape[2], shape[3]};
+  int v[5] = {shape[0], shape[1], shape[2], shape[3], shape[4]};
   if (!ring_set_shape(kind, c->lev[level].g, v)) return set_err(c, BFIBM_EINVAL, "bad shape");
   CK(cudaStreamSynchronize(c->stream));
   drop_graph(c);

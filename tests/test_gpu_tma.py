@@ -103,7 +103,7 @@ def test_pinned_sweep_shape_gives_the_same_bits():
     a = sweep(c, f, 1, False, 2)
     for d in range(3):
         c.sweep_set_shape(0, d, (4, 8, 2, 32))
-        assert c.sweep_shape(0, d) == (4, 8, 2, 32)
+        assert c.sweep_shape(0, d) == (4, 8, 2, 32, 0)
     b = sweep(c, f, 1, False, 2)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
