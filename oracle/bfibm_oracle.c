@@ -84,6 +84,8 @@ typedef struct {
   double gamma_levels[8]; /* ... unless gamma_levels[l] > 0: gamma_lh of coarse level l */
   double div_tol;         /* > 0: relative-residual pressure solves also run until the
                              divergence the projection will leave is at most div_tol */
+  int32_t open_flow;      /* 1: the flow axis is the open duct of Sec. 3.6 (inflow at 0,
+                             outflow at n h) instead of periodic */
 } or_params;
 
 typedef struct {
@@ -114,7 +116,9 @@ typedef struct {
   double *uvel[3];        /* velocity state u^n */
   double *rho[3];         /* density on the d-faces */
   double *frc[3];         /* Eulerian force density on the d-faces */
-  double G;               /* body force actually used */
+  double G;               /* body force actually used (0 in an open duct) */
+  int open;               /* the open flow axis, or -1 */
+  double p_out;           /* open duct: the pressure held at the outflow */
   long eta;
   double *X, *U, *F;      /* eta x 3 */
   long nspring;
@@ -176,10 +180,11 @@ static void level_free(or_level* L) {
   }
 }
 
-/* Loop bounds of the unknown d-faces. */
+/* Loop bounds of the unknown d-faces. Along an open flow axis the inflow face
+   0 holds the prescribed velocity and the outflow face n is an unknown. */
 static void face_range(const or_sim* S, const or_level* L, int d, int lo[3], int hi[3]) {
   for (int a = 0; a < 3; ++a) { lo[a] = 0; hi[a] = (a < S->D) ? L->n[a] : 1; }
-  if (!S->P.periodic[d]) { lo[d] = 1; hi[d] = L->n[d]; }
+  if (!S->P.periodic[d]) { lo[d] = 1; hi[d] = L->n[d] + (d == S->open ? 1 : 0); }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -252,6 +257,15 @@ static double p_apply_point(const or_sim* S, const or_level* L, const double* p,
       double b = L->beta[a][LIc(L, fp)];
       flux_hi = b * (p[LIc(L, cp)] - p[ic]) / h;
       dg += b;
+    } else if (a == S->open) {
+      /* the outflow face: p held there (Sec. 3.6), ghost 2 p_out - p; the
+         operator is the homogeneous part (ghost -p), p_out goes to the
+         right-hand side */
+      int fp[3] = {c[0], c[1], c[2]};
+      fp[a] = c[a] + 1;
+      double b = L->beta[a][LIc(L, fp)];
+      flux_hi = b * (-p[ic] - p[ic]) / h;
+      dg += 2.0 * b;
     }
     if (per || c[a] > 0) {
       int cm[3] = {c[0], c[1], c[2]};
@@ -340,6 +354,8 @@ static double ud_at(const or_sim* S, const or_level* L, const double* ud, int d,
   (void)d;
   if (S->P.periodic[e]) { c[e] = wrapi(q, L->n[e]); return ud[LIc(L, c)]; }
   if (q < 0) { c[e] = 0; return -ud[LIc(L, c)]; }
+  /* beyond the outflow of an open axis du_d/dx_e = 0 (Sec. 3.6): even ghost */
+  if (q >= L->n[e] && e == S->open) { c[e] = L->n[e] - 1; return ud[LIc(L, c)]; }
   if (q >= L->n[e]) { c[e] = L->n[e] - 1; return -ud[LIc(L, c)]; }
   c[e] = q;
   return ud[LIc(L, c)];
@@ -358,6 +374,10 @@ static double v_apply_point(const or_sim* S, const or_level* L, double* const u[
   int Fp[3] = {F[0], F[1], F[2]}, Fm[3] = {F[0], F[1], F[2]};
   Fp[d] = perd ? wrapi(F[d] + 1, nd) : F[d] + 1;
   Fm[d] = perd ? wrapi(F[d] - 1, nd) : F[d] - 1;
+  /* the outflow face of an open axis: du_d/dx_d = 0 there, so the cell beyond
+     mirrors the last cell (viscosity and the face beyond it) */
+  const int outflow = d == S->open && F[d] == nd;
+  if (outflow) { Cp[d] = nd - 1; Fp[d] = nd - 1; }
   double mcp = L->muc[LIc(L, Cp)], mcm = L->muc[LIc(L, Cm)];
   double tau_p = 2.0 * mcp * (ud[LIc(L, Fp)] - ud[iF]) / h;
   double tau_m = 2.0 * mcm * (ud[iF] - ud[LIc(L, Fm)]) / h;
@@ -379,7 +399,7 @@ static double v_apply_point(const or_sim* S, const or_level* L, double* const u[
       {
         int a1[3] = {F[0], F[1], F[2]}, a0[3] = {F[0], F[1], F[2]};
         a1[e] = qq; a0[e] = qq;
-        a1[d] = F[d];
+        a1[d] = outflow ? nd - 1 : F[d];   /* beyond the outflow u_e mirrors (even) */
         a0[d] = perd ? wrapi(F[d] - 1, nd) : F[d] - 1;
         due_dd = (ue[LIc(L, a1)] - ue[LIc(L, a0)]) / h;
       }
@@ -387,7 +407,9 @@ static double v_apply_point(const or_sim* S, const or_level* L, double* const u[
       double me = mu[LIc(L, E)];
       tau[side] = me * (dud_de + due_dd);
       int wall = (!pere) && (q == 0 || q == ne);
-      dg += (wall ? 2.0 : 1.0) * me;
+      /* on the outflow plane the ghost is u_d itself: no diagonal weight */
+      double wgt = (e == S->open && q == ne) ? 0.0 : (wall ? 2.0 : 1.0);
+      dg += wgt * me;
     }
     V += (tau[1] - tau[0]) / h;
   }
@@ -517,6 +539,7 @@ static void restrict_face(const or_sim* S, const or_level* Lf, const or_level* L
             double along = 0.0;
             for (int o = -1; o <= 1; ++o) {
               int q = 2 * C[d] + o;
+              if (d == S->open && q > nf) q = nf - 1;   /* even ghost beyond the outflow */
               f[d] = per ? wrapi(q, nf) : q;
               double wgt = (o == 0) ? 0.5 : 0.25;
               along += wgt * fine[LIc(Lf, f)];
@@ -529,14 +552,19 @@ static void restrict_face(const or_sim* S, const or_level* Lf, const or_level* L
 
 /* 1D prolongation stencil for a cell-centred axis: fine index i -> two coarse
    indices and weights; returns the number of coarse points (1 or 2). The
-   mirror sign (+1 for pressure, -1 for velocity) applies beyond a wall. */
-static int prol_cell_1d(int i, int nc, int per, double mirror, int idx[2], double w[2]) {
+   mirror signs (+1 even, -1 odd) apply beyond the lower and the upper end:
+   at a wall +1 for the pressure and -1 for tangential velocity; at the
+   outflow of an open axis -1 for the pressure (held there) and +1 for
+   tangential velocity (du/dn = 0). */
+static int prol_cell_1d(int i, int nc, int per, double mirror_lo, double mirror_hi, int idx[2],
+                        double w[2]) {
   int I = i >> 1;
   int o = (i & 1) ? 1 : -1;
   int J = I + o;
   idx[0] = I; w[0] = 0.75;
   if (per) { idx[1] = wrapi(J, nc); w[1] = 0.25; return 2; }
-  if (J < 0 || J >= nc) { w[0] = 0.75 + 0.25 * mirror; return 1; }
+  if (J < 0) { w[0] = 0.75 + 0.25 * mirror_lo; return 1; }
+  if (J >= nc) { w[0] = 0.75 + 0.25 * mirror_hi; return 1; }
   idx[1] = J; w[1] = 0.25;
   return 2;
 }
@@ -560,7 +588,8 @@ static void prolong_add_cell(const or_sim* S, const or_level* Lf, const or_level
         int idx[3][2]; double w[3][2]; int cnt[3] = {1, 1, 1};
         idx[2][0] = 0; w[2][0] = 1.0;
         for (int a = 0; a < S->D; ++a)
-          cnt[a] = prol_cell_1d(fi[a], Lc->n[a], S->P.periodic[a], 1.0, idx[a], w[a]);
+          cnt[a] = prol_cell_1d(fi[a], Lc->n[a], S->P.periodic[a], 1.0,
+                                a == S->open ? -1.0 : 1.0, idx[a], w[a]);
         double v = 0.0;
         for (int c = 0; c < cnt[2]; ++c)
           for (int b = 0; b < cnt[1]; ++b)
@@ -583,7 +612,8 @@ static void prolong_add_face(const or_sim* S, const or_level* Lf, const or_level
         idx[2][0] = 0; w[2][0] = 1.0;
         for (int a = 0; a < S->D; ++a) {
           if (a == d) cnt[a] = prol_face_1d(fi[a], Lc->n[a], S->P.periodic[a], idx[a], w[a]);
-          else cnt[a] = prol_cell_1d(fi[a], Lc->n[a], S->P.periodic[a], -1.0, idx[a], w[a]);
+          else cnt[a] = prol_cell_1d(fi[a], Lc->n[a], S->P.periodic[a], -1.0,
+                                     a == S->open ? 1.0 : -1.0, idx[a], w[a]);
         }
         double v = 0.0;
         for (int c = 0; c < cnt[2]; ++c)
@@ -705,9 +735,15 @@ static void vcycle_p(or_sim* S, int l) {
   or_level* L = &S->lev[l];
   if (l == S->L - 1) {
     /* coarsest grid: the singular Neumann/periodic problem needs a
-       zero-mean right-hand side; then a fixed number of sweeps */
-    cell_sub(S, L, L->pf, cell_mean(S, L, L->pf));
-    for (int it = 0; it < S->P.coarse_sweeps; ++it) p_rbgs(S, l);
+       zero-mean right-hand side (an open duct's outflow pressure makes it
+       regular); then a fixed number of sweeps */
+    if (S->open < 0) cell_sub(S, L, L->pf, cell_mean(S, L, L->pf));
+    /* with the outflow pressure held the slowest coarse mode is no longer the
+       constant the mean removes: at least 2 n^2 sweeps along the open axis */
+    int sweeps = S->P.coarse_sweeps;
+    if (S->open >= 0 && sweeps < 2 * L->n[S->open] * L->n[S->open])
+      sweeps = 2 * L->n[S->open] * L->n[S->open];
+    for (int it = 0; it < sweeps; ++it) p_rbgs(S, l);
     return;
   }
   for (int it = 0; it < S->P.nu1; ++it) p_rbgs(S, l);
@@ -784,7 +820,7 @@ static int solve_p(or_sim* S, int ncycles) {
   double dscale = S->P.euler * S->P.dt / S->P.sigma;
   for (cyc = 1; cyc <= maxc; ++cyc) {
     vcycle_p(S, 0);
-    cell_sub(S, L, L->p, cell_mean(S, L, L->p));
+    if (S->open < 0) cell_sub(S, L, L->p, cell_mean(S, L, L->p));
     if (ncycles <= 0) {
       p_residual(S, 0);
       rel = fn > 0.0 ? sqrt(norm2_cells(S, L, L->pr)) / fn : 0.0;
@@ -860,7 +896,7 @@ static double ue_avg_at_face(const or_sim* S, const or_level* L, const double* u
   if (S->P.periodic[e]) q = wrapi(q, ne);
   int a1[3] = {F[0], F[1], F[2]}, a0[3] = {F[0], F[1], F[2]};
   a1[e] = q; a0[e] = q;
-  a1[d] = F[d];
+  a1[d] = (d == S->open && F[d] == nd) ? nd - 1 : F[d];   /* even ghost beyond the outflow */
   a0[d] = S->P.periodic[d] ? wrapi(F[d] - 1, nd) : F[d] - 1;
   return 0.5 * (ue[LIc(L, a0)] + ue[LIc(L, a1)]);
 }
@@ -871,12 +907,13 @@ static double advection_point(const or_sim* S, const or_level* L, double* const 
   const double* ud = u[d];
   int nd = L->n[d], perd = S->P.periodic[d];
   double udF = ud[LIc(L, F)];
+  const int outflow = d == S->open && F[d] == nd;   /* beyond it: even ghost */
   double adv = 0.0, cons = 0.0;
   for (int e = 0; e < S->D; ++e) {
     double up, um, Uhi, Ulo;   /* u_d one step up/down along e; U_e at the flux points */
     if (e == d) {
       int Fp[3] = {F[0], F[1], F[2]}, Fm[3] = {F[0], F[1], F[2]};
-      Fp[d] = perd ? wrapi(F[d] + 1, nd) : F[d] + 1;
+      Fp[d] = perd ? wrapi(F[d] + 1, nd) : (outflow ? nd - 1 : F[d] + 1);
       Fm[d] = perd ? wrapi(F[d] - 1, nd) : F[d] - 1;
       up = ud[LIc(L, Fp)];
       um = ud[LIc(L, Fm)];
@@ -953,7 +990,22 @@ static void divergence_rhs(or_sim* S) {
         int c[3] = {i, j, k};
         L->pf[LIc(L, c)] = sc * div_cell(S, L, L->u, c);
       }
-  cell_sub(S, L, L->pf, cell_mean(S, L, L->pf));
+  if (S->open < 0) {
+    cell_sub(S, L, L->pf, cell_mean(S, L, L->pf));
+  } else {
+    /* the pressure held at the outflow: D.(beta D p) = b becomes
+       A p = b - 2 beta p_out / h^2 in the last cells (A: ghost -p) */
+    int o = S->open;
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < L->n[1]; ++j)
+        for (int i = 0; i < L->n[0]; ++i) {
+          int c[3] = {i, j, k};
+          if (c[o] != L->n[o] - 1) continue;
+          int f[3] = {i, j, k};
+          f[o] = L->n[o];
+          L->pf[LIc(L, c)] -= 2.0 * L->beta[o][LIc(L, f)] * S->p_out / (L->h * L->h);
+        }
+  }
 }
 
 static double max_div(const or_sim* S, double* const u[3]) {
@@ -976,7 +1028,9 @@ static void project(or_sim* S) {
   for (int d = 0; d < S->D; ++d) {
     int lo[3], hi[3];
     face_range(S, L, d, lo, hi);
-    for (long x = 0; x < L->size; ++x) S->uvel[d][x] = 0.0;
+    /* faces that are not unknowns keep the iterate's value: 0 on walls,
+       the prescribed inflow on an open axis */
+    for (long x = 0; x < L->size; ++x) S->uvel[d][x] = L->u[d][x];
     for (int k = lo[2]; k < hi[2]; ++k)
       for (int j = lo[1]; j < hi[1]; ++j)
         for (int i = lo[0]; i < hi[0]; ++i) {
@@ -984,7 +1038,10 @@ static void project(or_sim* S) {
           int Cm[3] = {i, j, k};
           Cm[d] = S->P.periodic[d] ? wrapi(F[d] - 1, L->n[d]) : F[d] - 1;
           long iF = LIc(L, F);
-          double gp = (L->p[iF] - L->p[LIc(L, Cm)]) / L->h;
+          /* at the outflow the cell beyond holds the ghost 2 p_out - p */
+          double pF = (d == S->open && F[d] == L->n[d]) ? 2.0 * S->p_out - L->p[LIc(L, Cm)]
+                                                        : L->p[iF];
+          double gp = (pF - L->p[LIc(L, Cm)]) / L->h;
           S->uvel[d][iF] = L->u[d][iF] - sc * L->beta[d][iF] * gp;
         }
   }
@@ -1277,6 +1334,7 @@ void* or_create(const or_params* P) {
   }
   long sz = S->lev[0].size;
   for (int a = 0; a < 3; ++a) { S->uvel[a] = dalloc(sz); S->rho[a] = dalloc(sz); S->frc[a] = dalloc(sz); }
+  S->open = (P->open_flow && !S->P.periodic[P->flow_axis]) ? P->flow_axis : -1;
   compute_G(S);
   /* laminar initial velocity along the flow axis, evaluated at the faces; the
      profile depends only on the wall-axis coordinates, so it is summed once
@@ -1301,6 +1359,27 @@ void* or_create(const or_params* P) {
           int a = c[ta[0]], b = (S->D == 3) ? c[ta[1]] : 0;
           S->uvel[fa][LIc(L, c)] = col[(long)b * n0 + a];
         }
+    if (S->open >= 0) {
+      /* Sec. 3.6: the inflow face holds the laminar profile itself, and the
+         pressure falls linearly along the duct, Eq. (pressLam): p(0) = 0,
+         eps kappa = -G (the pressure gradient that drives the same flow as
+         the body force G), so p_out = kappa L; no body force acts */
+      lo[fa] = 0;
+      hi[fa] = 1;
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+          for (int i = lo[0]; i < hi[0]; ++i) {
+            int c[3] = {i, j, k};
+            int a = c[ta[0]], b = (S->D == 3) ? c[ta[1]] : 0;
+            double v = P->ic_scale != 0.0 ? col[(long)b * n0 + a] / P->ic_scale
+                                           : S->G / (P->inv_re * P->mu_f) *
+                                                 laminar_unit(S, (double[2]){(a + 0.5) * L->h,
+                                                                            (b + 0.5) * L->h});
+            S->uvel[fa][LIc(L, c)] = v;
+          }
+      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);
+      S->G = 0.0;
+    }
     free(col);
   }
   /* uniform fluid until nodes arrive */
@@ -1325,6 +1404,7 @@ void or_destroy(void* sim) {
 
 int or_levels(void* sim) { return ((or_sim*)sim)->L; }
 double or_body_force(void* sim) { return ((or_sim*)sim)->G; }
+double or_outflow_pressure(void* sim) { return ((or_sim*)sim)->p_out; }
 void or_level_dims(void* sim, int l, int32_t* n, int32_t* s) {
   or_sim* S = (or_sim*)sim;
   for (int a = 0; a < 3; ++a) { n[a] = S->lev[l].n[a]; s[a] = S->lev[l].s[a]; }

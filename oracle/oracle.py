@@ -33,7 +33,8 @@ class OrParams(C.Structure):
                 ("sigma", C.c_double), ("euler", C.c_double), ("inv_re", C.c_double),
                 ("c_force", C.c_double), ("body_force", C.c_double), ("u_center", C.c_double),
                 ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double),
-                ("gamma_levels", C.c_double * 8), ("div_tol", C.c_double)]
+                ("gamma_levels", C.c_double * 8), ("div_tol", C.c_double),
+                ("open_flow", C.c_int32)]
 
 
 class OrStats(C.Structure):
@@ -56,6 +57,7 @@ def _lib(omp=False):
     sig = {
         "or_create": (p, [C.POINTER(OrParams)]), "or_destroy": (v, [p]),
         "or_phi": (d, [i, d]), "or_levels": (i, [p]), "or_body_force": (d, [p]),
+        "or_outflow_pressure": (d, [p]),
         "or_level_dims": (v, [p, i, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "or_level_size": (l, [p, i]),
         "or_set_nodes": (v, [p, l, _DP]),
@@ -116,6 +118,7 @@ def make_params(prm):
     for l, v in enumerate(prm.get("gamma_levels", [])[:8]):
         P.gamma_levels[l] = float(v)
     P.div_tol = float(prm.get("div_tol", 0.0))
+    P.open_flow = int(prm.get("open_flow", 0))
     return P
 
 
@@ -161,6 +164,10 @@ class Oracle:
     @property
     def body_force(self):
         return self.lib.or_body_force(self.h)
+
+    def outflow_pressure(self):
+        """The pressure held at the outflow of an open duct (0 otherwise)."""
+        return self.lib.or_outflow_pressure(self.h)
 
     # -- state ------------------------------------------------------------
     def set_nodes(self, X):

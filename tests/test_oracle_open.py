@@ -1,0 +1,262 @@
+"""Pins for the open duct of Sec. 3.6 in the oracle.
+
+The reading: the inflow face holds the laminar velocity; the outflow face is
+an unknown with du/dn = 0 and the pressure held there at p_out = kappa L,
+where eps kappa = -G is the laminar pressure gradient, Eq. (pressLam). The
+pressure carries no flux through the inflow or the walls. The paper's
+Dirichlet values upstream and on the top wall are the values this solution
+takes.
+
+* Mass balance: the flux through the outflow equals the flux through the
+  inflow, to rounding.
+* The projection identity max |D.u| = (eps dt / sigma) max |r_p| still holds.
+* The pressure operator with the outflow pressure held: a manufactured
+  solution converges at O(h^2).
+* The viscous operator with the Neumann outflow and a prescribed inflow: a
+  manufactured solution converges at O(h^2).
+* Converged multigrid equals a dense solve, on tiny grids in 2D and 3D, for
+  both operators; the pressure V(2,2) cycle contracts by at most 0.1 per
+  cycle, independently of h.
+* A biofilm-free duct started from the laminar profile develops towards it
+  at the outflow as h falls. This scheme does not keep the laminar state to
+  rounding: its pressure correction is not incremental, so a uniform
+  gradient leaves the term (eps dt / sigma) beta Re^-1 V_mu(grad p) next to
+  the walls, an O(dt) boundary error.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1302_3663_gb300 import workloads as W
+
+from test_oracle_operators import cell_mask, face_mask, mesh, set_coefficients
+
+
+def chan(n, **kw):
+    h = 1.0 / n
+    prm = W.base_params(2, (2 * n, n // 2), (0, 0), 0, h, open_flow=1, **kw)
+    return O.Oracle(prm)
+
+
+def duct(n, **kw):
+    h = 1.0 / n
+    prm = W.base_params(3, (n, n, 2 * n), (0, 0, 0), 2, h, open_flow=1, **kw)
+    return O.Oracle(prm)
+
+
+def no_nodes(o):
+    o.set_nodes(np.zeros((0, o.dim)))
+    o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+
+
+def open_face_mask(o, d, level=0):
+    """Unknown faces of component d, the outflow face included."""
+    m = face_mask(o, d, level)
+    fa = o.prm["flow_axis"]
+    if d == fa:
+        n, _ = o.dims(level)
+        m[tuple(slice(0, n[a]) if a != fa else n[fa] for a in reversed(range(o.dim)))] = True
+    return m
+
+
+@pytest.mark.parametrize("case", ["chan", "duct_mound"])
+def test_mass_balance_and_projection_identity(case):
+    # the flux out minus the flux in is the sum of D.u over the cells, so the
+    # balance holds to the solver tolerance: solve to 1e-12
+    tol = dict(vc_visc=0, vc_p=0, rtol=1e-12, max_cycles=200)
+    if case == "chan":
+        o = chan(32, **tol)
+        no_nodes(o)
+    else:
+        inst = W.c2()
+        n = 16
+        prm = W.base_params(3, (n, n, 2 * n), (0, 0, 0), 2, 1.0 / n, open_flow=1,
+                            rho_ratio=1.5, mu_ratio=100.0, omega=0.05, omega_mu=0.05,
+                            d0_vol=inst["params"]["d0_vol"], **tol)
+        o = O.Oracle(prm)
+        o.set_nodes(inst["X"][::10])   # the mound sits in z in [0.35, 0.65] of [0, 2]
+        o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+    fa = o.prm["flow_axis"]
+    h = o.prm["h"]
+    for _ in range(3):
+        o.step(1)
+    u = o.get("u", fa)
+    n, _ = o.dims()
+    cross = [slice(0, n[a]) for a in reversed(range(o.dim)) if a != fa]
+
+    def plane(idx):
+        sl = [slice(0, n[a]) if a != fa else idx for a in reversed(range(o.dim))]
+        return u[tuple(sl)]
+
+    fin, fout = plane(0).sum(), plane(n[fa]).sum()
+    assert abs(fout - fin) <= 1e-10 * abs(fin), (fin, fout)
+    # projection identity after a deliberately loose pressure solve
+    o.stage("rhs")
+    o.solve_visc(2)
+    o.stage("divergence")
+    o.solve_p(1)
+    rp = o.residual_p()[cell_mask(o)]
+    o.stage("project")
+    pred = o.prm["euler"] * o.prm["dt"] / o.prm["sigma"] * np.abs(rp).max()
+    st = o.stats()
+    assert st["div_max"] > 1e-8
+    assert abs(st["div_max"] - pred) <= 1e-9 * pred
+
+
+def test_pressure_mms_with_outflow_pressure_held():
+    # p* = p_out + cos(pi x / (2 L)) cos(pi y / H): dp/dx = 0 at the inflow,
+    # p = p_out at the outflow, dp/dy = 0 on the walls; smooth beta
+    L, H, pout = 2.0, 0.5, -0.7
+    errs = []
+    for n in (16, 32, 64, 128):
+        o = chan(n, rtol=1e-13, max_cycles=200)
+        h = o.prm["h"]
+        beta = lambda x, y: 1.0 + 0.5 * np.sin(np.pi * x / L) * np.cos(np.pi * y / H)
+        set_coefficients(o, rho_fn=lambda x, y: 1.0 / beta(x, y))
+        X, Y = mesh(o, [1, 1])
+        ps = pout + np.cos(np.pi * X / (2 * L)) * np.cos(np.pi * Y / H)
+        # f = div(beta grad p*), analytic
+        px = -np.pi / (2 * L) * np.sin(np.pi * X / (2 * L)) * np.cos(np.pi * Y / H)
+        py = -np.pi / H * np.cos(np.pi * X / (2 * L)) * np.sin(np.pi * Y / H)
+        pxx = -(np.pi / (2 * L)) ** 2 * np.cos(np.pi * X / (2 * L)) * np.cos(np.pi * Y / H)
+        pyy = -(np.pi / H) ** 2 * np.cos(np.pi * X / (2 * L)) * np.cos(np.pi * Y / H)
+        bx = 0.5 * np.pi / L * np.cos(np.pi * X / L) * np.cos(np.pi * Y / H)
+        by = -0.5 * np.pi / H * np.sin(np.pi * X / L) * np.sin(np.pi * Y / H)
+        f = beta(X, Y) * (pxx + pyy) + bx * px + by * py
+        # the held outflow value enters the right-hand side of the last cells
+        cm = cell_mask(o)
+        n0, n1 = 2 * n, n // 2
+        bo = o.get("beta", 0)[:n1, n0]
+        f[:n1, n0 - 1] -= 2.0 * bo * pout / (h * h)
+        o.set("prhs", np.where(cm, f, 0.0))
+        o.set("p", np.zeros(o.shape()))
+        o.solve_p(0)
+        errs.append(np.abs(o.get("p") - ps)[cm].max())
+    r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(r > 1.85), (errs, r)
+
+
+def test_viscous_mms_with_neumann_outflow():
+    sp = pytest.importorskip("sympy")
+    x, y = sp.symbols("x y")
+    L, H = 2, sp.Rational(1, 2)
+    # no slip on the walls; du/dx = 0 at the outflow x = L; the inflow face
+    # holds u*, which is tangentially 0 there
+    u = [sp.sin(sp.pi * y / H) * (1 + sp.Rational(3, 10) * sp.cos(sp.pi * x / L)),
+         sp.Rational(1, 5) * sp.sin(2 * sp.pi * y / H) * (1 - sp.cos(sp.pi * x / L))]
+    mu = sp.Rational(1, 20) * (1 + sp.Rational(1, 2) * sp.cos(sp.pi * x / L) * sp.cos(sp.pi * y / H))
+    m0 = 10.0
+    Xs = [x, y]
+    f = [m0 * u[d] - sum(sp.diff(mu * (sp.diff(u[d], Xs[e]) + sp.diff(u[e], Xs[d])), Xs[e])
+                         for e in range(2)) for d in range(2)]
+    lam = lambda ex: sp.lambdify((x, y), ex, "numpy")
+    us, fs, mus = [lam(c) for c in u], [lam(c) for c in f], lam(mu)
+    errs = []
+    for n in (16, 32, 64, 128):
+        o = chan(n, rtol=1e-12, max_cycles=200, dt=1.0)
+        set_coefficients(o, rho_fn=lambda *X: m0 + 0 * X[0], mu_fn=lambda *X: mus(*X) + 0 * X[0])
+        for d in range(2):
+            stag = [1, 1]
+            stag[d] = 0
+            P = mesh(o, stag)
+            um = open_face_mask(o, d)
+            o.set("urhs", np.where(um, fs[d](*P) + 0 * P[0], 0.0), d)
+            # the iterate starts at 0 except on the inflow face, which holds u*
+            start = np.zeros(o.shape())
+            if d == 0:
+                start[:, 0] = (us[0](*P) + 0 * P[0])[:, 0]
+            o.set("ut", start, d)
+        o.solve_visc(0)
+        e = 0.0
+        for d in range(2):
+            stag = [1, 1]
+            stag[d] = 0
+            P = mesh(o, stag)
+            um = open_face_mask(o, d)
+            e = max(e, np.abs(o.get("ut", d)[um] - (us[d](*P) + 0 * P[0])[um]).max())
+        errs.append(e)
+    r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(r > 1.85), (errs, r)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_open_mg_equals_dense_solve_tiny(dim):
+    o = chan(8, rtol=1e-14, max_cycles=300) if dim == 2 else duct(4, rtol=1e-14, max_cycles=300)
+    rng = np.random.default_rng(4)
+    set_coefficients(o, rho_fn=lambda *X: 1.0 + rng.uniform(0, 1, size=X[0].shape),
+                     mu_fn=lambda *X: 0.01 * np.exp(rng.uniform(0, np.log(100), size=X[0].shape)))
+    # pressure: regular now (the outflow pressure is held)
+    cm = cell_mask(o)
+    idx = np.flatnonzero(cm.ravel())
+    A = np.zeros((idx.size, idx.size))
+    for c, i in enumerate(idx):
+        e = np.zeros(o.shape())
+        e.ravel()[i] = 1.0
+        A[:, c] = o.apply_p(e).ravel()[idx]
+    assert np.linalg.matrix_rank(A) == idx.size
+    b = rng.normal(size=idx.size)
+    bb = np.zeros(o.shape())
+    bb.ravel()[idx] = b
+    o.set("prhs", bb)
+    o.set("p", np.zeros(o.shape()))
+    o.solve_p(0)
+    xs = np.linalg.solve(A, b)
+    assert np.abs(o.get("p").ravel()[idx] - xs).max() < 1e-11 * np.abs(xs).max()
+    # viscous: the outflow faces are unknowns
+    fidx = [np.flatnonzero(open_face_mask(o, d).ravel()) for d in range(o.dim)]
+    cols = []
+    for d in range(o.dim):
+        for i in fidx[d]:
+            e = [np.zeros(o.shape()) for _ in range(o.dim)]
+            e[d].ravel()[i] = 1.0
+            Ae = o.apply_visc(e)
+            cols.append(np.concatenate([Ae[q].ravel()[fidx[q]] for q in range(o.dim)]))
+    M = np.array(cols).T
+    rhs = rng.normal(size=M.shape[0])
+    off = 0
+    for d in range(o.dim):
+        a = np.zeros(o.shape())
+        a.ravel()[fidx[d]] = rhs[off:off + fidx[d].size]
+        off += fidx[d].size
+        o.set("urhs", a, d)
+        o.set("ut", np.zeros(o.shape()), d)
+    o.solve_visc(0)
+    sol = np.linalg.solve(M, rhs)
+    got = np.concatenate([o.get("ut", d).ravel()[fidx[d]] for d in range(o.dim)])
+    assert np.abs(got - sol).max() < 1e-11 * np.abs(sol).max()
+
+
+def test_open_channel_develops_towards_the_laminar_profile():
+    errs = []
+    for n in (16, 32, 64):
+        o = chan(n, vc_visc=0, vc_p=0, rtol=1e-12, max_cycles=200)
+        no_nodes(o)
+        lam = o.get("u", 0)[: n // 2, 0].copy()
+        o.step(60)
+        errs.append(np.abs(o.get("u", 0)[: n // 2, 2 * n] - lam).max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 2e-3, errs
+
+
+def _p_factors(o, ncyc=8):
+    rng = np.random.default_rng(2)
+    cm = cell_mask(o)
+    o.set("prhs", np.where(cm, rng.normal(size=o.shape()), 0.0))
+    o.set("p", np.zeros(o.shape()))
+    norms = [np.linalg.norm(o.residual_p()[cm])]
+    for _ in range(ncyc):
+        o.vcycle_p()
+        norms.append(np.linalg.norm(o.residual_p()[cm]))
+    return np.array(norms[1:]) / np.array(norms[:-1])
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_open_pressure_vcycle_contraction(n):
+    # the correction's odd mirror at the held outflow pressure and the even
+    # one at the inflow and the walls keep the V(2,2) cycle contracting by
+    # 0.07-0.08 independently of h (an even mirror at the outflow drifts
+    # above 0.1 at n = 128); the coarsest solve takes 2 n^2 sweeps along the
+    # open axis (16 left it at 0.63)
+    o = chan(n)
+    set_coefficients(o)
+    f = _p_factors(o)
+    assert f[2:].max() <= 0.1, f
