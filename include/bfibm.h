@@ -88,6 +88,14 @@ typedef struct {
   double div_tol;         /* > 0: every projection (Eq. NSdis2) checks max |D.u| in FP64
                              on the device against it (Eq. NSdis4 makes D.u vanish) and
                              counts a violation; 0: the maximum is still recorded */
+  int32_t open_flow;      /* 1: the flow axis is the open duct of Sec. 3.6 instead of
+                             periodic (periodic[flow_axis] = 0, precision 0, u_center > 0,
+                             walls on the cross axes): face 0 holds the laminar profile
+                             (Eq. 2DlaminarSoln / 3DlaminarFlow), the outflow face n is an
+                             unknown with du/dn = 0 and the pressure held there at
+                             kappa L (Eq. pressLam, euler kappa = -G of the same laminar
+                             flow); no body force, no pressure flux through the inflow or
+                             the walls */
 } bfibm_params;
 
 typedef struct {
@@ -352,7 +360,8 @@ bfibm_status bfibm_launch_counts(bfibm_ctx* c, int64_t out[5]);
    u0, u1, u2: device pointers to the velocity components in the dense field
    layout above (u2 ignored when dim == 2); b: device pointer, same layout,
    only the cell entries are written. p supplies dim, n, periodic, h, dt,
-   sigma and euler. stream: the stream to queue on (NULL = legacy default).
+   sigma and euler (periodic or walled axes only: an open duct is refused
+   with BFIBM_EINVAL). stream: the stream to queue on (NULL = legacy default).
    Returns once the kernels are queued.
    Scratch: a fixed device array in the library (512 KB per GPU, held until
    the process exits); grids of more than 2^24 cells are rejected with

@@ -42,7 +42,8 @@ class bfibm_params(C.Structure):
                 ("sigma", C.c_double), ("euler", C.c_double), ("inv_re", C.c_double),
                 ("c_force", C.c_double), ("body_force", C.c_double), ("u_center", C.c_double),
                 ("ic_scale", C.c_double), ("rtol", C.c_double), ("gamma_coarse", C.c_double),
-                ("gamma_levels", C.c_double * 8), ("div_tol", C.c_double)]
+                ("gamma_levels", C.c_double * 8), ("div_tol", C.c_double),
+                ("open_flow", C.c_int32)]
 
 
 class bfibm_stats(C.Structure):
@@ -158,6 +159,7 @@ def make_params(prm):
     for l, v in enumerate(prm.get("gamma_levels", [])[:8]):
         P.gamma_levels[l] = float(v)
     P.div_tol = float(prm.get("div_tol", 0.0))
+    P.open_flow = int(prm.get("open_flow", 0))
     return P
 
 

@@ -22,6 +22,9 @@ struct Geo {
   int per[3];
   long long st[3];   // strides in elements: 1, pitch, pitch * s[1]
   double h;
+  int open;          // the open flow axis of a duct with inflow and outflow (Sec. 3.6), or -1:
+                     // face 0 along it holds the prescribed inflow, face n is the outflow (an
+                     // unknown with du/dn = 0 and the pressure held there)
 };
 
 __host__ __device__ inline long long gidx(const Geo& g, int i, int j, int k) {
@@ -207,8 +210,11 @@ void launch_coef_restrict(int D, const Geo& gf, const Geo& gc, const LevelPtrs<d
 void launch_adv_rhs(int D, const Geo& g, double* const uvel[3], double* const rho[3],
                     double* const frc[3], const LevelPtrs<double>& L0, double c_force,
                     int flow_axis, const double* G_dev, cudaStream_t s);
+// (an open duct keeps the mean and moves the held outflow pressure p_out into
+// the last cells: b -= 2 beta_out p_out / h^2)
 void launch_divergence(int D, const Geo& g, double* const u[3], double* b, double scale,
-                       Scalars sc, cudaStream_t s);
+                       Scalars sc, cudaStream_t s, const double* beta_open = nullptr,
+                       double p_out = 0.0);
 // The divergence check fused into the projection: out[acc] accumulates the
 // max |D.u| of the projected velocity (bit pattern of a double); a small
 // kernel then copies it to out[step], folds it into out[all] (max over all
@@ -219,6 +225,7 @@ struct DivCheck {
   int acc, step, all;
   double tol;
   int* viol;
+  double p_out;   // open duct: the pressure held at the outflow
 };
 void launch_project(int D, const Geo& g, double* const ut[3], const double* p,
                     double* const beta[3], double* uvel[3], double coef, const DivCheck& dc,

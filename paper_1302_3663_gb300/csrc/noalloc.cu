@@ -134,6 +134,7 @@ extern "C" bfibm_status bfibm_divergence_noalloc(const bfibm_params* p, const do
     return BFIBM_EINVAL;
   if (!(p->h > 0.0) || !(p->dt > 0.0) || !(p->sigma > 0.0) || !(p->euler > 0.0))
     return BFIBM_EINVAL;
+  if (p->open_flow) return BFIBM_EINVAL;   // the open duct's divergence keeps its mean
   int D = p->dim;
   DenseGeo g;
   for (int a = 0; a < 3; ++a) {

@@ -31,8 +31,9 @@ int edge_count(int D) { return D == 3 ? 3 : 1; }
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
-Geo make_geo(const int n[3], const int per[3], int D, double h) {
+Geo make_geo(const int n[3], const int per[3], int D, double h, int open) {
   Geo g;
+  g.open = open;
   for (int a = 0; a < 3; ++a) {
     g.n[a] = n[a];
     g.per[a] = per[a];
@@ -65,8 +66,9 @@ int build_levels(const bfibm_params& P, Geo out[kMaxLevels]) {
   int per[3] = {P.periodic[0], P.periodic[1], D == 3 ? P.periodic[2] : 1};
   int L = 0;
   double h = P.h;
+  const int open = P.open_flow ? P.flow_axis : -1;
   for (;;) {
-    out[L] = make_geo(n, per, D, h);
+    out[L] = make_geo(n, per, D, h, open);
     ++L;
     if (L >= P.mg_levels_max || L >= kMaxLevels) break;
     bool ok = true;
@@ -111,7 +113,9 @@ const char* validate(const bfibm_params* p) {
   }
   if (p->dim == 2 && p->n[2] != 1) return "n[2] must be 1 when dim == 2";
   if (p->flow_axis < 0 || p->flow_axis >= p->dim) return "flow_axis out of range";
-  if (!p->periodic[p->flow_axis]) return "the flow axis must be periodic";
+  if (!p->periodic[p->flow_axis] && !p->open_flow)
+    return "the flow axis must be periodic (or open, with open_flow = 1)";
+  if (p->periodic[p->flow_axis] && p->open_flow) return "an open flow axis is not periodic";
   for (int a = 0; a < p->dim; ++a)
     if (a != p->flow_axis && p->periodic[a]) {
       // laminar profile is defined between walls; periodic cross axes are allowed
@@ -135,6 +139,14 @@ const char* validate(const bfibm_params* p) {
     if (!(p->gamma_levels[l] >= 0.0) || !std::isfinite(p->gamma_levels[l]))
       return "gamma_levels entries must be >= 0";
   if (!(p->div_tol >= 0.0) || !std::isfinite(p->div_tol)) return "div_tol must be >= 0";
+  if (p->open_flow != 0 && p->open_flow != 1) return "open_flow must be 0 or 1";
+  if (p->open_flow) {
+    if (p->precision != 0) return "the open duct runs in FP64 (precision 0)";
+    if (!(p->u_center > 0.0)) return "the open duct needs u_center > 0 (the laminar inflow)";
+    for (int a = 0; a < p->dim; ++a)
+      if (a != p->flow_axis && p->periodic[a]) return "the open duct needs walls on the cross axes";
+    if (p->n[p->flow_axis] % 2) return "the open flow axis needs an even cell count";
+  }
   return nullptr;
 }
 
@@ -154,6 +166,7 @@ struct bfibm_ctx {
   double* rho[3] = {nullptr, nullptr, nullptr};
   double* frc[3] = {nullptr, nullptr, nullptr};
   double* G_dev = nullptr;
+  double p_out = 0.0;             // open duct: the pressure held at the outflow
   Scalars sc{};
   double* host_sc = nullptr;  // pinned mirror of sc.out
   char* pool = nullptr;
@@ -406,7 +419,7 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
   if (!tol) {
     for (int k = 0; k < ncycles; ++k) {
       vcycle_p(c, 0);
-      launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
+      if (L0.g.open < 0) launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
     }
     if (c->collect_stats) {
       launch_p_residual<double>(c->D, L0.g, L0.d, s);
@@ -420,7 +433,7 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
     c->loop_inner[1] = 1;
     bfibm_status cs = capture_while(c, 1, [&](cudaGraphConditionalHandle h) {
       vcycle_p(c, 0);
-      launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, c->stream);
+      if (L0.g.open < 0) launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, c->stream);
       launch_p_residual<double>(c->D, L0.g, L0.d, c->stream);
       launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, c->stream);
       if (c->P.div_tol > 0.0) launch_absmax_cells(c->D, L0.g, L0.d.pr, c->sc, SL_PRMAX, c->stream);
@@ -435,7 +448,7 @@ bfibm_status solve_p(bfibm_ctx* c, int ncycles, int* used) {
   int k = 0;
   for (k = 1; k <= c->P.max_cycles; ++k) {
     vcycle_p(c, 0);
-    launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
+    if (L0.g.open < 0) launch_sub_mean(c->D, L0.g, L0.d.p, c->sc, s);
     launch_p_residual<double>(c->D, L0.g, L0.d, s);
     launch_norm2(c->D, L0.g, res, 0, c->sc, SL_PR, s);
     if (c->P.div_tol > 0.0) launch_absmax_cells(c->D, L0.g, L0.d.pr, c->sc, SL_PRMAX, s);
@@ -818,11 +831,14 @@ void stage_rhs(bfibm_ctx* c) {
 }
 void stage_divergence(bfibm_ctx* c) {
   double scale = c->P.sigma / c->P.euler / c->P.dt;
-  launch_divergence(c->D, c->lev[0].g, c->lev[0].d.u, c->lev[0].d.pf, scale, c->sc, c->stream);
+  const int o = c->lev[0].g.open;
+  launch_divergence(c->D, c->lev[0].g, c->lev[0].d.u, c->lev[0].d.pf, scale, c->sc, c->stream,
+                    o >= 0 ? c->lev[0].d.beta[o] : nullptr, c->p_out);
 }
 void stage_project(bfibm_ctx* c) {
   double coef = c->P.euler * c->P.dt / c->P.sigma;
-  DivCheck dc{c->sc.out, SL_DIVACC, SL_DIVSTEP, SL_DIVALL, c->P.div_tol, c->counters + 5};
+  DivCheck dc{c->sc.out, SL_DIVACC, SL_DIVSTEP, SL_DIVALL, c->P.div_tol, c->counters + 5,
+              c->p_out};
   launch_project(c->D, c->lev[0].g, c->lev[0].d.u, c->lev[0].d.p, c->lev[0].d.beta, c->uvel,
                  coef, dc, c->stream);
 }
@@ -1268,6 +1284,19 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   double mu_eff = p->inv_re * p->mu_f;
   launch_laminar(D, L0.g, p->flow_axis, mu_eff, p->u_center, p->body_force, p->ic_scale,
                  c->uvel[p->flow_axis], c->G_dev, s);
+  if (p->open_flow) {
+    // Sec. 3.6: no body force; the pressure falls linearly along the duct,
+    // Eq. (pressLam), p(0) = 0 and euler kappa = -G (G the body force that
+    // drives the same laminar flow), so p_out = kappa L
+    double G = 0.0;
+    if (cudaMemcpyAsync(&G, c->G_dev, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemsetAsync(c->G_dev, 0, sizeof(double), s) != cudaSuccess) {
+      bfibm_destroy(c);
+      return BFIBM_ECUDA;
+    }
+    c->p_out = -G / p->euler * (p->n[p->flow_axis] * p->h);
+  }
   launch_reset_fields(D, L0.g, c->frc, c->rho, L0.d.muc, L0.d.mue, p->rho_f, p->mu_f, s);
   build_coefficients(c);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1875,6 +1904,8 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
   } else if (option == BFIBM_OPT_GRAPH) {
     c->use_graph = value != 0;
   } else if (option == BFIBM_OPT_FUSED) {
+    if (value != 0 && c->P.open_flow)
+      return set_err(c, BFIBM_EINVAL, "the open duct uses one kernel per colour");
     c->fused = value != 0;
   } else if (option == BFIBM_OPT_TMA) {
     if (value < 0 || value > 2) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_TMA takes 0, 1 or 2");

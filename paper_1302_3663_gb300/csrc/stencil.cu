@@ -29,6 +29,11 @@ inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
   return dim3((unsigned)((nx + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y),
               (unsigned)((nz + b.z - 1) / b.z));
 }
+// extent of the points a kernel covers along axis a: the cells, plus the
+// outflow plane of an open axis when `outflow` (its faces are unknowns)
+inline int ext(const Geo& g, int a, bool outflow) {
+  return g.n[a] + (outflow && g.open == a ? 1 : 0);
+}
 inline int red_grid(long long n) {
   long long b = (n + kBlock1D - 1) / kBlock1D;
   return (int)(b < kRedBlocks ? (b > 0 ? b : 1) : kRedBlocks);
@@ -109,6 +114,10 @@ __device__ __forceinline__ void p_terms(const Geo& g, const LevelPtrs<T>& L, con
       T bb = b[cp];
       num += bb * L.p[cp];
       dg += bb;
+    } else if (a == g.open) {
+      // the outflow face, pressure held there: the homogeneous ghost -p
+      // (the held value is in the right-hand side)
+      dg += T(2) * b[c + g.st[a]];
     }
   }
 }
@@ -151,13 +160,19 @@ __global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
 // Beyond a wall along e the tangential u_d takes the mirror ghost -u_d(F),
 // which doubles that edge's weight in dgV; u_e on the wall is a stored 0.
 // ---------------------------------------------------------------------------
+// On the outflow face of an open axis (d = open, index n) du/dn = 0: the face
+// beyond mirrors the face n - 1, the cell beyond mirrors the last cell (its
+// viscosity) and the tangential components mirror too (du_e/dx_d = 0 there).
+// Across the outflow (e = open, last cell) the tangential u_d mirrors evenly:
+// that edge contributes its cross term only.
 template <int D, int d, typename T>
 __device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
                                         long long F, T& off, T& dgV) {
   const T* __restrict__ ud = L.u[d];
-  long long od_p = offp(g, d, ci[d]);
+  const bool outflow = d == g.open && ci[d] == g.n[d];
   long long od_m = offm(g, d, ci[d]);
-  T mcp = L.muc[F], mcm = L.muc[F + od_m];
+  long long od_p = outflow ? od_m : offp(g, d, ci[d]);
+  T mcp = outflow ? L.muc[F + od_m] : L.muc[F], mcm = L.muc[F + od_m];
   off = T(2) * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
   dgV = T(2) * (mcp + mcm);
 #pragma unroll
@@ -168,15 +183,16 @@ __device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, con
     bool pe = g.per[e] != 0;
     bool wp = !pe && ci[e] == g.n[e] - 1;
     bool wm = !pe && ci[e] == 0;
+    bool neu = wp && e == g.open;   // beyond the outflow: even ghost, no weight
     long long Ep = F + offp(g, e, ci[e]);   // e-face index ci[e] + 1
     T mep = me[Ep], mem = me[F];
-    T cp = ue[Ep] - ue[Ep + od_m];
-    T cm = ue[F] - ue[F + od_m];
+    T cp = outflow ? T(0) : ue[Ep] - ue[Ep + od_m];
+    T cm = outflow ? T(0) : ue[F] - ue[F + od_m];
     T udp = T(0), udm = T(0);
     if (!wp) udp = ud[Ep];
     if (!wm) udm = ud[F + offm(g, e, ci[e])];
     off += mep * (udp + cp) + mem * (udm - cm);
-    dgV += (wp ? T(2) : T(1)) * mep + (wm ? T(2) : T(1)) * mem;
+    dgV += (neu ? T(0) : (wp ? T(2) : T(1))) * mep + (wm ? T(2) : T(1)) * mem;
   }
 }
 
@@ -185,9 +201,12 @@ __global__ void __launch_bounds__(256) k_v_rbgs(Geo g, LevelPtrs<T> L, int colou
   int ih = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (j >= g.n[1] || k >= g.n[2]) return;
+  // the faces of component d: along an open axis d the outflow face n too
+  const int e0 = g.n[0] + (d == 0 && g.open == 0), e1 = g.n[1] + (d == 1 && g.open == 1),
+            e2 = g.n[2] + (d == 2 && g.open == 2);
+  if (j >= e1 || k >= e2) return;
   int i = 2 * ih + ((j + k + colour) & 1);
-  if (i >= g.n[0]) return;
+  if (i >= e0) return;
   int ci[3] = {i, j, k};
   if (!g.per[d] && ci[d] == 0) return;   // wall face
   long long F = gidx(g, i, j, k);
@@ -199,6 +218,8 @@ __global__ void __launch_bounds__(256) k_v_rbgs(Geo g, LevelPtrs<T> L, int colou
 template <int D, int d, typename T>
 __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T>& L,
                                                  const int ci[3], long long F, T ir) {
+  // the plane beyond the last cells of an open axis holds only its outflow faces
+  if (g.open >= 0 && g.open != d && ci[g.open] == g.n[g.open]) return;
   if (!g.per[d] && ci[d] == 0) {
     L.ur[d][F] = T(0);
     return;
@@ -213,7 +234,8 @@ __global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir)
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  if (i >= g.n[0] + (g.open == 0) || j >= g.n[1] + (g.open == 1) || k >= g.n[2] + (g.open == 2))
+    return;
   int ci[3] = {i, j, k};
   long long F = gidx(g, i, j, k);
   v_residual_point<D, 0, T>(g, L, ci, F, ir);
@@ -265,7 +287,7 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* 
   }
   long long c = gidx(gc, C[0], C[1], C[2]);
   xc[c] = T(0);
-  bool wallface = !gc.per[d] && (C[d] == 0 || C[d] == gc.n[d]);
+  bool wallface = !gc.per[d] && (C[d] == 0 || (C[d] == gc.n[d] && d != gc.open));
   if (wallface) {
     fc[c] = T(0);
     return;
@@ -286,6 +308,7 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* 
       for (int o = -1; o <= 1; ++o) {
         int q = 2 * C[d] + o;
         if (gf.per[d]) q = q < 0 ? q + nf : (q >= nf ? q - nf : q);
+        if (d == gf.open && q > nf) q = nf - 1;   // even ghost beyond the outflow
         f[d] = q;
         T w = (o == 0) ? T(0.5) : T(0.25);
         along += w * rf[gidx(gf, f[0], f[1], f[2])];
@@ -302,7 +325,8 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* 
 // coarse face, or the mean of the two coarse faces around a midway face.
 // The weights are exact binary fractions in any precision.
 template <typename T>
-__device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, int mirror, int idx[2], T w[2]) {
+__device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, int mirror_lo, int mirror_hi,
+                                            int idx[2], T w[2]) {
   int I = i >> 1;
   int J = I + ((i & 1) ? 1 : -1);
   idx[0] = I;
@@ -314,6 +338,7 @@ __device__ __forceinline__ int prol_cell_1d(int i, int nc, int per, int mirror, 
     return 2;
   }
   if (J < 0 || J >= nc) {
+    const int mirror = J < 0 ? mirror_lo : mirror_hi;
     w[0] = mirror > 0 ? T(1) : T(0.5);
     idx[1] = I;   // weight 0: any valid index
     return 1;
@@ -373,7 +398,10 @@ __global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* _
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
 #pragma unroll
-  for (int a = 0; a < D; ++a) prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, idx[a], w[a]);
+  // the pressure correction mirrors evenly at walls and the inflow, oddly at
+  // the outflow, where the pressure is held
+  for (int a = 0; a < D; ++a)
+    prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, a == gc.open ? -1 : +1, idx[a], w[a]);
   xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
 }
 
@@ -384,7 +412,10 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
   fi[0] = blockIdx.x * blockDim.x + threadIdx.x;
   fi[1] = blockIdx.y * blockDim.y + threadIdx.y;
   fi[2] = blockIdx.z * blockDim.z + threadIdx.z;
-  if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
+  // along an open axis d the outflow face n is an unknown too
+  if (fi[0] >= gf.n[0] + (d == 0 && gf.open == 0) || fi[1] >= gf.n[1] + (d == 1 && gf.open == 1) ||
+      fi[2] >= gf.n[2] + (d == 2 && gf.open == 2))
+    return;
   if (!gf.per[d] && fi[d] == 0) return;
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
@@ -392,8 +423,8 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
   for (int a = 0; a < D; ++a) {
     if (a == d)
       prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
-    else
-      prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, idx[a], w[a]);
+    else   // tangential velocity: odd at walls and the inflow, even beyond the outflow
+      prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, a == gc.open ? +1 : -1, idx[a], w[a]);
   }
   xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
 }
@@ -433,22 +464,24 @@ __global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int s
     __syncthreads();
   }
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-  double s = 0.0;
-  for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
-    int i, j, k;
-    decode(g, q, i, j, k);
-    s += (double)L.pf[gidx(g, i, j, k)];
+  if (g.open < 0) {   // the singular problem needs a zero-mean right-hand side
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
+      int i, j, k;
+      decode(g, q, i, j, k);
+      s += (double)L.pf[gidx(g, i, j, k)];
+    }
+    s = block_sum(s, sh);
+    __shared__ double mean;
+    if (threadIdx.x == 0) mean = s / (double)ncell;
+    __syncthreads();
+    for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
+      int i, j, k;
+      decode(g, q, i, j, k);
+      L.pf[gidx(g, i, j, k)] -= (T)mean;
+    }
+    __syncthreads();
   }
-  s = block_sum(s, sh);
-  __shared__ double mean;
-  if (threadIdx.x == 0) mean = s / (double)ncell;
-  __syncthreads();
-  for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
-    int i, j, k;
-    decode(g, q, i, j, k);
-    L.pf[gidx(g, i, j, k)] -= (T)mean;
-  }
-  __syncthreads();
   int nh = (g.n[0] + 1) >> 1;
   long long npts = (long long)nh * g.n[1] * g.n[2];
   T h2 = (T)(g.h * g.h);
@@ -482,15 +515,18 @@ __global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int s
 template <int D, int d, typename T, bool INV>
 __device__ __forceinline__ void coarse_v_phase(const Geo& g, const LevelPtrs<T>& L, int colour,
                                                T ir) {
-  const int nh = (g.n[0] + 1) >> 1;
-  const int npts = nh * g.n[1] * g.n[2];   // a few thousand at most on the coarsest grid
+  // the faces of component d (the outflow face too along an open axis d)
+  const int e0 = g.n[0] + (d == 0 && g.open == 0), e1 = g.n[1] + (d == 1 && g.open == 1),
+            e2 = g.n[2] + (d == 2 && g.open == 2);
+  const int nh = (e0 + 1) >> 1;
+  const int npts = nh * e1 * e2;   // a few thousand at most on the coarsest grid
   for (int q = threadIdx.x; q < npts; q += blockDim.x) {
     int ih = q % nh;
     int r = q / nh;
-    int j = r % g.n[1];
-    int k = r / g.n[1];
+    int j = r % e1;
+    int k = r / e1;
     int i = 2 * ih + ((j + k + colour) & 1);
-    if (i >= g.n[0]) continue;
+    if (i >= e0) continue;
     int ci[3] = {i, j, k};
     if (!g.per[d] && ci[d] == 0) continue;
     long long F = gidx(g, i, j, k);
@@ -506,12 +542,14 @@ __device__ __forceinline__ void coarse_v_phase(const Geo& g, const LevelPtrs<T>&
 // only its own m_d)
 template <int D, int d, typename T>
 __device__ __forceinline__ void coarse_v_invert(const Geo& g, const LevelPtrs<T>& L, T ir) {
-  const int ncell = g.n[0] * g.n[1] * g.n[2];
+  const int e0 = g.n[0] + (d == 0 && g.open == 0), e1 = g.n[1] + (d == 1 && g.open == 1),
+            e2 = g.n[2] + (d == 2 && g.open == 2);
+  const int ncell = e0 * e1 * e2;
   for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
-    int i = q % g.n[0];
-    int r = q / g.n[0];
-    int j = r % g.n[1];
-    int k = r / g.n[1];
+    int i = q % e0;
+    int r = q / e0;
+    int j = r % e1;
+    int k = r / e1;
     int ci[3] = {i, j, k};
     if (!g.per[d] && ci[d] == 0) continue;
     long long F = gidx(g, i, j, k);
@@ -705,13 +743,18 @@ __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, cons
                                               const Ptr3& frc, const LevelPtrs<double>& L0,
                                               const int ci[3], long long F, double c_force,
                                               double gflow, double c4) {
-  if (!g.per[d] && ci[d] == 0) {
+  if (!g.per[d] && ci[d] == 0) {   // not an unknown: 0 on a wall, the inflow on an open axis
     L0.uf[d][F] = 0.0;
-    L0.u[d][F] = 0.0;
+    L0.u[d][F] = d == g.open ? uv.a[d][F] : 0.0;
     return;
   }
+  // the plane beyond the last cells of an open axis holds only its outflow faces
+  if (g.open >= 0 && g.open != d && ci[g.open] == g.n[g.open]) return;
   const double* __restrict__ ud = uv.a[d];
-  long long od_p = offp(g, d, ci[d]), od_m = offm(g, d, ci[d]);
+  // on the outflow face everything beyond mirrors evenly (du/dn = 0)
+  const bool outflow = d == g.open && ci[d] == g.n[d];
+  long long od_m = offm(g, d, ci[d]), od_p = outflow ? od_m : offp(g, d, ci[d]);
+  long long oc = outflow ? od_m : 0;   // the cell beyond the outflow is the last cell
   double udF = ud[F], udp = ud[F + od_p], udm = ud[F + od_m];
   // 4 h Adv_d, one axis at a time
   double a4 = (udF + udp) * udp - (udm + udF) * udm;
@@ -723,9 +766,10 @@ __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, cons
     long long oe_p = offp(g, e, ci[e]);
     double up = -udF, um = -udF;   // mirror ghosts beyond a wall (U_e = 0 there)
     if (pe || ci[e] != g.n[e] - 1) up = ud[F + oe_p];
+    else if (e == g.open) up = udF;   // beyond the outflow: even ghost
     if (pe || ci[e] != 0) um = ud[F + offm(g, e, ci[e])];
-    double s_lo = ue[F + od_m] + ue[F];                 // 2 x u_e on the lower edge
-    double s_hi = ue[F + oe_p + od_m] + ue[F + oe_p];   // 2 x u_e on the upper edge
+    double s_lo = ue[F + od_m] + ue[F + oc];                 // 2 x u_e on the lower edge
+    double s_hi = ue[F + oe_p + od_m] + ue[F + oe_p + oc];   // 2 x u_e on the upper edge
     a4 += s_hi * up - s_lo * um;
   }
   double A = c4 * a4;
@@ -740,7 +784,8 @@ __global__ void __launch_bounds__(256) k_adv_rhs(Geo g, Ptr3 uv, Ptr3 rho, Ptr3 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  if (i >= g.n[0] + (g.open == 0) || j >= g.n[1] + (g.open == 1) || k >= g.n[2] + (g.open == 2))
+    return;
   int ci[3] = {i, j, k};
   long long F = gidx(g, i, j, k);
   double G = *G_dev;
@@ -765,7 +810,9 @@ __device__ __forceinline__ double div_at(const Geo& g, const Ptr3& u, const int 
 
 template <int D>
 __global__ void __launch_bounds__(256) k_divergence(Geo g, Ptr3 u, double* __restrict__ b,
-                                                    double scale, double* __restrict__ partial) {
+                                                    double scale, double* __restrict__ partial,
+                                                    const double* __restrict__ beta_open,
+                                                    double pbc) {
   __shared__ double sh[32];
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   double acc = 0.0;
@@ -775,6 +822,8 @@ __global__ void __launch_bounds__(256) k_divergence(Geo g, Ptr3 u, double* __res
     decode(g, q, ci[0], ci[1], ci[2]);
     long long c = gidx(g, ci[0], ci[1], ci[2]);
     double v = scale * div_at<D>(g, u, ci, c);
+    // the held outflow pressure: b -= 2 beta_out p_out / h^2 (pbc = 2 p_out / h^2)
+    if (g.open >= 0 && ci[g.open] == g.n[g.open] - 1) v -= beta_open[c + g.st[g.open]] * pbc;
     b[c] = v;
     acc += v;
   }
@@ -834,12 +883,25 @@ __device__ __forceinline__ double proj_face(double ut, double beta, double pF, d
 template <int D>
 __global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* __restrict__ p,
                                                  Ptr3 beta, Ptr3 uv, double coef,
-                                                 unsigned long long* __restrict__ divacc) {
+                                                 unsigned long long* __restrict__ divacc,
+                                                 double p_out) {
   __shared__ double sh[32];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z * blockDim.z + threadIdx.z;
   double mx = 0.0;
+  if (g.open >= 0) {   // the outflow faces, one plane beyond the last cells
+    const int ci[3] = {i, j, k};
+    const int o = g.open;
+    bool beyond = ci[o] == g.n[o];
+    for (int a = 0; a < D; ++a)
+      if (a != o && ci[a] >= g.n[a]) beyond = false;
+    if (beyond) {
+      long long F = gidx(g, i, j, k);
+      const double pm = p[F - g.st[o]];
+      uv.a[o][F] = proj_face(ut.a[o][F], beta.a[o][F], 2.0 * p_out - pm, pm, coef, g.h);
+    }
+  }
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
     int ci[3] = {i, j, k};
     long long F = gidx(g, i, j, k);
@@ -849,7 +911,9 @@ __global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* _
     for (int d = 0; d < D; ++d) {
       double lo = 0.0;
       if (!g.per[d] && ci[d] == 0) {
-        uv.a[d][F] = 0.0;
+        // not an unknown: 0 on a wall, the prescribed inflow on an open axis
+        lo = ut.a[d][F];
+        uv.a[d][F] = lo;
       } else {
         lo = proj_face(ut.a[d][F], beta.a[d][F], pF, p[F + offm(g, d, ci[d])], coef, g.h);
         uv.a[d][F] = lo;
@@ -858,6 +922,9 @@ __global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* _
       if (g.per[d] || ci[d] != g.n[d] - 1) {
         long long Fu = F + offp(g, d, ci[d]);
         hi = proj_face(ut.a[d][Fu], beta.a[d][Fu], p[Fu], pF, coef, g.h);
+      } else if (d == g.open) {   // the outflow face: ghost 2 p_out - p
+        long long Fu = F + g.st[d];
+        hi = proj_face(ut.a[d][Fu], beta.a[d][Fu], 2.0 * p_out - pF, pF, coef, g.h);
       }
       s += (hi - lo) / g.h;
     }
@@ -907,6 +974,10 @@ __global__ void __launch_bounds__(256) k_norm2(Geo g, Ptr3 a, int ncomp,
       acc += v * v;
     } else {
       for (int d = 0; d < ncomp; ++d) {
+        if (d == g.open && ci[d] == g.n[d] - 1) {   // the outflow face is an unknown too
+          double v = a.a[d][c + g.st[d]];
+          acc += v * v;
+        }
         if (!g.per[d] && ci[d] == 0) continue;
         double v = a.a[d][c];
         acc += v * v;
@@ -930,6 +1001,10 @@ __global__ void __launch_bounds__(256) k_div_ke(Geo g, Ptr3 u, double* __restric
     long long c = gidx(g, ci[0], ci[1], ci[2]);
     mx = fmax(mx, fabs(div_at<D>(g, u, ci, c)));
     for (int d = 0; d < D; ++d) {
+      if (d == g.open && ci[d] == g.n[d] - 1) {   // the outflow face
+        double v = u.a[d][c + g.st[d]];
+        acc += v * v;
+      }
       if (!g.per[d] && ci[d] == 0) continue;
       double v = u.a[d][c];
       acc += v * v;
@@ -978,15 +1053,21 @@ __global__ void k_laminar(Geo g, int D, int fa, int ta0, int ta1, double mu_eff,
   int n0 = g.n[ta0], n1 = (D == 3) ? g.n[ta1] : 1;
   if (a >= n0 || b >= n1) return;
   double A = g.n[ta0] * g.h, B = (D == 3) ? g.n[ta1] * g.h : 0.0;
-  double v = ic_scale * (*G_dev) / mu_eff *
-             laminar_unit(D, A, B, (a + 0.5) * g.h, (b + 0.5) * g.h);
-  int lo = g.per[fa] ? 0 : 1;
-  for (int q = lo; q < g.n[fa]; ++q) {
+  double full = (*G_dev) / mu_eff * laminar_unit(D, A, B, (a + 0.5) * g.h, (b + 0.5) * g.h);
+  double v = ic_scale * full;
+  int lo = g.per[fa] ? 0 : 1, hi = g.n[fa] + (fa == g.open ? 1 : 0);
+  for (int q = lo; q < hi; ++q) {
     int c[3] = {0, 0, 0};
     c[fa] = q;
     c[ta0] = a;
     if (D == 3) c[ta1] = b;
     u[gidx(g, c[0], c[1], c[2])] = v;
+  }
+  if (fa == g.open) {   // the inflow face holds the laminar profile itself (Sec. 3.6)
+    int c[3] = {0, 0, 0};
+    c[ta0] = a;
+    if (D == 3) c[ta1] = b;
+    u[gidx(g, c[0], c[1], c[2])] = full;
   }
 }
 
@@ -1066,7 +1147,7 @@ template <typename T>
 void launch_v_rbgs(int D, const Geo& g, const LevelPtrs<T>& L, int d, int colour, double inv_re,
                    cudaStream_t s) {
   dim3 b = blk3(D);
-  dim3 gr = grd3((g.n[0] + 1) / 2, g.n[1], g.n[2], b);
+  dim3 gr = grd3((ext(g, 0, d == 0) + 1) / 2, ext(g, 1, d == 1), ext(g, 2, d == 2), b);
   T ir = (T)(inv_re / (g.h * g.h));
   if (D == 3) {
     if (d == 0) k_v_rbgs<3, 0, T><<<gr, b, 0, s>>>(g, L, colour, ir);
@@ -1081,7 +1162,7 @@ void launch_v_rbgs(int D, const Geo& g, const LevelPtrs<T>& L, int d, int colour
 template <typename T>
 void launch_v_residual(int D, const Geo& g, const LevelPtrs<T>& L, double inv_re, cudaStream_t s) {
   dim3 b = blk3(D);
-  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  dim3 gr = grd3(ext(g, 0, true), ext(g, 1, true), ext(g, 2, true), b);
   T ir = (T)(inv_re / (g.h * g.h));
   if (D == 3) k_v_residual<3, T><<<gr, b, 0, s>>>(g, L, ir);
   else k_v_residual<2, T><<<gr, b, 0, s>>>(g, L, ir);
@@ -1123,7 +1204,7 @@ template <typename T>
 void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec, T* xf,
                          cudaStream_t s) {
   dim3 b = blk3(D);
-  dim3 gr = grd3(gf.n[0], gf.n[1], gf.n[2], b);
+  dim3 gr = grd3(ext(gf, 0, d == 0), ext(gf, 1, d == 1), ext(gf, 2, d == 2), b);
   if (D == 3) {
     if (d == 0) k_prolong_face<3, 0, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
     else if (d == 1) k_prolong_face<3, 1, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
@@ -1144,6 +1225,9 @@ static const size_t kCoarseSmemMax = 160 * 1024;
 
 template <typename T>
 void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cudaStream_t s) {
+  // with the outflow pressure held the slowest coarse mode is no longer the
+  // constant the mean removes: at least 2 n^2 sweeps along the open axis
+  if (g.open >= 0 && sweeps < 2 * g.n[g.open] * g.n[g.open]) sweeps = 2 * g.n[g.open] * g.n[g.open];
   long long nel = g.st[2] * g.s[2];
   size_t smem = coarse_smem_bytes(D, g, sizeof(T), false);
   int use = smem <= kCoarseSmemMax;
@@ -1228,7 +1312,7 @@ void launch_adv_rhs(int D, const Geo& g, double* const uvel[3], double* const rh
                     double* const frc[3], const LevelPtrs<double>& L0, double c_force,
                     int flow_axis, const double* G_dev, cudaStream_t s) {
   dim3 b = blk3(D);
-  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  dim3 gr = grd3(ext(g, 0, true), ext(g, 1, true), ext(g, 2, true), b);
   if (D == 3)
     k_adv_rhs<3><<<gr, b, 0, s>>>(g, ptr3(uvel), ptr3(rho), ptr3(frc), L0, c_force, flow_axis, G_dev);
   else
@@ -1236,11 +1320,13 @@ void launch_adv_rhs(int D, const Geo& g, double* const uvel[3], double* const rh
 }
 
 void launch_divergence(int D, const Geo& g, double* const u[3], double* b, double scale,
-                       Scalars sc, cudaStream_t s) {
+                       Scalars sc, cudaStream_t s, const double* beta_open, double p_out) {
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   int nb = red_grid(ncell);
-  if (D == 3) k_divergence<3><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), b, scale, sc.partial);
-  else k_divergence<2><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), b, scale, sc.partial);
+  const double pbc = 2.0 * p_out / (g.h * g.h);
+  if (D == 3) k_divergence<3><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), b, scale, sc.partial, beta_open, pbc);
+  else k_divergence<2><<<nb, kBlock1D, 0, s>>>(g, ptr3(u), b, scale, sc.partial, beta_open, pbc);
+  if (g.open >= 0) return;   // a regular problem: the mean stays
   k_finalize<<<1, 1024, 0, s>>>(sc.partial, nb, sc.out, 0, 1.0 / (double)ncell, 0);
   dim3 bb = blk3(D);
   k_sub_scalar<<<grd3(g.n[0], g.n[1], g.n[2], bb), bb, 0, s>>>(g, b, sc.out);
@@ -1259,10 +1345,12 @@ void launch_project(int D, const Geo& g, double* const ut[3], const double* p,
                     double* const beta[3], double* uvel[3], double coef, const DivCheck& dc,
                     cudaStream_t s) {
   dim3 b = blk3(D);
-  dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
+  dim3 gr = grd3(ext(g, 0, true), ext(g, 1, true), ext(g, 2, true), b);
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(dc.out + dc.acc);
-  if (D == 3) k_project<3><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef, acc);
-  else k_project<2><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef, acc);
+  if (D == 3)
+    k_project<3><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef, acc, dc.p_out);
+  else
+    k_project<2><<<gr, b, 0, s>>>(g, ptr3(ut), p, ptr3(beta), ptr3(uvel), coef, acc, dc.p_out);
   k_div_check<<<1, 32, 0, s>>>(dc.out, dc.acc, dc.step, dc.all, dc.tol, dc.viol);
 }
 

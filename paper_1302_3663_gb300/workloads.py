@@ -306,7 +306,32 @@ def mound_2d(n=64, rho_ratio=1.0, mu_ratio=1.0, omega=0.02, seed=0):
     return _instance(prm, X, r, 1.0, 0.5, 20, "mound_2d", dict(spacing=spacing))
 
 
-CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "paper_units": paper_units_duct}
+def open_channel_2d(seed=0, n=64):
+    """The open channel of Sec. 3.6 in 2D: c1's mound (150 nodes in a half-
+    disc of radius 0.1 at x = 0.5 on the y = 0 wall) in a channel of
+    2n x n/2 cells on [0, 2] x [0, 0.5], the laminar profile held at the
+    inflow x = 0, du/dn = 0 and the pressure held at the outflow x = 2."""
+    base = c1(seed)
+    h = 1.0 / n
+    prm = dict(base["params"], n=[2 * n, n // 2, 1], periodic=[0, 0, 1], open_flow=1, h=h,
+               dt=0.1 * h)
+    return dict(base, params=prm, name="open_channel_2d")
+
+
+def open_duct(seed=1, e=64):
+    """The open square tube of Sec. 3.6: c2's hemispherical mound (2,000
+    nodes, radius 0.15, centred at z = 0.5) in an e x e x 2e duct of side 1
+    and length 2, the laminar profile of Eq. (3DlaminarFlow) held at the
+    inflow z = 0, du/dn = 0 and the pressure held at the outflow z = 2."""
+    base = c2(seed)
+    h = 1.0 / e
+    prm = dict(base["params"], n=[e, e, 2 * e], periodic=[0, 0, 0], open_flow=1, h=h,
+               dt=0.1 * h)
+    return dict(base, params=prm, name="open_duct")
+
+
+CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "paper_units": paper_units_duct,
+           "open_duct": open_duct}
 
 
 def cells(prm):
