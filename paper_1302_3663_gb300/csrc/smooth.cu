@@ -17,6 +17,8 @@
 // precomputed inverse diagonal instead of dividing by the diagonal.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace bf {
@@ -549,7 +551,7 @@ __device__ __forceinline__ PSet psel(bool t, const PSet& a, const PSet& b) {
 }
 
 template <int d, bool PERZ>
-__global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
+__global__ void __launch_bounds__(512, 2) k_v_rb_pair(Geo g, LevelPtrs<float> L,
                                                    float* __restrict__ out, int TY, int KC,
                                                    float ir) {
   constexpr int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
@@ -628,11 +630,13 @@ __global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
   int sk = 0;                                // ring slot of plane k
   PSet keep{};                               // the black point's set of plane k - 1
   float red_prev = 0.f;
-  int par_prev = 0;
-  for (int k = k0 - 1; k <= k1; ++k) {
+  // One plane. PAR is the element of the red point, (j + k) & 1: a warp
+  // holds one row, so it is the same in every lane, and the black point of
+  // plane k - 1 is element PAR as well.
+  auto step = [&](auto par_tag, const int k) {
+    constexpr int PAR = decltype(par_tag)::value;
     const bool planevalid = PERZ || (k >= 0 && k < n2);
     const int kw = pz(k), kp = pz(k + 1);
-    const int par = (j + kw) & 1;            // element index of the red point
     const bool wpz = !PERZ && kw == n2 - 1, wmz = !PERZ && kw == 0;
     float redv = 0.f;
     PSet blk{};
@@ -673,11 +677,11 @@ __global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
     }
     PRow N0{}, N1{}, N2{}, N3{};
     if (ld && planevalid) {
-      // u_d at the rows beside (old values) and one value beside the pair
+      // u_d at the rows beside (old values) and the value beside the red point
       const PRow UDym = row(ud, oym, kw, false, false), UDyp = row(ud, oyp, kw, false, false);
       PRow UDx = UDc;
       const int ox = oy0 + kw * st2;
-      if (par) UDx.r = __ldg(ud + ox + 2);
+      if constexpr (PAR == 1) UDx.r = __ldg(ud + ox + 2);
       else UDx.l = __ldg(ud + ox - x0 + xl);
       PSet c0, c1;
       if constexpr (d == 0) {
@@ -729,32 +733,31 @@ __global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
         N3 = MC;
       }
       // the red point: its set and its old neighbours along d, e1, e2
-      const PSet cr = psel(par != 0, c1, c0);
       float np_[3], nm_[3];
-      np_[0] = par ? pe<2>(UDx) : pe<1>(UDx);
-      nm_[0] = par ? pe<0>(UDx) : pe<-1>(UDx);
-      np_[1] = par ? pe<1>(UDyp) : pe<0>(UDyp);
-      nm_[1] = par ? pe<1>(UDym) : pe<0>(UDym);
-      np_[2] = par ? pe<1>(UDp) : pe<0>(UDp);
-      nm_[2] = par ? pe<1>(UDm) : pe<0>(UDm);
-      redv = psolve(cr, ir, np_[d], nm_[d], np_[e1], nm_[e1], np_[e2], nm_[e2]);
-      const bool wall_red = (d == 0 && x0 + par == 0) || (d == 1 && j == 0) ||
+      np_[0] = pe<PAR + 1>(UDx);
+      nm_[0] = pe<PAR - 1>(UDx);
+      np_[1] = pe<PAR>(UDyp);
+      nm_[1] = pe<PAR>(UDym);
+      np_[2] = pe<PAR>(UDp);
+      nm_[2] = pe<PAR>(UDm);
+      redv = psolve(PAR ? c1 : c0, ir, np_[d], nm_[d], np_[e1], nm_[e1], np_[e2], nm_[e2]);
+      const bool wall_red = (d == 0 && x0 + PAR == 0) || (d == 1 && j == 0) ||
                             (d == 2 && !PERZ && kw == 0);
       if (wall_red) redv = 0.f;
-      blk = psel(par != 0, c0, c1);
+      blk = PAR ? c0 : c1;
     }
     if (lane_ok) {
-      const float2 rv = make_float2(par ? 0.f : redv, par ? redv : 0.f);
+      const float2 rv = PAR ? make_float2(0.f, redv) : make_float2(redv, 0.f);
       *reinterpret_cast<float2*>(ring + sk * plane + r * W + x0) = rv;
     }
     __syncthreads();
-    // the black point of plane k - 1 on the block's own rows; the pair out
+    // the black point (element PAR) of plane k - 1 on the block's own rows;
+    // the pair out
     const int kb = k - 1;
     if (own && kb >= k0 && kb < k1) {
       const int kbw = pz(kb);
       const int s_m = (sk + 2) & 3, s_0 = (sk + 3) & 3;   // planes k - 2, k - 1 (k: sk)
-      const int eb = par_prev ^ 1;
-      const int xb = x0 + eb;
+      const int xb = x0 + PAR;
       const float* R0 = ring + s_0 * plane + r * W;
       float np_[3], nm_[3];
       np_[0] = xb + 1 < n0 ? R0[xb + 1] : 0.f;
@@ -767,13 +770,12 @@ __global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
       const bool wall_blk = (d == 0 && xb == 0) || (d == 1 && j == 0) ||
                             (d == 2 && !PERZ && kbw == 0);
       if (wall_blk) bv = 0.f;
-      const float2 o = eb ? make_float2(red_prev, bv) : make_float2(bv, red_prev);
+      const float2 o = PAR ? make_float2(red_prev, bv) : make_float2(bv, red_prev);
       *reinterpret_cast<float2*>(out + oy0 + kbw * st2) = o;
     }
     // advance the queues by one plane
     keep = blk;
     red_prev = redv;
-    par_prev = par;
     sk = (sk + 1) & 3;
     UDm = UDc;
     UDc = UDp;
@@ -810,6 +812,22 @@ __global__ void __launch_bounds__(512) k_v_rb_pair(Geo g, LevelPtrs<float> L,
         }
       }
     }
+  };
+  using P0 = std::integral_constant<int, 0>;
+  using P1 = std::integral_constant<int, 1>;
+  int k = k0 - 1;
+  for (; k + 1 <= k1; k += 2) {   // two planes per iteration: the parity alternates
+    if ((j + k) & 1) {
+      step(P1{}, k);
+      step(P0{}, k + 1);
+    } else {
+      step(P0{}, k);
+      step(P1{}, k + 1);
+    }
+  }
+  if (k <= k1) {
+    if ((j + k) & 1) step(P1{}, k);
+    else step(P0{}, k);
   }
 }
 
