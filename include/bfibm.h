@@ -394,6 +394,42 @@ bfibm_status bfibm_batch_wait(bfibm_batch* b);
    them); BFIBM_ESTATE if the member was not stepped. */
 bfibm_status bfibm_batch_slot_ms(bfibm_batch* b, int32_t slot, float* ms);
 void bfibm_batch_destroy(bfibm_batch* b);
+/* Batch options. BFIBM_BATCH_PERSISTENT (default 0): 1 steps the members in
+   lock step, one CUDA graph per batch step in which every multigrid level and
+   phase of both solves (Sec. 3.5, the mixed-precision form: FP32 V-cycles in
+   FP64 defect correction, and flexible CG for the viscous solve when the
+   members use it) is one launch over a device work list of (member, block)
+   items covering members of different sizes; each solve's device loop runs
+   while any member still iterates, and a member whose tolerance test is met
+   drops out of the mask every launch of the loop reads. The stages around the
+   solves run per member on forked branches of the graph. Every member must be
+   3D, mixed precision (precision 1), closed (no open duct), solve to a
+   tolerance (vc_visc = vc_p = 0), have a stream of its own, and share nu1,
+   nu2, BFIBM_OPT_INNER and BFIBM_OPT_KRYLOV with the others; each member then
+   gets the same bits as stepped alone. bfibm_batch_step must then give every
+   member it steps the same count; the plan (member table, work lists, graph)
+   is rebuilt when the stepped members or their options change.
+   BFIBM_BATCH_TUNE (default 1): time the batched sweeps' tile rows, chunk
+   planes, planes per phase and grid on every level of at least 2^19 cells in
+   all when a plan is built. Either option drops the current plan. */
+enum {
+  BFIBM_BATCH_PERSISTENT = 0,
+  BFIBM_BATCH_TUNE = 1
+};
+bfibm_status bfibm_batch_set_option(bfibm_batch* b, int option, int64_t value);
+/* out[0] persistent mode, out[1] plans built so far; with a plan: out[2]
+   members, out[3] kernel nodes of the batch step graph outside its loops,
+   out[4] / out[5] kernel nodes of one iteration of the viscous / pressure
+   loop, out[6] / out[7] iterations of those loops so far (waits for the
+   batch's work). */
+bfibm_status bfibm_batch_info(bfibm_batch* b, int64_t out[8]);
+/* The batched sweep of the current plan on a level (kind 0 viscous, 1
+   pressure): out = {tile rows, chunk planes, planes per phase, threads per
+   row, one block per item (1) or resident blocks striding (0), grid}.
+   BFIBM_EINVAL without a plan or for a level it does not have. */
+bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[6]);
+/* Message of the last batch call that failed on the batch itself. */
+const char* bfibm_batch_error(bfibm_batch* b);
 /* Device bytes a context with these parameters allocates for its grids. */
 bfibm_status bfibm_footprint(const bfibm_params* p, int64_t eta, int64_t nsprings,
                              int64_t* bytes);

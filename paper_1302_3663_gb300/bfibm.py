@@ -22,6 +22,7 @@ FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "m
          "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12, "idg": 13}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
 OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER, OPT_KRYLOV, OPT_WAIT_NS = range(7)
+BATCH_PERSISTENT, BATCH_TUNE = range(2)
 
 
 class BfibmError(RuntimeError):
@@ -117,8 +118,13 @@ SIGNATURES = {
     "bfibm_batch_wait": [_V],
     "bfibm_batch_slot_ms": [_V, C.c_int32, C.POINTER(C.c_float)],
     "bfibm_batch_destroy": [_V],
+    "bfibm_batch_set_option": [_V, _i, _L],
+    "bfibm_batch_info": [_V, C.POINTER(_L)],
+    "bfibm_batch_sweep_shape": [_V, _i, _i, _IP],
+    "bfibm_batch_error": [_V],
 }
-_RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None, "bfibm_batch_destroy": None}
+_RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None, "bfibm_batch_destroy": None,
+        "bfibm_batch_error": C.c_char_p}
 
 _LIB = None
 
@@ -489,9 +495,11 @@ def load_instance(inst, stream=None, prm_override=None):
 
 
 class Batch:
-    """Independent contexts stepped together (see bfibm_batch_*)."""
+    """Independent contexts stepped together (see bfibm_batch_*). With
+    persistent=True the members step in lock step, each multigrid level of
+    their solves one launch over all of them (BFIBM_BATCH_PERSISTENT)."""
 
-    def __init__(self):
+    def __init__(self, persistent=False, tune=True):
         self.lib = lib()
         h = _V()
         st = self.lib.bfibm_batch_create(C.byref(h))
@@ -499,6 +507,35 @@ class Batch:
             raise BfibmError(st, "bfibm_batch_create")
         self.h = h
         self.members = {}
+        if persistent:
+            self.set_option(BATCH_PERSISTENT, 1)
+        if not tune:
+            self.set_option(BATCH_TUNE, 0)
+
+    def set_option(self, option, value):
+        st = self.lib.bfibm_batch_set_option(self.h, int(option), int(value))
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_set_option")
+
+    def info(self):
+        """dict of bfibm_batch_info's fields"""
+        out = (_L * 8)()
+        st = self.lib.bfibm_batch_info(self.h, out)
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_info")
+        keys = ("persistent", "builds", "members", "graph_kernels", "visc_body_kernels",
+                "p_body_kernels", "visc_iterations", "p_iterations")
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def sweep_shape(self, level, kind):
+        """(tile rows, chunk planes, planes per phase, threads per row, one
+        block per item, grid) of the plan's batched sweep; kind 0 viscous, 1
+        pressure"""
+        out = (C.c_int32 * 6)()
+        st = self.lib.bfibm_batch_sweep_shape(self.h, int(level), int(kind), out)
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_sweep_shape")
+        return tuple(int(v) for v in out)
 
     def add(self, ctx):
         slot = C.c_int32(-1)
@@ -525,7 +562,9 @@ class Batch:
             self._keep = a
         st = self.lib.bfibm_batch_step(self.h, arr)
         if st not in (OK, ENOCONV):
-            raise BfibmError(st, "bfibm_batch_step: " + self._member_errors())
+            msg = (self.lib.bfibm_batch_error(self.h) or b"").decode()
+            raise BfibmError(st, "bfibm_batch_step: " + "; ".join(
+                m for m in (msg, self._member_errors()) if m))
 
     def _member_errors(self):
         msgs = []

@@ -78,6 +78,91 @@ struct Scalars {
   double* out;       // 16 finalized scalars
 };
 
+// ------------------------------------------------------- batched launches
+// The block a kernel body works on: its coordinates and the extent of the
+// grid it belongs to. A single-instance kernel passes its own blockIdx and
+// gridDim; a batched kernel passes the block of one member's grid that an
+// item of its work list names. Partial sums are indexed by linear(), so a
+// member's reductions come out the same in a batch as alone.
+struct Blk {
+  int x, y, z, gx, gy, gz;
+  __device__ __forceinline__ int linear() const { return x + gx * (y + gy * z); }
+};
+__device__ __forceinline__ Blk own_blk() {
+  return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+             (int)gridDim.x,  (int)gridDim.y,  (int)gridDim.z};
+}
+
+// One item of a batched launch's work list: block (x, y, z) of the
+// gx x gy x gz grid the single-instance launch would use on member m.
+struct BItem {
+  int m;
+  unsigned short x, y, z, gx, gy, gz;
+};
+
+// One member of a persistent batch as the batched kernels see it.
+struct BMember {
+  Geo g[kMaxLevels];
+  LevelPtrs<float> f[kMaxLevels];
+  LevelPtrs<double> d[kMaxLevels];
+  int L;                    // levels
+  double inv_re;
+  double* vdiag[3];         // FP64 viscous diagonal (level 0)
+  double* cg_p[3];          // flexible-CG direction, A times it, preconditioned residual
+  double* cg_q[3];
+  double* cg_z[3];
+  Scalars sc;
+  int* cycles;              // device-loop iterations of the last solves (viscous, pressure)
+  long long* total;         // device-loop iterations so far (viscous, pressure)
+  int* nonconv;             // solves stopped above their tolerance
+  double rtol;
+  int maxc;                 // outer iterations of a solve at most
+  double dscale, div_tol;   // the pressure loop's second test: dscale max |r_p| <= div_tol
+  int coarse_sweeps;
+};
+
+// What every batched kernel takes: its work list, the member table, the mask
+// of members whose solve is still iterating (null: every member), the level,
+// and which buffer holds each current iterate (bit e: u_e is in u2[e]; bit 3:
+// p is in p2), as the out-of-place sweeps leave them.
+struct BArgs {
+  const BItem* items;
+  int n;
+  const BMember* tab;
+  const int* act;
+  int lev;
+  int cur;
+};
+
+// The persistent loop of a batched kernel: the launch's blocks stride over
+// the work list; a masked member's items are skipped. The barrier after each
+// item lets the next one reuse shared memory.
+template <class F>
+__device__ __forceinline__ void for_items(const BArgs& A, F&& f) {
+  for (int w = blockIdx.x; w < A.n; w += gridDim.x) {
+    const BItem it = A.items[w];
+    if (A.act && !A.act[it.m]) continue;
+    f(A.tab[it.m], Blk{it.x, it.y, it.z, it.gx, it.gy, it.gz});
+    __syncthreads();
+  }
+}
+
+// a member's FP32 arrays of one level with the current iterates in front
+__device__ __forceinline__ LevelPtrs<float> cur_ptrs(const LevelPtrs<float>& in, int cur) {
+  LevelPtrs<float> L = in;
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+    if ((cur >> e) & 1) {
+      L.u[e] = in.u2[e];
+      L.u2[e] = in.u[e];
+    }
+  if ((cur >> 3) & 1) {
+    L.p = in.p2;
+    L.p2 = in.p;
+  }
+  return L;
+}
+
 // ---------------------------------------------------------------- stencil.cu
 // Pressure: one colour of red-black Gauss-Seidel for D.(beta D p) = f.
 template <typename T>
@@ -175,6 +260,75 @@ void launch_finalize_sum(const double* partial, int nb, double* out, int slot, d
 cudaError_t coarse_set_smem();
 
 cudaError_t fused_set_carveout();
+
+// ------------------------------------------- batched kernels (3D, FP32 V-cycles)
+// One launch covers a level (or phase) of every member its work list names;
+// `grid` blocks stride over the list (for_items). Transfers take A.lev as the
+// fine level. Each does, per member, the arithmetic of the single-instance
+// launch it mirrors, on that launch's block decomposition.
+// stencil.cu
+void launch_b_v_residual32(const BArgs& A, int grid, cudaStream_t s);
+void launch_b_p_residual32(const BArgs& A, int grid, cudaStream_t s);
+void launch_b_restrict_face32(const BArgs& A, int d, int grid, cudaStream_t s);
+void launch_b_restrict_cell32(const BArgs& A, int grid, cudaStream_t s);
+void launch_b_prolong_face32(const BArgs& A, int d, int grid, cudaStream_t s);
+void launch_b_prolong_cell32(const BArgs& A, int grid, cudaStream_t s);
+// The coarsest level A.lev of each listed member (one item each): its FP32
+// right-hand side converted to FP64, the iterate zeroed, the FP64 coarse
+// solve, the result rounded to FP32. smem: the largest b_coarse_smem of the
+// members.
+void launch_b_coarse(const BArgs& A, bool viscous, size_t smem, cudaStream_t s);
+size_t b_coarse_smem(const Geo& g, bool viscous);
+cudaError_t b_coarse_set_smem();
+// level 0: per-block sums of uf . uf (viscous) or pf^2 into sc.partial
+void launch_b_norm2(const BArgs& A, bool viscous, int grid, cudaStream_t s);
+// level 0: the two passes of the pressure's mean removal around a finalize
+void launch_b_partial_sum_p(const BArgs& A, int grid, cudaStream_t s);
+void launch_b_sub_scalar_p(const BArgs& A, int grid, cudaStream_t s);
+// one item per member with gx = nb, the partials its producer wrote:
+// out[slot] = scale * (sum or max of partial[off nb .. off nb + nb)), scale
+// 1, or 1 / cells with `mean`
+void launch_b_finalize(const BArgs& A, int off, int slot, bool is_max, bool mean,
+                       cudaStream_t s);
+// Start of a batched solve: every member active, its loop counter (`which`:
+// 0 viscous, 1 pressure) zeroed and out[zero_slot] = 0 when zero_slot >= 0.
+void launch_b_begin(const BMember* tab, int nm, int* act, int which, int zero_slot,
+                    cudaStream_t s);
+// End of an iteration of a batched device loop: for each active member the
+// test of the single-instance loop (||r||/||f|| from out[sr], out[sf]; with
+// smax >= 0 also dscale out[smax] <= div_tol); a member that stops leaves the
+// mask; the loop runs again while any member is active.
+// iters[which] counts the loop's iterations.
+void launch_b_tol_check(cudaGraphConditionalHandle h, const BMember* tab, int nm, int* act,
+                        int which, int sf, int sr, int smax, long long* iters, cudaStream_t s);
+// counts in each member's nonconv the solves whose ||r||/||f|| exceeds slack rtol
+void launch_b_res_check(const BMember* tab, int nm, int sf, int sr, double slack,
+                        cudaStream_t s);
+// mixed.cu (level 0, FP64)
+void launch_b_v_residual_mixed(const BArgs& A, bool partial, bool r64, int grid, cudaStream_t s);
+void launch_b_p_residual_mixed(const BArgs& A, bool partial, int grid, cudaStream_t s);
+void launch_b_add_correction(const BArgs& A, bool viscous, int grid, cudaStream_t s);
+void launch_b_z_to_f64(const BArgs& A, int grid, cudaStream_t s);
+void launch_b_fcg_apply(const BArgs& A, int grid, cudaStream_t s);
+void launch_b_fcg_dir(const BArgs& A, int sl_zq, int sl_pq, int grid, cudaStream_t s);
+void launch_b_fcg_update(const BArgs& A, int sl_pq, int sl_pr, int grid, cudaStream_t s);
+// blocks of the single-instance launches the batched ones mirror: the 1D
+// reductions over n cells, the 3D launches (32 x 4 x 2 threads) over
+// nx x ny x nz points, the flat conversions over n elements
+int red_grid_of(long long n);
+dim3 stencil_grid3(long long nx, long long ny, long long nz);
+int flat_convert_blocks(long long n);
+// smooth.cu: one ring sweep of viscous component K (0..2) or the pressure
+// (K = 3) on level A.lev of every listed member, out of place (the output
+// buffer is the one A.cur marks as not current); TY rows, KC planes, NP
+// planes per phase, blocks of bx x (TY + 2) threads
+void launch_b_sweep(const BArgs& A, int K, int TY, int KC, int NP, int bx, size_t smem, int grid,
+                    cudaStream_t s);
+const void* b_sweep_kernel(int K, int NP);
+size_t b_sweep_smem(int NP, int TY, int W);
+// after an odd count of sweeps: the current iterate of kind K copied back to
+// its own buffer (items: flat blocks over the level's elements)
+void launch_b_copy_back(const BArgs& A, int K, int grid, cudaStream_t s);
 
 // ---------------------------------------------------------------- smooth_tma.cu
 // 3D FP32 red-black sweeps with TMA-staged inputs. Kind K: 0..2 viscous

@@ -63,9 +63,6 @@ inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
   return dim3((unsigned)((nx + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y),
               (unsigned)((nz + b.z - 1) / b.z));
 }
-__device__ __forceinline__ int block_linear() {
-  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-}
 
 // FP64 pressure residual written as the FP32 right-hand side of the
 // correction equation; the FP32 correction is zeroed; per-block partial sums
@@ -74,12 +71,12 @@ __device__ __forceinline__ int block_linear() {
 // NSdis4: max |D.u| = (euler dt / sigma) max |r|) in partial[nb .. 2 nb),
 // nb the launch's blocks; a non-finite residual counts as infinity.
 template <int D>
-__global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<double> L, float* r32,
-                                                          float* e32, double* partial) {
+__device__ __forceinline__ void p_residual_mixed_body(const Blk& B, Geo g, LevelPtrs<double> L,
+                                                      float* r32, float* e32, double* partial) {
   __shared__ double sh[32];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   double r2 = 0.0, ra = 0.0;
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
     int ci[3] = {i, j, k};
@@ -111,11 +108,17 @@ __global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<doubl
     r2 = block_sum(r2, sh);
     ra = block_max(ra, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
-      const int nb = gridDim.x * gridDim.y * gridDim.z;
-      partial[block_linear()] = r2;
-      partial[nb + block_linear()] = ra;
+      const int nb = B.gx * B.gy * B.gz;
+      partial[B.linear()] = r2;
+      partial[nb + B.linear()] = ra;
     }
   }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<double> L, float* r32,
+                                                          float* e32, double* partial) {
+  p_residual_mixed_body<D>(own_blk(), g, L, r32, e32, partial);
 }
 
 // Diagonal of the FP64 viscous operator of component d at face F:
@@ -250,13 +253,13 @@ __device__ __forceinline__ double v_res_any(const Geo& g, const LevelPtrs<double
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
-                                                          F32x3 e32, Ptr3d diag, double ir,
-                                                          double* partial, Ptr3d r64) {
+__device__ __forceinline__ void v_residual_mixed_body(const Blk& B, Geo g, LevelPtrs<double> L,
+                                                      F32x3 r32, F32x3 e32, Ptr3d diag, double ir,
+                                                      double* partial, Ptr3d r64) {
   __shared__ double sh[32];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   double r2 = 0.0;
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
     int ci[3] = {i, j, k};
@@ -277,16 +280,24 @@ __global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<doubl
   }
   if (partial) {
     r2 = block_sum(r2, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) partial[block_linear()] = r2;
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) partial[B.linear()] = r2;
   }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
+                                                          F32x3 e32, Ptr3d diag, double ir,
+                                                          double* partial, Ptr3d r64) {
+  v_residual_mixed_body<D>(own_blk(), g, L, r32, e32, diag, ir, partial, r64);
 }
 
 // x += e over the unknowns of ncomp face components (ncomp = 0: cells)
 template <int D>
-__global__ void __launch_bounds__(256) k_add_correction(Geo g, Ptr3d x, F32x3 e, int ncomp) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+__device__ __forceinline__ void add_correction_body(const Blk& B, Geo g, Ptr3d x, F32x3 e,
+                                                    int ncomp) {
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
   int ci[3] = {i, j, k};
   long long c = gidx(g, i, j, k);
@@ -296,6 +307,11 @@ __global__ void __launch_bounds__(256) k_add_correction(Geo g, Ptr3d x, F32x3 e,
   }
   for (int d = 0; d < ncomp; ++d)
     if (g.per[d] || ci[d] != 0) x.a[d][c] += (double)e.a[d][c];
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_add_correction(Geo g, Ptr3d x, F32x3 e, int ncomp) {
+  add_correction_body<D>(own_blk(), g, x, e, ncomp);
 }
 
 template <typename Tin, typename Tout>
@@ -387,13 +403,13 @@ __device__ __forceinline__ bool block_leader() {
 
 // w = A z on every unknown face (0 on the fixed wall faces); partial sums of z.q
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, Ptr3d z,
-                                                   Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
-                                                   double* partial) {
+__device__ __forceinline__ void fcg_apply_body(const Blk& B, Geo g, LevelPtrs<double> L, Ptr3d z,
+                                               Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
+                                               double* partial) {
   __shared__ double sh[32];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   double zq = 0.0;
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
     int ci[3] = {i, j, k};
@@ -411,7 +427,14 @@ __global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, P
     }
   }
   zq = block_sum(zq, sh);
-  if (block_leader()) partial[block_linear()] = zq;
+  if (block_leader()) partial[B.linear()] = zq;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, Ptr3d z,
+                                                   Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
+                                                   double* partial) {
+  fcg_apply_body<D>(own_blk(), g, L, z, diag, ir, w, q, partial);
 }
 
 // The direction and update passes touch every stored element of the level
@@ -421,9 +444,10 @@ constexpr int kFlatBlocks = 1216;   // 8 blocks of 256 threads per SM on 152 SMs
 
 // p = z + beta p, q = w + beta q; partial sums of p.q (first nb) and p.r (next nb)
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d w, Ptr3d p,
-                                                 Ptr3d q, Ptr3d r, const double* __restrict__ out,
-                                                 int sl_zq, int sl_pq, double* partial) {
+__device__ __forceinline__ void fcg_dir_body(const Blk& B, long long npair, Ptr3d z, Ptr3d w,
+                                             Ptr3d p, Ptr3d q, Ptr3d r,
+                                             const double* __restrict__ out, int sl_zq, int sl_pq,
+                                             double* partial) {
   __shared__ double sh[32];
   const double pq_old = out[sl_pq];
   // the first direction is z itself: the previous solve's p and q are not read
@@ -437,8 +461,8 @@ __global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d
     const double2* __restrict__ rr = reinterpret_cast<const double2*>(r.a[d]);
     double2* pp = reinterpret_cast<double2*>(p.a[d]);
     double2* qq = reinterpret_cast<double2*>(q.a[d]);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < npair;
-         k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = B.x * (long long)blockDim.x + threadIdx.x; k < npair;
+         k += (long long)B.gx * blockDim.x) {
       double2 zv = zz[k], wv = ww[k], rv = rr[k], pv = zv, qv = wv;
       if (!first) {
         const double2 po = pp[k], qo = qq[k];
@@ -456,18 +480,25 @@ __global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d
   pq = block_sum(pq, sh);
   pr = block_sum(pr, sh);
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = pq;
-    partial[gridDim.x + blockIdx.x] = pr;
+    partial[B.x] = pq;
+    partial[B.gx + B.x] = pr;
   }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_fcg_dir(long long npair, Ptr3d z, Ptr3d w, Ptr3d p,
+                                                 Ptr3d q, Ptr3d r, const double* __restrict__ out,
+                                                 int sl_zq, int sl_pq, double* partial) {
+  fcg_dir_body<D>(own_blk(), npair, z, w, p, q, r, out, sl_zq, sl_pq, partial);
 }
 
 // x += alpha p, r -= alpha q; the new residual as the FP32 right-hand side of
 // the next preconditioning (correction zeroed); partial sums of r.r
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_update(long long npair, Ptr3d x, Ptr3d p, Ptr3d q,
-                                                    Ptr3d r, F32x3 r32, F32x3 e32,
-                                                    const double* __restrict__ out, int sl_pq,
-                                                    int sl_pr, double* partial) {
+__device__ __forceinline__ void fcg_update_body(const Blk& B, long long npair, Ptr3d x, Ptr3d p,
+                                                Ptr3d q, Ptr3d r, F32x3 r32, F32x3 e32,
+                                                const double* __restrict__ out, int sl_pq,
+                                                int sl_pr, double* partial) {
   __shared__ double sh[32];
   const double pq = out[sl_pq];
   const double alpha = pq != 0.0 ? out[sl_pr] / pq : 0.0;
@@ -480,8 +511,8 @@ __global__ void __launch_bounds__(256) k_fcg_update(long long npair, Ptr3d x, Pt
     double2* rr = reinterpret_cast<double2*>(r.a[d]);
     float2* r2 = reinterpret_cast<float2*>(r32.a[d]);
     float2* e2 = reinterpret_cast<float2*>(e32.a[d]);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < npair;
-         k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = B.x * (long long)blockDim.x + threadIdx.x; k < npair;
+         k += (long long)B.gx * blockDim.x) {
       double2 xv = xx[k], pv = pp[k], qv = qq[k], rv = rr[k];
       xv.x += alpha * pv.x;
       xv.y += alpha * pv.y;
@@ -495,7 +526,15 @@ __global__ void __launch_bounds__(256) k_fcg_update(long long npair, Ptr3d x, Pt
     }
   }
   rs = block_sum(rs, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = rs;
+  if (threadIdx.x == 0) partial[B.x] = rs;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_fcg_update(long long npair, Ptr3d x, Ptr3d p, Ptr3d q,
+                                                    Ptr3d r, F32x3 r32, F32x3 e32,
+                                                    const double* __restrict__ out, int sl_pq,
+                                                    int sl_pr, double* partial) {
+  fcg_update_body<D>(own_blk(), npair, x, p, q, r, r32, e32, out, sl_pq, sl_pr, partial);
 }
 
 namespace {
@@ -523,7 +562,7 @@ void launch_fcg_apply(int D, const Geo& g, const LevelPtrs<double>& L, double* c
 
 // flat loops run over pairs: the level arrays hold an even number of
 // elements (rows padded to a multiple of 8) and start on 256-byte boundaries
-long long flat_elems(const Geo& g) { return g.st[2] * g.s[2]; }
+__host__ __device__ long long flat_elems(const Geo& g) { return g.st[2] * g.s[2]; }
 
 int fcg_flat_blocks(const Geo& g) {
   long long npair = flat_elems(g) / 2;
@@ -582,17 +621,11 @@ void launch_add_correction(int D, const Geo& g, double* const x[3], float* const
 }
 
 void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s) {
-  long long nb = (n + kBlock1D - 1) / kBlock1D;
-  if (nb > 4096) nb = 4096;
-  if (nb < 1) nb = 1;
-  k_convert<float, double><<<(unsigned)nb, kBlock1D, 0, s>>>(in, out, n);
+  k_convert<float, double><<<(unsigned)flat_convert_blocks(n), kBlock1D, 0, s>>>(in, out, n);
 }
 
 void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s) {
-  long long nb = (n + kBlock1D - 1) / kBlock1D;
-  if (nb > 4096) nb = 4096;
-  if (nb < 1) nb = 1;
-  k_convert<double, float><<<(unsigned)nb, kBlock1D, 0, s>>>(in, out, n);
+  k_convert<double, float><<<(unsigned)flat_convert_blocks(n), kBlock1D, 0, s>>>(in, out, n);
 }
 
 void launch_v_idg32(int D, const Geo& g, const LevelPtrs<double>& L64,
@@ -625,6 +658,133 @@ void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
   long long nb = (n + kBlock1D - 1) / kBlock1D;
   if (nb > 4096) nb = 4096;
   k_convert_list<<<(unsigned)nb, kBlock1D, 0, s>>>(cl, n);
+}
+
+// ------------------------------------------------------------------ batched
+// The level-0 FP64 steps of the batched solves: the bodies above over a
+// persistent batch's work list, each with a member's own arrays, scalars and
+// the block decomposition of its single-instance launch.
+__global__ void __launch_bounds__(256) kb_v_residual_mixed(BArgs A, int with_partial, int with_r64) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const Geo g = M.g[0];
+    F32x3 r, e;
+    Ptr3d dg, rr;
+    for (int d = 0; d < 3; ++d) {
+      r.a[d] = M.f[0].uf[d];
+      e.a[d] = M.f[0].u[d];
+      dg.a[d] = M.vdiag[d];
+      rr.a[d] = with_r64 ? M.d[0].ur[d] : nullptr;
+    }
+    v_residual_mixed_body<3>(B, g, M.d[0], r, e, dg, M.inv_re / (g.h * g.h),
+                             with_partial ? M.sc.partial : nullptr, rr);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_p_residual_mixed(BArgs A, int with_partial) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    p_residual_mixed_body<3>(B, M.g[0], M.d[0], M.f[0].pf, M.f[0].p,
+                             with_partial ? M.sc.partial : nullptr);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_add_correction(BArgs A, int viscous) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    Ptr3d x;
+    F32x3 e;
+    for (int d = 0; d < 3; ++d) {
+      x.a[d] = viscous ? M.d[0].u[d] : (d == 0 ? M.d[0].p : nullptr);
+      e.a[d] = viscous ? M.f[0].u[d] : (d == 0 ? M.f[0].p : nullptr);
+    }
+    add_correction_body<3>(B, M.g[0], x, e, viscous ? 3 : 0);
+  });
+}
+
+// z = the V-cycle's FP32 result in FP64, on every stored element
+__global__ void __launch_bounds__(256) kb_z_to_f64(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const long long n = flat_elems(M.g[0]);
+    for (int d = 0; d < 3; ++d) {
+      const float* __restrict__ in = M.f[0].u[d];
+      double* __restrict__ out = M.cg_z[d];
+      for (long long q = B.x * (long long)blockDim.x + threadIdx.x; q < n;
+           q += (long long)B.gx * blockDim.x)
+        out[q] = (double)in[q];
+    }
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_fcg_apply(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const Geo g = M.g[0];
+    Ptr3d z, dg, w, q;
+    for (int d = 0; d < 3; ++d) {
+      z.a[d] = M.cg_z[d];
+      dg.a[d] = M.vdiag[d];
+      w.a[d] = M.d[0].u2[d];
+      q.a[d] = M.cg_q[d];
+    }
+    fcg_apply_body<3>(B, g, M.d[0], z, dg, M.inv_re / (g.h * g.h), w, q, M.sc.partial);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_fcg_dir(BArgs A, int sl_zq, int sl_pq) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    Ptr3d z, w, p, q, r;
+    for (int d = 0; d < 3; ++d) {
+      z.a[d] = M.cg_z[d];
+      w.a[d] = M.d[0].u2[d];
+      p.a[d] = M.cg_p[d];
+      q.a[d] = M.cg_q[d];
+      r.a[d] = M.d[0].ur[d];
+    }
+    fcg_dir_body<3>(B, flat_elems(M.g[0]) / 2, z, w, p, q, r, M.sc.out, sl_zq, sl_pq,
+                    M.sc.partial);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_fcg_update(BArgs A, int sl_pq, int sl_pr) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    Ptr3d x, p, q, r;
+    F32x3 r32, e32;
+    for (int d = 0; d < 3; ++d) {
+      x.a[d] = M.d[0].u[d];
+      p.a[d] = M.cg_p[d];
+      q.a[d] = M.cg_q[d];
+      r.a[d] = M.d[0].ur[d];
+      r32.a[d] = M.f[0].uf[d];
+      e32.a[d] = M.f[0].u[d];
+    }
+    fcg_update_body<3>(B, flat_elems(M.g[0]) / 2, x, p, q, r, r32, e32, M.sc.out, sl_pq, sl_pr,
+                       M.sc.partial);
+  });
+}
+
+int flat_convert_blocks(long long n) {
+  long long nb = (n + kBlock1D - 1) / kBlock1D;
+  if (nb > 4096) nb = 4096;
+  return (int)(nb < 1 ? 1 : nb);
+}
+
+void launch_b_v_residual_mixed(const BArgs& A, bool partial, bool r64, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_v_residual_mixed<<<grid, blk3(3), 0, s>>>(A, partial ? 1 : 0, r64 ? 1 : 0);
+}
+void launch_b_p_residual_mixed(const BArgs& A, bool partial, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_p_residual_mixed<<<grid, blk3(3), 0, s>>>(A, partial ? 1 : 0);
+}
+void launch_b_add_correction(const BArgs& A, bool viscous, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_add_correction<<<grid, blk3(3), 0, s>>>(A, viscous ? 1 : 0);
+}
+void launch_b_z_to_f64(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_z_to_f64<<<grid, kBlock1D, 0, s>>>(A);
+}
+void launch_b_fcg_apply(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_fcg_apply<<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_fcg_dir(const BArgs& A, int sl_zq, int sl_pq, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_fcg_dir<<<grid, 256, 0, s>>>(A, sl_zq, sl_pq);
+}
+void launch_b_fcg_update(const BArgs& A, int sl_pq, int sl_pr, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_fcg_update<<<grid, 256, 0, s>>>(A, sl_pq, sl_pr);
 }
 
 }  // namespace bf

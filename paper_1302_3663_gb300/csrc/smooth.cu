@@ -149,15 +149,15 @@ __device__ __forceinline__ int add_mod(int s, int o, int R) {
 }
 
 template <int D, typename T, int NP>
-__global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* __restrict__ out,
-                                                     int TY, int KC) {
+__device__ __forceinline__ void p_rb_fused_body(const Blk& B, Geo g, LevelPtrs<T> L,
+                                                T* __restrict__ out, int TY, int KC) {
   constexpr int RA = Ax<D>::R, SA = Ax<D>::S, RING = Ax<D>::RING;
   constexpr int R = NP + 2;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   Ring<T> rg{reinterpret_cast<T*>(sm_raw), TY + 2 * RING, g.s[0]};
   const int n0 = g.n[0], nR = g.n[RA], nS = g.n[SA];
-  const int j0 = blockIdx.x * TY;
-  const int k0 = blockIdx.y * KC;
+  const int j0 = B.x * TY;
+  const int k0 = B.y * KC;
   const int k1 = min(k0 + KC, nS);
   const int r = threadIdx.y;
   const int j = j0 + r - RING;
@@ -235,6 +235,12 @@ __global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* _
     kw += NP;
     if (g.per[SA] && kw >= nS) kw -= nS;
   }
+}
+
+template <int D, typename T, int NP>
+__global__ void __launch_bounds__(1024) k_p_rb_fused(Geo g, LevelPtrs<T> L, T* __restrict__ out,
+                                                     int TY, int KC) {
+  p_rb_fused_body<D, T, NP>(own_blk(), g, L, out, TY, KC);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,15 +362,15 @@ __device__ __forceinline__ T v_black(const LevelPtrs<T>& L, const Ring<T>& rg, c
 }
 
 template <int D, int d, typename T, int NP>
-__global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* __restrict__ out,
-                                                     int TY, int KC, T ir) {
+__device__ __forceinline__ void v_rb_fused_body(const Blk& B, Geo g, LevelPtrs<T> L,
+                                                T* __restrict__ out, int TY, int KC, T ir) {
   constexpr int RA = Ax<D>::R, SA = Ax<D>::S, RING = Ax<D>::RING;
   constexpr int R = NP + 2;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   Ring<T> rg{reinterpret_cast<T*>(sm_raw), TY + 2 * RING, g.s[0]};
   const int n0 = g.n[0], nR = g.n[RA], nS = g.n[SA];
-  const int j0 = blockIdx.x * TY;
-  const int k0 = blockIdx.y * KC;
+  const int j0 = B.x * TY;
+  const int k0 = B.y * KC;
   const int k1 = min(k0 + KC, nS);
   const int r = threadIdx.y;
   const int j = j0 + r - RING;
@@ -443,6 +449,12 @@ __global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* _
     kw += NP;
     if (g.per[SA] && kw >= nS) kw -= nS;
   }
+}
+
+template <int D, int d, typename T, int NP>
+__global__ void __launch_bounds__(1024) k_v_rb_fused(Geo g, LevelPtrs<T> L, T* __restrict__ out,
+                                                     int TY, int KC, T ir) {
+  v_rb_fused_body<D, d, T, NP>(own_blk(), g, L, out, TY, KC, ir);
 }
 
 // ---------------------------------------------------------------------------
@@ -837,6 +849,41 @@ struct FusedShape {
   size_t smem;
 };
 
+// ---------------------------------------------------------------------------
+// Batched ring sweep: the one-pass sweep above over a persistent batch's work
+// list. Each item is a (row tile, plane chunk) block of one member's level;
+// the ring is sized for the widest member's rows. K 0..2: viscous component,
+// 3: pressure. The output is the buffer that A.cur marks as not current.
+// ---------------------------------------------------------------------------
+template <int K, int NP>
+__global__ void __launch_bounds__(1024) kb_sweep(BArgs A, int TY, int KC) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const Geo g = M.g[A.lev];
+    const LevelPtrs<float> L = cur_ptrs(M.f[A.lev], A.cur);
+    if constexpr (K == 3) {
+      p_rb_fused_body<3, float, NP>(B, g, L, L.p2, TY, KC);
+    } else {
+      const float ir = (float)(M.inv_re / (g.h * g.h));
+      v_rb_fused_body<3, K, float, NP>(B, g, L, L.u2[K], TY, KC, ir);
+    }
+  });
+}
+
+// after an odd count of sweeps the current iterate (in the second buffer) is
+// copied to its own buffer, on every stored element
+template <int K>
+__global__ void __launch_bounds__(256) kb_copy_back(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const Geo& g = M.g[A.lev];
+    const long long n = g.st[2] * g.s[2];
+    const float* __restrict__ src = K == 3 ? M.f[A.lev].p2 : M.f[A.lev].u2[K];
+    float* __restrict__ dst = K == 3 ? M.f[A.lev].p : M.f[A.lev].u[K];
+    for (long long q = B.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)B.gx * blockDim.x)
+      dst[q] = src[q];
+  });
+}
+
 // Tile rows TYo, chunk planes KCo and threads per row BXo (3D) come from the
 // autotuner when it has timed this level shape; 0 selects the built-in
 // heuristic. A row of fewer threads than point pairs has each thread update
@@ -1004,6 +1051,11 @@ cudaError_t fused_set_carveout() {
   set((const void*)k_v_rb_fused<3, 2, double, 2>);
   set((const void*)k_v_rb_fused<2, 0, double, 1>);
   set((const void*)k_v_rb_fused<2, 1, double, 1>);
+  for (int K = 0; K < 4; ++K)
+    for (int NP = 1; NP <= 2; ++NP)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(b_sweep_kernel(K, NP),
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 50);
   // the pair sweeps keep most of the unified storage as L1: their row loads
   // are reused by neighbouring rows and by the next plane
   for (int d = 0; d < 3; ++d)
@@ -1037,6 +1089,36 @@ int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int BX, int waves) 
   if (chunks < 1) return 0;
   int KC = (int)((g.n[2] + chunks - 1) / chunks);
   return KC < 2 ? 2 : KC;
+}
+
+const void* b_sweep_kernel(int K, int NP) {
+  if (NP == 2)
+    return K == 0 ? (const void*)kb_sweep<0, 2>
+                  : K == 1 ? (const void*)kb_sweep<1, 2>
+                           : K == 2 ? (const void*)kb_sweep<2, 2> : (const void*)kb_sweep<3, 2>;
+  return K == 0 ? (const void*)kb_sweep<0, 1>
+                : K == 1 ? (const void*)kb_sweep<1, 1>
+                         : K == 2 ? (const void*)kb_sweep<2, 1> : (const void*)kb_sweep<3, 1>;
+}
+
+size_t b_sweep_smem(int NP, int TY, int W) {
+  return (size_t)(NP + 2) * (TY + 2) * W * sizeof(float);
+}
+
+void launch_b_sweep(const BArgs& A, int K, int TY, int KC, int NP, int bx, size_t smem, int grid,
+                    cudaStream_t s) {
+  if (A.n <= 0) return;
+  const dim3 block(bx, TY + 2, 1);
+  void* args[] = {(void*)&A, (void*)&TY, (void*)&KC};
+  cudaLaunchKernel(b_sweep_kernel(K, NP == 2 ? 2 : 1), dim3(grid), block, args, smem, s);
+}
+
+void launch_b_copy_back(const BArgs& A, int K, int grid, cudaStream_t s) {
+  if (A.n <= 0) return;
+  if (K == 0) kb_copy_back<0><<<grid, 256, 0, s>>>(A);
+  else if (K == 1) kb_copy_back<1><<<grid, 256, 0, s>>>(A);
+  else if (K == 2) kb_copy_back<2><<<grid, 256, 0, s>>>(A);
+  else kb_copy_back<3><<<grid, 256, 0, s>>>(A);
 }
 
 size_t fused_smem_bytes(int D, const Geo& g, int elem) {

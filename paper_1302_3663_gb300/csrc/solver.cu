@@ -204,6 +204,8 @@ struct bfibm_ctx {
   int cycles_visc = 0, cycles_p = 0;
   int loop_inner[2] = {1, 1};    // V-cycles per device-loop iteration (visc, p) when captured
   long long graph_kernels = -1;   // kernel nodes in the captured step graph
+  long long version = 0;          // bumped whenever the step graph is dropped: a batch plan
+                                  // built on this context is then rebuilt
   long long partial_cap = 0;      // doubles in sc.partial
   std::string err;
 };
@@ -234,6 +236,7 @@ bfibm_status cuda_fail(bfibm_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 void drop_graph(bfibm_ctx* c) {
+  ++c->version;
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
@@ -1111,6 +1114,606 @@ cudaError_t dmalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
+// ---------------------------------------------------------- persistent batch
+// A batch in persistent mode steps its members in lock step, one CUDA graph
+// per batch step. Inside it every level and phase of the mixed-precision
+// solves (sweeps, residuals, transfers, coarsest solves, the FP64 level-0
+// steps and reductions) is one launch over a device work list of (member,
+// block) items, so members of different sizes share each launch; a block
+// of a launch strides over the list. Each solve's device loop runs while any
+// member still iterates: a member whose test is met leaves the mask that
+// every launch of the loop reads, so it stops where it would stop alone. The
+// stages around the solves (right-hand side, divergence, projection, nodes,
+// springs, spread, coefficients) run per member on forked branches of the
+// same graph. Per member the arithmetic, the block decompositions of the
+// reductions and the tests are those of its own step graph, so results come
+// out bit-identical to the member stepped alone.
+struct PList {
+  BItem* dev = nullptr;
+  int n = 0;
+  int grid = 0;   // blocks of a 256-thread launch over the list
+};
+
+struct PShape {   // a batched ring sweep: rows, chunk planes, planes per phase, threads per row
+  int TY = 4, KC = 8, NP = 1, bx = 32;
+  int all = 0;    // 1: one block per item; 0: the resident blocks stride over the items
+  size_t smem = 0;
+  int grid = 0;
+};
+
+struct Persist {
+  std::vector<bfibm_ctx*> mem;       // table order: level-0 cells descending
+  std::vector<long long> version;    // the members' versions the plan was built for
+  BMember* tab = nullptr;
+  int* act = nullptr;                // the mask of the solve being run
+  long long* iters = nullptr;        // batch device-loop iterations so far (viscous, pressure)
+  int depth = 0;                     // levels of the deepest member
+  int nu1 = 2, nu2 = 2, inner = 1, krylov = 0;
+  // per level l: the members that smooth on l (l below their coarsest level)
+  PList swv[kMaxLevels], swp[kMaxLevels];   // ring-sweep blocks (viscous, pressure shape)
+  PShape shv[kMaxLevels], shp[kMaxLevels];
+  PList en[kMaxLevels];   // 3D blocks over the cells of l: residuals, prolongations
+  PList rs[kMaxLevels];   // over the stored faces of l + 1: face restriction
+  PList rn[kMaxLevels];   // over the cells of l + 1: cell restriction
+  PList fl[kMaxLevels];   // flat blocks over the elements of l: copies after odd sweep counts
+  PList co[kMaxLevels];   // one item per member whose coarsest level is l
+  size_t co_smem[kMaxLevels][2] = {};
+  // level 0, every member
+  PList a3, ared, aflat, aconv;      // 3D, cell reductions, flat CG passes, conversions
+  PList fin3, finred, finflat;       // one item per member, gx = its producer's blocks
+  bool masked = false;               // queuing the body of a device loop
+  cudaStream_t stream = nullptr, aux = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_kernels = 0, body_kernels[2] = {0, 0};
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+void persist_free(Persist* P) {
+  if (!P) return;
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  for (void* a : P->allocs) cudaFree(a);
+  for (cudaEvent_t e : P->join) cudaEventDestroy(e);
+  if (P->fork) cudaEventDestroy(P->fork);
+  if (P->done) cudaEventDestroy(P->done);
+  if (P->aux) cudaStreamDestroy(P->aux);
+  if (P->stream) cudaStreamDestroy(P->stream);
+  cudaGetLastError();
+  delete P;
+}
+
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  return n;
+}
+
+// Items of the members `use` accepts, each member's blocks in the order
+// x, y, z; `grid_of(member)` gives the block grid its single-instance launch
+// would use.
+template <class Use, class Grid>
+bool make_items(int nm, Use use, Grid grid_of, std::vector<BItem>& v) {
+  v.clear();
+  for (int m = 0; m < nm; ++m) {
+    if (!use(m)) continue;
+    const dim3 gr = grid_of(m);
+    if (gr.x > 65535u || gr.y > 65535u || gr.z > 65535u) return false;
+    for (unsigned z = 0; z < gr.z; ++z)
+      for (unsigned y = 0; y < gr.y; ++y)
+        for (unsigned x = 0; x < gr.x; ++x)
+          v.push_back(BItem{m, (unsigned short)x, (unsigned short)y, (unsigned short)z,
+                            (unsigned short)gr.x, (unsigned short)gr.y, (unsigned short)gr.z});
+  }
+  return true;
+}
+
+cudaError_t upload(Persist& P, const std::vector<BItem>& v, PList& L) {
+  L.n = (int)v.size();
+  L.dev = nullptr;
+  L.grid = 0;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)&L.dev, v.size() * sizeof(BItem));
+  if (e != cudaSuccess) return e;
+  P.allocs.push_back(L.dev);
+  const int cap = device_sms() * 8;   // 256-thread blocks resident per SM
+  L.grid = L.n < cap ? L.n : cap;
+  return cudaMemcpy(L.dev, v.data(), v.size() * sizeof(BItem), cudaMemcpyHostToDevice);
+}
+
+long long cells_of(const Geo& g) { return (long long)g.n[0] * g.n[1] * g.n[2]; }
+
+// The sweep items of level l for a shape, and the launch's grid and shared memory.
+cudaError_t sweep_list(Persist& P, int l, int K, PShape& sh, PList& L) {
+  const int nm = (int)P.mem.size();
+  int W = 0;
+  for (int m = 0; m < nm; ++m)
+    if (l < P.mem[m]->L - 1) W = std::max(W, P.mem[m]->lev[l].g.s[0]);
+  sh.smem = b_sweep_smem(sh.NP, sh.TY, W);
+  std::vector<BItem> v;
+  make_items(nm, [&](int m) { return l < P.mem[m]->L - 1; },
+             [&](int m) {
+               const Geo& g = P.mem[m]->lev[l].g;
+               return dim3((g.n[1] + sh.TY - 1) / sh.TY, (g.n[2] + sh.KC - 1) / sh.KC, 1);
+             }, v);
+  if (L.dev) {
+    cudaFree(L.dev);
+    P.allocs.erase(std::remove(P.allocs.begin(), P.allocs.end(), (void*)L.dev), P.allocs.end());
+  }
+  cudaError_t e = upload(P, v, L);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_sweep_kernel(K, sh.NP),
+                                                    sh.bx * (sh.TY + 2), sh.smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int cap = device_sms() * std::max(per_sm, 1);
+  sh.grid = sh.all || L.n < cap ? L.n : cap;
+  return cudaSuccess;
+}
+
+// The built-in sweep shape of level l: one thread per point pair of the
+// widest member's rows (at most 128), 4 rows, chunks giving about three
+// blocks per SM.
+PShape default_shape(const Persist& P, int l) {
+  PShape sh;
+  int np = 1, nR = 1 << 30;
+  long long tiles = 0;
+  for (bfibm_ctx* c : P.mem)
+    if (l < c->L - 1) {
+      const Geo& g = c->lev[l].g;
+      np = std::max(np, (g.n[0] + 1) / 2);
+      nR = std::min(nR, g.n[1]);
+    }
+  sh.bx = std::min(128, (np + 31) / 32 * 32);
+  sh.TY = std::max(1, std::min(4, nR));
+  for (bfibm_ctx* c : P.mem)
+    if (l < c->L - 1) tiles += (long long)((c->lev[l].g.n[1] + sh.TY - 1) / sh.TY) * c->lev[l].g.n[2];
+  long long KC = tiles / (3LL * device_sms());
+  sh.KC = (int)std::max(4LL, std::min(16LL, KC));
+  return sh;
+}
+
+BArgs bargs(const Persist& P, const PList& L, int lev, int cur = 0) {
+  return BArgs{L.dev, L.n, P.tab, P.masked ? P.act : nullptr, lev, cur};
+}
+
+// Time the candidate shapes of the batched sweep of kind K (component x for
+// the viscous shape, the pressure for its own) on level l and keep the
+// fastest; the sweeps are out of place, so only the second buffers change.
+cudaError_t tune_level(Persist& P, int l, int K) {
+  PShape& best = K == 3 ? P.shp[l] : P.shv[l];
+  PList& L = K == 3 ? P.swp[l] : P.swv[l];
+  cudaEvent_t e0, e1;
+  cudaError_t st = cudaEventCreate(&e0);
+  if (st != cudaSuccess) return st;
+  st = cudaEventCreate(&e1);
+  if (st != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return st;
+  }
+  float best_ms = 1e30f;
+  PShape keep = best;
+  for (int NP : {1, 2})
+    for (int TY : {2, 4, 6, 8})
+      for (int KC : {4, 8, 16, 32})
+        for (int all : {0, 1}) {
+          PShape sh = best;
+          sh.NP = NP;
+          sh.TY = TY;
+          sh.KC = KC;
+          sh.all = all;
+          if (sh.bx * (TY + 2) > 1024) continue;
+          st = sweep_list(P, l, K, sh, L);
+          if (st != cudaSuccess) break;
+          if (sh.smem > 48 * 1024) continue;
+          const BArgs A = bargs(P, L, l);
+          float t = 1e30f;
+          for (int round = 0; round < 3 && st == cudaSuccess; ++round) {
+            cudaEventRecord(e0, P.stream);
+            for (int r = 0; r < 3; ++r)
+              launch_b_sweep(A, K, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem, sh.grid, P.stream);
+            cudaEventRecord(e1, P.stream);
+            st = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (st == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            if (round > 0 && ms < t) t = ms;   // the first round warms up
+          }
+          if (st != cudaSuccess) break;
+          if (t < best_ms) {
+            best_ms = t;
+            keep = sh;
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != cudaSuccess) return st;
+  best = keep;
+  return sweep_list(P, l, K, best, L);
+}
+
+bool persist_compatible(const bfibm_ctx* a, const bfibm_ctx* c, std::string& why) {
+  if (c->D != 3 || c->P.precision != 1) why = "every member must be a 3D mixed-precision context";
+  else if (c->P.open_flow) why = "the open duct is not batched";
+  else if (c->P.vc_visc > 0 || c->P.vc_p > 0) why = "members must solve to a tolerance (vc_visc = vc_p = 0)";
+  else if ((uintptr_t)c->stream <= 2) why = "members need a stream of their own";
+  else if (a && (a->P.nu1 != c->P.nu1 || a->P.nu2 != c->P.nu2 || a->inner != c->inner ||
+                 a->krylov != c->krylov))
+    why = "members must share nu1, nu2, the inner cycle count and the viscous solver";
+  else return true;
+  return false;
+}
+
+// Builds the member table and the work lists (tuning the sweeps when asked).
+bfibm_status persist_build(Persist& P, bool tune) {
+  const int nm = (int)P.mem.size();
+  const bfibm_ctx* c0 = P.mem[0];
+  P.nu1 = c0->P.nu1;
+  P.nu2 = c0->P.nu2;
+  P.inner = c0->inner;
+  P.krylov = c0->krylov;
+  auto fail = [&](cudaError_t e, const char* where) {
+    cudaGetLastError();
+    P.err = std::string(where) + ": " + cudaGetErrorString(e);
+    return BFIBM_ECUDA;
+  };
+#define PK(call)                                     \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return fail(e_, #call);   \
+  } while (0)
+  // the tuner writes the members' second FP32 buffers: their queued work
+  // must be done first
+  for (bfibm_ctx* c : P.mem) PK(cudaStreamSynchronize(c->stream));
+  PK(cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking));
+  PK(cudaStreamCreateWithFlags(&P.aux, cudaStreamNonBlocking));
+  PK(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
+  PK(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
+  P.join.resize(nm, nullptr);
+  for (int m = 0; m < nm; ++m) PK(cudaEventCreateWithFlags(&P.join[m], cudaEventDisableTiming));
+  std::vector<BMember> host(nm);
+  P.depth = 0;
+  for (int m = 0; m < nm; ++m) {
+    bfibm_ctx* c = P.mem[m];
+    BMember& B = host[m];
+    std::memset(&B, 0, sizeof(B));
+    for (int l = 0; l < c->L; ++l) {
+      B.g[l] = c->lev[l].g;
+      B.f[l] = c->lev[l].f;
+      B.d[l] = c->lev[l].d;
+    }
+    B.L = c->L;
+    B.inv_re = c->P.inv_re;
+    for (int d = 0; d < 3; ++d) {
+      B.vdiag[d] = c->vdiag[d];
+      B.cg_p[d] = c->cg_p[d];
+      B.cg_q[d] = c->cg_q[d];
+      B.cg_z[d] = c->cg_z[d];
+    }
+    B.sc = c->sc;
+    B.cycles = c->dev_cycles;
+    B.total = c->loop_total;
+    B.nonconv = c->counters + 4;
+    B.rtol = c->P.rtol;
+    B.maxc = dc_iterations(c->P.max_cycles, c->inner);
+    B.dscale = div_scale(c);
+    B.div_tol = c->P.div_tol;
+    B.coarse_sweeps = c->P.coarse_sweeps;
+    P.depth = std::max(P.depth, c->L);
+  }
+  PK(cudaMalloc((void**)&P.tab, nm * sizeof(BMember)));
+  P.allocs.push_back(P.tab);
+  PK(cudaMemcpy(P.tab, host.data(), nm * sizeof(BMember), cudaMemcpyHostToDevice));
+  PK(cudaMalloc((void**)&P.act, nm * sizeof(int)));
+  P.allocs.push_back(P.act);
+  PK(cudaMemset(P.act, 0, nm * sizeof(int)));
+  PK(cudaMalloc((void**)&P.iters, 2 * sizeof(long long)));
+  P.allocs.push_back(P.iters);
+  PK(cudaMemset(P.iters, 0, 2 * sizeof(long long)));
+  PK(b_coarse_set_smem());
+  std::vector<BItem> v;
+  bool ok = true;   // every grid within the items' 16-bit block coordinates
+  auto lev = [&](int m, int l) -> const Geo& { return P.mem[m]->lev[l].g; };
+  for (int l = 0; l < P.depth; ++l) {
+    auto smooths = [&](int m) { return l < P.mem[m]->L - 1; };
+    ok &= make_items(nm, smooths, [&](int m) {
+      const Geo& g = lev(m, l);
+      return stencil_grid3(g.n[0], g.n[1], g.n[2]);
+    }, v);
+    PK(upload(P, v, P.en[l]));
+    ok &= make_items(nm, smooths, [&](int m) {
+      const Geo& g = lev(m, l + 1);
+      return stencil_grid3(g.s[0], g.s[1], g.s[2]);
+    }, v);
+    PK(upload(P, v, P.rs[l]));
+    ok &= make_items(nm, smooths, [&](int m) {
+      const Geo& g = lev(m, l + 1);
+      return stencil_grid3(g.n[0], g.n[1], g.n[2]);
+    }, v);
+    PK(upload(P, v, P.rn[l]));
+    ok &= make_items(nm, smooths, [&](int m) {
+      return dim3(flat_convert_blocks(level_elems(lev(m, l))), 1, 1);
+    }, v);
+    PK(upload(P, v, P.fl[l]));
+    ok &= make_items(nm, [&](int m) { return l == P.mem[m]->L - 1; },
+                     [&](int) { return dim3(1, 1, 1); }, v);
+    PK(upload(P, v, P.co[l]));
+    for (int vis = 0; vis < 2; ++vis) {
+      size_t mx = 0;
+      for (int m = 0; m < nm; ++m)
+        if (l == P.mem[m]->L - 1) mx = std::max(mx, b_coarse_smem(lev(m, l), vis != 0));
+      P.co_smem[l][vis] = mx;
+    }
+    P.shv[l] = default_shape(P, l);
+    P.shp[l] = P.shv[l];
+    PK(sweep_list(P, l, 0, P.shv[l], P.swv[l]));
+    PK(sweep_list(P, l, 3, P.shp[l], P.swp[l]));
+  }
+  auto all = [](int) { return true; };
+  ok &= make_items(nm, all, [&](int m) {
+    const Geo& g = lev(m, 0);
+    return stencil_grid3(g.n[0], g.n[1], g.n[2]);
+  }, v);
+  PK(upload(P, v, P.a3));
+  ok &= make_items(nm, all, [&](int m) { return dim3(red_grid_of(cells_of(lev(m, 0))), 1, 1); },
+                   v);
+  PK(upload(P, v, P.ared));
+  ok &= make_items(nm, all, [&](int m) { return dim3(fcg_flat_blocks(lev(m, 0)), 1, 1); }, v);
+  PK(upload(P, v, P.aflat));
+  ok &= make_items(nm, all, [&](int m) {
+    return dim3(flat_convert_blocks(level_elems(lev(m, 0))), 1, 1);
+  }, v);
+  PK(upload(P, v, P.aconv));
+  auto one_per = [&](auto nb_of) {
+    v.clear();
+    for (int m = 0; m < nm; ++m)
+      v.push_back(BItem{m, 0, 0, 0, (unsigned short)nb_of(m), 1, 1});
+  };
+  one_per([&](int m) { return red_blocks_3d(3, lev(m, 0)); });
+  PK(upload(P, v, P.fin3));
+  one_per([&](int m) { return red_grid_of(cells_of(lev(m, 0))); });
+  PK(upload(P, v, P.finred));
+  one_per([&](int m) { return fcg_flat_blocks(lev(m, 0)); });
+  PK(upload(P, v, P.finflat));
+  if (!ok) {
+    P.err = "a member's grid has more than 65535 blocks along an axis";
+    return BFIBM_EINVAL;
+  }
+  if (tune) {
+    // levels of at least 2^19 cells in all are timed; smaller ones keep the
+    // built-in shape (a launch of a few microseconds cannot tell them apart)
+    for (int l = 0; l < P.depth; ++l) {
+      long long cells = 0;
+      for (int m = 0; m < nm; ++m)
+        if (l < P.mem[m]->L - 1) cells += cells_of(lev(m, l));
+      if (cells < (1LL << 19)) continue;
+      PK(tune_level(P, l, 0));
+      PK(tune_level(P, l, 3));
+    }
+  }
+#undef PK
+  return BFIBM_OK;
+}
+
+// n sweeps of the viscous components (or the pressure) on level l of every
+// member that smooths there; the current buffer of each iterate is tracked
+// here, as the single-instance path swaps its pointers, and an odd count
+// ends with a copy back.
+void b_smooth(Persist& P, int l, int n, bool V) {
+  int cur = 0;
+  for (int it = 0; it < n; ++it) {
+    if (V) {
+      for (int d = 0; d < 3; ++d) {
+        const PShape& sh = P.shv[l];
+        launch_b_sweep(bargs(P, P.swv[l], l, cur), d, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem, sh.grid,
+                       P.stream);
+        cur ^= 1 << d;
+      }
+    } else {
+      const PShape& sh = P.shp[l];
+      launch_b_sweep(bargs(P, P.swp[l], l, cur), 3, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem, sh.grid,
+                     P.stream);
+      cur ^= 8;
+    }
+  }
+  for (int K = 0; K < 4; ++K)
+    if ((cur >> K) & 1) launch_b_copy_back(bargs(P, P.fl[l], l), K, P.fl[l].grid, P.stream);
+}
+
+void b_vcycle(Persist& P, int l, bool V) {
+  cudaStream_t s = P.stream;
+  if (P.co[l].n) launch_b_coarse(bargs(P, P.co[l], l), V, P.co_smem[l][V ? 1 : 0], s);
+  if (!P.en[l].n) return;
+  b_smooth(P, l, P.nu1, V);
+  if (V) {
+    launch_b_v_residual32(bargs(P, P.en[l], l), P.en[l].grid, s);
+    for (int d = 0; d < 3; ++d) launch_b_restrict_face32(bargs(P, P.rs[l], l), d, P.rs[l].grid, s);
+  } else {
+    launch_b_p_residual32(bargs(P, P.en[l], l), P.en[l].grid, s);
+    launch_b_restrict_cell32(bargs(P, P.rn[l], l), P.rn[l].grid, s);
+  }
+  b_vcycle(P, l + 1, V);
+  if (V)
+    for (int d = 0; d < 3; ++d) launch_b_prolong_face32(bargs(P, P.en[l], l), d, P.en[l].grid, s);
+  else
+    launch_b_prolong_cell32(bargs(P, P.en[l], l), P.en[l].grid, s);
+  b_smooth(P, l, P.nu2, V);
+}
+
+// A device-side loop in the batch graph being captured on P.stream: a
+// conditional WHILE node whose body `body` queues (on P.stream, pointed at
+// the auxiliary stream meanwhile) with every launch masked.
+template <typename Body>
+bfibm_status p_capture_while(Persist& P, int which, Body body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  auto fail = [&](cudaError_t e, const char* where) {
+    cudaGetLastError();
+    P.err = std::string(where) + ": " + cudaGetErrorString(e);
+    return BFIBM_ECUDA;
+  };
+  cudaError_t e = cudaStreamGetCaptureInfo(P.stream, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return fail(e, "cudaStreamGetCaptureInfo");
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &np);
+  if (e != cudaSuccess) return fail(e, "cudaGraphAddNode");
+  e = cudaStreamUpdateCaptureDependencies(P.stream, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return fail(e, "cudaStreamUpdateCaptureDependencies");
+  cudaGraph_t bg = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(P.aux, bg, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(e, "cudaStreamBeginCaptureToGraph");
+  cudaStream_t main = P.stream;
+  P.stream = P.aux;
+  P.masked = true;
+  body(h);
+  P.masked = false;
+  P.stream = main;
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(P.aux, &out);
+  if (e != cudaSuccess) return fail(e, "cudaStreamEndCapture");
+  P.body_kernels[which] = count_kernel_nodes(bg);
+  return BFIBM_OK;
+}
+
+// The viscous solve of every member (Eq. NSdis1-1), as solve_v_fcg or
+// solve_v_mixed queue it in tolerance mode.
+bfibm_status b_solve_v(Persist& P) {
+  const int nm = (int)P.mem.size();
+  cudaStream_t s = P.stream;
+  launch_b_norm2(bargs(P, P.ared, 0), true, P.ared.grid, s);
+  launch_b_finalize(bargs(P, P.finred, 0), 0, SL_VF, false, false, s);
+  if (P.krylov) {
+    launch_b_v_residual_mixed(bargs(P, P.a3, 0), true, true, P.a3.grid, s);
+    launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_VR, false, false, s);
+    launch_b_begin(P.tab, nm, P.act, 0, SL_PQ, s);
+    bfibm_status st = p_capture_while(P, 0, [&](cudaGraphConditionalHandle h) {
+      cudaStream_t b = P.stream;
+      for (int q = 0; q < P.inner; ++q) b_vcycle(P, 0, true);
+      launch_b_z_to_f64(bargs(P, P.aconv, 0), P.aconv.grid, b);
+      launch_b_fcg_apply(bargs(P, P.a3, 0), P.a3.grid, b);
+      launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_ZQ, false, false, b);
+      launch_b_fcg_dir(bargs(P, P.aflat, 0), SL_ZQ, SL_PQ, P.aflat.grid, b);
+      launch_b_finalize(bargs(P, P.finflat, 0), 0, SL_PQ, false, false, b);
+      launch_b_finalize(bargs(P, P.finflat, 0), 1, SL_PRR, false, false, b);
+      launch_b_fcg_update(bargs(P, P.aflat, 0), SL_PQ, SL_PRR, P.aflat.grid, b);
+      launch_b_finalize(bargs(P, P.finflat, 0), 0, SL_VR, false, false, b);
+      launch_b_tol_check(h, P.tab, nm, P.act, 0, SL_VF, SL_VR, -1, P.iters, b);
+    });
+    if (st != BFIBM_OK) return st;
+    // the true FP64 residual of every member's final iterate, checked
+    launch_b_v_residual_mixed(bargs(P, P.a3, 0), true, false, P.a3.grid, s);
+    launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_VR, false, false, s);
+    launch_b_res_check(P.tab, nm, SL_VF, SL_VR, kTrueResidualSlack, s);
+    return BFIBM_OK;
+  }
+  launch_b_begin(P.tab, nm, P.act, 0, -1, s);
+  launch_b_v_residual_mixed(bargs(P, P.a3, 0), false, false, P.a3.grid, s);
+  return p_capture_while(P, 0, [&](cudaGraphConditionalHandle h) {
+    cudaStream_t b = P.stream;
+    for (int q = 0; q < P.inner; ++q) b_vcycle(P, 0, true);
+    launch_b_add_correction(bargs(P, P.a3, 0), true, P.a3.grid, b);
+    launch_b_v_residual_mixed(bargs(P, P.a3, 0), true, false, P.a3.grid, b);
+    launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_VR, false, false, b);
+    launch_b_tol_check(h, P.tab, nm, P.act, 0, SL_VF, SL_VR, -1, P.iters, b);
+  });
+}
+
+// The pressure solve of every member (Eq. NSdis3), as solve_p_mixed queues it
+// in tolerance mode.
+bfibm_status b_solve_p(Persist& P) {
+  const int nm = (int)P.mem.size();
+  cudaStream_t s = P.stream;
+  launch_b_norm2(bargs(P, P.ared, 0), false, P.ared.grid, s);
+  launch_b_finalize(bargs(P, P.finred, 0), 0, SL_PF, false, false, s);
+  launch_b_begin(P.tab, nm, P.act, 1, -1, s);
+  launch_b_p_residual_mixed(bargs(P, P.a3, 0), false, P.a3.grid, s);
+  return p_capture_while(P, 1, [&](cudaGraphConditionalHandle h) {
+    cudaStream_t b = P.stream;
+    for (int q = 0; q < P.inner; ++q) b_vcycle(P, 0, false);
+    launch_b_add_correction(bargs(P, P.a3, 0), false, P.a3.grid, b);
+    launch_b_partial_sum_p(bargs(P, P.ared, 0), P.ared.grid, b);
+    launch_b_finalize(bargs(P, P.finred, 0), 0, 0, false, true, b);
+    launch_b_sub_scalar_p(bargs(P, P.a3, 0), P.a3.grid, b);
+    launch_b_p_residual_mixed(bargs(P, P.a3, 0), true, P.a3.grid, b);
+    launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_PR, false, false, b);
+    launch_b_finalize(bargs(P, P.fin3, 0), 1, SL_PRMAX, true, false, b);
+    launch_b_tol_check(h, P.tab, nm, P.act, 1, SL_PF, SL_PR, SL_PRMAX, P.iters, b);
+  });
+}
+
+// Queues `stage` for every member on a branch of its own (its stream, forked
+// from and joined back into the batch stream).
+template <typename Stage>
+void fork_members(Persist& P, Stage stage) {
+  cudaEventRecord(P.fork, P.stream);
+  for (size_t m = 0; m < P.mem.size(); ++m) {
+    bfibm_ctx* c = P.mem[m];
+    cudaStreamWaitEvent(c->stream, P.fork, 0);
+    stage(c);
+    cudaEventRecord(P.join[m], c->stream);
+  }
+  for (size_t m = 0; m < P.mem.size(); ++m) cudaStreamWaitEvent(P.stream, P.join[m], 0);
+}
+
+// One batch step in the order of queue_step (Sec. 3.4), captured once.
+bfibm_status persist_capture(Persist& P) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    P.err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+    return BFIBM_ECUDA;
+  }
+  fork_members(P, [](bfibm_ctx* c) { stage_rhs(c); });
+  bfibm_status st = b_solve_v(P);
+  if (st == BFIBM_OK) {
+    fork_members(P, [](bfibm_ctx* c) { stage_divergence(c); });
+    st = b_solve_p(P);
+  }
+  if (st == BFIBM_OK)
+    fork_members(P, [](bfibm_ctx* c) {
+      stage_project(c);
+      stage_interp_advance(c);
+      launch_step_increment(c->step_dev, c->stream);
+      refresh(c);
+    });
+  e = cudaStreamEndCapture(P.stream, &graph);
+  if (st != BFIBM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e == cudaSuccess) {
+    P.graph_kernels = count_kernel_nodes(graph);
+    e = cudaGraphInstantiate(&P.gexec, graph, 0);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    P.err = std::string("batch graph: ") + cudaGetErrorString(e);
+    return BFIBM_ECUDA;
+  }
+  return BFIBM_OK;
+}
+
 }  // namespace
 
 // =========================================================================
@@ -1936,6 +2539,11 @@ struct bfibm_batch {
     bool timed = false;
   };
   std::vector<Slot> slots;
+  int persistent = 0;    // BFIBM_BATCH_PERSISTENT
+  int tune = 1;          // BFIBM_BATCH_TUNE
+  Persist* ps = nullptr; // the plan of the last persistent step
+  long long builds = 0;  // plans built
+  std::string err;
 };
 
 bfibm_status bfibm_batch_create(bfibm_batch** out) {
@@ -1975,8 +2583,134 @@ bfibm_status bfibm_batch_remove(bfibm_batch* b, int32_t slot) {
   return BFIBM_OK;
 }
 
+namespace {
+// The members stepped by nsteps in table order (level-0 cells descending),
+// with a plan built for exactly them, then n launches of its graph.
+bfibm_status persist_step(bfibm_batch* b, const int32_t* nsteps) {
+  std::vector<int> idx;
+  int n = -1;
+  for (size_t q = 0; q < b->slots.size(); ++q) {
+    bfibm_batch::Slot& s = b->slots[q];
+    if (!s.c) continue;
+    const int k = nsteps ? nsteps[q] : 1;
+    s.timed = false;
+    if (k <= 0) continue;
+    if (n >= 0 && k != n) {
+      b->err = "a persistent batch steps every member it steps the same number of steps";
+      return BFIBM_EINVAL;
+    }
+    n = k;
+    idx.push_back((int)q);
+  }
+  if (idx.empty()) return BFIBM_OK;
+  std::vector<bfibm_ctx*> mem;
+  for (int q : idx) {
+    bfibm_ctx* c = b->slots[q].c;
+    READY(c);
+    std::string why;
+    if (!persist_compatible(mem.empty() ? nullptr : mem[0], c, why)) {
+      b->err = why;
+      return BFIBM_EINVAL;
+    }
+    mem.push_back(c);
+  }
+  std::stable_sort(mem.begin(), mem.end(), [](const bfibm_ctx* x, const bfibm_ctx* y) {
+    return cells_of(x->lev[0].g) > cells_of(y->lev[0].g);
+  });
+  std::vector<long long> ver;
+  for (bfibm_ctx* c : mem) ver.push_back(c->version);
+  if (!b->ps || b->ps->mem != mem || b->ps->version != ver) {
+    persist_free(b->ps);
+    b->ps = new (std::nothrow) Persist();
+    if (!b->ps) return BFIBM_ENOMEM;
+    b->ps->mem = mem;
+    b->ps->version = ver;
+    bfibm_status st = persist_build(*b->ps, b->tune != 0);
+    if (st == BFIBM_OK) st = persist_capture(*b->ps);
+    if (st != BFIBM_OK) {
+      b->err = b->ps->err;
+      persist_free(b->ps);
+      b->ps = nullptr;
+      return st;
+    }
+    ++b->builds;
+  }
+  Persist& P = *b->ps;
+  for (size_t m = 0; m < mem.size(); ++m) {
+    bfibm_ctx* c = mem[m];
+    bfibm_status st = ensure_ready(c);
+    if (st != BFIBM_OK) return st;
+    CK(cudaEventRecord(P.join[m], c->stream));
+    CK(cudaStreamWaitEvent(P.stream, P.join[m], 0));
+  }
+  bfibm_ctx* c = mem[0];   // for the error path of CK
+  for (int q : idx) CK(cudaEventRecord(b->slots[q].e0, P.stream));
+  for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(P.gexec, P.stream));
+  for (int q : idx) {
+    CK(cudaEventRecord(b->slots[q].e1, P.stream));
+    b->slots[q].timed = true;
+  }
+  CK(cudaEventRecord(P.done, P.stream));
+  for (bfibm_ctx* m : mem) {
+    CK(cudaStreamWaitEvent(m->stream, P.done, 0));
+    m->step_host += n;
+    m->cycles_visc = m->cycles_p = -1;   // counted on the device
+    m->loop_inner[0] = m->loop_inner[1] = P.inner;
+  }
+  return BFIBM_OK;
+}
+}  // namespace
+
+bfibm_status bfibm_batch_set_option(bfibm_batch* b, int option, int64_t value) {
+  if (!b) return BFIBM_EINVAL;
+  if (option == BFIBM_BATCH_PERSISTENT) b->persistent = value != 0;
+  else if (option == BFIBM_BATCH_TUNE) b->tune = value != 0;
+  else return BFIBM_EINVAL;
+  persist_free(b->ps);
+  b->ps = nullptr;
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_batch_info(bfibm_batch* b, int64_t out[8]) {
+  if (!b || !out) return BFIBM_EINVAL;
+  std::memset(out, 0, 8 * sizeof(int64_t));
+  out[0] = b->persistent;
+  out[1] = b->builds;
+  if (!b->ps) return BFIBM_OK;
+  Persist& P = *b->ps;
+  long long it[2] = {0, 0};
+  if (cudaMemcpyAsync(it, P.iters, sizeof(it), cudaMemcpyDeviceToHost, P.stream) != cudaSuccess ||
+      cudaStreamSynchronize(P.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BFIBM_ECUDA;
+  }
+  out[2] = (int64_t)P.mem.size();
+  out[3] = P.graph_kernels;
+  out[4] = P.body_kernels[0];
+  out[5] = P.body_kernels[1];
+  out[6] = it[0];
+  out[7] = it[1];
+  return BFIBM_OK;
+}
+
+bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[6]) {
+  if (!b || !out || !b->ps || level < 0 || level >= b->ps->depth || kind < 0 || kind > 1)
+    return BFIBM_EINVAL;
+  const PShape& sh = kind == 0 ? b->ps->shv[level] : b->ps->shp[level];
+  out[0] = sh.TY;
+  out[1] = sh.KC;
+  out[2] = sh.NP;
+  out[3] = sh.bx;
+  out[4] = sh.all;
+  out[5] = sh.grid;
+  return BFIBM_OK;
+}
+
+const char* bfibm_batch_error(bfibm_batch* b) { return b ? b->err.c_str() : ""; }
+
 bfibm_status bfibm_batch_step(bfibm_batch* b, const int32_t* nsteps) {
   if (!b) return BFIBM_EINVAL;
+  if (b->persistent) return persist_step(b, nsteps);
   bfibm_status agg = BFIBM_OK;
   for (size_t q = 0; q < b->slots.size(); ++q) {
     bfibm_batch::Slot& s = b->slots[q];
@@ -2025,6 +2759,7 @@ bfibm_status bfibm_batch_slot_ms(bfibm_batch* b, int32_t slot, float* ms) {
 
 void bfibm_batch_destroy(bfibm_batch* b) {
   if (!b) return;
+  persist_free(b->ps);
   for (auto& s : b->slots) {
     if (s.e0) cudaEventDestroy(s.e0);
     if (s.e1) cudaEventDestroy(s.e1);

@@ -139,10 +139,10 @@ __global__ void __launch_bounds__(256) k_p_rbgs(Geo g, LevelPtrs<T> L, int colou
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+__device__ __forceinline__ void p_residual_body(const Blk& B, Geo g, LevelPtrs<T> L) {
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
   int ci[3] = {i, j, k};
   long long c = gidx(g, i, j, k);
@@ -150,6 +150,11 @@ __global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
   p_terms<D, T>(g, L, ci, c, num, dg);
   T ih2 = (T)(1.0 / (g.h * g.h));
   L.pr[c] = L.pf[c] - (num - dg * L.p[c]) * ih2;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
+  p_residual_body<D, T>(own_blk(), g, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,10 +235,10 @@ __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+__device__ __forceinline__ void v_residual_body(const Blk& B, Geo g, LevelPtrs<T> L, T ir) {
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   if (i >= g.n[0] + (g.open == 0) || j >= g.n[1] + (g.open == 1) || k >= g.n[2] + (g.open == 2))
     return;
   int ci[3] = {i, j, k};
@@ -243,6 +248,11 @@ __global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir)
   if constexpr (D == 3) v_residual_point<D, 2, T>(g, L, ci, F, ir);
 }
 
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir) {
+  v_residual_body<D, T>(own_blk(), g, L, ir);
+}
+
 // ---------------------------------------------------------------------------
 // Grid transfers (Sec. 3.5).
 // Cell-centred restriction: mean of the 2^D children. Face restriction along
@@ -250,11 +260,12 @@ __global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir)
 // axes the mean of the two children. Both zero the coarse iterate.
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_restrict_cell(Geo gf, Geo gc, const T* __restrict__ rf,
-                                                       T* __restrict__ fc, T* __restrict__ xc) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  int J = blockIdx.y * blockDim.y + threadIdx.y;
-  int K = blockIdx.z * blockDim.z + threadIdx.z;
+__device__ __forceinline__ void restrict_cell_body(const Blk& B, Geo gf, Geo gc,
+                                                   const T* __restrict__ rf, T* __restrict__ fc,
+                                                   T* __restrict__ xc) {
+  int I = B.x * blockDim.x + threadIdx.x;
+  int J = B.y * blockDim.y + threadIdx.y;
+  int K = B.z * blockDim.z + threadIdx.z;
   if (I >= gc.n[0] || J >= gc.n[1] || K >= gc.n[2]) return;
   long long f0 = gidx(gf, 2 * I, 2 * J, D == 3 ? 2 * K : 0);
   long long sy = gf.st[1], sz = gf.st[2];
@@ -272,13 +283,20 @@ __global__ void __launch_bounds__(256) k_restrict_cell(Geo gf, Geo gc, const T* 
   xc[c] = T(0);
 }
 
-template <int D, int d, typename T>
-__global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* __restrict__ rf,
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_restrict_cell(Geo gf, Geo gc, const T* __restrict__ rf,
                                                        T* __restrict__ fc, T* __restrict__ xc) {
+  restrict_cell_body<D, T>(own_blk(), gf, gc, rf, fc, xc);
+}
+
+template <int D, int d, typename T>
+__device__ __forceinline__ void restrict_face_body(const Blk& B, Geo gf, Geo gc,
+                                                   const T* __restrict__ rf, T* __restrict__ fc,
+                                                   T* __restrict__ xc) {
   int C[3];
-  C[0] = blockIdx.x * blockDim.x + threadIdx.x;
-  C[1] = blockIdx.y * blockDim.y + threadIdx.y;
-  C[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  C[0] = B.x * blockDim.x + threadIdx.x;
+  C[1] = B.y * blockDim.y + threadIdx.y;
+  C[2] = B.z * blockDim.z + threadIdx.z;
   // along d cover the stored faces (walls included), across d the cells
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -317,6 +335,12 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* 
     }
   }
   fc[c] = s * (D == 3 ? T(0.25) : T(0.5));
+}
+
+template <int D, int d, typename T>
+__global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* __restrict__ rf,
+                                                       T* __restrict__ fc, T* __restrict__ xc) {
+  restrict_face_body<D, d, T>(own_blk(), gf, gc, rf, fc, xc);
 }
 
 // 1D prolongation weights. Cell-centred axis: 3/4 on the parent, 1/4 on the
@@ -388,12 +412,12 @@ __device__ __forceinline__ T prol_sum(const Geo& gc, const T* __restrict__ ec, c
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* __restrict__ ec,
-                                                      T* __restrict__ xf) {
+__device__ __forceinline__ void prolong_cell_body(const Blk& B, Geo gf, Geo gc,
+                                                  const T* __restrict__ ec, T* __restrict__ xf) {
   int fi[3];
-  fi[0] = blockIdx.x * blockDim.x + threadIdx.x;
-  fi[1] = blockIdx.y * blockDim.y + threadIdx.y;
-  fi[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  fi[0] = B.x * blockDim.x + threadIdx.x;
+  fi[1] = B.y * blockDim.y + threadIdx.y;
+  fi[2] = B.z * blockDim.z + threadIdx.z;
   if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
   int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
@@ -405,13 +429,19 @@ __global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* _
   xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
 }
 
-template <int D, int d, typename T>
-__global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* __restrict__ ec,
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* __restrict__ ec,
                                                       T* __restrict__ xf) {
+  prolong_cell_body<D, T>(own_blk(), gf, gc, ec, xf);
+}
+
+template <int D, int d, typename T>
+__device__ __forceinline__ void prolong_face_body(const Blk& B, Geo gf, Geo gc,
+                                                  const T* __restrict__ ec, T* __restrict__ xf) {
   int fi[3];
-  fi[0] = blockIdx.x * blockDim.x + threadIdx.x;
-  fi[1] = blockIdx.y * blockDim.y + threadIdx.y;
-  fi[2] = blockIdx.z * blockDim.z + threadIdx.z;
+  fi[0] = B.x * blockDim.x + threadIdx.x;
+  fi[1] = B.y * blockDim.y + threadIdx.y;
+  fi[2] = B.z * blockDim.z + threadIdx.z;
   // along an open axis d the outflow face n is an unknown too
   if (fi[0] >= gf.n[0] + (d == 0 && gf.open == 0) || fi[1] >= gf.n[1] + (d == 1 && gf.open == 1) ||
       fi[2] >= gf.n[2] + (d == 2 && gf.open == 2))
@@ -429,6 +459,12 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
   xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
 }
 
+template <int D, int d, typename T>
+__global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* __restrict__ ec,
+                                                      T* __restrict__ xf) {
+  prolong_face_body<D, d, T>(own_blk(), gf, gc, ec, xf);
+}
+
 // ---------------------------------------------------------------------------
 // Coarsest level: one block does the whole solve (the grid holds at most a
 // few thousand points and stays in L2). Colour phases are separated by
@@ -436,6 +472,12 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
 // ---------------------------------------------------------------------------
 // The coarsest level's arrays are copied to shared memory when they fit
 // (nel elements each); the sweeps then run on the copies.
+constexpr size_t kCoarseSmemMax = 160 * 1024;
+__host__ __device__ inline size_t coarse_bytes(int D, const Geo& g, int elem, bool viscous) {
+  long long nel = g.st[2] * g.s[2];
+  int narr = viscous ? 3 * D + 1 + (D == 3 ? 3 : 1) : 2 + D;
+  return (size_t)narr * nel * elem;
+}
 template <typename T>
 __device__ __forceinline__ void stage_in(T* dst, const T* src, long long nel) {
   for (long long q = threadIdx.x; q < nel; q += blockDim.x) dst[q] = src[q];
@@ -446,8 +488,8 @@ __device__ __forceinline__ void stage_out(T* dst, const T* src, long long nel) {
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int sweeps,
-                                                   long long nel, int use_smem) {
+__device__ __forceinline__ void coarse_p_body(const Blk& B, Geo g, LevelPtrs<T> Lg, int sweeps,
+                                              long long nel, int use_smem) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ double sh[32];
   LevelPtrs<T> L = Lg;
@@ -509,6 +551,12 @@ __global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int s
   }
 }
 
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_p(Geo g, LevelPtrs<T> Lg, int sweeps,
+                                                   long long nel, int use_smem) {
+  coarse_p_body<D, T>(own_blk(), g, Lg, sweeps, nel, use_smem);
+}
+
 // One colour of component d on the coarsest grid. INV: L.m[d] holds the
 // inverse of the whole diagonal (formed once per solve in shared memory), so
 // the update multiplies instead of forming the diagonal and dividing.
@@ -560,8 +608,8 @@ __device__ __forceinline__ void coarse_v_invert(const Geo& g, const LevelPtrs<T>
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> Lg, int sweeps, T ir,
-                                                   long long nel, int use_smem) {
+__device__ __forceinline__ void coarse_v_body(const Blk& B, Geo g, LevelPtrs<T> Lg, int sweeps,
+                                              T ir, long long nel, int use_smem) {
   extern __shared__ __align__(16) unsigned char csm[];
   LevelPtrs<T> L = Lg;
   if (use_smem) {
@@ -610,6 +658,12 @@ __global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> Lg, int s
       coarse_v_phase<D, 2, T, false>(g, L, 1, ir);
     }
   }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_v(Geo g, LevelPtrs<T> Lg, int sweeps, T ir,
+                                                   long long nel, int use_smem) {
+  coarse_v_body<D, T>(own_blk(), g, Lg, sweeps, ir, nel, use_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -831,25 +885,30 @@ __global__ void __launch_bounds__(256) k_divergence(Geo g, Ptr3 u, double* __res
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(256) k_partial_sum(Geo g, const double* __restrict__ a,
-                                                     double* __restrict__ partial) {
+__device__ __forceinline__ void partial_sum_body(const Blk& B, Geo g, const double* __restrict__ a,
+                                                 double* __restrict__ partial) {
   __shared__ double sh[32];
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   double acc = 0.0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = B.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)B.gx * blockDim.x) {
     int i, j, k;
     decode(g, q, i, j, k);
     acc += a[gidx(g, i, j, k)];
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (threadIdx.x == 0) partial[B.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_partial_sum(Geo g, const double* __restrict__ a,
+                                                     double* __restrict__ partial) {
+  partial_sum_body(own_blk(), g, a, partial);
 }
 
 // out[slot] = scale * (sum or max of partial[0..nb)), in a fixed order
-__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ partial, int nb,
-                                                   double* __restrict__ out, int slot,
-                                                   double scale, int is_max) {
+__device__ __forceinline__ void finalize_body(const Blk& B, const double* __restrict__ partial,
+                                              int nb, double* __restrict__ out, int slot,
+                                              double scale, int is_max) {
   __shared__ double sh[32];
   double v = 0.0;
   for (int q = threadIdx.x; q < nb; q += blockDim.x) v = is_max ? fmax(v, partial[q]) : v + partial[q];
@@ -857,13 +916,24 @@ __global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ pa
   if (threadIdx.x == 0) out[slot] = v * scale;
 }
 
-__global__ void __launch_bounds__(256) k_sub_scalar(Geo g, double* __restrict__ a,
-                                                    const double* __restrict__ s) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z * blockDim.z + threadIdx.z;
+__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ partial, int nb,
+                                                   double* __restrict__ out, int slot,
+                                                   double scale, int is_max) {
+  finalize_body(own_blk(), partial, nb, out, slot, scale, is_max);
+}
+
+__device__ __forceinline__ void sub_scalar_body(const Blk& B, Geo g, double* __restrict__ a,
+                                                const double* __restrict__ s) {
+  int i = B.x * blockDim.x + threadIdx.x;
+  int j = B.y * blockDim.y + threadIdx.y;
+  int k = B.z * blockDim.z + threadIdx.z;
   if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
   a[gidx(g, i, j, k)] -= *s;
+}
+
+__global__ void __launch_bounds__(256) k_sub_scalar(Geo g, double* __restrict__ a,
+                                                    const double* __restrict__ s) {
+  sub_scalar_body(own_blk(), g, a, s);
 }
 
 // u_d on one face after the projection, Eq. (NSdis2); pM is p of the cell
@@ -959,13 +1029,13 @@ __global__ void k_div_check(double* __restrict__ out, int acc, int step, int all
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_norm2(Geo g, Ptr3 a, int ncomp,
-                                               double* __restrict__ partial) {
+__device__ __forceinline__ void norm2_body(const Blk& B, Geo g, Ptr3 a, int ncomp,
+                                           double* __restrict__ partial) {
   __shared__ double sh[32];
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   double acc = 0.0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = B.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)B.gx * blockDim.x) {
     int ci[3];
     decode(g, q, ci[0], ci[1], ci[2]);
     long long c = gidx(g, ci[0], ci[1], ci[2]);
@@ -985,7 +1055,13 @@ __global__ void __launch_bounds__(256) k_norm2(Geo g, Ptr3 a, int ncomp,
     }
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (threadIdx.x == 0) partial[B.x] = acc;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_norm2(Geo g, Ptr3 a, int ncomp,
+                                               double* __restrict__ partial) {
+  norm2_body<D>(own_blk(), g, a, ncomp, partial);
 }
 
 template <int D>
@@ -1122,6 +1198,174 @@ __global__ void k_fill(double* a, long long n, double v) {
     a[q] = v;
 }
 
+
+// ===========================================================================
+// Batched kernels: the bodies above, run over a persistent batch's work list
+// (3D, FP32 V-cycle arrays; FP64 on level 0 and the coarsest level). Each
+// copies a member's geometry and pointers out of the table before the body
+// runs, so the body's stores cannot alias them.
+// ===========================================================================
+__global__ void __launch_bounds__(256) kb_v_residual32(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const Geo g = M.g[A.lev];
+    const float ir = (float)(M.inv_re / (g.h * g.h));
+    v_residual_body<3, float>(B, g, cur_ptrs(M.f[A.lev], A.cur), ir);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_p_residual32(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    p_residual_body<3, float>(B, M.g[A.lev], cur_ptrs(M.f[A.lev], A.cur));
+  });
+}
+
+template <int d>
+__global__ void __launch_bounds__(256) kb_restrict_face32(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const int l = A.lev;
+    restrict_face_body<3, d, float>(B, M.g[l], M.g[l + 1], M.f[l].ur[d], M.f[l + 1].uf[d],
+                                    M.f[l + 1].u[d]);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_restrict_cell32(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const int l = A.lev;
+    restrict_cell_body<3, float>(B, M.g[l], M.g[l + 1], M.f[l].pr, M.f[l + 1].pf, M.f[l + 1].p);
+  });
+}
+
+template <int d>
+__global__ void __launch_bounds__(256) kb_prolong_face32(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const int l = A.lev;
+    prolong_face_body<3, d, float>(B, M.g[l], M.g[l + 1], M.f[l + 1].u[d], M.f[l].u[d]);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_prolong_cell32(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const int l = A.lev;
+    prolong_cell_body<3, float>(B, M.g[l], M.g[l + 1], M.f[l + 1].p, M.f[l].p);
+  });
+}
+
+// The coarsest level of one member per block, as the single-instance
+// V-cycle does it in four launches: the FP32 right-hand side converted to
+// FP64 and the FP64 iterate zeroed on every stored element, the FP64 coarse
+// solve (staged in shared memory under the same size rule), the result
+// rounded to FP32.
+template <bool V>
+__global__ void __launch_bounds__(1024) kb_coarse(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const Geo g = M.g[A.lev];
+    const LevelPtrs<double> Ld = M.d[A.lev];
+    const LevelPtrs<float> Lf = M.f[A.lev];
+    const long long nel = g.st[2] * g.s[2];
+    for (long long q = threadIdx.x; q < nel; q += blockDim.x) {
+      if (V) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          Ld.uf[d][q] = (double)Lf.uf[d][q];
+          Ld.u[d][q] = 0.0;
+        }
+      } else {
+        Ld.pf[q] = (double)Lf.pf[q];
+        Ld.p[q] = 0.0;
+      }
+    }
+    __syncthreads();
+    const int use = coarse_bytes(3, g, (int)sizeof(double), V) <= kCoarseSmemMax;
+    if (V) coarse_v_body<3, double>(B, g, Ld, M.coarse_sweeps, M.inv_re / (g.h * g.h), nel, use);
+    else coarse_p_body<3, double>(B, g, Ld, M.coarse_sweeps, nel, use);
+    __syncthreads();
+    for (long long q = threadIdx.x; q < nel; q += blockDim.x) {
+      if (V) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Lf.u[d][q] = (float)Ld.u[d][q];
+      } else {
+        Lf.p[q] = (float)Ld.p[q];
+      }
+    }
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_norm2(BArgs A, int viscous) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    Ptr3 a;
+    for (int d = 0; d < 3; ++d) a.a[d] = viscous ? M.d[0].uf[d] : (d == 0 ? M.d[0].pf : nullptr);
+    norm2_body<3>(B, M.g[0], a, viscous ? 3 : 0, M.sc.partial);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_partial_sum_p(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    partial_sum_body(B, M.g[0], M.d[0].p, M.sc.partial);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_sub_scalar_p(BArgs A) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    sub_scalar_body(B, M.g[0], M.d[0].p, M.sc.out);
+  });
+}
+
+__global__ void __launch_bounds__(1024) kb_finalize(BArgs A, int off, int slot, int is_max,
+                                                    int mean) {
+  for_items(A, [&](const BMember& M, const Blk& B) {
+    const int nb = B.gx;
+    const Geo& g = M.g[0];
+    const double scale = mean ? 1.0 / (double)((long long)g.n[0] * g.n[1] * g.n[2]) : 1.0;
+    finalize_body(B, M.sc.partial + (long long)off * nb, nb, M.sc.out, slot, scale, is_max);
+  });
+}
+
+__global__ void kb_begin(const BMember* __restrict__ tab, int nm, int* __restrict__ act,
+                         int which, int zero_slot) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
+    act[m] = 1;
+    tab[m].cycles[which] = 0;
+    if (zero_slot >= 0) tab[m].sc.out[zero_slot] = 0.0;
+  }
+}
+
+// the test of k_tol_check per active member; one block
+__global__ void __launch_bounds__(1024) kb_tol_check(cudaGraphConditionalHandle h,
+                                                     const BMember* __restrict__ tab, int nm,
+                                                     int* __restrict__ act, int which, int sf,
+                                                     int sr, int smax, long long* iters) {
+  int any = 0;
+  for (int m = threadIdx.x; m < nm; m += blockDim.x) {
+    if (!act[m]) continue;
+    const BMember& M = tab[m];
+    const int n = ++M.cycles[which];
+    ++M.total[which];
+    const double f2 = M.sc.out[sf], r2 = M.sc.out[sr];
+    const double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
+    const double mtol = smax >= 0 ? M.div_tol : 0.0;
+    const bool met = rel <= M.rtol && (mtol <= 0.0 || M.dscale * M.sc.out[smax] <= mtol);
+    const bool again = !met && n < M.maxc;
+    if (!again && !met) ++(*M.nonconv);
+    act[m] = again ? 1 : 0;
+    any |= again ? 1 : 0;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    ++iters[which];
+    cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
+}
+
+__global__ void kb_res_check(const BMember* __restrict__ tab, int nm, int sf, int sr,
+                             double slack) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
+    const BMember& M = tab[m];
+    const double f2 = M.sc.out[sf], r2 = M.sc.out[sr];
+    const double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
+    if (!(rel <= slack * M.rtol)) ++(*M.nonconv);
+  }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1216,12 +1460,8 @@ void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec
 }
 
 size_t coarse_smem_bytes(int D, const Geo& g, int elem, bool viscous) {
-  long long nel = g.st[2] * g.s[2];
-  int narr = viscous ? 3 * D + 1 + (D == 3 ? 3 : 1) : 2 + D;
-  return (size_t)narr * nel * elem;
+  return coarse_bytes(D, g, elem, viscous);
 }
-
-static const size_t kCoarseSmemMax = 160 * 1024;
 
 template <typename T>
 void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cudaStream_t s) {
@@ -1423,6 +1663,80 @@ void launch_fill(double* a, long long n, double v, cudaStream_t s) {
   if (n <= 0) return;
   int nb = red_grid(n);
   k_fill<<<nb, kBlock1D, 0, s>>>(a, n, v);
+}
+
+// the block decompositions the single-instance launches use, for the work
+// lists of batched launches
+int red_grid_of(long long n) { return red_grid(n); }
+dim3 stencil_grid3(long long nx, long long ny, long long nz) { return grd3(nx, ny, nz, blk3(3)); }
+
+// ------------------------------------------------------------------ batched
+void launch_b_v_residual32(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_v_residual32<<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_p_residual32(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_p_residual32<<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_restrict_face32(const BArgs& A, int d, int grid, cudaStream_t s) {
+  if (A.n <= 0) return;
+  if (d == 0) kb_restrict_face32<0><<<grid, blk3(3), 0, s>>>(A);
+  else if (d == 1) kb_restrict_face32<1><<<grid, blk3(3), 0, s>>>(A);
+  else kb_restrict_face32<2><<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_restrict_cell32(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_restrict_cell32<<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_prolong_face32(const BArgs& A, int d, int grid, cudaStream_t s) {
+  if (A.n <= 0) return;
+  if (d == 0) kb_prolong_face32<0><<<grid, blk3(3), 0, s>>>(A);
+  else if (d == 1) kb_prolong_face32<1><<<grid, blk3(3), 0, s>>>(A);
+  else kb_prolong_face32<2><<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_prolong_cell32(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_prolong_cell32<<<grid, blk3(3), 0, s>>>(A);
+}
+size_t b_coarse_smem(const Geo& g, bool viscous) {
+  const size_t b = coarse_bytes(3, g, (int)sizeof(double), viscous);
+  return b <= kCoarseSmemMax ? b : 0;
+}
+void launch_b_coarse(const BArgs& A, bool viscous, size_t smem, cudaStream_t s) {
+  if (A.n <= 0) return;
+  if (viscous) kb_coarse<true><<<A.n, 1024, smem, s>>>(A);
+  else kb_coarse<false><<<A.n, 1024, smem, s>>>(A);
+}
+cudaError_t b_coarse_set_smem() {
+  cudaError_t e = cudaFuncSetAttribute((const void*)kb_coarse<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kCoarseSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)kb_coarse<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
+  return e;
+}
+void launch_b_norm2(const BArgs& A, bool viscous, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_norm2<<<grid, kBlock1D, 0, s>>>(A, viscous ? 1 : 0);
+}
+void launch_b_partial_sum_p(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_partial_sum_p<<<grid, kBlock1D, 0, s>>>(A);
+}
+void launch_b_sub_scalar_p(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_sub_scalar_p<<<grid, blk3(3), 0, s>>>(A);
+}
+void launch_b_finalize(const BArgs& A, int off, int slot, bool is_max, bool mean,
+                       cudaStream_t s) {
+  if (A.n > 0) kb_finalize<<<A.n, 1024, 0, s>>>(A, off, slot, is_max ? 1 : 0, mean ? 1 : 0);
+}
+void launch_b_begin(const BMember* tab, int nm, int* act, int which, int zero_slot,
+                    cudaStream_t s) {
+  if (nm > 0) kb_begin<<<(nm + 255) / 256, 256, 0, s>>>(tab, nm, act, which, zero_slot);
+}
+void launch_b_tol_check(cudaGraphConditionalHandle h, const BMember* tab, int nm, int* act,
+                        int which, int sf, int sr, int smax, long long* iters, cudaStream_t s) {
+  kb_tol_check<<<1, 1024, 0, s>>>(h, tab, nm, act, which, sf, sr, smax, iters);
+}
+void launch_b_res_check(const BMember* tab, int nm, int sf, int sr, double slack,
+                        cudaStream_t s) {
+  if (nm > 0) kb_res_check<<<(nm + 255) / 256, 256, 0, s>>>(tab, nm, sf, sr, slack);
 }
 
 }  // namespace bf
