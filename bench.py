@@ -96,6 +96,19 @@ def parse():
     ap.add_argument("--no-tune-gamma", action="store_true",
                     help="keep one coarse viscosity scaling for every level instead of tuning "
                          "it per level before the timed region")
+    ap.add_argument("--forms", default="persistent,replay,fp64",
+                    help="batched sweep: which of persistent, replay, fp64 to run")
+    ap.add_argument("--unroll", type=int, default=0,
+                    help="persistent batch: solve loops unrolled to this many iterations "
+                         "(for a profiler that cannot see inside conditional graph nodes)")
+    ap.add_argument("--batch-tail", type=int, default=None,
+                    help="persistent batch: cell threshold of its coarse-level kernel (0: none)")
+    ap.add_argument("--save-batch-shapes", default=None,
+                    help="write the persistent batch's tuned sweep shapes to this JSON file")
+    ap.add_argument("--load-batch-shapes", default=None,
+                    help="pin the persistent batch's sweep shapes from this JSON file")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched sweep (64 uneven ducts, persistent vs replay)")
     ap.add_argument("--no-open", action="store_true",
                     help="skip the open-duct block of the default run")
     ap.add_argument("--no-e2e", action="store_true")
@@ -470,6 +483,8 @@ def run_ours(args):
         out["open_duct"] = run_open(args, world, stream)
     if not args.no_e2e:
         out["e2e"] = run_e2e(inst, args, world, stream)
+    if not args.no_batched and args.solver == "tol" and prm.get("precision", 0) == 1:
+        out["batched"] = batched_forms(args, 64, 50, world, fp64_subset=8)
     if not args.no_served:
         out["served"] = run_served_stream(args.requests or 8, args.request_steps or 10,
                                           args.budget_frac, fp64_subset=8,
@@ -667,54 +682,135 @@ def run_served_stream(nreq, steps, budget_frac, fp64_subset=None, solver=None):
     return out
 
 
-def run_batched(args):
-    """c4: independent ducts of uneven sizes stepped together."""
-    import torch
+def div_summary(stats):
+    """The per-step device checks of several simulations: the largest max
+    |div u| after any projection, projections above div_tol, solves stopped
+    above their tolerance."""
+    return {"div_max_all_steps": max(st["div_max_steps"] for st in stats),
+            "div_violations": sum(st["div_violations"] for st in stats),
+            "nonconverged_solves": sum(st["nonconv_total"] for st in stats)}
 
+
+def batch_form(insts, steps, warmup, persistent, world, args=None):
+    """Every instance stepped together for `steps` steps after `warmup`:
+    persistent (lock step, one launch per multigrid level and phase over all
+    members, per-member masks) or concurrent replay of each member's own step
+    graph on its own stream. Wall time around the queued steps and the final
+    wait (the host queues faster than the device runs)."""
     from paper_1302_3663_gb300 import bfibm, workloads as W
-    world, rank, local = dist_setup(args)
-    insts = [W.c4_instance(i) for i in range(args.instances)]
-    for inst in insts:
-        inst["params"].update(solver_override(args))
+    import torch
     ctxs = []
-    batch = bfibm.Batch()
+    pinned = persistent and args is not None and args.load_batch_shapes
+    batch = bfibm.Batch(persistent=persistent, tune=not pinned)
+    if persistent and args is not None and args.unroll:
+        batch.set_option(bfibm.BATCH_UNROLL, args.unroll)
+    if persistent and args is not None and args.batch_tail is not None:
+        batch.set_option(bfibm.BATCH_TAIL, args.batch_tail)
     for inst in insts:
         c = bfibm.load_instance(inst)
         c.set_option(bfibm.OPT_STATS, 0)
         ctxs.append(c)
         batch.add(c)
-    for _ in range(args.warmup):
+    t = time.perf_counter()
+    batch.step()                  # plan (tuned sweeps) or member graphs built here
+    batch.wait()
+    first_s = time.perf_counter() - t
+    if pinned:
+        with open(args.load_batch_shapes) as f:
+            batch.pin_sweep_shapes(json.load(f))
+    if persistent and args is not None and args.save_batch_shapes:
+        with open(args.save_batch_shapes, "w") as f:
+            json.dump(batch.sweep_shapes(), f)
+    for _ in range(max(warmup - 1, 0)):
         batch.step()
     batch.wait()
+    info0 = batch.info()
+    lc0 = [c.launch_counts() for c in ctxs]
     barrier(world)
+    torch.cuda.nvtx.range_push("timed_batch")
+    t = time.perf_counter()
+    for _ in range(steps):
+        batch.step()
+    batch.wait()
+    el = max_over_ranks(world, time.perf_counter() - t)
+    torch.cuda.nvtx.range_pop()
+    info1 = batch.info()
     cells = sum(W.cells(i["params"]) for i in insts)
-    with Clocks(local) as clk:
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            batch.step()
-        batch.wait()
-        el = time.perf_counter() - t0
-    el = max_over_ranks(world, el)
-    value = cells * args.steps * world / el
-    # every instance alone, one after another: plain FP64, then mixed precision
-    from paper_1302_3663_gb300 import serve
-    sub = [serve.Request(i, insts[i], args.steps, 0.0) for i in range(len(insts))]
-    v64, _ = serve.serial(sub, precision=0)
-    v32, _ = serve.serial(sub, precision=None)
+    out = {"value": cells * steps * world / el, "unit": UNIT, "ms_per_step": el / steps * 1e3,
+           "first_step_s": first_s}
+    if persistent:
+        out["gpu_launches"] = (steps * info1["graph_kernels"] +
+                               (info1["visc_iterations"] - info0["visc_iterations"]) *
+                               info1["visc_body_kernels"] +
+                               (info1["p_iterations"] - info0["p_iterations"]) *
+                               info1["p_body_kernels"])
+        out["loop_iterations_per_step"] = {
+            "viscous": (info1["visc_iterations"] - info0["visc_iterations"]) / steps,
+            "pressure": (info1["p_iterations"] - info0["p_iterations"]) / steps}
+        out["sweep_shapes_finest"] = {"viscous": batch.sweep_shape(0, 0),
+                                      "pressure": batch.sweep_shape(0, 1)}
+    else:
+        n = 0
+        for c, a in zip(ctxs, lc0):
+            b = c.launch_counts()
+            n += (steps * b["top"] + (b["iters_visc"] - a["iters_visc"]) * b["body_visc"] +
+                  (b["iters_p"] - a["iters_p"]) * b["body_p"])
+        out["gpu_launches"] = n
+    out["step_checks"] = div_summary([c.get_stats() for c in ctxs])
     batch.close()
     for c in ctxs:
         c.close()
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+    return out
+
+
+def batched_forms(args, count, steps, world, fp64_subset=None):
+    """The batched sweep (64 uneven ducts): the persistent form, concurrent
+    graph replay, and each instance alone in plain FP64 (on the first
+    fp64_subset instances), all with the tolerance solver and the per-step
+    divergence check."""
+    from paper_1302_3663_gb300 import serve, workloads as W
+    insts = [W.c4_instance(i) for i in range(count)]
+    for inst in insts:
+        inst["params"].update(solver_override(args))
+    cells = sum(W.cells(i["params"]) for i in insts)
+    out = {"workload": "c4: %d independent ducts (edges 32-96, length 2 edges, %d cells in all), "
+                       "500-8,000 nodes each, %d steps each" % (count, cells, steps),
+           "cells": cells}
+    forms = args.forms.split(",")
+    if "persistent" in forms:
+        out["persistent"] = batch_form(insts, steps, args.warmup, True, world, args)
+    if "replay" in forms:
+        out["replay"] = batch_form(insts, steps, args.warmup, False, world)
+    if "fp64" in forms:
+        sub = insts[:fp64_subset] if fp64_subset else insts
+        reqs = [serve.Request(i, inst, steps, 0.0) for i, inst in enumerate(sub)]
+        chk = []
+        v64, _ = serve.serial(reqs, precision=0, checks=chk)
+        out["fp64_single_instance_serial"] = {"value": v64, "unit": UNIT,
+                                              "instances": len(reqs),
+                                              "step_checks": div_summary(chk)}
+    return out
+
+
+def run_batched(args):
+    """c4: independent ducts of uneven sizes stepped together; the line's
+    value is the persistent form."""
+    world, rank, local = dist_setup(args)
+    with Clocks(local) as clk:
+        res = batched_forms(args, args.instances, args.steps, world)
+    per = res.get("persistent") or res.get("replay") or res["fp64_single_instance_serial"]
+    out = {"metric": METRIC, "value": per["value"], "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
            "data": "synthetic", "config": {
-               "workload": "c4: %d independent ducts (edges 32-96, length 2 edges), 500-8,000 "
-                           "nodes each, all stepped together" % len(insts),
-               "cells": cells, "precision": "fp32 V-cycles in fp64 defect correction",
-               "parallelism": "one stream per instance, step graphs replayed together"},
-           "clocks": clk.summary(),
-           "fp64_single_instance_serial": {"cell_steps_per_s": v64, "instances": len(sub)},
-           "mixed_single_instance_serial": {"cell_steps_per_s": v32, "instances": len(sub)}}
+               "workload": res["workload"], "cells": res["cells"],
+               "precision": "fp32 V-cycles in fp64 flexible CG (viscous) and defect correction "
+                            "(pressure)",
+               "parallelism": "persistent batch: one launch per multigrid level and phase over "
+                              "every instance, per-instance convergence masks, one graph per "
+                              "batch step",
+               "div_target": DIV_TARGET},
+           "clocks": clk.summary(), "gpu_launches": per.get("gpu_launches"), "batched": res}
     if rank == 0:
         print(json.dumps(out))
 

@@ -274,7 +274,12 @@ bfibm_status bfibm_body_force(bfibm_ctx* c, double* G);
    default 2e9; 0 tests the barrier once without waiting. A sweep whose wait
    runs out drains its copies in flight, stops and raises
    bfibm_stats.wait_timeouts; the step then reports BFIBM_ETIMEOUT. Short
-   limits exist to exercise that path). */
+   limits exist to exercise that path), BFIBM_OPT_TAIL (3D mixed precision:
+   the FP32 V-cycle levels of at most this many cells, down to and with the
+   FP64 coarsest solve, run in one launch per V-cycle, a cluster of 8 thread
+   blocks with a cluster barrier between phases and in-place red-black sweeps;
+   default 8192, 0 keeps one launch per sweep, residual and transfer; the same
+   results to the bit either way). */
 enum {
   BFIBM_OPT_STATS = 0,
   BFIBM_OPT_GRAPH = 1,
@@ -282,7 +287,8 @@ enum {
   BFIBM_OPT_TMA = 3,
   BFIBM_OPT_INNER = 4,
   BFIBM_OPT_KRYLOV = 5,
-  BFIBM_OPT_WAIT_NS = 6
+  BFIBM_OPT_WAIT_NS = 6,
+  BFIBM_OPT_TAIL = 7
 };
 bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value);
 /* Checkpoint and resume. The state a time step starts from (Sec. 3.4): the
@@ -411,10 +417,24 @@ void bfibm_batch_destroy(bfibm_batch* b);
    is rebuilt when the stepped members or their options change.
    BFIBM_BATCH_TUNE (default 1): time the batched sweeps' tile rows, chunk
    planes, planes per phase and grid on every level of at least 2^19 cells in
-   all when a plan is built. Either option drops the current plan. */
+   all when a plan is built. BFIBM_BATCH_UNROLL (default 0): k > 0 queues
+   each solve loop as k iterations one after another instead of a device-side
+   loop; the masks still stop every member where its tolerance is met, so
+   results are the same while k covers the iterations the slowest member needs
+   (a member not done after k iterations stops there without being counted as
+   unconverged). It serves a profiler that cannot see kernels inside
+   conditional graph nodes. BFIBM_BATCH_TAIL (default 4096): the levels of at
+   most this many cells, down to and with each member's coarsest solve, run
+   in the coarse-level kernel of BFIBM_OPT_TAIL with one thread block per
+   member, on a branch of the graph beside the other members' launches (0:
+   one launch per level and phase throughout); the members' own
+   BFIBM_OPT_TAIL does not apply in the batch, and the results are the same
+   to the bit. Every option drops the current plan. */
 enum {
   BFIBM_BATCH_PERSISTENT = 0,
-  BFIBM_BATCH_TUNE = 1
+  BFIBM_BATCH_TUNE = 1,
+  BFIBM_BATCH_UNROLL = 2,
+  BFIBM_BATCH_TAIL = 3
 };
 bfibm_status bfibm_batch_set_option(bfibm_batch* b, int option, int64_t value);
 /* out[0] persistent mode, out[1] plans built so far; with a plan: out[2]
@@ -428,6 +448,13 @@ bfibm_status bfibm_batch_info(bfibm_batch* b, int64_t out[8]);
    row, one block per item (1) or resident blocks striding (0), grid}.
    BFIBM_EINVAL without a plan or for a level it does not have. */
 bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[6]);
+/* Pin the batched sweep of the current plan on a level (kind as above):
+   shape = {tile rows, chunk planes, planes per phase (1 or 2), threads per row
+   (a multiple of 32; rows x (tile rows + 2) threads at most 1024), one block
+   per item}; the plan's graph is captured again. BFIBM_EINVAL without a plan,
+   for a level it does not have or a shape out of range (the plan unchanged). */
+bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
+                                         const int32_t shape[5]);
 /* Message of the last batch call that failed on the batch itself. */
 const char* bfibm_batch_error(bfibm_batch* b);
 /* Device bytes a context with these parameters allocates for its grids. */

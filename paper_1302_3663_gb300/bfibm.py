@@ -21,8 +21,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ETIMEOUT", "ESTAT
 FIELD = {"u": 0, "ut": 1, "urhs": 2, "p": 3, "prhs": 4, "rho": 5, "force": 6, "muc": 7,
          "mue": 8, "beta": 9, "m": 10, "ures": 11, "pres": 12, "idg": 13}
 STAGE = {"rhs": 0, "divergence": 1, "project": 2, "interp_advance": 3, "springs": 4}
-OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER, OPT_KRYLOV, OPT_WAIT_NS = range(7)
-BATCH_PERSISTENT, BATCH_TUNE = range(2)
+OPT_STATS, OPT_GRAPH, OPT_FUSED, OPT_TMA, OPT_INNER, OPT_KRYLOV, OPT_WAIT_NS, OPT_TAIL = range(8)
+BATCH_PERSISTENT, BATCH_TUNE, BATCH_UNROLL, BATCH_TAIL = range(4)
 
 
 class BfibmError(RuntimeError):
@@ -122,6 +122,7 @@ SIGNATURES = {
     "bfibm_batch_info": [_V, C.POINTER(_L)],
     "bfibm_batch_sweep_shape": [_V, _i, _i, _IP],
     "bfibm_batch_error": [_V],
+    "bfibm_batch_set_sweep_shape": [_V, _i, _i, _IP],
 }
 _RES = {"bfibm_last_error": C.c_char_p, "bfibm_destroy": None, "bfibm_batch_destroy": None,
         "bfibm_batch_error": C.c_char_p}
@@ -536,6 +537,28 @@ class Batch:
         if st != OK:
             raise BfibmError(st, "bfibm_batch_sweep_shape")
         return tuple(int(v) for v in out)
+
+    def set_sweep_shape(self, level, kind, shape):
+        a = (C.c_int32 * 5)(*[int(v) for v in shape[:5]])
+        st = self.lib.bfibm_batch_set_sweep_shape(self.h, int(level), int(kind), a)
+        if st != OK:
+            raise BfibmError(st, "bfibm_batch_set_sweep_shape: " +
+                             (self.lib.bfibm_batch_error(self.h) or b"").decode())
+
+    def sweep_shapes(self):
+        """{level: (viscous shape, pressure shape)} of the current plan"""
+        out = {}
+        for lev in range(8):
+            try:
+                out[lev] = (self.sweep_shape(lev, 0)[:5], self.sweep_shape(lev, 1)[:5])
+            except BfibmError:
+                break
+        return out
+
+    def pin_sweep_shapes(self, shapes):
+        for lev, (v, p) in shapes.items():
+            self.set_sweep_shape(int(lev), 0, v)
+            self.set_sweep_shape(int(lev), 1, p)
 
     def add(self, ctx):
         slot = C.c_int32(-1)

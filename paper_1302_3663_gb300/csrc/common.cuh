@@ -119,6 +119,8 @@ struct BMember {
   int maxc;                 // outer iterations of a solve at most
   double dscale, div_tol;   // the pressure loop's second test: dscale max |r_p| <= div_tol
   int coarse_sweeps;
+  int nu1, nu2;             // sweeps before and after the coarse-grid correction
+  int tail;                 // first level of the coarse-level cluster kernel (L: none)
 };
 
 // What every batched kernel takes: its work list, the member table, the mask
@@ -187,6 +189,13 @@ void launch_prolong_cell(int D, const Geo& gf, const Geo& gc, const T* ec, T* xf
 template <typename T>
 void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec, T* xf,
                          cudaStream_t s);
+// the three face components in one launch (3D, no open axis)
+template <typename T>
+void launch_restrict_face3(const Geo& gf, const Geo& gc, T* const rf[3], T* const fc[3],
+                           T* const xc[3], cudaStream_t s);
+template <typename T>
+void launch_prolong_face3(const Geo& gf, const Geo& gc, T* const ec[3], T* const xf[3],
+                          cudaStream_t s);
 // Coarsest level: the whole solve in one block.
 template <typename T>
 void launch_coarse_p(int D, const Geo& g, const LevelPtrs<T>& L, int sweeps, cudaStream_t s);
@@ -244,6 +253,8 @@ void launch_v_diag(int D, const Geo& g, const LevelPtrs<double>& L, double* cons
 void launch_add_correction(int D, const Geo& g, double* const x[3], float* const e[3], int ncomp,
                            cudaStream_t s);
 void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
+// three arrays of n elements each in one launch
+void launch_f32_to_f64_3(float* const in[3], double* const out[3], long long n, cudaStream_t s);
 void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
 // 1 / diagonal of the viscous operator per face component, from the FP64
 // coefficients of one level, stored in L32.idg (0 on the fixed wall faces)
@@ -269,9 +280,9 @@ cudaError_t fused_set_carveout();
 // stencil.cu
 void launch_b_v_residual32(const BArgs& A, int grid, cudaStream_t s);
 void launch_b_p_residual32(const BArgs& A, int grid, cudaStream_t s);
-void launch_b_restrict_face32(const BArgs& A, int d, int grid, cudaStream_t s);
+void launch_b_restrict_face32(const BArgs& A, int grid, cudaStream_t s);   // 3 components
 void launch_b_restrict_cell32(const BArgs& A, int grid, cudaStream_t s);
-void launch_b_prolong_face32(const BArgs& A, int d, int grid, cudaStream_t s);
+void launch_b_prolong_face32(const BArgs& A, int grid, cudaStream_t s);    // 3 components
 void launch_b_prolong_cell32(const BArgs& A, int grid, cudaStream_t s);
 // The coarsest level A.lev of each listed member (one item each): its FP32
 // right-hand side converted to FP64, the iterate zeroed, the FP64 coarse
@@ -298,9 +309,25 @@ void launch_b_begin(const BMember* tab, int nm, int* act, int which, int zero_sl
 // test of the single-instance loop (||r||/||f|| from out[sr], out[sf]; with
 // smax >= 0 also dscale out[smax] <= div_tol); a member that stops leaves the
 // mask; the loop runs again while any member is active.
-// iters[which] counts the loop's iterations.
+// The coarse levels of an FP32 V-cycle in one launch (stencil.cu): one
+// cluster of kTailCtas CTAs per listed member runs its levels tail .. L - 1
+// (tail from the member table): nu1 in-place red-black sweeps per level,
+// residual and restriction down to the coarsest level, the FP64 coarse solve
+// there (with its conversions), prolongation and nu2 sweeps back up, with a
+// cluster barrier between phases. Same arithmetic, point for point, as the
+// launches it replaces. viscous: the viscous components, else the pressure;
+// act (may be null) masks members; smem: the largest tail_smem of the members;
+// ctas 1 gives each member one CTA (a batch's members then run side by side).
+constexpr int kTailCtas = 8;
+void launch_tail(bool viscous, const BMember* tab, const int* list, int nlist, const int* act,
+                 size_t smem, cudaStream_t s, int ctas = kTailCtas);
+size_t tail_smem(const Geo& coarsest, bool viscous);
+cudaError_t tail_set_smem();
+// iters[which] counts the loop's iterations; use_h false: no loop node to
+// steer (an unrolled loop), the masks alone decide.
 void launch_b_tol_check(cudaGraphConditionalHandle h, const BMember* tab, int nm, int* act,
-                        int which, int sf, int sr, int smax, long long* iters, cudaStream_t s);
+                        int which, int sf, int sr, int smax, long long* iters, cudaStream_t s,
+                        bool use_h = true);
 // counts in each member's nonconv the solves whose ||r||/||f|| exceeds slack rtol
 void launch_b_res_check(const BMember* tab, int nm, int sf, int sr, double slack,
                         cudaStream_t s);

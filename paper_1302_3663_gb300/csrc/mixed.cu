@@ -322,6 +322,17 @@ __global__ void __launch_bounds__(256) k_convert(const Tin* __restrict__ in, Tou
     out[q] = (Tout)in[q];
 }
 
+}  // namespace
+
+// three FP32 arrays to FP64 on every stored element
+__global__ void __launch_bounds__(256) k_convert3(F32x3 in, Ptr3d out, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    for (int d = 0; d < 3; ++d) out.a[d][q] = (double)in.a[d][q];
+}
+
+namespace {
+
 struct ConvList {
   const double* in[12];
   float* out[12];
@@ -622,6 +633,16 @@ void launch_add_correction(int D, const Geo& g, double* const x[3], float* const
 
 void launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s) {
   k_convert<float, double><<<(unsigned)flat_convert_blocks(n), kBlock1D, 0, s>>>(in, out, n);
+}
+
+void launch_f32_to_f64_3(float* const in[3], double* const out[3], long long n, cudaStream_t s) {
+  F32x3 i;
+  Ptr3d o;
+  for (int d = 0; d < 3; ++d) {
+    i.a[d] = in[d];
+    o.a[d] = out[d];
+  }
+  k_convert3<<<(unsigned)flat_convert_blocks(n), kBlock1D, 0, s>>>(i, o, n);
 }
 
 void launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s) {

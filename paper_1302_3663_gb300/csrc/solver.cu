@@ -207,6 +207,11 @@ struct bfibm_ctx {
   long long version = 0;          // bumped whenever the step graph is dropped: a batch plan
                                   // built on this context is then rebuilt
   long long partial_cap = 0;      // doubles in sc.partial
+  long long tail_cells = 8192;    // BFIBM_OPT_TAIL: FP32 V-cycle levels of at most this many
+                                  // cells run in the coarse-level cluster kernel (0: none)
+  int tail_lev = kMaxLevels;      // the first of them (L: none)
+  BMember* self_tab = nullptr;    // this context as the one member of that kernel's table
+  int* self_list = nullptr;       // {0}
   std::string err;
 };
 
@@ -292,6 +297,28 @@ void smooth_v(bfibm_ctx* c, int l, int n) {
     }
 }
 
+// The face components' transfers: one launch for all three in 3D without an
+// open axis, else one per component.
+template <typename T>
+void restrict_faces(bfibm_ctx* c, const Geo& gf, const Geo& gc, T* const rf[3], T* const fc[3],
+                    T* const xc[3]) {
+  if (c->D == 3 && gf.open < 0) {
+    launch_restrict_face3<T>(gf, gc, rf, fc, xc, c->stream);
+    return;
+  }
+  for (int d = 0; d < c->D; ++d)
+    launch_restrict_face<T>(c->D, d, gf, gc, rf[d], fc[d], xc[d], c->stream);
+}
+
+template <typename T>
+void prolong_faces(bfibm_ctx* c, const Geo& gf, const Geo& gc, T* const ec[3], T* const xf[3]) {
+  if (c->D == 3 && gf.open < 0) {
+    launch_prolong_face3<T>(gf, gc, ec, xf, c->stream);
+    return;
+  }
+  for (int d = 0; d < c->D; ++d) launch_prolong_face<T>(c->D, d, gf, gc, ec[d], xf[d], c->stream);
+}
+
 void vcycle_p(bfibm_ctx* c, int l) {
   Level& Lv = c->lev[l];
   cudaStream_t s = c->stream;
@@ -318,11 +345,9 @@ void vcycle_v(bfibm_ctx* c, int l) {
   smooth_v(c, l, c->P.nu1);
   launch_v_residual<double>(c->D, Lv.g, Lv.d, c->P.inv_re, s);
   Level& Lc = c->lev[l + 1];
-  for (int d = 0; d < c->D; ++d)
-    launch_restrict_face<double>(c->D, d, Lv.g, Lc.g, Lv.d.ur[d], Lc.d.uf[d], Lc.d.u[d], s);
+  restrict_faces(c, Lv.g, Lc.g, Lv.d.ur, Lc.d.uf, Lc.d.u);
   vcycle_v(c, l + 1);
-  for (int d = 0; d < c->D; ++d)
-    launch_prolong_face<double>(c->D, d, Lv.g, Lc.g, Lc.d.u[d], Lv.d.u[d], s);
+  prolong_faces(c, Lv.g, Lc.g, Lc.d.u, Lv.d.u);
   smooth_v(c, l, c->P.nu2);
 }
 
@@ -350,6 +375,59 @@ bool p_converged(const bfibm_ctx* c, const double* hs) {
 // that stops the loop; a solve whose true relative residual exceeds this many
 // times rtol is reported as not converged.
 constexpr double kTrueResidualSlack = 2.0;
+
+inline int dc_iterations(int vcycles, int inner) { return (vcycles + inner - 1) / inner; }
+
+long long cells_of(const Geo& g) { return (long long)g.n[0] * g.n[1] * g.n[2]; }
+
+// First level of the coarse-level cluster kernel: the first level of at most
+// tail_cells cells (3D mixed precision, closed duct), else L.
+int tail_level(const bfibm_ctx* c) {
+  if (c->D != 3 || c->P.precision != 1 || c->tail_cells <= 0 || c->P.open_flow) return c->L;
+  for (int l = 0; l < c->L; ++l)
+    if (cells_of(c->lev[l].g) <= c->tail_cells) return l;
+  return c->L;
+}
+
+// The context as a member of a batched kernel's table.
+void fill_member(const bfibm_ctx* c, BMember& B) {
+  std::memset(&B, 0, sizeof(B));
+  for (int l = 0; l < c->L; ++l) {
+    B.g[l] = c->lev[l].g;
+    B.f[l] = c->lev[l].f;
+    B.d[l] = c->lev[l].d;
+  }
+  B.L = c->L;
+  B.inv_re = c->P.inv_re;
+  for (int d = 0; d < 3; ++d) {
+    B.vdiag[d] = c->vdiag[d];
+    B.cg_p[d] = c->cg_p[d];
+    B.cg_q[d] = c->cg_q[d];
+    B.cg_z[d] = c->cg_z[d];
+  }
+  B.sc = c->sc;
+  B.cycles = c->dev_cycles;
+  B.total = c->loop_total;
+  B.nonconv = c->counters + 4;
+  B.rtol = c->P.rtol;
+  B.maxc = dc_iterations(c->P.max_cycles, c->inner);
+  B.dscale = div_scale(c);
+  B.div_tol = c->P.div_tol;
+  B.coarse_sweeps = c->P.coarse_sweeps;
+  B.nu1 = c->P.nu1;
+  B.nu2 = c->P.nu2;
+  B.tail = c->tail_lev;
+}
+
+// the context's own one-member table, with its current settings
+cudaError_t upload_self(bfibm_ctx* c) {
+  c->tail_lev = tail_level(c);
+  if (!c->self_tab) return cudaSuccess;
+  BMember B;
+  fill_member(c, B);
+  cudaError_t e = cudaMemcpyAsync(c->self_tab, &B, sizeof(B), cudaMemcpyHostToDevice, c->stream);
+  return e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
+}
 
 bfibm_status read_scalars(bfibm_ctx* c) {
   CK(cudaMemcpyAsync(c->host_sc, c->sc.out, 16 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -571,6 +649,11 @@ void smooth_v32(bfibm_ctx* c, int l, int n) {
 void vcycle_p32(bfibm_ctx* c, int l) {
   Level& Lv = c->lev[l];
   cudaStream_t s = c->stream;
+  if (l == c->tail_lev) {
+    launch_tail(false, c->self_tab, c->self_list, 1, nullptr,
+                tail_smem(c->lev[c->L - 1].g, false), s);
+    return;
+  }
   if (l == c->L - 1) {
     long long n = level_elems(Lv.g);
     launch_f32_to_f64(Lv.f.pf, Lv.d.pf, n, s);
@@ -591,6 +674,11 @@ void vcycle_p32(bfibm_ctx* c, int l) {
 void vcycle_v32(bfibm_ctx* c, int l) {
   Level& Lv = c->lev[l];
   cudaStream_t s = c->stream;
+  if (l == c->tail_lev) {
+    launch_tail(true, c->self_tab, c->self_list, 1, nullptr,
+                tail_smem(c->lev[c->L - 1].g, true), s);
+    return;
+  }
   if (l == c->L - 1) {
     long long n = level_elems(Lv.g);
     for (int d = 0; d < c->D; ++d) {
@@ -604,11 +692,9 @@ void vcycle_v32(bfibm_ctx* c, int l) {
   smooth_v32(c, l, c->P.nu1);
   launch_v_residual<float>(c->D, Lv.g, Lv.f, c->P.inv_re, s);
   Level& Lc = c->lev[l + 1];
-  for (int d = 0; d < c->D; ++d)
-    launch_restrict_face<float>(c->D, d, Lv.g, Lc.g, Lv.f.ur[d], Lc.f.uf[d], Lc.f.u[d], s);
+  restrict_faces(c, Lv.g, Lc.g, Lv.f.ur, Lc.f.uf, Lc.f.u);
   vcycle_v32(c, l + 1);
-  for (int d = 0; d < c->D; ++d)
-    launch_prolong_face<float>(c->D, d, Lv.g, Lc.g, Lc.f.u[d], Lv.f.u[d], s);
+  prolong_faces(c, Lv.g, Lc.g, Lc.f.u, Lv.f.u);
   smooth_v32(c, l, c->P.nu2);
 }
 
@@ -618,8 +704,6 @@ void vcycle_v32(bfibm_ctx* c, int l) {
 // residual per `inner` of them), x += e in FP64. ncycles > 0: that many
 // V-cycles; else until rtol, with max_cycles V-cycles at most. Returns the
 // V-cycles used (a multiple of c->inner in tolerance mode).
-inline int dc_iterations(int vcycles, int inner) { return (vcycles + inner - 1) / inner; }
-
 bfibm_status solve_p_mixed(bfibm_ctx* c, int ncycles, int* used) {
   Level& L0 = c->lev[0];
   cudaStream_t s = c->stream;
@@ -761,7 +845,9 @@ bfibm_status solve_v_fcg(bfibm_ctx* c, int ncycles, int* used) {
   CK(cudaMemsetAsync(c->sc.out + SL_PQ, 0, sizeof(double), s));
   auto iteration = [&](cudaStream_t b, int nv) {
     for (int q = 0; q < nv; ++q) vcycle_v32(c, 0);
-    for (int d = 0; d < D; ++d) launch_f32_to_f64(L0.f.u[d], c->cg_z[d], level_elems(L0.g), b);
+    if (D == 3) launch_f32_to_f64_3(L0.f.u, c->cg_z, level_elems(L0.g), b);
+    else
+      for (int d = 0; d < D; ++d) launch_f32_to_f64(L0.f.u[d], c->cg_z[d], level_elems(L0.g), b);
     launch_fcg_apply(D, L0.g, L0.d, c->cg_z, c->vdiag, c->P.inv_re, w, c->cg_q, c->sc.partial, b);
     launch_finalize_sum(c->sc.partial, nb, c->sc.out, SL_ZQ, 1.0, b);
     launch_fcg_dir(D, L0.g, c->cg_z, w, c->cg_p, c->cg_q, r, c->sc.out, SL_ZQ, SL_PQ,
@@ -1149,6 +1235,9 @@ struct Persist {
   long long* iters = nullptr;        // batch device-loop iterations so far (viscous, pressure)
   int depth = 0;                     // levels of the deepest member
   int nu1 = 2, nu2 = 2, inner = 1, krylov = 0;
+  int unroll = 0;                    // > 0: each solve loop unrolled to this many iterations
+  long long tail_cells = 4096;       // levels of at most this many cells: the coarse-level kernel
+  std::vector<int> ptail;            // each member's first level in that kernel (L: none)
   // per level l: the members that smooth on l (l below their coarsest level)
   PList swv[kMaxLevels], swp[kMaxLevels];   // ring-sweep blocks (viscous, pressure shape)
   PShape shv[kMaxLevels], shp[kMaxLevels];
@@ -1158,6 +1247,13 @@ struct Persist {
   PList fl[kMaxLevels];   // flat blocks over the elements of l: copies after odd sweep counts
   PList co[kMaxLevels];   // one item per member whose coarsest level is l
   size_t co_smem[kMaxLevels][2] = {};
+  int* tail[kMaxLevels] = {};        // members whose coarse-level cluster kernel starts on l
+  int ntail[kMaxLevels] = {};
+  size_t tail_smem[kMaxLevels][2] = {};
+  // that kernel runs on a branch of its own, beside the other members' work on
+  // the same and deeper levels
+  cudaStream_t tstream[kMaxLevels] = {};
+  cudaEvent_t tfork[kMaxLevels] = {}, tjoin[kMaxLevels] = {};
   // level 0, every member
   PList a3, ared, aflat, aconv;      // 3D, cell reductions, flat CG passes, conversions
   PList fin3, finred, finflat;       // one item per member, gx = its producer's blocks
@@ -1171,12 +1267,23 @@ struct Persist {
   std::string err;
 };
 
+// whether member m smooths on level l with launches (above its coarsest level
+// and above the level where its coarse-level cluster kernel starts)
+bool p_smooths(const Persist& P, int m, int l) {
+  return l < std::min(P.ptail[m], P.mem[m]->L - 1);
+}
+
 void persist_free(Persist* P) {
   if (!P) return;
   if (P->stream) cudaStreamSynchronize(P->stream);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   for (void* a : P->allocs) cudaFree(a);
   for (cudaEvent_t e : P->join) cudaEventDestroy(e);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (P->tfork[l]) cudaEventDestroy(P->tfork[l]);
+    if (P->tjoin[l]) cudaEventDestroy(P->tjoin[l]);
+    if (P->tstream[l]) cudaStreamDestroy(P->tstream[l]);
+  }
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->done) cudaEventDestroy(P->done);
   if (P->aux) cudaStreamDestroy(P->aux);
@@ -1227,17 +1334,15 @@ cudaError_t upload(Persist& P, const std::vector<BItem>& v, PList& L) {
   return cudaMemcpy(L.dev, v.data(), v.size() * sizeof(BItem), cudaMemcpyHostToDevice);
 }
 
-long long cells_of(const Geo& g) { return (long long)g.n[0] * g.n[1] * g.n[2]; }
-
 // The sweep items of level l for a shape, and the launch's grid and shared memory.
 cudaError_t sweep_list(Persist& P, int l, int K, PShape& sh, PList& L) {
   const int nm = (int)P.mem.size();
   int W = 0;
   for (int m = 0; m < nm; ++m)
-    if (l < P.mem[m]->L - 1) W = std::max(W, P.mem[m]->lev[l].g.s[0]);
+    if (p_smooths(P, m, l)) W = std::max(W, P.mem[m]->lev[l].g.s[0]);
   sh.smem = b_sweep_smem(sh.NP, sh.TY, W);
   std::vector<BItem> v;
-  make_items(nm, [&](int m) { return l < P.mem[m]->L - 1; },
+  make_items(nm, [&](int m) { return p_smooths(P, m, l); },
              [&](int m) {
                const Geo& g = P.mem[m]->lev[l].g;
                return dim3((g.n[1] + sh.TY - 1) / sh.TY, (g.n[2] + sh.KC - 1) / sh.KC, 1);
@@ -1266,16 +1371,19 @@ PShape default_shape(const Persist& P, int l) {
   PShape sh;
   int np = 1, nR = 1 << 30;
   long long tiles = 0;
-  for (bfibm_ctx* c : P.mem)
-    if (l < c->L - 1) {
-      const Geo& g = c->lev[l].g;
+  for (size_t m = 0; m < P.mem.size(); ++m)
+    if (p_smooths(P, (int)m, l)) {
+      const Geo& g = P.mem[m]->lev[l].g;
       np = std::max(np, (g.n[0] + 1) / 2);
       nR = std::min(nR, g.n[1]);
     }
   sh.bx = std::min(128, (np + 31) / 32 * 32);
   sh.TY = std::max(1, std::min(4, nR));
-  for (bfibm_ctx* c : P.mem)
-    if (l < c->L - 1) tiles += (long long)((c->lev[l].g.n[1] + sh.TY - 1) / sh.TY) * c->lev[l].g.n[2];
+  for (size_t m = 0; m < P.mem.size(); ++m)
+    if (p_smooths(P, (int)m, l)) {
+      const Geo& g = P.mem[m]->lev[l].g;
+      tiles += (long long)((g.n[1] + sh.TY - 1) / sh.TY) * g.n[2];
+    }
   long long KC = tiles / (3LL * device_sms());
   sh.KC = (int)std::max(4LL, std::min(16LL, KC));
   return sh;
@@ -1376,36 +1484,27 @@ bfibm_status persist_build(Persist& P, bool tune) {
   PK(cudaStreamCreateWithFlags(&P.aux, cudaStreamNonBlocking));
   PK(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
   PK(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
+  for (int l = 0; l < kMaxLevels; ++l) {
+    PK(cudaStreamCreateWithFlags(&P.tstream[l], cudaStreamNonBlocking));
+    PK(cudaEventCreateWithFlags(&P.tfork[l], cudaEventDisableTiming));
+    PK(cudaEventCreateWithFlags(&P.tjoin[l], cudaEventDisableTiming));
+  }
   P.join.resize(nm, nullptr);
   for (int m = 0; m < nm; ++m) PK(cudaEventCreateWithFlags(&P.join[m], cudaEventDisableTiming));
   std::vector<BMember> host(nm);
   P.depth = 0;
+  P.ptail.assign(nm, 0);
   for (int m = 0; m < nm; ++m) {
-    bfibm_ctx* c = P.mem[m];
-    BMember& B = host[m];
-    std::memset(&B, 0, sizeof(B));
-    for (int l = 0; l < c->L; ++l) {
-      B.g[l] = c->lev[l].g;
-      B.f[l] = c->lev[l].f;
-      B.d[l] = c->lev[l].d;
-    }
-    B.L = c->L;
-    B.inv_re = c->P.inv_re;
-    for (int d = 0; d < 3; ++d) {
-      B.vdiag[d] = c->vdiag[d];
-      B.cg_p[d] = c->cg_p[d];
-      B.cg_q[d] = c->cg_q[d];
-      B.cg_z[d] = c->cg_z[d];
-    }
-    B.sc = c->sc;
-    B.cycles = c->dev_cycles;
-    B.total = c->loop_total;
-    B.nonconv = c->counters + 4;
-    B.rtol = c->P.rtol;
-    B.maxc = dc_iterations(c->P.max_cycles, c->inner);
-    B.dscale = div_scale(c);
-    B.div_tol = c->P.div_tol;
-    B.coarse_sweeps = c->P.coarse_sweeps;
+    const bfibm_ctx* c = P.mem[m];
+    fill_member(c, host[m]);
+    // the batch's own threshold: each member's kernel has one CTA here
+    int t = c->L;
+    for (int l = 0; P.tail_cells > 0 && l < c->L; ++l)
+      if (cells_of(c->lev[l].g) <= P.tail_cells) {
+        t = l;
+        break;
+      }
+    host[m].tail = P.ptail[m] = t;
     P.depth = std::max(P.depth, c->L);
   }
   PK(cudaMalloc((void**)&P.tab, nm * sizeof(BMember)));
@@ -1418,11 +1517,15 @@ bfibm_status persist_build(Persist& P, bool tune) {
   P.allocs.push_back(P.iters);
   PK(cudaMemset(P.iters, 0, 2 * sizeof(long long)));
   PK(b_coarse_set_smem());
+  PK(tail_set_smem());
   std::vector<BItem> v;
   bool ok = true;   // every grid within the items' 16-bit block coordinates
   auto lev = [&](int m, int l) -> const Geo& { return P.mem[m]->lev[l].g; };
+  // member m smooths on level l above both its coarsest level and the level
+  // where the coarse-level cluster kernel takes over (tail)
+  auto tail_of = [&](int m) { return P.ptail[m]; };
   for (int l = 0; l < P.depth; ++l) {
-    auto smooths = [&](int m) { return l < P.mem[m]->L - 1; };
+    auto smooths = [&](int m) { return l < std::min(tail_of(m), P.mem[m]->L - 1); };
     ok &= make_items(nm, smooths, [&](int m) {
       const Geo& g = lev(m, l);
       return stencil_grid3(g.n[0], g.n[1], g.n[2]);
@@ -1442,14 +1545,27 @@ bfibm_status persist_build(Persist& P, bool tune) {
       return dim3(flat_convert_blocks(level_elems(lev(m, l))), 1, 1);
     }, v);
     PK(upload(P, v, P.fl[l]));
-    ok &= make_items(nm, [&](int m) { return l == P.mem[m]->L - 1; },
-                     [&](int) { return dim3(1, 1, 1); }, v);
+    auto coarse_here = [&](int m) { return tail_of(m) >= P.mem[m]->L && l == P.mem[m]->L - 1; };
+    ok &= make_items(nm, coarse_here, [&](int) { return dim3(1, 1, 1); }, v);
     PK(upload(P, v, P.co[l]));
+    std::vector<int> tl;
+    for (int m = 0; m < nm; ++m)
+      if (tail_of(m) == l) tl.push_back(m);
+    P.ntail[l] = (int)tl.size();
+    if (!tl.empty()) {
+      PK(cudaMalloc((void**)&P.tail[l], tl.size() * sizeof(int)));
+      P.allocs.push_back(P.tail[l]);
+      PK(cudaMemcpy(P.tail[l], tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     for (int vis = 0; vis < 2; ++vis) {
-      size_t mx = 0;
-      for (int m = 0; m < nm; ++m)
-        if (l == P.mem[m]->L - 1) mx = std::max(mx, b_coarse_smem(lev(m, l), vis != 0));
+      size_t mx = 0, mt = 0;
+      for (int m = 0; m < nm; ++m) {
+        const Geo& gc = lev(m, P.mem[m]->L - 1);
+        if (coarse_here(m)) mx = std::max(mx, b_coarse_smem(gc, vis != 0));
+        if (tail_of(m) == l) mt = std::max(mt, tail_smem(gc, vis != 0));
+      }
       P.co_smem[l][vis] = mx;
+      P.tail_smem[l][vis] = mt;
     }
     P.shv[l] = default_shape(P, l);
     P.shp[l] = P.shv[l];
@@ -1492,7 +1608,7 @@ bfibm_status persist_build(Persist& P, bool tune) {
     for (int l = 0; l < P.depth; ++l) {
       long long cells = 0;
       for (int m = 0; m < nm; ++m)
-        if (l < P.mem[m]->L - 1) cells += cells_of(lev(m, l));
+        if (p_smooths(P, m, l)) cells += cells_of(lev(m, l));
       if (cells < (1LL << 19)) continue;
       PK(tune_level(P, l, 0));
       PK(tune_level(P, l, 3));
@@ -1527,21 +1643,39 @@ void b_smooth(Persist& P, int l, int n, bool V) {
     if ((cur >> K) & 1) launch_b_copy_back(bargs(P, P.fl[l], l), K, P.fl[l].grid, P.stream);
 }
 
+void b_level(Persist& P, int l, bool V);
+
+// One V-cycle from level l for every member still in it.
 void b_vcycle(Persist& P, int l, bool V) {
+  cudaStream_t s = P.stream;
+  if (P.ntail[l]) {   // forked: joined again at the end of this level
+    cudaEventRecord(P.tfork[l], s);
+    cudaStreamWaitEvent(P.tstream[l], P.tfork[l], 0);
+    launch_tail(V, P.tab, P.tail[l], P.ntail[l], P.masked ? P.act : nullptr,
+                P.tail_smem[l][V ? 1 : 0], P.tstream[l], 1);
+    cudaEventRecord(P.tjoin[l], P.tstream[l]);
+  }
+  b_level(P, l, V);
+  if (P.ntail[l]) cudaStreamWaitEvent(s, P.tjoin[l], 0);
+}
+
+// Level l of the members that smooth on it (their coarse levels recursively),
+// and the coarsest solve of the members whose coarsest level it is.
+void b_level(Persist& P, int l, bool V) {
   cudaStream_t s = P.stream;
   if (P.co[l].n) launch_b_coarse(bargs(P, P.co[l], l), V, P.co_smem[l][V ? 1 : 0], s);
   if (!P.en[l].n) return;
   b_smooth(P, l, P.nu1, V);
   if (V) {
     launch_b_v_residual32(bargs(P, P.en[l], l), P.en[l].grid, s);
-    for (int d = 0; d < 3; ++d) launch_b_restrict_face32(bargs(P, P.rs[l], l), d, P.rs[l].grid, s);
+    launch_b_restrict_face32(bargs(P, P.rs[l], l), P.rs[l].grid, s);
   } else {
     launch_b_p_residual32(bargs(P, P.en[l], l), P.en[l].grid, s);
     launch_b_restrict_cell32(bargs(P, P.rn[l], l), P.rn[l].grid, s);
   }
   b_vcycle(P, l + 1, V);
   if (V)
-    for (int d = 0; d < 3; ++d) launch_b_prolong_face32(bargs(P, P.en[l], l), d, P.en[l].grid, s);
+    launch_b_prolong_face32(bargs(P, P.en[l], l), P.en[l].grid, s);
   else
     launch_b_prolong_cell32(bargs(P, P.en[l], l), P.en[l].grid, s);
   b_smooth(P, l, P.nu2, V);
@@ -1552,6 +1686,22 @@ void b_vcycle(Persist& P, int l, bool V) {
 // the auxiliary stream meanwhile) with every launch masked.
 template <typename Body>
 bfibm_status p_capture_while(Persist& P, int which, Body body) {
+  if (P.unroll > 0) {   // the iterations queued one after another; masked members skip them
+    const long long k0 = 0;
+    cudaGraph_t g = nullptr;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamGetCaptureInfo(P.stream, &cs, nullptr, &g) != cudaSuccess) {
+      cudaGetLastError();
+      P.err = "cudaStreamGetCaptureInfo";
+      return BFIBM_ECUDA;
+    }
+    const long long before = count_kernel_nodes(g);
+    P.masked = true;
+    for (int k = 0; k < P.unroll; ++k) body((cudaGraphConditionalHandle)k0);
+    P.masked = false;
+    P.body_kernels[which] = (count_kernel_nodes(g) - before) / P.unroll;
+    return BFIBM_OK;
+  }
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -1616,7 +1766,7 @@ bfibm_status b_solve_v(Persist& P) {
       launch_b_finalize(bargs(P, P.finflat, 0), 1, SL_PRR, false, false, b);
       launch_b_fcg_update(bargs(P, P.aflat, 0), SL_PQ, SL_PRR, P.aflat.grid, b);
       launch_b_finalize(bargs(P, P.finflat, 0), 0, SL_VR, false, false, b);
-      launch_b_tol_check(h, P.tab, nm, P.act, 0, SL_VF, SL_VR, -1, P.iters, b);
+      launch_b_tol_check(h, P.tab, nm, P.act, 0, SL_VF, SL_VR, -1, P.iters, b, P.unroll == 0);
     });
     if (st != BFIBM_OK) return st;
     // the true FP64 residual of every member's final iterate, checked
@@ -1633,7 +1783,7 @@ bfibm_status b_solve_v(Persist& P) {
     launch_b_add_correction(bargs(P, P.a3, 0), true, P.a3.grid, b);
     launch_b_v_residual_mixed(bargs(P, P.a3, 0), true, false, P.a3.grid, b);
     launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_VR, false, false, b);
-    launch_b_tol_check(h, P.tab, nm, P.act, 0, SL_VF, SL_VR, -1, P.iters, b);
+    launch_b_tol_check(h, P.tab, nm, P.act, 0, SL_VF, SL_VR, -1, P.iters, b, P.unroll == 0);
   });
 }
 
@@ -1656,7 +1806,8 @@ bfibm_status b_solve_p(Persist& P) {
     launch_b_p_residual_mixed(bargs(P, P.a3, 0), true, P.a3.grid, b);
     launch_b_finalize(bargs(P, P.fin3, 0), 0, SL_PR, false, false, b);
     launch_b_finalize(bargs(P, P.fin3, 0), 1, SL_PRMAX, true, false, b);
-    launch_b_tol_check(h, P.tab, nm, P.act, 1, SL_PF, SL_PR, SL_PRMAX, P.iters, b);
+    launch_b_tol_check(h, P.tab, nm, P.act, 1, SL_PF, SL_PR, SL_PRMAX, P.iters, b,
+                       P.unroll == 0);
   });
 }
 
@@ -1877,7 +2028,23 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
       return BFIBM_ECUDA;
     }
   }
-  if (coarse_set_smem() != cudaSuccess || fused_set_carveout() != cudaSuccess) {
+  if (coarse_set_smem() != cudaSuccess || fused_set_carveout() != cudaSuccess ||
+      tail_set_smem() != cudaSuccess) {
+    cudaGetLastError();
+    bfibm_destroy(c);
+    return BFIBM_ECUDA;
+  }
+  if (p->precision == 1 && D == 3) {
+    static const int zero = 0;
+    if (cudaMalloc((void**)&c->self_tab, sizeof(BMember)) != cudaSuccess ||
+        cudaMalloc((void**)&c->self_list, sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(c->self_list, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      bfibm_destroy(c);
+      return BFIBM_ENOMEM;
+    }
+  }
+  if (upload_self(c) != cudaSuccess) {
     cudaGetLastError();
     bfibm_destroy(c);
     return BFIBM_ECUDA;
@@ -1944,6 +2111,8 @@ void bfibm_destroy(bfibm_ctx* c) {
   if (c->loop_total) cudaFree(c->loop_total);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->host_sc) cudaFreeHost(c->host_sc);
+  if (c->self_tab) cudaFree(c->self_tab);
+  if (c->self_list) cudaFree(c->self_list);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -2523,10 +2692,14 @@ bfibm_status bfibm_set_option(bfibm_ctx* c, int option, int64_t value) {
     if (value < 1 || value > 16)
       return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_INNER takes 1 to 16");
     c->inner = (int)value;
+  } else if (option == BFIBM_OPT_TAIL) {
+    if (value < 0) return set_err(c, BFIBM_EINVAL, "BFIBM_OPT_TAIL takes a value >= 0");
+    c->tail_cells = value;
   } else {
     return set_err(c, BFIBM_EINVAL, "unknown option");
   }
   CK(cudaStreamSynchronize(c->stream));
+  CK(upload_self(c));
   drop_graph(c);
   return BFIBM_OK;
 }
@@ -2541,6 +2714,8 @@ struct bfibm_batch {
   std::vector<Slot> slots;
   int persistent = 0;    // BFIBM_BATCH_PERSISTENT
   int tune = 1;          // BFIBM_BATCH_TUNE
+  int unroll = 0;        // BFIBM_BATCH_UNROLL
+  long long tail = 4096; // BFIBM_BATCH_TAIL
   Persist* ps = nullptr; // the plan of the last persistent step
   long long builds = 0;  // plans built
   std::string err;
@@ -2625,6 +2800,8 @@ bfibm_status persist_step(bfibm_batch* b, const int32_t* nsteps) {
     if (!b->ps) return BFIBM_ENOMEM;
     b->ps->mem = mem;
     b->ps->version = ver;
+    b->ps->unroll = b->unroll;
+    b->ps->tail_cells = b->tail;
     bfibm_status st = persist_build(*b->ps, b->tune != 0);
     if (st == BFIBM_OK) st = persist_capture(*b->ps);
     if (st != BFIBM_OK) {
@@ -2665,6 +2842,8 @@ bfibm_status bfibm_batch_set_option(bfibm_batch* b, int option, int64_t value) {
   if (!b) return BFIBM_EINVAL;
   if (option == BFIBM_BATCH_PERSISTENT) b->persistent = value != 0;
   else if (option == BFIBM_BATCH_TUNE) b->tune = value != 0;
+  else if (option == BFIBM_BATCH_UNROLL && value >= 0 && value <= 1000) b->unroll = (int)value;
+  else if (option == BFIBM_BATCH_TAIL && value >= 0) b->tail = value;
   else return BFIBM_EINVAL;
   persist_free(b->ps);
   b->ps = nullptr;
@@ -2704,6 +2883,51 @@ bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_
   out[4] = sh.all;
   out[5] = sh.grid;
   return BFIBM_OK;
+}
+
+bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
+                                         const int32_t shape[5]) {
+  if (!b || !shape || !b->ps || level < 0 || level >= b->ps->depth || kind < 0 || kind > 1)
+    return BFIBM_EINVAL;
+  Persist& P = *b->ps;
+  PShape sh = kind == 0 ? P.shv[level] : P.shp[level];
+  sh.TY = shape[0];
+  sh.KC = shape[1];
+  sh.NP = shape[2];
+  sh.bx = shape[3];
+  sh.all = shape[4] != 0;
+  if (sh.TY < 1 || sh.KC < 1 || (sh.NP != 1 && sh.NP != 2) || sh.bx < 32 || sh.bx % 32 ||
+      sh.bx * (sh.TY + 2) > 1024) {
+    b->err = "a sweep shape needs rows >= 1, planes >= 1, 1 or 2 planes per phase and "
+             "32 k threads per row, at most 1024 threads";
+    return BFIBM_EINVAL;
+  }
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BFIBM_ECUDA;
+  }
+  PList& L = kind == 0 ? P.swv[level] : P.swp[level];
+  cudaError_t e = sweep_list(P, level, kind == 0 ? 0 : 3, sh, L);
+  if (e == cudaSuccess && sh.smem > 48 * 1024) {
+    b->err = "the sweep shape needs more than 48 KB of shared memory";
+    sh = kind == 0 ? P.shv[level] : P.shp[level];
+    e = sweep_list(P, level, kind == 0 ? 0 : 3, sh, L);
+    if (e == cudaSuccess) return BFIBM_EINVAL;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BFIBM_ECUDA;
+  }
+  (kind == 0 ? P.shv[level] : P.shp[level]) = sh;
+  if (P.gexec) cudaGraphExecDestroy(P.gexec);
+  P.gexec = nullptr;
+  bfibm_status st = persist_capture(P);
+  if (st != BFIBM_OK) {   // a plan without its graph is of no use
+    b->err = P.err;
+    persist_free(b->ps);
+    b->ps = nullptr;
+  }
+  return st;
 }
 
 const char* bfibm_batch_error(bfibm_batch* b) { return b ? b->err.c_str() : ""; }

@@ -13,6 +13,7 @@
 #include <math_constants.h>
 
 #include "common.cuh"
+#include "point.cuh"
 
 namespace bf {
 
@@ -95,7 +96,7 @@ __device__ __forceinline__ void decode(const Geo& g, long long idx, int& i, int&
 // beta_nb p_nb over the existing neighbours, dg = sum of beta_nb; then
 // (A p)(c) = (num - dg p(c)) / h^2. No flux crosses a wall.
 // ---------------------------------------------------------------------------
-template <int D, typename T>
+template <int D, typename T, bool COH = false>
 __device__ __forceinline__ void p_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
                                         long long c, T& num, T& dg) {
   num = T(0);
@@ -106,13 +107,13 @@ __device__ __forceinline__ void p_terms(const Geo& g, const LevelPtrs<T>& L, con
     if (ci[a] > 0 || g.per[a]) {
       long long cm = c + offm(g, a, ci[a]);
       T bb = b[c];
-      num += bb * L.p[cm];
+      num += bb * ldm<COH>(L.p + cm);
       dg += bb;
     }
     if (ci[a] < g.n[a] - 1 || g.per[a]) {
       long long cp = c + offp(g, a, ci[a]);
       T bb = b[cp];
-      num += bb * L.p[cp];
+      num += bb * ldm<COH>(L.p + cp);
       dg += bb;
     } else if (a == g.open) {
       // the outflow face, pressure held there: the homogeneous ghost -p
@@ -138,6 +139,15 @@ __global__ void __launch_bounds__(256) k_p_rbgs(Geo g, LevelPtrs<T> L, int colou
   L.p[c] = (num - h2 * L.pf[c]) / dg;
 }
 
+template <int D, typename T, bool COH = false>
+__device__ __forceinline__ void p_residual_at(const Geo& g, const LevelPtrs<T>& L,
+                                              const int ci[3], long long c) {
+  T num, dg;
+  p_terms<D, T, COH>(g, L, ci, c, num, dg);
+  T ih2 = (T)(1.0 / (g.h * g.h));
+  L.pr[c] = ldm<COH>(L.pf + c) - (num - dg * ldm<COH>(L.p + c)) * ih2;
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void p_residual_body(const Blk& B, Geo g, LevelPtrs<T> L) {
   int i = B.x * blockDim.x + threadIdx.x;
@@ -145,11 +155,7 @@ __device__ __forceinline__ void p_residual_body(const Blk& B, Geo g, LevelPtrs<T
   int k = B.z * blockDim.z + threadIdx.z;
   if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
   int ci[3] = {i, j, k};
-  long long c = gidx(g, i, j, k);
-  T num, dg;
-  p_terms<D, T>(g, L, ci, c, num, dg);
-  T ih2 = (T)(1.0 / (g.h * g.h));
-  L.pr[c] = L.pf[c] - (num - dg * L.p[c]) * ih2;
+  p_residual_at<D, T>(g, L, ci, gidx(g, i, j, k));
 }
 
 template <int D, typename T>
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
 // viscosity) and the tangential components mirror too (du_e/dx_d = 0 there).
 // Across the outflow (e = open, last cell) the tangential u_d mirrors evenly:
 // that edge contributes its cross term only.
-template <int D, int d, typename T>
+template <int D, int d, typename T, bool COH = false>
 __device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
                                         long long F, T& off, T& dgV) {
   const T* __restrict__ ud = L.u[d];
@@ -178,7 +184,7 @@ __device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, con
   long long od_m = offm(g, d, ci[d]);
   long long od_p = outflow ? od_m : offp(g, d, ci[d]);
   T mcp = outflow ? L.muc[F + od_m] : L.muc[F], mcm = L.muc[F + od_m];
-  off = T(2) * (mcp * ud[F + od_p] + mcm * ud[F + od_m]);
+  off = T(2) * (mcp * ldm<COH>(ud + F + od_p) + mcm * ldm<COH>(ud + F + od_m));
   dgV = T(2) * (mcp + mcm);
 #pragma unroll
   for (int e = 0; e < D; ++e) {
@@ -191,11 +197,11 @@ __device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, con
     bool neu = wp && e == g.open;   // beyond the outflow: even ghost, no weight
     long long Ep = F + offp(g, e, ci[e]);   // e-face index ci[e] + 1
     T mep = me[Ep], mem = me[F];
-    T cp = outflow ? T(0) : ue[Ep] - ue[Ep + od_m];
-    T cm = outflow ? T(0) : ue[F] - ue[F + od_m];
+    T cp = outflow ? T(0) : ldm<COH>(ue + Ep) - ldm<COH>(ue + Ep + od_m);
+    T cm = outflow ? T(0) : ldm<COH>(ue + F) - ldm<COH>(ue + F + od_m);
     T udp = T(0), udm = T(0);
-    if (!wp) udp = ud[Ep];
-    if (!wm) udm = ud[F + offm(g, e, ci[e])];
+    if (!wp) udp = ldm<COH>(ud + Ep);
+    if (!wm) udm = ldm<COH>(ud + F + offm(g, e, ci[e]));
     off += mep * (udp + cp) + mem * (udm - cm);
     dgV += (neu ? T(0) : (wp ? T(2) : T(1))) * mep + (wm ? T(2) : T(1)) * mem;
   }
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(256) k_v_rbgs(Geo g, LevelPtrs<T> L, int colou
   L.u[d][F] = (L.uf[d][F] + ir * off) / (L.m[d][F] + ir * dgV);
 }
 
-template <int D, int d, typename T>
+template <int D, int d, typename T, bool COH = false>
 __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T>& L,
                                                  const int ci[3], long long F, T ir) {
   // the plane beyond the last cells of an open axis holds only its outflow faces
@@ -230,8 +236,8 @@ __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T
     return;
   }
   T off, dgV;
-  v_terms<D, d, T>(g, L, ci, F, off, dgV);
-  L.ur[d][F] = L.uf[d][F] - (L.m[d][F] + ir * dgV) * L.u[d][F] + ir * off;
+  v_terms<D, d, T, COH>(g, L, ci, F, off, dgV);
+  L.ur[d][F] = ldm<COH>(L.uf[d] + F) - (L.m[d][F] + ir * dgV) * ldm<COH>(L.u[d] + F) + ir * off;
 }
 
 template <int D, typename T>
@@ -259,6 +265,26 @@ __global__ void __launch_bounds__(256) k_v_residual(Geo g, LevelPtrs<T> L, T ir)
 // its own axis: (1/4, 1/2, 1/4) on the faces 2I-1, 2I, 2I+1; across the other
 // axes the mean of the two children. Both zero the coarse iterate.
 // ---------------------------------------------------------------------------
+template <int D, typename T, bool COH = false>
+__device__ __forceinline__ void restrict_cell_at(const Geo& gf, const Geo& gc,
+                                                 const T* __restrict__ rf, T* __restrict__ fc,
+                                                 T* __restrict__ xc, int I, int J, int K) {
+  long long f0 = gidx(gf, 2 * I, 2 * J, D == 3 ? 2 * K : 0);
+  long long sy = gf.st[1], sz = gf.st[2];
+  T s = ldm<COH>(rf + f0) + ldm<COH>(rf + f0 + 1);
+  s += ldm<COH>(rf + f0 + sy);
+  s += ldm<COH>(rf + f0 + sy + 1);
+  if constexpr (D == 3) {
+    s += ldm<COH>(rf + f0 + sz);
+    s += ldm<COH>(rf + f0 + sz + 1);
+    s += ldm<COH>(rf + f0 + sz + sy);
+    s += ldm<COH>(rf + f0 + sz + sy + 1);
+  }
+  long long c = gidx(gc, I, J, K);
+  fc[c] = s * (D == 3 ? T(0.125) : T(0.25));
+  xc[c] = T(0);
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void restrict_cell_body(const Blk& B, Geo gf, Geo gc,
                                                    const T* __restrict__ rf, T* __restrict__ fc,
@@ -267,20 +293,7 @@ __device__ __forceinline__ void restrict_cell_body(const Blk& B, Geo gf, Geo gc,
   int J = B.y * blockDim.y + threadIdx.y;
   int K = B.z * blockDim.z + threadIdx.z;
   if (I >= gc.n[0] || J >= gc.n[1] || K >= gc.n[2]) return;
-  long long f0 = gidx(gf, 2 * I, 2 * J, D == 3 ? 2 * K : 0);
-  long long sy = gf.st[1], sz = gf.st[2];
-  T s = rf[f0] + rf[f0 + 1];
-  s += rf[f0 + sy];
-  s += rf[f0 + sy + 1];
-  if constexpr (D == 3) {
-    s += rf[f0 + sz];
-    s += rf[f0 + sz + 1];
-    s += rf[f0 + sz + sy];
-    s += rf[f0 + sz + sy + 1];
-  }
-  long long c = gidx(gc, I, J, K);
-  fc[c] = s * (D == 3 ? T(0.125) : T(0.25));
-  xc[c] = T(0);
+  restrict_cell_at<D, T>(gf, gc, rf, fc, xc, I, J, K);
 }
 
 template <int D, typename T>
@@ -289,20 +302,11 @@ __global__ void __launch_bounds__(256) k_restrict_cell(Geo gf, Geo gc, const T* 
   restrict_cell_body<D, T>(own_blk(), gf, gc, rf, fc, xc);
 }
 
-template <int D, int d, typename T>
-__device__ __forceinline__ void restrict_face_body(const Blk& B, Geo gf, Geo gc,
-                                                   const T* __restrict__ rf, T* __restrict__ fc,
-                                                   T* __restrict__ xc) {
-  int C[3];
-  C[0] = B.x * blockDim.x + threadIdx.x;
-  C[1] = B.y * blockDim.y + threadIdx.y;
-  C[2] = B.z * blockDim.z + threadIdx.z;
-  // along d cover the stored faces (walls included), across d the cells
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int lim = (a == d && a < D) ? gc.s[a] : gc.n[a];
-    if (C[a] >= lim) return;
-  }
+// one coarse face C (a stored face along d, a cell across it)
+template <int D, int d, typename T, bool COH = false>
+__device__ __forceinline__ void restrict_face_at(const Geo& gf, const Geo& gc,
+                                                 const T* __restrict__ rf, T* __restrict__ fc,
+                                                 T* __restrict__ xc, const int C[3]) {
   long long c = gidx(gc, C[0], C[1], C[2]);
   xc[c] = T(0);
   bool wallface = !gc.per[d] && (C[d] == 0 || (C[d] == gc.n[d] && d != gc.open));
@@ -329,7 +333,7 @@ __device__ __forceinline__ void restrict_face_body(const Blk& B, Geo gf, Geo gc,
         if (d == gf.open && q > nf) q = nf - 1;   // even ghost beyond the outflow
         f[d] = q;
         T w = (o == 0) ? T(0.5) : T(0.25);
-        along += w * rf[gidx(gf, f[0], f[1], f[2])];
+        along += w * ldm<COH>(rf + gidx(gf, f[0], f[1], f[2]));
       }
       s += along;
     }
@@ -338,9 +342,52 @@ __device__ __forceinline__ void restrict_face_body(const Blk& B, Geo gf, Geo gc,
 }
 
 template <int D, int d, typename T>
+__device__ __forceinline__ void restrict_face_body(const Blk& B, Geo gf, Geo gc,
+                                                   const T* __restrict__ rf, T* __restrict__ fc,
+                                                   T* __restrict__ xc) {
+  int C[3];
+  C[0] = B.x * blockDim.x + threadIdx.x;
+  C[1] = B.y * blockDim.y + threadIdx.y;
+  C[2] = B.z * blockDim.z + threadIdx.z;
+  // along d cover the stored faces (walls included), across d the cells
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int lim = (a == d && a < D) ? gc.s[a] : gc.n[a];
+    if (C[a] >= lim) return;
+  }
+  restrict_face_at<D, d, T>(gf, gc, rf, fc, xc, C);
+}
+
+template <int D, int d, typename T>
 __global__ void __launch_bounds__(256) k_restrict_face(Geo gf, Geo gc, const T* __restrict__ rf,
                                                        T* __restrict__ fc, T* __restrict__ xc) {
   restrict_face_body<D, d, T>(own_blk(), gf, gc, rf, fc, xc);
+}
+
+template <typename T>
+struct Faces3 {
+  T* a[3];
+};
+
+// the three components in one pass over the coarse level's stored extent (3D)
+template <typename T>
+__device__ __forceinline__ void restrict_face3_body(const Blk& B, const Geo& gf, const Geo& gc,
+                                                    const Faces3<T>& rf, const Faces3<T>& fc,
+                                                    const Faces3<T>& xc) {
+  const int C[3] = {(int)(B.x * blockDim.x + threadIdx.x), (int)(B.y * blockDim.y + threadIdx.y),
+                    (int)(B.z * blockDim.z + threadIdx.z)};
+  if (C[0] < gc.s[0] && C[1] < gc.n[1] && C[2] < gc.n[2])
+    restrict_face_at<3, 0, T>(gf, gc, rf.a[0], fc.a[0], xc.a[0], C);
+  if (C[0] < gc.n[0] && C[1] < gc.s[1] && C[2] < gc.n[2])
+    restrict_face_at<3, 1, T>(gf, gc, rf.a[1], fc.a[1], xc.a[1], C);
+  if (C[0] < gc.n[0] && C[1] < gc.n[1] && C[2] < gc.s[2])
+    restrict_face_at<3, 2, T>(gf, gc, rf.a[2], fc.a[2], xc.a[2], C);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_face3(Geo gf, Geo gc, Faces3<T> rf, Faces3<T> fc,
+                                                        Faces3<T> xc) {
+  restrict_face3_body<T>(own_blk(), gf, gc, rf, fc, xc);
 }
 
 // 1D prolongation weights. Cell-centred axis: 3/4 on the parent, 1/4 on the
@@ -392,7 +439,7 @@ __device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], 
 // takes two terms; a missing term has weight 0 and a valid index, and adding
 // its exact zero leaves the sum unchanged, so the loops unroll fully and the
 // index and weight arrays stay in registers.
-template <typename T>
+template <typename T, bool COH = false>
 __device__ __forceinline__ T prol_sum(const Geo& gc, const T* __restrict__ ec, const int idx[3][2],
                                       const T w[3][2]) {
   T v = T(0);
@@ -402,13 +449,29 @@ __device__ __forceinline__ T prol_sum(const Geo& gc, const T* __restrict__ ec, c
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       long long r = gidx(gc, 0, idx[1][b], idx[2][c]);
-      T row = w[0][0] * ec[r + idx[0][0]];
-      row += w[0][1] * ec[r + idx[0][1]];
+      T row = w[0][0] * ldm<COH>(ec + r + idx[0][0]);
+      row += w[0][1] * ldm<COH>(ec + r + idx[0][1]);
       col += w[1][b] * row;
     }
     v += w[2][c] * col;
   }
   return v;
+}
+
+// the coarse correction added at one fine cell fi
+template <int D, typename T, bool COH = false>
+__device__ __forceinline__ void prolong_cell_at(const Geo& gf, const Geo& gc,
+                                                const T* __restrict__ ec, T* __restrict__ xf,
+                                                const int fi[3]) {
+  int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
+  // the pressure correction mirrors evenly at walls and the inflow, oddly at
+  // the outflow, where the pressure is held
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, a == gc.open ? -1 : +1, idx[a], w[a]);
+  const long long x = gidx(gf, fi[0], fi[1], fi[2]);
+  xf[x] = ldm<COH>(xf + x) + prol_sum<T, COH>(gc, ec, idx, w);
 }
 
 template <int D, typename T>
@@ -419,20 +482,31 @@ __device__ __forceinline__ void prolong_cell_body(const Blk& B, Geo gf, Geo gc,
   fi[1] = B.y * blockDim.y + threadIdx.y;
   fi[2] = B.z * blockDim.z + threadIdx.z;
   if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
-  int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
-#pragma unroll
-  // the pressure correction mirrors evenly at walls and the inflow, oddly at
-  // the outflow, where the pressure is held
-  for (int a = 0; a < D; ++a)
-    prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, a == gc.open ? -1 : +1, idx[a], w[a]);
-  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
+  prolong_cell_at<D, T>(gf, gc, ec, xf, fi);
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_prolong_cell(Geo gf, Geo gc, const T* __restrict__ ec,
                                                       T* __restrict__ xf) {
   prolong_cell_body<D, T>(own_blk(), gf, gc, ec, xf);
+}
+
+// the coarse correction added at one fine face fi of component d (not a wall face)
+template <int D, int d, typename T, bool COH = false>
+__device__ __forceinline__ void prolong_face_at(const Geo& gf, const Geo& gc,
+                                                const T* __restrict__ ec, T* __restrict__ xf,
+                                                const int fi[3]) {
+  int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a == d)
+      prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
+    else   // tangential velocity: odd at walls and the inflow, even beyond the outflow
+      prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, a == gc.open ? +1 : -1, idx[a], w[a]);
+  }
+  const long long x = gidx(gf, fi[0], fi[1], fi[2]);
+  xf[x] = ldm<COH>(xf + x) + prol_sum<T, COH>(gc, ec, idx, w);
 }
 
 template <int D, int d, typename T>
@@ -447,22 +521,30 @@ __device__ __forceinline__ void prolong_face_body(const Blk& B, Geo gf, Geo gc,
       fi[2] >= gf.n[2] + (d == 2 && gf.open == 2))
     return;
   if (!gf.per[d] && fi[d] == 0) return;
-  int idx[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (a == d)
-      prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], idx[a], w[a]);
-    else   // tangential velocity: odd at walls and the inflow, even beyond the outflow
-      prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, a == gc.open ? +1 : -1, idx[a], w[a]);
-  }
-  xf[gidx(gf, fi[0], fi[1], fi[2])] += prol_sum<T>(gc, ec, idx, w);
+  prolong_face_at<D, d, T>(gf, gc, ec, xf, fi);
 }
 
 template <int D, int d, typename T>
 __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* __restrict__ ec,
                                                       T* __restrict__ xf) {
   prolong_face_body<D, d, T>(own_blk(), gf, gc, ec, xf);
+}
+
+// the three components in one pass over the fine cells (3D, no open axis)
+template <typename T>
+__device__ __forceinline__ void prolong_face3_body(const Blk& B, const Geo& gf, const Geo& gc,
+                                                   const Faces3<T>& ec, const Faces3<T>& xf) {
+  const int fi[3] = {(int)(B.x * blockDim.x + threadIdx.x), (int)(B.y * blockDim.y + threadIdx.y),
+                     (int)(B.z * blockDim.z + threadIdx.z)};
+  if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
+  if (gf.per[0] || fi[0] != 0) prolong_face_at<3, 0, T>(gf, gc, ec.a[0], xf.a[0], fi);
+  if (gf.per[1] || fi[1] != 0) prolong_face_at<3, 1, T>(gf, gc, ec.a[1], xf.a[1], fi);
+  if (gf.per[2] || fi[2] != 0) prolong_face_at<3, 2, T>(gf, gc, ec.a[2], xf.a[2], fi);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_face3(Geo gf, Geo gc, Faces3<T> ec, Faces3<T> xf) {
+  prolong_face3_body<T>(own_blk(), gf, gc, ec, xf);
 }
 
 // ---------------------------------------------------------------------------
@@ -1219,12 +1301,16 @@ __global__ void __launch_bounds__(256) kb_p_residual32(BArgs A) {
   });
 }
 
-template <int d>
 __global__ void __launch_bounds__(256) kb_restrict_face32(BArgs A) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     const int l = A.lev;
-    restrict_face_body<3, d, float>(B, M.g[l], M.g[l + 1], M.f[l].ur[d], M.f[l + 1].uf[d],
-                                    M.f[l + 1].u[d]);
+    Faces3<float> rf, fc, xc;
+    for (int d = 0; d < 3; ++d) {
+      rf.a[d] = M.f[l].ur[d];
+      fc.a[d] = M.f[l + 1].uf[d];
+      xc.a[d] = M.f[l + 1].u[d];
+    }
+    restrict_face3_body<float>(B, M.g[l], M.g[l + 1], rf, fc, xc);
   });
 }
 
@@ -1235,11 +1321,15 @@ __global__ void __launch_bounds__(256) kb_restrict_cell32(BArgs A) {
   });
 }
 
-template <int d>
 __global__ void __launch_bounds__(256) kb_prolong_face32(BArgs A) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     const int l = A.lev;
-    prolong_face_body<3, d, float>(B, M.g[l], M.g[l + 1], M.f[l + 1].u[d], M.f[l].u[d]);
+    Faces3<float> ec, xf;
+    for (int d = 0; d < 3; ++d) {
+      ec.a[d] = M.f[l + 1].u[d];
+      xf.a[d] = M.f[l].u[d];
+    }
+    prolong_face3_body<float>(B, M.g[l], M.g[l + 1], ec, xf);
   });
 }
 
@@ -1333,7 +1423,8 @@ __global__ void kb_begin(const BMember* __restrict__ tab, int nm, int* __restric
 __global__ void __launch_bounds__(1024) kb_tol_check(cudaGraphConditionalHandle h,
                                                      const BMember* __restrict__ tab, int nm,
                                                      int* __restrict__ act, int which, int sf,
-                                                     int sr, int smax, long long* iters) {
+                                                     int sr, int smax, long long* iters,
+                                                     int use_h) {
   int any = 0;
   for (int m = threadIdx.x; m < nm; m += blockDim.x) {
     if (!act[m]) continue;
@@ -1352,7 +1443,7 @@ __global__ void __launch_bounds__(1024) kb_tol_check(cudaGraphConditionalHandle 
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) {
     ++iters[which];
-    cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (use_h) cudaGraphSetConditional(h, any ? 1u : 0u);
   }
 }
 
@@ -1364,6 +1455,233 @@ __global__ void kb_res_check(const BMember* __restrict__ tab, int nm, int sf, in
     const double rel = f2 > 0.0 ? sqrt(r2) / sqrt(f2) : 0.0;
     if (!(rel <= slack * M.rtol)) ++(*M.nonconv);
   }
+}
+
+
+// ===========================================================================
+// Coarse-level V-cycle in one launch (one cluster per member). The levels
+// below a few thousand cells cost a launch per sweep, residual, transfer and
+// conversion, each a few microseconds of mostly idle GPU; here one cluster of
+// kTailCtas CTAs runs them all, phase after phase, with a cluster barrier
+// (release / acquire) between phases. Sweeps are in place: all red points of
+// a component, a barrier, all black points. The red update reads the old
+// black neighbours and the black update the new red ones, as in the one-pass
+// sweeps, with the same point function (v_red / p_red), so the bits are those
+// of the launches it replaces. Every array a phase writes is read back through
+// L2 (the COH point functions), never through the read-only cache.
+// ===========================================================================
+// the barrier between phases: the cluster's (release / acquire at cluster
+// scope), or the block's when the member has one CTA
+template <int C>
+__device__ __forceinline__ void tail_sync() {
+  if constexpr (C == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("barrier.cluster.arrive.release;\n\t"
+                 "barrier.cluster.wait.acquire;" ::: "memory");
+  }
+}
+
+// one colour of viscous component d on level g, in place
+template <int d>
+__device__ __forceinline__ void tail_v_colour(const Geo& g, const LevelPtrs<float>& L, float ir,
+                                              int colour, int t0, int T) {
+  const int nh = (g.n[0] + 1) >> 1;
+  const int npts = nh * g.n[1] * g.n[2];
+  for (int q = t0; q < npts; q += T) {
+    const int ih = q % nh, r = q / nh;
+    const int j = r % g.n[1], k = r / g.n[1];
+    const int i = 2 * ih + ((j + k + colour) & 1);
+    if (i >= g.n[0]) continue;
+    const int ci[3] = {i, j, k};
+    if (!g.per[d] && ci[d] == 0) continue;   // the wall face stays 0
+    Pt pt;
+    make_pt<3>(g, ci, pt);
+    L.u[d][pt.F] = v_red<3, d, float, true>(L, pt, ir);
+  }
+}
+
+__device__ __forceinline__ void tail_p_colour(const Geo& g, const LevelPtrs<float>& L, float h2,
+                                              int colour, int t0, int T) {
+  const int nh = (g.n[0] + 1) >> 1;
+  const int npts = nh * g.n[1] * g.n[2];
+  for (int q = t0; q < npts; q += T) {
+    const int ih = q % nh, r = q / nh;
+    const int j = r % g.n[1], k = r / g.n[1];
+    const int i = 2 * ih + ((j + k + colour) & 1);
+    if (i >= g.n[0]) continue;
+    const int ci[3] = {i, j, k};
+    Pt pt;
+    make_pt<3>(g, ci, pt);
+    L.p[pt.F] = p_red<3, float, true>(L, pt, h2);
+  }
+}
+
+template <bool V, int C>
+__device__ __forceinline__ void tail_smooth(const BMember& M, int l, int n, int t0, int T) {
+  const Geo g = M.g[l];
+  const LevelPtrs<float> L = M.f[l];
+  for (int it = 0; it < n; ++it) {
+    if (V) {
+      const float ir = (float)(M.inv_re / (g.h * g.h));
+      for (int c = 0; c < 2; ++c) {
+        tail_v_colour<0>(g, L, ir, c, t0, T);
+        tail_sync<C>();
+      }
+      for (int c = 0; c < 2; ++c) {
+        tail_v_colour<1>(g, L, ir, c, t0, T);
+        tail_sync<C>();
+      }
+      for (int c = 0; c < 2; ++c) {
+        tail_v_colour<2>(g, L, ir, c, t0, T);
+        tail_sync<C>();
+      }
+    } else {
+      const float h2 = (float)(g.h * g.h);
+      for (int c = 0; c < 2; ++c) {
+        tail_p_colour(g, L, h2, c, t0, T);
+        tail_sync<C>();
+      }
+    }
+  }
+}
+
+// residual on level l, restricted to level l + 1 (whose iterate it zeroes)
+template <bool V, int C>
+__device__ __forceinline__ void tail_down(const BMember& M, int l, int t0, int T) {
+  const Geo g = M.g[l], gc = M.g[l + 1];
+  const LevelPtrs<float> L = M.f[l], Lc = M.f[l + 1];
+  const int ncell = g.n[0] * g.n[1] * g.n[2];
+  const float ir = (float)(M.inv_re / (g.h * g.h));
+  for (int q = t0; q < ncell; q += T) {
+    const int ci[3] = {q % g.n[0], (q / g.n[0]) % g.n[1], q / (g.n[0] * g.n[1])};
+    const long long F = gidx(g, ci[0], ci[1], ci[2]);
+    if (V) {
+      v_residual_point<3, 0, float, true>(g, L, ci, F, ir);
+      v_residual_point<3, 1, float, true>(g, L, ci, F, ir);
+      v_residual_point<3, 2, float, true>(g, L, ci, F, ir);
+    } else {
+      p_residual_at<3, float, true>(g, L, ci, F);
+    }
+  }
+  tail_sync<C>();
+  if (V) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // along d the stored faces (walls included), across d the cells
+      const int e0 = d == 0 ? gc.s[0] : gc.n[0], e1 = d == 1 ? gc.s[1] : gc.n[1],
+                e2 = d == 2 ? gc.s[2] : gc.n[2];
+      for (int q = t0; q < e0 * e1 * e2; q += T) {
+        const int C[3] = {q % e0, (q / e0) % e1, q / (e0 * e1)};
+        if (d == 0) restrict_face_at<3, 0, float, true>(g, gc, L.ur[0], Lc.uf[0], Lc.u[0], C);
+        else if (d == 1) restrict_face_at<3, 1, float, true>(g, gc, L.ur[1], Lc.uf[1], Lc.u[1], C);
+        else restrict_face_at<3, 2, float, true>(g, gc, L.ur[2], Lc.uf[2], Lc.u[2], C);
+      }
+    }
+  } else {
+    const int nc = gc.n[0] * gc.n[1] * gc.n[2];
+    for (int q = t0; q < nc; q += T)
+      restrict_cell_at<3, float, true>(g, gc, L.pr, Lc.pf, Lc.p, q % gc.n[0],
+                                       (q / gc.n[0]) % gc.n[1], q / (gc.n[0] * gc.n[1]));
+  }
+  tail_sync<C>();
+}
+
+// the correction of level l + 1 prolonged onto level l
+template <bool V, int C>
+__device__ __forceinline__ void tail_up(const BMember& M, int l, int t0, int T) {
+  const Geo g = M.g[l], gc = M.g[l + 1];
+  const LevelPtrs<float> L = M.f[l], Lc = M.f[l + 1];
+  const int ncell = g.n[0] * g.n[1] * g.n[2];
+  for (int q = t0; q < ncell; q += T) {
+    const int fi[3] = {q % g.n[0], (q / g.n[0]) % g.n[1], q / (g.n[0] * g.n[1])};
+    if (V) {
+      if (g.per[0] || fi[0] != 0) prolong_face_at<3, 0, float, true>(g, gc, Lc.u[0], L.u[0], fi);
+      if (g.per[1] || fi[1] != 0) prolong_face_at<3, 1, float, true>(g, gc, Lc.u[1], L.u[1], fi);
+      if (g.per[2] || fi[2] != 0) prolong_face_at<3, 2, float, true>(g, gc, Lc.u[2], L.u[2], fi);
+    } else {
+      prolong_cell_at<3, float, true>(g, gc, Lc.p, L.p, fi);
+    }
+  }
+  tail_sync<C>();
+}
+
+// the coarsest level, on the cluster's first CTA: as kb_coarse
+template <bool V, int C>
+__device__ __forceinline__ void tail_coarse(const BMember& M, int rank) {
+  const int l = M.L - 1;
+  if (rank == 0) {
+    const Geo g = M.g[l];
+    const LevelPtrs<double> Ld = M.d[l];
+    const LevelPtrs<float> Lf = M.f[l];
+    const long long nel = g.st[2] * g.s[2];
+    for (long long q = threadIdx.x; q < nel; q += blockDim.x) {
+      if (V) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          Ld.uf[d][q] = (double)__ldcg(Lf.uf[d] + q);
+          Ld.u[d][q] = 0.0;
+        }
+      } else {
+        Ld.pf[q] = (double)__ldcg(Lf.pf + q);
+        Ld.p[q] = 0.0;
+      }
+    }
+    __syncthreads();
+    const int use = coarse_bytes(3, g, (int)sizeof(double), V) <= kCoarseSmemMax;
+    const Blk B{0, 0, 0, 1, 1, 1};
+    if (V) coarse_v_body<3, double>(B, g, Ld, M.coarse_sweeps, M.inv_re / (g.h * g.h), nel, use);
+    else coarse_p_body<3, double>(B, g, Ld, M.coarse_sweeps, nel, use);
+    __syncthreads();
+    for (long long q = threadIdx.x; q < nel; q += blockDim.x) {
+      if (V) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Lf.u[d][q] = (float)Ld.u[d][q];
+      } else {
+        Lf.p[q] = (float)Ld.p[q];
+      }
+    }
+  }
+  tail_sync<C>();
+}
+
+// one member per C CTAs (a cluster when C > 1)
+template <bool V, int C>
+__device__ __forceinline__ void tail_run(const BMember* __restrict__ tab,
+                                         const int* __restrict__ list, int nlist,
+                                         const int* __restrict__ act) {
+  const int item = blockIdx.x / C;
+  if (item >= nlist) return;
+  const int m = list[item];
+  if (act && !act[m]) return;               // all C CTAs leave together
+  const BMember& M = tab[m];
+  const int rank = blockIdx.x % C;
+  const int t0 = rank * blockDim.x + threadIdx.x, T = C * blockDim.x;
+  const int ls = M.tail, lc = M.L - 1;
+  for (int l = ls; l < lc; ++l) {
+    tail_smooth<V, C>(M, l, M.nu1, t0, T);
+    tail_down<V, C>(M, l, t0, T);
+  }
+  tail_coarse<V, C>(M, rank);
+  for (int l = lc - 1; l >= ls; --l) {
+    tail_up<V, C>(M, l, t0, T);
+    tail_smooth<V, C>(M, l, M.nu2, t0, T);
+  }
+}
+
+template <bool V>
+__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(1024)
+    k_tail(const BMember* __restrict__ tab, const int* __restrict__ list, int nlist,
+           const int* __restrict__ act) {
+  tail_run<V, kTailCtas>(tab, list, nlist, act);
+}
+
+// one CTA per member: many members side by side in one wave
+template <bool V>
+__global__ void __launch_bounds__(1024) k_tail1(const BMember* __restrict__ tab,
+                                                const int* __restrict__ list, int nlist,
+                                                const int* __restrict__ act) {
+  tail_run<V, 1>(tab, list, nlist, act);
 }
 
 }  // namespace
@@ -1458,6 +1776,39 @@ void launch_prolong_face(int D, int d, const Geo& gf, const Geo& gc, const T* ec
     else k_prolong_face<2, 1, T><<<gr, b, 0, s>>>(gf, gc, ec, xf);
   }
 }
+
+template <typename T>
+void launch_restrict_face3(const Geo& gf, const Geo& gc, T* const rf[3], T* const fc[3],
+                           T* const xc[3], cudaStream_t s) {
+  Faces3<T> r, f, x;
+  for (int d = 0; d < 3; ++d) {
+    r.a[d] = rf[d];
+    f.a[d] = fc[d];
+    x.a[d] = xc[d];
+  }
+  dim3 b = blk3(3);
+  k_restrict_face3<T><<<grd3(gc.s[0], gc.s[1], gc.s[2], b), b, 0, s>>>(gf, gc, r, f, x);
+}
+
+template <typename T>
+void launch_prolong_face3(const Geo& gf, const Geo& gc, T* const ec[3], T* const xf[3],
+                          cudaStream_t s) {
+  Faces3<T> e, x;
+  for (int d = 0; d < 3; ++d) {
+    e.a[d] = ec[d];
+    x.a[d] = xf[d];
+  }
+  dim3 b = blk3(3);
+  k_prolong_face3<T><<<grd3(gf.n[0], gf.n[1], gf.n[2], b), b, 0, s>>>(gf, gc, e, x);
+}
+template void launch_restrict_face3<float>(const Geo&, const Geo&, float* const[3],
+                                           float* const[3], float* const[3], cudaStream_t);
+template void launch_restrict_face3<double>(const Geo&, const Geo&, double* const[3],
+                                            double* const[3], double* const[3], cudaStream_t);
+template void launch_prolong_face3<float>(const Geo&, const Geo&, float* const[3],
+                                          float* const[3], cudaStream_t);
+template void launch_prolong_face3<double>(const Geo&, const Geo&, double* const[3],
+                                           double* const[3], cudaStream_t);
 
 size_t coarse_smem_bytes(int D, const Geo& g, int elem, bool viscous) {
   return coarse_bytes(D, g, elem, viscous);
@@ -1677,20 +2028,14 @@ void launch_b_v_residual32(const BArgs& A, int grid, cudaStream_t s) {
 void launch_b_p_residual32(const BArgs& A, int grid, cudaStream_t s) {
   if (A.n > 0) kb_p_residual32<<<grid, blk3(3), 0, s>>>(A);
 }
-void launch_b_restrict_face32(const BArgs& A, int d, int grid, cudaStream_t s) {
-  if (A.n <= 0) return;
-  if (d == 0) kb_restrict_face32<0><<<grid, blk3(3), 0, s>>>(A);
-  else if (d == 1) kb_restrict_face32<1><<<grid, blk3(3), 0, s>>>(A);
-  else kb_restrict_face32<2><<<grid, blk3(3), 0, s>>>(A);
+void launch_b_restrict_face32(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_restrict_face32<<<grid, blk3(3), 0, s>>>(A);
 }
 void launch_b_restrict_cell32(const BArgs& A, int grid, cudaStream_t s) {
   if (A.n > 0) kb_restrict_cell32<<<grid, blk3(3), 0, s>>>(A);
 }
-void launch_b_prolong_face32(const BArgs& A, int d, int grid, cudaStream_t s) {
-  if (A.n <= 0) return;
-  if (d == 0) kb_prolong_face32<0><<<grid, blk3(3), 0, s>>>(A);
-  else if (d == 1) kb_prolong_face32<1><<<grid, blk3(3), 0, s>>>(A);
-  else kb_prolong_face32<2><<<grid, blk3(3), 0, s>>>(A);
+void launch_b_prolong_face32(const BArgs& A, int grid, cudaStream_t s) {
+  if (A.n > 0) kb_prolong_face32<<<grid, blk3(3), 0, s>>>(A);
 }
 void launch_b_prolong_cell32(const BArgs& A, int grid, cudaStream_t s) {
   if (A.n > 0) kb_prolong_cell32<<<grid, blk3(3), 0, s>>>(A);
@@ -1731,12 +2076,37 @@ void launch_b_begin(const BMember* tab, int nm, int* act, int which, int zero_sl
   if (nm > 0) kb_begin<<<(nm + 255) / 256, 256, 0, s>>>(tab, nm, act, which, zero_slot);
 }
 void launch_b_tol_check(cudaGraphConditionalHandle h, const BMember* tab, int nm, int* act,
-                        int which, int sf, int sr, int smax, long long* iters, cudaStream_t s) {
-  kb_tol_check<<<1, 1024, 0, s>>>(h, tab, nm, act, which, sf, sr, smax, iters);
+                        int which, int sf, int sr, int smax, long long* iters, cudaStream_t s,
+                        bool use_h) {
+  kb_tol_check<<<1, 1024, 0, s>>>(h, tab, nm, act, which, sf, sr, smax, iters, use_h ? 1 : 0);
 }
 void launch_b_res_check(const BMember* tab, int nm, int sf, int sr, double slack,
                         cudaStream_t s) {
   if (nm > 0) kb_res_check<<<(nm + 255) / 256, 256, 0, s>>>(tab, nm, sf, sr, slack);
+}
+
+size_t tail_smem(const Geo& coarsest, bool viscous) { return b_coarse_smem(coarsest, viscous); }
+
+cudaError_t tail_set_smem() {
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {(const void*)k_tail<true>, (const void*)k_tail<false>,
+                        (const void*)k_tail1<true>, (const void*)k_tail1<false>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kCoarseSmemMax);
+  return e;
+}
+
+void launch_tail(bool viscous, const BMember* tab, const int* list, int nlist, const int* act,
+                 size_t smem, cudaStream_t s, int ctas) {
+  if (nlist <= 0) return;
+  if (ctas == 1) {
+    if (viscous) k_tail1<true><<<nlist, 1024, smem, s>>>(tab, list, nlist, act);
+    else k_tail1<false><<<nlist, 1024, smem, s>>>(tab, list, nlist, act);
+  } else {
+    if (viscous) k_tail<true><<<nlist * kTailCtas, 1024, smem, s>>>(tab, list, nlist, act);
+    else k_tail<false><<<nlist * kTailCtas, 1024, smem, s>>>(tab, list, nlist, act);
+  }
 }
 
 }  // namespace bf

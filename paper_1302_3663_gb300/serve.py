@@ -129,11 +129,12 @@ def summarize(finished, elapsed, busy=None):
     return out
 
 
-def serial(requests, precision=None, params=None):
+def serial(requests, precision=None, params=None, checks=None):
     """The same requests one after another, each alone (the baseline the
     service is compared with): one untimed step (it captures the step graph),
     then the request's steps timed on the device. Returns cell-steps per
-    second of device time and the total device milliseconds."""
+    second of device time and the total device milliseconds; `checks`, a
+    list, receives each request's statistics after its steps."""
     import torch
     total_ms = 0.0
     cell_steps = 0
@@ -155,5 +156,7 @@ def serial(requests, precision=None, params=None):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
         cell_steps += r.cells * r.steps
+        if checks is not None:
+            checks.append(ctx.get_stats())
         ctx.close()
     return cell_steps / (total_ms / 1e3), total_ms

@@ -93,7 +93,9 @@ def test_uneven_members_bit_identical_to_alone(tune):
     for lev in range(3):
         for kind in (0, 1):
             TY, KC, NP, bx, allb, grid = b.sweep_shape(lev, kind)
-            assert TY >= 1 and KC >= 1 and NP in (1, 2) and bx % 32 == 0 and grid >= 1
+            assert TY >= 1 and KC >= 1 and NP in (1, 2) and bx % 32 == 0
+            # levels the coarse-level cluster kernel takes over have no sweep launch
+            assert grid >= (1 if lev == 0 else 0)
     b.close()
     for c in ctxs:
         c.close()
@@ -168,3 +170,53 @@ def test_members_outside_its_range_are_refused():
         b.close()
         for c in cs:
             c.close()
+
+
+def test_unrolled_loops_and_pinned_shapes_give_the_same_bits():
+    # loops queued as fixed iterations (the masks still stop each member) and
+    # sweep shapes pinned after the plan is built: the same bits again
+    insts = members([32, 48])
+    want = alone(insts, 2)
+    ctxs = [bfibm.load_instance(inst) for inst in insts]
+    b = bfibm.Batch(persistent=True, tune=False)
+    b.set_option(bfibm.BATCH_UNROLL, 40)
+    for c in ctxs:
+        b.add(c)
+    b.step()
+    b.wait()
+    b.set_sweep_shape(0, 0, (2, 5, 2, 64, 0))
+    b.set_sweep_shape(1, 1, (3, 7, 1, 32, 1))
+    assert b.sweep_shape(0, 0)[:5] == (2, 5, 2, 64, 0)
+    assert b.sweep_shape(1, 1)[:5] == (3, 7, 1, 32, 1)
+    for bad in ((0, 8, 1, 32, 0), (4, 8, 3, 32, 0), (4, 8, 1, 48, 0), (40, 8, 1, 64, 0)):
+        with pytest.raises(bfibm.BfibmError):
+            b.set_sweep_shape(0, 0, bad)
+    assert b.sweep_shape(0, 0)[:5] == (2, 5, 2, 64, 0)
+    b.step()
+    assert b.wait() == bfibm.OK
+    for k, c in enumerate(ctxs):
+        assert_same(snapshot(c), want[k][0], "member %d" % k)
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("tail", [0, 8192])
+def test_batch_coarse_level_threshold_keeps_the_bits(tail):
+    # the batch's coarse-level kernel from no level at all to every level of
+    # at most 8192 cells: the same bits as alone
+    insts = members([32, 48, 64])
+    want = alone(insts, 2)
+    ctxs = [bfibm.load_instance(inst) for inst in insts]
+    b = bfibm.Batch(persistent=True, tune=False)
+    b.set_option(bfibm.BATCH_TAIL, tail)
+    for c in ctxs:
+        b.add(c)
+    for _ in range(2):
+        b.step()
+    assert b.wait() == bfibm.OK
+    for k, c in enumerate(ctxs):
+        assert_same(snapshot(c), want[k][0], "member %d" % k)
+    b.close()
+    for c in ctxs:
+        c.close()
