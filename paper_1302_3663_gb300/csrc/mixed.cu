@@ -285,7 +285,7 @@ __device__ __forceinline__ void v_residual_mixed_body(const Blk& B, Geo g, Level
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
+__global__ void __launch_bounds__(256, 3) k_v_residual_mixed(Geo g, LevelPtrs<double> L, F32x3 r32,
                                                           F32x3 e32, Ptr3d diag, double ir,
                                                           double* partial, Ptr3d r64) {
   v_residual_mixed_body<D>(own_blk(), g, L, r32, e32, diag, ir, partial, r64);
@@ -412,7 +412,11 @@ __device__ __forceinline__ bool block_leader() {
   return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
 }
 
-// w = A z on every unknown face (0 on the fixed wall faces); partial sums of z.q
+// w = A z on every unknown face (0 on the fixed wall faces); partial sums of z.q.
+// GB300's FP64 rate bounds this kernel and the FP64 residual: their launch
+// bounds keep 4 and 3 blocks resident per SM (64 and 80 registers) so that
+// enough warps hide the FP64 pipe's and the loads' latency (the batched forms,
+// with the work-list loop's registers on top, keep 2).
 template <int D>
 __device__ __forceinline__ void fcg_apply_body(const Blk& B, Geo g, LevelPtrs<double> L, Ptr3d z,
                                                Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
@@ -442,7 +446,7 @@ __device__ __forceinline__ void fcg_apply_body(const Blk& B, Geo g, LevelPtrs<do
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_fcg_apply(Geo g, LevelPtrs<double> L, Ptr3d z,
+__global__ void __launch_bounds__(256, 4) k_fcg_apply(Geo g, LevelPtrs<double> L, Ptr3d z,
                                                    Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
                                                    double* partial) {
   fcg_apply_body<D>(own_blk(), g, L, z, diag, ir, w, q, partial);
@@ -685,7 +689,7 @@ void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
 // The level-0 FP64 steps of the batched solves: the bodies above over a
 // persistent batch's work list, each with a member's own arrays, scalars and
 // the block decomposition of its single-instance launch.
-__global__ void __launch_bounds__(256) kb_v_residual_mixed(BArgs A, int with_partial, int with_r64) {
+__global__ void __launch_bounds__(256, 2) kb_v_residual_mixed(BArgs A, int with_partial, int with_r64) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     const Geo g = M.g[0];
     F32x3 r, e;
@@ -734,7 +738,7 @@ __global__ void __launch_bounds__(256) kb_z_to_f64(BArgs A) {
   });
 }
 
-__global__ void __launch_bounds__(256) kb_fcg_apply(BArgs A) {
+__global__ void __launch_bounds__(256, 2) kb_fcg_apply(BArgs A) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     const Geo g = M.g[0];
     Ptr3d z, dg, w, q;

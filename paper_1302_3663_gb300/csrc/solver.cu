@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -204,7 +205,7 @@ struct bfibm_ctx {
   int cycles_visc = 0, cycles_p = 0;
   int loop_inner[2] = {1, 1};    // V-cycles per device-loop iteration (visc, p) when captured
   long long graph_kernels = -1;   // kernel nodes in the captured step graph
-  long long version = 0;          // bumped whenever the step graph is dropped: a batch plan
+  long long version = 0;          // changes whenever the step graph is dropped: a batch plan
                                   // built on this context is then rebuilt
   long long partial_cap = 0;      // doubles in sc.partial
   long long tail_cells = 8192;    // BFIBM_OPT_TAIL: FP32 V-cycle levels of at most this many
@@ -240,8 +241,16 @@ bfibm_status cuda_fail(bfibm_ctx* c, cudaError_t e, const char* where) {
     if ((c)->poisoned) return set_err((c), BFIBM_ESTATE, "context poisoned: " + (c)->err); \
   } while (0)
 
+// Versions come from one counter for the whole process: a context created
+// where a destroyed one lived never takes over its version, so a batch plan
+// built for the old one is never mistaken for a plan of the new one.
+long long next_version() {
+  static std::atomic<long long> counter{1};
+  return counter.fetch_add(1);
+}
+
 void drop_graph(bfibm_ctx* c) {
-  ++c->version;
+  c->version = next_version();
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
@@ -1889,6 +1898,7 @@ bfibm_status bfibm_create(const bfibm_params* p, void* stream, bfibm_ctx** out) 
   cudaGetLastError();  // a stale error of an earlier call is not ours
   bfibm_ctx* c = new (std::nothrow) bfibm_ctx();
   if (!c) return BFIBM_ENOMEM;
+  c->version = next_version();
   c->P = *p;
   c->D = p->dim;
   Geo geos[kMaxLevels];
@@ -2753,6 +2763,10 @@ bfibm_status bfibm_batch_add(bfibm_batch* b, bfibm_ctx* c, int32_t* slot) {
 
 bfibm_status bfibm_batch_remove(bfibm_batch* b, int32_t slot) {
   if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].c) return BFIBM_EINVAL;
+  if (b->ps) {   // the plan holds the member's arrays, which may be freed next
+    persist_free(b->ps);
+    b->ps = nullptr;
+  }
   b->slots[slot].c = nullptr;
   b->slots[slot].timed = false;
   return BFIBM_OK;

@@ -4,8 +4,10 @@ Requests (a parameter set, nodes and springs, and a number of time steps)
 arrive over time. A request is admitted as soon as its device footprint fits
 the memory budget (first come, first served); it then keeps its grids and
 node state on the device and advances one time step per tick together with
-every other admitted simulation (one ``bfibm_batch_step`` per tick, each
-simulation replaying its step graph on its own stream). Finished simulations
+every other admitted simulation (one ``bfibm_batch_step`` per tick: each
+simulation replaying its step graph on its own stream, or, with
+``persistent``, all of them in lock step, each multigrid level of their
+solves one launch over all of them). Finished simulations
 hand back their results and free their memory, which admits waiting
 requests. Per-request step latencies come from CUDA events around each
 simulation's step.
@@ -36,11 +38,13 @@ class Request:
 class Server:
     """Admission by device-memory footprint, continuous batching of steps."""
 
-    def __init__(self, budget_bytes, keep_results=True, margin=1.05):
+    def __init__(self, budget_bytes, keep_results=True, margin=1.05, persistent=False):
         self.budget = int(budget_bytes)
         self.margin = margin
         self.keep_results = keep_results
-        self.batch = bfibm.Batch()
+        # the persistent plan is rebuilt whenever a request joins or leaves, so
+        # its sweep shapes keep the built-in choice instead of being timed
+        self.batch = bfibm.Batch(persistent=persistent, tune=False)
         self.used = 0
         self.active = {}          # slot -> (request, context)
         self.ticks = 0

@@ -70,6 +70,33 @@ def test_batch_equals_alone_with_staggered_members(precision):
     b.close()
 
 
+TOL_SOLVER = {"vc_visc": 0, "vc_p": 0, "rtol": 1e-11, "max_cycles": 100, "gamma_coarse": 0.8,
+              "inner_cycles": 2, "krylov": 1, "div_tol": 1e-10}
+
+
+def test_persistent_server_matches_alone_bit_for_bit():
+    # requests stepped in lock step (each multigrid level one launch over the
+    # admitted ones) while others arrive and leave: each result is the bits
+    # of the request alone
+    insts = [small_instance(i, e=32 + 16 * (i % 2)) for i in range(4)]
+    for inst in insts:
+        inst["params"].update(TOL_SOLVER)
+    reqs = [serve.Request(i, inst, 3 + i, arrival=0.01 * i) for i, inst in enumerate(insts)]
+    budget = int(1.05 * (sorted(r.footprint for r in reqs)[-1] + sorted(r.footprint for r in reqs)[-2]))
+    srv = serve.Server(budget, persistent=True)
+    done = srv.run(reqs)
+    srv.close()
+    assert len(done) == 4
+    for r in done:
+        c = bfibm.load_instance(r.inst)
+        c.step(r.steps)
+        want = state(c)
+        c.close()
+        got = r.result["u"] + [r.result["p"], r.result["X"]]
+        for x, y in zip(got, want):
+            assert np.array_equal(x, y)
+
+
 def test_server_queues_by_footprint_and_matches_alone():
     insts = [small_instance(i, e=32 + 16 * (i % 2)) for i in range(4)]
     reqs = [serve.Request(i, inst, 5, arrival=0.02 * i) for i, inst in enumerate(insts)]
