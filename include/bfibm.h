@@ -415,9 +415,9 @@ void bfibm_batch_destroy(bfibm_batch* b);
    gets the same bits as stepped alone. bfibm_batch_step must then give every
    member it steps the same count; the plan (member table, work lists, graph)
    is rebuilt when the stepped members or their options change.
-   BFIBM_BATCH_TUNE (default 1): time the batched sweeps' tile rows, chunk
-   planes, planes per phase and grid on every level of at least 2^19 cells in
-   all when a plan is built. BFIBM_BATCH_UNROLL (default 0): k > 0 queues
+   BFIBM_BATCH_TUNE (default 1): time the batched sweeps' kernel (ring or pair),
+   tile rows, chunk planes, planes per phase and grid on every level of at
+   least 2^19 cells in all when a plan is built. BFIBM_BATCH_UNROLL (default 0): k > 0 queues
    each solve loop as k iterations one after another instead of a device-side
    loop; the masks still stop every member where its tolerance is met, so
    results are the same while k covers the iterations the slowest member needs
@@ -445,16 +445,20 @@ bfibm_status bfibm_batch_set_option(bfibm_batch* b, int option, int64_t value);
 bfibm_status bfibm_batch_info(bfibm_batch* b, int64_t out[8]);
 /* The batched sweep of the current plan on a level (kind 0 viscous, 1
    pressure): out = {tile rows, chunk planes, planes per phase, threads per
-   row, one block per item (1) or resident blocks striding (0), grid}.
-   BFIBM_EINVAL without a plan or for a level it does not have. */
-bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[6]);
+   row, one block per item (1) or resident blocks striding (0), grid, kernel
+   (0 the ring sweep, 1 the pair sweep)}. BFIBM_EINVAL without a plan or for
+   a level it does not have. */
+bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[7]);
 /* Pin the batched sweep of the current plan on a level (kind as above):
    shape = {tile rows, chunk planes, planes per phase (1 or 2), threads per row
    (a multiple of 32; rows x (tile rows + 2) threads at most 1024), one block
-   per item}; the plan's graph is captured again. BFIBM_EINVAL without a plan,
-   for a level it does not have or a shape out of range (the plan unchanged). */
+   per item, kernel (1: the pair sweep, for the viscous kind where every
+   member smoothing on the level has walls across x and y and even rows the
+   block covers, at most 512 threads)}; the plan's graph is captured again.
+   BFIBM_EINVAL without a plan, for a level it does not have or a shape out of
+   range (the plan unchanged). */
 bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
-                                         const int32_t shape[5]);
+                                         const int32_t shape[6]);
 /* Message of the last batch call that failed on the batch itself. */
 const char* bfibm_batch_error(bfibm_batch* b);
 /* Device bytes a context with these parameters allocates for its grids. */

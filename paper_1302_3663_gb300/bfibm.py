@@ -530,16 +530,19 @@ class Batch:
 
     def sweep_shape(self, level, kind):
         """(tile rows, chunk planes, planes per phase, threads per row, one
-        block per item, grid) of the plan's batched sweep; kind 0 viscous, 1
-        pressure"""
-        out = (C.c_int32 * 6)()
+        block per item, grid, kernel: 0 ring, 1 pair) of the plan's batched
+        sweep; kind 0 viscous, 1 pressure"""
+        out = (C.c_int32 * 7)()
         st = self.lib.bfibm_batch_sweep_shape(self.h, int(level), int(kind), out)
         if st != OK:
             raise BfibmError(st, "bfibm_batch_sweep_shape")
         return tuple(int(v) for v in out)
 
     def set_sweep_shape(self, level, kind, shape):
-        a = (C.c_int32 * 5)(*[int(v) for v in shape[:5]])
+        """shape: (rows, chunk planes, planes per phase, threads per row, one
+        block per item[, kernel: 0 ring, 1 pair])"""
+        shape = list(shape[:6]) + [0] * (6 - len(shape[:6]))
+        a = (C.c_int32 * 6)(*[int(v) for v in shape])
         st = self.lib.bfibm_batch_set_sweep_shape(self.h, int(level), int(kind), a)
         if st != OK:
             raise BfibmError(st, "bfibm_batch_set_sweep_shape: " +
@@ -550,7 +553,8 @@ class Batch:
         out = {}
         for lev in range(8):
             try:
-                out[lev] = (self.sweep_shape(lev, 0)[:5], self.sweep_shape(lev, 1)[:5])
+                v, p = self.sweep_shape(lev, 0), self.sweep_shape(lev, 1)
+                out[lev] = (v[:5] + v[6:], p[:5] + p[6:])
             except BfibmError:
                 break
         return out

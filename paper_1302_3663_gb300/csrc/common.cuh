@@ -353,6 +353,11 @@ void launch_b_sweep(const BArgs& A, int K, int TY, int KC, int NP, int bx, size_
                     cudaStream_t s);
 const void* b_sweep_kernel(int K, int NP);
 size_t b_sweep_smem(int NP, int TY, int W);
+// the pair sweep of viscous component d over a work list of pair-eligible
+// members sharing the streaming axis' periodicity (perz); one block of
+// bx x (TY + 2) threads per item; smem: 4 (TY + 2) W floats, W the widest row
+void launch_b_pair(const BArgs& A, int d, bool perz, int TY, int KC, int bx, size_t smem,
+                   cudaStream_t s);
 // after an odd count of sweeps: the current iterate of kind K copied back to
 // its own buffer (items: flat blocks over the level's elements)
 void launch_b_copy_back(const BArgs& A, int K, int grid, cudaStream_t s);

@@ -435,9 +435,8 @@ __device__ __forceinline__ PSet psel(bool t, const PSet& a, const PSet& b) {
 }
 
 template <int d, bool PERZ>
-__global__ void __launch_bounds__(512, 2) k_v_rb_pair(Geo g, LevelPtrs<float> L,
-                                                   float* __restrict__ out, int TY, int KC,
-                                                   float ir) {
+__device__ __forceinline__ void v_rb_pair_body(const Blk& B, Geo g, LevelPtrs<float> L,
+                                               float* __restrict__ out, int TY, int KC, float ir) {
   constexpr int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   float* ring = reinterpret_cast<float*>(sm_raw);
@@ -445,8 +444,8 @@ __global__ void __launch_bounds__(512, 2) k_v_rb_pair(Geo g, LevelPtrs<float> L,
   const int W = n0;                        // ring row pitch
   const int plane = (TY + 2) * W;
   const int x0 = 2 * threadIdx.x, r = threadIdx.y;
-  const int j0 = blockIdx.x * TY;
-  const int k0 = blockIdx.y * KC, k1 = min(k0 + KC, n2);
+  const int j0 = B.x * TY;
+  const int k0 = B.y * KC, k1 = min(k0 + KC, n2);
   const int j = j0 - 1 + r;
   const bool lane_ok = x0 < n0;
   const bool rowvalid = lane_ok && j >= 0 && j < n1;
@@ -715,6 +714,13 @@ __global__ void __launch_bounds__(512, 2) k_v_rb_pair(Geo g, LevelPtrs<float> L,
   }
 }
 
+template <int d, bool PERZ>
+__global__ void __launch_bounds__(512, 2) k_v_rb_pair(Geo g, LevelPtrs<float> L,
+                                                   float* __restrict__ out, int TY, int KC,
+                                                   float ir) {
+  v_rb_pair_body<d, PERZ>(own_blk(), g, L, out, TY, KC, ir);
+}
+
 struct FusedShape {
   dim3 grid, block;
   int TY, KC;
@@ -739,6 +745,21 @@ __global__ void __launch_bounds__(1024) kb_sweep(BArgs A, int TY, int KC) {
       v_rb_fused_body<3, K, float, NP>(B, g, L, L.u2[K], TY, KC, ir);
     }
   });
+}
+
+// Batched pair sweep of viscous component d: block b does item b of the list
+// (one block per item, so no work-list loop adds registers to a kernel at its
+// limit); the block is as wide as the widest member's row needs, and the lanes
+// past a narrower member's row only take part in the barriers.
+template <int d, bool PERZ>
+__global__ void __launch_bounds__(512, 2) kb_pair(BArgs A, int TY, int KC) {
+  const BItem it = A.items[blockIdx.x];
+  if (A.act && !A.act[it.m]) return;
+  const BMember& M = A.tab[it.m];
+  const Geo g = M.g[A.lev];
+  const LevelPtrs<float> L = cur_ptrs(M.f[A.lev], A.cur);
+  const float ir = (float)(M.inv_re / (g.h * g.h));
+  v_rb_pair_body<d, PERZ>(Blk{it.x, it.y, it.z, it.gx, it.gy, it.gz}, g, L, L.u2[d], TY, KC, ir);
 }
 
 // after an odd count of sweeps the current iterate (in the second buffer) is
@@ -935,6 +956,12 @@ cudaError_t fused_set_carveout() {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pair_kernel(d, perz), cudaFuncAttributePreferredSharedMemoryCarveout,
                                  25);
+  const void* bp[6] = {(const void*)kb_pair<0, false>, (const void*)kb_pair<1, false>,
+                       (const void*)kb_pair<2, false>, (const void*)kb_pair<0, true>,
+                       (const void*)kb_pair<1, true>, (const void*)kb_pair<2, true>};
+  for (const void* f : bp)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
   return e;
 }
 
@@ -983,6 +1010,21 @@ void launch_b_sweep(const BArgs& A, int K, int TY, int KC, int NP, int bx, size_
   const dim3 block(bx, TY + 2, 1);
   void* args[] = {(void*)&A, (void*)&TY, (void*)&KC};
   cudaLaunchKernel(b_sweep_kernel(K, NP == 2 ? 2 : 1), dim3(grid), block, args, smem, s);
+}
+
+void launch_b_pair(const BArgs& A, int d, bool perz, int TY, int KC, int bx, size_t smem,
+                   cudaStream_t s) {
+  if (A.n <= 0) return;
+  const dim3 block(bx, TY + 2, 1);
+  if (perz) {
+    if (d == 0) kb_pair<0, true><<<A.n, block, smem, s>>>(A, TY, KC);
+    else if (d == 1) kb_pair<1, true><<<A.n, block, smem, s>>>(A, TY, KC);
+    else kb_pair<2, true><<<A.n, block, smem, s>>>(A, TY, KC);
+  } else {
+    if (d == 0) kb_pair<0, false><<<A.n, block, smem, s>>>(A, TY, KC);
+    else if (d == 1) kb_pair<1, false><<<A.n, block, smem, s>>>(A, TY, KC);
+    else kb_pair<2, false><<<A.n, block, smem, s>>>(A, TY, KC);
+  }
 }
 
 void launch_b_copy_back(const BArgs& A, int K, int grid, cudaStream_t s) {

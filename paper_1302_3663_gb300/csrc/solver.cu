@@ -1229,9 +1229,11 @@ struct PList {
   int grid = 0;   // blocks of a 256-thread launch over the list
 };
 
-struct PShape {   // a batched ring sweep: rows, chunk planes, planes per phase, threads per row
+struct PShape {   // a batched sweep: rows, chunk planes, planes per phase, threads per row
   int TY = 4, KC = 8, NP = 1, bx = 32;
   int all = 0;    // 1: one block per item; 0: the resident blocks stride over the items
+  int kern = 0;   // 0 the ring sweep, 1 the pair sweep (viscous; one block per item)
+  int perz = 0;   // the pair sweep: the streaming axis is periodic in every member
   size_t smem = 0;
   int grid = 0;
 };
@@ -1348,8 +1350,10 @@ cudaError_t sweep_list(Persist& P, int l, int K, PShape& sh, PList& L) {
   const int nm = (int)P.mem.size();
   int W = 0;
   for (int m = 0; m < nm; ++m)
-    if (p_smooths(P, m, l)) W = std::max(W, P.mem[m]->lev[l].g.s[0]);
-  sh.smem = b_sweep_smem(sh.NP, sh.TY, W);
+    if (p_smooths(P, m, l))
+      W = std::max(W, sh.kern ? P.mem[m]->lev[l].g.n[0] : P.mem[m]->lev[l].g.s[0]);
+  sh.smem = sh.kern ? (size_t)4 * (sh.TY + 2) * W * sizeof(float) : b_sweep_smem(sh.NP, sh.TY, W);
+  if (sh.kern) sh.all = 1;
   std::vector<BItem> v;
   make_items(nm, [&](int m) { return p_smooths(P, m, l); },
              [&](int m) {
@@ -1362,6 +1366,10 @@ cudaError_t sweep_list(Persist& P, int l, int K, PShape& sh, PList& L) {
   }
   cudaError_t e = upload(P, v, L);
   if (e != cudaSuccess) return e;
+  if (sh.kern) {
+    sh.grid = L.n;
+    return cudaSuccess;
+  }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_sweep_kernel(K, sh.NP),
                                                     sh.bx * (sh.TY + 2), sh.smem) != cudaSuccess) {
@@ -1423,6 +1431,7 @@ cudaError_t tune_level(Persist& P, int l, int K) {
       for (int KC : {4, 8, 16, 32})
         for (int all : {0, 1}) {
           PShape sh = best;
+          sh.kern = 0;
           sh.NP = NP;
           sh.TY = TY;
           sh.KC = KC;
@@ -1449,6 +1458,51 @@ cudaError_t tune_level(Persist& P, int l, int K) {
             keep = sh;
           }
         }
+  // the pair sweep (viscous): where every member smoothing on the level can
+  // take it, with one block width (the widest row's) for all
+  int bxu = 0, n1min = 1 << 30, perz = -1;
+  bool pair_ok = K < 3 && st == cudaSuccess;
+  for (size_t m = 0; pair_ok && m < P.mem.size(); ++m) {
+    if (!p_smooths(P, (int)m, l)) continue;
+    const Geo& g = P.mem[m]->lev[l].g;
+    pair_ok = !g.per[0] && !g.per[1] && !(g.n[0] & 1) && g.n[0] >= 4 && g.n[0] <= 256 &&
+              (perz < 0 || perz == g.per[2]);
+    perz = g.per[2];
+    bxu = std::max(bxu, (g.n[0] / 2 + 31) / 32 * 32);
+    n1min = std::min(n1min, g.n[1]);
+  }
+  if (pair_ok && perz >= 0)
+    for (int TY : {2, 4, 6, 8, 10, 14})
+      for (int KC : {4, 8, 16, 32}) {
+        if (TY > n1min || bxu * (TY + 2) > 512) continue;
+        PShape sh = best;
+        sh.kern = 1;
+        sh.perz = perz;
+        sh.TY = TY;
+        sh.KC = KC;
+        sh.NP = 1;
+        sh.bx = bxu;
+        st = sweep_list(P, l, K, sh, L);
+        if (st != cudaSuccess) break;
+        if (sh.smem > 48 * 1024) continue;
+        const BArgs A = bargs(P, L, l);
+        float t = 1e30f;
+        for (int round = 0; round < 3 && st == cudaSuccess; ++round) {
+          cudaEventRecord(e0, P.stream);
+          for (int r = 0; r < 3; ++r)
+            launch_b_pair(A, K, sh.perz != 0, sh.TY, sh.KC, sh.bx, sh.smem, P.stream);
+          cudaEventRecord(e1, P.stream);
+          st = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (st == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+          if (round > 0 && ms < t) t = ms;
+        }
+        if (st != cudaSuccess) break;
+        if (t < best_ms) {
+          best_ms = t;
+          keep = sh;
+        }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != cudaSuccess) return st;
@@ -1637,8 +1691,12 @@ void b_smooth(Persist& P, int l, int n, bool V) {
     if (V) {
       for (int d = 0; d < 3; ++d) {
         const PShape& sh = P.shv[l];
-        launch_b_sweep(bargs(P, P.swv[l], l, cur), d, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem, sh.grid,
-                       P.stream);
+        if (sh.kern)
+          launch_b_pair(bargs(P, P.swv[l], l, cur), d, sh.perz != 0, sh.TY, sh.KC, sh.bx, sh.smem,
+                        P.stream);
+        else
+          launch_b_sweep(bargs(P, P.swv[l], l, cur), d, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem,
+                         sh.grid, P.stream);
         cur ^= 1 << d;
       }
     } else {
@@ -2886,7 +2944,7 @@ bfibm_status bfibm_batch_info(bfibm_batch* b, int64_t out[8]) {
   return BFIBM_OK;
 }
 
-bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[6]) {
+bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_t out[7]) {
   if (!b || !out || !b->ps || level < 0 || level >= b->ps->depth || kind < 0 || kind > 1)
     return BFIBM_EINVAL;
   const PShape& sh = kind == 0 ? b->ps->shv[level] : b->ps->shp[level];
@@ -2896,11 +2954,12 @@ bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_
   out[3] = sh.bx;
   out[4] = sh.all;
   out[5] = sh.grid;
+  out[6] = sh.kern;
   return BFIBM_OK;
 }
 
 bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
-                                         const int32_t shape[5]) {
+                                         const int32_t shape[6]) {
   if (!b || !shape || !b->ps || level < 0 || level >= b->ps->depth || kind < 0 || kind > 1)
     return BFIBM_EINVAL;
   Persist& P = *b->ps;
@@ -2910,11 +2969,30 @@ bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
   sh.NP = shape[2];
   sh.bx = shape[3];
   sh.all = shape[4] != 0;
+  sh.kern = shape[5];
   if (sh.TY < 1 || sh.KC < 1 || (sh.NP != 1 && sh.NP != 2) || sh.bx < 32 || sh.bx % 32 ||
-      sh.bx * (sh.TY + 2) > 1024) {
-    b->err = "a sweep shape needs rows >= 1, planes >= 1, 1 or 2 planes per phase and "
-             "32 k threads per row, at most 1024 threads";
+      sh.bx * (sh.TY + 2) > 1024 || sh.kern < 0 || sh.kern > 1) {
+    b->err = "a sweep shape needs rows >= 1, planes >= 1, 1 or 2 planes per phase, "
+             "32 k threads per row, at most 1024 threads and kernel 0 or 1";
     return BFIBM_EINVAL;
+  }
+  if (sh.kern) {   // the pair sweep: viscous, every member eligible, one row width
+    bool ok = kind == 0 && sh.NP == 1 && sh.bx * (sh.TY + 2) <= 512;
+    int perz = -1;
+    for (size_t m = 0; ok && m < P.mem.size(); ++m) {
+      if (!p_smooths(P, (int)m, level)) continue;
+      const Geo& g = P.mem[m]->lev[level].g;
+      ok = !g.per[0] && !g.per[1] && !(g.n[0] & 1) && g.n[0] >= 4 && g.n[0] <= 256 &&
+           sh.TY <= g.n[1] && (g.n[0] / 2 + 31) / 32 * 32 <= sh.bx && (perz < 0 || perz == g.per[2]);
+      perz = g.per[2];
+    }
+    if (!ok) {
+      b->err = "the pair sweep needs the viscous kind, walls across x and y, even rows of 4 to "
+               "256 points no wider than the block, rows >= tile rows, one periodicity along z "
+               "and at most 512 threads";
+      return BFIBM_EINVAL;
+    }
+    sh.perz = perz > 0;
   }
   if (cudaStreamSynchronize(P.stream) != cudaSuccess) {
     cudaGetLastError();

@@ -92,7 +92,8 @@ def test_uneven_members_bit_identical_to_alone(tune):
     assert info["p_iterations"] == sum(max(c[s][1] for c in cyc) // 2 for s in range(3))
     for lev in range(3):
         for kind in (0, 1):
-            TY, KC, NP, bx, allb, grid = b.sweep_shape(lev, kind)
+            TY, KC, NP, bx, allb, grid, kern = b.sweep_shape(lev, kind)
+            assert kern in (0, 1) and (kern == 0 or kind == 0)
             assert TY >= 1 and KC >= 1 and NP in (1, 2) and bx % 32 == 0
             # levels the coarse-level cluster kernel takes over have no sweep launch
             assert grid >= (1 if lev == 0 else 0)
@@ -174,9 +175,10 @@ def test_members_outside_its_range_are_refused():
 
 def test_unrolled_loops_and_pinned_shapes_give_the_same_bits():
     # loops queued as fixed iterations (the masks still stop each member) and
-    # sweep shapes pinned after the plan is built: the same bits again
+    # sweep shapes pinned after the plan is built (the ring sweep, then the
+    # pair sweep): the same bits again
     insts = members([32, 48])
-    want = alone(insts, 2)
+    want = alone(insts, 3)
     ctxs = [bfibm.load_instance(inst) for inst in insts]
     b = bfibm.Batch(persistent=True, tune=False)
     b.set_option(bfibm.BATCH_UNROLL, 40)
@@ -188,10 +190,19 @@ def test_unrolled_loops_and_pinned_shapes_give_the_same_bits():
     b.set_sweep_shape(1, 1, (3, 7, 1, 32, 1))
     assert b.sweep_shape(0, 0)[:5] == (2, 5, 2, 64, 0)
     assert b.sweep_shape(1, 1)[:5] == (3, 7, 1, 32, 1)
-    for bad in ((0, 8, 1, 32, 0), (4, 8, 3, 32, 0), (4, 8, 1, 48, 0), (40, 8, 1, 64, 0)):
+    for bad in ((0, 8, 1, 32, 0), (4, 8, 3, 32, 0), (4, 8, 1, 48, 0), (40, 8, 1, 64, 0),
+                (4, 8, 2, 64, 1, 1),      # the pair sweep takes one plane per phase
+                (40, 8, 1, 64, 1, 1),     # more than 512 threads
+                (4, 8, 1, 64, 1, 2)):
         with pytest.raises(bfibm.BfibmError):
             b.set_sweep_shape(0, 0, bad)
+    with pytest.raises(bfibm.BfibmError):   # no pair sweep for the pressure
+        b.set_sweep_shape(0, 1, (4, 8, 1, 64, 1, 1))
     assert b.sweep_shape(0, 0)[:5] == (2, 5, 2, 64, 0)
+    b.step()
+    b.wait()
+    b.set_sweep_shape(0, 0, (4, 7, 1, 64, 1, 1))   # the pair sweep on the finest level
+    assert b.sweep_shape(0, 0)[6] == 1
     b.step()
     assert b.wait() == bfibm.OK
     for k, c in enumerate(ctxs):
