@@ -305,8 +305,9 @@ __device__ __forceinline__ void add_correction_body(const Blk& B, Geo g, Ptr3d x
     x.a[0][c] += (double)e.a[0][c];
     return;
   }
-  for (int d = 0; d < ncomp; ++d)
-    if (g.per[d] || ci[d] != 0) x.a[d][c] += (double)e.a[d][c];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)   // compile-time components: no local-memory copies
+    if (d < ncomp && (g.per[d] || ci[d] != 0)) x.a[d][c] += (double)e.a[d][c];
 }
 
 template <int D>

@@ -83,6 +83,27 @@ __device__ double block_max(double v, double* sh) {
   return v;
 }
 
+// Tests of the open axis written with compile-time indices only: an array
+// index taken from g.open (or from a value the compiler knows equals it)
+// would put the whole geometry into local memory.
+__device__ __forceinline__ bool is_open(const Geo& g, int a) {
+  return (a == 0 && g.open == 0) || (a == 1 && g.open == 1) || (a == 2 && g.open == 2);
+}
+__device__ __forceinline__ long long st_of(const Geo& g, int a) {
+  return a == 0 ? g.st[0] : (a == 1 ? g.st[1] : g.st[2]);
+}
+// a point on the plane beyond the last cells of an open axis other than d
+template <int d>
+__device__ __forceinline__ bool beyond_outflow(const Geo& g, const int ci[3]) {
+  return (d != 0 && g.open == 0 && ci[0] == g.n[0]) || (d != 1 && g.open == 1 && ci[1] == g.n[1]) ||
+         (d != 2 && g.open == 2 && ci[2] == g.n[2]);
+}
+// a cell in the last layer along the open axis
+__device__ __forceinline__ bool last_open_cell(const Geo& g, const int ci[3]) {
+  return (g.open == 0 && ci[0] == g.n[0] - 1) || (g.open == 1 && ci[1] == g.n[1] - 1) ||
+         (g.open == 2 && ci[2] == g.n[2] - 1);
+}
+
 // decode a flattened cell index over n[0] x n[1] x n[2]
 __device__ __forceinline__ void decode(const Geo& g, long long idx, int& i, int& j, int& k) {
   i = (int)(idx % g.n[0]);
@@ -115,10 +136,10 @@ __device__ __forceinline__ void p_terms(const Geo& g, const LevelPtrs<T>& L, con
       T bb = b[cp];
       num += bb * ldm<COH>(L.p + cp);
       dg += bb;
-    } else if (a == g.open) {
+    } else if (is_open(g, a)) {
       // the outflow face, pressure held there: the homogeneous ghost -p
       // (the held value is in the right-hand side)
-      dg += T(2) * b[c + g.st[a]];
+      dg += T(2) * b[c + st_of(g, a)];
     }
   }
 }
@@ -230,7 +251,7 @@ template <int D, int d, typename T, bool COH = false>
 __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T>& L,
                                                  const int ci[3], long long F, T ir) {
   // the plane beyond the last cells of an open axis holds only its outflow faces
-  if (g.open >= 0 && g.open != d && ci[g.open] == g.n[g.open]) return;
+  if (beyond_outflow<d>(g, ci)) return;
   if (!g.per[d] && ci[d] == 0) {
     L.ur[d][F] = T(0);
     return;
@@ -885,7 +906,7 @@ __device__ __forceinline__ void adv_rhs_point(const Geo& g, const Ptr3& uv, cons
     return;
   }
   // the plane beyond the last cells of an open axis holds only its outflow faces
-  if (g.open >= 0 && g.open != d && ci[g.open] == g.n[g.open]) return;
+  if (beyond_outflow<d>(g, ci)) return;
   const double* __restrict__ ud = uv.a[d];
   // on the outflow face everything beyond mirrors evenly (du/dn = 0)
   const bool outflow = d == g.open && ci[d] == g.n[d];
@@ -959,7 +980,7 @@ __global__ void __launch_bounds__(256) k_divergence(Geo g, Ptr3 u, double* __res
     long long c = gidx(g, ci[0], ci[1], ci[2]);
     double v = scale * div_at<D>(g, u, ci, c);
     // the held outflow pressure: b -= 2 beta_out p_out / h^2 (pbc = 2 p_out / h^2)
-    if (g.open >= 0 && ci[g.open] == g.n[g.open] - 1) v -= beta_open[c + g.st[g.open]] * pbc;
+    if (last_open_cell(g, ci)) v -= beta_open[c + st_of(g, g.open)] * pbc;
     b[c] = v;
     acc += v;
   }
@@ -1044,14 +1065,18 @@ __global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* _
   double mx = 0.0;
   if (g.open >= 0) {   // the outflow faces, one plane beyond the last cells
     const int ci[3] = {i, j, k};
-    const int o = g.open;
-    bool beyond = ci[o] == g.n[o];
-    for (int a = 0; a < D; ++a)
-      if (a != o && ci[a] >= g.n[a]) beyond = false;
-    if (beyond) {
-      long long F = gidx(g, i, j, k);
-      const double pm = p[F - g.st[o]];
-      uv.a[o][F] = proj_face(ut.a[o][F], beta.a[o][F], 2.0 * p_out - pm, pm, coef, g.h);
+#pragma unroll
+    for (int o = 0; o < D; ++o) {   // the open axis, as a compile-time index (see is_open)
+      if (!is_open(g, o)) continue;
+      bool beyond = ci[o] == g.n[o];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (a != o && ci[a] >= g.n[a]) beyond = false;
+      if (beyond) {
+        long long F = gidx(g, i, j, k);
+        const double pm = p[F - g.st[o]];
+        uv.a[o][F] = proj_face(ut.a[o][F], beta.a[o][F], 2.0 * p_out - pm, pm, coef, g.h);
+      }
     }
   }
   if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
@@ -1074,8 +1099,8 @@ __global__ void __launch_bounds__(256) k_project(Geo g, Ptr3 ut, const double* _
       if (g.per[d] || ci[d] != g.n[d] - 1) {
         long long Fu = F + offp(g, d, ci[d]);
         hi = proj_face(ut.a[d][Fu], beta.a[d][Fu], p[Fu], pF, coef, g.h);
-      } else if (d == g.open) {   // the outflow face: ghost 2 p_out - p
-        long long Fu = F + g.st[d];
+      } else if (is_open(g, d)) {   // the outflow face: ghost 2 p_out - p
+        long long Fu = F + st_of(g, d);
         hi = proj_face(ut.a[d][Fu], beta.a[d][Fu], 2.0 * p_out - pF, pF, coef, g.h);
       }
       s += (hi - lo) / g.h;
@@ -1125,9 +1150,11 @@ __device__ __forceinline__ void norm2_body(const Blk& B, Geo g, Ptr3 a, int ncom
       double v = a.a[0][c];
       acc += v * v;
     } else {
-      for (int d = 0; d < ncomp; ++d) {
-        if (d == g.open && ci[d] == g.n[d] - 1) {   // the outflow face is an unknown too
-          double v = a.a[d][c + g.st[d]];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {   // compile-time components (see is_open)
+        if (d >= ncomp) break;
+        if (is_open(g, d) && ci[d] == g.n[d] - 1) {   // the outflow face is an unknown too
+          double v = a.a[d][c + st_of(g, d)];
           acc += v * v;
         }
         if (!g.per[d] && ci[d] == 0) continue;
@@ -1669,8 +1696,15 @@ __device__ __forceinline__ void tail_run(const BMember* __restrict__ tab,
   }
 }
 
+// Threads per CTA: the pressure's coarsest solve sums the right-hand side's
+// mean over 1024 threads, as the one-block coarse kernel does (the same order,
+// the same bits); the viscous kernel has no block reduction and takes 512
+// threads, so that each may hold 128 registers.
 template <bool V>
-__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(1024)
+constexpr int kTailThreads = V ? 512 : 1024;
+
+template <bool V>
+__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads<V>)
     k_tail(const BMember* __restrict__ tab, const int* __restrict__ list, int nlist,
            const int* __restrict__ act) {
   tail_run<V, kTailCtas>(tab, list, nlist, act);
@@ -1678,9 +1712,9 @@ __global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(1024)
 
 // one CTA per member: many members side by side in one wave
 template <bool V>
-__global__ void __launch_bounds__(1024) k_tail1(const BMember* __restrict__ tab,
-                                                const int* __restrict__ list, int nlist,
-                                                const int* __restrict__ act) {
+__global__ void __launch_bounds__(kTailThreads<V>) k_tail1(const BMember* __restrict__ tab,
+                                                           const int* __restrict__ list,
+                                                           int nlist, const int* __restrict__ act) {
   tail_run<V, 1>(tab, list, nlist, act);
 }
 
@@ -2101,11 +2135,13 @@ void launch_tail(bool viscous, const BMember* tab, const int* list, int nlist, c
                  size_t smem, cudaStream_t s, int ctas) {
   if (nlist <= 0) return;
   if (ctas == 1) {
-    if (viscous) k_tail1<true><<<nlist, 1024, smem, s>>>(tab, list, nlist, act);
-    else k_tail1<false><<<nlist, 1024, smem, s>>>(tab, list, nlist, act);
+    if (viscous) k_tail1<true><<<nlist, kTailThreads<true>, smem, s>>>(tab, list, nlist, act);
+    else k_tail1<false><<<nlist, kTailThreads<false>, smem, s>>>(tab, list, nlist, act);
   } else {
-    if (viscous) k_tail<true><<<nlist * kTailCtas, 1024, smem, s>>>(tab, list, nlist, act);
-    else k_tail<false><<<nlist * kTailCtas, 1024, smem, s>>>(tab, list, nlist, act);
+    if (viscous)
+      k_tail<true><<<nlist * kTailCtas, kTailThreads<true>, smem, s>>>(tab, list, nlist, act);
+    else
+      k_tail<false><<<nlist * kTailCtas, kTailThreads<false>, smem, s>>>(tab, list, nlist, act);
   }
 }
 
