@@ -101,6 +101,9 @@ def parse():
     ap.add_argument("--unroll", type=int, default=0,
                     help="persistent batch: solve loops unrolled to this many iterations "
                          "(for a profiler that cannot see inside conditional graph nodes)")
+    ap.add_argument("--tail", type=int, default=None,
+                    help="cell threshold of the coarse-level cluster kernel (0: a launch per "
+                         "phase on every level)")
     ap.add_argument("--batch-tail", type=int, default=None,
                     help="persistent batch: cell threshold of its coarse-level kernel (0: none)")
     ap.add_argument("--save-batch-shapes", default=None,
@@ -418,6 +421,8 @@ def run_ours(args):
     if args.no_graph:
         ctx.set_option(bfibm.OPT_GRAPH, 0)
     ctx.set_option(bfibm.OPT_TMA, args.tma)
+    if args.tail is not None:
+        ctx.set_option(bfibm.OPT_TAIL, args.tail)
     if args.load_plans:
         with open(args.load_plans) as f:
             ctx.pin_sweep_plans(json.load(f))
