@@ -669,9 +669,11 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
   // the one-pass sweep that reads global memory: tile rows and chunk planes
   const int npairs = (g.n[0] + 1) / 2;
   const int bx = npairs >= 128 ? 128 : (npairs + 31) / 32 * 32;
-  // shapes are searched on large levels only: on small ones a launch lasts a
-  // few microseconds and the timing cannot tell the candidates apart
-  const bool search = (long long)g.n[0] * g.n[1] * g.n[2] >= (1 << 19);
+  // shapes are searched on levels of at least 2^16 cells (the 32 x 32 x 64
+  // level and up, where a sweep lasts 5-15 us and the pair sweep beats the
+  // built-in ring shape); on smaller ones a launch lasts a few microseconds and
+  // the timing cannot tell the candidates apart
+  const bool search = (long long)g.n[0] * g.n[1] * g.n[2] >= (1 << 16);
   // bring the clocks up before the first candidate is timed
   for (int r = 0; r < 10; ++r) {
     if (K == 3) launch_p_rb_fused<float>(D, g, L, out, s);
