@@ -121,6 +121,9 @@ struct BMember {
   int coarse_sweeps;
   int nu1, nu2;             // sweeps before and after the coarse-grid correction
   int tail;                 // first level of the coarse-level cluster kernel (L: none)
+  double ir[kMaxLevels];    // inv_re / h^2 per level and 1 / h^2, formed on the host (IEEE
+  double ih2[kMaxLevels];   // division, the same bits as on the device) so that no thread
+                            // divides in FP64
 };
 
 // What every batched kernel takes: its work list, the member table, the mask

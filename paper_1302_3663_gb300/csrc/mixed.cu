@@ -72,7 +72,8 @@ inline dim3 grd3(long long nx, long long ny, long long nz, dim3 b) {
 // nb the launch's blocks; a non-finite residual counts as infinity.
 template <int D>
 __device__ __forceinline__ void p_residual_mixed_body(const Blk& B, Geo g, LevelPtrs<double> L,
-                                                      float* r32, float* e32, double* partial) {
+                                                      float* r32, float* e32, double* partial,
+                                                      double ih2) {
   __shared__ double sh[32];
   int i = B.x * blockDim.x + threadIdx.x;
   int j = B.y * blockDim.y + threadIdx.y;
@@ -97,7 +98,7 @@ __device__ __forceinline__ void p_residual_mixed_body(const Blk& B, Geo g, Level
         dg += bb;
       }
     }
-    double r = L.pf[c] - (num - dg * L.p[c]) * (1.0 / (g.h * g.h));
+    double r = L.pf[c] - (num - dg * L.p[c]) * ih2;   // ih2 = 1 / h^2 from the host
     r32[c] = (float)r;
     e32[c] = 0.0f;
     r2 = r * r;
@@ -117,8 +118,8 @@ __device__ __forceinline__ void p_residual_mixed_body(const Blk& B, Geo g, Level
 
 template <int D>
 __global__ void __launch_bounds__(256) k_p_residual_mixed(Geo g, LevelPtrs<double> L, float* r32,
-                                                          float* e32, double* partial) {
-  p_residual_mixed_body<D>(own_blk(), g, L, r32, e32, partial);
+                                                          float* e32, double* partial, double ih2) {
+  p_residual_mixed_body<D>(own_blk(), g, L, r32, e32, partial, ih2);
 }
 
 // Diagonal of the FP64 viscous operator of component d at face F:
@@ -358,8 +359,9 @@ void launch_p_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, fl
                              float* e32, double* partial, cudaStream_t s) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
-  if (D == 3) k_p_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r32, e32, partial);
-  else k_p_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r32, e32, partial);
+  const double ih2 = 1.0 / (g.h * g.h);
+  if (D == 3) k_p_residual_mixed<3><<<gr, b, 0, s>>>(g, L, r32, e32, partial, ih2);
+  else k_p_residual_mixed<2><<<gr, b, 0, s>>>(g, L, r32, e32, partial, ih2);
 }
 
 void launch_v_residual_mixed(int D, const Geo& g, const LevelPtrs<double>& L, float* const r32[3],
@@ -701,7 +703,7 @@ __global__ void __launch_bounds__(256, 2) kb_v_residual_mixed(BArgs A, int with_
       dg.a[d] = M.vdiag[d];
       rr.a[d] = with_r64 ? M.d[0].ur[d] : nullptr;
     }
-    v_residual_mixed_body<3>(B, g, M.d[0], r, e, dg, M.inv_re / (g.h * g.h),
+    v_residual_mixed_body<3>(B, g, M.d[0], r, e, dg, M.ir[0],
                              with_partial ? M.sc.partial : nullptr, rr);
   });
 }
@@ -709,7 +711,7 @@ __global__ void __launch_bounds__(256, 2) kb_v_residual_mixed(BArgs A, int with_
 __global__ void __launch_bounds__(256) kb_p_residual_mixed(BArgs A, int with_partial) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     p_residual_mixed_body<3>(B, M.g[0], M.d[0], M.f[0].pf, M.f[0].p,
-                             with_partial ? M.sc.partial : nullptr);
+                             with_partial ? M.sc.partial : nullptr, M.ih2[0]);
   });
 }
 
@@ -749,7 +751,7 @@ __global__ void __launch_bounds__(256, 2) kb_fcg_apply(BArgs A) {
       w.a[d] = M.d[0].u2[d];
       q.a[d] = M.cg_q[d];
     }
-    fcg_apply_body<3>(B, g, M.d[0], z, dg, M.inv_re / (g.h * g.h), w, q, M.sc.partial);
+    fcg_apply_body<3>(B, g, M.d[0], z, dg, M.ir[0], w, q, M.sc.partial);
   });
 }
 

@@ -741,8 +741,7 @@ __global__ void __launch_bounds__(1024) kb_sweep(BArgs A, int TY, int KC) {
     if constexpr (K == 3) {
       p_rb_fused_body<3, float, NP>(B, g, L, L.p2, TY, KC);
     } else {
-      const float ir = (float)(M.inv_re / (g.h * g.h));
-      v_rb_fused_body<3, K, float, NP>(B, g, L, L.u2[K], TY, KC, ir);
+      v_rb_fused_body<3, K, float, NP>(B, g, L, L.u2[K], TY, KC, (float)M.ir[A.lev]);
     }
   });
 }
@@ -758,8 +757,8 @@ __global__ void __launch_bounds__(512, 2) kb_pair(BArgs A, int TY, int KC) {
   const BMember& M = A.tab[it.m];
   const Geo g = M.g[A.lev];
   const LevelPtrs<float> L = cur_ptrs(M.f[A.lev], A.cur);
-  const float ir = (float)(M.inv_re / (g.h * g.h));
-  v_rb_pair_body<d, PERZ>(Blk{it.x, it.y, it.z, it.gx, it.gy, it.gz}, g, L, L.u2[d], TY, KC, ir);
+  v_rb_pair_body<d, PERZ>(Blk{it.x, it.y, it.z, it.gx, it.gy, it.gz}, g, L, L.u2[d], TY, KC,
+                          (float)M.ir[A.lev]);
 }
 
 // after an odd count of sweeps the current iterate (in the second buffer) is

@@ -426,6 +426,11 @@ void fill_member(const bfibm_ctx* c, BMember& B) {
   B.nu1 = c->P.nu1;
   B.nu2 = c->P.nu2;
   B.tail = c->tail_lev;
+  for (int l = 0; l < c->L; ++l) {
+    const double h = c->lev[l].g.h;
+    B.ir[l] = c->P.inv_re / (h * h);
+    B.ih2[l] = 1.0 / (h * h);
+  }
 }
 
 // the context's own one-member table, with its current settings

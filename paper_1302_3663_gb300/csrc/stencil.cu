@@ -160,28 +160,28 @@ __global__ void __launch_bounds__(256) k_p_rbgs(Geo g, LevelPtrs<T> L, int colou
   L.p[c] = (num - h2 * L.pf[c]) / dg;
 }
 
+// ih2 = (T)(1 / h^2), formed once on the host
 template <int D, typename T, bool COH = false>
 __device__ __forceinline__ void p_residual_at(const Geo& g, const LevelPtrs<T>& L,
-                                              const int ci[3], long long c) {
+                                              const int ci[3], long long c, T ih2) {
   T num, dg;
   p_terms<D, T, COH>(g, L, ci, c, num, dg);
-  T ih2 = (T)(1.0 / (g.h * g.h));
   L.pr[c] = ldm<COH>(L.pf + c) - (num - dg * ldm<COH>(L.p + c)) * ih2;
 }
 
 template <int D, typename T>
-__device__ __forceinline__ void p_residual_body(const Blk& B, Geo g, LevelPtrs<T> L) {
+__device__ __forceinline__ void p_residual_body(const Blk& B, Geo g, LevelPtrs<T> L, T ih2) {
   int i = B.x * blockDim.x + threadIdx.x;
   int j = B.y * blockDim.y + threadIdx.y;
   int k = B.z * blockDim.z + threadIdx.z;
   if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
   int ci[3] = {i, j, k};
-  p_residual_at<D, T>(g, L, ci, gidx(g, i, j, k));
+  p_residual_at<D, T>(g, L, ci, gidx(g, i, j, k), ih2);
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L) {
-  p_residual_body<D, T>(own_blk(), g, L);
+__global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L, T ih2) {
+  p_residual_body<D, T>(own_blk(), g, L, ih2);
 }
 
 // ---------------------------------------------------------------------------
@@ -1316,15 +1316,13 @@ __global__ void k_fill(double* a, long long n, double v) {
 // ===========================================================================
 __global__ void __launch_bounds__(256) kb_v_residual32(BArgs A) {
   for_items(A, [&](const BMember& M, const Blk& B) {
-    const Geo g = M.g[A.lev];
-    const float ir = (float)(M.inv_re / (g.h * g.h));
-    v_residual_body<3, float>(B, g, cur_ptrs(M.f[A.lev], A.cur), ir);
+    v_residual_body<3, float>(B, M.g[A.lev], cur_ptrs(M.f[A.lev], A.cur), (float)M.ir[A.lev]);
   });
 }
 
 __global__ void __launch_bounds__(256) kb_p_residual32(BArgs A) {
   for_items(A, [&](const BMember& M, const Blk& B) {
-    p_residual_body<3, float>(B, M.g[A.lev], cur_ptrs(M.f[A.lev], A.cur));
+    p_residual_body<3, float>(B, M.g[A.lev], cur_ptrs(M.f[A.lev], A.cur), (float)M.ih2[A.lev]);
   });
 }
 
@@ -1393,7 +1391,7 @@ __global__ void __launch_bounds__(1024) kb_coarse(BArgs A) {
     }
     __syncthreads();
     const int use = coarse_bytes(3, g, (int)sizeof(double), V) <= kCoarseSmemMax;
-    if (V) coarse_v_body<3, double>(B, g, Ld, M.coarse_sweeps, M.inv_re / (g.h * g.h), nel, use);
+    if (V) coarse_v_body<3, double>(B, g, Ld, M.coarse_sweeps, M.ir[A.lev], nel, use);
     else coarse_p_body<3, double>(B, g, Ld, M.coarse_sweeps, nel, use);
     __syncthreads();
     for (long long q = threadIdx.x; q < nel; q += blockDim.x) {
@@ -1550,7 +1548,7 @@ __device__ __forceinline__ void tail_smooth(const BMember& M, int l, int n, int 
   const LevelPtrs<float> L = M.f[l];
   for (int it = 0; it < n; ++it) {
     if (V) {
-      const float ir = (float)(M.inv_re / (g.h * g.h));
+      const float ir = (float)M.ir[l];
       for (int c = 0; c < 2; ++c) {
         tail_v_colour<0>(g, L, ir, c, t0, T);
         tail_sync<C>();
@@ -1579,7 +1577,7 @@ __device__ __forceinline__ void tail_down(const BMember& M, int l, int t0, int T
   const Geo g = M.g[l], gc = M.g[l + 1];
   const LevelPtrs<float> L = M.f[l], Lc = M.f[l + 1];
   const int ncell = g.n[0] * g.n[1] * g.n[2];
-  const float ir = (float)(M.inv_re / (g.h * g.h));
+  const float ir = (float)M.ir[l];
   for (int q = t0; q < ncell; q += T) {
     const int ci[3] = {q % g.n[0], (q / g.n[0]) % g.n[1], q / (g.n[0] * g.n[1])};
     const long long F = gidx(g, ci[0], ci[1], ci[2]);
@@ -1588,7 +1586,7 @@ __device__ __forceinline__ void tail_down(const BMember& M, int l, int t0, int T
       v_residual_point<3, 1, float, true>(g, L, ci, F, ir);
       v_residual_point<3, 2, float, true>(g, L, ci, F, ir);
     } else {
-      p_residual_at<3, float, true>(g, L, ci, F);
+      p_residual_at<3, float, true>(g, L, ci, F, (float)M.ih2[l]);
     }
   }
   tail_sync<C>();
@@ -1657,7 +1655,7 @@ __device__ __forceinline__ void tail_coarse(const BMember& M, int rank) {
     __syncthreads();
     const int use = coarse_bytes(3, g, (int)sizeof(double), V) <= kCoarseSmemMax;
     const Blk B{0, 0, 0, 1, 1, 1};
-    if (V) coarse_v_body<3, double>(B, g, Ld, M.coarse_sweeps, M.inv_re / (g.h * g.h), nel, use);
+    if (V) coarse_v_body<3, double>(B, g, Ld, M.coarse_sweeps, M.ir[l], nel, use);
     else coarse_p_body<3, double>(B, g, Ld, M.coarse_sweeps, nel, use);
     __syncthreads();
     for (long long q = threadIdx.x; q < nel; q += blockDim.x) {
@@ -1735,8 +1733,9 @@ template <typename T>
 void launch_p_residual(int D, const Geo& g, const LevelPtrs<T>& L, cudaStream_t s) {
   dim3 b = blk3(D);
   dim3 gr = grd3(g.n[0], g.n[1], g.n[2], b);
-  if (D == 3) k_p_residual<3, T><<<gr, b, 0, s>>>(g, L);
-  else k_p_residual<2, T><<<gr, b, 0, s>>>(g, L);
+  const T ih2 = (T)(1.0 / (g.h * g.h));
+  if (D == 3) k_p_residual<3, T><<<gr, b, 0, s>>>(g, L, ih2);
+  else k_p_residual<2, T><<<gr, b, 0, s>>>(g, L, ih2);
 }
 
 template <typename T>
