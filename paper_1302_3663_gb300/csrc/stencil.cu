@@ -197,13 +197,16 @@ __global__ void __launch_bounds__(256) k_p_residual(Geo g, LevelPtrs<T> L, T ih2
 // viscosity) and the tangential components mirror too (du_e/dx_d = 0 there).
 // Across the outflow (e = open, last cell) the tangential u_d mirrors evenly:
 // that edge contributes its cross term only.
+// q: the point's neighbour offsets and wall flags (make_pt), formed once per
+// point and shared by the components of a residual.
 template <int D, int d, typename T, bool COH = false>
-__device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
-                                        long long F, T& off, T& dgV) {
+__device__ __forceinline__ void v_terms_q(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
+                                          const Pt& q, T& off, T& dgV) {
   const T* __restrict__ ud = L.u[d];
+  const int F = q.F;
   const bool outflow = d == g.open && ci[d] == g.n[d];
-  long long od_m = offm(g, d, ci[d]);
-  long long od_p = outflow ? od_m : offp(g, d, ci[d]);
+  const int od_m = q.om[d];
+  const int od_p = outflow ? od_m : q.op[d];
   T mcp = outflow ? L.muc[F + od_m] : L.muc[F], mcm = L.muc[F + od_m];
   off = T(2) * (mcp * ldm<COH>(ud + F + od_p) + mcm * ldm<COH>(ud + F + od_m));
   dgV = T(2) * (mcp + mcm);
@@ -212,20 +215,27 @@ __device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, con
     if (e == d) continue;
     const T* __restrict__ ue = L.u[e];
     const T* __restrict__ me = L.mue[edge_id(d, e)];
-    bool pe = g.per[e] != 0;
-    bool wp = !pe && ci[e] == g.n[e] - 1;
-    bool wm = !pe && ci[e] == 0;
+    const bool wp = q.wp[e];
+    const bool wm = q.wm[e];
     bool neu = wp && e == g.open;   // beyond the outflow: even ghost, no weight
-    long long Ep = F + offp(g, e, ci[e]);   // e-face index ci[e] + 1
+    const int Ep = F + q.op[e];     // e-face index ci[e] + 1
     T mep = me[Ep], mem = me[F];
     T cp = outflow ? T(0) : ldm<COH>(ue + Ep) - ldm<COH>(ue + Ep + od_m);
     T cm = outflow ? T(0) : ldm<COH>(ue + F) - ldm<COH>(ue + F + od_m);
     T udp = T(0), udm = T(0);
     if (!wp) udp = ldm<COH>(ud + Ep);
-    if (!wm) udm = ldm<COH>(ud + F + offm(g, e, ci[e]));
+    if (!wm) udm = ldm<COH>(ud + F + q.om[e]);
     off += mep * (udp + cp) + mem * (udm - cm);
     dgV += (neu ? T(0) : (wp ? T(2) : T(1))) * mep + (wm ? T(2) : T(1)) * mem;
   }
+}
+
+template <int D, int d, typename T, bool COH = false>
+__device__ __forceinline__ void v_terms(const Geo& g, const LevelPtrs<T>& L, const int ci[3],
+                                        long long F, T& off, T& dgV) {
+  Pt q;
+  make_pt<D>(g, ci, q);
+  v_terms_q<D, d, T, COH>(g, L, ci, q, off, dgV);
 }
 
 template <int D, int d, typename T>
@@ -249,7 +259,8 @@ __global__ void __launch_bounds__(256) k_v_rbgs(Geo g, LevelPtrs<T> L, int colou
 
 template <int D, int d, typename T, bool COH = false>
 __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T>& L,
-                                                 const int ci[3], long long F, T ir) {
+                                                 const int ci[3], const Pt& q, T ir) {
+  const int F = q.F;
   // the plane beyond the last cells of an open axis holds only its outflow faces
   if (beyond_outflow<d>(g, ci)) return;
   if (!g.per[d] && ci[d] == 0) {
@@ -257,7 +268,7 @@ __device__ __forceinline__ void v_residual_point(const Geo& g, const LevelPtrs<T
     return;
   }
   T off, dgV;
-  v_terms<D, d, T, COH>(g, L, ci, F, off, dgV);
+  v_terms_q<D, d, T, COH>(g, L, ci, q, off, dgV);
   L.ur[d][F] = ldm<COH>(L.uf[d] + F) - (L.m[d][F] + ir * dgV) * ldm<COH>(L.u[d] + F) + ir * off;
 }
 
@@ -269,10 +280,11 @@ __device__ __forceinline__ void v_residual_body(const Blk& B, Geo g, LevelPtrs<T
   if (i >= g.n[0] + (g.open == 0) || j >= g.n[1] + (g.open == 1) || k >= g.n[2] + (g.open == 2))
     return;
   int ci[3] = {i, j, k};
-  long long F = gidx(g, i, j, k);
-  v_residual_point<D, 0, T>(g, L, ci, F, ir);
-  v_residual_point<D, 1, T>(g, L, ci, F, ir);
-  if constexpr (D == 3) v_residual_point<D, 2, T>(g, L, ci, F, ir);
+  Pt q;
+  make_pt<D>(g, ci, q);
+  v_residual_point<D, 0, T>(g, L, ci, q, ir);
+  v_residual_point<D, 1, T>(g, L, ci, q, ir);
+  if constexpr (D == 3) v_residual_point<D, 2, T>(g, L, ci, q, ir);
 }
 
 template <int D, typename T>
@@ -1580,13 +1592,14 @@ __device__ __forceinline__ void tail_down(const BMember& M, int l, int t0, int T
   const float ir = (float)M.ir[l];
   for (int q = t0; q < ncell; q += T) {
     const int ci[3] = {q % g.n[0], (q / g.n[0]) % g.n[1], q / (g.n[0] * g.n[1])};
-    const long long F = gidx(g, ci[0], ci[1], ci[2]);
+    Pt pt;
+    make_pt<3>(g, ci, pt);
     if (V) {
-      v_residual_point<3, 0, float, true>(g, L, ci, F, ir);
-      v_residual_point<3, 1, float, true>(g, L, ci, F, ir);
-      v_residual_point<3, 2, float, true>(g, L, ci, F, ir);
+      v_residual_point<3, 0, float, true>(g, L, ci, pt, ir);
+      v_residual_point<3, 1, float, true>(g, L, ci, pt, ir);
+      v_residual_point<3, 2, float, true>(g, L, ci, pt, ir);
     } else {
-      p_residual_at<3, float, true>(g, L, ci, F, (float)M.ih2[l]);
+      p_residual_at<3, float, true>(g, L, ci, pt.F, (float)M.ih2[l]);
     }
   }
   tail_sync<C>();
