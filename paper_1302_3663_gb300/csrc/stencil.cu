@@ -563,16 +563,39 @@ __global__ void __launch_bounds__(256) k_prolong_face(Geo gf, Geo gc, const T* _
   prolong_face_body<D, d, T>(own_blk(), gf, gc, ec, xf);
 }
 
-// the three components in one pass over the fine cells (3D, no open axis)
+// the three components in one pass over the fine cells (3D, no open axis).
+// Each axis's 1D weights and indices are formed once per cell, by the cell
+// rule (a tangential axis, odd mirror at walls) and by the face rule (the
+// component's own axis), and shared by the components; the sums are those of
+// prolong_face_at, term for term.
 template <typename T>
 __device__ __forceinline__ void prolong_face3_body(const Blk& B, const Geo& gf, const Geo& gc,
                                                    const Faces3<T>& ec, const Faces3<T>& xf) {
   const int fi[3] = {(int)(B.x * blockDim.x + threadIdx.x), (int)(B.y * blockDim.y + threadIdx.y),
                      (int)(B.z * blockDim.z + threadIdx.z)};
   if (fi[0] >= gf.n[0] || fi[1] >= gf.n[1] || fi[2] >= gf.n[2]) return;
-  if (gf.per[0] || fi[0] != 0) prolong_face_at<3, 0, T>(gf, gc, ec.a[0], xf.a[0], fi);
-  if (gf.per[1] || fi[1] != 0) prolong_face_at<3, 1, T>(gf, gc, ec.a[1], xf.a[1], fi);
-  if (gf.per[2] || fi[2] != 0) prolong_face_at<3, 2, T>(gf, gc, ec.a[2], xf.a[2], fi);
+  int cidx[3][2], fidx[3][2];
+  T cw[3][2], fw[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, -1, cidx[a], cw[a]);
+    prol_face_1d<T>(fi[a], gc.n[a], gc.per[a], fidx[a], fw[a]);
+  }
+  const long long x = gidx(gf, fi[0], fi[1], fi[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (!gf.per[d] && fi[d] == 0) continue;   // the wall face
+    int idx[3][2];
+    T w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        idx[a][t] = a == d ? fidx[a][t] : cidx[a][t];
+        w[a][t] = a == d ? fw[a][t] : cw[a][t];
+      }
+    xf.a[d][x] = xf.a[d][x] + prol_sum<T>(gc, ec.a[d], idx, w);
+  }
 }
 
 template <typename T>
