@@ -1431,16 +1431,23 @@ cudaError_t tune_level(Persist& P, int l, int K) {
   }
   float best_ms = 1e30f;
   PShape keep = best;
+  // the ring sweep: one thread per point pair of the widest row on up to 8
+  // rows, or 32 threads per row (several pairs each) on taller tiles
+  const int bx0 = best.bx;
+  const int rows[7][2] = {{2, 0}, {4, 0}, {6, 0}, {8, 0}, {8, 32}, {12, 32}, {16, 32}};
   for (int NP : {1, 2})
-    for (int TY : {2, 4, 6, 8})
+    for (const auto& rw : rows)
       for (int KC : {4, 8, 16, 32})
         for (int all : {0, 1}) {
+          const int TY = rw[0];
           PShape sh = best;
           sh.kern = 0;
           sh.NP = NP;
           sh.TY = TY;
           sh.KC = KC;
           sh.all = all;
+          sh.bx = rw[1] ? rw[1] : bx0;
+          if (rw[1] && rw[1] >= bx0) continue;
           if (sh.bx * (TY + 2) > 1024) continue;
           st = sweep_list(P, l, K, sh, L);
           if (st != cudaSuccess) break;
