@@ -320,18 +320,16 @@ bfibm_status bfibm_tma_plan(bfibm_ctx* c, int level, int kind, int32_t out[5]);
    {tile rows, planes per chunk, planes per phase, threads per row, kernel};
    kernel 0 is the ring sweep (a thread per point pair or per 32-thread row
    group, a ring of new red planes, 0 in the first four fields standing for the
-   built-in choice), kernel 1 the pair sweep of a viscous component (a thread
-   per (red, black) pair of a row marching over the planes, two float2 row
-   loads per array and plane; planes per phase 1, threads per row 0). Both
-   give the same bits. BFIBM_EINVAL for an FP64 context, a bad level or kind,
+   built-in choice), kernel 1 the pair sweep (a thread per (red, black) pair
+   of a row marching over the planes, float2 row loads; planes per phase 1,
+   threads per row 0). Both give the same bits. BFIBM_EINVAL for an FP64 context, a bad level or kind,
    or a level shape the tuner has not timed. No counterpart in the paper. */
 bfibm_status bfibm_sweep_shape(bfibm_ctx* c, int level, int kind, int32_t out[5]);
 /* Pin the one-pass FP32 sweep with shape {tile rows (0: built-in), planes per
    chunk (0: built-in), planes per phase (1 or 2), threads per row (0 or a
    multiple of 32 up to 128), kernel (0 ring sweep; 1 pair sweep, which takes
    tile rows >= 1, planes per chunk >= 1, planes per phase 1, threads per row
-   0, a viscous kind and a level with walls in x and y and an even row of at
-   most 256 points)} for the shape of one level and kind, process-wide, in
+   0 and a level with walls in x and y and an even row of at most 256 points)} for the shape of one level and kind, process-wide, in
    place of the autotuner's choice (the TMA sweep is no longer used there);
    the next step captures a new step graph. 3D mixed-precision contexts only;
    BFIBM_EINVAL otherwise or for a shape outside those ranges. Same results to
@@ -452,9 +450,9 @@ bfibm_status bfibm_batch_sweep_shape(bfibm_batch* b, int level, int kind, int32_
 /* Pin the batched sweep of the current plan on a level (kind as above):
    shape = {tile rows, chunk planes, planes per phase (1 or 2), threads per row
    (a multiple of 32; rows x (tile rows + 2) threads at most 1024), one block
-   per item, kernel (1: the pair sweep, for the viscous kind where every
-   member smoothing on the level has walls across x and y and even rows the
-   block covers, at most 512 threads)}; the plan's graph is captured again.
+   per item, kernel (1: the pair sweep, where every member smoothing on the
+   level has walls across x and y and even rows the block covers, at most 512
+   threads)}; the plan's graph is captured again.
    BFIBM_EINVAL without a plan, for a level it does not have or a shape out of
    range (the plan unchanged). */
 bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,

@@ -73,6 +73,21 @@ __device__ __forceinline__ float vx_final(float rhs, float ir, float off, float 
   return __fmul_rn(__fmaf_rn(ir, off, rhs), idg);
 }
 
+// The FP32 pressure point update, Eq. (divergenceGrad) in the order of the
+// two-kernel sweep (neighbours axis 0, 1, 2, lower then upper), every
+// rounding written out so that every FP32 pressure sweep (ring, pair, TMA,
+// the coarse-level kernel) gives the same bits:
+//   num = fma(beta_nb, p_nb, num), dg = dg + beta_nb per neighbour,
+//   p = fma(-h^2, f, num) / dg
+// A neighbour beyond a wall may enter with beta 0 and p 0: it changes no bit.
+__device__ __forceinline__ void px_acc(float& num, float& dg, float b, float p) {
+  num = __fmaf_rn(b, p, num);
+  dg = __fadd_rn(dg, b);
+}
+__device__ __forceinline__ float px_final(float num, float dg, float h2, float f) {
+  return __fdiv_rn(__fmaf_rn(-h2, f, num), dg);
+}
+
 struct Scalars {
   double* partial;   // kRedBlocks partial results
   double* out;       // 16 finalized scalars
@@ -222,6 +237,10 @@ int ring_fill_kc(int D, int K, const Geo& g, int TY, int NP, int BX, int waves);
 bool pair_eligible(int D, const Geo& g, int TY);
 void launch_v_rb_pair(const Geo& g, const LevelPtrs<float>& L, int d, float* out, double inv_re,
                       cudaStream_t s, int TY, int KC);
+// the pair sweep of the 3D FP32 pressure (same eligibility and shapes)
+void launch_p_rb_pair(const Geo& g, const LevelPtrs<float>& L, float* out, cudaStream_t s, int TY,
+                      int KC);
+// d: 0..2 viscous component, 3 pressure
 int pair_fill_kc(const Geo& g, int d, int TY, int waves);
 
 // Mixed precision (mixed.cu).
@@ -361,6 +380,9 @@ size_t b_sweep_smem(int NP, int TY, int W);
 // bx x (TY + 2) threads per item; smem: 4 (TY + 2) W floats, W the widest row
 void launch_b_pair(const BArgs& A, int d, bool perz, int TY, int KC, int bx, size_t smem,
                    cudaStream_t s);
+// the same for the pressure
+void launch_b_ppair(const BArgs& A, bool perz, int TY, int KC, int bx, size_t smem,
+                    cudaStream_t s);
 // after an odd count of sweeps: the current iterate of kind K copied back to
 // its own buffer (items: flat blocks over the level's elements)
 void launch_b_copy_back(const BArgs& A, int K, int grid, cudaStream_t s);

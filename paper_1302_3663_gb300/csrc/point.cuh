@@ -63,16 +63,23 @@ __device__ __forceinline__ T p_red(const LevelPtrs<T>& L, const Pt& q, T h2) {
     const T* __restrict__ b = L.beta[a];
     if (!q.wm[a]) {
       T bb = b[q.F];
-      num += bb * ldm<COH>(L.p + q.F + q.om[a]);
-      dg += bb;
+      if constexpr (sizeof(T) == 4) px_acc(num, dg, bb, ldm<COH>(L.p + q.F + q.om[a]));
+      else {
+        num += bb * ldm<COH>(L.p + q.F + q.om[a]);
+        dg += bb;
+      }
     }
     if (!q.wp[a]) {
       T bb = b[q.F + q.op[a]];
-      num += bb * ldm<COH>(L.p + q.F + q.op[a]);
-      dg += bb;
+      if constexpr (sizeof(T) == 4) px_acc(num, dg, bb, ldm<COH>(L.p + q.F + q.op[a]));
+      else {
+        num += bb * ldm<COH>(L.p + q.F + q.op[a]);
+        dg += bb;
+      }
     }
   }
-  return (num - h2 * ldm<COH>(L.pf + q.F)) / dg;
+  if constexpr (sizeof(T) == 4) return px_final(num, dg, h2, ldm<COH>(L.pf + q.F));
+  else return (num - h2 * ldm<COH>(L.pf + q.F)) / dg;
 }
 
 // ---------------------------------------------------------------------------

@@ -79,16 +79,25 @@ __device__ __forceinline__ T p_black(const LevelPtrs<T>& L, const Ring<T>& rg, c
     const T* __restrict__ b = L.beta[a];
     if (!q.wm[a]) {
       T bb = b[q.F];
-      num += bb * ring_nb<D, T>(rg, q, i, n0, a, -1, r, sl_m, sl_0, sl_p);
-      dg += bb;
+      const T pn = ring_nb<D, T>(rg, q, i, n0, a, -1, r, sl_m, sl_0, sl_p);
+      if constexpr (sizeof(T) == 4) px_acc(num, dg, bb, pn);
+      else {
+        num += bb * pn;
+        dg += bb;
+      }
     }
     if (!q.wp[a]) {
       T bb = b[q.F + q.op[a]];
-      num += bb * ring_nb<D, T>(rg, q, i, n0, a, +1, r, sl_m, sl_0, sl_p);
-      dg += bb;
+      const T pn = ring_nb<D, T>(rg, q, i, n0, a, +1, r, sl_m, sl_0, sl_p);
+      if constexpr (sizeof(T) == 4) px_acc(num, dg, bb, pn);
+      else {
+        num += bb * pn;
+        dg += bb;
+      }
     }
   }
-  return (num - h2 * L.pf[q.F]) / dg;
+  if constexpr (sizeof(T) == 4) return px_final(num, dg, h2, L.pf[q.F]);
+  else return (num - h2 * L.pf[q.F]) / dg;
 }
 
 // NP planes per iteration: the red values of planes k .. k+NP-1 (independent
@@ -761,6 +770,213 @@ __global__ void __launch_bounds__(512, 2) kb_pair(BArgs A, int TY, int KC) {
                           (float)M.ir[A.lev]);
 }
 
+// ---------------------------------------------------------------------------
+// Pair sweep of the pressure (3D FP32, walls in x and y), built like the
+// viscous pair sweep: one thread per (red, black) pair of a row, TY rows plus
+// two ring rows per block, marching over a chunk of planes. At plane k the
+// red point is solved from old black values: the p rows of its plane and of
+// the rows below and above, and p of the planes below and above from a
+// register queue. The black point's weights (its six betas, 0 beyond a wall)
+// and right-hand side are kept; after one barrier the black point of plane
+// k - 1 is solved from the four-slot ring of new red values. The point
+// arithmetic is px_acc / px_final in the order of p_red; a neighbour beyond a
+// wall enters with beta 0 and p 0, which changes no bit.
+// ---------------------------------------------------------------------------
+struct PPSet {
+  float b[6];   // beta of the x-, x+, y-, y+, z-, z+ neighbours
+  float f;      // right-hand side
+};
+
+__device__ __forceinline__ float ppsolve(const PPSet& c, float h2, const float nb[6]) {
+  float num = 0.f, dg = 0.f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) px_acc(num, dg, c.b[t], nb[t]);
+  return px_final(num, dg, h2, c.f);
+}
+
+template <bool PERZ>
+__device__ __forceinline__ void p_rb_pair_body(const Blk& B, Geo g, LevelPtrs<float> L,
+                                               float* __restrict__ out, int TY, int KC, float h2) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* ring = reinterpret_cast<float*>(sm_raw);
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int W = n0;
+  const int plane = (TY + 2) * W;
+  const int x0 = 2 * threadIdx.x, r = threadIdx.y;
+  const int j0 = B.x * TY;
+  const int k0 = B.y * KC, k1 = min(k0 + KC, n2);
+  const int j = j0 - 1 + r;
+  const bool lane_ok = x0 < n0;
+  const bool rowvalid = lane_ok && j >= 0 && j < n1;
+  const bool own = rowvalid && r >= 1 && r <= TY;
+  const int st1 = (int)g.st[1], st2 = (int)g.st[2];
+  const int xl = x0 > 0 ? x0 - 1 : 0;
+  const bool wpy = j == n1 - 1, wmy = j == 0;
+  const bool wmx0 = x0 == 0, wpx1 = x0 + 1 == n0 - 1;
+  for (int q = threadIdx.y * blockDim.x + threadIdx.x; q < 4 * plane; q += blockDim.x * blockDim.y)
+    ring[q] = 0.f;
+  const float* __restrict__ pp = L.p;
+  const float* __restrict__ bx = L.beta[0];
+  const float* __restrict__ by = L.beta[1];
+  const float* __restrict__ bz = L.beta[2];
+  const float* __restrict__ pf = L.pf;
+  const int jm = j > 0 ? j - 1 : j;
+  const int oy0 = j * st1 + x0, oym = jm * st1 + x0, oyp = (j + 1) * st1 + x0;
+  auto pz = [&](int k) -> int {
+    if constexpr (PERZ) return k < 0 ? k + n2 : (k >= n2 ? k - n2 : k);
+    else return k < 0 ? 0 : (k > n2 ? n2 : k);
+  };
+  const bool ld = rowvalid;
+  // register queues along z: p of planes k - 1 and k, beta_z of plane k
+  float2 Pm = make_float2(0.f, 0.f), Pc = Pm, BZc = Pm;
+  if (ld) {
+    Pm = ldp(pp, oy0 + pz(k0 - 2) * st2);
+    Pc = ldp(pp, oy0 + pz(k0 - 1) * st2);
+    BZc = ldp(bz, oy0 + pz(k0 - 1) * st2);
+  }
+  __syncthreads();
+  int sk = 0;
+  PPSet keep{};
+  float red_prev = 0.f;
+  auto step = [&](auto par_tag, const int k) {
+    constexpr int PAR = decltype(par_tag)::value;
+    const bool planevalid = PERZ || (k >= 0 && k < n2);
+    const int kw = pz(k), kp = pz(k + 1);
+    const bool wpz = !PERZ && kw == n2 - 1, wmz = !PERZ && kw == 0;
+    float redv = 0.f;
+    PPSet blk{};
+    float2 Pp = make_float2(0.f, 0.f), BZp = Pp;
+    if (ld) {
+      Pp = ldp(pp, oy0 + kp * st2);
+      BZp = ldp(bz, oy0 + kp * st2);
+    }
+    if (ld && k < k1) {   // the rows the next plane loads
+      const int kn = pz(k + 1) * st2, kn2 = pz(k + 2) * st2;
+      pf1(pp, oy0 + kn2);
+      pf1(bz, oy0 + kn2);
+      pf1(pp, oym + kn);
+      pf1(pp, oyp + kn);
+      pf1(bx, oy0 + kn);
+      pf1(by, oy0 + kn);
+      pf1(by, oyp + kn);
+      pf1(pf, oy0 + kn);
+    }
+    if (ld && planevalid) {
+      const int oz = kw * st2;
+      // p of this row (queued) with the value left (red at x0 + 1) or right (red at x0)
+      const float2 P0 = Pc;
+      const float Pl = PAR ? 0.f : __ldg(pp + oy0 + oz - x0 + xl);
+      const float Pr = PAR ? __ldg(pp + oy0 + oz + 2) : 0.f;
+      const float2 PYm = ldp(pp, oym + oz), PYp = ldp(pp, oyp + oz);
+      const float2 BX = ldp(bx, oy0 + oz);
+      const float BXr = __ldg(bx + oy0 + oz + 2);
+      const float2 BY = ldp(by, oy0 + oz), BYp = ldp(by, oyp + oz);
+      const float2 F = ldp(pf, oy0 + oz);
+      // the two points' weights: x at x0 uses beta_x(x0), beta_x(x0 + 1); x0 + 1
+      // uses beta_x(x0 + 1), beta_x(x0 + 2)
+      PPSet c0, c1;
+      c0.b[0] = wmx0 ? 0.f : BX.x;
+      c0.b[1] = BX.y;
+      c1.b[0] = BX.y;
+      c1.b[1] = wpx1 ? 0.f : BXr;
+      c0.b[2] = wmy ? 0.f : BY.x;
+      c1.b[2] = wmy ? 0.f : BY.y;
+      c0.b[3] = wpy ? 0.f : BYp.x;
+      c1.b[3] = wpy ? 0.f : BYp.y;
+      c0.b[4] = wmz ? 0.f : BZc.x;
+      c1.b[4] = wmz ? 0.f : BZc.y;
+      c0.b[5] = wpz ? 0.f : BZp.x;
+      c1.b[5] = wpz ? 0.f : BZp.y;
+      c0.f = F.x;
+      c1.f = F.y;
+      // the red point (element PAR): its old neighbours, 0 beyond a wall
+      float nb[6];
+      if constexpr (PAR == 0) {
+        nb[0] = wmx0 ? 0.f : Pl;
+        nb[1] = P0.y;
+        nb[2] = wmy ? 0.f : PYm.x;
+        nb[3] = wpy ? 0.f : PYp.x;
+        nb[4] = wmz ? 0.f : Pm.x;
+        nb[5] = wpz ? 0.f : Pp.x;
+      } else {
+        nb[0] = P0.x;
+        nb[1] = wpx1 ? 0.f : Pr;
+        nb[2] = wmy ? 0.f : PYm.y;
+        nb[3] = wpy ? 0.f : PYp.y;
+        nb[4] = wmz ? 0.f : Pm.y;
+        nb[5] = wpz ? 0.f : Pp.y;
+      }
+      redv = ppsolve(PAR ? c1 : c0, h2, nb);
+      blk = PAR ? c0 : c1;
+    }
+    if (lane_ok) {
+      const float2 rv = PAR ? make_float2(0.f, redv) : make_float2(redv, 0.f);
+      *reinterpret_cast<float2*>(ring + sk * plane + r * W + x0) = rv;
+    }
+    __syncthreads();
+    // the black point (element PAR) of plane k - 1 on the block's own rows;
+    // the pair out
+    const int kb = k - 1;
+    if (own && kb >= k0 && kb < k1) {
+      const int kbw = pz(kb);
+      const int s_m = (sk + 2) & 3, s_0 = (sk + 3) & 3;
+      const int xb = x0 + PAR;
+      const float* R0 = ring + s_0 * plane + r * W;
+      float nb[6];
+      nb[0] = xb > 0 ? R0[xb - 1] : 0.f;
+      nb[1] = xb + 1 < n0 ? R0[xb + 1] : 0.f;
+      nb[2] = R0[-W + xb];
+      nb[3] = R0[W + xb];
+      nb[4] = ring[s_m * plane + r * W + xb];
+      nb[5] = ring[sk * plane + r * W + xb];
+      const float bv = ppsolve(keep, h2, nb);
+      const float2 o = PAR ? make_float2(red_prev, bv) : make_float2(bv, red_prev);
+      *reinterpret_cast<float2*>(out + oy0 + kbw * st2) = o;
+    }
+    keep = blk;
+    red_prev = redv;
+    sk = (sk + 1) & 3;
+    Pm = Pc;
+    Pc = Pp;
+    BZc = BZp;
+  };
+  using P0t = std::integral_constant<int, 0>;
+  using P1t = std::integral_constant<int, 1>;
+  int k = k0 - 1;
+  for (; k + 1 <= k1; k += 2) {   // two planes per iteration: the parity alternates
+    if ((j + k) & 1) {
+      step(P1t{}, k);
+      step(P0t{}, k + 1);
+    } else {
+      step(P0t{}, k);
+      step(P1t{}, k + 1);
+    }
+  }
+  if (k <= k1) {
+    if ((j + k) & 1) step(P1t{}, k);
+    else step(P0t{}, k);
+  }
+}
+
+template <bool PERZ>
+__global__ void __launch_bounds__(512, 2) k_p_rb_pair(Geo g, LevelPtrs<float> L,
+                                                   float* __restrict__ out, int TY, int KC,
+                                                   float h2) {
+  p_rb_pair_body<PERZ>(own_blk(), g, L, out, TY, KC, h2);
+}
+
+// the batched pressure pair sweep: one block per item, as kb_pair
+template <bool PERZ>
+__global__ void __launch_bounds__(512, 2) kb_ppair(BArgs A, int TY, int KC) {
+  const BItem it = A.items[blockIdx.x];
+  if (A.act && !A.act[it.m]) return;
+  const BMember& M = A.tab[it.m];
+  const Geo g = M.g[A.lev];
+  const LevelPtrs<float> L = cur_ptrs(M.f[A.lev], A.cur);
+  p_rb_pair_body<PERZ>(Blk{it.x, it.y, it.z, it.gx, it.gy, it.gz}, g, L, L.p2, TY, KC,
+                       (float)(g.h * g.h));
+}
+
 // after an odd count of sweeps the current iterate (in the second buffer) is
 // copied to its own buffer, on every stored element
 template <int K>
@@ -882,11 +1098,35 @@ void launch_v_rb_pair(const Geo& g, const LevelPtrs<float>& L, int d, float* out
   }
 }
 
-// Chunk planes giving `waves` full waves of resident pair-sweep blocks; 0
-// where the occupancy cannot be had.
+const void* p_pair_kernel(bool perz) {
+  return perz ? (const void*)k_p_rb_pair<true> : (const void*)k_p_rb_pair<false>;
+}
+
+void launch_p_rb_pair(const Geo& g, const LevelPtrs<float>& L, float* out, cudaStream_t s, int TY,
+                      int KC) {
+  const int bx = ((g.n[0] / 2 + 31) / 32) * 32;
+  if (KC < 1) KC = 1;
+  dim3 block(bx, TY + 2, 1);
+  dim3 grid((g.n[1] + TY - 1) / TY, (g.n[2] + KC - 1) / KC, 1);
+  const float h2 = (float)(g.h * g.h);
+  const size_t sm = pair_smem(g, TY);
+  if (g.per[2]) k_p_rb_pair<true><<<grid, block, sm, s>>>(g, L, out, TY, KC, h2);
+  else k_p_rb_pair<false><<<grid, block, sm, s>>>(g, L, out, TY, KC, h2);
+}
+
+void launch_b_ppair(const BArgs& A, bool perz, int TY, int KC, int bx, size_t smem,
+                    cudaStream_t s) {
+  if (A.n <= 0) return;
+  const dim3 block(bx, TY + 2, 1);
+  if (perz) kb_ppair<true><<<A.n, block, smem, s>>>(A, TY, KC);
+  else kb_ppair<false><<<A.n, block, smem, s>>>(A, TY, KC);
+}
+
+// Chunk planes giving `waves` full waves of resident pair-sweep blocks (kind
+// d: 0..2 viscous, 3 pressure); 0 where the occupancy cannot be had.
 int pair_fill_kc(const Geo& g, int d, int TY, int waves) {
   if (!pair_eligible(3, g, TY)) return 0;
-  const void* fn = pair_kernel(d, g.per[2] != 0);
+  const void* fn = d == 3 ? p_pair_kernel(g.per[2] != 0) : pair_kernel(d, g.per[2] != 0);
   const int bx = ((g.n[0] / 2 + 31) / 32) * 32;
   int bps = 0, dev = 0, nsm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, bx * (TY + 2), pair_smem(g, TY)) !=
@@ -955,9 +1195,11 @@ cudaError_t fused_set_carveout() {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pair_kernel(d, perz), cudaFuncAttributePreferredSharedMemoryCarveout,
                                  25);
-  const void* bp[6] = {(const void*)kb_pair<0, false>, (const void*)kb_pair<1, false>,
-                       (const void*)kb_pair<2, false>, (const void*)kb_pair<0, true>,
-                       (const void*)kb_pair<1, true>, (const void*)kb_pair<2, true>};
+  const void* bp[10] = {(const void*)kb_pair<0, false>, (const void*)kb_pair<1, false>,
+                        (const void*)kb_pair<2, false>, (const void*)kb_pair<0, true>,
+                        (const void*)kb_pair<1, true>,  (const void*)kb_pair<2, true>,
+                        (const void*)k_p_rb_pair<false>, (const void*)k_p_rb_pair<true>,
+                        (const void*)kb_ppair<false>,   (const void*)kb_ppair<true>};
   for (const void* f : bp)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 25);

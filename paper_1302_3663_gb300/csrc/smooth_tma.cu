@@ -267,18 +267,10 @@ __global__ void __launch_bounds__(kTmaThreads) k_rb_tma(const __grid_constant__ 
         float num = 0.f, dg = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          if (!wm(a)) {
-            float bb = at(2 + a);
-            num += bb * nb(a, -1);
-            dg += bb;
-          }
-          if (!wp(a)) {
-            float bb = sh(2 + a, a, +1, 0, 0);
-            num += bb * nb(a, +1);
-            dg += bb;
-          }
+          if (!wm(a)) px_acc(num, dg, at(2 + a), nb(a, -1));
+          if (!wp(a)) px_acc(num, dg, sh(2 + a, a, +1, 0, 0), nb(a, +1));
         }
-        return (num - c * at(1)) / dg;
+        return px_final(num, dg, c, at(1));
       } else {
         constexpr int d = K;
         constexpr int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
@@ -724,8 +716,8 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
   }
   if (status != cudaSuccess) break;
   }
-  // the pair sweep (viscous components): tile rows and chunk planes
-  if (K < 3 && search && status == cudaSuccess) {
+  // the pair sweep (viscous components and pressure): tile rows and chunk planes
+  if (search && status == cudaSuccess) {
     for (int pTY : {2, 4, 6, 8, 10, 14}) {
       if (!pair_eligible(D, g, pTY)) continue;
       int kcs_pair[5] = {8, 16, 32, pair_fill_kc(g, K, pTY, 1), pair_fill_kc(g, K, pTY, 2)};
@@ -735,7 +727,10 @@ cudaError_t tma_autotune(int D, const Geo& g, const LevelPtrs<float>& L, int K, 
         bool seen = false;
         for (int cj = 0; cj < ci; ++cj) seen = seen || kcs_pair[cj] == pKC;
         if (seen) continue;
-        auto pr = [&]() { launch_v_rb_pair(g, L, K, out, coef * g.h * g.h, s, pTY, pKC); };
+        auto pr = [&]() {
+          if (K == 3) launch_p_rb_pair(g, L, out, s, pTY, pKC);
+          else launch_v_rb_pair(g, L, K, out, coef * g.h * g.h, s, pTY, pKC);
+        };
         pr();
         float ms = per_launch_ms(pr);
         if (status != cudaSuccess) break;
@@ -847,7 +842,7 @@ bool ring_set_shape(int K, const Geo& g, const int in[5]) {
   if (in[0] < 0 || in[1] < 0 || (in[2] != 1 && in[2] != 2) || in[3] < 0 || in[3] > 128 ||
       in[3] % 32 != 0 || (in[4] != 0 && in[4] != 1))
     return false;
-  if (in[4] == 1 && (K == 3 || in[0] < 1 || in[1] < 1 || in[2] != 1 || in[3] != 0 ||
+  if (in[4] == 1 && (in[0] < 1 || in[1] < 1 || in[2] != 1 || in[3] != 0 ||
                      !pair_eligible(3, g, in[0])))
     return false;
   std::lock_guard<std::mutex> lock(g_plan_mu);

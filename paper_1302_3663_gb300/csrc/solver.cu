@@ -620,8 +620,10 @@ void smooth_p32(bfibm_ctx* c, int l, int n) {
                     c->tma_wait_ns);
     else {
       int ty = 0, kc = 0, np = 1, bx = 0;
-      ring_shape_of(3, Lv.g, &ty, &kc, &np, &bx);
-      launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc, np, bx);
+      int kern = 0;
+      ring_shape_of(3, Lv.g, &ty, &kc, &np, &bx, &kern);
+      if (kern == 1) launch_p_rb_pair(Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc);
+      else launch_p_rb_fused<float>(c->D, Lv.g, Lv.f, Lv.f.p2, c->stream, ty, kc, np, bx);
     }
     std::swap(Lv.f.p, Lv.f.p2);
   }
@@ -1473,7 +1475,7 @@ cudaError_t tune_level(Persist& P, int l, int K) {
   // the pair sweep (viscous): where every member smoothing on the level can
   // take it, with one block width (the widest row's) for all
   int bxu = 0, n1min = 1 << 30, perz = -1;
-  bool pair_ok = K < 3 && st == cudaSuccess;
+  bool pair_ok = st == cudaSuccess;
   for (size_t m = 0; pair_ok && m < P.mem.size(); ++m) {
     if (!p_smooths(P, (int)m, l)) continue;
     const Geo& g = P.mem[m]->lev[l].g;
@@ -1501,8 +1503,10 @@ cudaError_t tune_level(Persist& P, int l, int K) {
         float t = 1e30f;
         for (int round = 0; round < 3 && st == cudaSuccess; ++round) {
           cudaEventRecord(e0, P.stream);
-          for (int r = 0; r < 3; ++r)
-            launch_b_pair(A, K, sh.perz != 0, sh.TY, sh.KC, sh.bx, sh.smem, P.stream);
+          for (int r = 0; r < 3; ++r) {
+            if (K == 3) launch_b_ppair(A, sh.perz != 0, sh.TY, sh.KC, sh.bx, sh.smem, P.stream);
+            else launch_b_pair(A, K, sh.perz != 0, sh.TY, sh.KC, sh.bx, sh.smem, P.stream);
+          }
           cudaEventRecord(e1, P.stream);
           st = cudaEventSynchronize(e1);
           float ms = 0.f;
@@ -1713,8 +1717,12 @@ void b_smooth(Persist& P, int l, int n, bool V) {
       }
     } else {
       const PShape& sh = P.shp[l];
-      launch_b_sweep(bargs(P, P.swp[l], l, cur), 3, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem, sh.grid,
-                     P.stream);
+      if (sh.kern)
+        launch_b_ppair(bargs(P, P.swp[l], l, cur), sh.perz != 0, sh.TY, sh.KC, sh.bx, sh.smem,
+                       P.stream);
+      else
+        launch_b_sweep(bargs(P, P.swp[l], l, cur), 3, sh.TY, sh.KC, sh.NP, sh.bx, sh.smem,
+                       sh.grid, P.stream);
       cur ^= 8;
     }
   }
@@ -2988,8 +2996,8 @@ bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
              "32 k threads per row, at most 1024 threads and kernel 0 or 1";
     return BFIBM_EINVAL;
   }
-  if (sh.kern) {   // the pair sweep: viscous, every member eligible, one row width
-    bool ok = kind == 0 && sh.NP == 1 && sh.bx * (sh.TY + 2) <= 512;
+  if (sh.kern) {   // the pair sweep: every member eligible, one row width
+    bool ok = sh.NP == 1 && sh.bx * (sh.TY + 2) <= 512;
     int perz = -1;
     for (size_t m = 0; ok && m < P.mem.size(); ++m) {
       if (!p_smooths(P, (int)m, level)) continue;
@@ -2999,9 +3007,9 @@ bfibm_status bfibm_batch_set_sweep_shape(bfibm_batch* b, int level, int kind,
       perz = g.per[2];
     }
     if (!ok) {
-      b->err = "the pair sweep needs the viscous kind, walls across x and y, even rows of 4 to "
-               "256 points no wider than the block, rows >= tile rows, one periodicity along z "
-               "and at most 512 threads";
+      b->err = "the pair sweep needs walls across x and y, even rows of 4 to 256 points no wider "
+               "than the block, rows >= tile rows, one periodicity along z and at most 512 "
+               "threads";
       return BFIBM_EINVAL;
     }
     sh.perz = perz > 0;

@@ -93,7 +93,7 @@ def test_uneven_members_bit_identical_to_alone(tune):
     for lev in range(3):
         for kind in (0, 1):
             TY, KC, NP, bx, allb, grid, kern = b.sweep_shape(lev, kind)
-            assert kern in (0, 1) and (kern == 0 or kind == 0)
+            assert kern in (0, 1)
             assert TY >= 1 and KC >= 1 and NP in (1, 2) and bx % 32 == 0
             # levels the coarse-level cluster kernel takes over have no sweep launch
             assert grid >= (1 if lev == 0 else 0)
@@ -196,13 +196,12 @@ def test_unrolled_loops_and_pinned_shapes_give_the_same_bits():
                 (4, 8, 1, 64, 1, 2)):
         with pytest.raises(bfibm.BfibmError):
             b.set_sweep_shape(0, 0, bad)
-    with pytest.raises(bfibm.BfibmError):   # no pair sweep for the pressure
-        b.set_sweep_shape(0, 1, (4, 8, 1, 64, 1, 1))
     assert b.sweep_shape(0, 0)[:5] == (2, 5, 2, 64, 0)
     b.step()
     b.wait()
-    b.set_sweep_shape(0, 0, (4, 7, 1, 64, 1, 1))   # the pair sweep on the finest level
-    assert b.sweep_shape(0, 0)[6] == 1
+    b.set_sweep_shape(0, 0, (4, 7, 1, 64, 1, 1))   # the pair sweeps on the finest level
+    b.set_sweep_shape(0, 1, (6, 5, 1, 32, 1, 1))
+    assert b.sweep_shape(0, 0)[6] == 1 and b.sweep_shape(0, 1)[6] == 1
     b.step()
     assert b.wait() == bfibm.OK
     for k, c in enumerate(ctxs):
