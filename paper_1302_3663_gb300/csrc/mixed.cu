@@ -418,8 +418,10 @@ __device__ __forceinline__ bool block_leader() {
 // w = A z on every unknown face (0 on the fixed wall faces); partial sums of z.q.
 // GB300's FP64 rate bounds this kernel and the FP64 residual: their launch
 // bounds keep 4 and 3 blocks resident per SM (64 and 80 registers) so that
-// enough warps hide the FP64 pipe's and the loads' latency (the batched forms,
-// with the work-list loop's registers on top, keep 2).
+// enough warps hide the FP64 pipe's and the loads' latency. The batched forms
+// hold a member's pointers in registers on top and keep 3 at 80 registers:
+// their spills (about 110 bytes a thread) cost less than the third block
+// gains (1 % of a 64-duct batch step).
 template <int D>
 __device__ __forceinline__ void fcg_apply_body(const Blk& B, Geo g, LevelPtrs<double> L, Ptr3d z,
                                                Ptr3d diag, double ir, Ptr3d w, Ptr3d q,
@@ -692,7 +694,7 @@ void launch_coef_to_f32(int D, const Geo& g, const LevelPtrs<double>& L64,
 // The level-0 FP64 steps of the batched solves: the bodies above over a
 // persistent batch's work list, each with a member's own arrays, scalars and
 // the block decomposition of its single-instance launch.
-__global__ void __launch_bounds__(256, 2) kb_v_residual_mixed(BArgs A, int with_partial, int with_r64) {
+__global__ void __launch_bounds__(256, 3) kb_v_residual_mixed(BArgs A, int with_partial, int with_r64) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     const Geo g = M.g[0];
     F32x3 r, e;
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(256) kb_z_to_f64(BArgs A) {
   });
 }
 
-__global__ void __launch_bounds__(256, 2) kb_fcg_apply(BArgs A) {
+__global__ void __launch_bounds__(256, 3) kb_fcg_apply(BArgs A) {
   for_items(A, [&](const BMember& M, const Blk& B) {
     const Geo g = M.g[0];
     Ptr3d z, dg, w, q;
