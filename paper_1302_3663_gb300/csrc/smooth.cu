@@ -47,8 +47,6 @@ struct Ring {
   __device__ __forceinline__ T* row(int slot, int r) const { return buf + (slot * nrow + r) * W; }
 };
 
-__device__ __forceinline__ int slot_of(int k) { return ((k % 3) + 3) % 3; }
-
 // ---------------------------------------------------------------------------
 // Pressure: red from the old black values (global), black from the new red
 // values (shared). Neighbours are summed axis 0, 1, 2, lower then upper, as
@@ -429,20 +427,6 @@ __device__ __forceinline__ float psolve(const PSet& c, float ir, float up_d, flo
   return vx_final(c.uf, ir, off, c.idg);
 }
 
-__device__ __forceinline__ PSet psel(bool t, const PSet& a, const PSet& b) {
-  PSet c;
-  c.cross = t ? a.cross : b.cross;
-  c.cdp = t ? a.cdp : b.cdp;
-  c.cdm = t ? a.cdm : b.cdm;
-  c.cep0 = t ? a.cep0 : b.cep0;
-  c.cem0 = t ? a.cem0 : b.cem0;
-  c.cep1 = t ? a.cep1 : b.cep1;
-  c.cem1 = t ? a.cem1 : b.cem1;
-  c.uf = t ? a.uf : b.uf;
-  c.idg = t ? a.idg : b.idg;
-  return c;
-}
-
 template <int d, bool PERZ>
 __device__ __forceinline__ void v_rb_pair_body(const Blk& B, Geo g, LevelPtrs<float> L,
                                                float* __restrict__ out, int TY, int KC, float ir) {
@@ -529,7 +513,8 @@ __device__ __forceinline__ void v_rb_pair_body(const Blk& B, Geo g, LevelPtrs<fl
     constexpr int PAR = decltype(par_tag)::value;
     const bool planevalid = PERZ || (k >= 0 && k < n2);
     const int kw = pz(k), kp = pz(k + 1);
-    const bool wpz = !PERZ && kw == n2 - 1, wmz = !PERZ && kw == 0;
+    // the z walls of plane k (unused by the z component: z is its own axis)
+    [[maybe_unused]] const bool wpz = !PERZ && kw == n2 - 1, wmz = !PERZ && kw == 0;
     float redv = 0.f;
     PSet blk{};
     PRow UDp{};
@@ -567,7 +552,8 @@ __device__ __forceinline__ void v_rb_pair_body(const Blk& B, Geo g, LevelPtrs<fl
         pf1(ub, oyp + kn);
       }
     }
-    PRow N0{}, N1{}, N2{}, N3{};
+    PRow N0{}, N1{};
+    [[maybe_unused]] PRow N2{}, N3{};   // the y and z components queue more rows
     if (ld && planevalid) {
       // u_d at the rows beside (old values) and the value beside the red point
       const PRow UDym = row(ud, oym, kw, false, false), UDyp = row(ud, oyp, kw, false, false);

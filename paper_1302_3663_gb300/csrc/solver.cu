@@ -1023,8 +1023,6 @@ bfibm_status queue_step(bfibm_ctx* c) {
   return (st == BFIBM_ENOCONV || st2 == BFIBM_ENOCONV) ? BFIBM_ENOCONV : BFIBM_OK;
 }
 
-bool fixed_mode(const bfibm_ctx* c) { return c->P.vc_visc > 0 && c->P.vc_p > 0; }
-
 bfibm_status ensure_ready(bfibm_ctx* c) {
   if (c->dirty) {
     refresh(c);

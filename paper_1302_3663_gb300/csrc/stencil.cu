@@ -1633,10 +1633,10 @@ __device__ __forceinline__ void tail_down(const BMember& M, int l, int t0, int T
       const int e0 = d == 0 ? gc.s[0] : gc.n[0], e1 = d == 1 ? gc.s[1] : gc.n[1],
                 e2 = d == 2 ? gc.s[2] : gc.n[2];
       for (int q = t0; q < e0 * e1 * e2; q += T) {
-        const int C[3] = {q % e0, (q / e0) % e1, q / (e0 * e1)};
-        if (d == 0) restrict_face_at<3, 0, float, true>(g, gc, L.ur[0], Lc.uf[0], Lc.u[0], C);
-        else if (d == 1) restrict_face_at<3, 1, float, true>(g, gc, L.ur[1], Lc.uf[1], Lc.u[1], C);
-        else restrict_face_at<3, 2, float, true>(g, gc, L.ur[2], Lc.uf[2], Lc.u[2], C);
+        const int cc[3] = {q % e0, (q / e0) % e1, q / (e0 * e1)};
+        if (d == 0) restrict_face_at<3, 0, float, true>(g, gc, L.ur[0], Lc.uf[0], Lc.u[0], cc);
+        else if (d == 1) restrict_face_at<3, 1, float, true>(g, gc, L.ur[1], Lc.uf[1], Lc.u[1], cc);
+        else restrict_face_at<3, 2, float, true>(g, gc, L.ur[2], Lc.uf[2], Lc.u[2], cc);
       }
     }
   } else {
