@@ -1408,6 +1408,32 @@ PShape default_shape(const Persist& P, int l) {
     }
   long long KC = tiles / (3LL * device_sms());
   sh.KC = (int)std::max(4LL, std::min(16LL, KC));
+  // the pair sweep where every member smoothing here can take it and the
+  // level holds at least 2^19 cells in all, in the shape the tuner picks on
+  // such levels of uneven ducts: six tile rows (fewer where the rows are
+  // wide), 16-plane chunks, one block per item
+  int bxu = 0, perz = -1;
+  long long cells = 0;
+  bool pair_ok = true;
+  for (size_t m = 0; pair_ok && m < P.mem.size(); ++m) {
+    if (!p_smooths(P, (int)m, l)) continue;
+    const Geo& g = P.mem[m]->lev[l].g;
+    pair_ok = !g.per[0] && !g.per[1] && !(g.n[0] & 1) && g.n[0] >= 4 && g.n[0] <= 256 &&
+              (perz < 0 || perz == g.per[2]);
+    perz = g.per[2];
+    bxu = std::max(bxu, (g.n[0] / 2 + 31) / 32 * 32);
+    cells += (long long)g.n[0] * g.n[1] * g.n[2];
+  }
+  const int pTY = std::min({6, bxu > 0 ? 512 / bxu - 2 : 0, nR});
+  if (pair_ok && perz >= 0 && cells >= (1LL << 19) && pTY >= 1) {
+    sh.kern = 1;
+    sh.perz = perz;
+    sh.TY = pTY;
+    sh.KC = 16;
+    sh.NP = 1;
+    sh.bx = bxu;
+    sh.all = 1;
+  }
   return sh;
 }
 
