@@ -416,7 +416,7 @@ void bfibm_batch_destroy(bfibm_batch* b);
    BFIBM_BATCH_TUNE (default 1): time the batched sweeps' kernel (ring or pair),
    tile rows, chunk planes, planes per phase and grid on every level of at
    least 2^19 cells in all when a plan is built (0: such levels take the pair
-   sweep with 6 tile rows and 16-plane chunks where every member can, the
+   sweep with up to 6 tile rows and 16-plane chunks where every member can, the
    ring sweep otherwise; smaller levels always keep a built-in ring shape). BFIBM_BATCH_UNROLL (default 0): k > 0 queues
    each solve loop as k iterations one after another instead of a device-side
    loop; the masks still stop every member where its tolerance is met, so
