@@ -419,8 +419,9 @@ void bfibm_batch_destroy(bfibm_batch* b);
    sweep with up to 6 tile rows and 16-plane chunks where every member can, the
    ring sweep otherwise; smaller levels always keep a built-in ring shape).
    BFIBM_BATCH_UNROLL (default 0): k > 0 queues each solve loop as k
-   iterations one after another instead of a device-side loop; the masks still stop every member where its tolerance is met, so
-   results are the same while k covers the iterations the slowest member needs
+   iterations one after another instead of a device-side loop; the masks
+   still stop every member where its tolerance is met, so results are the
+   same while k covers the iterations the slowest member needs
    (a member not done after k iterations stops there without being counted as
    unconverged). It serves a profiler that cannot see kernels inside
    conditional graph nodes. BFIBM_BATCH_TAIL (default 4096): the levels of at
