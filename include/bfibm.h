@@ -57,7 +57,9 @@ typedef enum {
    euler = Euler number, inv_re = 1/Re, c_force = L f0 / (rho0 u0^2). */
 typedef struct {
   int32_t dim;            /* 2 or 3 */
-  int32_t n[3];           /* cells per axis; n[2] = 1 when dim == 2; each >= 2 */
+  int32_t n[3];           /* cells per axis; n[2] = 1 when dim == 2; each >= 2;
+                             a level array (s[a] points per axis, rows padded
+                             to 8) holds at most 2^31 - 1 elements */
   int32_t periodic[3];    /* 1: periodic axis, 0: no-slip walls */
   int32_t flow_axis;      /* axis of the body force */
   int32_t phi_kind;       /* 1: Eq. (PhiPeskin), 2: Eq. (PhiCosAlternative) */

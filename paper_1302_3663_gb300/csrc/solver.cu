@@ -113,6 +113,14 @@ const char* validate(const bfibm_params* p) {
     if (p->periodic[a] && (p->n[a] % 2)) return "a periodic axis needs an even cell count";
   }
   if (p->dim == 2 && p->n[2] != 1) return "n[2] must be 1 when dim == 2";
+  // the grid kernels index within a level array with 32-bit offsets
+  long long elems = 1;
+  for (int a = 0; a < 3; ++a) {
+    long long ext = a < p->dim ? (long long)p->n[a] + (p->periodic[a] ? 0 : 1) : 1;
+    if (a == 0) ext = (ext + 7) / 8 * 8;
+    elems *= ext;
+    if (elems > 2147483647LL) return "a level array would hold more than 2^31 - 1 elements";
+  }
   if (p->flow_axis < 0 || p->flow_axis >= p->dim) return "flow_axis out of range";
   if (!p->periodic[p->flow_axis] && !p->open_flow)
     return "the flow axis must be periodic (or open, with open_flow = 1)";

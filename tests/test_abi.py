@@ -48,3 +48,15 @@ def test_footprint_and_validation_without_gpu():
                      ("mu_ratio", 0.5)):
         with pytest.raises(bfibm.BfibmError):
             bfibm.footprint(dict(W.c1()["params"], **{key: val}))
+
+
+def test_grids_beyond_32_bit_offsets_are_refused():
+    # the kernels index within a level array with 32-bit offsets: a 3D grid
+    # whose level-0 arrays would hold 2^31 elements or more is refused before
+    # any allocation; the 1024^3 grid (about 1.08e9 elements) is not
+    prm = W.c3()["params"]
+    big = dict(prm, n=[2048, 1024, 1024])
+    with pytest.raises(bfibm.BfibmError) as e:
+        bfibm.footprint(big)
+    assert e.value.status == bfibm.EINVAL
+    assert bfibm.footprint(dict(prm, n=[1024, 1024, 1024]), 0, 0) > 0
