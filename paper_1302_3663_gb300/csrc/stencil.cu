@@ -468,27 +468,36 @@ __device__ __forceinline__ int prol_face_1d(int i, int nc, int per, int idx[2], 
   return 2;
 }
 
-// separable tensor-product sum: x-rows first, then y, then z. Every axis
-// takes two terms; a missing term has weight 0 and a valid index, and adding
-// its exact zero leaves the sum unchanged, so the loops unroll fully and the
-// index and weight arrays stay in registers.
+// Roundings of the prolongation written out, so that every form of it (one
+// point per thread, two points per thread, the coarse-level cluster kernel)
+// gives the same bits whatever the compiler would contract.
+__device__ __forceinline__ float pmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double pmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float pfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double pfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float padd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double padd(double a, double b) { return __dadd_rn(a, b); }
+
+// separable tensor-product sum: x-rows first, then y, then z, each pair of
+// terms as w1 t1 + (w0 t0) with one rounding of the product and one of the
+// fused sum. Every axis takes two terms; a missing term has weight 0 and a
+// valid index, and adding its exact zero leaves the sum unchanged, so the
+// loops unroll fully and the index and weight arrays stay in registers.
 template <typename T, bool COH = false>
 __device__ __forceinline__ T prol_sum(const Geo& gc, const T* __restrict__ ec, const int idx[3][2],
                                       const T w[3][2]) {
-  T v = T(0);
+  T col[2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    T col = T(0);
+    T row[2];
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       long long r = gidx(gc, 0, idx[1][b], idx[2][c]);
-      T row = w[0][0] * ldm<COH>(ec + r + idx[0][0]);
-      row += w[0][1] * ldm<COH>(ec + r + idx[0][1]);
-      col += w[1][b] * row;
+      row[b] = pfma(w[0][1], ldm<COH>(ec + r + idx[0][1]), pmul(w[0][0], ldm<COH>(ec + r + idx[0][0])));
     }
-    v += w[2][c] * col;
+    col[c] = pfma(w[1][1], row[1], pmul(w[1][0], row[0]));
   }
-  return v;
+  return pfma(w[2][1], col[1], pmul(w[2][0], col[0]));
 }
 
 // the coarse correction added at one fine cell fi
@@ -504,7 +513,7 @@ __device__ __forceinline__ void prolong_cell_at(const Geo& gf, const Geo& gc,
   for (int a = 0; a < D; ++a)
     prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], +1, a == gc.open ? -1 : +1, idx[a], w[a]);
   const long long x = gidx(gf, fi[0], fi[1], fi[2]);
-  xf[x] = ldm<COH>(xf + x) + prol_sum<T, COH>(gc, ec, idx, w);
+  xf[x] = padd(ldm<COH>(xf + x), prol_sum<T, COH>(gc, ec, idx, w));
 }
 
 template <int D, typename T>
@@ -539,7 +548,7 @@ __device__ __forceinline__ void prolong_face_at(const Geo& gf, const Geo& gc,
       prol_cell_1d<T>(fi[a], gc.n[a], gc.per[a], -1, a == gc.open ? +1 : -1, idx[a], w[a]);
   }
   const long long x = gidx(gf, fi[0], fi[1], fi[2]);
-  xf[x] = ldm<COH>(xf + x) + prol_sum<T, COH>(gc, ec, idx, w);
+  xf[x] = padd(ldm<COH>(xf + x), prol_sum<T, COH>(gc, ec, idx, w));
 }
 
 template <int D, int d, typename T>
@@ -594,13 +603,78 @@ __device__ __forceinline__ void prolong_face3_body(const Blk& B, const Geo& gf, 
         idx[a][t] = a == d ? fidx[a][t] : cidx[a][t];
         w[a][t] = a == d ? fw[a][t] : cw[a][t];
       }
-    xf.a[d][x] = xf.a[d][x] + prol_sum<T>(gc, ec.a[d], idx, w);
+    xf.a[d][x] = padd(xf.a[d][x], prol_sum<T>(gc, ec.a[d], idx, w));
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_face3(Geo gf, Geo gc, Faces3<T> ec, Faces3<T> xf) {
   prolong_face3_body<T>(own_blk(), gf, gc, ec, xf);
+}
+
+// The same corrections, two fine points along x per thread: cells or faces
+// 2I and 2I + 1 share the coarse x index I and every y and z index and
+// weight, so each coarse row is addressed once and its value at I loaded once
+// for both; each point's sum is prol_sum's, term for term. The fine x extent
+// is even (twice the coarse one).
+template <typename T>
+__device__ __forceinline__ void prol_pair_sum(const Geo& gc, const T* __restrict__ e, int I,
+                                              const int xa[2], const T wa[2], const int xb[2],
+                                              const T wb[2], const int iy[2], const T wy[2],
+                                              const int iz[2], const T wz[2], T& va, T& vb) {
+  T cola[2], colb[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    T rowa[2], rowb[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const T* __restrict__ r = e + gidx(gc, 0, iy[b], iz[c]);
+      const T e0 = r[I];   // xa[0] == xb[0] == I
+      rowa[b] = pfma(wa[1], r[xa[1]], pmul(wa[0], e0));
+      rowb[b] = pfma(wb[1], r[xb[1]], pmul(wb[0], e0));
+    }
+    cola[c] = pfma(wy[1], rowa[1], pmul(wy[0], rowa[0]));
+    colb[c] = pfma(wy[1], rowb[1], pmul(wy[0], rowb[0]));
+  }
+  va = pfma(wz[1], cola[1], pmul(wz[0], cola[0]));
+  vb = pfma(wz[1], colb[1], pmul(wz[0], colb[0]));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_face3_pair(Geo gf, Geo gc, Faces3<T> ec,
+                                                           Faces3<T> xf) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  const int i0 = 2 * I;
+  if (i0 >= gf.n[0] || j >= gf.n[1] || k >= gf.n[2]) return;
+  // per axis the cell-centred and the face weights (x: both points)
+  int cxa[2], cxb[2], fxa[2], fxb[2], cy[2], fy[2], cz[2], fz[2];
+  T wcxa[2], wcxb[2], wfxa[2], wfxb[2], wcy[2], wfy[2], wcz[2], wfz[2];
+  prol_cell_1d<T>(i0, gc.n[0], gc.per[0], -1, -1, cxa, wcxa);
+  prol_cell_1d<T>(i0 + 1, gc.n[0], gc.per[0], -1, -1, cxb, wcxb);
+  prol_face_1d<T>(i0, gc.n[0], gc.per[0], fxa, wfxa);
+  prol_face_1d<T>(i0 + 1, gc.n[0], gc.per[0], fxb, wfxb);
+  prol_cell_1d<T>(j, gc.n[1], gc.per[1], -1, -1, cy, wcy);
+  prol_face_1d<T>(j, gc.n[1], gc.per[1], fy, wfy);
+  prol_cell_1d<T>(k, gc.n[2], gc.per[2], -1, -1, cz, wcz);
+  prol_face_1d<T>(k, gc.n[2], gc.per[2], fz, wfz);
+  const long long x = gidx(gf, i0, j, k);
+  T va, vb;
+  // x-faces: the wall face 0 (the first point of the first pair) is fixed
+  prol_pair_sum<T>(gc, ec.a[0], I, fxa, wfxa, fxb, wfxb, cy, wcy, cz, wcz, va, vb);
+  if (gf.per[0] || i0 != 0) xf.a[0][x] = padd(xf.a[0][x], va);
+  xf.a[0][x + 1] = padd(xf.a[0][x + 1], vb);
+  if (gf.per[1] || j != 0) {   // y-faces
+    prol_pair_sum<T>(gc, ec.a[1], I, cxa, wcxa, cxb, wcxb, fy, wfy, cz, wcz, va, vb);
+    xf.a[1][x] = padd(xf.a[1][x], va);
+    xf.a[1][x + 1] = padd(xf.a[1][x + 1], vb);
+  }
+  if (gf.per[2] || k != 0) {   // z-faces
+    prol_pair_sum<T>(gc, ec.a[2], I, cxa, wcxa, cxb, wcxb, cy, wcy, fz, wfz, va, vb);
+    xf.a[2][x] = padd(xf.a[2][x], va);
+    xf.a[2][x + 1] = padd(xf.a[2][x + 1], vb);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1868,7 +1942,10 @@ void launch_prolong_face3(const Geo& gf, const Geo& gc, T* const ec[3], T* const
     x.a[d] = xf[d];
   }
   dim3 b = blk3(3);
-  k_prolong_face3<T><<<grd3(gf.n[0], gf.n[1], gf.n[2], b), b, 0, s>>>(gf, gc, e, x);
+  if (gf.n[0] % 2 == 0)
+    k_prolong_face3_pair<T><<<grd3(gf.n[0] / 2, gf.n[1], gf.n[2], b), b, 0, s>>>(gf, gc, e, x);
+  else
+    k_prolong_face3<T><<<grd3(gf.n[0], gf.n[1], gf.n[2], b), b, 0, s>>>(gf, gc, e, x);
 }
 template void launch_restrict_face3<float>(const Geo&, const Geo&, float* const[3],
                                            float* const[3], float* const[3], cudaStream_t);
