@@ -1,7 +1,8 @@
 """Host pieces of the benchmark line, without a GPU: the algorithmic bytes of
-the roofline's sweep and the reading of the clock samples taken during the
+the roofline's sweep, the reading of the clock samples taken during the
 timed region (median SM clock, the largest maximum clock, every throttle
-reason seen active)."""
+reason seen active), the peak's source, the defaults of a plain run, the
+benchmark workload with its solver, and the combined device checks."""
 import os
 import sys
 
@@ -54,3 +55,34 @@ def test_the_peak_falls_back_when_no_measurement_is_present(monkeypatch, tmp_pat
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6795.8}')
     peak, src = bench.measured_peak()
     assert peak == pytest.approx(6795.8) and src.startswith("measured")
+
+
+def test_defaults_are_one_gpu_and_a_short_run(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.impl == "ours" and a.config == "c3"
+    assert a.warmup >= 3 and 1 <= a.steps <= 50
+    assert a.solver == "tol"
+
+
+def test_the_benchmark_workload_and_its_solver(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    inst = bench.load_workload("c3", None, a)
+    p = inst["params"]
+    # the 128x128x256 duct with 20,000 nodes, solved to relative residual
+    # 1e-11 with the divergence target of 1e-10
+    assert list(p["n"][:3]) == [128, 128, 256] and inst["X"].shape[0] == 20000
+    assert p["vc_visc"] == 0 and p["vc_p"] == 0 and p["rtol"] == 1e-11
+    assert p["div_tol"] == 1e-10 and p["precision"] == 1
+    cfg = bench.describe(inst)
+    assert cfg["cells"] == 128 * 128 * 256
+    assert cfg["workload"].startswith("c3: 128x128x256 grid, 20000 nodes")
+    assert "1e-11" in cfg["solver"]
+
+
+def test_device_checks_of_several_simulations_are_combined():
+    stats = [{"div_max_steps": 3e-11, "div_violations": 0, "nonconv_total": 1},
+             {"div_max_steps": 9e-11, "div_violations": 2, "nonconv_total": 0}]
+    assert bench.div_summary(stats) == {"div_max_all_steps": 9e-11, "div_violations": 2,
+                                        "nonconverged_solves": 1}
