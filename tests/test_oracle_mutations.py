@@ -1,0 +1,85 @@
+"""The oracle's pins catch plausible mistakes. Each case plants one mistake
+in a copy of the oracle's source (a dropped factor, a wrong sign, a flux
+taken at the wrong edge, wrong transfer weights), builds that copy, and runs
+the pin tests of the function it touches against it, through the oracle's
+build override: at least one pin must fail. A control build of the unchanged
+source passes the same pins, so a failure is the planted mistake's."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from oracle import build as oracle_build
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ADVECTION = "tests/test_oracle_advection.py"
+MULTIGRID = "tests/test_oracle_multigrid.py"
+
+MUTATIONS = {
+    # Eq. NSdis1-1: the skew-symmetric advection is the mean of two halves
+    "advection_dropped_half": (
+        "  return 0.5 * (adv + cons);", "  return (adv + cons);", ADVECTION),
+    "advection_sign_slip": (
+        "adv += 0.5 * (Uhi * (up - udF) / h + Ulo * (udF - um) / h);",
+        "adv += 0.5 * (Uhi * (up - udF) / h - Ulo * (udF - um) / h);", ADVECTION),
+    "advection_upper_flux_at_lower_edge": (
+        "Uhi = ue_avg_at_face(S, L, u[e], d, e, F, 1);",
+        "Uhi = ue_avg_at_face(S, L, u[e], d, e, F, 0);", ADVECTION),
+    # full-weighting restriction along the face axis: (1/4, 1/2, 1/4)
+    "restriction_weights": (
+        "double wgt = (o == 0) ? 0.5 : 0.25;", "double wgt = (o == 0) ? 0.6 : 0.2;", MULTIGRID),
+    # linear prolongation: 3/4 on the parent cell
+    "prolongation_parent_weight": (
+        "idx[0] = I; w[0] = 0.75;", "idx[0] = I; w[0] = 0.7;", MULTIGRID),
+    # a fine face on a coarse face takes its value
+    "prolongation_coincident_face": (
+        "if ((i & 1) == 0) { idx[0] = per ? wrapi(I, nc) : I; w[0] = 1.0; return 1; }",
+        "if ((i & 1) == 0) { idx[0] = per ? wrapi(I, nc) : I; w[0] = 0.9; return 1; }",
+        MULTIGRID),
+    # the coarse edge viscosity is the mean of its two fine edges (3D)
+    "edge_viscosity_mean_halved": (
+        "double wt = S->D == 3 ? 0.5 : 1.0;", "double wt = S->D == 3 ? 0.25 : 1.0;", MULTIGRID),
+}
+
+
+def build_copy(src, out):
+    cmd = (["gcc"] + oracle_build.FLAGS + ["-fopenmp", "-o", str(out), str(src), "-lm"])
+    subprocess.run(cmd, check=True, capture_output=True)
+
+
+def run_pins(lib, test_file):
+    env = dict(os.environ, **{O.OVERRIDE_ENV: str(lib)})
+    return subprocess.run([sys.executable, "-m", "pytest", test_file, "-x", "-q",
+                           "-p", "no:cacheprovider"], cwd=ROOT, env=env,
+                          capture_output=True, text=True)
+
+
+def source():
+    with open(oracle_build.SRC) as f:
+        return f.read()
+
+
+def test_unchanged_copy_passes_the_pins(tmp_path):
+    src = tmp_path / "same.c"
+    src.write_text(source())
+    lib = tmp_path / "libsame.so"
+    build_copy(src, lib)
+    for test_file in (ADVECTION, MULTIGRID):
+        r = run_pins(lib, test_file)
+        assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    old, new, test_file = MUTATIONS[name]
+    text = source()
+    assert text.count(old) == 1, "the mutation site is no longer unique"
+    src = tmp_path / (name + ".c")
+    src.write_text(text.replace(old, new))
+    lib = tmp_path / ("lib%s.so" % name)
+    build_copy(src, lib)
+    r = run_pins(lib, test_file)
+    assert r.returncode == 1, "no pin failed:\n" + r.stdout[-2000:]
+    assert "failed" in r.stdout
