@@ -1,9 +1,10 @@
 """The oracle's pins catch plausible mistakes. Each case plants one mistake
 in a copy of the oracle's source (a dropped factor, a wrong sign, a flux
-taken at the wrong edge, wrong transfer weights), builds that copy, and runs
-the pin tests of the function it touches against it, through the oracle's
-build override: at least one pin must fail. A control build of the unchanged
-source passes the same pins, so a failure is the planted mistake's."""
+taken at the wrong edge, wrong transfer weights, a wrong kernel period or
+spring tension), builds that copy, and runs the pin tests of the function it
+touches against it, through the oracle's build override: at least one pin
+must fail. A control build of the unchanged source passes the same pins, so
+a failure is the planted mistake's."""
 import os
 import subprocess
 import sys
@@ -16,6 +17,9 @@ from oracle import oracle as O
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ADVECTION = "tests/test_oracle_advection.py"
 MULTIGRID = "tests/test_oracle_multigrid.py"
+OPERATORS = "tests/test_oracle_operators.py"
+DELTA = "tests/test_oracle_delta.py"
+TRANSFER = "tests/test_oracle_transfer.py"
 
 MUTATIONS = {
     # Eq. NSdis1-1: the skew-symmetric advection is the mean of two halves
@@ -41,6 +45,24 @@ MUTATIONS = {
     # the coarse edge viscosity is the mean of its two fine edges (3D)
     "edge_viscosity_mean_halved": (
         "double wt = S->D == 3 ? 0.5 : 1.0;", "double wt = S->D == 3 ? 0.25 : 1.0;", MULTIGRID),
+    # Eq. divergenceGrad: the normal stress is 2 mu du_d/dx_d
+    "viscous_normal_stress_without_2": (
+        "double tau_p = 2.0 * mcp * (ud[LIc(L, Fp)] - ud[iF]) / h;",
+        "double tau_p = mcp * (ud[LIc(L, Fp)] - ud[iF]) / h;", OPERATORS),
+    # Eq. divergencePartial: the shear stress sums both cross derivatives
+    "viscous_shear_sign": (
+        "tau[side] = me * (dud_de + due_dd);", "tau[side] = me * (dud_de - due_dd);", OPERATORS),
+    # Eq. NSdis4: the divergence of the two face fluxes
+    "pressure_flux_sign": (
+        "acc += (flux_hi - flux_lo) / h;", "acc += (flux_hi + flux_lo) / h;", OPERATORS),
+    # Eq. PhiCosAlternative: the cosine kernel's period
+    "phi2_period": (
+        "if (a < 2.0) return 0.25 * (1.0 + cos(M_PI * r / 2.0));",
+        "if (a < 2.0) return 0.25 * (1.0 + cos(M_PI * r / 2.2));", DELTA),
+    # Eq. springF: Hookean tension on the stretch beyond the rest length
+    "spring_tension_sign": (
+        "double T = S->K[q] * (len - S->rest[q]);", "double T = S->K[q] * (len + S->rest[q]);",
+        TRANSFER),
 }
 
 
@@ -66,7 +88,7 @@ def test_unchanged_copy_passes_the_pins(tmp_path):
     src.write_text(source())
     lib = tmp_path / "libsame.so"
     build_copy(src, lib)
-    for test_file in (ADVECTION, MULTIGRID):
+    for test_file in (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER):
         r = run_pins(lib, test_file)
         assert r.returncode == 0, r.stdout[-2000:]
 
