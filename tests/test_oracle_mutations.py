@@ -1,10 +1,10 @@
 """The oracle's pins catch plausible mistakes. Each case plants one mistake
 in a copy of the oracle's source (a dropped factor, a wrong sign, a flux
-taken at the wrong edge, wrong transfer weights, a wrong kernel period or
-spring tension), builds that copy, and runs the pin tests of the function it
-touches against it, through the oracle's build override: at least one pin
-must fail. A control build of the unchanged source passes the same pins, so
-a failure is the planted mistake's."""
+taken at the wrong edge, wrong transfer weights, a wrong kernel period,
+spring tension or projection), builds that copy, and runs the pin tests of
+the function it touches against it, through the oracle's build override: at
+least one pin must fail. A control build of the unchanged source passes the
+same pins, so a failure is the planted mistake's."""
 import os
 import subprocess
 import sys
@@ -20,6 +20,7 @@ MULTIGRID = "tests/test_oracle_multigrid.py"
 OPERATORS = "tests/test_oracle_operators.py"
 DELTA = "tests/test_oracle_delta.py"
 TRANSFER = "tests/test_oracle_transfer.py"
+FLOW = "tests/test_oracle_flow.py"
 
 MUTATIONS = {
     # Eq. NSdis1-1: the skew-symmetric advection is the mean of two halves
@@ -63,6 +64,14 @@ MUTATIONS = {
     "spring_tension_sign": (
         "double T = S->K[q] * (len - S->rest[q]);", "double T = S->K[q] * (len + S->rest[q]);",
         TRANSFER),
+    # Eq. NSdis2: the projection subtracts the scaled pressure gradient
+    "projection_sign": (
+        "S->uvel[d][iF] = L->u[d][iF] - sc * L->beta[d][iF] * gp;",
+        "S->uvel[d][iF] = L->u[d][iF] + sc * L->beta[d][iF] * gp;", FLOW),
+    # Eq. NSdis4: the right-hand side sigma / (euler dt) D.u
+    "divergence_scale_inverted": (
+        "double sc = S->P.sigma / S->P.euler / S->P.dt;",
+        "double sc = S->P.euler / S->P.sigma / S->P.dt;", FLOW),
 }
 
 
@@ -75,7 +84,7 @@ def run_pins(lib, test_file):
     env = dict(os.environ, **{O.OVERRIDE_ENV: str(lib)})
     return subprocess.run([sys.executable, "-m", "pytest", test_file, "-x", "-q",
                            "-p", "no:cacheprovider"], cwd=ROOT, env=env,
-                          capture_output=True, text=True)
+                          capture_output=True, text=True, timeout=600)
 
 
 def source():
@@ -88,7 +97,7 @@ def test_unchanged_copy_passes_the_pins(tmp_path):
     src.write_text(source())
     lib = tmp_path / "libsame.so"
     build_copy(src, lib)
-    for test_file in (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER):
+    for test_file in (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER, FLOW):
         r = run_pins(lib, test_file)
         assert r.returncode == 0, r.stdout[-2000:]
 
