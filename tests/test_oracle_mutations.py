@@ -72,6 +72,20 @@ MUTATIONS = {
     "divergence_scale_inverted": (
         "double sc = S->P.sigma / S->P.euler / S->P.dt;",
         "double sc = S->P.euler / S->P.sigma / S->P.dt;", FLOW),
+    # Sec. 3.5, the V-cycle: the coarse correction starts from zero, the
+    # coarse right-hand side is the restricted residual, and the correction
+    # is smoothed after it is added
+    "pressure_coarse_guess_not_zeroed": (
+        "  memset(Lc->p, 0, sizeof(double) * Lc->size);\n  vcycle_p(S, l + 1);",
+        "  vcycle_p(S, l + 1);", OPERATORS),
+    "pressure_restricts_the_iterate": (
+        "  restrict_cell(S, L, Lc, L->pr, Lc->pf);", "  restrict_cell(S, L, Lc, L->p, Lc->pf);",
+        OPERATORS),
+    "viscous_post_smoothing_skipped": (
+        "  for (int d = 0; d < S->D; ++d) prolong_add_face(S, L, Lc, d, Lc->u[d], L->u[d]);\n"
+        "  for (int it = 0; it < S->P.nu2; ++it) v_rbgs(S, l);",
+        "  for (int d = 0; d < S->D; ++d) prolong_add_face(S, L, Lc, d, Lc->u[d], L->u[d]);",
+        MULTIGRID),
 }
 
 
