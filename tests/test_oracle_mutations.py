@@ -81,6 +81,18 @@ MUTATIONS = {
     "pressure_restricts_the_iterate": (
         "  restrict_cell(S, L, Lc, L->pr, Lc->pf);", "  restrict_cell(S, L, Lc, L->p, Lc->pf);",
         OPERATORS),
+    # Sec. 3.4, Eq. discrVelCouple: nodes move by dt / sigma times the
+    # velocity interpolated with the delta of width h
+    "node_velocity_with_the_spreading_width": (
+        "S->U[3 * s + d] = interp_one(S, kind_face(d), S->uvel[d], &S->X[3 * s], P->h);",
+        "S->U[3 * s + d] = interp_one(S, kind_face(d), S->uvel[d], &S->X[3 * s], P->omega);",
+        TRANSFER),
+    "node_move_without_sigma": (
+        "double c = P->dt / P->sigma;", "double c = P->dt;", TRANSFER),
+    # Eq. ViscExp: the viscosity bump's amplitude (2 w)^D (mu_max - mu_out)
+    "viscosity_amplitude_width": (
+        "double coef = pow(2.0 * w, D) * (mu_max - mu_out);",
+        "double coef = pow(w, D) * (mu_max - mu_out);", TRANSFER),
     "viscous_post_smoothing_skipped": (
         "  for (int d = 0; d < S->D; ++d) prolong_add_face(S, L, Lc, d, Lc->u[d], L->u[d]);\n"
         "  for (int it = 0; it < S->P.nu2; ++it) v_rbgs(S, l);",

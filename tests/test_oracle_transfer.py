@@ -8,6 +8,10 @@
 * Eq. (discrVelCouple) with phi1 and width h reproduces linear fields.
 * Eq. (ViscExp): mu = mu_max at a node lying on a grid point (Fig. 4 setup).
 * Eq. (springF), Eq. (defineK): two-node tension and the breaking rule.
+* Sec. 3.4 with Eq. (discrVelCouple): a node moves by dt / sigma times the
+  velocity interpolated with the width-h delta (a uniform flow moves it
+  exactly; the velocity of faces 1.3h-1.9h away moves it, of faces beyond
+  2h does not).
 """
 import json
 import math
@@ -223,3 +227,54 @@ def test_per_level_gamma_scales_coarse_viscosity():
     assert np.array_equal(mu[0][0], mu[1][0])
     for l in (1, 2):
         assert np.max(np.abs(mu[1][l] - 0.5 * mu[0][l])) <= 1e-15 * np.max(np.abs(mu[0][l]))
+
+
+# --------------------------------------------------------------------------
+# The node move of one time step (Sec. 3.4, Eq. discrVelCouple): X += (dt /
+# sigma) U, U interpolated from each component's own face grid with the delta
+# of width h, whatever the spreading width omega.
+def advance_case(ux_of, uy_of, X, sigma=0.5, dt=0.003):
+    h = 1.0 / 32
+    prm = grid2(h=h, sigma=sigma, dt=dt, omega=0.6 * h, omega_mu=0.6 * h)
+    o = O.Oracle(prm)
+    o.set_nodes(np.array([X]))
+    o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+    n, s = o.dims()
+    # x-faces at (i h, (j + 1/2) h), y-faces at ((i + 1/2) h, j h)
+    xi, yj = np.meshgrid(np.arange(s[0]) * h, (np.arange(s[1]) + 0.5) * h)
+    xc, yf = np.meshgrid((np.arange(s[0]) + 0.5) * h, np.arange(s[1]) * h)
+    o.set("u", ux_of(xi, yj), 0)
+    o.set("u", uy_of(xc, yf), 1)
+    o.stage("interp_advance")
+    dX = o.nodes()[0] - np.asarray(X)
+    o.close()
+    return dX, h, dt / sigma
+
+
+def test_node_moves_by_dt_over_sigma_in_a_uniform_flow():
+    # partition of unity: any delta of unit mass returns the uniform velocity
+    # (the node sits 8 cells from both walls, so no wall face is in reach)
+    U0, V0 = 0.3, -0.2
+    dX, h, c = advance_case(lambda x, y: np.full_like(x, U0),
+                            lambda x, y: np.where((y > 0) & (y < 0.5), V0, 0.0),
+                            (0.41 + 0.3 / 32, 0.25 + 0.2 / 32))
+    assert np.allclose(dX, [c * U0, c * V0], rtol=0, atol=1e-15)
+
+
+def test_node_velocity_uses_the_width_h_support():
+    # the delta of width h reaches faces closer than 2h along x and no
+    # further: x-velocity on the faces 1.3h-1.9h from the node moves it, and
+    # on the faces beyond 2.05h does not (a delta of the spreading width
+    # 0.6h would miss the first band)
+    X = (0.41 + 0.3 / 32, 0.25 + 0.2 / 32)
+    h = 1.0 / 32
+
+    def band(lo, hi):
+        return lambda x, y: np.where((np.abs(x - X[0]) > lo * h) & (np.abs(x - X[0]) < hi * h),
+                                     1.0, 0.0)
+
+    zero = lambda x, y: np.zeros_like(x)   # noqa: E731
+    dX, _, c = advance_case(band(1.3, 1.9), zero, X)
+    assert dX[0] > 1e-3 * c and dX[1] == 0.0
+    dX, _, _ = advance_case(band(2.05, 100.0), zero, X)
+    assert dX[0] == 0.0 and dX[1] == 0.0
