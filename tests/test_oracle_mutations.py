@@ -8,8 +8,7 @@ same pins, so a failure is the planted mistake's."""
 import os
 import subprocess
 import sys
-
-import pytest
+from concurrent.futures import ThreadPoolExecutor
 
 from oracle import build as oracle_build
 from oracle import oracle as O
@@ -21,6 +20,7 @@ OPERATORS = "tests/test_oracle_operators.py"
 DELTA = "tests/test_oracle_delta.py"
 TRANSFER = "tests/test_oracle_transfer.py"
 FLOW = "tests/test_oracle_flow.py"
+RHS = "tests/test_oracle_rhs.py"
 
 MUTATIONS = {
     # Eq. NSdis1-1: the skew-symmetric advection is the mean of two halves
@@ -93,6 +93,16 @@ MUTATIONS = {
     "viscosity_amplitude_width": (
         "double coef = pow(2.0 * w, D) * (mu_max - mu_out);",
         "double coef = pow(w, D) * (mu_max - mu_out);", TRANSFER),
+    # Eq. NSdis1-1: rhs = (rho sigma / dt) u - rho Adv(u) + c_f f + G
+    "rhs_advection_without_density": (
+        "S->uvel[d][iF] - S->rho[d][iF] * adv +", "S->uvel[d][iF] - adv +", RHS),
+    "rhs_advection_sign": (
+        "S->uvel[d][iF] - S->rho[d][iF] * adv +", "S->uvel[d][iF] + S->rho[d][iF] * adv +", RHS),
+    "rhs_force_dropped": (
+        "                         S->P.c_force * S->frc[d][iF] + g;", "                         g;",
+        RHS),
+    "mass_without_sigma": (
+        "  double msc = S->P.sigma / S->P.dt;", "  double msc = 1.0 / S->P.dt;", RHS),
     "viscous_post_smoothing_skipped": (
         "  for (int d = 0; d < S->D; ++d) prolong_add_face(S, L, Lc, d, Lc->u[d], L->u[d]);\n"
         "  for (int it = 0; it < S->P.nu2; ++it) v_rbgs(S, l);",
@@ -107,10 +117,11 @@ def build_copy(src, out):
 
 
 def run_pins(lib, test_file):
-    env = dict(os.environ, **{O.OVERRIDE_ENV: str(lib)})
-    return subprocess.run([sys.executable, "-m", "pytest", test_file, "-x", "-q",
+    # one thread per child: the cases run side by side
+    env = dict(os.environ, **{O.OVERRIDE_ENV: str(lib), "OMP_NUM_THREADS": "1"})
+    return subprocess.run([sys.executable, "-m", "pytest", test_file, "-x", "-q", "-m", "not gpu",
                            "-p", "no:cacheprovider"], cwd=ROOT, env=env,
-                          capture_output=True, text=True, timeout=600)
+                          capture_output=True, text=True, timeout=900)
 
 
 def source():
@@ -118,25 +129,34 @@ def source():
         return f.read()
 
 
-def test_unchanged_copy_passes_the_pins(tmp_path):
-    src = tmp_path / "same.c"
-    src.write_text(source())
-    lib = tmp_path / "libsame.so"
+def run_case(tmp, name, text, test_files):
+    """Build `text` as a copy of the oracle and run the pin files against it:
+    (name, [(file, exit status, output tail)])."""
+    src = os.path.join(tmp, name + ".c")
+    with open(src, "w") as f:
+        f.write(text)
+    lib = os.path.join(tmp, "lib%s.so" % name)
     build_copy(src, lib)
-    for test_file in (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER, FLOW):
+    out = []
+    for test_file in test_files:
         r = run_pins(lib, test_file)
-        assert r.returncode == 0, r.stdout[-2000:]
+        out.append((test_file, r.returncode, r.stdout[-1500:]))
+    return name, out
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_fails_a_pin(tmp_path, name):
-    old, new, test_file = MUTATIONS[name]
+def test_planted_mistakes_fail_a_pin_and_the_unchanged_copy_passes(tmp_path):
     text = source()
-    assert text.count(old) == 1, "the mutation site is no longer unique"
-    src = tmp_path / (name + ".c")
-    src.write_text(text.replace(old, new))
-    lib = tmp_path / ("lib%s.so" % name)
-    build_copy(src, lib)
-    r = run_pins(lib, test_file)
-    assert r.returncode == 1, "no pin failed:\n" + r.stdout[-2000:]
-    assert "failed" in r.stdout
+    cases = [("unchanged", text, (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER, FLOW, RHS))]
+    for name in sorted(MUTATIONS):
+        old, new, test_file = MUTATIONS[name]
+        assert text.count(old) == 1, "%s: the mutation site is no longer unique" % name
+        cases.append((name, text.replace(old, new), (test_file,)))
+    workers = max(2, min(8, os.cpu_count() or 2))
+    with ThreadPoolExecutor(workers) as pool:
+        results = dict(pool.map(lambda c: run_case(str(tmp_path), *c), cases))
+    for test_file, rc, tail in results.pop("unchanged"):
+        assert rc == 0, "the unchanged copy fails %s:\n%s" % (test_file, tail)
+    escaped = [(name, tail) for name, runs in results.items()
+               for _, rc, tail in runs if rc != 1 or "failed" not in tail]
+    assert not escaped, "no pin failed for: %s\n%s" % ([e[0] for e in escaped],
+                                                      escaped[0][1] if escaped else "")
