@@ -89,6 +89,20 @@ MUTATIONS = {
         TRANSFER),
     "node_move_without_sigma": (
         "double c = P->dt / P->sigma;", "double c = P->dt;", TRANSFER),
+    # Eqs. discrForceCouple, discrDensCouple, ViscExp with the widths of
+    # Sec. 3.1: forces and density spread with omega, viscosity with omega_mu,
+    # the biofilm's density (rho_ratio - 1) rho_f on d0^D
+    "biofilm_density_without_d0": (
+        "amp[s] = rho_b * P->d0_vol;", "amp[s] = rho_b;", TRANSFER),
+    "biofilm_density_ratio": (
+        "double rho_b = (P->rho_ratio - 1.0) * P->rho_f;",
+        "double rho_b = P->rho_ratio * P->rho_f;", TRANSFER),
+    "viscosity_spread_with_omega": (
+        "spread_max(S, kind_cell(), L0->muc, P->omega_mu, P->mu_f, mu_max);",
+        "spread_max(S, kind_cell(), L0->muc, P->omega, P->mu_f, mu_max);", TRANSFER),
+    "force_spread_with_h": (
+        "spread_sum(S, kind_face(d), S->frc[d], &S->F[d], 3, P->omega);",
+        "spread_sum(S, kind_face(d), S->frc[d], &S->F[d], 3, P->h);", TRANSFER),
     # Eq. ViscExp: the viscosity bump's amplitude (2 w)^D (mu_max - mu_out)
     "viscosity_amplitude_width": (
         "double coef = pow(2.0 * w, D) * (mu_max - mu_out);",

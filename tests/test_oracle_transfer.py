@@ -8,6 +8,9 @@
 * Eq. (discrVelCouple) with phi1 and width h reproduces linear fields.
 * Eq. (ViscExp): mu = mu_max at a node lying on a grid point (Fig. 4 setup).
 * Eq. (springF), Eq. (defineK): two-node tension and the breaking rule.
+* A time step's spreads: the density adds the biofilm's mass eta (rho_ratio -
+  1) rho_f d0^D exactly (phi1, omega a multiple of h); forces reach 2 omega
+  and no further, the viscosity 2 omega_mu.
 * Sec. 3.4 with Eq. (discrVelCouple): a node moves by dt / sigma times the
   velocity interpolated with the width-h delta (a uniform flow moves it
   exactly; the velocity of faces 1.3h-1.9h away moves it, of faces beyond
@@ -278,3 +281,59 @@ def test_node_velocity_uses_the_width_h_support():
     assert dX[0] > 1e-3 * c and dX[1] == 0.0
     dX, _, _ = advance_case(band(2.05, 100.0), zero, X)
     assert dX[0] == 0.0 and dX[1] == 0.0
+
+
+# --------------------------------------------------------------------------
+# A time step's spreads (Eqs. discrForceCouple, discrDensCouple, ViscExp, with
+# the widths of Sec. 3.1): forces and density with omega, viscosity with
+# omega_mu; the biofilm's density rho_b = (rho_ratio - 1) rho_f on d0^D.
+H32 = 1.0 / 32
+
+
+def refreshed(**kw):
+    h = H32
+    prm = grid2(n=(32, 32), periodic=(1, 0), h=h, **kw)
+    o = O.Oracle(prm)
+    A = np.array([0.5 + 0.3 * h, 0.3 + 0.15 * h])
+    B = np.array([0.5 + 0.3 * h, 0.7 + 0.15 * h])   # 12.8 h away along y
+    o.set_nodes(np.array([A, B]))
+    # a stretched spring: a force of 3 (0.4 - 0.1) along y on each node
+    o.set_springs(np.array([[0, 1]]), np.array([0.1]), np.array([3.0]), np.array([100.0]))
+    o.refresh()
+    return o, prm, A, h
+
+
+def near_a(o, A, h, stag):
+    n, s = o.dims()
+    x = (np.arange(s[0]) + 0.5 * stag[0]) * h - A[0]
+    y = (np.arange(s[1]) + 0.5 * stag[1]) * h - A[1]
+    return np.meshgrid(np.abs(x), np.abs(y))
+
+
+def test_density_spread_adds_the_biofilm_mass():
+    # with phi1 and omega a multiple of h the discrete unity sum is exact:
+    # sum over each face grid of (rho_d - rho_f) h^2 = eta rho_b d0^2
+    o, prm, A, h = refreshed(phi_kind=1, omega=2 * H32, omega_mu=2 * H32, rho_ratio=2.5,
+                             d0_vol=0.7 * H32 * H32)
+    mass = 2 * (2.5 - 1.0) * prm["rho_f"] * prm["d0_vol"]
+    for d in range(2):
+        added = (o.get("rho", d) - prm["rho_f"]).sum() * h * h
+        assert abs(added - mass) <= 1e-13 * mass, (d, added, mass)
+    o.close()
+
+
+def test_forces_spread_with_omega_and_viscosity_with_omega_mu():
+    # omega = 2h: the force on A reaches y-faces 2.2h-3.8h away along x and
+    # nothing 4h or more away; omega_mu = h: the viscosity rises only within
+    # 2h of a node, so cells 2.2h-3.8h away along x keep mu_f exactly
+    o, prm, A, h = refreshed(omega=2 * H32, omega_mu=H32, mu_ratio=10.0)
+    fy = o.get("force", 1)
+    dx, dy = near_a(o, A, h, (1, 0))
+    band = (dx > 2.2 * h) & (dx < 3.8 * h) & (dy < h)
+    assert np.abs(fy[band]).max() > 0.0
+    assert np.all(fy[(dx >= 4 * h) & (dy < 5 * h)] == 0.0)
+    mc = o.get("muc")
+    dx, dy = near_a(o, A, h, (1, 1))
+    assert mc[(dx < 0.5 * h) & (dy < 0.5 * h)].min() > prm["mu_f"]
+    assert np.all(mc[(dx > 2.2 * h) & (dx < 3.8 * h) & (dy < h)] == prm["mu_f"])
+    o.close()
