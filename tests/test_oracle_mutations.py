@@ -87,6 +87,9 @@ MUTATIONS = {
         "S->U[3 * s + d] = interp_one(S, kind_face(d), S->uvel[d], &S->X[3 * s], P->h);",
         "S->U[3 * s + d] = interp_one(S, kind_face(d), S->uvel[d], &S->X[3 * s], P->omega);",
         TRANSFER),
+    "nodes_moved_before_the_projection": (
+        "    project(S);\n    interp_advance(S);", "    interp_advance(S);\n    project(S);",
+        TRANSFER),
     "node_move_without_sigma": (
         "double c = P->dt / P->sigma;", "double c = P->dt;", TRANSFER),
     # Eqs. discrForceCouple, discrDensCouple, ViscExp with the widths of

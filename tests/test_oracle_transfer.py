@@ -14,7 +14,8 @@
 * Sec. 3.4 with Eq. (discrVelCouple): a node moves by dt / sigma times the
   velocity interpolated with the width-h delta (a uniform flow moves it
   exactly; the velocity of faces 1.3h-1.9h away moves it, of faces beyond
-  2h does not).
+  2h does not), and a whole step moves it with the velocity its projection
+  leaves, interpolated at the old position.
 """
 import json
 import math
@@ -336,4 +337,32 @@ def test_forces_spread_with_omega_and_viscosity_with_omega_mu():
     dx, dy = near_a(o, A, h, (1, 1))
     assert mc[(dx < 0.5 * h) & (dy < 0.5 * h)].min() > prm["mu_f"]
     assert np.all(mc[(dx > 2.2 * h) & (dx < 3.8 * h) & (dy < h)] == prm["mu_f"])
+    o.close()
+
+
+def test_a_step_moves_the_nodes_with_its_projected_velocity():
+    # Sec. 3.4's order: the nodes move with u^{n+1}, the velocity the step's
+    # projection leaves, interpolated at X^n (the c1 mound: its density and
+    # viscosity change the flow within the step, so u^{n+1} != u^n)
+    inst = W.c1()
+    o = O.Oracle(inst["params"])
+    o.set_nodes(inst["X"])
+    o.set_springs(inst["ab"], inst["rest"], inst["K"], inst["brk"])
+    o.step(1)
+    u_before = [o.get("u", d) for d in range(2)]
+    X0 = o.nodes()
+    o.step(1)
+    u1 = [o.get("u", d) for d in range(2)]
+    assert max(np.abs(a - b).max() for a, b in zip(u1, u_before)) > 1e-6
+    prm = inst["params"]
+    at_x0 = O.Oracle(prm)   # the interpolation evaluates at an instance's own nodes
+    at_x0.set_nodes(X0)
+    for d in range(2):
+        step = prm["dt"] / prm["sigma"] * at_x0.interp(O.KIND_FACE[d], u1[d], prm["h"])
+        moved = o.nodes()[:, d] - X0[:, d]
+        Lx = prm["n"][d] * prm["h"]
+        if prm["periodic"][d]:   # across the periodic seam
+            moved = (moved + 0.5 * Lx) % Lx - 0.5 * Lx
+        assert np.allclose(moved, step, rtol=0, atol=1e-15), d
+    at_x0.close()
     o.close()
