@@ -135,3 +135,19 @@ def test_divergence_target_holds_after_every_projection():
     assert max(divs[0.0]) > 1e-10
     assert max(divs[1e-10]) <= 1e-10
     assert sum(cyc[1e-10]) > sum(cyc[0.0])
+
+
+def test_divergence_target_holds_with_sigma_and_euler_not_one():
+    # the pressure solve's second test scales max |r_p| by euler dt / sigma,
+    # the factor of the projection (Eq. NSdis2 - NSdis4); with euler / sigma =
+    # 80 a test without it stops too early and leaves max |D.u| above div_tol
+    c = W.c1()
+    prm = dict(c["params"], vc_visc=0, vc_p=0, rtol=1e-9, max_cycles=100, div_tol=1e-10,
+               sigma=0.5, euler=40.0)
+    o = O.Oracle(prm)
+    o.set_nodes(c["X"])
+    o.set_springs(c["ab"], c["rest"], c["K"], c["brk"])
+    for _ in range(3):
+        o.step(1)
+        assert o.stats()["div_max"] <= 1e-10
+    o.close()

@@ -72,6 +72,10 @@ MUTATIONS = {
     "divergence_scale_inverted": (
         "double sc = S->P.sigma / S->P.euler / S->P.dt;",
         "double sc = S->P.euler / S->P.sigma / S->P.dt;", FLOW),
+    # the pressure solve's divergence test: (euler dt / sigma) max |r_p|
+    "divergence_test_without_euler_over_sigma": (
+        "  double dscale = S->P.euler * S->P.dt / S->P.sigma;\n  for (cyc = 1; cyc <= maxc; ++cyc) {",
+        "  double dscale = S->P.dt;\n  for (cyc = 1; cyc <= maxc; ++cyc) {", FLOW),
     # Sec. 3.5, the V-cycle: the coarse correction starts from zero, the
     # coarse right-hand side is the restricted residual, and the correction
     # is smoothed after it is added
