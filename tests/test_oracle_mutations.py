@@ -110,6 +110,13 @@ MUTATIONS = {
     "force_spread_with_h": (
         "spread_sum(S, kind_face(d), S->frc[d], &S->F[d], 3, P->omega);",
         "spread_sum(S, kind_face(d), S->frc[d], &S->F[d], 3, P->h);", TRANSFER),
+    # grid points beyond a wall do not exist: the kernel is cut there
+    "kernel_folded_onto_the_wall": (
+        "  if (i < 0 || i > hi) return -1;\n  return i;",
+        "  if (i < 0) i = 0;\n  if (i > hi) i = hi;\n  return i;", TRANSFER),
+    "cell_point_beyond_the_top_wall_kept": (
+        "  int hi = g.stag[a] ? L->n[a] - 1 : L->n[a];", "  int hi = g.stag[a] ? L->n[a] : L->n[a];",
+        TRANSFER),
     # Eq. ViscExp: the viscosity bump's amplitude (2 w)^D (mu_max - mu_out)
     "viscosity_amplitude_width": (
         "double coef = pow(2.0 * w, D) * (mu_max - mu_out);",

@@ -10,7 +10,8 @@
 * Eq. (springF), Eq. (defineK): two-node tension and the breaking rule.
 * A time step's spreads: the density adds the biofilm's mass eta (rho_ratio -
   1) rho_f d0^D exactly (phi1, omega a multiple of h); forces reach 2 omega
-  and no further, the viscosity 2 omega_mu.
+  and no further, the viscosity 2 omega_mu; near a wall the kernel beyond it
+  is dropped, the same at both walls.
 * Sec. 3.4 with Eq. (discrVelCouple): a node moves by dt / sigma times the
   velocity interpolated with the width-h delta (a uniform flow moves it
   exactly; the velocity of faces 1.3h-1.9h away moves it, of faces beyond
@@ -366,3 +367,25 @@ def test_a_step_moves_the_nodes_with_its_projected_velocity():
         assert np.allclose(moved, step, rtol=0, atol=1e-15), d
     at_x0.close()
     o.close()
+
+
+def test_spreads_drop_the_kernel_beyond_a_wall():
+    # grid points beyond a wall do not exist: a node 0.3h from the bottom wall
+    # loses the kernel mass beyond it, and by the grid's mirror symmetry a
+    # node 0.3h from the top wall loses the same (phi1, omega = 2h, where a
+    # node away from the walls adds the whole mass)
+    h = H32
+    prm = grid2(n=(32, 32), periodic=(1, 0), h=h, phi_kind=1, omega=2 * h, omega_mu=2 * h,
+                rho_ratio=2.5, d0_vol=0.7 * h * h)
+    full = (2.5 - 1.0) * prm["rho_f"] * prm["d0_vol"]
+    added = {}
+    for where, Y in (("bottom", 0.3 * h), ("top", 1.0 - 0.3 * h)):
+        o = O.Oracle(prm)
+        o.set_nodes(np.array([[0.5 + 0.3 * h, Y]]))
+        o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+        o.refresh()
+        added[where] = [(o.get("rho", d) - prm["rho_f"]).sum() * h * h for d in range(2)]
+        o.close()
+    for d in range(2):
+        assert abs(added["bottom"][d] - added["top"][d]) <= 1e-13 * full, d
+        assert added["bottom"][d] < 0.9 * full, d
