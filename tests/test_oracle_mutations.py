@@ -110,6 +110,14 @@ MUTATIONS = {
     "force_spread_with_h": (
         "spread_sum(S, kind_face(d), S->frc[d], &S->F[d], 3, P->omega);",
         "spread_sum(S, kind_face(d), S->frc[d], &S->F[d], 3, P->h);", TRANSFER),
+    # the edge viscosities spread on the edge grid; a node carried past a
+    # wall stops on it and is counted
+    "edge_viscosity_on_the_cell_grid": (
+        "spread_max(S, kind_edge(d, e), me, P->omega_mu, P->mu_f, mu_max);",
+        "spread_max(S, kind_cell(), me, P->omega_mu, P->mu_f, mu_max);", TRANSFER),
+    "node_reflected_at_the_wall": (
+        "        if (x < 0.0) { x = 0.0; S->st.clamped_total++; }",
+        "        if (x < 0.0) { x = -x; S->st.clamped_total++; }", TRANSFER),
     # grid points beyond a wall do not exist: the kernel is cut there
     "kernel_folded_onto_the_wall": (
         "  if (i < 0 || i > hi) return -1;\n  return i;",

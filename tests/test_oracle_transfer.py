@@ -16,7 +16,10 @@
   velocity interpolated with the width-h delta (a uniform flow moves it
   exactly; the velocity of faces 1.3h-1.9h away moves it, of faces beyond
   2h does not), and a whole step moves it with the velocity its projection
-  leaves, interpolated at the old position.
+  leaves, interpolated at the old position; a node carried past a wall stops
+  on it and is counted.
+* A step's viscosity spread: a node on a cell centre or on a corner sets
+  mu_c or mu_e there to mu_max.
 """
 import json
 import math
@@ -389,3 +392,43 @@ def test_spreads_drop_the_kernel_beyond_a_wall():
     for d in range(2):
         assert abs(added["bottom"][d] - added["top"][d]) <= 1e-13 * full, d
         assert added["bottom"][d] < 0.9 * full, d
+
+
+def test_a_step_spreads_viscosity_on_centres_and_edges():
+    # Eq. ViscExp at a node on a grid point of a kind gives mu_max there: a
+    # node on a cell centre sets mu_c there to mu_max, a node on a corner
+    # (the 2D edge grid) sets mu_e there to mu_max
+    h = H32
+    for kind, X, field in (("centre", (16.5 * h, 9.5 * h), "muc"), ("edge", (16 * h, 9 * h), "mue")):
+        prm = grid2(n=(32, 32), periodic=(1, 0), h=h, omega=1.5 * h, omega_mu=1.5 * h,
+                    mu_ratio=50.0)
+        o = O.Oracle(prm)
+        o.set_nodes(np.array([X]))
+        o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+        o.refresh()
+        mu = o.get(field, 0)
+        mu_max = prm["mu_f"] * prm["mu_ratio"]
+        assert abs(mu[9, 16] - mu_max) <= 1e-13 * mu_max, kind
+        o.close()
+
+
+def test_a_node_leaving_through_a_wall_is_clamped_onto_it_and_counted():
+    # a strong flow into the bottom wall would carry the node 0.2h from it
+    # past the wall: it stops on the wall, and the step counts it
+    h = 1.0 / 32
+    prm = grid2(h=h, sigma=0.5, dt=0.003, omega=0.6 * h, omega_mu=0.6 * h)
+    o = O.Oracle(prm)
+    X = np.array([[0.5 + 0.3 * h, 0.2 * h]])
+    o.set_nodes(X)
+    o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+    n, s = o.dims()
+    o.set("u", np.zeros(o.shape()), 0)
+    vy = np.full(o.shape(), -10.0)
+    vy[0, :] = 0.0     # the wall faces
+    vy[n[1]:, :] = 0.0
+    o.set("u", vy, 1)
+    o.stage("interp_advance")
+    Y = o.nodes()[0]
+    assert Y[0] == X[0, 0] and Y[1] == 0.0
+    assert o.stats()["clamped_total"] == 1
+    o.close()
