@@ -21,6 +21,7 @@ DELTA = "tests/test_oracle_delta.py"
 TRANSFER = "tests/test_oracle_transfer.py"
 FLOW = "tests/test_oracle_flow.py"
 RHS = "tests/test_oracle_rhs.py"
+OPEN = "tests/test_oracle_open.py"
 
 MUTATIONS = {
     # Eq. NSdis1-1: the skew-symmetric advection is the mean of two halves
@@ -118,6 +119,17 @@ MUTATIONS = {
     "node_reflected_at_the_wall": (
         "        if (x < 0.0) { x = 0.0; S->st.clamped_total++; }",
         "        if (x < 0.0) { x = -x; S->st.clamped_total++; }", TRANSFER),
+    # the open duct of Sec. 3.6: du/dn = 0 beyond the outflow (even ghosts in
+    # the restriction and the prolongation), the pressure held at kappa L
+    "outflow_restriction_without_the_even_ghost": (
+        "              if (d == S->open && q > nf) q = nf - 1;   /* even ghost beyond the outflow */",
+        "              if (d == S->open && q > nf) q = nf;", OPEN),
+    "outflow_tangential_prolongation_odd": (
+        "                                     a == S->open ? 1.0 : -1.0, idx[a], w[a]);",
+        "                                     -1.0, idx[a], w[a]);", OPEN),
+    "outflow_pressure_sign": (
+        "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);",
+        "      S->p_out = S->G / P->euler * (P->n[fa] * P->h);", OPEN),
     # grid points beyond a wall do not exist: the kernel is cut there
     "kernel_folded_onto_the_wall": (
         "  if (i < 0 || i > hi) return -1;\n  return i;",
@@ -182,7 +194,8 @@ def run_case(tmp, name, text, test_files):
 
 def test_planted_mistakes_fail_a_pin_and_the_unchanged_copy_passes(tmp_path):
     text = source()
-    cases = [("unchanged", text, (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER, FLOW, RHS))]
+    cases = [("unchanged", text, (ADVECTION, MULTIGRID, OPERATORS, DELTA, TRANSFER, FLOW, RHS,
+                                  OPEN))]
     for name in sorted(MUTATIONS):
         old, new, test_file = MUTATIONS[name]
         assert text.count(old) == 1, "%s: the mutation site is no longer unique" % name

@@ -17,6 +17,10 @@ takes.
 * Converged multigrid equals a dense solve, on tiny grids in 2D and 3D, for
   both operators; the pressure V(2,2) cycle contracts by at most 0.1 per
   cycle, independently of h.
+* Along the flow axis the face restriction takes the even ghost beyond the
+  outflow (a field even about it restricts in closed form), a tangential
+  component prolongs evenly there and oddly at the inflow, and the pressure
+  falls from about 0 at the inflow to the held p_out = kappa L < 0.
 * A biofilm-free duct started from the laminar profile develops towards it
   at the outflow as h falls. This scheme does not keep the laminar state to
   rounding: its pressure correction is not incremental, so a uniform
@@ -260,3 +264,57 @@ def test_open_pressure_vcycle_contraction(n):
     set_coefficients(o)
     f = _p_factors(o)
     assert f[2:].max() <= 0.1, f
+
+
+def test_face_restriction_takes_the_even_ghost_beyond_the_outflow():
+    # along the flow axis a field even about the outflow face, (x - L)^2,
+    # restricts with weights (1/4, 1/2, 1/4) to (X - L)^2 + h^2 / 2 on every
+    # coarse face, the outflow face included, where the third fine face is
+    # the ghost beyond the outflow (h the fine spacing)
+    o = chan(16)
+    h = o.prm["h"]
+    L = o.prm["n"][0] * h
+    n, s = o.dims()
+    x = np.arange(s[0]) * h
+    fine = np.tile((x - L) ** 2, (s[1], 1))
+    coarse = o.restrict(fine, 0, 0)
+    nc, _ = o.dims(1)
+    X = np.arange(nc[0] + 1) * 2 * h
+    for j in range(nc[1]):
+        assert np.allclose(coarse[j, 1:nc[0] + 1], (X[1:] - L) ** 2 + h * h / 2,
+                           rtol=0, atol=1e-15)
+    o.close()
+
+
+def test_tangential_velocity_prolongs_evenly_beyond_the_outflow():
+    # a coarse constant of the tangential component (u_y: cell-centred along
+    # the flow axis) prolongs to the constant in the last fine column (the
+    # even ghost of du/dn = 0), and to half of it in the first (odd at the
+    # inflow, where the velocity is prescribed)
+    o = chan(16)
+    n, s = o.dims()
+    nc, sc = o.dims(1)
+    coarse = np.zeros(o.shape(1))
+    coarse[1:nc[1], :nc[0]] = 1.0      # the unknown y-faces of the coarse grid
+    fine = o.prolong_add(coarse, np.zeros(o.shape()), 0, 1)
+    rows = slice(2, n[1] - 1)            # y-faces coarse-coincident or between two of them
+    assert np.all(fine[rows, n[0] - 1] == 1.0)
+    assert np.all(fine[rows, 0] == 0.5)
+    o.close()
+
+
+def test_pressure_is_held_at_the_outflow_and_falls_from_zero_at_the_inflow():
+    # Eq. pressLam with eps kappa = -G and p(0) = 0: the pressure falls along
+    # the flow from about 0 at the inflow to p_out = kappa L < 0 at the outflow
+    o = chan(16, vc_visc=0, vc_p=0, rtol=1e-12, max_cycles=200)
+    no_nodes(o)
+    o.step(2)
+    p_out = o.outflow_pressure()
+    assert p_out < 0.0
+    p = o.get("p")
+    n, _ = o.dims()
+    first, last = p[1:n[1] - 1, 0].mean(), p[1:n[1] - 1, n[0] - 1].mean()
+    assert abs(first) < 0.2 * abs(p_out)
+    assert abs(last - p_out) < 0.1 * abs(p_out)
+    assert first > last
+    o.close()
