@@ -130,6 +130,24 @@ MUTATIONS = {
     "outflow_pressure_sign": (
         "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);",
         "      S->p_out = S->G / P->euler * (P->n[fa] * P->h);", OPEN),
+    # 3D: the spring length takes all three axes, every edge grid gets its
+    # viscosity, and the max-spread's z kernel sits on the grid's own stagger
+    "spring_length_without_z": (
+        "    len2 = len2 + dv[2] * dv[2];", "    len2 = len2;", TRANSFER),
+    "yz_edge_viscosity_not_spread": (
+        "    for (int e = d + 1; e < D; ++e) {", "    for (int e = d + 1; e < D - (d == 1); ++e) {",
+        TRANSFER),
+    "viscosity_z_kernel_stagger": (
+        "    const double* X = &S->X[3 * s];\n    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};\n"
+        "    for (int ax = 0; ax < D; ++ax) support(L, g, ax, X[ax], w, &lo[ax], &hi[ax]);\n"
+        "    for (int k = lo[2]; k <= hi[2]; ++k) {\n      int kk = 0; double pz = 1.0;\n"
+        "      if (D == 3) {\n        kk = kind_index(S, L, g, 2, k);\n        if (kk < 0) continue;\n"
+        "        pz = phi(kind, ((k + 0.5 * g.stag[2]) * L->h - X[2]) / w);",
+        "    const double* X = &S->X[3 * s];\n    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};\n"
+        "    for (int ax = 0; ax < D; ++ax) support(L, g, ax, X[ax], w, &lo[ax], &hi[ax]);\n"
+        "    for (int k = lo[2]; k <= hi[2]; ++k) {\n      int kk = 0; double pz = 1.0;\n"
+        "      if (D == 3) {\n        kk = kind_index(S, L, g, 2, k);\n        if (kk < 0) continue;\n"
+        "        pz = phi(kind, ((k + 0.5 * g.stag[1]) * L->h - X[2]) / w);", TRANSFER),
     # grid points beyond a wall do not exist: the kernel is cut there
     "kernel_folded_onto_the_wall": (
         "  if (i < 0 || i > hi) return -1;\n  return i;",

@@ -19,7 +19,9 @@
   leaves, interpolated at the old position; a node carried past a wall stops
   on it and is counted.
 * A step's viscosity spread: a node on a cell centre or on a corner sets
-  mu_c or mu_e there to mu_max.
+  mu_c or mu_e there to mu_max, in 2D and on every grid of 3D; in 3D a spring
+  stretched along all three axes pulls along its separation and breaks on
+  its whole length.
 """
 import json
 import math
@@ -432,3 +434,46 @@ def test_a_node_leaving_through_a_wall_is_clamped_onto_it_and_counted():
     assert Y[0] == X[0, 0] and Y[1] == 0.0
     assert o.stats()["clamped_total"] == 1
     o.close()
+
+
+def test_spring_tension_and_break_in_3d():
+    # a spring stretched along every axis of a 3D grid: the tension of Eq.
+    # (springF) along the separation, and a break once the whole length
+    # passes (1 + eps_b) r, whatever axis carries the stretch
+    prm = grid3()
+    d = np.array([0.02, 0.03, 0.06])   # length 0.07
+    for rest, brk, broken in ((0.05, 1.0, False), (0.05, 0.3, True)):
+        o = O.Oracle(prm)
+        X = np.array([[0.4, 0.45, 0.5], [0.4, 0.45, 0.5] + d])
+        o.set_nodes(X)
+        o.set_springs(np.array([[0, 1]]), np.array([rest]), np.array([2.0]), np.array([brk]))
+        o.refresh()
+        F = o.node_forces()
+        if broken:   # 0.07 > 1.3 * 0.05
+            assert len(o.broken()[0]) == 1 and np.all(F == 0.0)
+        else:
+            T = 2.0 * (0.07 - rest)
+            assert np.allclose(F[0], T * d / 0.07, rtol=0, atol=1e-15)
+            assert np.allclose(F[1], -T * d / 0.07, rtol=0, atol=1e-15)
+        o.close()
+
+
+def test_a_step_spreads_viscosity_on_every_3d_grid():
+    # Eq. ViscExp in 3D: a node on a point of the centre grid or of one of
+    # the three edge grids sets mu there to mu_max
+    h = 1.0 / 8
+    mu_max = 0.01 * 50.0
+    # grid point (i, j, k) of each kind: coordinates i h + s_x h / 2 per axis
+    kinds = {"muc": (None, (1, 1, 1)), "mue_xy": (0, (0, 0, 1)), "mue_xz": (1, (0, 1, 0)),
+             "mue_yz": (2, (1, 0, 0))}
+    for name, (e, stag) in kinds.items():
+        prm = grid3(h=h, omega=1.5 * h, omega_mu=1.5 * h, mu_ratio=50.0)
+        o = O.Oracle(prm)
+        ijk = (4, 3, 8)
+        X = [(ijk[a] + 0.5 * stag[a]) * h for a in range(3)]
+        o.set_nodes(np.array([X]))
+        o.set_springs(np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), np.zeros(0))
+        o.refresh()
+        mu = o.get("muc") if e is None else o.get("mue", e)
+        assert abs(mu[ijk[2], ijk[1], ijk[0]] - mu_max) <= 1e-13 * mu_max, name
+        o.close()
