@@ -151,3 +151,16 @@ def test_divergence_target_holds_with_sigma_and_euler_not_one():
         o.step(1)
         assert o.stats()["div_max"] <= 1e-10
     o.close()
+
+
+def test_initial_velocity_is_the_laminar_profile_times_ic_scale():
+    # reading 4: u^0 = ic_scale x the laminar profile, whatever the scale
+    c = W.c1()
+    u = {}
+    for scale in (1.0, 0.5):
+        o = O.Oracle(dict(c["params"], ic_scale=scale))
+        u[scale] = [o.get("u", d) for d in range(2)]
+        o.close()
+    assert np.abs(u[1.0][0]).max() > 0.0
+    for d in range(2):
+        assert np.array_equal(u[0.5][d], 0.5 * u[1.0][d])

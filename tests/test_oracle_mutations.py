@@ -73,6 +73,10 @@ MUTATIONS = {
     "divergence_scale_inverted": (
         "double sc = S->P.sigma / S->P.euler / S->P.dt;",
         "double sc = S->P.euler / S->P.sigma / S->P.dt;", FLOW),
+    # reading 4: the initial velocity is ic_scale times the laminar profile
+    "initial_velocity_without_ic_scale": (
+        "        col[(long)b * n0 + a] = P->ic_scale * S->G / (P->inv_re * P->mu_f) * laminar_unit(S, y);",
+        "        col[(long)b * n0 + a] = S->G / (P->inv_re * P->mu_f) * laminar_unit(S, y);", FLOW),
     # the pressure solve's divergence test: (euler dt / sigma) max |r_p|
     "divergence_test_without_euler_over_sigma": (
         "  double dscale = S->P.euler * S->P.dt / S->P.sigma;\n  for (cyc = 1; cyc <= maxc; ++cyc) {",
