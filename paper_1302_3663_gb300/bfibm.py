@@ -174,6 +174,18 @@ def _dp(a):
     return a.ctypes.data_as(_DP)
 
 
+def _out(out, shape):
+    """A caller's output buffer, checked before the library writes into it
+    (a wrong one would be written past its end), or a new one."""
+    if out is None:
+        return np.empty(shape)
+    if (not isinstance(out, np.ndarray) or out.dtype != np.float64 or
+            not out.flags.c_contiguous or not out.flags.writeable or tuple(out.shape) != tuple(shape)):
+        raise ValueError("out must be a writeable C-contiguous float64 array of shape %s"
+                         % (tuple(shape),))
+    return out
+
+
 def footprint(prm, eta=0, nsprings=0):
     out = _L(0)
     P = make_params(prm)
@@ -283,17 +295,17 @@ class Context:
         return self._chk(self.lib.bfibm_step(self.h, int(n)), "bfibm_step", (OK, ENOCONV))
 
     def get_velocity(self, comp, out=None):
-        out = np.empty(self.shape()) if out is None else out
+        out = _out(out, self.shape())
         self._chk(self.lib.bfibm_get_velocity(self.h, comp, _dp(out)), "bfibm_get_velocity")
         return out
 
     def get_pressure(self, out=None):
-        out = np.empty(self.shape()) if out is None else out
+        out = _out(out, self.shape())
         self._chk(self.lib.bfibm_get_pressure(self.h, _dp(out)), "bfibm_get_pressure")
         return out
 
     def get_nodes(self, out=None):
-        out = np.empty((self.eta, self.dim)) if out is None else out
+        out = _out(out, (self.eta, self.dim))
         self._chk(self.lib.bfibm_get_nodes(self.h, _dp(out)), "bfibm_get_nodes")
         return out
 

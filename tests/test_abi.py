@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1302_3663_gb300 import bfibm, workloads as W
@@ -60,3 +61,18 @@ def test_grids_beyond_32_bit_offsets_are_refused():
         bfibm.footprint(big)
     assert e.value.status == bfibm.EINVAL
     assert bfibm.footprint(dict(prm, n=[1024, 1024, 1024]), 0, 0) > 0
+
+
+def test_output_buffers_are_checked_before_the_library_writes():
+    out = bfibm._out(None, (3, 4))
+    assert out.shape == (3, 4) and out.dtype == np.float64
+    good = np.zeros((3, 4))
+    assert bfibm._out(good, (3, 4)) is good
+    for bad in (np.zeros((4, 3)), np.zeros((3, 4), np.float32), np.zeros((4, 3)).T,
+                np.zeros(12), [[0.0] * 4] * 3):
+        with pytest.raises(ValueError):
+            bfibm._out(bad, (3, 4))
+    ro = np.zeros((3, 4))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        bfibm._out(ro, (3, 4))
