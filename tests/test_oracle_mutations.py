@@ -123,6 +123,19 @@ MUTATIONS = {
     "node_reflected_at_the_wall": (
         "        if (x < 0.0) { x = 0.0; S->st.clamped_total++; }",
         "        if (x < 0.0) { x = -x; S->st.clamped_total++; }", TRANSFER),
+    # no-slip walls: no pressure flux through them, the tangential velocity's
+    # odd mirror ghost at both, and its doubled diagonal weight
+    "pressure_flux_through_the_top_wall": (
+        "    if (per || c[a] < L->n[a] - 1) {", "    if (per || c[a] < L->n[a]) {", FLOW),
+    "tangential_ghost_even_at_the_bottom_wall": (
+        "  if (q < 0) { c[e] = 0; return -ud[LIc(L, c)]; }",
+        "  if (q < 0) { c[e] = 0; return ud[LIc(L, c)]; }", FLOW),
+    "tangential_ghost_zero_at_the_top_wall": (
+        "  if (q >= L->n[e]) { c[e] = L->n[e] - 1; return -ud[LIc(L, c)]; }",
+        "  if (q >= L->n[e]) { c[e] = L->n[e] - 1; return 0.0; }", FLOW),
+    "wall_diagonal_weight_not_doubled": (
+        "      double wgt = (e == S->open && q == ne) ? 0.0 : (wall ? 2.0 : 1.0);",
+        "      double wgt = (e == S->open && q == ne) ? 0.0 : (wall ? 1.0 : 1.0);", OPERATORS),
     # the open duct of Sec. 3.6: du/dn = 0 beyond the outflow (even ghosts in
     # the restriction and the prolongation), the pressure held at kappa L
     "outflow_restriction_without_the_even_ghost": (
