@@ -144,6 +144,9 @@ MUTATIONS = {
     "outflow_tangential_prolongation_odd": (
         "                                     a == S->open ? 1.0 : -1.0, idx[a], w[a]);",
         "                                     -1.0, idx[a], w[a]);", OPEN),
+    "outflow_advecting_velocity_past_the_ghost": (
+        "  a1[d] = (d == S->open && F[d] == nd) ? nd - 1 : F[d];   /* even ghost beyond the outflow */",
+        "  a1[d] = (d == S->open && F[d] == nd) ? nd : F[d];", OPEN),
     "outflow_pressure_sign": (
         "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);",
         "      S->p_out = S->G / P->euler * (P->n[fa] * P->h);", OPEN),

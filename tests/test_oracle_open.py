@@ -20,7 +20,9 @@ takes.
 * Along the flow axis the face restriction takes the even ghost beyond the
   outflow (a field even about it restricts in closed form), a tangential
   component prolongs evenly there and oddly at the inflow, and the pressure
-  falls from about 0 at the inflow to the held p_out = kappa L < 0.
+  falls from about 0 at the inflow to the held p_out = kappa L < 0; a field
+  uniform along the flow has the same advection at the outflow face as at
+  the face before it.
 * A biofilm-free duct started from the laminar profile develops towards it
   at the outflow as h falls. This scheme does not keep the laminar state to
   rounding: its pressure correction is not incremental, so a uniform
@@ -317,4 +319,27 @@ def test_pressure_is_held_at_the_outflow_and_falls_from_zero_at_the_inflow():
     assert abs(first) < 0.2 * abs(p_out)
     assert abs(last - p_out) < 0.1 * abs(p_out)
     assert first > last
+    o.close()
+
+
+def test_advection_at_the_outflow_face_sees_even_ghosts():
+    # du/dn = 0 beyond the outflow: for a field that does not vary along the
+    # flow axis, the advection of the outflow face equals that of the face
+    # before it, term for term (the values beyond the outflow are the even
+    # ghosts of the last cells, never the storage past them)
+    o = chan(16)
+    h = o.prm["h"]
+    n, s = o.dims()
+    y_c = (np.arange(s[1]) + 0.5) * h    # x-faces: cell-centred along y
+    y_f = np.arange(s[1]) * h            # y-faces: face-centred along y
+    H = n[1] * h
+    ux = np.tile((np.sin(np.pi * y_c / H) + 0.3)[:, None], (1, s[0]))
+    uy = np.tile((np.sin(2 * np.pi * y_f / H) * 0.4)[:, None], (1, s[0]))
+    uy[0, :] = 0.0                       # the wall faces
+    uy[n[1]:, :] = 0.0
+    uy[:, n[0]:] = 7.0                   # storage past the last cell along x
+    A = o.advection([ux, uy])
+    rows = slice(0, n[1])
+    assert np.abs(A[0][rows, n[0] - 1]).max() > 0.0
+    assert np.array_equal(A[0][rows, n[0]], A[0][rows, n[0] - 1])
     o.close()
