@@ -147,6 +147,9 @@ MUTATIONS = {
     "outflow_advecting_velocity_past_the_ghost": (
         "  a1[d] = (d == S->open && F[d] == nd) ? nd - 1 : F[d];   /* even ghost beyond the outflow */",
         "  a1[d] = (d == S->open && F[d] == nd) ? nd : F[d];", OPEN),
+    "outflow_plane_edge_in_the_viscous_diagonal": (
+        "      double wgt = (e == S->open && q == ne) ? 0.0 : (wall ? 2.0 : 1.0);",
+        "      double wgt = (e == S->open && q == ne) ? 1.0 : (wall ? 2.0 : 1.0);", OPEN),
     "outflow_pressure_sign": (
         "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);",
         "      S->p_out = S->G / P->euler * (P->n[fa] * P->h);", OPEN),

@@ -22,7 +22,8 @@ takes.
   component prolongs evenly there and oddly at the inflow, and the pressure
   falls from about 0 at the inflow to the held p_out = kappa L < 0; a field
   uniform along the flow has the same advection at the outflow face as at
-  the face before it.
+  the face before it; next to and on the outflow the viscous diagonal is the
+  operator's own coefficient of the unknown.
 * A biofilm-free duct started from the laminar profile develops towards it
   at the outflow as h falls. This scheme does not keep the laminar state to
   rounding: its pressure correction is not incremental, so a uniform
@@ -342,4 +343,30 @@ def test_advection_at_the_outflow_face_sees_even_ghosts():
     rows = slice(0, n[1])
     assert np.abs(A[0][rows, n[0] - 1]).max() > 0.0
     assert np.array_equal(A[0][rows, n[0]], A[0][rows, n[0] - 1])
+    o.close()
+
+
+def test_viscous_diagonal_at_the_outflow_is_the_operator_s_own():
+    # the smoother divides by the diagonal: at the faces next to and on the
+    # outflow it must be the operator's own coefficient of the unknown (an
+    # edge on the outflow plane, whose ghost is the unknown itself, adds
+    # nothing to it)
+    o = chan(8)
+    rng = np.random.default_rng(4)
+    set_coefficients(o, rho_fn=lambda *X: 1.0 + rng.uniform(0, 1, size=X[0].shape),
+                     mu_fn=lambda *X: 0.01 * np.exp(rng.uniform(0, np.log(1e3), size=X[0].shape)))
+    n, s = o.dims()
+    checked = 0
+    for d in range(2):
+        m = open_face_mask(o, d)
+        for j in range(s[1]):
+            for i in range(max(0, n[0] - 2), s[0]):
+                if not m[j, i]:
+                    continue
+                e = [np.zeros(o.shape()) for _ in range(2)]
+                e[d][j, i] = 1.0
+                Ae = o.apply_visc(e)[d][j, i]
+                assert abs(o.visc_diag(0, d, i, j, 0) - Ae) < 1e-12 * abs(Ae), (d, i, j)
+                checked += 1
+    assert checked > 10
     o.close()
