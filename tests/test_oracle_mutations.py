@@ -61,6 +61,16 @@ MUTATIONS = {
     "phi2_period": (
         "if (a < 2.0) return 0.25 * (1.0 + cos(M_PI * r / 2.0));",
         "if (a < 2.0) return 0.25 * (1.0 + cos(M_PI * r / 2.2));", DELTA),
+    # Peskin's phi1 (both branches) and the cosine kernel's amplitude
+    "phi1_inner_branch_coefficient": (
+        "  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;",
+        "  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 3.9 * a * a)) / 8.0;", DELTA),
+    "phi1_outer_branch_sign": (
+        "  if (a < 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;",
+        "  if (a < 2.0) return (5.0 - 2.0 * a + sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;", DELTA),
+    "phi2_amplitude": (
+        "if (a < 2.0) return 0.25 * (1.0 + cos(M_PI * r / 2.0));",
+        "if (a < 2.0) return 0.3 * (1.0 + cos(M_PI * r / 2.0));", DELTA),
     # Eq. springF: Hookean tension on the stretch beyond the rest length
     "spring_tension_sign": (
         "double T = S->K[q] * (len - S->rest[q]);", "double T = S->K[q] * (len + S->rest[q]);",
