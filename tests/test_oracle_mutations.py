@@ -160,6 +160,12 @@ MUTATIONS = {
     "outflow_plane_edge_in_the_viscous_diagonal": (
         "      double wgt = (e == S->open && q == ne) ? 0.0 : (wall ? 2.0 : 1.0);",
         "      double wgt = (e == S->open && q == ne) ? 1.0 : (wall ? 2.0 : 1.0);", OPEN),
+    "inflow_scaled_by_ic_scale": (
+        "            double v = P->ic_scale != 0.0 ? col[(long)b * n0 + a] / P->ic_scale",
+        "            double v = P->ic_scale != 0.0 ? col[(long)b * n0 + a]", OPEN),
+    "open_duct_keeps_the_body_force": (
+        "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);\n      S->G = 0.0;",
+        "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);", OPEN),
     "outflow_pressure_sign": (
         "      S->p_out = -S->G / P->euler * (P->n[fa] * P->h);",
         "      S->p_out = S->G / P->euler * (P->n[fa] * P->h);", OPEN),

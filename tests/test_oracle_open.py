@@ -23,7 +23,8 @@ takes.
   falls from about 0 at the inflow to the held p_out = kappa L < 0; a field
   uniform along the flow has the same advection at the outflow face as at
   the face before it; next to and on the outflow the viscous diagonal is the
-  operator's own coefficient of the unknown.
+  operator's own coefficient of the unknown; the inflow holds the full
+  laminar profile whatever the initial velocity's scale.
 * A biofilm-free duct started from the laminar profile develops towards it
   at the outflow as h falls. This scheme does not keep the laminar state to
   rounding: its pressure correction is not incremental, so a uniform
@@ -370,3 +371,17 @@ def test_viscous_diagonal_at_the_outflow_is_the_operator_s_own():
                 checked += 1
     assert checked > 10
     o.close()
+
+
+def test_inflow_holds_the_full_laminar_profile_whatever_ic_scale():
+    # the initial velocity is ic_scale times the laminar profile, but the
+    # inflow face prescribes the profile itself (Sec. 3.6)
+    u = {}
+    for scale in (1.0, 0.5):
+        o = chan(16, ic_scale=scale)
+        u[scale] = o.get("u", 0)
+        o.close()
+    n = 32
+    assert np.abs(u[1.0][:, 0]).max() > 0.0
+    assert np.array_equal(u[0.5][:, 0], u[1.0][:, 0])           # the inflow face
+    assert np.array_equal(u[0.5][:, 1:n + 1], 0.5 * u[1.0][:, 1:n + 1])
